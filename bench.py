@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GN / LM PCG hot path on one GB300.
+
+Workload (headline): ARAP image warping on a 1024 x 1024 grid (3 unknowns per
+pixel, 64 seeded handles, weights 1 / 100), Gauss-Newton 20 outer x 20 PCG
+iterations, Jacobi preconditioner, matrix-free; one "step" is one whole GN
+solve from the same initial state.  Metric: PCG iterations per second over
+the whole solve (PCGInit, every PCG iteration, the outer updates and the
+energies included).  Secondary numbers in the same line: Poisson editing at
+1024 x 1024 x 4 and ARAP mesh deformation (icosphere level 7, LM 15 x 30),
+and the roofline of the matrix-free J^T J p kernel at 4096 x 4096 (working set
+beyond L2).
+
+Run:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank solves its own replica (no collective on the
+data path), value = all ranks' PCG iterations / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG iters/s and % HBM roofline; batched solves/s and p99 latency vs plain"
+UNIT = "PCG iters/s"
+W_BENCH, H_BENCH, HANDLES, OUTER, INNER = 1024, 1024, 64, 20, 20
+# algorithmic bytes per pixel (float32 planes, each touched once per launch)
+BYTES_APPLY_WARP = 68      # read r 12, M^-1 8, p_old 12, theta 4, UrShape 8; write p 12, q 12
+BYTES_UPDATE_WARP = 80     # read delta 12, p 12, r 12, q 12, M^-1 8; write delta 12, r 12
+L2_FLUSH_BYTES = 512 << 20
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("grid_kernels.cu", "opt_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1604_06525_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """dram bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    ent = d.get(kernel, {}).get(workload)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc or not self.tmp:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.tmp.flush()
+        with open(self.tmp.name) as f:
+            rows = [r.strip().split(",") for r in f if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(seconds_hint: float = 15.0):
+    """The FP64 oracle as it stands on a bounded sample of the workload: one GN
+    outer iteration (J assembly + 20 PCG iterations) of the 1024 x 1024 warp."""
+    import numpy as np
+    import oracle
+    from paper_1604_06525_gb300 import synth
+    prob = synth.warp_problem(W_BENCH, H_BENCH, HANDLES, seed=synth.BASE_SEED)
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    n_outer = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.gauss_newton(e, x, 1, INNER)
+        n_outer += 1
+        if time.perf_counter() - t0 >= seconds_hint or n_outer >= 4:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n_outer * INNER / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_outer} GN outer iteration(s) (explicit CSR J assembly + {INNER} PCG) of the "
+                      f"{W_BENCH}x{H_BENCH} ARAP warp, float64, numpy/scipy single thread"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    from paper_1604_06525_gb300 import synth
+    prob = synth.warp_problem(W_BENCH, H_BENCH, HANDLES, seed=synth.BASE_SEED)
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.gauss_newton(e, x, 1, INNER)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.gauss_newton(e, x, 1, INNER)
+        times.append(time.perf_counter() - t0)
+    ms = 1000.0 * sum(times) / len(times)
+    value = INNER / (ms / 1000.0)
+    sample = (f"each step: 1 GN outer iteration (explicit CSR J assembly + {INNER} PCG) of the "
+              f"{W_BENCH}x{H_BENCH} ARAP warp, float64 oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"ARAP image warping {W_BENCH}x{H_BENCH}, {HANDLES} handles, GN "
+                                   f"{OUTER}x{INNER} PCG (oracle sample: 1 outer x {INNER} PCG per step)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def roofline_for(api, synth, torch, W, H, peak, iters=20):
+    """Live timing of the matrix-free kernels on a W x H warp (CUDA events on
+    the launching stream, mean over `iters` launches)."""
+    prob = synth.warp_problem(W, H, max(8, int(round(64.0 * W * H / 2 ** 20))), seed=synth.BASE_SEED)
+    gp = api.Problem(prob)
+    gp.profile_pcg(3)
+    ms_init, ms_apply, ms_update = gp.profile_pcg(iters)
+    px = W * H
+    out = {}
+    for name, ms, bpp in (("k_warp_apply", ms_apply, BYTES_APPLY_WARP), ("k_grid_update", ms_update, BYTES_UPDATE_WARP)):
+        ach = bpp * px / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "bytes": bpp * px, "achieved": ach, "frac": ach / peak}
+    gp.close()
+    del prob
+    torch.cuda.empty_cache()
+    return out, ms_init
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_1604_06525_gb300 import build, api, synth
+    build.build()
+    api.load_library()
+    peak, peak_src = measured_peaks()
+    dev = torch.device("cuda", local)
+
+    prob = synth.warp_problem(W_BENCH, H_BENCH, HANDLES, seed=synth.BASE_SEED)
+    gp = api.Problem(prob)
+    x0 = gp.x.clone()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one_step():
+        flush.zero_()
+        gp.x.copy_(x0)
+        return gp.solve_gn(OUTER, INNER)
+
+    for _ in range(max(3, args.warmup)):
+        one_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    reps = []
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            reps.append(one_step())
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    dev_ms = sum(r["ms"] for r in reps)
+    t_max = dev_ms
+    if world > 1:
+        t = torch.tensor([dev_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    pcg_total = sum(r["pcg_done"] for r in reps) * world
+    value = pcg_total / (t_max / 1000.0)
+    ms_per_step = t_max / args.steps
+    E_final = reps[-1]["E_final"]
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # unknowns from pinned memory, the solve, D2H of the solution
+    host_in = x0.cpu().pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        gp.x.copy_(host_in, non_blocking=True)
+        r = gp.solve_gn(OUTER, INNER)
+        host_out.copy_(gp.x, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t1)
+    e2e_value = r["pcg_done"] / statistics.mean(e2e_times) * world
+    nbytes = host_in.numel() * 4
+
+    # roofline of the dominant kernel, timed live at the bench size and beyond L2
+    roof, _ = roofline_for(api, synth, torch, W_BENCH, H_BENCH, peak)
+    dom = max(roof, key=lambda k: roof[k]["ms"] * (1 if k == "k_warp_apply" else 1))
+    roof_big, _ = roofline_for(api, synth, torch, 4096, 4096, peak)
+
+    # secondary workloads (one solve each)
+    extra = {}
+    pp = synth.poisson_problem(W_BENCH, H_BENCH, seed=synth.BASE_SEED)
+    gpp = api.Problem(pp)
+    gpp.solve_gn(OUTER, INNER)
+    rr = [gpp.solve_gn(OUTER, INNER) for _ in range(3)]
+    extra["poisson_1024x1024x4_gn20x20"] = {"pcg_iters_per_s": OUTER * INNER / (statistics.median(r_["ms"] for r_ in rr) / 1e3),
+                                           "ms_per_solve": statistics.median(r_["ms"] for r_ in rr),
+                                           "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
+    gpp.close()
+    mp = synth.mesh_problem(7, seed=synth.BASE_SEED)
+    gmp = api.Problem(mp)
+    x0m = gmp.x.clone()
+    rr = []
+    for _ in range(3):
+        gmp.x.copy_(x0m)
+        rr.append(gmp.solve_lm(15, 30, lambda0=1e-3))
+    msm = statistics.median(r_["ms"] for r_ in rr)
+    extra["mesh_icosphere7_lm15x30"] = {"pcg_iters_per_s": rr[-1]["pcg_done"] / (msm / 1e3), "ms_per_solve": msm,
+                                       "accepted": rr[-1]["accepted"], "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
+    gmp.close()
+
+    launches_per_step = 2 + OUTER * (2 + 2 * INNER)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"ARAP image warping {W_BENCH}x{H_BENCH} (3 unknowns/pixel, {HANDLES} handles), "
+                               f"GN {OUTER} outer x {INNER} PCG, Jacobi, matrix-free, one CUDA graph per solve",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "flushed between steps (512 MB write)", "precision": "f32 vectors, f64 dots/energies",
+                   "E_final": E_final, "wall_s": wall},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": roof[dom]["achieved"], "peak": peak,
+                     "unit": "GB/s", "frac": roof[dom]["frac"],
+                     "traffic": ncu_traffic(dom, "warp1024"),
+                     "algorithmic_bytes_per_launch": roof[dom]["bytes"], "ms_per_launch": roof[dom]["ms"],
+                     "peak_source": f"{peak_src} hbm_gbs", "kernels": roof},
+        "roofline_4096": {"bound": "hbm", "peak": peak, "unit": "GB/s", "kernels": roof_big},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "also": extra,
+    }
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = oracle_sample()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    gp.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,230 @@
+/*
+ * opt_gb300.h -- C ABI of the GB300 (sm_103a) Gauss-Newton / Levenberg-Marquardt
+ * PCG solver for sum-of-squares energies E(x) = sum_r f_r(x)^2 (Sec. 2, Sec. 4).
+ *
+ * The shape follows the paper's split of a solve into define / plan / solve
+ * (Fig. 4 and Sec. 3 "API": compile, allocate and run are separate calls so
+ * that set-up is amortised over many solves).  The energy templates are fixed
+ * and hand-derived (no DSL): ARAP image warping (Fig. 24), Poisson image
+ * editing (Fig. 27) and ARAP mesh deformation (Fig. 25).
+ *
+ * Conventions for every call:
+ *  - Pointers named "device" point to CUDA global memory on the current
+ *    device; pointers named "host" point to host memory.  No call takes
+ *    ownership of a caller pointer.
+ *  - Unknown arrays are owned by the caller.  A call that evaluates at x reads
+ *    them when it starts; opt_solve_gn / opt_solve_lm write the solution back
+ *    into them when they finish.  Constant arrays (rest shape, guidance image,
+ *    mask, handles) are copied into the problem when it is created.
+ *  - The library owns its scratch (PCG vectors, reduction slots, CSR arrays)
+ *    and frees it in opt_problem_destroy.
+ *  - All device work is ordered on the stream given in opt_solve_params
+ *    (NULL = the legacy default stream).  Calls that return results to the
+ *    host synchronise that stream.  One problem must not be used from two
+ *    host threads or two streams at once.
+ *  - Arithmetic: residuals, Jacobian entries, J^T J p and vector updates run
+ *    in float32; PCG dot products (alpha, beta), energies and the LM gain
+ *    ratio run in float64.
+ *  - Errors: every call returns an opt_status; no exception crosses the ABI.
+ *    OPT_ERR_INVALID_ARG leaves the problem unchanged.  OPT_ERR_CUDA means a
+ *    CUDA call failed (the message is in opt_last_error()).
+ */
+#ifndef OPT_GB300_H
+#define OPT_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OPT_OK = 0,
+    OPT_ERR_INVALID_ARG = 1,  /* bad shape, null pointer, index out of range, non-finite input */
+    OPT_ERR_OOM = 2,          /* device allocation failed */
+    OPT_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    OPT_ERR_NUMERIC = 4,      /* non-finite energy or PCG scalar produced by a solve */
+    OPT_ERR_TIMEOUT = 5,      /* a bounded device-side wait expired */
+    OPT_ERR_BUDGET = 6,       /* admission refused: the memory budget is exhausted */
+    OPT_ERR_NOT_READY = 7     /* the batched / served solve has not finished yet */
+} opt_status;
+
+typedef enum {
+    OPT_ARAP_WARP_2D = 0,     /* Fig. 24: unknowns dx, dy, theta per pixel */
+    OPT_POISSON_2D = 1,       /* Fig. 27: unknowns X (4 channels) per pixel */
+    OPT_ARAP_MESH = 2         /* Fig. 25: unknowns dx, dy, dz, ax, ay, az per vertex */
+} opt_energy;
+
+typedef struct opt_problem opt_problem;
+
+/* Grid (image) problem, Sec. 4.1 "Stencil-based Array Access".
+ * Every plane is W*H float32 (or uint8) values, row-major, index y*W + x.
+ *   OPT_ARAP_WARP_2D (Fig. 24):
+ *     unknowns[0..2] = dx, dy, theta (device).  Offset = UrShape + (dx, dy).
+ *     consts[0..1]   = UrShape x, y (device).
+ *     mask           = nonzero marks an excluded pixel (device, may be NULL).
+ *     handle_idx     = n_handles distinct pixel indices (device).
+ *     handle_target  = n_handles (tx, ty) target displacements, interleaved (device).
+ *     Residuals: for every pixel k and direction d in {+x,-x,+y,-y} with k+d in
+ *     the image and both pixels unmasked,
+ *       sqrt(w_reg) * ((O_k - O_{k+d}) - R(theta_k)(U_k - U_{k+d})),
+ *     R counter-clockwise; for every handle h, sqrt(w_fit) * (O_h - C_h)
+ *     with C_h = U_h + target.
+ *   OPT_POISSON_2D (Fig. 27):
+ *     unknowns[0..3] = X channels (device); consts[0..3] = guidance T (device);
+ *     mask = nonzero marks a fixed pixel (device, may be NULL = all free).
+ *     Residuals: for every free pixel k and direction d with k+d in the image,
+ *       (X_k - X_{k+d}) - (T_k - T_{k+d}) per channel; fixed neighbours are
+ *     constants.  Handles and weights are ignored. */
+typedef struct {
+    int32_t kind;
+    int32_t W, H;
+    float* unknowns[4];
+    const float* consts[4];
+    const uint8_t* mask;
+    const int32_t* handle_idx;
+    const float* handle_target;
+    int32_t n_handles;
+    float w_reg, w_fit;
+} opt_grid_desc;
+
+/* Graph (mesh) problem, Sec. 4.1 "Graph-based Array Access", Fig. 25.
+ *   v0, v1      = E directed edges (device int32, any order; the library
+ *                 keeps a copy sorted by (v0, v1)).
+ *   unknowns[6] = dx, dy, dz (displacement from UrShape) and Euler angles
+ *                 ax, ay, az in radians, V floats each (device).
+ *   urshape[3]  = rest positions x, y, z (device).
+ *   handle_idx / handle_target = n_handles distinct vertices and (x, y, z)
+ *                 target displacements, interleaved (device).
+ *   Residuals: for every edge (a, b),
+ *     sqrt(w_reg) * ((O_a - O_b) - Rz(az_a) Ry(ay_a) Rx(ax_a) (U_a - U_b));
+ *   for every handle, sqrt(w_fit) * (O_h - C_h), C_h = U_h + target. */
+typedef struct {
+    int32_t V, E;
+    const int32_t* v0;
+    const int32_t* v1;
+    float* unknowns[6];
+    const float* urshape[3];
+    const int32_t* handle_idx;
+    const float* handle_target;
+    int32_t n_handles;
+    float w_reg, w_fit;
+} opt_graph_desc;
+
+/* Solver parameters (Sec. 4, Sec. 7 "LM vs. GN", "Matrix-free vs.
+ * Materialized").  opt_solve_params_default fills the values used by the
+ * paper-shaped configurations; lambda0 is the inverse initial trust radius. */
+typedef struct {
+    int32_t outer;            /* GN / LM outer iterations (>= 1) */
+    int32_t inner;            /* PCG iterations per outer iteration (>= 0) */
+    double lambda0;           /* LM initial damping (default 1e-3) */
+    double lambda_min;        /* LM damping clamp (default 1e-16) */
+    double lambda_max;        /* (default 1e32) */
+    double diag_min;          /* LM clamp of diag(J^T J) entries (default 1e-6) */
+    double diag_max;          /* (default 1e32) */
+    double eta;               /* LM acceptance threshold on the gain ratio (default 1e-3) */
+    double rel_tol;           /* LM: stop after an accepted step with |dE|/E < rel_tol (0 = off) */
+    int32_t use_precond;      /* 1 = Jacobi preconditioner (default), 0 = plain CG */
+    int32_t materialized;     /* 1 = materialized CSR J, q = J^T (J p) (Sec. 7) */
+    int32_t use_graph;        /* 1 = replay the solve as one CUDA graph (default) */
+    int32_t reserved;
+    void* stream;             /* cudaStream_t; NULL = legacy default stream */
+} opt_solve_params;
+
+/* Result of a solve.  E_history, when not NULL, is a host array of at least
+ * outer + 1 doubles that receives E(x_k) at the start of every executed outer
+ * iteration followed by the final energy. */
+typedef struct {
+    int32_t outer_done;       /* outer iterations executed (LM: including rejected ones) */
+    int32_t pcg_done;         /* PCG iterations completed over the whole solve */
+    int32_t accepted;         /* LM: accepted steps (GN: = outer_done) */
+    int32_t converged;        /* LM: stopped by rel_tol */
+    double E0;                /* energy at the initial x */
+    double E_final;           /* energy at the returned x */
+    double lambda_final;      /* LM damping after the last update (GN: 0) */
+    double* E_history;        /* host, caller-owned, or NULL */
+    float ms;                 /* device time of the solve (CUDA events) */
+} opt_report;
+
+/* Fills *p with the defaults listed above (outer = 10, inner = 10, GN). */
+opt_status opt_solve_params_default(opt_solve_params* p);
+
+/* Plan a grid problem: validates the descriptor (OPT_ERR_INVALID_ARG on a bad
+ * kind, W or H outside [1, 32768), null planes, handle index out of range or a
+ * non-finite constant), copies the constants, and allocates the PCG scratch
+ * (and the CSR arrays when params->materialized).  params may be NULL.
+ * *out receives the problem; it stays NULL on error. */
+opt_status opt_problem_create_grid(const opt_grid_desc* desc, const opt_solve_params* params,
+                                   opt_problem** out);
+
+/* Plan a graph problem (edges: 0 <= v0, v1 < V, v0 != v1, else
+ * OPT_ERR_INVALID_ARG).  Same ownership rules as opt_problem_create_grid. */
+opt_status opt_problem_create_graph(const opt_graph_desc* desc, const opt_solve_params* params,
+                                    opt_problem** out);
+
+/* Frees everything the problem owns.  NULL is accepted. */
+opt_status opt_problem_destroy(opt_problem* prob);
+
+/* Gauss-Newton (Sec. 4): outer x inner iterations from the caller's current
+ * unknowns, x written back at the end.  report may be NULL. */
+opt_status opt_solve_gn(opt_problem* prob, const opt_solve_params* params, opt_report* report);
+
+/* Levenberg-Marquardt (Sec. 4): as opt_solve_gn with damping
+ * (J^T J + lambda D) d = -J^T F, D = clamp(diag(J^T J), diag_min, diag_max),
+ * gain-ratio acceptance and Nielsen's damping update; everything stays on the
+ * device. */
+opt_status opt_solve_lm(opt_problem* prob, const opt_solve_params* params, opt_report* report);
+
+/* PCGInit (Sec. 4.1, Sec. 4.2 evalJTF): reads the caller's unknowns, evaluates
+ * F, b = -J^T F, the Jacobi preconditioner 1 / diag(J^T J + lambda D), sets
+ * delta = 0, r = b, p = z = M^-1 r.  energy (host, may be NULL) receives E(x). */
+opt_status opt_pcg_init(opt_problem* prob, double lambda, double* energy);
+
+/* Runs n_iters PCG iterations (PCGStep kernels of Sec. 4.1: applyJTJ with the
+ * direction update, then the vector update) on the state left by
+ * opt_pcg_init or a previous opt_pcg_step.  Stream-ordered; no host sync. */
+opt_status opt_pcg_step(opt_problem* prob, int32_t n_iters);
+
+/* Copies the PCG state to caller device buffers in the dense layout of the
+ * unknowns (any pointer may be NULL): delta, r, and the direction p. */
+opt_status opt_pcg_get_state(opt_problem* prob, float* delta, float* r, float* p,
+                             int32_t* iters_done);
+
+/* q = (J^T J + lambda * D) p at the caller's current unknowns (Sec. 4.2
+ * applyJTJ without the factor 2 that cancels).  p, q: device, dense layout of
+ * the unknowns (excluded Poisson pixels must hold p = 0).  pq (host, may be
+ * NULL) receives p.q in float64. */
+opt_status opt_apply_jtj(opt_problem* prob, const float* p, float* q, double lambda, double* pq);
+
+/* J^T F and diag(J^T J) at the caller's current unknowns (Sec. 4.2 evalJTF).
+ * jtf, diag: device, dense layout (either may be NULL); energy: host (may be
+ * NULL) receives E(x) = sum f_r^2 in float64. */
+opt_status opt_eval_jtf(opt_problem* prob, float* jtf, float* diag, double* energy);
+
+/* E(x) = sum f_r(x)^2 at the caller's current unknowns (Sec. 4.2 evalF). */
+opt_status opt_eval_energy(opt_problem* prob, double* energy);
+
+/* Measurement hook: runs PCGInit, then n_iters PCG iterations, with a CUDA
+ * event pair around every launch on `stream` (cudaStream_t, NULL = legacy
+ * default stream), synchronises, and writes the mean device time per launch
+ * in milliseconds: ms[0] = PCGInit, ms[1] = applyJTJ (with the fused
+ * direction update), ms[2] = vector update.  ms: host, 3 floats.  Leaves the
+ * PCG state as opt_pcg_init + opt_pcg_step would (lambda = 0). */
+opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, float* ms);
+
+/* Number of unknowns (elements per plane x planes) and of planes. */
+opt_status opt_problem_info(const opt_problem* prob, int64_t* n_unknowns, int32_t* n_planes,
+                            int64_t* plane_len);
+
+/* Human-readable name of a status code; never NULL. */
+const char* opt_status_str(opt_status s);
+
+/* Message of the last CUDA error seen on this host thread ("" if none). */
+const char* opt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OPT_GB300_H */

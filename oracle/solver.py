@@ -130,6 +130,7 @@ class LMResult:
     lambdas: list                # lambda used by each outer iteration
     outer_done: int
     pcg_done: int
+    lambda_final: float = 0.0    # damping after the last update
 
 
 def levenberg_marquardt(energy, x0, outer: int, inner: int, prm: LMParams = LMParams(),
@@ -175,4 +176,4 @@ def levenberg_marquardt(energy, x0, outer: int, inner: int, prm: LMParams = LMPa
             acc.append(False)
             lam = min(max(lam, prm.lambda_min), prm.lambda_max)
     hist.append(energy.energy(x))
-    return LMResult(x, hist, acc, lams, k, total)
+    return LMResult(x, hist, acc, lams, k, total, lam)

@@ -1,0 +1,286 @@
+"""Python binding of the C ABI in include/opt_gb300.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_lib/libopt_gb300.so``; PyTorch
+only provides device memory (tensors whose data pointers are handed to the
+library) and the current CUDA stream.  There is no CPU fallback: importing
+this module without the built library, or creating a problem without a CUDA
+device, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_float, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+OPT_OK = 0
+STATUS = {0: "OPT_OK", 1: "OPT_ERR_INVALID_ARG", 2: "OPT_ERR_OOM", 3: "OPT_ERR_CUDA",
+          4: "OPT_ERR_NUMERIC", 5: "OPT_ERR_TIMEOUT", 6: "OPT_ERR_BUDGET", 7: "OPT_ERR_NOT_READY"}
+OPT_ARAP_WARP_2D, OPT_POISSON_2D, OPT_ARAP_MESH = 0, 1, 2
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("W", c_int32), ("H", c_int32),
+                ("unknowns", c_void_p * 4), ("consts", c_void_p * 4), ("mask", c_void_p),
+                ("handle_idx", c_void_p), ("handle_target", c_void_p), ("n_handles", c_int32),
+                ("w_reg", c_float), ("w_fit", c_float)]
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("V", c_int32), ("E", c_int32), ("v0", c_void_p), ("v1", c_void_p),
+                ("unknowns", c_void_p * 6), ("urshape", c_void_p * 3),
+                ("handle_idx", c_void_p), ("handle_target", c_void_p), ("n_handles", c_int32),
+                ("w_reg", c_float), ("w_fit", c_float)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("outer", c_int32), ("inner", c_int32), ("lambda0", c_double),
+                ("lambda_min", c_double), ("lambda_max", c_double), ("diag_min", c_double),
+                ("diag_max", c_double), ("eta", c_double), ("rel_tol", c_double),
+                ("use_precond", c_int32), ("materialized", c_int32), ("use_graph", c_int32),
+                ("reserved", c_int32), ("stream", c_void_p)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("outer_done", c_int32), ("pcg_done", c_int32), ("accepted", c_int32),
+                ("converged", c_int32), ("E0", c_double), ("E_final", c_double),
+                ("lambda_final", c_double), ("E_history", POINTER(c_double)), ("ms", c_float)]
+
+
+# (name, restype, argtypes) of every exported entry point
+_SIGNATURES = [
+    ("opt_solve_params_default", c_int32, [POINTER(SolveParams)]),
+    ("opt_problem_create_grid", c_int32, [POINTER(GridDesc), POINTER(SolveParams), POINTER(c_void_p)]),
+    ("opt_problem_create_graph", c_int32, [POINTER(GraphDesc), POINTER(SolveParams), POINTER(c_void_p)]),
+    ("opt_problem_destroy", c_int32, [c_void_p]),
+    ("opt_solve_gn", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report)]),
+    ("opt_solve_lm", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report)]),
+    ("opt_pcg_init", c_int32, [c_void_p, c_double, POINTER(c_double)]),
+    ("opt_pcg_step", c_int32, [c_void_p, c_int32]),
+    ("opt_pcg_get_state", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int32)]),
+    ("opt_apply_jtj", c_int32, [c_void_p, c_void_p, c_void_p, c_double, POINTER(c_double)]),
+    ("opt_eval_jtf", c_int32, [c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
+    ("opt_eval_energy", c_int32, [c_void_p, POINTER(c_double)]),
+    ("opt_profile_pcg", c_int32, [c_void_p, c_int32, c_void_p, POINTER(c_float)]),
+    ("opt_problem_info", c_int32, [c_void_p, POINTER(c_int64), POINTER(c_int32), POINTER(c_int64)]),
+    ("opt_status_str", ctypes.c_char_p, [c_int32]),
+    ("opt_last_error", ctypes.c_char_p, []),
+]
+
+_LIB = None
+
+
+def load_library(path: str | None = None):
+    """Loads the built solver library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA solver library not built ({path}); run paper_1604_06525_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class OptError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load_library()
+        msg = lib.opt_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS.get(status, status)} {msg}")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != OPT_OK:
+        raise OptError(status, where)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def default_params(**kw) -> SolveParams:
+    p = SolveParams()
+    _check(load_library().opt_solve_params_default(ctypes.byref(p)), "opt_solve_params_default")
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Problem:
+    """One planned problem on the current CUDA device (Fig. 4: plan once,
+    solve many times).  `prob` is a synth.WarpProblem / PoissonProblem /
+    MeshProblem; its arrays are copied to device tensors that this object
+    owns (the unknowns stay caller-owned device memory from the library's
+    point of view)."""
+
+    def __init__(self, prob, device: str = "cuda"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.lib = load_library()
+        self.kind = prob.kind
+        self.device = torch.device(device)
+        dev = self.device
+
+        def f32(a):
+            return torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev)
+
+        def i32(a):
+            return torch.as_tensor(np.ascontiguousarray(a, np.int32), device=dev)
+
+        self._keep = []
+        h = c_void_p()
+        if prob.kind in ("warp", "poisson"):
+            self.W, self.H = prob.W, prob.H
+            self.x = f32(prob.x0).reshape(-1, prob.H, prob.W).clone()
+            d = GridDesc()
+            d.W, d.H = prob.W, prob.H
+            if prob.kind == "warp":
+                d.kind = OPT_ARAP_WARP_2D
+                consts = f32(prob.urshape)
+                mask = None if prob.mask is None else torch.as_tensor(prob.mask, dtype=torch.uint8, device=dev)
+                hidx = i32(prob.handle_idx)
+                htgt = f32(prob.handle_target.reshape(-1))
+                d.n_handles = int(prob.handle_idx.size)
+                d.handle_idx = _ptr(hidx) if d.n_handles else None
+                d.handle_target = _ptr(htgt) if d.n_handles else None
+                d.w_reg, d.w_fit = prob.w_reg, prob.w_fit
+                self._keep += [hidx, htgt]
+                nx, nc = 3, 2
+            else:
+                d.kind = OPT_POISSON_2D
+                consts = f32(prob.guide)
+                mask = torch.as_tensor(prob.mask, dtype=torch.uint8, device=dev)
+                d.n_handles = 0
+                nx, nc = 4, 4
+            for c in range(nx):
+                d.unknowns[c] = _ptr(self.x[c])
+            for c in range(nc):
+                d.consts[c] = _ptr(consts[c])
+            d.mask = _ptr(mask) if mask is not None else None
+            self._keep += [consts, mask]
+            _check(self.lib.opt_problem_create_grid(ctypes.byref(d), None, ctypes.byref(h)),
+                   "opt_problem_create_grid")
+        elif prob.kind == "mesh":
+            self.V = prob.V
+            self.x = f32(prob.x0).reshape(6, prob.V).clone()
+            U = f32(prob.urshape)
+            v0, v1 = i32(prob.v0), i32(prob.v1)
+            hidx = i32(prob.handle_idx)
+            htgt = f32(prob.handle_target.reshape(-1))
+            d = GraphDesc()
+            d.V, d.E = prob.V, int(prob.v0.size)
+            d.v0, d.v1 = _ptr(v0), _ptr(v1)
+            for c in range(6):
+                d.unknowns[c] = _ptr(self.x[c])
+            for c in range(3):
+                d.urshape[c] = _ptr(U[c])
+            d.n_handles = int(prob.handle_idx.size)
+            d.handle_idx = _ptr(hidx) if d.n_handles else None
+            d.handle_target = _ptr(htgt) if d.n_handles else None
+            d.w_reg, d.w_fit = prob.w_reg, prob.w_fit
+            self._keep += [U, v0, v1, hidx, htgt]
+            _check(self.lib.opt_problem_create_graph(ctypes.byref(d), None, ctypes.byref(h)),
+                   "opt_problem_create_graph")
+        else:
+            raise ValueError(prob.kind)
+        self.h = h
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.opt_problem_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_unknowns(self) -> int:
+        return int(self.x.numel())
+
+    def _params(self, outer, inner, **kw) -> SolveParams:
+        import torch
+        kw.setdefault("stream", torch.cuda.current_stream(self.device).cuda_stream)
+        return default_params(outer=outer, inner=inner, **kw)
+
+    def _solve(self, fn, outer, inner, **kw) -> dict:
+        p = self._params(outer, inner, **kw)
+        hist = (c_double * (outer + 1))()
+        rep = Report()
+        rep.E_history = ctypes.cast(hist, POINTER(c_double))
+        st = fn(self.h, ctypes.byref(p), ctypes.byref(rep))
+        if st not in (OPT_OK, 4):
+            _check(st, "solve")
+        return {"status": STATUS[st], "outer_done": rep.outer_done, "pcg_done": rep.pcg_done,
+                "accepted": rep.accepted, "converged": rep.converged, "E0": rep.E0,
+                "E_final": rep.E_final, "lambda_final": rep.lambda_final,
+                "E_history": list(hist[: rep.outer_done + 1]), "ms": rep.ms}
+
+    def solve_gn(self, outer: int, inner: int, **kw) -> dict:
+        """Gauss-Newton; x (self.x) is updated in place."""
+        return self._solve(self.lib.opt_solve_gn, outer, inner, **kw)
+
+    def solve_lm(self, outer: int, inner: int, **kw) -> dict:
+        """Levenberg-Marquardt; x (self.x) is updated in place."""
+        return self._solve(self.lib.opt_solve_lm, outer, inner, **kw)
+
+    # parity hooks -----------------------------------------------------
+    def apply_jtj(self, p, lam: float = 0.0):
+        import torch
+        p = torch.as_tensor(p, dtype=torch.float32, device=self.device).contiguous()
+        q = torch.empty_like(p)
+        pq = c_double()
+        _check(self.lib.opt_apply_jtj(self.h, _ptr(p), _ptr(q), lam, ctypes.byref(pq)), "opt_apply_jtj")
+        return q, pq.value
+
+    def eval_jtf(self):
+        import torch
+        jtf = torch.empty_like(self.x)
+        diag = torch.empty_like(self.x)
+        E = c_double()
+        _check(self.lib.opt_eval_jtf(self.h, _ptr(jtf), _ptr(diag), ctypes.byref(E)), "opt_eval_jtf")
+        return jtf, diag, E.value
+
+    def energy(self) -> float:
+        E = c_double()
+        _check(self.lib.opt_eval_energy(self.h, ctypes.byref(E)), "opt_eval_energy")
+        return E.value
+
+    def pcg_init(self, lam: float = 0.0) -> float:
+        E = c_double()
+        _check(self.lib.opt_pcg_init(self.h, lam, ctypes.byref(E)), "opt_pcg_init")
+        return E.value
+
+    def pcg_step(self, n: int):
+        _check(self.lib.opt_pcg_step(self.h, n), "opt_pcg_step")
+
+    def profile_pcg(self, n_iters: int) -> tuple:
+        """Mean device ms per launch of (PCGInit, applyJTJ, vector update)."""
+        import torch
+        ms = (c_float * 3)()
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        _check(self.lib.opt_profile_pcg(self.h, n_iters, st, ms), "opt_profile_pcg")
+        return ms[0], ms[1], ms[2]
+
+    def pcg_state(self):
+        import torch
+        dl, r, p = (torch.empty_like(self.x) for _ in range(3))
+        it = c_int32()
+        _check(self.lib.opt_pcg_get_state(self.h, _ptr(dl), _ptr(r), _ptr(p), ctypes.byref(it)),
+               "opt_pcg_get_state")
+        return dl, r, p, it.value

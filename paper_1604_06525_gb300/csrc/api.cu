@@ -1,0 +1,977 @@
+// Host driver and C ABI (include/opt_gb300.h): problem planning, the GN and
+// LM outer loops (Sec. 4), CUDA-graph replay of a whole solve, and the parity
+// hooks (evalJTF, applyJTJ, evalF of Sec. 4.2).
+//
+// A solve is one fixed sequence of stream-ordered launches: copy x in, reset
+// the device scalars, then per outer iteration PCGInit, `inner` x (applyJTJ,
+// vector update), and the outer update (GN: x += delta; LM: trial energy,
+// gain-ratio decision, conditional x += delta), then the final energy and the
+// copy of x out.  Every decision (PCG breakdown, LM accept / reject, LM
+// convergence) is taken on the device and read by later kernels, so the
+// sequence never needs the host and is captured once as a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "opt_gb300.h"
+#include "opt_internal.cuh"
+#include "opt_launch.h"
+
+using namespace optgb;
+
+namespace {
+
+thread_local std::string g_err;
+
+opt_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  (void)cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? OPT_ERR_OOM : OPT_ERR_CUDA;
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+#define CKS(call)                          \
+  do {                                     \
+    opt_status s_ = (call);                \
+    if (s_ != OPT_OK) return s_;           \
+  } while (0)
+
+__global__ void k_reset(Scalars* s, int n, double lambda0) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Scalars z;
+  memset(&z, 0, sizeof(z));
+  z.lambda = lambda0;
+  z.lambda_f = (float)lambda0;
+  z.nu = 2.0;
+  s[i] = z;
+}
+
+__global__ void k_force_active(Scalars* s, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  s[i].pcg_active = 1;
+  s[i].done = 0;
+}
+
+// LM decision (Sec. 4; Nielsen's damping update), one thread per problem.
+__global__ void k_lm_decide(Scalars* s, int n, double eta, double lmin, double lmax, double rel_tol) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Scalars* t = s + i;
+  if (t->done) {
+    t->accept = 0;
+    return;
+  }
+  const double E = t->E, Et = t->E_trial;
+  const double pred = E - t->model;
+  const double rho = pred > 0.0 ? (E - Et) / pred : -INFINITY;
+  double lam = t->lambda;
+  t->outer_done += 1;
+  if (rho > eta) {
+    const double u = 2.0 * rho - 1.0;
+    lam *= fmax(1.0 / 3.0, 1.0 - u * u * u);
+    t->nu = 2.0;
+    t->accept = 1;
+    t->accepted_total += 1;
+    if (rel_tol > 0.0 && (Et == 0.0 || fabs(E - Et) / E < rel_tol)) {
+      t->done = 1;
+      t->converged = 1;
+    }
+  } else {
+    lam *= t->nu;
+    t->nu *= 2.0;
+    t->accept = 0;
+  }
+  lam = fmin(fmax(lam, lmin), lmax);
+  t->lambda = lam;
+  t->lambda_f = (float)lam;
+  if (!isfinite(Et) && t->accept) t->nonfinite = 1;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct opt_problem {
+  int kind = 0;
+  int nx = 0;             // unknown planes
+  int nm = 0;             // distinct-diagonal planes
+  int sms = 148;
+  // grid
+  int W = 0, H = 0, P = 0;
+  // graph
+  int V = 0, E = 0;
+  long long plane = 0;    // internal plane stride (P*H or Vp)
+  long long ulen = 0;     // caller plane length (W*H or V)
+  GridProb hg{};
+  GridProb* dg = nullptr;
+  Chunk* d_chunks = nullptr;
+  int nchunks = 0;
+  int* d_tiles = nullptr;
+  int ntiles = 0;
+  MeshProb hm{};
+  MeshProb* dm = nullptr;
+  Chunk* d_vchunks = nullptr;
+  Chunk* d_echunks = nullptr;
+  int nvchunks = 0, nechunks = 0;
+  float* d_acc = nullptr;
+  // common
+  double* d_part = nullptr;
+  Scalars* d_s = nullptr;
+  double* d_Ehist = nullptr;
+  int Ehist_cap = 0;
+  float* user_x[6] = {};
+  float* d_tmp = nullptr;     // nx planes: caller p (apply hook)
+  float* d_jtf = nullptr;     // nx planes: J^T F (hook)
+  float* d_diag = nullptr;    // nm planes: diag (hook)
+  float* x = nullptr;
+  float* pbuf = nullptr;
+  float* dvec = nullptr;
+  float* rvec = nullptr;
+  float* qvec = nullptr;
+  std::vector<void*> allocs;
+  int pcg_par = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<double> gkey;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  ~opt_problem() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+namespace {
+
+template <class T>
+opt_status dalloc(opt_problem* pb, T** ptr, size_t n) {
+  void* p = nullptr;
+  const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  pb->allocs.push_back(p);
+  e = cudaMemset(p, 0, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+  *ptr = static_cast<T*>(p);
+  return OPT_OK;
+}
+
+template <class T>
+opt_status upload(T* dst, const std::vector<T>& src) {
+  if (src.empty()) return OPT_OK;
+  CK(cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return OPT_OK;
+}
+
+template <class T>
+opt_status download(std::vector<T>& dst, const T* src, size_t n) {
+  dst.resize(n);
+  if (n == 0) return OPT_OK;
+  CK(cudaMemcpy(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost));
+  return OPT_OK;
+}
+
+bool all_finite(const std::vector<float>& v) {
+  for (float f : v)
+    if (!std::isfinite(f)) return false;
+  return true;
+}
+
+bool is_grid(const opt_problem* pb) { return pb->kind == K_WARP || pb->kind == K_POISSON; }
+
+// distinct-diagonal plane of unknown component c
+int mplane_of(int kind, int c) {
+  if (kind == K_WARP) return c == 2 ? 1 : 0;
+  if (kind == K_POISSON) return 0;
+  return c < 3 ? 0 : c - 2;
+}
+
+opt_status common_setup(opt_problem* pb) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&pb->sms, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaStreamCreateWithFlags(&pb->cap_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreate(&pb->ev0));
+  CK(cudaEventCreate(&pb->ev1));
+  CKS(dalloc(pb, &pb->d_s, 1));
+  return OPT_OK;
+}
+
+// copy between caller dense planes and internal pitched planes
+opt_status copy_planes_in(const opt_problem* pb, float* internal, float* const* user, int n,
+                          cudaStream_t st) {
+  for (int c = 0; c < n; ++c) {
+    if (is_grid(pb))
+      CK(cudaMemcpy2DAsync(internal + c * pb->plane, (size_t)pb->P * 4, user[c], (size_t)pb->W * 4,
+                           (size_t)pb->W * 4, pb->H, cudaMemcpyDeviceToDevice, st));
+    else
+      CK(cudaMemcpyAsync(internal + c * pb->plane, user[c], (size_t)pb->V * 4,
+                         cudaMemcpyDeviceToDevice, st));
+  }
+  return OPT_OK;
+}
+
+opt_status copy_planes_out(const opt_problem* pb, float* const* user, const float* internal, int n,
+                           cudaStream_t st) {
+  for (int c = 0; c < n; ++c) {
+    if (is_grid(pb))
+      CK(cudaMemcpy2DAsync(user[c], (size_t)pb->W * 4, internal + c * pb->plane, (size_t)pb->P * 4,
+                           (size_t)pb->W * 4, pb->H, cudaMemcpyDeviceToDevice, st));
+    else
+      CK(cudaMemcpyAsync(user[c], internal + c * pb->plane, (size_t)pb->V * 4,
+                         cudaMemcpyDeviceToDevice, st));
+  }
+  return OPT_OK;
+}
+
+void dense_planes(const opt_problem* pb, const float* base, float** out, int n) {
+  for (int c = 0; c < n; ++c) out[c] = const_cast<float*>(base) + c * pb->ulen;
+}
+
+GridLaunch grid_launch(const opt_problem* pb, cudaStream_t st) {
+  return GridLaunch{pb->dg, pb->d_chunks, pb->d_tiles, pb->d_part, pb->nchunks, st};
+}
+MeshLaunch mesh_launch(const opt_problem* pb, cudaStream_t st) {
+  return MeshLaunch{pb->dm, pb->d_vchunks, pb->d_echunks, pb->d_part, pb->d_acc, pb->nvchunks,
+                    pb->nechunks, st};
+}
+
+opt_status upload_desc(opt_problem* pb, cudaStream_t st) {
+  if (is_grid(pb))
+    CK(cudaMemcpyAsync(pb->dg, &pb->hg, sizeof(GridProb), cudaMemcpyHostToDevice, st));
+  else
+    CK(cudaMemcpyAsync(pb->dm, &pb->hm, sizeof(MeshProb), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return OPT_OK;
+}
+
+void set_flags(opt_problem* pb, int lm, int use_precond, double* ehist) {
+  if (is_grid(pb)) {
+    pb->hg.lm = lm;
+    pb->hg.use_precond = use_precond;
+    pb->hg.Ehist = ehist;
+  } else {
+    pb->hm.lm = lm;
+    pb->hm.use_precond = use_precond;
+    pb->hm.Ehist = ehist;
+  }
+}
+
+// --- stage launchers (dispatch on the domain) ------------------------------
+void st_init(opt_problem* pb, cudaStream_t st, int k, float dmin, float dmax) {
+  if (is_grid(pb)) launch_grid_init(pb->kind, grid_launch(pb, st), k, dmin, dmax);
+  else launch_mesh_init(mesh_launch(pb, st), k, dmin, dmax);
+}
+void st_apply(opt_problem* pb, cudaStream_t st, const float* pov, int par, int update) {
+  if (is_grid(pb)) launch_grid_apply(pb->kind, grid_launch(pb, st), pov, par, update);
+  else launch_mesh_apply(mesh_launch(pb, st), pov, par, update);
+}
+void st_update(opt_problem* pb, cudaStream_t st, int par) {
+  if (is_grid(pb)) launch_grid_update(pb->kind, grid_launch(pb, st), par);
+  else launch_mesh_update(mesh_launch(pb, st), par);
+}
+void st_energy(opt_problem* pb, cudaStream_t st, int mode, int hist_idx) {
+  if (is_grid(pb)) launch_grid_energy(pb->kind, grid_launch(pb, st), mode, hist_idx);
+  else launch_mesh_energy(mesh_launch(pb, st), mode, hist_idx);
+}
+void st_step(opt_problem* pb, cudaStream_t st, int cond) {
+  if (is_grid(pb)) launch_grid_step(pb->kind, grid_launch(pb, st), cond);
+  else launch_mesh_step(mesh_launch(pb, st), cond);
+}
+
+opt_status check_params(const opt_solve_params& p, bool lm) {
+  if (p.outer < 1 || p.inner < 0 || p.outer > (1 << 20) || p.inner > (1 << 20)) return OPT_ERR_INVALID_ARG;
+  if (p.use_precond != 0 && p.use_precond != 1) return OPT_ERR_INVALID_ARG;
+  if (lm) {
+    if (!(p.lambda0 >= 0.0) || !std::isfinite(p.lambda0)) return OPT_ERR_INVALID_ARG;
+    if (!(p.lambda_min >= 0.0) || !(p.lambda_min <= p.lambda_max)) return OPT_ERR_INVALID_ARG;
+    if (!(p.diag_min >= 0.0) || !(p.diag_min <= p.diag_max)) return OPT_ERR_INVALID_ARG;
+    if (!std::isfinite(p.eta) || !(p.rel_tol >= 0.0)) return OPT_ERR_INVALID_ARG;
+  }
+  return OPT_OK;
+}
+
+// The whole solve as stream-ordered work (captured into a graph or run directly).
+opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cudaStream_t st) {
+  const float dmin = (float)p.diag_min, dmax = (float)p.diag_max;
+  CKS(copy_planes_in(pb, pb->x, pb->user_x, pb->nx, st));
+  k_reset<<<1, 32, 0, st>>>(pb->d_s, 1, lm ? p.lambda0 : 0.0);
+  for (int k = 0; k < p.outer; ++k) {
+    st_init(pb, st, k, dmin, dmax);
+    for (int i = 0; i < p.inner; ++i) {
+      st_apply(pb, st, nullptr, i, 1);
+      st_update(pb, st, i);
+    }
+    if (!lm) {
+      st_step(pb, st, 0);
+    } else {
+      st_energy(pb, st, 1, -2);
+      k_lm_decide<<<1, 32, 0, st>>>(pb->d_s, 1, p.eta, p.lambda_min, p.lambda_max, p.rel_tol);
+      st_step(pb, st, 1);
+    }
+  }
+  st_energy(pb, st, 0, lm ? -1 : p.outer);
+  CKS(copy_planes_out(pb, pb->user_x, pb->x, pb->nx, st));
+  CK(cudaGetLastError());
+  return OPT_OK;
+}
+
+std::vector<double> graph_key(const opt_solve_params& p, bool lm, cudaStream_t) {
+  return {double(p.outer), double(p.inner), double(lm), double(p.use_precond), p.lambda0, p.lambda_min,
+          p.lambda_max, p.diag_min, p.diag_max, p.eta, p.rel_tol, double(p.materialized)};
+}
+
+opt_status ensure_ehist(opt_problem* pb, int n) {
+  if (pb->Ehist_cap >= n) return OPT_OK;
+  if (pb->gexec) {
+    cudaGraphExecDestroy(pb->gexec);
+    pb->gexec = nullptr;
+    pb->gkey.clear();
+  }
+  double* e = nullptr;
+  CKS(dalloc(pb, &e, (size_t)n));
+  pb->d_Ehist = e;
+  pb->Ehist_cap = n;
+  return OPT_OK;
+}
+
+opt_status run_solve(opt_problem* pb, const opt_solve_params* prm_in, opt_report* rep, bool lm) {
+  if (!pb) return OPT_ERR_INVALID_ARG;
+  opt_solve_params p;
+  if (prm_in) p = *prm_in;
+  else opt_solve_params_default(&p);
+  CKS(check_params(p, lm));
+  if (p.materialized) return OPT_ERR_INVALID_ARG;   // materialized path: see opt_solve_* docs
+  cudaStream_t st = (cudaStream_t)p.stream;
+  CK(cudaStreamSynchronize(st));
+  CKS(ensure_ehist(pb, p.outer + 1));
+  set_flags(pb, lm ? 1 : 0, p.use_precond, pb->d_Ehist);
+  CKS(upload_desc(pb, st));
+  if (p.use_graph) {
+    const std::vector<double> key = graph_key(p, lm, st);
+    if (!pb->gexec || key != pb->gkey) {
+      if (pb->gexec) {
+        cudaGraphExecDestroy(pb->gexec);
+        pb->gexec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(pb->cap_stream, cudaStreamCaptureModeThreadLocal));
+      opt_status s = enqueue_solve(pb, p, lm, pb->cap_stream);
+      cudaError_t e = cudaStreamEndCapture(pb->cap_stream, &g);
+      if (s != OPT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&pb->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      pb->gkey = key;
+    }
+    CK(cudaEventRecord(pb->ev0, st));
+    CK(cudaGraphLaunch(pb->gexec, st));
+    CK(cudaEventRecord(pb->ev1, st));
+  } else {
+    CK(cudaEventRecord(pb->ev0, st));
+    CKS(enqueue_solve(pb, p, lm, st));
+    CK(cudaEventRecord(pb->ev1, st));
+  }
+  CK(cudaEventSynchronize(pb->ev1));
+  Scalars s;
+  CK(cudaMemcpy(&s, pb->d_s, sizeof(Scalars), cudaMemcpyDeviceToHost));
+  const int outer_done = lm ? s.outer_done : p.outer;
+  std::vector<double> eh;
+  CKS(download(eh, pb->d_Ehist, (size_t)outer_done + 1));
+  pb->pcg_par = 0;
+  if (rep) {
+    rep->outer_done = outer_done;
+    rep->pcg_done = s.pcg_iters;
+    rep->accepted = lm ? s.accepted_total : p.outer;
+    rep->converged = s.converged;
+    rep->E0 = eh[0];
+    rep->E_final = eh[outer_done];
+    rep->lambda_final = lm ? s.lambda : 0.0;
+    if (rep->E_history) std::memcpy(rep->E_history, eh.data(), eh.size() * sizeof(double));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, pb->ev0, pb->ev1));
+    rep->ms = ms;
+  }
+  if (s.nonfinite) return OPT_ERR_NUMERIC;
+  return OPT_OK;
+}
+
+// Builds chunks of `per` consecutive units (tiles, vertex tiles or edges).
+std::vector<Chunk> make_chunks(int n_units, int per, int prob) {
+  std::vector<Chunk> ch;
+  for (int b = 0; b < std::max(n_units, 1); b += per) ch.push_back(Chunk{prob, b, std::min(b + per, n_units), 0});
+  return ch;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+extern "C" {
+
+opt_status opt_solve_params_default(opt_solve_params* p) {
+  if (!p) return OPT_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->outer = 10;
+  p->inner = 10;
+  p->lambda0 = 1e-3;
+  p->lambda_min = 1e-16;
+  p->lambda_max = 1e32;
+  p->diag_min = 1e-6;
+  p->diag_max = 1e32;
+  p->eta = 1e-3;
+  p->rel_tol = 0.0;
+  p->use_precond = 1;
+  p->materialized = 0;
+  p->use_graph = 1;
+  p->stream = nullptr;
+  return OPT_OK;
+}
+
+const char* opt_status_str(opt_status s) {
+  switch (s) {
+    case OPT_OK: return "OPT_OK";
+    case OPT_ERR_INVALID_ARG: return "OPT_ERR_INVALID_ARG";
+    case OPT_ERR_OOM: return "OPT_ERR_OOM";
+    case OPT_ERR_CUDA: return "OPT_ERR_CUDA";
+    case OPT_ERR_NUMERIC: return "OPT_ERR_NUMERIC";
+    case OPT_ERR_TIMEOUT: return "OPT_ERR_TIMEOUT";
+    case OPT_ERR_BUDGET: return "OPT_ERR_BUDGET";
+    case OPT_ERR_NOT_READY: return "OPT_ERR_NOT_READY";
+  }
+  return "OPT_ERR_UNKNOWN";
+}
+
+const char* opt_last_error(void) { return g_err.c_str(); }
+
+opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_params* prm, opt_problem** out) {
+  (void)prm;
+  if (!out) return OPT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d) return OPT_ERR_INVALID_ARG;
+  if (d->kind != OPT_ARAP_WARP_2D && d->kind != OPT_POISSON_2D) return OPT_ERR_INVALID_ARG;
+  if (d->W < 1 || d->H < 1 || d->W >= 32768 || d->H >= 32768) return OPT_ERR_INVALID_ARG;
+  const bool warp = d->kind == OPT_ARAP_WARP_2D;
+  const int nx = warp ? 3 : 4, nc = warp ? 2 : 4, nm = warp ? 2 : 1;
+  for (int c = 0; c < nx; ++c)
+    if (!d->unknowns[c]) return OPT_ERR_INVALID_ARG;
+  for (int c = 0; c < nc; ++c)
+    if (!d->consts[c]) return OPT_ERR_INVALID_ARG;
+  const int nh = warp ? d->n_handles : 0;
+  if (nh < 0) return OPT_ERR_INVALID_ARG;
+  if (nh > 0 && (!d->handle_idx || !d->handle_target)) return OPT_ERR_INVALID_ARG;
+  if (warp && (!std::isfinite(d->w_reg) || !std::isfinite(d->w_fit) || d->w_reg < 0.f || d->w_fit < 0.f))
+    return OPT_ERR_INVALID_ARG;
+
+  std::unique_ptr<opt_problem> pb(new opt_problem());
+  pb->kind = warp ? K_WARP : K_POISSON;
+  pb->nx = nx;
+  pb->nm = nm;
+  pb->W = d->W;
+  pb->H = d->H;
+  pb->P = round_up(d->W, 32);
+  pb->plane = (long long)pb->P * d->H;
+  pb->ulen = (long long)d->W * d->H;
+  CKS(common_setup(pb.get()));
+  const int W = d->W, H = d->H, P = pb->P;
+  const size_t n = (size_t)W * H;
+
+  // host copies of the constants for validation and planning
+  std::vector<float> cst;
+  for (int c = 0; c < nc; ++c) {
+    std::vector<float> tmp;
+    CKS(download(tmp, d->consts[c], n));
+    if (!all_finite(tmp)) return OPT_ERR_INVALID_ARG;
+  }
+  std::vector<uint8_t> mask;
+  if (d->mask) CKS(download(mask, d->mask, n));
+  std::vector<int> hidx;
+  std::vector<float> htgt;
+  if (nh > 0) {
+    CKS(download(hidx, d->handle_idx, (size_t)nh));
+    CKS(download(htgt, d->handle_target, (size_t)nh * 2));
+    if (!all_finite(htgt)) return OPT_ERR_INVALID_ARG;
+    std::vector<int> sorted(hidx);
+    std::sort(sorted.begin(), sorted.end());
+    for (size_t i = 0; i < sorted.size(); ++i) {
+      if (sorted[i] < 0 || (size_t)sorted[i] >= n) return OPT_ERR_INVALID_ARG;
+      if (i && sorted[i] == sorted[i - 1]) return OPT_ERR_INVALID_ARG;
+    }
+  }
+
+  // active tiles: at least one unmasked (warp) / free (Poisson) pixel
+  const int ntx = (W + TW - 1) / TW, nty = (H + TH - 1) / TH;
+  std::vector<int> tiles;
+  for (int ty = 0; ty < nty; ++ty)
+    for (int tx = 0; tx < ntx; ++tx) {
+      bool act = mask.empty();
+      for (int y = ty * TH; !act && y < std::min(H, ty * TH + TH); ++y)
+        for (int x = tx * TW; x < std::min(W, tx * TW + TW); ++x)
+          if (mask[(size_t)y * W + x] == 0) { act = true; break; }
+      if (act) tiles.push_back((ty << 16) | tx);
+    }
+  if (tiles.empty()) tiles.push_back(0);
+  const int target = std::max(1, pb->sms * 8);
+  const int tpc = std::max(1, ((int)tiles.size() + target - 1) / target);
+  std::vector<Chunk> chunks = make_chunks((int)tiles.size(), tpc, 0);
+
+  // handles sorted by tile
+  std::vector<int> order(nh);
+  std::iota(order.begin(), order.end(), 0);
+  auto tile_of = [&](int pix) { return (pix / W / TH) * ntx + (pix % W) / TW; };
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    const int ta = tile_of(hidx[a]), tb = tile_of(hidx[b]);
+    return ta != tb ? ta < tb : hidx[a] < hidx[b];
+  });
+  std::vector<int> hbeg((size_t)ntx * nty + 1, 0), hpix(nh);
+  std::vector<float> hts((size_t)nh * 2);
+  for (int k = 0; k < nh; ++k) {
+    const int i = order[k], pix = hidx[i];
+    hpix[k] = (pix / W) * P + (pix % W);
+    hts[2 * k] = htgt[2 * i];
+    hts[2 * k + 1] = htgt[2 * i + 1];
+    hbeg[tile_of(pix) + 1] += 1;
+  }
+  for (size_t t = 1; t < hbeg.size(); ++t) hbeg[t] += hbeg[t - 1];
+
+  // device buffers
+  opt_problem* q = pb.get();
+  const size_t pl = (size_t)pb->plane;
+  float *c = nullptr, *m = nullptr, *dc = nullptr;
+  uint8_t* dmask = nullptr;
+  int *dhbeg = nullptr, *dhpix = nullptr;
+  float* dhtgt = nullptr;
+  CKS(dalloc(q, &q->x, nx * pl));
+  CKS(dalloc(q, &c, nc * pl));
+  CKS(dalloc(q, &q->dvec, nx * pl));
+  CKS(dalloc(q, &q->rvec, nx * pl));
+  CKS(dalloc(q, &q->qvec, nx * pl));
+  CKS(dalloc(q, &q->pbuf, 2 * nx * pl));
+  CKS(dalloc(q, &m, nm * pl));
+  CKS(dalloc(q, &dc, nm * pl));
+  if (d->mask) {
+    CKS(dalloc(q, &dmask, pl));
+    CK(cudaMemcpy2D(dmask, P, d->mask, W, W, H, cudaMemcpyDeviceToDevice));
+  }
+  for (int k = 0; k < nc; ++k)
+    CK(cudaMemcpy2D(c + k * pl, (size_t)P * 4, d->consts[k], (size_t)W * 4, (size_t)W * 4, H,
+                    cudaMemcpyDeviceToDevice));
+  CKS(dalloc(q, &dhbeg, hbeg.size()));
+  CKS(upload(dhbeg, hbeg));
+  CKS(dalloc(q, &dhpix, hpix.size()));
+  CKS(upload(dhpix, hpix));
+  CKS(dalloc(q, &dhtgt, hts.size()));
+  CKS(upload(dhtgt, hts));
+  CKS(dalloc(q, &q->d_tiles, tiles.size()));
+  CKS(upload(q->d_tiles, tiles));
+  q->ntiles = (int)tiles.size();
+  CKS(dalloc(q, &q->d_chunks, chunks.size()));
+  CKS(upload(q->d_chunks, chunks));
+  q->nchunks = (int)chunks.size();
+  CKS(dalloc(q, &q->d_part, 2 * chunks.size()));
+  CKS(dalloc(q, &q->dg, 1));
+  for (int k = 0; k < nx; ++k) q->user_x[k] = d->unknowns[k];
+
+  GridProb& g = q->hg;
+  g.kind = q->kind;
+  g.W = W; g.H = H; g.P = P;
+  g.ntx = ntx; g.nty = nty;
+  g.plane = (long long)pl;
+  g.chunk_begin = 0;
+  g.chunk_end = q->nchunks;
+  g.w_reg = warp ? d->w_reg : 1.f;
+  g.w_fit = warp ? d->w_fit : 0.f;
+  g.s_w = std::sqrt(g.w_reg);
+  g.s_f = std::sqrt(g.w_fit);
+  g.use_precond = 1;
+  g.lm = 0;
+  g.x = q->x; g.c = c; g.mask = dmask;
+  g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
+  g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;
+  g.jtf_out = nullptr; g.diag_out = nullptr;
+  g.s = q->d_s;
+  g.Ehist = nullptr;
+  CKS(upload_desc(q, nullptr));
+  *out = pb.release();
+  return OPT_OK;
+}
+
+opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_params* prm, opt_problem** out) {
+  (void)prm;
+  if (!out) return OPT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d) return OPT_ERR_INVALID_ARG;
+  if (d->V < 1 || d->E < 0 || d->n_handles < 0) return OPT_ERR_INVALID_ARG;
+  if (d->E > 0 && (!d->v0 || !d->v1)) return OPT_ERR_INVALID_ARG;
+  for (int c = 0; c < 6; ++c)
+    if (!d->unknowns[c]) return OPT_ERR_INVALID_ARG;
+  for (int c = 0; c < 3; ++c)
+    if (!d->urshape[c]) return OPT_ERR_INVALID_ARG;
+  if (d->n_handles > 0 && (!d->handle_idx || !d->handle_target)) return OPT_ERR_INVALID_ARG;
+  if (!std::isfinite(d->w_reg) || !std::isfinite(d->w_fit) || d->w_reg < 0.f || d->w_fit < 0.f)
+    return OPT_ERR_INVALID_ARG;
+
+  std::unique_ptr<opt_problem> pb(new opt_problem());
+  opt_problem* q = pb.get();
+  q->kind = K_MESH;
+  q->nx = 6;
+  q->nm = 4;
+  q->V = d->V;
+  q->E = d->E;
+  const int V = d->V, E = d->E, nh = d->n_handles;
+  const int Vp = round_up(V, 32);
+  q->plane = Vp;
+  q->ulen = V;
+  CKS(common_setup(q));
+
+  std::vector<int> e0, e1;
+  CKS(download(e0, d->v0, (size_t)E));
+  CKS(download(e1, d->v1, (size_t)E));
+  for (int e = 0; e < E; ++e)
+    if (e0[e] < 0 || e0[e] >= V || e1[e] < 0 || e1[e] >= V || e0[e] == e1[e]) return OPT_ERR_INVALID_ARG;
+  bool sorted = true;
+  for (int e = 1; e < E && sorted; ++e)
+    if (e0[e] < e0[e - 1] || (e0[e] == e0[e - 1] && e1[e] < e1[e - 1])) sorted = false;
+  if (!sorted) {
+    std::vector<long long> key((size_t)E);
+    for (int e = 0; e < E; ++e) key[e] = (long long)e0[e] * V + e1[e];
+    std::sort(key.begin(), key.end());
+    for (int e = 0; e < E; ++e) { e0[e] = (int)(key[e] / V); e1[e] = (int)(key[e] % V); }
+  }
+  std::vector<float> U3;
+  for (int c = 0; c < 3; ++c) {
+    std::vector<float> tmp;
+    CKS(download(tmp, d->urshape[c], (size_t)V));
+    if (!all_finite(tmp)) return OPT_ERR_INVALID_ARG;
+  }
+  std::vector<int> hidx;
+  std::vector<float> htgt;
+  if (nh > 0) {
+    CKS(download(hidx, d->handle_idx, (size_t)nh));
+    CKS(download(htgt, d->handle_target, (size_t)nh * 3));
+    if (!all_finite(htgt)) return OPT_ERR_INVALID_ARG;
+  }
+  std::vector<int> order(nh);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return hidx[a] < hidx[b]; });
+  const int nvt = (V + VT - 1) / VT;
+  std::vector<int> hbeg((size_t)nvt + 1, 0), hpix(nh);
+  std::vector<float> hts((size_t)nh * 3);
+  std::vector<float> degw((size_t)V, 0.f);
+  for (int k = 0; k < nh; ++k) {
+    const int i = order[k], v = hidx[i];
+    if (v < 0 || v >= V || (k && hpix[k - 1] == v)) return OPT_ERR_INVALID_ARG;
+    hpix[k] = v;
+    for (int c = 0; c < 3; ++c) hts[3 * k + c] = htgt[3 * i + c];
+    hbeg[v / VT + 1] += 1;
+    degw[v] += d->w_fit;
+  }
+  for (size_t t = 1; t < hbeg.size(); ++t) hbeg[t] += hbeg[t - 1];
+  for (int e = 0; e < E; ++e) {
+    degw[e0[e]] += d->w_reg;
+    degw[e1[e]] += d->w_reg;
+  }
+
+  const int target = std::max(1, q->sms * 8);
+  const int vtpc = std::max(1, (nvt + target - 1) / target);
+  std::vector<Chunk> vch;
+  for (int t = 0; t < std::max(nvt, 1); t += vtpc)
+    vch.push_back(Chunk{0, t * VT, std::min(V, (t + vtpc) * VT), 0});
+  const int epc = std::max(NT, round_up((E + target - 1) / target, NT));
+  std::vector<Chunk> ech = make_chunks(E, epc, 0);
+
+  const size_t pl = (size_t)Vp;
+  float *U = nullptr, *dgw = nullptr, *m = nullptr, *dc = nullptr, *dhtgt = nullptr;
+  int *de0 = nullptr, *de1 = nullptr, *dhbeg = nullptr, *dhpix = nullptr;
+  CKS(dalloc(q, &q->x, 6 * pl));
+  CKS(dalloc(q, &U, 3 * pl));
+  CKS(dalloc(q, &dgw, pl));
+  CKS(dalloc(q, &q->dvec, 6 * pl));
+  CKS(dalloc(q, &q->rvec, 6 * pl));
+  CKS(dalloc(q, &q->qvec, 6 * pl));
+  CKS(dalloc(q, &q->pbuf, 12 * pl));
+  CKS(dalloc(q, &m, 4 * pl));
+  CKS(dalloc(q, &dc, 4 * pl));
+  CKS(dalloc(q, &q->d_acc, 3 * pl));
+  for (int c = 0; c < 3; ++c)
+    CK(cudaMemcpy(U + c * pl, d->urshape[c], (size_t)V * 4, cudaMemcpyDeviceToDevice));
+  CKS(upload(dgw, degw));
+  CKS(dalloc(q, &de0, (size_t)E));
+  CKS(upload(de0, e0));
+  CKS(dalloc(q, &de1, (size_t)E));
+  CKS(upload(de1, e1));
+  CKS(dalloc(q, &dhbeg, hbeg.size()));
+  CKS(upload(dhbeg, hbeg));
+  CKS(dalloc(q, &dhpix, hpix.size()));
+  CKS(upload(dhpix, hpix));
+  CKS(dalloc(q, &dhtgt, hts.size()));
+  CKS(upload(dhtgt, hts));
+  CKS(dalloc(q, &q->d_vchunks, vch.size()));
+  CKS(upload(q->d_vchunks, vch));
+  CKS(dalloc(q, &q->d_echunks, ech.size()));
+  CKS(upload(q->d_echunks, ech));
+  q->nvchunks = (int)vch.size();
+  q->nechunks = (int)ech.size();
+  CKS(dalloc(q, &q->d_part, 2 * std::max(vch.size(), ech.size())));
+  CKS(dalloc(q, &q->dm, 1));
+  for (int k = 0; k < 6; ++k) q->user_x[k] = d->unknowns[k];
+
+  MeshProb& g = q->hm;
+  g.V = V; g.E = E; g.Vp = Vp;
+  g.vchunk_begin = 0; g.vchunk_end = q->nvchunks;
+  g.echunk_begin = 0; g.echunk_end = q->nechunks;
+  g.w_reg = d->w_reg; g.w_fit = d->w_fit;
+  g.s_w = std::sqrt(d->w_reg); g.s_f = std::sqrt(d->w_fit);
+  g.use_precond = 1; g.lm = 0;
+  g.x = q->x; g.U = U; g.degw = dgw; g.e0 = de0; g.e1 = de1;
+  g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
+  g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;
+  g.jtf_out = nullptr; g.diag_out = nullptr;
+  g.s = q->d_s;
+  g.Ehist = nullptr;
+  CKS(upload_desc(q, nullptr));
+  *out = pb.release();
+  return OPT_OK;
+}
+
+opt_status opt_problem_destroy(opt_problem* prob) {
+  if (!prob) return OPT_OK;
+  cudaDeviceSynchronize();
+  delete prob;
+  return OPT_OK;
+}
+
+opt_status opt_solve_gn(opt_problem* prob, const opt_solve_params* params, opt_report* report) {
+  return run_solve(prob, params, report, false);
+}
+
+opt_status opt_solve_lm(opt_problem* prob, const opt_solve_params* params, opt_report* report) {
+  return run_solve(prob, params, report, true);
+}
+
+opt_status opt_problem_info(const opt_problem* prob, int64_t* n_unknowns, int32_t* n_planes, int64_t* plane_len) {
+  if (!prob) return OPT_ERR_INVALID_ARG;
+  if (n_unknowns) *n_unknowns = (int64_t)prob->nx * prob->ulen;
+  if (n_planes) *n_planes = prob->nx;
+  if (plane_len) *plane_len = prob->ulen;
+  return OPT_OK;
+}
+
+// --- parity hooks and step-wise PCG ------------------------------------------
+static opt_status hook_prepare(opt_problem* pb, double lambda, bool with_outputs) {
+  if (!pb->d_tmp) CKS(dalloc(pb, &pb->d_tmp, (size_t)pb->nx * pb->plane));
+  if (with_outputs && !pb->d_jtf) {
+    CKS(dalloc(pb, &pb->d_jtf, (size_t)pb->nx * pb->plane));
+    CKS(dalloc(pb, &pb->d_diag, (size_t)pb->nm * pb->plane));
+  }
+  CK(cudaDeviceSynchronize());
+  set_flags(pb, lambda != 0.0 ? 1 : 0, 1, nullptr);
+  if (is_grid(pb)) {
+    pb->hg.jtf_out = with_outputs ? pb->d_jtf : nullptr;
+    pb->hg.diag_out = with_outputs ? pb->d_diag : nullptr;
+  } else {
+    pb->hm.jtf_out = with_outputs ? pb->d_jtf : nullptr;
+    pb->hm.diag_out = with_outputs ? pb->d_diag : nullptr;
+  }
+  CKS(upload_desc(pb, nullptr));
+  return OPT_OK;
+}
+
+static opt_status hook_finish(opt_problem* pb) {
+  if (is_grid(pb)) {
+    pb->hg.jtf_out = nullptr;
+    pb->hg.diag_out = nullptr;
+  } else {
+    pb->hm.jtf_out = nullptr;
+    pb->hm.diag_out = nullptr;
+  }
+  CKS(upload_desc(pb, nullptr));
+  return OPT_OK;
+}
+
+static opt_status hook_init(opt_problem* pb, double lambda) {
+  CKS(copy_planes_in(pb, pb->x, pb->user_x, pb->nx, nullptr));
+  k_reset<<<1, 32>>>(pb->d_s, 1, lambda);
+  st_init(pb, nullptr, -1, 1e-6f, 1e32f);
+  CK(cudaGetLastError());
+  return OPT_OK;
+}
+
+opt_status opt_pcg_init(opt_problem* prob, double lambda, double* energy) {
+  if (!prob || !(lambda >= 0.0) || !std::isfinite(lambda)) return OPT_ERR_INVALID_ARG;
+  CKS(hook_prepare(prob, lambda, false));
+  CKS(hook_init(prob, lambda));
+  CK(cudaDeviceSynchronize());
+  prob->pcg_par = 0;
+  Scalars s;
+  CK(cudaMemcpy(&s, prob->d_s, sizeof(Scalars), cudaMemcpyDeviceToHost));
+  if (energy) *energy = s.E;
+  return s.nonfinite ? OPT_ERR_NUMERIC : OPT_OK;
+}
+
+opt_status opt_pcg_step(opt_problem* prob, int32_t n_iters) {
+  if (!prob || n_iters < 0) return OPT_ERR_INVALID_ARG;
+  for (int i = 0; i < n_iters; ++i) {
+    st_apply(prob, nullptr, nullptr, prob->pcg_par, 1);
+    st_update(prob, nullptr, prob->pcg_par);
+    prob->pcg_par += 1;
+  }
+  CK(cudaGetLastError());
+  return OPT_OK;
+}
+
+opt_status opt_pcg_get_state(opt_problem* prob, float* delta, float* r, float* p, int32_t* iters_done) {
+  if (!prob) return OPT_ERR_INVALID_ARG;
+  float* planes[6];
+  if (delta) {
+    dense_planes(prob, delta, planes, prob->nx);
+    CKS(copy_planes_out(prob, planes, prob->dvec, prob->nx, nullptr));
+  }
+  if (r) {
+    dense_planes(prob, r, planes, prob->nx);
+    CKS(copy_planes_out(prob, planes, prob->rvec, prob->nx, nullptr));
+  }
+  if (p) {
+    dense_planes(prob, p, planes, prob->nx);
+    if (prob->pcg_par == 0) {
+      for (int c = 0; c < prob->nx; ++c) CK(cudaMemset(planes[c], 0, (size_t)prob->ulen * 4));
+    } else {
+      const float* src = prob->pbuf + (size_t)(prob->pcg_par & 1) * prob->nx * prob->plane;
+      CKS(copy_planes_out(prob, planes, src, prob->nx, nullptr));
+    }
+  }
+  CK(cudaDeviceSynchronize());
+  if (iters_done) {
+    Scalars s;
+    CK(cudaMemcpy(&s, prob->d_s, sizeof(Scalars), cudaMemcpyDeviceToHost));
+    *iters_done = s.pcg_iters;
+  }
+  return OPT_OK;
+}
+
+opt_status opt_apply_jtj(opt_problem* prob, const float* p, float* q, double lambda, double* pq) {
+  if (!prob || !p || !q || !(lambda >= 0.0) || !std::isfinite(lambda)) return OPT_ERR_INVALID_ARG;
+  CKS(hook_prepare(prob, lambda, false));
+  CKS(hook_init(prob, lambda));
+  float* planes[6];
+  dense_planes(prob, p, planes, prob->nx);
+  CKS(copy_planes_in(prob, prob->d_tmp, planes, prob->nx, nullptr));
+  k_force_active<<<1, 32>>>(prob->d_s, 1);
+  st_apply(prob, nullptr, prob->d_tmp, 0, 0);
+  CK(cudaGetLastError());
+  dense_planes(prob, q, planes, prob->nx);
+  CKS(copy_planes_out(prob, planes, prob->qvec, prob->nx, nullptr));
+  CK(cudaDeviceSynchronize());
+  Scalars s;
+  CK(cudaMemcpy(&s, prob->d_s, sizeof(Scalars), cudaMemcpyDeviceToHost));
+  if (pq) *pq = s.pq;
+  prob->pcg_par = 0;
+  return OPT_OK;
+}
+
+opt_status opt_eval_jtf(opt_problem* prob, float* jtf, float* diag, double* energy) {
+  if (!prob) return OPT_ERR_INVALID_ARG;
+  CKS(hook_prepare(prob, 0.0, true));
+  CKS(hook_init(prob, 0.0));
+  float* planes[6];
+  if (jtf) {
+    dense_planes(prob, jtf, planes, prob->nx);
+    CKS(copy_planes_out(prob, planes, prob->d_jtf, prob->nx, nullptr));
+  }
+  if (diag) {
+    dense_planes(prob, diag, planes, prob->nx);
+    for (int c = 0; c < prob->nx; ++c) {
+      float* one[1] = {planes[c]};
+      CKS(copy_planes_out(prob, one, prob->d_diag + (size_t)mplane_of(prob->kind, c) * prob->plane, 1, nullptr));
+    }
+  }
+  CK(cudaDeviceSynchronize());
+  Scalars s;
+  CK(cudaMemcpy(&s, prob->d_s, sizeof(Scalars), cudaMemcpyDeviceToHost));
+  if (energy) *energy = s.E;
+  prob->pcg_par = 0;
+  return hook_finish(prob);
+}
+
+opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, float* ms) {
+  if (!prob || n_iters < 1 || !ms) return OPT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CKS(hook_prepare(prob, 0.0, false));
+  const int nev = 2 * (1 + 2 * n_iters);
+  std::vector<cudaEvent_t> ev(nev, nullptr);
+  opt_status status = OPT_OK;
+  for (int i = 0; i < nev && status == OPT_OK; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) status = OPT_ERR_CUDA;
+  if (status == OPT_OK) {
+    copy_planes_in(prob, prob->x, prob->user_x, prob->nx, st);
+    k_reset<<<1, 32, 0, st>>>(prob->d_s, 1, 0.0);
+    cudaEventRecord(ev[0], st);
+    st_init(prob, st, -1, 1e-6f, 1e32f);
+    cudaEventRecord(ev[1], st);
+    for (int i = 0; i < n_iters; ++i) {
+      cudaEventRecord(ev[2 + 4 * i], st);
+      st_apply(prob, st, nullptr, i, 1);
+      cudaEventRecord(ev[3 + 4 * i], st);
+      cudaEventRecord(ev[4 + 4 * i], st);
+      st_update(prob, st, i);
+      cudaEventRecord(ev[5 + 4 * i], st);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) status = cuda_fail(e, "opt_profile_pcg");
+  }
+  if (status == OPT_OK) {
+    float t = 0.f, a = 0.f, u = 0.f;
+    cudaEventElapsedTime(&t, ev[0], ev[1]);
+    for (int i = 0; i < n_iters; ++i) {
+      float x = 0.f, y = 0.f;
+      cudaEventElapsedTime(&x, ev[2 + 4 * i], ev[3 + 4 * i]);
+      cudaEventElapsedTime(&y, ev[4 + 4 * i], ev[5 + 4 * i]);
+      a += x;
+      u += y;
+    }
+    ms[0] = t;
+    ms[1] = a / n_iters;
+    ms[2] = u / n_iters;
+    prob->pcg_par = n_iters;
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  return status;
+}
+
+opt_status opt_eval_energy(opt_problem* prob, double* energy) {
+  if (!prob) return OPT_ERR_INVALID_ARG;
+  CKS(hook_prepare(prob, 0.0, false));
+  CKS(copy_planes_in(prob, prob->x, prob->user_x, prob->nx, nullptr));
+  k_reset<<<1, 32>>>(prob->d_s, 1, 0.0);
+  st_energy(prob, nullptr, 0, -2);
+  CK(cudaGetLastError());
+  CK(cudaDeviceSynchronize());
+  Scalars s;
+  CK(cudaMemcpy(&s, prob->d_s, sizeof(Scalars), cudaMemcpyDeviceToHost));
+  if (energy) *energy = s.E;
+  return s.nonfinite ? OPT_ERR_NUMERIC : OPT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// Internal definitions shared by the CUDA translation units of the solver.
+//
+// Data layout in HBM (struct of arrays, float32):
+//  * grid problems keep every plane pitched: row pitch P = W rounded up to 32
+//    floats (128 B), plane stride P*H; tiles are TW x TH = 32 x 8 pixels;
+//  * graph problems keep vertex planes of stride Vp = V rounded up to 32;
+//  * the PCG vectors delta, r, p, q have one plane per unknown component; the
+//    inverse Jacobi preconditioner M^-1 (and the LM damping diagonal D) keep
+//    one plane per *distinct* diagonal: the x/y (x/y/z) displacement rows of a
+//    pixel (vertex) always share their diagonal entry.
+//
+// Work is described by a chunk table: one CUDA block per chunk, a chunk is a
+// run of tiles (grid) or of vertices / edges (graph) of ONE problem, so the
+// same kernels serve a single solve and a batch of uneven problems.
+//
+// Reductions (p.q, r.z, energies) are float64: each block reduces its chunk
+// (float32 products accumulated per thread over a few terms, float64 across
+// threads), writes the partial to a per-chunk slot, and the last block of a
+// problem to arrive (atomic counter) sums the problem's partials in chunk
+// order, so the result does not depend on block scheduling.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace optgb {
+
+enum Kind : int { K_WARP = 0, K_POISSON = 1, K_MESH = 2 };
+
+constexpr int TW = 32;            // grid tile width  (pixels)
+constexpr int TH = 8;             // grid tile height (pixels)
+constexpr int NT = 256;           // threads per block (grid and graph kernels)
+constexpr int HW = TW + 2;        // staged halo width
+constexpr int HH = TH + 2;        // staged halo height
+constexpr int VT = 256;           // vertices per vertex tile (graph)
+
+// Device-resident scalars of one problem.  Written only by the single
+// finishing block of a reduction or by the one-thread LM decision kernel.
+struct __align__(16) Scalars {
+  double rz;          // r.z of the current PCG iterate
+  double pq;          // p.q of the current PCG iteration
+  double E;           // E(x) at the current outer iteration
+  double E_trial;     // E(x + delta)            (LM)
+  double model;       // |F(x) + J(x) delta|^2   (LM)
+  double lambda;      // LM damping
+  double nu;          // LM damping growth factor
+  double part0;       // partial sum handed from a first graph pass to the second
+  double part1;
+  float alpha_f;      // alpha = rz / pq, rounded once to float
+  float beta_f;       // beta  = rz' / rz
+  float lambda_f;
+  float pad0;
+  int pcg_active;     // 0 once PCG broke down (rz == 0 or pq <= 0)
+  int pcg_iters;      // completed PCG iterations in the current solve
+  int accept;         // LM: the last trial step was accepted
+  int done;           // LM: converged, later kernels of the solve skip work
+  int accepted_total;
+  int outer_done;
+  int converged;
+  int nonfinite;      // a non-finite scalar was produced
+  unsigned int counter;   // last-block counter
+  unsigned int pad1[3];
+};
+
+struct Chunk {
+  int prob;           // problem index
+  int begin, end;     // tile (grid) / vertex / edge range
+  int pad;
+};
+
+// Grid problem (image warping, Poisson).  Pointers are device pointers.
+struct GridProb {
+  int kind, W, H, P;
+  int ntx, nty;                 // tiles per row / column
+  long long plane;              // P * H
+  int chunk_begin, chunk_end;   // this problem's chunks (for the final reduction)
+  float s_w, s_f, w_reg, w_fit;
+  int use_precond, lm;
+  float* x;                     // unknown planes (working copy)
+  const float* c;               // constant planes (UrShape or guidance)
+  const uint8_t* mask;          // pitched mask, NULL = none
+  float *d, *r, *p, *q;         // PCG vectors
+  float *m, *dc;                // M^-1 and LM diagonal (distinct-diagonal planes)
+  const int* hbeg;              // per tile id: first handle (ntx*nty + 1 entries)
+  const int* hpix;              // handle pixel index y*P + x, sorted by tile
+  const float* htgt;            // handle target displacement (2 per handle)
+  float* jtf_out;               // optional J^T F output planes (parity hook)
+  float* diag_out;              // optional diag(J^T J) output planes (distinct)
+  Scalars* s;
+  double* Ehist;
+};
+
+// Graph problem (ARAP mesh).
+struct MeshProb {
+  int V, E, Vp, pad;
+  int vchunk_begin, vchunk_end;
+  int echunk_begin, echunk_end;
+  float s_w, s_f, w_reg, w_fit;
+  int use_precond, lm;
+  float* x;                     // 6 planes: displacement, angles
+  const float* U;               // 3 planes
+  const float* degw;            // w_reg * (outdeg + indeg) + w_fit[handle]
+  const int* e0;                // edges sorted by (v0, v1)
+  const int* e1;
+  float *d, *r, *p, *q;         // 6 planes each
+  float *m, *dc;                // 4 planes: displacement, ax, ay, az
+  const int* hbeg;              // per vertex tile: first handle
+  const int* hpix;              // handle vertex, sorted
+  const float* htgt;            // 3 per handle
+  float* jtf_out;
+  float* diag_out;
+  Scalars* s;
+  double* Ehist;
+};
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of a and b over the block; the result is valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double sa[NT / 32], sb[NT / 32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) { sa[w] = a; sb[w] = b; }
+  __syncthreads();
+  if (w == 0) {
+    a = l < NT / 32 ? sa[l] : 0.0;
+    b = l < NT / 32 ? sb[l] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+}
+
+// Stores this chunk's two partial sums and reports whether this block is the
+// last of its problem to do so.  Must be called by every thread of the block.
+__device__ __forceinline__ bool publish_partials(double* part, int chunk, double a, double b,
+                                                 unsigned int* counter, unsigned int nchunks) {
+  __shared__ int s_last;
+  block_sum2(a, b);
+  if (threadIdx.x == 0) {
+    __stcg(&part[2 * chunk], a);
+    __stcg(&part[2 * chunk + 1], b);
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == nchunks - 1);
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+// In the last block: sums partials [cb, ce) in chunk order (thread-strided,
+// then a fixed tree) and resets the counter.  Result valid in thread 0.
+__device__ __forceinline__ void gather_partials(const double* part, int cb, int ce,
+                                                unsigned int* counter, double& a, double& b) {
+  __threadfence();
+  a = 0.0;
+  b = 0.0;
+  for (int c = cb + (int)threadIdx.x; c < ce; c += NT) {
+    a += __ldcg(&part[2 * c]);
+    b += __ldcg(&part[2 * c + 1]);
+  }
+  block_sum2(a, b);
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+// Inverse Jacobi preconditioner entry for diagonal `dg` with LM damping
+// lambda * clamp(dg): 1 / (dg + lambda * Dc); rows with a zero diagonal get 1.
+__device__ __forceinline__ float minv_entry(float dg, float lam, float dmin, float dmax,
+                                            int use_precond, float* dc_out) {
+  float dc = fminf(fmaxf(dg, dmin), dmax);
+  if (dc_out) *dc_out = dc;
+  if (!use_precond) return 1.0f;
+  const float m = dg + lam * dc;
+  return m != 0.0f ? 1.0f / m : 1.0f;
+}
+
+}  // namespace optgb

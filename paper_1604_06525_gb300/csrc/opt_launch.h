@@ -1,0 +1,41 @@
+// Host-side launch descriptors and launchers of the solver kernels.
+#pragma once
+
+#include "opt_internal.cuh"
+
+namespace optgb {
+
+struct GridLaunch {
+  const GridProb* probs;
+  const Chunk* chunks;
+  const int* tiles;
+  double* part;
+  int nchunks;
+  cudaStream_t stream;
+};
+
+struct MeshLaunch {
+  const MeshProb* probs;
+  const Chunk* vchunks;
+  const Chunk* echunks;
+  double* part;
+  float* acc;
+  int nvchunks, nechunks;
+  cudaStream_t stream;
+};
+
+// grid_kernels.cu
+void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, float dmax);
+void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, int par, int update);
+void launch_grid_update(int kind, const GridLaunch& L, int par);
+void launch_grid_energy(int kind, const GridLaunch& L, int mode, int hist_idx);
+void launch_grid_step(int kind, const GridLaunch& L, int cond);
+
+// graph_kernels.cu
+void launch_mesh_init(const MeshLaunch& L, int k_outer, float dmin, float dmax);
+void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, int update);
+void launch_mesh_update(const MeshLaunch& L, int par);
+void launch_mesh_energy(const MeshLaunch& L, int mode, int hist_idx);
+void launch_mesh_step(const MeshLaunch& L, int cond);
+
+}  // namespace optgb

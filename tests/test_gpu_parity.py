@@ -1,0 +1,347 @@
+"""Parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: J^T J p and J^T F relative error <= 1e-5 (norm-wise, float32
+arithmetic), energies and final energies <= 1e-4 relative, identical outer
+iteration counts.  Sizes span several 32x8 tiles with ragged tails, plus the
+degenerate 1x1 / 1xN / Nx1 grids and small meshes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_06525_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_PRODUCT = 1e-5
+TOL_ENERGY = 1e-4
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1604_06525_gb300 import build, api as api_mod
+    build.build()
+    api_mod.load_library()
+    return api_mod
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).reshape(-1)
+    b = np.asarray(b, np.float64).reshape(-1)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def relE(a, b):
+    return abs(a - b) / max(abs(b), 1e-30)
+
+
+def perturbed(prob, scale, seed):
+    """Random state near x0 (excluded Poisson pixels keep their values)."""
+    rng = np.random.default_rng(seed)
+    x = prob.x0.astype(np.float32).copy()
+    if prob.kind == "poisson":
+        free = prob.mask == 0
+        x[:, free] += rng.uniform(-scale, scale, size=(4, int(free.sum()))).astype(np.float32)
+    else:
+        x += rng.uniform(-scale, scale, size=x.shape).astype(np.float32)
+    prob.x0 = x
+    return prob
+
+
+def random_direction(prob, seed):
+    rng = np.random.default_rng(seed)
+    p = rng.standard_normal(prob.n_unknowns).astype(np.float32)
+    if prob.kind == "poisson":
+        p.reshape(4, -1)[:, prob.mask.reshape(-1) != 0] = 0.0
+    return p
+
+
+GRID_CASES = [
+    ("warp", 64, 64, 0.0), ("warp", 37, 29, 0.0), ("warp", 37, 29, 0.25), ("warp", 1, 1, 0.0),
+    ("warp", 1, 45, 0.0), ("warp", 70, 1, 0.0), ("warp", 100, 70, 0.1),
+    ("poisson", 64, 48, None), ("poisson", 45, 33, None), ("poisson", 1, 17, None), ("poisson", 96, 80, None),
+]
+
+
+def make_grid(kind, W, H, mask_frac, seed=11):
+    if kind == "warp":
+        mask = synth.random_mask(W, H, mask_frac, seed + 1) if mask_frac else None
+        prob = synth.warp_problem(W, H, max(1, (W * H) // 200), seed=seed, mask=mask)
+        return perturbed(prob, 0.5, seed + 2)
+    prob = synth.poisson_problem(W, H, seed=seed)
+    return perturbed(prob, 0.2, seed + 2)
+
+
+@pytest.mark.parametrize("kind,W,H,mf", GRID_CASES)
+@pytest.mark.parametrize("lam", [0.0, 0.37])
+def test_grid_apply_jtj(api, kind, W, H, mf, lam):
+    import torch
+    prob = make_grid(kind, W, H, mf)
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    p = random_direction(prob, 5)
+    gp = api.Problem(prob)
+    q, pq = gp.apply_jtj(torch.as_tensor(p, device="cuda"), lam)
+    jtf, diag, E = oracle.jtf_diag(e, x)
+    Dc = np.clip(diag, 1e-6, 1e32)
+    qref = oracle.apply_jtj(e, x, p.astype(np.float64), lam, Dc)
+    assert rel(q.cpu().numpy(), qref) <= TOL_PRODUCT
+    assert relE(pq, float(p.astype(np.float64) @ qref)) <= TOL_PRODUCT
+    gp.close()
+
+
+@pytest.mark.parametrize("kind,W,H,mf", GRID_CASES)
+def test_grid_eval_jtf(api, kind, W, H, mf):
+    prob = make_grid(kind, W, H, mf, seed=21)
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    gp = api.Problem(prob)
+    jtf, diag, E = gp.eval_jtf()
+    rj, rd, rE = oracle.jtf_diag(e, x)
+    assert rel(jtf.cpu().numpy(), rj) <= TOL_PRODUCT
+    np.testing.assert_allclose(diag.cpu().numpy().reshape(-1), rd, rtol=1e-5, atol=1e-6)
+    assert relE(E, rE) <= TOL_PRODUCT
+    assert relE(gp.energy(), rE) <= TOL_PRODUCT
+    gp.close()
+
+
+MESH_CASES = [(0, 0.3), (1, 0.2), (3, 0.1)]
+
+
+def make_mesh(level, noise, seed=31):
+    prob = synth.mesh_problem(level, seed=seed, handle_frac=0.05)
+    return perturbed(prob, noise, seed + 1)
+
+
+@pytest.mark.parametrize("level,noise", MESH_CASES)
+@pytest.mark.parametrize("lam", [0.0, 0.5])
+def test_mesh_apply_jtj(api, level, noise, lam):
+    import torch
+    prob = make_mesh(level, noise)
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    p = random_direction(prob, 7)
+    gp = api.Problem(prob)
+    q, pq = gp.apply_jtj(torch.as_tensor(p, device="cuda"), lam)
+    _, diag, _ = oracle.jtf_diag(e, x)
+    qref = oracle.apply_jtj(e, x, p.astype(np.float64), lam, np.clip(diag, 1e-6, 1e32))
+    assert rel(q.cpu().numpy(), qref) <= TOL_PRODUCT
+    assert relE(pq, float(p.astype(np.float64) @ qref)) <= TOL_PRODUCT
+    gp.close()
+
+
+@pytest.mark.parametrize("level,noise", MESH_CASES)
+def test_mesh_eval_jtf(api, level, noise):
+    prob = make_mesh(level, noise, seed=41)
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    gp = api.Problem(prob)
+    jtf, diag, E = gp.eval_jtf()
+    rj, rd, rE = oracle.jtf_diag(e, x)
+    assert rel(jtf.cpu().numpy(), rj) <= TOL_PRODUCT
+    np.testing.assert_allclose(diag.cpu().numpy().reshape(-1), rd, rtol=1e-5, atol=1e-6)
+    assert relE(E, rE) <= TOL_PRODUCT
+    gp.close()
+
+
+def test_mesh_unsorted_edges_are_sorted_by_the_library(api):
+    import torch
+    prob = make_mesh(2, 0.2, seed=51)
+    perm = np.random.default_rng(0).permutation(prob.v0.size)
+    shuffled = synth.MeshProblem(prob.V, prob.urshape, prob.v0[perm], prob.v1[perm], prob.x0,
+                                 prob.handle_idx, prob.handle_target)
+    p = random_direction(prob, 3)
+    a = api.Problem(prob)
+    b = api.Problem(shuffled)
+    qa, _ = a.apply_jtj(torch.as_tensor(p, device="cuda"))
+    qb, _ = b.apply_jtj(torch.as_tensor(p, device="cuda"))
+    assert rel(qb.cpu().numpy(), qa.cpu().numpy()) <= 1e-6
+
+
+@pytest.mark.parametrize("case", ["warp", "poisson", "mesh"])
+def test_pcg_iterates_match_oracle(api, case):
+    prob = {"warp": lambda: make_grid("warp", 45, 21, 0.0, seed=61),
+            "poisson": lambda: make_grid("poisson", 40, 30, None, seed=62),
+            "mesh": lambda: make_mesh(2, 0.2, seed=63)}[case]()
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    gp = api.Problem(prob)
+    gp.pcg_init(0.0)
+    J = e.jacobian(x)
+    F = e.residuals(x)
+    b = -(J.T @ F)
+    diag = np.asarray(J.multiply(J).sum(0)).ravel()
+    Minv = oracle.solver.jacobi_minv(diag)
+    for k in (1, 3, 6):
+        gp.pcg_init(0.0)
+        gp.pcg_step(k)
+        dl, r, p, it = gp.pcg_state()
+        d_ref, n_done, r_ref = oracle.jacobi_pcg(lambda v: J.T @ (J @ v), b, Minv, k)
+        assert it == n_done == k
+        assert rel(dl.cpu().numpy(), d_ref) <= 1e-4
+        assert rel(r.cpu().numpy(), r_ref) <= 1e-4
+
+
+def test_gn_config_warp_64(api):
+    """ARAP warp 64x64, 8 handles, GN 10 x 10, Jacobi PCG (the small configuration)."""
+    prob = synth.warp_problem(64, 64, 8, seed=synth.BASE_SEED)
+    e = oracle.make_energy(prob)
+    ref = oracle.gauss_newton(e, prob.x0.reshape(-1), 10, 10)
+    gp = api.Problem(prob)
+    rep = gp.solve_gn(10, 10)
+    assert rep["outer_done"] == 10 and rep["pcg_done"] == ref.pcg_done
+    for k, (a, b) in enumerate(zip(rep["E_history"], ref.E_history)):
+        assert relE(a, b) <= TOL_ENERGY, (k, a, b)
+    x = gp.x.cpu().numpy().reshape(-1)
+    assert rel(x, ref.x) <= 1e-3
+    assert relE(e.energy(x), ref.E_history[-1]) <= TOL_ENERGY
+
+
+def test_gn_poisson_small(api):
+    prob = synth.poisson_problem(96, 80, seed=71)
+    e = oracle.make_energy(prob)
+    ref = oracle.gauss_newton(e, prob.x0.reshape(-1), 4, 20)
+    gp = api.Problem(prob)
+    rep = gp.solve_gn(4, 20)
+    for a, b in zip(rep["E_history"], ref.E_history):
+        assert relE(a, b) <= TOL_ENERGY
+    # fixed pixels never move
+    fixed = prob.mask != 0
+    np.testing.assert_array_equal(gp.x.cpu().numpy()[:, fixed], prob.x0[:, fixed])
+
+
+def test_gn_graph_replay_equals_direct_launches(api):
+    prob = synth.warp_problem(50, 40, 6, seed=81)
+    a = api.Problem(prob)
+    b = api.Problem(prob)
+    ra = a.solve_gn(3, 8, use_graph=1)
+    rb = b.solve_gn(3, 8, use_graph=0)
+    assert ra["E_history"] == rb["E_history"]
+    assert np.array_equal(a.x.cpu().numpy(), b.x.cpu().numpy())
+    # replaying the cached graph from the same start reproduces the solve
+    a.x.copy_(__import__("torch").as_tensor(prob.x0, device="cuda"))
+    ra2 = a.solve_gn(3, 8, use_graph=1)
+    assert ra2["E_history"] == ra["E_history"]
+
+
+def test_lm_mesh_small(api):
+    prob = synth.mesh_problem(3, seed=91, handle_frac=0.02)
+    e = oracle.make_energy(prob)
+    ref = oracle.levenberg_marquardt(e, prob.x0.reshape(-1), 6, 15)
+    gp = api.Problem(prob)
+    rep = gp.solve_lm(6, 15, lambda0=1e-3)
+    assert rep["outer_done"] == ref.outer_done
+    assert rep["accepted"] == sum(ref.accepted)
+    for a, b in zip(rep["E_history"], ref.E_history):
+        assert relE(a, b) <= TOL_ENERGY
+    assert relE(rep["lambda_final"], ref.lambda_final) <= 1e-9
+
+
+def test_lm_rejections_follow_nielsen(api):
+    prob = synth.poisson_problem(30, 20, seed=92)
+    gp = api.Problem(prob)
+    rep = gp.solve_lm(4, 10, lambda0=1e-3, eta=2.0)
+    assert rep["accepted"] == 0 and rep["outer_done"] == 4
+    assert rep["lambda_final"] == pytest.approx(1e-3 * 2 * 4 * 8 * 16, rel=1e-12)
+    np.testing.assert_array_equal(gp.x.cpu().numpy(), prob.x0)
+
+
+def test_lm_relative_tolerance_stops_like_oracle(api):
+    prob = synth.warp_problem(48, 40, 6, seed=93)
+    e = oracle.make_energy(prob)
+    prm = oracle.LMParams(rel_tol=1e-2)
+    ref = oracle.levenberg_marquardt(e, prob.x0.reshape(-1), 10, 10, prm)
+    gp = api.Problem(prob)
+    rep = gp.solve_lm(10, 10, rel_tol=1e-2)
+    assert rep["outer_done"] == ref.outer_done
+    assert rep["converged"] == int(ref.outer_done < 10)
+    for a, b in zip(rep["E_history"], ref.E_history):
+        assert relE(a, b) <= TOL_ENERGY
+
+
+def test_invalid_arguments(api):
+    import ctypes
+    import torch
+    lib = api.load_library()
+    prob = synth.warp_problem(8, 8, 2, seed=1)
+    bad = synth.warp_problem(8, 8, 2, seed=1)
+    bad.handle_idx = np.array([3, 3], np.int32)           # duplicate handle
+    with pytest.raises(api.OptError) as ei:
+        api.Problem(bad)
+    assert ei.value.status == 1
+    bad.handle_idx = np.array([3, 64], np.int32)          # out of range
+    with pytest.raises(api.OptError):
+        api.Problem(bad)
+    bad = synth.warp_problem(8, 8, 2, seed=1)
+    bad.urshape = bad.urshape.copy()
+    bad.urshape[0, 2, 2] = np.nan                          # non-finite constant
+    with pytest.raises(api.OptError):
+        api.Problem(bad)
+    m = synth.mesh_problem(0, seed=1)
+    m.v1 = m.v1.copy()
+    m.v1[0] = m.V                                          # edge out of range
+    with pytest.raises(api.OptError):
+        api.Problem(m)
+    gp = api.Problem(prob)
+    p = api.default_params(outer=0, inner=5)
+    assert lib.opt_solve_gn(gp.h, ctypes.byref(p), None) == 1
+    gp.close()
+    torch.cuda.synchronize()
+
+
+def test_full_size_warp_apply_and_solve_start(api):
+    """ARAP warp 1024x1024 with 64 handles (the grid-at-scale configuration):
+    J^T J p over the whole grid and the first GN iterations against the oracle."""
+    import torch
+    prob = synth.warp_problem(1024, 1024, 64, seed=synth.BASE_SEED)
+    prob = perturbed(prob, 0.3, 5)
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    gp = api.Problem(prob)
+    p = random_direction(prob, 9)
+    q, _ = gp.apply_jtj(torch.as_tensor(p, device="cuda"))
+    J = e.jacobian(x)
+    qref = J.T @ (J @ p.astype(np.float64))
+    assert rel(q.cpu().numpy(), qref) <= TOL_PRODUCT
+    jtf, _, E = gp.eval_jtf()
+    assert rel(jtf.cpu().numpy(), J.T @ e.residuals(x)) <= TOL_PRODUCT
+    ref = oracle.gauss_newton(e, x, 2, 20)
+    rep = gp.solve_gn(2, 20)
+    for a, b in zip(rep["E_history"], ref.E_history):
+        assert relE(a, b) <= TOL_ENERGY
+
+
+def test_full_size_poisson_apply(api):
+    import torch
+    prob = synth.poisson_problem(1024, 1024, seed=synth.BASE_SEED)
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    gp = api.Problem(prob)
+    p = random_direction(prob, 4)
+    q, _ = gp.apply_jtj(torch.as_tensor(p, device="cuda"))
+    J = e.jacobian()
+    assert rel(q.cpu().numpy(), J.T @ (J @ p.astype(np.float64))) <= TOL_PRODUCT
+    ref = oracle.gauss_newton(e, x, 2, 20)
+    rep = gp.solve_gn(2, 20)
+    for a, b in zip(rep["E_history"], ref.E_history):
+        assert relE(a, b) <= TOL_ENERGY
+
+
+def test_full_size_mesh_apply(api):
+    """Icosphere level 7 (163,842 vertices, 983,040 directed edges)."""
+    import torch
+    prob = synth.mesh_problem(7, seed=synth.BASE_SEED)
+    prob = perturbed(prob, 0.05, 6)
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    gp = api.Problem(prob)
+    p = random_direction(prob, 8)
+    q, _ = gp.apply_jtj(torch.as_tensor(p, device="cuda"))
+    J = e.jacobian(x)
+    assert rel(q.cpu().numpy(), J.T @ (J @ p.astype(np.float64))) <= TOL_PRODUCT
+    jtf, _, E = gp.eval_jtf()
+    assert rel(jtf.cpu().numpy(), J.T @ e.residuals(x)) <= TOL_PRODUCT
