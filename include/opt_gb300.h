@@ -217,6 +217,37 @@ opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, flo
 opt_status opt_problem_info(const opt_problem* prob, int64_t* n_unknowns, int32_t* n_planes,
                             int64_t* plane_len);
 
+/* Allocation-free variant of the warp J^T J p (no counterpart in the paper).
+ * For callers that cannot call cudaMalloc: interactive loops on a fixed frame
+ * budget that must not stall on an allocation, and host applications or
+ * plug-in hosts that own all device memory and hand a component only its
+ * buffers.  Computes q = J^T J p (lambda = 0) for an OPT_ARAP_WARP_2D energy
+ * at x, exactly as opt_apply_jtj does, and p.q in float64, without any
+ * allocation: its only scratch (float64 reduction partials, an arrival
+ * counter) is a file-scope device array of 262,400 bytes that every device
+ * loading the library holds until the process exits.
+ *   x        device, 3*W*H floats: dx, dy, theta planes (row-major, y*W + x)
+ *   urshape  device, 2*W*H floats: UrShape x, y planes
+ *   mask     device, W*H bytes (nonzero = excluded) or NULL
+ *   handle_idx device, n_handles pixel indices (may be NULL if n_handles = 0)
+ *   p        device, 3*W*H floats (input direction)
+ *   q        device, 3*W*H floats (output)
+ *   pq       device, one double (output p.q) or NULL
+ *   stream   cudaStream_t (NULL = legacy default stream); the call only
+ *            enqueues work and does not synchronise.
+ * Limits: ceil(W/32) * ceil(H/8) <= OPT_NOALLOC_MAX_TILES (e.g. 2048 x 2048);
+ * larger grids, W or H outside [1, 32768), null inputs or negative weights
+ * return OPT_ERR_INVALID_ARG before any device work.  The first call made
+ * with a given device current looks up the array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.  All calls
+ * share the array and each clears its counter on entry: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller. */
+#define OPT_NOALLOC_MAX_TILES 16384
+opt_status opt_warp_apply_jtj_noalloc(int32_t W, int32_t H, const float* x, const float* urshape,
+                                      const uint8_t* mask, const int32_t* handle_idx, int32_t n_handles,
+                                      float w_reg, float w_fit, const float* p, float* q, double* pq,
+                                      void* stream);
+
 /* Human-readable name of a status code; never NULL. */
 const char* opt_status_str(opt_status s);
 

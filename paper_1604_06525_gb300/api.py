@@ -66,6 +66,9 @@ _SIGNATURES = [
     ("opt_eval_energy", c_int32, [c_void_p, POINTER(c_double)]),
     ("opt_profile_pcg", c_int32, [c_void_p, c_int32, c_void_p, POINTER(c_float)]),
     ("opt_problem_info", c_int32, [c_void_p, POINTER(c_int64), POINTER(c_int32), POINTER(c_int64)]),
+    ("opt_warp_apply_jtj_noalloc", c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
+                                             c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p,
+                                             c_void_p]),
     ("opt_status_str", ctypes.c_char_p, [c_int32]),
     ("opt_last_error", ctypes.c_char_p, []),
 ]
