@@ -50,11 +50,10 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
-    h = hashlib.sha256()
-    for f in ("grid_kernels.cu", "opt_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1604_06525_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+    """sha256[:16] of the grid kernel source (the traffic figure is dropped
+    when it changes)."""
+    with open(os.path.join(ROOT, "paper_1604_06525_gb300", "csrc", "grid_kernels.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str, workload: str):
@@ -274,15 +273,36 @@ def run_ours(args):
     dom = max(roof, key=lambda k: roof[k]["ms"] * (1 if k == "k_warp_apply" else 1))
     roof_big, _ = roofline_for(api, synth, torch, 4096, 4096, peak)
 
-    # secondary workloads (one solve each)
+    # secondary workloads: matrix-free vs materialized J (Sec. 8.3) on the
+    # warp and on Poisson editing at 1024 x 1024, then the mesh under LM
     extra = {}
+
+    def timed(g, x_init, fn, n=3, **kw):
+        out = []
+        for _ in range(n + 1):
+            flush.zero_()
+            g.x.copy_(x_init)
+            out.append(fn(OUTER, INNER, **kw))
+        return out[1:]
+
+    rr_mat = timed(gp, x0, gp.solve_gn, materialized=1)
+    ms_mat = statistics.median(r_["ms"] for r_ in rr_mat)
+    extra["warp_1024x1024_materialized_gn20x20"] = {
+        "pcg_iters_per_s": OUTER * INNER / (ms_mat / 1e3), "ms_per_solve": ms_mat,
+        "matrix_free_speedup": ms_mat / ms_per_step, "E_final": rr_mat[-1]["E_final"],
+        "E_final_matrix_free": E_final}
     pp = synth.poisson_problem(W_BENCH, H_BENCH, seed=synth.BASE_SEED)
     gpp = api.Problem(pp)
-    gpp.solve_gn(OUTER, INNER)
-    rr = [gpp.solve_gn(OUTER, INNER) for _ in range(3)]
-    extra["poisson_1024x1024x4_gn20x20"] = {"pcg_iters_per_s": OUTER * INNER / (statistics.median(r_["ms"] for r_ in rr) / 1e3),
-                                           "ms_per_solve": statistics.median(r_["ms"] for r_ in rr),
+    xp0 = gpp.x.clone()
+    rr = timed(gpp, xp0, gpp.solve_gn)
+    rrm = timed(gpp, xp0, gpp.solve_gn, materialized=1)
+    msp = statistics.median(r_["ms"] for r_ in rr)
+    mspm = statistics.median(r_["ms"] for r_ in rrm)
+    extra["poisson_1024x1024x4_gn20x20"] = {"pcg_iters_per_s": OUTER * INNER / (msp / 1e3), "ms_per_solve": msp,
                                            "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
+    extra["poisson_1024x1024x4_materialized_gn20x20"] = {
+        "pcg_iters_per_s": OUTER * INNER / (mspm / 1e3), "ms_per_solve": mspm,
+        "matrix_free_speedup": mspm / msp, "E_final": rrm[-1]["E_final"]}
     gpp.close()
     mp = synth.mesh_problem(7, seed=synth.BASE_SEED)
     gmp = api.Problem(mp)

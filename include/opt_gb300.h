@@ -217,6 +217,42 @@ opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, flo
 opt_status opt_problem_info(const opt_problem* prob, int64_t* n_unknowns, int32_t* n_planes,
                             int64_t* plane_len);
 
+/* ---------------------------------------------------------------------------
+ * Batched solves: many planned problems of uneven sizes advanced together,
+ * one launch per solver phase for the whole batch.  The paper solves one
+ * problem at a time; the batch runs, for every member, exactly the sequence of
+ * opt_solve_gn / opt_solve_lm (same outer / inner counts for all members), so
+ * each member's result equals its solo solve up to float rounding.
+ * ------------------------------------------------------------------------- */
+typedef struct opt_batch opt_batch;
+
+/* Builds a batch over n distinct planned problems (any mix of kinds; probs:
+ * host array).  The problems must outlive the batch and must not be solved
+ * on their own while a batched solve is in flight.  OPT_ERR_INVALID_ARG on a
+ * null or repeated problem or n < 1. */
+opt_status opt_batch_create(opt_problem* const* probs, int32_t n, opt_batch** out);
+
+/* Frees the batch (not its problems).  NULL is accepted. */
+opt_status opt_batch_destroy(opt_batch* batch);
+
+/* Work granularity: tiles_per_chunk consecutive 32x8 tiles of one problem per
+ * block (0 = each problem's own default, about 8 blocks per SM per problem). */
+opt_status opt_batch_set_chunking(opt_batch* batch, int32_t tiles_per_chunk);
+
+/* Autotuner: times one outer iteration (<= 4 PCG iterations) of the batch for
+ * each candidate granularity {default, 1, 2, 4, 8, 16} without writing the
+ * unknowns back, keeps the fastest and returns it in *chosen (host, may be
+ * NULL) and its time in *best_ms (host, may be NULL). */
+opt_status opt_batch_autotune(opt_batch* batch, const opt_solve_params* params, int32_t* chosen,
+                              float* best_ms);
+
+/* Batched Gauss-Newton / Levenberg-Marquardt over every member (Sec. 4), the
+ * whole batched solve replayed as one CUDA graph.  reports: host array of n
+ * opt_report (each E_history may be NULL), or NULL.  ms (host, may be NULL):
+ * device time of the batched solve.  params->materialized must be 0. */
+opt_status opt_batch_solve_gn(opt_batch* batch, const opt_solve_params* params, opt_report* reports, float* ms);
+opt_status opt_batch_solve_lm(opt_batch* batch, const opt_solve_params* params, opt_report* reports, float* ms);
+
 /* Allocation-free variant of the warp J^T J p (no counterpart in the paper).
  * For callers that cannot call cudaMalloc: interactive loops on a fixed frame
  * budget that must not stall on an allocation, and host applications or

@@ -22,6 +22,7 @@
 #include "opt_gb300.h"
 #include "opt_internal.cuh"
 #include "opt_launch.h"
+#include "opt_problem.h"
 
 using namespace optgb;
 
@@ -104,58 +105,6 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 }  // namespace
 
-struct opt_problem {
-  int kind = 0;
-  int nx = 0;             // unknown planes
-  int nm = 0;             // distinct-diagonal planes
-  int sms = 148;
-  // grid
-  int W = 0, H = 0, P = 0;
-  // graph
-  int V = 0, E = 0;
-  long long plane = 0;    // internal plane stride (P*H or Vp)
-  long long ulen = 0;     // caller plane length (W*H or V)
-  GridProb hg{};
-  GridProb* dg = nullptr;
-  Chunk* d_chunks = nullptr;
-  int nchunks = 0;
-  int* d_tiles = nullptr;
-  int ntiles = 0;
-  MeshProb hm{};
-  MeshProb* dm = nullptr;
-  Chunk* d_vchunks = nullptr;
-  Chunk* d_echunks = nullptr;
-  int nvchunks = 0, nechunks = 0;
-  float* d_acc = nullptr;
-  // common
-  double* d_part = nullptr;
-  Scalars* d_s = nullptr;
-  double* d_Ehist = nullptr;
-  int Ehist_cap = 0;
-  float* user_x[6] = {};
-  float* d_tmp = nullptr;     // nx planes: caller p (apply hook)
-  float* d_jtf = nullptr;     // nx planes: J^T F (hook)
-  float* d_diag = nullptr;    // nm planes: diag (hook)
-  float* x = nullptr;
-  float* pbuf = nullptr;
-  float* dvec = nullptr;
-  float* rvec = nullptr;
-  float* qvec = nullptr;
-  std::vector<void*> allocs;
-  int pcg_par = 0;
-  cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<double> gkey;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-
-  ~opt_problem() {
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (cap_stream) cudaStreamDestroy(cap_stream);
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-    for (void* p : allocs) cudaFree(p);
-  }
-};
 
 namespace {
 
@@ -314,8 +263,10 @@ opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cu
   k_reset<<<1, 32, 0, st>>>(pb->d_s, 1, lm ? p.lambda0 : 0.0);
   for (int k = 0; k < p.outer; ++k) {
     st_init(pb, st, k, dmin, dmax);
+    if (p.materialized) csr_evalj(pb, st);
     for (int i = 0; i < p.inner; ++i) {
-      st_apply(pb, st, nullptr, i, 1);
+      if (p.materialized) csr_apply(pb, st, i);
+      else st_apply(pb, st, nullptr, i, 1);
       st_update(pb, st, i);
     }
     if (!lm) {
@@ -357,7 +308,8 @@ opt_status run_solve(opt_problem* pb, const opt_solve_params* prm_in, opt_report
   if (prm_in) p = *prm_in;
   else opt_solve_params_default(&p);
   CKS(check_params(p, lm));
-  if (p.materialized) return OPT_ERR_INVALID_ARG;   // materialized path: see opt_solve_* docs
+  if (p.materialized != 0 && p.materialized != 1) return OPT_ERR_INVALID_ARG;
+  if (p.materialized) CKS(csr_build(pb));
   cudaStream_t st = (cudaStream_t)p.stream;
   CK(cudaStreamSynchronize(st));
   CKS(ensure_ehist(pb, p.outer + 1));
@@ -592,6 +544,8 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   CKS(dalloc(q, &q->d_part, 2 * chunks.size()));
   CKS(dalloc(q, &q->dg, 1));
   for (int k = 0; k < nx; ++k) q->user_x[k] = d->unknowns[k];
+  q->h_mask = mask;
+  q->h_hpix = hpix;
 
   GridProb& g = q->hg;
   g.kind = q->kind;
@@ -736,6 +690,9 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   CKS(dalloc(q, &q->d_part, 2 * std::max(vch.size(), ech.size())));
   CKS(dalloc(q, &q->dm, 1));
   for (int k = 0; k < 6; ++k) q->user_x[k] = d->unknowns[k];
+  q->h_e0 = e0;
+  q->h_e1 = e1;
+  q->h_hpix = hpix;
 
   MeshProb& g = q->hm;
   g.V = V; g.E = E; g.Vp = Vp;

@@ -24,45 +24,6 @@ namespace optgb {
 
 namespace {
 
-// Rotation R = Rz(c) Ry(b) Rx(a) applied to v, and its three angle
-// derivatives applied to v.
-struct RotV {
-  float rv[3];
-  float g[3][3];    // g[m] = dR/dA_m v
-};
-
-__device__ __forceinline__ RotV rot_apply(float ax, float ay, float az, float vx, float vy, float vz) {
-  float sa, ca, sb, cb, sc, cc;
-  sincosf(ax, &sa, &ca);
-  sincosf(ay, &sb, &cb);
-  sincosf(az, &sc, &cc);
-  // w = Rx v, w' = dRx v
-  const float w0 = vx, w1 = ca * vy - sa * vz, w2 = sa * vy + ca * vz;
-  const float wd1 = -sa * vy - ca * vz, wd2 = ca * vy - sa * vz;   // wd0 = 0
-  // y = Ry w, y' (from dRy) = dRy w, ya = Ry w'
-  const float y0 = cb * w0 + sb * w2, y1 = w1, y2 = -sb * w0 + cb * w2;
-  const float yb0 = -sb * w0 + cb * w2, yb2 = -cb * w0 - sb * w2;     // yb1 = 0
-  const float ya0 = sb * wd2, ya1 = wd1, ya2 = cb * wd2;
-  RotV o;
-  // R v = Rz y
-  o.rv[0] = cc * y0 - sc * y1;
-  o.rv[1] = sc * y0 + cc * y1;
-  o.rv[2] = y2;
-  // dR/dax v = Rz Ry dRx v = Rz ya
-  o.g[0][0] = cc * ya0 - sc * ya1;
-  o.g[0][1] = sc * ya0 + cc * ya1;
-  o.g[0][2] = ya2;
-  // dR/day v = Rz dRy Rx v = Rz yb
-  o.g[1][0] = cc * yb0;
-  o.g[1][1] = sc * yb0;
-  o.g[1][2] = yb2;
-  // dR/daz v = dRz Ry Rx v = dRz y
-  o.g[2][0] = -sc * y0 - cc * y1;
-  o.g[2][1] = cc * y0 - sc * y1;
-  o.g[2][2] = 0.f;
-  return o;
-}
-
 // Segment structure of a warp whose lanes hold sorted keys.
 struct Seg {
   unsigned flags;   // bit k: lane + 2^k is in this lane's segment

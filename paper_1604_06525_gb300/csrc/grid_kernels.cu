@@ -168,72 +168,139 @@ __global__ void __launch_bounds__(NT) k_warp_init(const GridProb* __restrict__ p
   }
 }
 
+// Cells of the one-pixel halo ring around a 32x8 tile: 2*HW + 2*TH = 84.
+constexpr int NHALO = 2 * HW + 2 * TH;
+
+__device__ __forceinline__ void halo_cell(int h, int& hy, int& hx) {
+  if (h < HW) { hy = 0; hx = h; }
+  else if (h < 2 * HW) { hy = HH - 1; hx = h - HW; }
+  else if (h < 2 * HW + TH) { hy = h - 2 * HW + 1; hx = 0; }
+  else { hy = h - 2 * HW - TH + 1; hx = HW - 1; }
+}
+
+// Global values of one staged warp cell, held in registers between the load
+// (issued one tile ahead) and the shared-memory store.
+struct WarpCell {
+  float r0, r1, r2, m0, m1, p0, p1, p2, th, u0, u1;
+  int inb;
+  int v;
+};
+
+__device__ __forceinline__ void warp_cell_load(WarpCell& c, const GridProb& pr, const float* __restrict__ pin,
+                                               int gx, int gy, int update, int use_beta) {
+  c.r0 = c.r1 = c.r2 = c.m0 = c.m1 = c.p0 = c.p1 = c.p2 = c.th = c.u0 = c.u1 = 0.f;
+  c.v = 0;
+  c.inb = (gx >= 0 && gx < pr.W && gy >= 0 && gy < pr.H);
+  if (!c.inb) return;
+  const long long pl = pr.plane;
+  const long long i = (long long)gy * pr.P + gx;
+  if (update) {
+    c.r0 = __ldg(pr.r + i);
+    c.r1 = __ldg(pr.r + pl + i);
+    c.r2 = __ldg(pr.r + 2 * pl + i);
+    c.m0 = __ldg(pr.m + i);
+    c.m1 = __ldg(pr.m + pl + i);
+  }
+  if (!update || use_beta) {
+    c.p0 = __ldg(pin + i);
+    c.p1 = __ldg(pin + pl + i);
+    c.p2 = __ldg(pin + 2 * pl + i);
+  }
+  c.th = __ldg(pr.x + 2 * pl + i);
+  c.u0 = __ldg(pr.c + i);
+  c.u1 = __ldg(pr.c + pl + i);
+  c.v = pr.mask ? (__ldg(pr.mask + i) == 0) : 1;
+}
+
+struct WarpApplyStage {
+  float a[HH][HW], b[HH][HW], t[HH][HW];   // direction p (x, y, theta)
+  float cs[HH][HW], sn[HH][HW];            // cos / sin theta
+  float ux[HH][HW], uy[HH][HW];            // UrShape
+  unsigned char v[HH][HW];                 // residuals touching the cell are valid
+};
+
+// Direction p = M^-1 r + beta p_old (or the caller's p) and trig of theta
+// into shared memory; owned cells also write the new direction.
+__device__ __forceinline__ void warp_cell_store(WarpApplyStage& st, int hy, int hx, const WarpCell& c,
+                                                int update, int use_beta, float beta,
+                                                float* __restrict__ pout, const GridProb& pr,
+                                                long long i_owned) {
+  float px = 0.f, py = 0.f, pt = 0.f, cs = 1.f, sn = 0.f;
+  if (c.inb) {
+    if (update) {
+      px = c.m0 * c.r0;
+      py = c.m0 * c.r1;
+      pt = c.m1 * c.r2;
+      if (use_beta) {
+        px += beta * c.p0;
+        py += beta * c.p1;
+        pt += beta * c.p2;
+      }
+      if (i_owned >= 0) {
+        const long long pl = pr.plane;
+        pout[i_owned] = px;
+        pout[pl + i_owned] = py;
+        pout[2 * pl + i_owned] = pt;
+      }
+    } else {
+      px = c.p0; py = c.p1; pt = c.p2;
+    }
+    sincosf(c.th, &sn, &cs);
+  }
+  st.a[hy][hx] = px; st.b[hy][hx] = py; st.t[hy][hx] = pt;
+  st.cs[hy][hx] = cs; st.sn[hy][hx] = sn;
+  st.ux[hy][hx] = c.u0; st.uy[hy][hx] = c.u1;
+  st.v[hy][hx] = (unsigned char)c.v;
+}
+
 // q = (J^T J + lambda D) p for the warp; with `update` the direction is
 // first advanced, p = M^-1 r + beta p_old, for every staged pixel (halo
-// included) and written for the owned pixels.
-__global__ void __launch_bounds__(NT) k_warp_apply(const GridProb* __restrict__ probs,
-                                                   const Chunk* __restrict__ chunks,
-                                                   const int* __restrict__ tiles,
-                                                   double* __restrict__ part,
-                                                   const float* __restrict__ p_in_override,
-                                                   int par, int update) {
+// included) and written for the owned pixels.  The global loads of tile t+1
+// are issued before tile t is computed, so they are in flight meanwhile.
+__global__ void __launch_bounds__(NT, 3) k_warp_apply(const GridProb* __restrict__ probs,
+                                                      const Chunk* __restrict__ chunks,
+                                                      const int* __restrict__ tiles,
+                                                      double* __restrict__ part,
+                                                      const float* __restrict__ p_in_override,
+                                                      int par, int update) {
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
-  __shared__ WarpStage st;
+  __shared__ WarpApplyStage st;
   const long long pl = pr.plane;
   const int P = pr.P, W = pr.W, H = pr.H;
-  const float sw = pr.s_w, wreg = pr.w_reg, wfit = pr.w_fit;
+  const float sw = pr.s_w, wfit = pr.w_fit;
   const float beta = s->beta_f;
+  const int use_beta = beta != 0.0f;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const float* __restrict__ pin = p_in_override ? p_in_override : pr.p + (long long)(par & 1) * 3 * pl;
   float* __restrict__ pout = pr.p + (long long)((par + 1) & 1) * 3 * pl;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const bool has_halo = tid < NHALO;
+  int hhy = 0, hhx = 0;
+  if (has_halo) halo_cell(tid, hhy, hhx);
   float acc = 0.f;
-  (void)wreg;
+  WarpCell A, B;
+  int tc = tiles[ch.begin];
+  warp_cell_load(A, pr, pin, tile_x0(tc) + tx, tile_y0(tc) + ty, update, use_beta);
+  if (has_halo) warp_cell_load(B, pr, pin, tile_x0(tc) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
   for (int t = ch.begin; t < ch.end; ++t) {
-    const int tc = tiles[t];
     const int x0 = tile_x0(tc), y0 = tile_y0(tc);
-    for (int hc = threadIdx.x; hc < HW * HH; hc += NT) {
-      const int hy = hc / HW, hx = hc - hy * HW;
-      const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-      float px = 0.f, py = 0.f, pt = 0.f, th = 0.f, ux = 0.f, uy = 0.f;
-      unsigned char v = 0;
-      if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-        const long long i = (long long)gy * P + gx;
-        if (update) {
-          const float md = pr.m[i], mt = pr.m[pl + i];
-          px = md * pr.r[i];
-          py = md * pr.r[pl + i];
-          pt = mt * pr.r[2 * pl + i];
-          if (beta != 0.0f) {
-            px += beta * pin[i];
-            py += beta * pin[pl + i];
-            pt += beta * pin[2 * pl + i];
-          }
-          if (hx >= 1 && hx <= TW && hy >= 1 && hy <= TH) {
-            pout[i] = px; pout[pl + i] = py; pout[2 * pl + i] = pt;
-          }
-        } else {
-          px = pin[i]; py = pin[pl + i]; pt = pin[2 * pl + i];
-        }
-        th = pr.x[2 * pl + i];
-        ux = pr.c[i];
-        uy = pr.c[pl + i];
-        v = pr.mask ? (pr.mask[i] == 0) : 1;
-      }
-      float sn, cs;
-      sincosf(th, &sn, &cs);
-      st.a[hy][hx] = px; st.b[hy][hx] = py; st.t[hy][hx] = pt;
-      st.cs[hy][hx] = cs; st.sn[hy][hx] = sn;
-      st.ux[hy][hx] = ux; st.uy[hy][hx] = uy; st.v[hy][hx] = v;
-    }
-    __syncthreads();
     const int gx = x0 + tx, gy = y0 + ty;
+    const long long i = (long long)gy * P + gx;
+    __syncthreads();
+    warp_cell_store(st, ty + 1, tx + 1, A, update, use_beta, beta, pout, pr, (gx < W && gy < H) ? i : -1);
+    if (has_halo) warp_cell_store(st, hhy, hhx, B, update, use_beta, beta, pout, pr, -1);
+    __syncthreads();
+    const int tcur = tc;
+    if (t + 1 < ch.end) {
+      tc = tiles[t + 1];
+      warp_cell_load(A, pr, pin, tile_x0(tc) + tx, tile_y0(tc) + ty, update, use_beta);
+      if (has_halo) warp_cell_load(B, pr, pin, tile_x0(tc) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
+    }
     if (gx < W && gy < H) {
       const int lx = tx + 1, ly = ty + 1;
-      const long long i = (long long)gy * P + gx;
       const float pxi = st.a[ly][lx], pyi = st.b[ly][lx], pti = st.t[ly][lx];
       float qx = 0.f, qy = 0.f, qt = 0.f;
       if (st.v[ly][lx]) {
@@ -262,8 +329,8 @@ __global__ void __launch_bounds__(NT) k_warp_apply(const GridProb* __restrict__ 
           qx -= sw * kpx;
           qy -= sw * kpy;
         }
-        const int tid = tile_id(pr, tc);
-        for (int h = pr.hbeg[tid]; h < pr.hbeg[tid + 1]; ++h) {
+        const int tid_ = tile_id(pr, tcur);
+        for (int h = pr.hbeg[tid_]; h < pr.hbeg[tid_ + 1]; ++h) {
           if (pr.hpix[h] == (int)i) { qx += wfit * pxi; qy += wfit * pyi; }
         }
         if (pr.lm) {
@@ -276,7 +343,6 @@ __global__ void __launch_bounds__(NT) k_warp_apply(const GridProb* __restrict__ 
       pr.q[i] = qx; pr.q[pl + i] = qy; pr.q[2 * pl + i] = qt;
       acc += pxi * qx + pyi * qy + pti * qt;
     }
-    __syncthreads();
   }
   if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double pq, unused;
@@ -504,66 +570,101 @@ __global__ void __launch_bounds__(NT) k_poisson_init(const GridProb* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(NT) k_poisson_apply(const GridProb* __restrict__ probs,
-                                                      const Chunk* __restrict__ chunks,
-                                                      const int* __restrict__ tiles,
-                                                      double* __restrict__ part,
-                                                      const float* __restrict__ p_in_override,
-                                                      int par, int update) {
+struct PoisCell {
+  float r[4], p[4], m;
+  int inb;
+  int f;
+};
+
+__device__ __forceinline__ void pois_cell_load(PoisCell& c, const GridProb& pr, const float* __restrict__ pin,
+                                               int gx, int gy, int update, int use_beta) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { c.r[k] = 0.f; c.p[k] = 0.f; }
+  c.m = 0.f;
+  c.f = 0;
+  c.inb = (gx >= 0 && gx < pr.W && gy >= 0 && gy < pr.H);
+  if (!c.inb) return;
+  const long long pl = pr.plane;
+  const long long i = (long long)gy * pr.P + gx;
+  if (update) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c.r[k] = __ldg(pr.r + k * pl + i);
+    c.m = __ldg(pr.m + i);
+  }
+  if (!update || use_beta) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) c.p[k] = __ldg(pin + k * pl + i);
+  }
+  c.f = pr.mask ? (__ldg(pr.mask + i) == 0 ? 2 : 1) : 2;
+}
+
+struct PoisApplyStage {
+  float p[4][HH][HW];
+  unsigned char f[HH][HW];   // 0 = outside, 1 = fixed, 2 = free
+};
+
+__device__ __forceinline__ void pois_cell_store(PoisApplyStage& st, int hy, int hx, const PoisCell& c,
+                                                int update, int use_beta, float beta,
+                                                float* __restrict__ pout, long long pl, long long i_owned) {
+  float pv[4] = {0.f, 0.f, 0.f, 0.f};
+  if (c.inb && c.f == 2) {   // fixed pixels carry no unknown: p = 0 there
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      pv[k] = update ? c.m * c.r[k] : c.p[k];
+      if (update && use_beta) pv[k] += beta * c.p[k];
+    }
+  }
+  if (update && c.inb && i_owned >= 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pout[k * pl + i_owned] = pv[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) st.p[k][hy][hx] = pv[k];
+  st.f[hy][hx] = (unsigned char)(c.inb ? c.f : 0);
+}
+
+__global__ void __launch_bounds__(NT, 3) k_poisson_apply(const GridProb* __restrict__ probs,
+                                                         const Chunk* __restrict__ chunks,
+                                                         const int* __restrict__ tiles,
+                                                         double* __restrict__ part,
+                                                         const float* __restrict__ p_in_override,
+                                                         int par, int update) {
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
-  __shared__ PoissonStage st;
+  __shared__ PoisApplyStage st;
   const long long pl = pr.plane;
   const int P = pr.P, W = pr.W, H = pr.H;
   const float beta = s->beta_f;
+  const int use_beta = beta != 0.0f;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const float* __restrict__ pin = p_in_override ? p_in_override : pr.p + (long long)(par & 1) * 4 * pl;
   float* __restrict__ pout = pr.p + (long long)((par + 1) & 1) * 4 * pl;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const bool has_halo = tid < NHALO;
+  int hhy = 0, hhx = 0;
+  if (has_halo) halo_cell(tid, hhy, hhx);
   float acc = 0.f;
+  PoisCell A, B;
+  int tc = tiles[ch.begin];
+  pois_cell_load(A, pr, pin, tile_x0(tc) + tx, tile_y0(tc) + ty, update, use_beta);
+  if (has_halo) pois_cell_load(B, pr, pin, tile_x0(tc) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
   for (int t = ch.begin; t < ch.end; ++t) {
-    const int tc = tiles[t];
     const int x0 = tile_x0(tc), y0 = tile_y0(tc);
-    for (int hc = threadIdx.x; hc < HW * HH; hc += NT) {
-      const int hy = hc / HW, hx = hc - hy * HW;
-      const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
-      unsigned char f = 0;
-      float pv[4] = {0.f, 0.f, 0.f, 0.f};
-      if (gx >= 0 && gx < W && gy >= 0 && gy < H) {
-        const long long i = (long long)gy * P + gx;
-        f = poisson_flag(pr, i);
-        if (update) {
-          const float mv = pr.m[i];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            float v = mv * pr.r[c * pl + i];
-            if (beta != 0.0f) v += beta * pin[c * pl + i];
-            pv[c] = v;
-          }
-          if (hx >= 1 && hx <= TW && hy >= 1 && hy <= TH) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) pout[c * pl + i] = pv[c];
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) pv[c] = pin[c * pl + i];
-        }
-        if (f != 2) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) pv[c] = 0.f;   // fixed pixels carry no unknown
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) st.x[c][hy][hx] = pv[c];
-      st.f[hy][hx] = f;
-    }
-    __syncthreads();
     const int gx = x0 + tx, gy = y0 + ty;
+    const long long i = (long long)gy * P + gx;
+    __syncthreads();
+    pois_cell_store(st, ty + 1, tx + 1, A, update, use_beta, beta, pout, pl, (gx < W && gy < H) ? i : -1);
+    if (has_halo) pois_cell_store(st, hhy, hhx, B, update, use_beta, beta, pout, pl, -1);
+    __syncthreads();
+    if (t + 1 < ch.end) {
+      tc = tiles[t + 1];
+      pois_cell_load(A, pr, pin, tile_x0(tc) + tx, tile_y0(tc) + ty, update, use_beta);
+      if (has_halo) pois_cell_load(B, pr, pin, tile_x0(tc) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
+    }
     if (gx < W && gy < H) {
       const int lx = tx + 1, ly = ty + 1;
-      const long long i = (long long)gy * P + gx;
       float q[4] = {0.f, 0.f, 0.f, 0.f};
       if (st.f[ly][lx] == 2) {
 #pragma unroll
@@ -571,23 +672,22 @@ __global__ void __launch_bounds__(NT) k_poisson_apply(const GridProb* __restrict
           const int nx = lx + dx4(k), ny = ly + dy4(k);
           const unsigned char fj = st.f[ny][nx];
           if (!fj) continue;
-          const float w = fj == 2 ? 2.0f : 1.0f;
+          const float w = fj == 2 ? 2.0f : 1.0f;   // own + (free neighbour) incoming
 #pragma unroll
-          for (int c = 0; c < 4; ++c) q[c] += w * (st.x[c][ly][lx] - st.x[c][ny][nx]);
+          for (int c = 0; c < 4; ++c) q[c] += w * (st.p[c][ly][lx] - st.p[c][ny][nx]);
         }
         if (pr.lm) {
           const float dd = lam * pr.dc[i];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) q[c] += dd * st.x[c][ly][lx];
+          for (int c = 0; c < 4; ++c) q[c] += dd * st.p[c][ly][lx];
         }
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         pr.q[c * pl + i] = q[c];
-        acc += st.x[c][ly][lx] * q[c];
+        acc += st.p[c][ly][lx] * q[c];
       }
     }
-    __syncthreads();
   }
   if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double pq, unused;
@@ -683,35 +783,58 @@ __global__ void __launch_bounds__(NT) k_poisson_energy(const GridProb* __restric
 // shared grid passes
 // ---------------------------------------------------------------------------
 // delta += alpha p, r -= alpha q, z = M^-1 r, float64 r.z -> beta.
+// Float4 stream over the tile rows (a tile row is 32 floats = 128 B of each
+// plane; the pitch keeps rows 16-byte aligned and the pitch padding holds
+// zeros in every vector).  All loads of a quad are issued before any use.
 template <int NX>
 __global__ void __launch_bounds__(NT) k_grid_update(const GridProb* __restrict__ probs,
                                                     const Chunk* __restrict__ chunks,
                                                     const int* __restrict__ tiles,
                                                     double* __restrict__ part, int par) {
+  constexpr int NM = NX == 3 ? 2 : 1;
+  constexpr int QPT = TW / 4 * TH;   // float4 quads per tile
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
-  const long long pl = pr.plane;
+  const long long pl4 = pr.plane / 4;
+  const int P4 = pr.P / 4;
   const float alpha = s->alpha_f;
-  const float* __restrict__ pn = pr.p + (long long)((par + 1) & 1) * NX * pl;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const float4* __restrict__ pn = reinterpret_cast<const float4*>(pr.p + (long long)((par + 1) & 1) * NX * pr.plane);
+  const float4* __restrict__ q4 = reinterpret_cast<const float4*>(pr.q);
+  const float4* __restrict__ m4 = reinterpret_cast<const float4*>(pr.m);
+  float4* __restrict__ d4 = reinterpret_cast<float4*>(pr.d);
+  float4* __restrict__ r4 = reinterpret_cast<float4*>(pr.r);
   float acc = 0.f;
-  for (int t = ch.begin; t < ch.end; ++t) {
-    const int tc = tiles[t];
-    const int gx = tile_x0(tc) + tx, gy = tile_y0(tc) + ty;
-    if (gx >= pr.W || gy >= pr.H) continue;
-    const long long i = (long long)gy * pr.P + gx;
+  const int nq = (ch.end - ch.begin) * QPT;
+  for (int k = threadIdx.x; k < nq; k += NT) {
+    const int tc = tiles[ch.begin + k / QPT];
+    const int w = k % QPT;
+    const int y = tile_y0(tc) + w / (TW / 4);
+    if (y >= pr.H) continue;
+    const long long j = (long long)y * P4 + tile_x0(tc) / 4 + w % (TW / 4);
+    float4 pv[NX], qv[NX], dv[NX], rv[NX], mv[NM];
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
-      const long long j = c * pl + i;
-      const float pv = pn[j], qv = pr.q[j];
-      pr.d[j] += alpha * pv;
-      const float rv = pr.r[j] - alpha * qv;
-      pr.r[j] = rv;
+      pv[c] = __ldg(pn + c * pl4 + j);
+      qv[c] = __ldg(q4 + c * pl4 + j);
+      dv[c] = d4[c * pl4 + j];
+      rv[c] = r4[c * pl4 + j];
+    }
+#pragma unroll
+    for (int c = 0; c < NM; ++c) mv[c] = __ldg(m4 + c * pl4 + j);
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
       // distinct-diagonal plane: warp (x, y) -> 0, theta -> 1; Poisson -> 0
-      const int mc = NX == 3 ? (c == 2 ? 1 : 0) : 0;
-      acc += rv * (pr.m[mc * pl + i] * rv);
+      const float4 m = mv[NX == 3 ? (c == 2 ? 1 : 0) : 0];
+      dv[c].x += alpha * pv[c].x; dv[c].y += alpha * pv[c].y;
+      dv[c].z += alpha * pv[c].z; dv[c].w += alpha * pv[c].w;
+      rv[c].x -= alpha * qv[c].x; rv[c].y -= alpha * qv[c].y;
+      rv[c].z -= alpha * qv[c].z; rv[c].w -= alpha * qv[c].w;
+      acc += rv[c].x * (m.x * rv[c].x) + rv[c].y * (m.y * rv[c].y) +
+             rv[c].z * (m.z * rv[c].z) + rv[c].w * (m.w * rv[c].w);
+      d4[c * pl4 + j] = dv[c];
+      r4[c * pl4 + j] = rv[c];
     }
   }
   if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.chunk_end - pr.chunk_begin)) {

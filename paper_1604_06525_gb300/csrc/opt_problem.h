@@ -1,0 +1,96 @@
+// Host-side state of one planned problem (shared by the host translation
+// units of the library; not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "opt_gb300.h"
+#include "opt_internal.cuh"
+
+// Materialized Jacobian (Sec. 7 "Matrix-free vs. Materialized"): J in CSR over
+// the residual rows, and its transpose in CSR over the non-empty unknown
+// columns, with the permutation that gathers J's values into J^T's.
+struct CsrJ {
+  int R = 0;                 // residual rows
+  long long nnz = 0;
+  int nT = 0;                // unknown columns with at least one entry
+  int ngroups = 0;           // residual groups refreshed by evalJ
+  int* rp = nullptr;         // R + 1
+  int* col = nullptr;        // nnz: internal unknown index
+  float* val = nullptr;      // nnz
+  int* t_unk = nullptr;      // nT: internal unknown index of each J^T row
+  int* t_ptr = nullptr;      // nT + 1
+  int* t_row = nullptr;      // nnz: J row of each J^T entry
+  int* t_perm = nullptr;     // nnz: index of each J^T entry in val
+  float* t_val = nullptr;    // nnz
+  float* tvec = nullptr;     // R: t = J p
+  double* part = nullptr;    // reduction partials of the J^T pass
+  int nblk_t = 0;            // blocks of the J^T pass
+};
+
+struct opt_problem {
+  int kind = 0;
+  int nx = 0;             // unknown planes
+  int nm = 0;             // distinct-diagonal planes
+  int sms = 148;
+  // grid
+  int W = 0, H = 0, P = 0;
+  // graph
+  int V = 0, E = 0;
+  long long plane = 0;    // internal plane stride (P*H or Vp)
+  long long ulen = 0;     // caller plane length (W*H or V)
+  optgb::GridProb hg{};
+  optgb::GridProb* dg = nullptr;
+  optgb::Chunk* d_chunks = nullptr;
+  int nchunks = 0;
+  int* d_tiles = nullptr;
+  int ntiles = 0;
+  optgb::MeshProb hm{};
+  optgb::MeshProb* dm = nullptr;
+  optgb::Chunk* d_vchunks = nullptr;
+  optgb::Chunk* d_echunks = nullptr;
+  int nvchunks = 0, nechunks = 0;
+  float* d_acc = nullptr;
+  // host copies kept for building the materialized Jacobian
+  std::vector<unsigned char> h_mask;    // grid mask (empty = none)
+  std::vector<int> h_hpix;              // grid handles (pitched index) / mesh handles (vertex)
+  std::vector<int> h_e0, h_e1;          // sorted edges
+  CsrJ csr;
+  // common
+  double* d_part = nullptr;
+  optgb::Scalars* d_s = nullptr;
+  double* d_Ehist = nullptr;
+  int Ehist_cap = 0;
+  float* user_x[6] = {};
+  float* d_tmp = nullptr;     // nx planes: caller p (apply hook)
+  float* d_jtf = nullptr;     // nx planes: J^T F (hook)
+  float* d_diag = nullptr;    // nm planes: diag (hook)
+  float* x = nullptr;
+  float* pbuf = nullptr;
+  float* dvec = nullptr;
+  float* rvec = nullptr;
+  float* qvec = nullptr;
+  std::vector<void*> allocs;
+  int pcg_par = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<double> gkey;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  ~opt_problem() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+namespace optgb {
+// materialize.cu
+opt_status csr_build(opt_problem* pb);
+void csr_evalj(opt_problem* pb, cudaStream_t st);
+void csr_apply(opt_problem* pb, cudaStream_t st, int par);
+}  // namespace optgb

@@ -347,3 +347,35 @@ def test_full_size_mesh_apply(api):
     assert rel(q.cpu().numpy(), J.T @ (J @ p.astype(np.float64))) <= TOL_PRODUCT
     jtf, _, E = gp.eval_jtf()
     assert rel(jtf.cpu().numpy(), J.T @ e.residuals(x)) <= TOL_PRODUCT
+
+
+@pytest.mark.parametrize("case", ["warp", "warp_masked", "poisson", "mesh"])
+def test_materialized_solve_matches_oracle_and_matrix_free(api, case):
+    """Materialized CSR J, q = J^T (J p) (Sec. 7), against the oracle and the
+    matrix-free path on the same problem."""
+    import torch
+    if case == "warp":
+        prob, lm, outer, inner = synth.warp_problem(70, 45, 6, seed=101), False, 4, 10
+    elif case == "warp_masked":
+        prob = synth.warp_problem(61, 37, 5, seed=102, mask=synth.random_mask(61, 37, 0.2, 3))
+        lm, outer, inner = False, 3, 10
+    elif case == "poisson":
+        prob, lm, outer, inner = synth.poisson_problem(96, 80, seed=103), False, 3, 20
+    else:
+        prob, lm, outer, inner = synth.mesh_problem(3, seed=104, handle_frac=0.02), True, 5, 15
+    e = oracle.make_energy(prob)
+    x0 = prob.x0.reshape(-1)
+    ref = (oracle.levenberg_marquardt(e, x0, outer, inner) if lm else oracle.gauss_newton(e, x0, outer, inner))
+    a, b = api.Problem(prob), api.Problem(prob)
+    solve = (lambda g, **kw: g.solve_lm(outer, inner, **kw)) if lm else (lambda g, **kw: g.solve_gn(outer, inner, **kw))
+    rm = solve(a, materialized=1)
+    rf = solve(b, materialized=0)
+    assert rm["outer_done"] == rf["outer_done"] == (ref.outer_done if lm else outer)
+    for x, y, z in zip(rm["E_history"], rf["E_history"], ref.E_history):
+        assert relE(x, z) <= TOL_ENERGY
+        assert relE(x, y) <= 1e-5
+    assert rel(a.x.cpu().numpy(), b.x.cpu().numpy()) <= 1e-4
+    # a second materialized solve from the same start replays the cached graph
+    a.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
+    rm2 = solve(a, materialized=1)
+    assert rm2["E_history"] == rm["E_history"] or all(relE(x, y) <= 1e-6 for x, y in zip(rm2["E_history"], rm["E_history"]))
