@@ -202,6 +202,158 @@ def roofline_for(api, synth, torch, W, H, peak, iters=20):
     return out, ms_init
 
 
+def pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, max(0, int(round(q / 100.0 * (len(v) - 1)))))]
+
+
+def bench_batched(api, synth, torch, flush, n=512, outer=10, inner=10):
+    """Batched precision form: n square warps, sides log-uniform in [32, 512],
+    GN outer x inner, all submitted at t = 0.  Batched = one autotuned batch
+    (one launch per phase, whole solve one CUDA graph); plain = each problem
+    solved in turn through opt_solve_gn.  Latency of a problem = time from the
+    common start until its result is on the host."""
+    probs = synth.batch_warps(n, 32, 512, seed=synth.BASE_SEED)
+    members = [api.Problem(p) for p in probs]
+    x0s = [m.x.clone() for m in members]
+    px = sum(p.W * p.H for p in probs)
+
+    def reset():
+        for m, x in zip(members, x0s):
+            m.x.copy_(x)
+
+    batch = api.Batch(members)
+    chosen, _ = batch.autotune(inner=4)
+    reset()
+    batch.solve_gn(outer, inner)           # capture + warm
+    bt = []
+    for _ in range(3):
+        reset()
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps_b, ms_b = batch.solve_gn(outer, inner)
+        bt.append((time.perf_counter() - t0, ms_b))
+    wall_b = statistics.median(t for t, _ in bt)
+    dev_b = statistics.median(m for _, m in bt)
+    # plain: one problem at a time (graphs captured in a warm-up pass)
+    reset()
+    for m in members:
+        m.solve_gn(outer, inner)
+    reset()
+    flush.zero_()
+    torch.cuda.synchronize()
+    lat, dev_p, reps_p = [], 0.0, []
+    t0 = time.perf_counter()
+    for m in members:
+        r = m.solve_gn(outer, inner)
+        reps_p.append(r)
+        dev_p += r["ms"]
+        lat.append(time.perf_counter() - t0)
+    wall_p = time.perf_counter() - t0
+    rel = [abs(a["E_final"] - b["E_final"]) / max(abs(b["E_final"]), 1e-30) for a, b in zip(reps_b, reps_p)]
+    # at the members' own chunking the batch is bit-identical to the plain solves
+    batch.set_chunking(0)
+    reset()
+    reps_0, _ = batch.solve_gn(outer, inner)
+    rel0 = max(abs(a["E_final"] - b["E_final"]) / max(abs(b["E_final"]), 1e-30) for a, b in zip(reps_0, reps_p))
+    batch.close()
+    for m in members:
+        m.close()
+    torch.cuda.empty_cache()
+    return {"problems": n, "pixels": px, "tiles_per_chunk": chosen,
+            "batched_solves_per_s": n / wall_b, "batched_wall_ms": 1e3 * wall_b, "batched_device_ms": dev_b,
+            "batched_p50_ms": 1e3 * wall_b, "batched_p99_ms": 1e3 * wall_b,
+            "plain_solves_per_s": n / wall_p, "plain_wall_ms": 1e3 * wall_p, "plain_device_ms": dev_p,
+            "plain_p50_ms": 1e3 * pct(lat, 50), "plain_p99_ms": 1e3 * pct(lat, 99),
+            "speedup_solves_per_s": wall_p / wall_b,
+            "max_rel_diff_E_final_autotuned_vs_plain": max(rel),
+            "members_within_1e-4_autotuned_vs_plain": sum(r <= 1e-4 for r in rel),
+            "max_rel_diff_E_final_default_chunking_vs_plain": rel0}
+
+
+def bench_serving(api, synth, torch, n_req=400, rate=2000.0, budget=120 << 30):
+    """Serving form: Poisson arrivals (mean `rate` per second), 50/50 mix of
+    ARAP warps (square, side log-uniform in [64, 1024]) and icosphere mesh
+    deformations (levels 4-6, 2.5k-41k vertices), each LM <= 10 outer x 10 PCG
+    to relative energy change 1e-6, admission by an HBM budget of 120 GB.
+    Requests reuse a pool of 24 warp templates and 3 meshes (fresh unknowns per
+    request).  Served = continuous batching (opt_server_*); plain = one
+    request at a time in arrival order (opt_solve_lm, direct launches)."""
+    import numpy as np
+    rng = np.random.default_rng(synth.BASE_SEED + 5)
+    sides = synth.batch_sides(24, 64, 1024, seed=synth.BASE_SEED + 6)
+    warps = [synth.warp_problem(int(s), int(s), synth.warp_handle_count(int(s), int(s)), seed=900 + i)
+             for i, s in enumerate(sides)]
+    meshes = [synth.mesh_problem(l, seed=950 + l) for l in (4, 5, 6)]
+    templates = [api.make_descriptor(p, "cuda") + (p.kind,) for p in warps + meshes]
+    kinds = rng.random(n_req) < 0.5
+    pick = np.where(kinds, rng.integers(0, len(warps), n_req), len(warps) + rng.integers(0, 3, n_req))
+    arrivals = synth.arrival_times(n_req, rate, seed=synth.BASE_SEED + 7)
+    OUT, INN, TOL = 10, 10, 1e-6
+
+    srv = api.Server(budget, outer=OUT, inner=INN, rel_tol=TOL)
+    # warm-up: one request of each template kind
+    for t in (0, len(warps)):
+        tk = srv.submit_template(templates[t])
+        while srv.poll(tk) is None:
+            srv.step()
+    torch.cuda.synchronize()
+    done, lat, nxt, rounds = {}, {}, 0, 0
+    pending = {}
+    t0 = time.perf_counter()
+    while len(done) < n_req:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrivals[nxt] <= now:
+            pending[srv.submit_template(templates[pick[nxt]])] = nxt
+            nxt += 1
+        if pending:
+            srv.step()
+            rounds += 1
+            tnow = time.perf_counter() - t0
+            for tk in list(pending):
+                r = srv.poll(tk)
+                if r is not None:
+                    i = pending.pop(tk)
+                    done[i] = r[0]
+                    lat[i] = tnow - arrivals[i]
+        else:
+            time.sleep(max(0.0, min(1e-3, arrivals[nxt] - now)))
+    span_served = max(arrivals[i] + lat[i] for i in range(n_req)) - arrivals[0]
+    srv.close()
+
+    # plain: a single worker, requests in arrival order
+    plain_lat, plain_done = {}, {}
+    probs = warps + meshes
+    solvers = {}
+    t0 = time.perf_counter()
+    for i in range(n_req):
+        now = time.perf_counter() - t0
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        g = api.Problem(probs[pick[i]])
+        r = g.solve_lm(OUT, INN, rel_tol=TOL, use_graph=0)
+        g.close()
+        plain_done[i] = r
+        plain_lat[i] = time.perf_counter() - t0 - arrivals[i]
+    span_plain = max(arrivals[i] + plain_lat[i] for i in range(n_req)) - arrivals[0]
+    diff = max(abs(done[i]["E_final"] - plain_done[i]["E_final"]) / max(abs(plain_done[i]["E_final"]), 1e-30)
+               for i in range(n_req))
+    same_outer = sum(done[i]["outer_done"] == plain_done[i]["outer_done"] for i in range(n_req))
+    L = list(lat.values())
+    PL = list(plain_lat.values())
+    for tpl in templates:
+        del tpl
+    torch.cuda.empty_cache()
+    return {"requests": n_req, "rate_per_s": rate, "budget_gb": budget / 2 ** 30, "rounds": rounds,
+            "served_solves_per_s": n_req / span_served, "served_p50_ms": 1e3 * pct(L, 50),
+            "served_p99_ms": 1e3 * pct(L, 99),
+            "plain_solves_per_s": n_req / span_plain, "plain_p50_ms": 1e3 * pct(PL, 50),
+            "plain_p99_ms": 1e3 * pct(PL, 99),
+            "speedup_solves_per_s": span_plain / span_served,
+            "max_rel_diff_E_final_served_vs_plain": diff, "same_outer_count": same_outer}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -315,6 +467,9 @@ def run_ours(args):
     extra["mesh_icosphere7_lm15x30"] = {"pcg_iters_per_s": rr[-1]["pcg_done"] / (msm / 1e3), "ms_per_solve": msm,
                                        "accepted": rr[-1]["accepted"], "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
     gmp.close()
+
+    extra["batched_512_warps_gn10x10"] = bench_batched(api, synth, torch, flush)
+    extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch)
 
     launches_per_step = 2 + OUTER * (2 + 2 * INNER)
     line = {

@@ -253,6 +253,47 @@ opt_status opt_batch_autotune(opt_batch* batch, const opt_solve_params* params, 
 opt_status opt_batch_solve_gn(opt_batch* batch, const opt_solve_params* params, opt_report* reports, float* ms);
 opt_status opt_batch_solve_lm(opt_batch* batch, const opt_solve_params* params, opt_report* reports, float* ms);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a request loop over LM solves with continuous batching.  The paper
+ * solves one problem per call; the server keeps every admitted request's
+ * unknowns and PCG state on the device, admits queued requests in arrival
+ * order while their estimated device footprint fits in hbm_budget_bytes, and
+ * advances all admitted requests together one LM outer iteration per
+ * opt_server_step (Sec. 4 LM, exactly the sequence of opt_solve_lm), so work of
+ * requests admitted at different times overlaps on the GPU.
+ * ------------------------------------------------------------------------- */
+typedef struct opt_server opt_server;
+
+/* params: outer = cap on LM outer iterations per request, inner = PCG
+ * iterations per outer iteration, rel_tol = convergence test (Sec. 4 LM;
+ * see opt_solve_params), lambda0 / clamps / eta as for opt_solve_lm;
+ * params->stream is ignored (the server owns a non-blocking stream).
+ * OPT_ERR_INVALID_ARG on a zero budget or invalid parameters. */
+opt_status opt_server_create(size_t hbm_budget_bytes, const opt_solve_params* params, opt_server** out);
+
+/* Waits for the server's stream and frees every request it still holds. */
+opt_status opt_server_destroy(opt_server* server);
+
+/* Queues a request.  The descriptor is copied; the device arrays it points to
+ * must stay valid until the request is polled as finished (the solution is
+ * written into its unknowns).  *ticket (host) identifies the request.
+ * OPT_ERR_BUDGET if the request alone exceeds the budget.  Planning errors
+ * (invalid descriptors) are reported by opt_server_poll. */
+opt_status opt_server_submit_grid(opt_server* server, const opt_grid_desc* desc, uint64_t* ticket);
+opt_status opt_server_submit_graph(opt_server* server, const opt_graph_desc* desc, uint64_t* ticket);
+
+/* Admits, runs one LM outer iteration of every admitted request, retires the
+ * finished ones (synchronises the server's stream).  n_active / n_queued
+ * (host, may be NULL) receive the counts after the step. */
+opt_status opt_server_step(opt_server* server, int32_t* n_active, int32_t* n_queued);
+
+/* OPT_OK and the report (E_history, if not NULL, receives outer_done + 1
+ * values) once the request finished; the ticket is then forgotten.
+ * OPT_ERR_NOT_READY while queued or running; OPT_ERR_INVALID_ARG for an
+ * unknown ticket; the request's own error status if its planning or solve
+ * failed. */
+opt_status opt_server_poll(opt_server* server, uint64_t ticket, opt_report* report);
+
 /* Allocation-free variant of the warp J^T J p (no counterpart in the paper).
  * For callers that cannot call cudaMalloc: interactive loops on a fixed frame
  * budget that must not stall on an allocation, and host applications or

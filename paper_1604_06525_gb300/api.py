@@ -66,6 +66,18 @@ _SIGNATURES = [
     ("opt_eval_energy", c_int32, [c_void_p, POINTER(c_double)]),
     ("opt_profile_pcg", c_int32, [c_void_p, c_int32, c_void_p, POINTER(c_float)]),
     ("opt_problem_info", c_int32, [c_void_p, POINTER(c_int64), POINTER(c_int32), POINTER(c_int64)]),
+    ("opt_batch_create", c_int32, [POINTER(c_void_p), c_int32, POINTER(c_void_p)]),
+    ("opt_batch_destroy", c_int32, [c_void_p]),
+    ("opt_batch_set_chunking", c_int32, [c_void_p, c_int32]),
+    ("opt_batch_autotune", c_int32, [c_void_p, POINTER(SolveParams), POINTER(c_int32), POINTER(c_float)]),
+    ("opt_batch_solve_gn", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report), POINTER(c_float)]),
+    ("opt_batch_solve_lm", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report), POINTER(c_float)]),
+    ("opt_server_create", c_int32, [ctypes.c_size_t, POINTER(SolveParams), POINTER(c_void_p)]),
+    ("opt_server_destroy", c_int32, [c_void_p]),
+    ("opt_server_submit_grid", c_int32, [c_void_p, POINTER(GridDesc), POINTER(ctypes.c_uint64)]),
+    ("opt_server_submit_graph", c_int32, [c_void_p, POINTER(GraphDesc), POINTER(ctypes.c_uint64)]),
+    ("opt_server_step", c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
+    ("opt_server_poll", c_int32, [c_void_p, ctypes.c_uint64, POINTER(Report)]),
     ("opt_warp_apply_jtj_noalloc", c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                              c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p,
                                              c_void_p]),
@@ -120,6 +132,70 @@ def default_params(**kw) -> SolveParams:
     return p
 
 
+def make_descriptor(prob, device):
+    """Device tensors and the C descriptor of a synth problem instance.
+    Returns (descriptor, unknown tensor, tensors to keep alive)."""
+    import torch
+    dev = torch.device(device)
+
+    def f32(a):
+        return torch.as_tensor(np.ascontiguousarray(a, np.float32), device=dev)
+
+    def i32(a):
+        return torch.as_tensor(np.ascontiguousarray(a, np.int32), device=dev)
+
+    keep = []
+    if prob.kind in ("warp", "poisson"):
+        x = f32(prob.x0).reshape(-1, prob.H, prob.W).clone()
+        d = GridDesc()
+        d.W, d.H = prob.W, prob.H
+        if prob.kind == "warp":
+            d.kind = OPT_ARAP_WARP_2D
+            consts = f32(prob.urshape)
+            mask = None if prob.mask is None else torch.as_tensor(prob.mask, dtype=torch.uint8, device=dev)
+            hidx = i32(prob.handle_idx)
+            htgt = f32(prob.handle_target.reshape(-1))
+            d.n_handles = int(prob.handle_idx.size)
+            d.handle_idx = _ptr(hidx) if d.n_handles else None
+            d.handle_target = _ptr(htgt) if d.n_handles else None
+            d.w_reg, d.w_fit = prob.w_reg, prob.w_fit
+            keep += [hidx, htgt]
+            nx, nc = 3, 2
+        else:
+            d.kind = OPT_POISSON_2D
+            consts = f32(prob.guide)
+            mask = torch.as_tensor(prob.mask, dtype=torch.uint8, device=dev)
+            d.n_handles = 0
+            nx, nc = 4, 4
+        for c in range(nx):
+            d.unknowns[c] = _ptr(x[c])
+        for c in range(nc):
+            d.consts[c] = _ptr(consts[c])
+        d.mask = _ptr(mask) if mask is not None else None
+        keep += [consts, mask, x]
+        return d, x, keep
+    if prob.kind == "mesh":
+        x = f32(prob.x0).reshape(6, prob.V).clone()
+        U = f32(prob.urshape)
+        v0, v1 = i32(prob.v0), i32(prob.v1)
+        hidx = i32(prob.handle_idx)
+        htgt = f32(prob.handle_target.reshape(-1))
+        d = GraphDesc()
+        d.V, d.E = prob.V, int(prob.v0.size)
+        d.v0, d.v1 = _ptr(v0), _ptr(v1)
+        for c in range(6):
+            d.unknowns[c] = _ptr(x[c])
+        for c in range(3):
+            d.urshape[c] = _ptr(U[c])
+        d.n_handles = int(prob.handle_idx.size)
+        d.handle_idx = _ptr(hidx) if d.n_handles else None
+        d.handle_target = _ptr(htgt) if d.n_handles else None
+        d.w_reg, d.w_fit = prob.w_reg, prob.w_fit
+        keep += [U, v0, v1, hidx, htgt, x]
+        return d, x, keep
+    raise ValueError(prob.kind)
+
+
 class Problem:
     """One planned problem on the current CUDA device (Fig. 4: plan once,
     solve many times).  `prob` is a synth.WarpProblem / PoissonProblem /
@@ -144,60 +220,15 @@ class Problem:
 
         self._keep = []
         h = c_void_p()
+        d, self.x, self._keep = make_descriptor(prob, self.device)
         if prob.kind in ("warp", "poisson"):
             self.W, self.H = prob.W, prob.H
-            self.x = f32(prob.x0).reshape(-1, prob.H, prob.W).clone()
-            d = GridDesc()
-            d.W, d.H = prob.W, prob.H
-            if prob.kind == "warp":
-                d.kind = OPT_ARAP_WARP_2D
-                consts = f32(prob.urshape)
-                mask = None if prob.mask is None else torch.as_tensor(prob.mask, dtype=torch.uint8, device=dev)
-                hidx = i32(prob.handle_idx)
-                htgt = f32(prob.handle_target.reshape(-1))
-                d.n_handles = int(prob.handle_idx.size)
-                d.handle_idx = _ptr(hidx) if d.n_handles else None
-                d.handle_target = _ptr(htgt) if d.n_handles else None
-                d.w_reg, d.w_fit = prob.w_reg, prob.w_fit
-                self._keep += [hidx, htgt]
-                nx, nc = 3, 2
-            else:
-                d.kind = OPT_POISSON_2D
-                consts = f32(prob.guide)
-                mask = torch.as_tensor(prob.mask, dtype=torch.uint8, device=dev)
-                d.n_handles = 0
-                nx, nc = 4, 4
-            for c in range(nx):
-                d.unknowns[c] = _ptr(self.x[c])
-            for c in range(nc):
-                d.consts[c] = _ptr(consts[c])
-            d.mask = _ptr(mask) if mask is not None else None
-            self._keep += [consts, mask]
             _check(self.lib.opt_problem_create_grid(ctypes.byref(d), None, ctypes.byref(h)),
                    "opt_problem_create_grid")
-        elif prob.kind == "mesh":
+        else:
             self.V = prob.V
-            self.x = f32(prob.x0).reshape(6, prob.V).clone()
-            U = f32(prob.urshape)
-            v0, v1 = i32(prob.v0), i32(prob.v1)
-            hidx = i32(prob.handle_idx)
-            htgt = f32(prob.handle_target.reshape(-1))
-            d = GraphDesc()
-            d.V, d.E = prob.V, int(prob.v0.size)
-            d.v0, d.v1 = _ptr(v0), _ptr(v1)
-            for c in range(6):
-                d.unknowns[c] = _ptr(self.x[c])
-            for c in range(3):
-                d.urshape[c] = _ptr(U[c])
-            d.n_handles = int(prob.handle_idx.size)
-            d.handle_idx = _ptr(hidx) if d.n_handles else None
-            d.handle_target = _ptr(htgt) if d.n_handles else None
-            d.w_reg, d.w_fit = prob.w_reg, prob.w_fit
-            self._keep += [U, v0, v1, hidx, htgt]
             _check(self.lib.opt_problem_create_graph(ctypes.byref(d), None, ctypes.byref(h)),
                    "opt_problem_create_graph")
-        else:
-            raise ValueError(prob.kind)
         self.h = h
 
     # ------------------------------------------------------------------
@@ -287,3 +318,147 @@ class Problem:
         _check(self.lib.opt_pcg_get_state(self.h, _ptr(dl), _ptr(r), _ptr(p), ctypes.byref(it)),
                "opt_pcg_get_state")
         return dl, r, p, it.value
+
+
+class Batch:
+    """Many planned problems solved together, one launch per solver phase for
+    the whole batch (opt_batch_* in the C ABI).  The Problem objects must stay
+    alive while the batch exists."""
+
+    def __init__(self, problems):
+        self.lib = load_library()
+        self.problems = list(problems)
+        arr = (c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        h = c_void_p()
+        _check(self.lib.opt_batch_create(arr, len(self.problems), ctypes.byref(h)), "opt_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.opt_batch_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_chunking(self, tiles_per_chunk: int):
+        _check(self.lib.opt_batch_set_chunking(self.h, tiles_per_chunk), "opt_batch_set_chunking")
+
+    def autotune(self, inner: int = 4, **kw):
+        import torch
+        kw.setdefault("stream", torch.cuda.current_stream().cuda_stream)
+        p = default_params(outer=1, inner=inner, **kw)
+        chosen, best = c_int32(), c_float()
+        _check(self.lib.opt_batch_autotune(self.h, ctypes.byref(p), ctypes.byref(chosen), ctypes.byref(best)),
+               "opt_batch_autotune")
+        return chosen.value, best.value
+
+    def _solve(self, fn, outer, inner, **kw):
+        import torch
+        kw.setdefault("stream", torch.cuda.current_stream().cuda_stream)
+        p = default_params(outer=outer, inner=inner, **kw)
+        n = len(self.problems)
+        hists = [(c_double * (outer + 1))() for _ in range(n)]
+        reps = (Report * n)()
+        for i in range(n):
+            reps[i].E_history = ctypes.cast(hists[i], POINTER(c_double))
+        ms = c_float()
+        st = fn(self.h, ctypes.byref(p), reps, ctypes.byref(ms))
+        if st not in (OPT_OK, 4):
+            _check(st, "batch solve")
+        out = []
+        for i in range(n):
+            r = reps[i]
+            out.append({"outer_done": r.outer_done, "pcg_done": r.pcg_done, "accepted": r.accepted,
+                        "converged": r.converged, "E0": r.E0, "E_final": r.E_final,
+                        "lambda_final": r.lambda_final, "E_history": list(hists[i][: r.outer_done + 1])})
+        return out, ms.value
+
+    def solve_gn(self, outer: int, inner: int, **kw):
+        """Returns (per-problem reports, device ms of the batched solve)."""
+        return self._solve(self.lib.opt_batch_solve_gn, outer, inner, **kw)
+
+    def solve_lm(self, outer: int, inner: int, **kw):
+        return self._solve(self.lib.opt_batch_solve_lm, outer, inner, **kw)
+
+
+class Server:
+    """Continuous-batching LM server (opt_server_* in the C ABI).  submit()
+    takes a synth problem instance, uploads its arrays and queues it; step()
+    admits under the HBM budget and advances every admitted request by one LM
+    outer iteration; poll() returns the report once the request finished."""
+
+    def __init__(self, hbm_budget_bytes: int, outer: int = 10, inner: int = 10, rel_tol: float = 1e-6,
+                 device: str = "cuda", **kw):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.lib = load_library()
+        self.device = torch.device(device)
+        self.outer = outer
+        p = default_params(outer=outer, inner=inner, rel_tol=rel_tol, **kw)
+        h = c_void_p()
+        _check(self.lib.opt_server_create(hbm_budget_bytes, ctypes.byref(p), ctypes.byref(h)), "opt_server_create")
+        self.h = h
+        self.inflight = {}
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.opt_server_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, prob, x=None) -> int:
+        d, xt, keep = make_descriptor(prob, self.device)
+        if x is not None:
+            xt.copy_(x)
+        t = ctypes.c_uint64()
+        if prob.kind == "mesh":
+            _check(self.lib.opt_server_submit_graph(self.h, ctypes.byref(d), ctypes.byref(t)), "submit")
+        else:
+            _check(self.lib.opt_server_submit_grid(self.h, ctypes.byref(d), ctypes.byref(t)), "submit")
+        self.inflight[t.value] = (xt, keep)
+        return t.value
+
+    def submit_template(self, template) -> int:
+        """Queues a request that shares a prepared template's device constants
+        (template = make_descriptor(prob, device) + (kind,)); only the
+        unknowns are fresh."""
+        d0, x0, keep, kind = template
+        xt = x0.clone()
+        d = type(d0).from_buffer_copy(d0)
+        for c in range(xt.shape[0]):
+            d.unknowns[c] = _ptr(xt[c])
+        t = ctypes.c_uint64()
+        fn = self.lib.opt_server_submit_graph if kind == "mesh" else self.lib.opt_server_submit_grid
+        _check(fn(self.h, ctypes.byref(d), ctypes.byref(t)), "submit")
+        self.inflight[t.value] = (xt, keep)
+        return t.value
+
+    def step(self):
+        a, q = c_int32(), c_int32()
+        _check(self.lib.opt_server_step(self.h, ctypes.byref(a), ctypes.byref(q)), "opt_server_step")
+        return a.value, q.value
+
+    def poll(self, ticket: int):
+        """None while running, else (report dict, solution tensor)."""
+        hist = (c_double * (self.outer + 2))()
+        rep = Report()
+        rep.E_history = ctypes.cast(hist, POINTER(c_double))
+        st = self.lib.opt_server_poll(self.h, ticket, ctypes.byref(rep))
+        if st == 7:
+            return None
+        xt, _ = self.inflight.pop(ticket)
+        if st not in (OPT_OK, 4):
+            _check(st, "opt_server_poll")
+        return ({"status": STATUS[st], "outer_done": rep.outer_done, "pcg_done": rep.pcg_done,
+                 "accepted": rep.accepted, "converged": rep.converged, "E0": rep.E0, "E_final": rep.E_final,
+                 "lambda_final": rep.lambda_final, "E_history": list(hist[: rep.outer_done + 1])}, xt)

@@ -703,6 +703,7 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   g.use_precond = 1; g.lm = 0;
   g.x = q->x; g.U = U; g.degw = dgw; g.e0 = de0; g.e1 = de1;
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
+  g.acc = q->d_acc;
   g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;
   g.jtf_out = nullptr; g.diag_out = nullptr;
   g.s = q->d_s;

@@ -536,3 +536,41 @@ opt_status opt_batch_autotune(opt_batch* b, const opt_solve_params* params, int3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Internal interface used by the serving engine (serve.cu): one LM outer
+// iteration of every member, without energy-history writes, and a gather of
+// the members' scalars.
+// ---------------------------------------------------------------------------
+namespace optgb {
+
+opt_status batch_prepare_round(opt_batch* b, const opt_solve_params& p) {
+  return refresh_descriptors(b, 1, p.use_precond, 1);
+}
+
+void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_t st) {
+  const float dmin = (float)p.diag_min, dmax = (float)p.diag_max;
+  const int n = (int)b->probs.size();
+  for (GridGroup& g : b->grids) launch_grid_init(g.kind, gl(g, st), -2, dmin, dmax);
+  if (!b->mesh.members.empty()) launch_mesh_init(ml(b->mesh, st), -2, dmin, dmax);
+  for (int i = 0; i < p.inner; ++i) {
+    for (GridGroup& g : b->grids) launch_grid_apply(g.kind, gl(g, st), nullptr, i, 1);
+    if (!b->mesh.members.empty()) launch_mesh_apply(ml(b->mesh, st), nullptr, i, 1);
+    for (GridGroup& g : b->grids) launch_grid_update(g.kind, gl(g, st), i);
+    if (!b->mesh.members.empty()) launch_mesh_update(ml(b->mesh, st), i);
+  }
+  for (GridGroup& g : b->grids) launch_grid_energy(g.kind, gl(g, st), 1, -2);
+  if (!b->mesh.members.empty()) launch_mesh_energy(ml(b->mesh, st), 1, -2);
+  k_lm_decide_tab<<<(n + 127) / 128, 128, 0, st>>>(b->d_stab, n, p.eta, p.lambda_min, p.lambda_max, p.rel_tol);
+  for (GridGroup& g : b->grids) launch_grid_step(g.kind, gl(g, st), 1);
+  if (!b->mesh.members.empty()) launch_mesh_step(ml(b->mesh, st), 1);
+  k_gather_results<<<n, 128, 0, st>>>(b->d_stab, b->d_htab, n, 0, b->d_sout, b->d_hout);
+}
+
+opt_status batch_read_scalars(opt_batch* b, Scalars* host_out, cudaStream_t st) {
+  BCK(cudaMemcpyAsync(host_out, b->d_sout, b->probs.size() * sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  return OPT_OK;
+}
+
+}  // namespace optgb

@@ -68,7 +68,7 @@ __device__ __forceinline__ int handle_of(const MeshProb& pr, int v) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_mesh_init_v(const MeshProb* __restrict__ probs,
                                                     const Chunk* __restrict__ chunks,
-                                                    double* __restrict__ part, float* __restrict__ acc) {
+                                                    double* __restrict__ part) {
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_v(const MeshProb* __restrict__
     }
     pr.q[v] = g0; pr.q[pl + v] = g1; pr.q[2 * pl + v] = g2;
     pr.q[3 * pl + v] = 0.f; pr.q[4 * pl + v] = 0.f; pr.q[5 * pl + v] = 0.f;
-    acc[v] = 0.f; acc[pl + v] = 0.f; acc[2 * pl + v] = 0.f;
+    pr.acc[v] = 0.f; pr.acc[pl + v] = 0.f; pr.acc[2 * pl + v] = 0.f;
   }
   if (publish_partials(part, blockIdx.x, e, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double a, b;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_v(const MeshProb* __restrict__
 
 __global__ void __launch_bounds__(NT) k_mesh_init_e(const MeshProb* __restrict__ probs,
                                                     const Chunk* __restrict__ chunks,
-                                                    double* __restrict__ part, float* __restrict__ acc) {
+                                                    double* __restrict__ part) {
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_e(const MeshProb* __restrict__
 #pragma unroll
       for (int k = 0; k < 6; ++k) atomicAdd(&pr.q[k * pl + a], c[k]);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) atomicAdd(&acc[k * pl + a], c[6 + k]);
+      for (int k = 0; k < 3; ++k) atomicAdd(&pr.acc[k * pl + a], c[6 + k]);
     }
     if (ok) {
       atomicAdd(&pr.q[b], rb0);
@@ -156,8 +156,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_e(const MeshProb* __restrict__
 
 __global__ void __launch_bounds__(NT) k_mesh_init_f(const MeshProb* __restrict__ probs,
                                                     const Chunk* __restrict__ chunks,
-                                                    double* __restrict__ part,
-                                                    const float* __restrict__ acc, int k_outer,
+                                                    double* __restrict__ part, int k_outer,
                                                     float dmin, float dmax) {
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
@@ -169,7 +168,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_f(const MeshProb* __restrict__
   for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
     float dg[4];
     dg[0] = pr.degw[v];
-    dg[1] = acc[v]; dg[2] = acc[pl + v]; dg[3] = acc[2 * pl + v];
+    dg[1] = pr.acc[v]; dg[2] = pr.acc[pl + v]; dg[3] = pr.acc[2 * pl + v];
     float mv[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -473,9 +472,9 @@ __global__ void __launch_bounds__(NT) k_mesh_step(const MeshProb* __restrict__ p
 // launchers
 // ---------------------------------------------------------------------------
 void launch_mesh_init(const MeshLaunch& L, int k_outer, float dmin, float dmax) {
-  k_mesh_init_v<<<L.nvchunks, NT, 0, L.stream>>>(L.probs, L.vchunks, L.part, L.acc);
-  k_mesh_init_e<<<L.nechunks, NT, 0, L.stream>>>(L.probs, L.echunks, L.part, L.acc);
-  k_mesh_init_f<<<L.nvchunks, NT, 0, L.stream>>>(L.probs, L.vchunks, L.part, L.acc, k_outer, dmin, dmax);
+  k_mesh_init_v<<<L.nvchunks, NT, 0, L.stream>>>(L.probs, L.vchunks, L.part);
+  k_mesh_init_e<<<L.nechunks, NT, 0, L.stream>>>(L.probs, L.echunks, L.part);
+  k_mesh_init_f<<<L.nvchunks, NT, 0, L.stream>>>(L.probs, L.vchunks, L.part, k_outer, dmin, dmax);
 }
 
 void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, int update) {

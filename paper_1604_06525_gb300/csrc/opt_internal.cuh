@@ -104,6 +104,7 @@ struct MeshProb {
   const int* e1;
   float *d, *r, *p, *q;         // 6 planes each
   float *m, *dc;                // 4 planes: displacement, ax, ay, az
+  float* acc;                   // 3 planes: angle-diagonal accumulators (PCGInit)
   const int* hbeg;              // per vertex tile: first handle
   const int* hpix;              // handle vertex, sorted
   const float* htgt;            // 3 per handle

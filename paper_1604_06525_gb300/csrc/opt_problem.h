@@ -88,7 +88,13 @@ struct opt_problem {
   }
 };
 
+struct opt_batch;
+
 namespace optgb {
+// batch.cu (serving engine interface)
+opt_status batch_prepare_round(opt_batch* b, const opt_solve_params& p);
+void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_t st);
+opt_status batch_read_scalars(opt_batch* b, Scalars* host_out, cudaStream_t st);
 // materialize.cu
 opt_status csr_build(opt_problem* pb);
 void csr_evalj(opt_problem* pb, cudaStream_t st);

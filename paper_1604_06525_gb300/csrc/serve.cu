@@ -1,0 +1,303 @@
+// Serving engine: a request loop with HBM-budget admission and continuous
+// batching over Levenberg-Marquardt solves (the serving form of the solver).
+//
+// Requests (grid warps / Poisson edits, mesh deformations) are queued by
+// opt_server_submit_*; each opt_server_step
+//   1. admits queued requests in arrival order while their estimated device
+//      footprint fits in the budget (planning = opt_problem_create_*),
+//   2. resets the new members' scalars and copies their unknowns in,
+//   3. runs ONE LM outer iteration (PCGInit, `inner` PCG iterations, trial
+//      energy, gain-ratio decision, conditional update) for every member in
+//      one launch per phase (the batched kernels), so requests admitted at
+//      different times overlap on the device,
+//   4. reads the members' scalars and retires those that converged (relative
+//      energy change below rel_tol after an accepted step) or reached the
+//      outer-iteration cap: their unknowns are written back, their report is
+//      stored for opt_server_poll, and their memory returns to the budget.
+// Every member follows exactly the LM sequence of opt_solve_lm with the same
+// parameters, so its result equals the one-at-a-time solve up to float
+// rounding (batch reductions run per problem in the same order).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "opt_gb300.h"
+#include "opt_internal.cuh"
+#include "opt_problem.h"
+
+using namespace optgb;
+
+namespace {
+
+struct ServeReq {
+  uint64_t ticket = 0;
+  bool graph = false;
+  opt_grid_desc gd{};
+  opt_graph_desc md{};
+  size_t est_bytes = 0;
+  opt_problem* pb = nullptr;
+  std::vector<double> hist;
+  opt_report rep{};
+  opt_status status = OPT_OK;
+  int state = 0;   // 0 queued, 1 active, 2 finished
+};
+
+__global__ void k_serve_reset(Scalars* s, double lambda0) {
+  Scalars z;
+  memset(&z, 0, sizeof(z));
+  z.lambda = lambda0;
+  z.lambda_f = (float)lambda0;
+  z.nu = 2.0;
+  *s = z;
+}
+
+size_t round32(size_t v) { return (v + 31) / 32 * 32; }
+
+// Device bytes a planned problem allocates (planes, tables, reduction slots).
+size_t estimate_grid(const opt_grid_desc& d) {
+  const size_t pl = round32((size_t)d.W) * (size_t)d.H;
+  const size_t planes = d.kind == OPT_ARAP_WARP_2D ? 24 : 30;
+  const size_t tiles = ((size_t)(d.W + 31) / 32) * ((size_t)(d.H + 7) / 8);
+  return planes * pl * 4 + (d.mask ? pl : 0) + tiles * 64 + (size_t)d.n_handles * 16 + (1 << 16);
+}
+size_t estimate_graph(const opt_graph_desc& d) {
+  const size_t pl = round32((size_t)d.V);
+  return 51 * pl * 4 + (size_t)d.E * 8 + (size_t)d.n_handles * 16 + (1 << 16);
+}
+
+}  // namespace
+
+struct opt_server {
+  size_t budget = 0, used = 0;
+  opt_solve_params prm{};
+  cudaStream_t st = nullptr;
+  std::mutex mu;
+  std::deque<ServeReq*> queue;
+  std::vector<ServeReq*> active;
+  std::unordered_map<uint64_t, std::unique_ptr<ServeReq>> reqs;
+  uint64_t next_ticket = 1;
+  opt_batch* batch = nullptr;
+  bool dirty = true;
+  std::vector<Scalars> sbuf;
+
+  ~opt_server() {
+    if (batch) opt_batch_destroy(batch);
+    for (auto& kv : reqs)
+      if (kv.second->pb) opt_problem_destroy(kv.second->pb);
+    if (st) cudaStreamDestroy(st);
+  }
+};
+
+namespace {
+
+opt_status submit(opt_server* s, ServeReq* r, uint64_t* ticket) {
+  if (r->est_bytes > s->budget) return OPT_ERR_BUDGET;
+  std::lock_guard<std::mutex> lk(s->mu);
+  r->ticket = s->next_ticket++;
+  if (ticket) *ticket = r->ticket;
+  s->queue.push_back(r);
+  s->reqs[r->ticket].reset(r);
+  return OPT_OK;
+}
+
+void finish(opt_server* s, ServeReq* r, opt_status st) {
+  r->status = st;
+  r->state = 2;
+  if (r->pb) {
+    opt_problem_destroy(r->pb);
+    r->pb = nullptr;
+  }
+  s->used -= std::min(s->used, r->est_bytes);
+}
+
+// Copies the member's working unknowns back to the caller's planes.
+opt_status write_back(opt_problem* pb, cudaStream_t st) {
+  for (int c = 0; c < pb->nx; ++c) {
+    cudaError_t e;
+    if (pb->kind == K_MESH)
+      e = cudaMemcpyAsync(pb->user_x[c], pb->x + c * pb->plane, (size_t)pb->V * 4, cudaMemcpyDeviceToDevice, st);
+    else
+      e = cudaMemcpy2DAsync(pb->user_x[c], (size_t)pb->W * 4, pb->x + c * pb->plane, (size_t)pb->P * 4,
+                            (size_t)pb->W * 4, pb->H, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return OPT_ERR_CUDA;
+  }
+  return OPT_OK;
+}
+
+opt_status copy_in(opt_problem* pb, cudaStream_t st) {
+  for (int c = 0; c < pb->nx; ++c) {
+    cudaError_t e;
+    if (pb->kind == K_MESH)
+      e = cudaMemcpyAsync(pb->x + c * pb->plane, pb->user_x[c], (size_t)pb->V * 4, cudaMemcpyDeviceToDevice, st);
+    else
+      e = cudaMemcpy2DAsync(pb->x + c * pb->plane, (size_t)pb->P * 4, pb->user_x[c], (size_t)pb->W * 4,
+                            (size_t)pb->W * 4, pb->H, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return OPT_ERR_CUDA;
+  }
+  return OPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+opt_status opt_server_create(size_t hbm_budget_bytes, const opt_solve_params* params, opt_server** out) {
+  if (!out) return OPT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (hbm_budget_bytes == 0) return OPT_ERR_INVALID_ARG;
+  std::unique_ptr<opt_server> s(new opt_server());
+  if (params) s->prm = *params;
+  else opt_solve_params_default(&s->prm);
+  if (s->prm.outer < 1 || s->prm.inner < 0 || s->prm.materialized) return OPT_ERR_INVALID_ARG;
+  s->budget = hbm_budget_bytes;
+  if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return OPT_ERR_CUDA;
+  }
+  *out = s.release();
+  return OPT_OK;
+}
+
+opt_status opt_server_destroy(opt_server* s) {
+  if (!s) return OPT_OK;
+  cudaStreamSynchronize(s->st);
+  delete s;
+  return OPT_OK;
+}
+
+opt_status opt_server_submit_grid(opt_server* s, const opt_grid_desc* d, uint64_t* ticket) {
+  if (!s || !d || d->W < 1 || d->H < 1) return OPT_ERR_INVALID_ARG;
+  ServeReq* r = new ServeReq();
+  r->gd = *d;
+  r->est_bytes = estimate_grid(*d);
+  const opt_status st = submit(s, r, ticket);
+  if (st != OPT_OK) delete r;
+  return st;
+}
+
+opt_status opt_server_submit_graph(opt_server* s, const opt_graph_desc* d, uint64_t* ticket) {
+  if (!s || !d || d->V < 1 || d->E < 0) return OPT_ERR_INVALID_ARG;
+  ServeReq* r = new ServeReq();
+  r->graph = true;
+  r->md = *d;
+  r->est_bytes = estimate_graph(*d);
+  const opt_status st = submit(s, r, ticket);
+  if (st != OPT_OK) delete r;
+  return st;
+}
+
+opt_status opt_server_step(opt_server* s, int32_t* n_active, int32_t* n_queued) {
+  if (!s) return OPT_ERR_INVALID_ARG;
+  // 1. admission in arrival order under the budget
+  std::vector<ServeReq*> admit;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    while (!s->queue.empty() && s->used + s->queue.front()->est_bytes <= s->budget) {
+      ServeReq* r = s->queue.front();
+      s->queue.pop_front();
+      s->used += r->est_bytes;
+      admit.push_back(r);
+    }
+  }
+  for (ServeReq* r : admit) {
+    opt_status st = r->graph ? opt_problem_create_graph(&r->md, &s->prm, &r->pb)
+                             : opt_problem_create_grid(&r->gd, &s->prm, &r->pb);
+    if (st != OPT_OK) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      finish(s, r, st);
+      continue;
+    }
+    if (copy_in(r->pb, s->st) != OPT_OK) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      finish(s, r, OPT_ERR_CUDA);
+      continue;
+    }
+    k_serve_reset<<<1, 1, 0, s->st>>>(r->pb->d_s, s->prm.lambda0);
+    r->state = 1;
+    s->active.push_back(r);
+    s->dirty = true;
+  }
+  // 2. one LM outer iteration of every member
+  if (!s->active.empty()) {
+    if (s->dirty) {
+      cudaStreamSynchronize(s->st);
+      if (s->batch) {
+        opt_batch_destroy(s->batch);
+        s->batch = nullptr;
+      }
+      std::vector<opt_problem*> ps;
+      for (ServeReq* r : s->active) ps.push_back(r->pb);
+      opt_status st = opt_batch_create(ps.data(), (int)ps.size(), &s->batch);
+      if (st != OPT_OK) return st;
+      st = batch_prepare_round(s->batch, s->prm);
+      if (st != OPT_OK) return st;
+      s->dirty = false;
+    }
+    batch_enqueue_lm_round(s->batch, s->prm, s->st);
+    if (cudaGetLastError() != cudaSuccess) return OPT_ERR_CUDA;
+    s->sbuf.resize(s->active.size());
+    opt_status st = batch_read_scalars(s->batch, s->sbuf.data(), s->st);
+    if (st != OPT_OK) return st;
+    // 3. retire converged / capped members
+    std::vector<ServeReq*> keep;
+    for (size_t i = 0; i < s->active.size(); ++i) {
+      ServeReq* r = s->active[i];
+      const Scalars& t = s->sbuf[i];
+      r->hist.push_back(t.E);
+      const bool capped = t.outer_done >= s->prm.outer;
+      if (!t.done && !capped && !t.nonfinite) {
+        keep.push_back(r);
+        continue;
+      }
+      const double Ef = t.accept ? t.E_trial : t.E;
+      r->hist.push_back(Ef);
+      r->rep.outer_done = t.outer_done;
+      r->rep.pcg_done = t.pcg_iters;
+      r->rep.accepted = t.accepted_total;
+      r->rep.converged = t.converged;
+      r->rep.E0 = r->hist.front();
+      r->rep.E_final = Ef;
+      r->rep.lambda_final = t.lambda;
+      r->rep.ms = 0.f;
+      opt_status ws = write_back(r->pb, s->st);
+      cudaStreamSynchronize(s->st);
+      std::lock_guard<std::mutex> lk(s->mu);
+      finish(s, r, t.nonfinite ? OPT_ERR_NUMERIC : ws);
+      s->dirty = true;
+    }
+    s->active.swap(keep);
+  }
+  if (n_active) *n_active = (int32_t)s->active.size();
+  if (n_queued) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    *n_queued = (int32_t)s->queue.size();
+  }
+  return OPT_OK;
+}
+
+opt_status opt_server_poll(opt_server* s, uint64_t ticket, opt_report* report) {
+  if (!s) return OPT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return OPT_ERR_INVALID_ARG;
+  ServeReq* r = it->second.get();
+  if (r->state != 2) return OPT_ERR_NOT_READY;
+  const opt_status st = r->status;
+  if (report) {
+    double* h = report->E_history;
+    *report = r->rep;
+    report->E_history = h;
+    if (h) std::memcpy(h, r->hist.data(), r->hist.size() * sizeof(double));
+  }
+  s->reqs.erase(it);
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,131 @@
+"""Serving engine: continuous batching of LM solves under an HBM budget.  Each
+request's result must equal its one-at-a-time solve (opt_solve_lm with the
+same parameters) within the stated tolerances, whatever else is in the mix."""
+import numpy as np
+import pytest
+
+from paper_1604_06525_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+OUTER, INNER, REL_TOL = 10, 10, 1e-3
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1604_06525_gb300 import build, api as api_mod
+    build.build()
+    api_mod.load_library()
+    return api_mod
+
+
+def relE(a, b):
+    return abs(a - b) / max(abs(b), 1e-30)
+
+
+def requests():
+    rs = [synth.warp_problem(int(s), int(s), synth.warp_handle_count(int(s), int(s)), seed=400 + i)
+          for i, s in enumerate(synth.batch_sides(6, 24, 96, seed=11))]
+    rs += [synth.mesh_problem(1, seed=410, handle_frac=0.1), synth.mesh_problem(2, seed=411, handle_frac=0.05)]
+    rs += [synth.poisson_problem(40, 30, seed=420), synth.poisson_problem(33, 51, seed=421)]
+    return rs
+
+
+def solo(api, prob):
+    g = api.Problem(prob)
+    r = g.solve_lm(OUTER, INNER, rel_tol=REL_TOL)
+    x = g.x.cpu().numpy().copy()
+    g.close()
+    return r, x
+
+
+def check_same(prob, rep, x, ref, xref):
+    assert rep["status"] == "OPT_OK"
+    assert rep["outer_done"] == ref["outer_done"]
+    assert rep["accepted"] == ref["accepted"]
+    assert rep["converged"] == ref["converged"]
+    tol = 1e-5 if prob.kind == "mesh" else 1e-6
+    for a, b in zip(rep["E_history"][:-1], ref["E_history"][:-1]):
+        assert relE(a, b) <= tol
+    assert relE(rep["E_final"], ref["E_final"]) <= 1e-5
+    xs = x.cpu().numpy().reshape(-1)
+    d = np.linalg.norm(xs - xref.reshape(-1)) / max(np.linalg.norm(xref), 1e-30)
+    assert d <= (1e-4 if prob.kind == "mesh" else 1e-6)
+
+
+def test_serve_alone_equals_mix(api):
+    probs = requests()
+    refs = [solo(api, p) for p in probs]
+    srv = api.Server(4 << 30, outer=OUTER, inner=INNER, rel_tol=REL_TOL)
+    tickets = [srv.submit(p) for p in probs[:5]]
+    srv.step()
+    srv.step()
+    tickets += [srv.submit(p) for p in probs[5:]]     # join while others are mid-solve
+    done = {}
+    for _ in range(200):
+        active, queued = srv.step()
+        for t in tickets:
+            if t not in done:
+                r = srv.poll(t)
+                if r is not None:
+                    done[t] = r
+        if len(done) == len(tickets):
+            break
+    assert len(done) == len(tickets)
+    for p, t, (ref, xref) in zip(probs, tickets, refs):
+        rep, x = done[t]
+        check_same(p, rep, x, ref, xref)
+    srv.close()
+
+
+def server_estimate_warp(W, H, n_handles):
+    """The server's footprint estimate of a planned warp (24 pitched planes,
+    tiles, handles, fixed overhead)."""
+    P = (W + 31) // 32 * 32
+    tiles = ((W + 31) // 32) * ((H + 7) // 8)
+    return 24 * P * H * 4 + tiles * 64 + n_handles * 16 + (1 << 16)
+
+
+def test_serve_budget_limits_admission(api):
+    probs = [synth.warp_problem(64, 48, 8, seed=500 + i) for i in range(6)]
+    refs = [solo(api, p) for p in probs]
+    est = server_estimate_warp(64, 48, 8)
+    srv = api.Server(2 * est + 100, outer=OUTER, inner=INNER, rel_tol=REL_TOL)   # room for exactly two
+    tickets = [srv.submit(p) for p in probs]
+    done, max_active = {}, 0
+    for _ in range(400):
+        active, queued = srv.step()
+        max_active = max(max_active, active)
+        for t in tickets:
+            if t not in done:
+                r = srv.poll(t)
+                if r is not None:
+                    done[t] = r
+        if len(done) == len(tickets):
+            break
+    assert len(done) == len(tickets)
+    assert max_active == 2
+    for p, t, (ref, xref) in zip(probs, tickets, refs):
+        rep, x = done[t]
+        check_same(p, rep, x, ref, xref)
+    srv.close()
+
+
+def test_serve_rejects_oversize_and_reports_planning_errors(api):
+    srv = api.Server(1 << 20, outer=OUTER, inner=INNER)
+    with pytest.raises(api.OptError) as ei:
+        srv.submit(synth.warp_problem(512, 512, 8, seed=1))
+    assert ei.value.status == 6
+    srv.close()
+    srv = api.Server(1 << 30, outer=OUTER, inner=INNER)
+    bad = synth.warp_problem(16, 16, 2, seed=2)
+    bad.handle_idx = np.array([5, 5], np.int32)           # duplicate handle: planning fails
+    t = srv.submit(bad)
+    srv.step()
+    with pytest.raises(api.OptError) as ei:
+        srv.poll(t)
+    assert ei.value.status == 1
+    srv.close()
