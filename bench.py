@@ -35,7 +35,7 @@ METRIC = "PCG iters/s and % HBM roofline; batched solves/s and p99 latency vs pl
 UNIT = "PCG iters/s"
 W_BENCH, H_BENCH, HANDLES, OUTER, INNER = 1024, 1024, 64, 20, 20
 # algorithmic bytes per pixel (float32 planes, each touched once per launch)
-BYTES_APPLY_WARP = 68      # read r 12, M^-1 8, p_old 12, theta 4, UrShape 8; write p 12, q 12
+BYTES_APPLY_WARP = 72      # read r 12, M^-1 8, p_old 12, cos/sin 8, UrShape 8; write p 12, q 12
 BYTES_UPDATE_WARP = 80     # read delta 12, p 12, r 12, q 12, M^-1 8; write delta 12, r 12
 L2_FLUSH_BYTES = 512 << 20
 
@@ -189,6 +189,7 @@ def roofline_for(api, synth, torch, W, H, peak, iters=20):
     the launching stream, mean over `iters` launches)."""
     prob = synth.warp_problem(W, H, max(8, int(round(64.0 * W * H / 2 ** 20))), seed=synth.BASE_SEED)
     gp = api.Problem(prob)
+    gp.autotune()
     gp.profile_pcg(3)
     ms_init, ms_apply, ms_update = gp.profile_pcg(iters)
     px = W * H
@@ -200,6 +201,20 @@ def roofline_for(api, synth, torch, W, H, peak, iters=20):
     del prob
     torch.cuda.empty_cache()
     return out, ms_init
+
+
+def aggregate_replicas(dev_ms: float, pcg_done: int, world: int, device=None):
+    """Replica timing across ranks: the slowest rank's time bounds the job and
+    every rank's PCG iterations count.  Returns (max ms, total iterations)."""
+    if world <= 1:
+        return dev_ms, pcg_done
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([dev_ms, float(pcg_done)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0].item()), int(round(t[1].item()))
 
 
 def pct(v, q):
@@ -370,6 +385,7 @@ def run_ours(args):
 
     prob = synth.warp_problem(W_BENCH, H_BENCH, HANDLES, seed=synth.BASE_SEED)
     gp = api.Problem(prob)
+    chunking, _ = gp.autotune()          # work granularity (outside the timed region)
     x0 = gp.x.clone()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -393,12 +409,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     dev_ms = sum(r["ms"] for r in reps)
-    t_max = dev_ms
-    if world > 1:
-        t = torch.tensor([dev_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    pcg_total = sum(r["pcg_done"] for r in reps) * world
+    t_max, pcg_total = aggregate_replicas(dev_ms, sum(r["pcg_done"] for r in reps), world, dev)
     value = pcg_total / (t_max / 1000.0)
     ms_per_step = t_max / args.steps
     E_final = reps[-1]["E_final"]
@@ -480,6 +491,7 @@ def run_ours(args):
                                f"GN {OUTER} outer x {INNER} PCG, Jacobi, matrix-free, one CUDA graph per solve",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed between steps (512 MB write)", "precision": "f32 vectors, f64 dots/energies",
+                   "tiles_per_block": chunking,
                    "E_final": E_final, "wall_s": wall},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": roof[dom]["achieved"], "peak": peak,
                      "unit": "GB/s", "frac": roof[dom]["frac"],

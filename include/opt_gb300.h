@@ -128,7 +128,8 @@ typedef struct {
     int32_t use_precond;      /* 1 = Jacobi preconditioner (default), 0 = plain CG */
     int32_t materialized;     /* 1 = materialized CSR J, q = J^T (J p) (Sec. 7) */
     int32_t use_graph;        /* 1 = replay the solve as one CUDA graph (default) */
-    int32_t reserved;
+    int32_t tile_w;           /* grid planning only: tile width 32 or 128 (warp), 0 = automatic
+                                 (128 for warps at least 256 pixels wide, else 32) */
     void* stream;             /* cudaStream_t; NULL = legacy default stream */
 } opt_solve_params;
 
@@ -212,6 +213,21 @@ opt_status opt_eval_energy(opt_problem* prob, double* energy);
  * direction update), ms[2] = vector update.  ms: host, 3 floats.  Leaves the
  * PCG state as opt_pcg_init + opt_pcg_step would (lambda = 0). */
 opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, float* ms);
+
+/* Work granularity of the problem's kernels.  units_per_block > 0: that many
+ * consecutive tiles (grid) or 256-vertex tiles and units_per_block * 256 edges
+ * (graph) per block; units_per_block < 0: the work split into
+ * (-units_per_block) x (number of SMs) balanced blocks (grid; graph: 4x that);
+ * 0 restores the default (balanced, 2 blocks per SM for grids, 8 for graphs).
+ * Drops the cached solve graph.  Synchronises the device. */
+opt_status opt_problem_set_chunking(opt_problem* prob, int32_t units_per_block);
+
+/* Autotuner: times applyJTJ + vector update (opt_profile_pcg) for each
+ * candidate granularity {-1, -2, -3, -4, -6, -8, 1, 4} (see
+ * opt_problem_set_chunking), keeps the fastest and
+ * returns it in *chosen and its per-iteration time in *best_ms (host, either
+ * may be NULL).  Leaves the PCG state as opt_profile_pcg does. */
+opt_status opt_problem_autotune(opt_problem* prob, int32_t* chosen, float* best_ms);
 
 /* Number of unknowns (elements per plane x planes) and of planes. */
 opt_status opt_problem_info(const opt_problem* prob, int64_t* n_unknowns, int32_t* n_planes,

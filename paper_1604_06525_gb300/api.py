@@ -41,7 +41,7 @@ class SolveParams(ctypes.Structure):
                 ("lambda_min", c_double), ("lambda_max", c_double), ("diag_min", c_double),
                 ("diag_max", c_double), ("eta", c_double), ("rel_tol", c_double),
                 ("use_precond", c_int32), ("materialized", c_int32), ("use_graph", c_int32),
-                ("reserved", c_int32), ("stream", c_void_p)]
+                ("tile_w", c_int32), ("stream", c_void_p)]
 
 
 class Report(ctypes.Structure):
@@ -65,6 +65,8 @@ _SIGNATURES = [
     ("opt_eval_jtf", c_int32, [c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
     ("opt_eval_energy", c_int32, [c_void_p, POINTER(c_double)]),
     ("opt_profile_pcg", c_int32, [c_void_p, c_int32, c_void_p, POINTER(c_float)]),
+    ("opt_problem_set_chunking", c_int32, [c_void_p, c_int32]),
+    ("opt_problem_autotune", c_int32, [c_void_p, POINTER(c_int32), POINTER(c_float)]),
     ("opt_problem_info", c_int32, [c_void_p, POINTER(c_int64), POINTER(c_int32), POINTER(c_int64)]),
     ("opt_batch_create", c_int32, [POINTER(c_void_p), c_int32, POINTER(c_void_p)]),
     ("opt_batch_destroy", c_int32, [c_void_p]),
@@ -203,7 +205,7 @@ class Problem:
     owns (the unknowns stay caller-owned device memory from the library's
     point of view)."""
 
-    def __init__(self, prob, device: str = "cuda"):
+    def __init__(self, prob, device: str = "cuda", tile_w: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -223,7 +225,8 @@ class Problem:
         d, self.x, self._keep = make_descriptor(prob, self.device)
         if prob.kind in ("warp", "poisson"):
             self.W, self.H = prob.W, prob.H
-            _check(self.lib.opt_problem_create_grid(ctypes.byref(d), None, ctypes.byref(h)),
+            plan = default_params(tile_w=tile_w)
+            _check(self.lib.opt_problem_create_grid(ctypes.byref(d), ctypes.byref(plan), ctypes.byref(h)),
                    "opt_problem_create_grid")
         else:
             self.V = prob.V
@@ -310,6 +313,15 @@ class Problem:
         st = torch.cuda.current_stream(self.device).cuda_stream
         _check(self.lib.opt_profile_pcg(self.h, n_iters, st, ms), "opt_profile_pcg")
         return ms[0], ms[1], ms[2]
+
+    def set_chunking(self, units_per_block: int):
+        _check(self.lib.opt_problem_set_chunking(self.h, units_per_block), "opt_problem_set_chunking")
+
+    def autotune(self):
+        """Picks the work granularity with the fastest applyJTJ + update."""
+        c, ms = c_int32(), c_float()
+        _check(self.lib.opt_problem_autotune(self.h, ctypes.byref(c), ctypes.byref(ms)), "opt_problem_autotune")
+        return c.value, ms.value
 
     def pcg_state(self):
         import torch

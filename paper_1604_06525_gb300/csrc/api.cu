@@ -194,7 +194,8 @@ void dense_planes(const opt_problem* pb, const float* base, float** out, int n) 
 }
 
 GridLaunch grid_launch(const opt_problem* pb, cudaStream_t st) {
-  return GridLaunch{pb->dg, pb->d_chunks, pb->d_tiles, pb->d_part, pb->nchunks, st};
+  return GridLaunch{pb->dg, pb->d_chunks, pb->d_tiles, pb->d_part, pb->nchunks, st, pb->hg.tw,
+                    pb->hg.mask != nullptr};
 }
 MeshLaunch mesh_launch(const opt_problem* pb, cudaStream_t st) {
   return MeshLaunch{pb->dm, pb->d_vchunks, pb->d_echunks, pb->d_part, pb->d_acc, pb->nvchunks,
@@ -375,6 +376,21 @@ std::vector<Chunk> make_chunks(int n_units, int per, int prob) {
   return ch;
 }
 
+// Splits n_units into exactly min(n_units, n_chunks) chunks whose sizes differ
+// by at most one unit (grids sized to a multiple of the SM count).
+std::vector<Chunk> make_chunks_balanced(int n_units, int n_chunks, int prob) {
+  std::vector<Chunk> ch;
+  const int n = std::max(n_units, 1);
+  const int c = std::max(1, std::min(n, n_chunks));
+  for (int k = 0; k < c; ++k)
+    ch.push_back(Chunk{prob, (int)((long long)k * n / c), (int)std::min<long long>((long long)(k + 1) * n / c, n_units), 0});
+  return ch;
+}
+
+// Default work split: two blocks per SM (the residency of the wide-tile
+// kernels), balanced.
+constexpr int kDefaultBlocksPerSM = 2;
+
 }  // namespace
 
 // =============================================================================
@@ -418,7 +434,6 @@ const char* opt_status_str(opt_status s) {
 const char* opt_last_error(void) { return g_err.c_str(); }
 
 opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_params* prm, opt_problem** out) {
-  (void)prm;
   if (!out) return OPT_ERR_INVALID_ARG;
   *out = nullptr;
   if (!d) return OPT_ERR_INVALID_ARG;
@@ -426,6 +441,11 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   if (d->W < 1 || d->H < 1 || d->W >= 32768 || d->H >= 32768) return OPT_ERR_INVALID_ARG;
   const bool warp = d->kind == OPT_ARAP_WARP_2D;
   const int nx = warp ? 3 : 4, nc = warp ? 2 : 4, nm = warp ? 2 : 1;
+  // tile width: 128-pixel tiles (float4 rows) for warps at least 256 wide,
+  // 32-pixel tiles otherwise; Poisson always uses 32
+  const int req_tw = prm ? prm->tile_w : 0;
+  if (req_tw != 0 && req_tw != 32 && req_tw != 128) return OPT_ERR_INVALID_ARG;
+  const int tw = !warp ? 32 : (req_tw ? req_tw : (d->W >= 256 ? 128 : 32));
   for (int c = 0; c < nx; ++c)
     if (!d->unknowns[c]) return OPT_ERR_INVALID_ARG;
   for (int c = 0; c < nc; ++c)
@@ -436,13 +456,14 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   if (warp && (!std::isfinite(d->w_reg) || !std::isfinite(d->w_fit) || d->w_reg < 0.f || d->w_fit < 0.f))
     return OPT_ERR_INVALID_ARG;
 
+  if (warp && tw == 128) CK(grid_kernels_prepare());
   std::unique_ptr<opt_problem> pb(new opt_problem());
   pb->kind = warp ? K_WARP : K_POISSON;
   pb->nx = nx;
   pb->nm = nm;
   pb->W = d->W;
   pb->H = d->H;
-  pb->P = round_up(d->W, 32);
+  pb->P = round_up(d->W, tw);
   pb->plane = (long long)pb->P * d->H;
   pb->ulen = (long long)d->W * d->H;
   CKS(common_setup(pb.get()));
@@ -473,25 +494,23 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   }
 
   // active tiles: at least one unmasked (warp) / free (Poisson) pixel
-  const int ntx = (W + TW - 1) / TW, nty = (H + TH - 1) / TH;
+  const int ntx = (W + tw - 1) / tw, nty = (H + TH - 1) / TH;
   std::vector<int> tiles;
   for (int ty = 0; ty < nty; ++ty)
     for (int tx = 0; tx < ntx; ++tx) {
       bool act = mask.empty();
       for (int y = ty * TH; !act && y < std::min(H, ty * TH + TH); ++y)
-        for (int x = tx * TW; x < std::min(W, tx * TW + TW); ++x)
+        for (int x = tx * tw; x < std::min(W, tx * tw + tw); ++x)
           if (mask[(size_t)y * W + x] == 0) { act = true; break; }
       if (act) tiles.push_back((ty << 16) | tx);
     }
   if (tiles.empty()) tiles.push_back(0);
-  const int target = std::max(1, pb->sms * 8);
-  const int tpc = std::max(1, ((int)tiles.size() + target - 1) / target);
-  std::vector<Chunk> chunks = make_chunks((int)tiles.size(), tpc, 0);
+  std::vector<Chunk> chunks = make_chunks_balanced((int)tiles.size(), pb->sms * kDefaultBlocksPerSM, 0);
 
   // handles sorted by tile
   std::vector<int> order(nh);
   std::iota(order.begin(), order.end(), 0);
-  auto tile_of = [&](int pix) { return (pix / W / TH) * ntx + (pix % W) / TW; };
+  auto tile_of = [&](int pix) { return (pix / W / TH) * ntx + (pix % W) / tw; };
   std::sort(order.begin(), order.end(), [&](int a, int b) {
     const int ta = tile_of(hidx[a]), tb = tile_of(hidx[b]);
     return ta != tb ? ta < tb : hidx[a] < hidx[b];
@@ -522,6 +541,8 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   CKS(dalloc(q, &q->pbuf, 2 * nx * pl));
   CKS(dalloc(q, &m, nm * pl));
   CKS(dalloc(q, &dc, nm * pl));
+  float* csn = nullptr;
+  if (warp && tw == 128) CKS(dalloc(q, &csn, 2 * pl));
   if (d->mask) {
     CKS(dalloc(q, &dmask, pl));
     CK(cudaMemcpy2D(dmask, P, d->mask, W, W, H, cudaMemcpyDeviceToDevice));
@@ -550,6 +571,8 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   GridProb& g = q->hg;
   g.kind = q->kind;
   g.W = W; g.H = H; g.P = P;
+  g.tw = tw;
+  g.csn = csn;
   g.ntx = ntx; g.nty = nty;
   g.plane = (long long)pl;
   g.chunk_begin = 0;
@@ -648,12 +671,9 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   }
 
   const int target = std::max(1, q->sms * 8);
-  const int vtpc = std::max(1, (nvt + target - 1) / target);
-  std::vector<Chunk> vch;
-  for (int t = 0; t < std::max(nvt, 1); t += vtpc)
-    vch.push_back(Chunk{0, t * VT, std::min(V, (t + vtpc) * VT), 0});
-  const int epc = std::max(NT, round_up((E + target - 1) / target, NT));
-  std::vector<Chunk> ech = make_chunks(E, epc, 0);
+  std::vector<Chunk> vch = make_chunks_balanced(nvt, target, 0);
+  for (Chunk& c : vch) { c.begin *= VT; c.end = std::min(V, c.end * VT); }
+  std::vector<Chunk> ech = make_chunks_balanced(E, target, 0);
 
   const size_t pl = (size_t)Vp;
   float *U = nullptr, *dgw = nullptr, *m = nullptr, *dc = nullptr, *dhtgt = nullptr;
@@ -668,6 +688,8 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   CKS(dalloc(q, &m, 4 * pl));
   CKS(dalloc(q, &dc, 4 * pl));
   CKS(dalloc(q, &q->d_acc, 3 * pl));
+  float* mcsn = nullptr;
+  CKS(dalloc(q, &mcsn, 6 * pl));
   for (int c = 0; c < 3; ++c)
     CK(cudaMemcpy(U + c * pl, d->urshape[c], (size_t)V * 4, cudaMemcpyDeviceToDevice));
   CKS(upload(dgw, degw));
@@ -704,6 +726,7 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   g.x = q->x; g.U = U; g.degw = dgw; g.e0 = de0; g.e1 = de1;
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
   g.acc = q->d_acc;
+  g.csn = mcsn;
   g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;
   g.jtf_out = nullptr; g.diag_out = nullptr;
   g.s = q->d_s;
@@ -916,6 +939,78 @@ opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, flo
   for (cudaEvent_t e : ev)
     if (e) cudaEventDestroy(e);
   return status;
+}
+
+// Rebuilds the problem's chunk table with `per` tiles (grid) or vertex tiles
+// (graph) per block; 0 restores the default (about 8 blocks per SM).
+static opt_status rechunk(opt_problem* pb, int per) {
+  CK(cudaDeviceSynchronize());
+  if (pb->gexec) {
+    cudaGraphExecDestroy(pb->gexec);
+    pb->gexec = nullptr;
+    pb->gkey.clear();
+  }
+  const int bps = per < 0 ? -per : kDefaultBlocksPerSM;     // blocks per SM for balanced splits
+  const int target = std::max(1, pb->sms * (is_grid(pb) ? bps : 4 * bps));
+  if (is_grid(pb)) {
+    std::vector<Chunk> chunks = per > 0 ? make_chunks(pb->ntiles, per, 0)
+                                        : make_chunks_balanced(pb->ntiles, target, 0);
+    if ((int)chunks.size() > pb->nchunks) {
+      CKS(dalloc(pb, &pb->d_chunks, chunks.size()));
+      CKS(dalloc(pb, &pb->d_part, 2 * chunks.size()));
+    }
+    CKS(upload(pb->d_chunks, chunks));
+    pb->nchunks = (int)chunks.size();
+    pb->hg.chunk_begin = 0;
+    pb->hg.chunk_end = pb->nchunks;
+  } else {
+    const int nvt = (pb->V + VT - 1) / VT;
+    std::vector<Chunk> vch = per > 0 ? make_chunks(nvt, per, 0) : make_chunks_balanced(nvt, target, 0);
+    for (Chunk& c : vch) { c.begin *= VT; c.end = std::min(pb->V, c.end * VT); }
+    std::vector<Chunk> ech = per > 0 ? make_chunks(pb->E, per * VT, 0) : make_chunks_balanced(pb->E, target, 0);
+    if ((int)vch.size() > pb->nvchunks) CKS(dalloc(pb, &pb->d_vchunks, vch.size()));
+    if ((int)ech.size() > pb->nechunks) CKS(dalloc(pb, &pb->d_echunks, ech.size()));
+    const size_t need = 2 * std::max(vch.size(), ech.size());
+    if (need > 2 * (size_t)std::max(pb->nvchunks, pb->nechunks)) CKS(dalloc(pb, &pb->d_part, need));
+    CKS(upload(pb->d_vchunks, vch));
+    CKS(upload(pb->d_echunks, ech));
+    pb->nvchunks = (int)vch.size();
+    pb->nechunks = (int)ech.size();
+    pb->hm.vchunk_begin = 0;
+    pb->hm.vchunk_end = pb->nvchunks;
+    pb->hm.echunk_begin = 0;
+    pb->hm.echunk_end = pb->nechunks;
+  }
+  CKS(upload_desc(pb, nullptr));
+  return OPT_OK;
+}
+
+opt_status opt_problem_set_chunking(opt_problem* prob, int32_t units_per_block) {
+  if (!prob || units_per_block < -64 || units_per_block > 65536) return OPT_ERR_INVALID_ARG;
+  return rechunk(prob, units_per_block);
+}
+
+opt_status opt_problem_autotune(opt_problem* prob, int32_t* chosen, float* best_ms) {
+  if (!prob) return OPT_ERR_INVALID_ARG;
+  // balanced splits with 1..8 blocks per SM, and fixed runs of 1 and 4 units
+  const int cand[] = {-1, -2, -3, -4, -6, -8, 1, 4};
+  int best = 0;
+  float bms = 1e30f;
+  for (int c : cand) {
+    CKS(rechunk(prob, c));
+    float ms[3];
+    CKS(opt_profile_pcg(prob, 4, nullptr, ms));
+    CKS(opt_profile_pcg(prob, 8, nullptr, ms));
+    const float t = ms[1] + ms[2];
+    if (t < bms) {
+      bms = t;
+      best = c;
+    }
+  }
+  CKS(rechunk(prob, best));
+  if (chosen) *chosen = best;
+  if (best_ms) *best_ms = bms;
+  return OPT_OK;
 }
 
 opt_status opt_eval_energy(opt_problem* prob, double* energy) {

@@ -130,6 +130,8 @@ opt_status bupload(std::vector<void*>& allocs, T** ptr, const std::vector<T>& v)
 
 struct GridGroup {
   int kind = 0;
+  int tw = 32;
+  int masked = 0;
   std::vector<int> members;            // indices into opt_batch::probs
   GridProb* d_probs = nullptr;
   Chunk* d_chunks = nullptr;
@@ -202,12 +204,18 @@ opt_status build_tables(opt_batch* b, int tpc) {
       opt_problem* pb = b->probs[g.members[mi]];
       std::vector<int> t(pb->ntiles);
       BCK(cudaMemcpy(t.data(), pb->d_tiles, t.size() * sizeof(int), cudaMemcpyDeviceToHost));
-      const int per = tpc > 0 ? tpc : std::max(1, (pb->ntiles + pb->sms * 8 - 1) / (pb->sms * 8));
       GridProb d = pb->hg;
       d.chunk_begin = (int)chunks.size();
       const int base = (int)tiles.size();
-      for (int s = 0; s < pb->ntiles; s += per)
-        chunks.push_back(Chunk{(int)mi, base + s, base + std::min(s + per, pb->ntiles), 0});
+      if (tpc > 0) {
+        for (int s = 0; s < pb->ntiles; s += tpc)
+          chunks.push_back(Chunk{(int)mi, base + s, base + std::min(s + tpc, pb->ntiles), 0});
+      } else {
+        // the member's own split: identical reductions to its solo solve
+        std::vector<Chunk> own(pb->nchunks);
+        BCK(cudaMemcpy(own.data(), pb->d_chunks, own.size() * sizeof(Chunk), cudaMemcpyDeviceToHost));
+        for (Chunk c : own) chunks.push_back(Chunk{(int)mi, base + c.begin, base + c.end, 0});
+      }
       d.chunk_end = (int)chunks.size();
       tiles.insert(tiles.end(), t.begin(), t.end());
       gp.push_back(d);
@@ -250,7 +258,7 @@ opt_status build_tables(opt_batch* b, int tpc) {
 }
 
 GridLaunch gl(const GridGroup& g, cudaStream_t st) {
-  return GridLaunch{g.d_probs, g.d_chunks, g.d_tiles, g.d_part, g.nchunks, st};
+  return GridLaunch{g.d_probs, g.d_chunks, g.d_tiles, g.d_part, g.nchunks, st, g.tw, g.masked};
 }
 MeshLaunch ml(const MeshGroup& g, cudaStream_t st) {
   return MeshLaunch{g.d_probs, g.d_vch, g.d_ech, g.d_part, nullptr, g.nv, g.ne, st};
@@ -441,13 +449,20 @@ opt_status opt_batch_create(opt_problem* const* probs, int32_t n, opt_batch** ou
       if (probs[i] == probs[j]) return OPT_ERR_INVALID_ARG;
   std::unique_ptr<opt_batch> b(new opt_batch());
   b->probs.assign(probs, probs + n);
-  for (int kind : {(int)K_WARP, (int)K_POISSON}) {
-    GridGroup g;
-    g.kind = kind;
-    for (int i = 0; i < n; ++i)
-      if (probs[i]->kind == kind) g.members.push_back(i);
-    if (!g.members.empty()) b->grids.push_back(g);
-  }
+  // one launch group per (kind, tile width, mask presence): each group runs
+  // one kernel variant
+  for (int kind : {(int)K_WARP, (int)K_POISSON})
+    for (int tw : {32, 128})
+      for (int masked : {0, 1}) {
+        GridGroup g;
+        g.kind = kind;
+        g.tw = tw;
+        g.masked = masked;
+        for (int i = 0; i < n; ++i)
+          if (probs[i]->kind == kind && probs[i]->hg.tw == tw && (probs[i]->hg.mask != nullptr) == (masked != 0))
+            g.members.push_back(i);
+        if (!g.members.empty()) b->grids.push_back(g);
+      }
   for (int i = 0; i < n; ++i)
     if (probs[i]->kind == K_MESH) b->mesh.members.push_back(i);
   BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));

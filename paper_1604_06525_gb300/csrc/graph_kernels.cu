@@ -88,6 +88,13 @@ __global__ void __launch_bounds__(NT) k_mesh_init_v(const MeshProb* __restrict__
     pr.q[v] = g0; pr.q[pl + v] = g1; pr.q[2 * pl + v] = g2;
     pr.q[3 * pl + v] = 0.f; pr.q[4 * pl + v] = 0.f; pr.q[5 * pl + v] = 0.f;
     pr.acc[v] = 0.f; pr.acc[pl + v] = 0.f; pr.acc[2 * pl + v] = 0.f;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      float sn, cs;
+      sincosf(pr.x[(3 + m) * pl + v], &sn, &cs);
+      pr.csn[(2 * m) * pl + v] = cs;
+      pr.csn[(2 * m + 1) * pl + v] = sn;
+    }
   }
   if (publish_partials(part, blockIdx.x, e, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double a, b;
@@ -118,7 +125,8 @@ __global__ void __launch_bounds__(NT) k_mesh_init_e(const MeshProb* __restrict__
       const float vx = pr.U[a] - pr.U[b];
       const float vy = pr.U[pl + a] - pr.U[pl + b];
       const float vz = pr.U[2 * pl + a] - pr.U[2 * pl + b];
-      const RotV R = rot_apply(pr.x[3 * pl + a], pr.x[4 * pl + a], pr.x[5 * pl + a], vx, vy, vz);
+      const RotV R = rot_apply_cs(pr.csn[a], pr.csn[pl + a], pr.csn[2 * pl + a], pr.csn[3 * pl + a],
+                                    pr.csn[4 * pl + a], pr.csn[5 * pl + a], vx, vy, vz);
       const float r0 = sw * ((pr.x[a] - pr.x[b]) + (vx - R.rv[0]));
       const float r1 = sw * ((pr.x[pl + a] - pr.x[pl + b]) + (vy - R.rv[1]));
       const float r2 = sw * ((pr.x[2 * pl + a] - pr.x[2 * pl + b]) + (vz - R.rv[2]));
@@ -206,6 +214,15 @@ __global__ void __launch_bounds__(NT) k_mesh_init_f(const MeshProb* __restrict__
 // ---------------------------------------------------------------------------
 // PCGStep: applyJTJ
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ld4g(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float c4(const float4& a, int k) {
+  return k == 0 ? a.x : (k == 1 ? a.y : (k == 2 ? a.z : a.w));
+}
+
+// Direction update and the vertex rows of q (fit + damping), four vertices per
+// thread: every load of a quad is issued before any store.  Vertex ranges
+// start at multiples of 256 and the planes are padded to 32 (zeros), so a quad
+// never leaves the plane.
 __global__ void __launch_bounds__(NT) k_mesh_apply_v(const MeshProb* __restrict__ probs,
                                                      const Chunk* __restrict__ chunks,
                                                      double* __restrict__ part,
@@ -221,31 +238,59 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_v(const MeshProb* __restrict_
   const float* __restrict__ pin = p_override ? p_override : pr.p + (long long)(par & 1) * 6 * pl;
   float* __restrict__ pout = pr.p + (long long)((par + 1) & 1) * 6 * pl;
   float acc = 0.f;
-  for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
-    float pv[6];
+  const int q0 = ch.begin / 4, q1 = (ch.end + 3) / 4;
+  for (int qi = q0 + threadIdx.x; qi < q1; qi += NT) {
+    const int v0 = 4 * qi;
+    float4 pv[6];
+    if (update) {
+      float4 rr[6], mm[4], po[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      if (update) {
-        float z = pr.m[(c < 3 ? 0 : c - 2) * pl + v] * pr.r[c * pl + v];
-        if (beta != 0.0f) z += beta * pin[c * pl + v];
-        pv[c] = z;
-        pout[c * pl + v] = z;
-      } else {
-        pv[c] = pin[c * pl + v];
+      for (int c = 0; c < 6; ++c) rr[c] = ld4g(pr.r + c * pl + v0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) mm[k] = ld4g(pr.m + k * pl + v0);
+      if (beta != 0.0f) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) po[c] = ld4g(pin + c * pl + v0);
       }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const float4 m = mm[c < 3 ? 0 : c - 2];
+        pv[c] = make_float4(m.x * rr[c].x, m.y * rr[c].y, m.z * rr[c].z, m.w * rr[c].w);
+        if (beta != 0.0f) {
+          pv[c].x = fmaf(beta, po[c].x, pv[c].x); pv[c].y = fmaf(beta, po[c].y, pv[c].y);
+          pv[c].z = fmaf(beta, po[c].z, pv[c].z); pv[c].w = fmaf(beta, po[c].w, pv[c].w);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) *reinterpret_cast<float4*>(pout + c * pl + v0) = pv[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) pv[c] = ld4g(pin + c * pl + v0);
     }
-    float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (handle_of(pr, v) >= 0) {
-      q[0] = pr.w_fit * pv[0]; q[1] = pr.w_fit * pv[1]; q[2] = pr.w_fit * pv[2];
-    }
+    float4 dc[4];
     if (pr.lm) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) q[c] += lam * pr.dc[(c < 3 ? 0 : c - 2) * pl + v] * pv[c];
+      for (int k = 0; k < 4; ++k) dc[k] = ld4g(pr.dc + k * pl + v0);
+    }
+    float q[6][4];
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) q[c][k] = pr.lm ? lam * c4(dc[c < 3 ? 0 : c - 2], k) * c4(pv[c], k) : 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int v = v0 + k;
+      if (v < pr.V && handle_of(pr, v) >= 0) {
+        q[0][k] += pr.w_fit * c4(pv[0], k);
+        q[1][k] += pr.w_fit * c4(pv[1], k);
+        q[2][k] += pr.w_fit * c4(pv[2], k);
+      }
     }
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      pr.q[c * pl + v] = q[c];
-      acc += pv[c] * q[c];
+      *reinterpret_cast<float4*>(pr.q + c * pl + v0) = make_float4(q[c][0], q[c][1], q[c][2], q[c][3]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc += c4(pv[c], k) * q[c][k];
     }
   }
   if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
@@ -280,7 +325,8 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_e(const MeshProb* __restrict_
       const float vx = pr.U[a] - pr.U[b];
       const float vy = pr.U[pl + a] - pr.U[pl + b];
       const float vz = pr.U[2 * pl + a] - pr.U[2 * pl + b];
-      const RotV R = rot_apply(pr.x[3 * pl + a], pr.x[4 * pl + a], pr.x[5 * pl + a], vx, vy, vz);
+      const RotV R = rot_apply_cs(pr.csn[a], pr.csn[pl + a], pr.csn[2 * pl + a], pr.csn[3 * pl + a],
+                                    pr.csn[4 * pl + a], pr.csn[5 * pl + a], vx, vy, vz);
       const float pa3 = p[3 * pl + a], pa4 = p[4 * pl + a], pa5 = p[5 * pl + a];
       float j0 = sw * (p[a] - p[b]);
       float j1 = sw * (p[pl + a] - p[pl + b]);
@@ -329,7 +375,8 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_e(const MeshProb* __restrict_
   }
 }
 
-// delta += alpha p, r -= alpha q, z = M^-1 r, float64 r.z -> beta.
+// delta += alpha p, r -= alpha q, z = M^-1 r, float64 r.z -> beta; four
+// vertices per thread, all loads first.
 __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__ probs,
                                                     const Chunk* __restrict__ chunks,
                                                     double* __restrict__ part, int par) {
@@ -341,14 +388,30 @@ __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__
   const float alpha = s->alpha_f;
   const float* __restrict__ pn = pr.p + (long long)((par + 1) & 1) * 6 * pl;
   float acc = 0.f;
-  for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
+  const int q0 = ch.begin / 4, q1 = (ch.end + 3) / 4;
+  for (int qi = q0 + threadIdx.x; qi < q1; qi += NT) {
+    const int v0 = 4 * qi;
+    float4 pv[6], qv[6], dv[6], rv[6], mv[4];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      const long long j = c * pl + v;
-      pr.d[j] += alpha * pn[j];
-      const float rv = pr.r[j] - alpha * pr.q[j];
-      pr.r[j] = rv;
-      acc += rv * (pr.m[(c < 3 ? 0 : c - 2) * pl + v] * rv);
+      pv[c] = ld4g(pn + c * pl + v0);
+      qv[c] = ld4g(pr.q + c * pl + v0);
+      dv[c] = *reinterpret_cast<const float4*>(pr.d + c * pl + v0);
+      rv[c] = *reinterpret_cast<const float4*>(pr.r + c * pl + v0);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mv[k] = ld4g(pr.m + k * pl + v0);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const float4 m = mv[c < 3 ? 0 : c - 2];
+      dv[c].x += alpha * pv[c].x; dv[c].y += alpha * pv[c].y;
+      dv[c].z += alpha * pv[c].z; dv[c].w += alpha * pv[c].w;
+      rv[c].x -= alpha * qv[c].x; rv[c].y -= alpha * qv[c].y;
+      rv[c].z -= alpha * qv[c].z; rv[c].w -= alpha * qv[c].w;
+      acc += rv[c].x * (m.x * rv[c].x) + rv[c].y * (m.y * rv[c].y) + rv[c].z * (m.z * rv[c].z) +
+             rv[c].w * (m.w * rv[c].w);
+      *reinterpret_cast<float4*>(pr.d + c * pl + v0) = dv[c];
+      *reinterpret_cast<float4*>(pr.r + c * pl + v0) = rv[c];
     }
   }
   if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {

@@ -21,6 +21,8 @@
 //   R'(t) v  = (-sin t v.x - cos t v.y, cos t v.x - sin t v.y).
 // Poisson algebra (per channel): r_{k,d} = (X_k - X_{k+d}) - (T_k - T_{k+d});
 //   the residual of a free neighbour towards k is exactly -r_{k,d}.
+#include <mutex>
+
 #include "opt_internal.cuh"
 #include "opt_launch.h"
 
@@ -32,7 +34,7 @@ namespace {
 __device__ __forceinline__ int dx4(int k) { return k == 0 ? 1 : (k == 1 ? -1 : 0); }
 __device__ __forceinline__ int dy4(int k) { return k == 2 ? 1 : (k == 3 ? -1 : 0); }
 
-__device__ __forceinline__ int tile_x0(int tc) { return (tc & 0xffff) * TW; }
+__device__ __forceinline__ int tile_x0(int tc, int tw) { return (tc & 0xffff) * tw; }
 __device__ __forceinline__ int tile_y0(int tc) { return (tc >> 16) * TH; }
 __device__ __forceinline__ int tile_id(const GridProb& pr, int tc) {
   return (tc >> 16) * pr.ntx + (tc & 0xffff);
@@ -71,9 +73,10 @@ __global__ void __launch_bounds__(NT) k_warp_init(const GridProb* __restrict__ p
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   float acc_rz = 0.f, acc_E = 0.f;
-  for (int t = ch.begin; t < ch.end; ++t) {
-    const int tc = tiles[t];
-    const int x0 = tile_x0(tc), y0 = tile_y0(tc);
+  const int nsub = pr.tw / TW;
+  for (int ts = ch.begin * nsub; ts < ch.end * nsub; ++ts) {
+    const int tc = tiles[ts / nsub];
+    const int x0 = tile_x0(tc, pr.tw) + TW * (ts % nsub), y0 = tile_y0(tc);
     for (int hc = threadIdx.x; hc < HW * HH; hc += NT) {
       const int hy = hc / HW, hx = hc - hy * HW;
       const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(NT) k_warp_init(const GridProb* __restrict__ p
       pr.m[i] = md; pr.m[pl + i] = mt;
       pr.d[i] = 0.f; pr.d[pl + i] = 0.f; pr.d[2 * pl + i] = 0.f;
       if (pr.lm) { pr.dc[i] = dcd; pr.dc[pl + i] = dct; }
+      if (pr.csn) { pr.csn[i] = ci; pr.csn[pl + i] = si; }
       if (pr.jtf_out) { pr.jtf_out[i] = gdx; pr.jtf_out[pl + i] = gdy; pr.jtf_out[2 * pl + i] = gt; }
       if (pr.diag_out) { pr.diag_out[i] = diag_d; pr.diag_out[pl + i] = diag_t; }
       acc_rz += md * (bx * bx + by * by) + mt * bt * bt;
@@ -283,10 +287,10 @@ __global__ void __launch_bounds__(NT, 3) k_warp_apply(const GridProb* __restrict
   float acc = 0.f;
   WarpCell A, B;
   int tc = tiles[ch.begin];
-  warp_cell_load(A, pr, pin, tile_x0(tc) + tx, tile_y0(tc) + ty, update, use_beta);
-  if (has_halo) warp_cell_load(B, pr, pin, tile_x0(tc) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
+  warp_cell_load(A, pr, pin, tile_x0(tc, 32) + tx, tile_y0(tc) + ty, update, use_beta);
+  if (has_halo) warp_cell_load(B, pr, pin, tile_x0(tc, 32) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
   for (int t = ch.begin; t < ch.end; ++t) {
-    const int x0 = tile_x0(tc), y0 = tile_y0(tc);
+    const int x0 = tile_x0(tc, 32), y0 = tile_y0(tc);
     const int gx = x0 + tx, gy = y0 + ty;
     const long long i = (long long)gy * P + gx;
     __syncthreads();
@@ -296,8 +300,8 @@ __global__ void __launch_bounds__(NT, 3) k_warp_apply(const GridProb* __restrict
     const int tcur = tc;
     if (t + 1 < ch.end) {
       tc = tiles[t + 1];
-      warp_cell_load(A, pr, pin, tile_x0(tc) + tx, tile_y0(tc) + ty, update, use_beta);
-      if (has_halo) warp_cell_load(B, pr, pin, tile_x0(tc) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
+      warp_cell_load(A, pr, pin, tile_x0(tc, 32) + tx, tile_y0(tc) + ty, update, use_beta);
+      if (has_halo) warp_cell_load(B, pr, pin, tile_x0(tc, 32) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
     }
     if (gx < W && gy < H) {
       const int lx = tx + 1, ly = ty + 1;
@@ -360,6 +364,639 @@ __global__ void __launch_bounds__(NT, 3) k_warp_apply(const GridProb* __restrict
   }
 }
 
+// ---------------------------------------------------------------------------
+// Wide-tile warp apply (tw = 128), staged with asynchronous copies.
+// Raw planes of the halo-extended tile (rows y0-1 .. y0+8, columns x0-1 ..
+// x0+128) are copied global -> shared with cp.async (16 bytes per thread per
+// plane for the quads, 4 bytes for the halo columns), so a whole tile is in
+// flight without occupying registers.  Phase 2 turns the raw planes into the
+// staged direction p = M^-1 r + beta p_old (and validity bits); once that is
+// done the raw buffer is free and the next tile's copies are issued, so they
+// overlap phase 3, the stencil (four pixels per thread, horizontal neighbours
+// by warp shuffles, vertical neighbours from shared memory).  For every valid
+// neighbour pair the own-residual and incoming-residual rows are summed in the
+// grouped form
+//   q_d,i += w [2 (p_i - p_j) + G_i p_t,i + G_j p_t,j],  q_t,i += w G_i . ((p_i - p_j) + G_i p_t,i)
+// with v = U_i - U_j and G_k = -R'(theta_k) v = (s_k v_x + c_k v_y, s_k v_y - c_k v_x).
+// ---------------------------------------------------------------------------
+constexpr int W4 = 128;          // wide tile width
+constexpr int SP = W4 + 8;       // staged row pitch (floats): columns -1..128 live at 3..132
+constexpr int SPB = W4 + 32;     // mask row pitch (bytes): columns 0..127 live at 16..143
+constexpr int NRAW = 12;         // r0 r1 r2 m0 m1 p0 p1 p2 cos sin ux uy
+constexpr int NSTG = 7;          // px py pt cos sin ux uy
+
+struct WideSmem {
+  float raw[NRAW][HH][SP];
+  float stg[NSTG][HH][SP];
+  unsigned int v[HH][SP / 4];    // validity bits of each staged quad (bit k = pixel k)
+  unsigned char mk[HH][SPB];
+  unsigned char vc[HH][2];       // validity of the halo columns -1 and 128
+};
+
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float4 mul4(float4 a, float4 b) {
+  return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+__device__ __forceinline__ float cmp(const float4& a, int k) {
+  return k == 0 ? a.x : (k == 1 ? a.y : (k == 2 ? a.z : a.w));
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;   // 0: the 16 destination bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+struct WidePlanes {
+  const float* src[NRAW];        // plane base pointers (nullptr: not needed this launch)
+};
+
+// Issues the copies of one tile: quads (own rows by every thread, the two
+// halo rows by threads 0..63) and the halo columns (threads 64..79).
+template <bool MASK>
+__device__ __forceinline__ void wide_issue(WideSmem& sm, const WidePlanes& pp, const GridProb& pr, int x0, int y0,
+                                           int tid) {
+  const int lane = tid & 31, ty = tid >> 5;
+  const int gx = x0 + 4 * lane;
+  // own row
+  {
+    const int gy = y0 + ty;
+    const bool ok = gy < pr.H;
+    const long long i = ok ? (long long)gy * pr.P + gx : 0;
+#pragma unroll
+    for (int k = 0; k < NRAW; ++k)
+      if (pp.src[k]) cp_async16(&sm.raw[k][ty + 1][4 + 4 * lane], pp.src[k] + i, ok);
+    if (MASK) cp_async4(&sm.mk[ty + 1][16 + 4 * lane], pr.mask + i, ok);
+  }
+  if (tid < 64) {
+    const int row = tid < 32 ? 0 : HH - 1;
+    const int gy = y0 - 1 + row;
+    const bool ok = gy >= 0 && gy < pr.H;
+    const long long i = ok ? (long long)gy * pr.P + gx : 0;
+#pragma unroll
+    for (int k = 0; k < NRAW; ++k)
+      if (pp.src[k]) cp_async16(&sm.raw[k][row][4 + 4 * lane], pp.src[k] + i, ok);
+    if (MASK) cp_async4(&sm.mk[row][16 + 4 * lane], pr.mask + i, ok);
+  } else if (tid < 64 + 2 * TH) {
+    const int h = tid - 64;
+    const int row = 1 + (h % TH), side = h / TH;
+    const int gy = y0 + row - 1, cx = side ? x0 + W4 : x0 - 1;
+    const bool ok = gy < pr.H && cx >= 0 && cx < pr.W;
+    const long long i = ok ? (long long)gy * pr.P + cx : 0;
+    const int col = side ? 4 + W4 : 3;
+#pragma unroll
+    for (int k = 0; k < NRAW; ++k)
+      if (pp.src[k]) cp_async4(&sm.raw[k][row][col], pp.src[k] + i, ok);
+  }
+  cp_async_commit();
+}
+
+// Phase 2 for one staged quad: direction, copied geometry, validity bits.
+template <bool MASK>
+__device__ __forceinline__ void wide_stage_quad(WideSmem& sm, int row, int lane, const GridProb& pr, int gx, int gy,
+                                                int update, int use_beta, float beta, float4* px, float4* py,
+                                                float4* pt) {
+  const int c = 4 + 4 * lane;
+  auto R = [&](int k) { return *reinterpret_cast<const float4*>(&sm.raw[k][row][c]); };
+  float4 a, b, t;
+  if (update) {
+    const float4 m0 = R(3), m1 = R(4);
+    a = mul4(m0, R(0));
+    b = mul4(m0, R(1));
+    t = mul4(m1, R(2));
+    if (use_beta) {
+      a = fma4(beta, R(5), a);
+      b = fma4(beta, R(6), b);
+      t = fma4(beta, R(7), t);
+    }
+  } else {
+    a = R(5); b = R(6); t = R(7);
+  }
+  *reinterpret_cast<float4*>(&sm.stg[0][row][c]) = a;
+  *reinterpret_cast<float4*>(&sm.stg[1][row][c]) = b;
+  *reinterpret_cast<float4*>(&sm.stg[2][row][c]) = t;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) *reinterpret_cast<float4*>(&sm.stg[3 + k][row][c]) = R(8 + k);
+  unsigned int v = 0u;
+  if (gy >= 0 && gy < pr.H) {
+    const unsigned int m4 = MASK ? *reinterpret_cast<const unsigned int*>(&sm.mk[row][16 + 4 * lane]) : 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (gx + k < pr.W && (!MASK || ((m4 >> (8 * k)) & 0xffu) == 0u)) v |= 1u << k;
+  }
+  sm.v[row][1 + lane] = v;
+  if (px) { *px = a; *py = b; *pt = t; }
+}
+
+// Adds the grouped own + incoming rows of the pair (i, j) to the accumulators.
+__device__ __forceinline__ void pair_terms(float pxi, float pyi, float pti, float ci, float si, float uxi,
+                                           float uyi, float pxj, float pyj, float ptj, float cj, float sj,
+                                           float uxj, float uyj, float& ax, float& ay, float& at) {
+  const float vx = uxi - uxj, vy = uyi - uyj;
+  const float a = pxi - pxj, b = pyi - pyj;
+  const float gix = fmaf(si, vx, ci * vy), giy = fmaf(si, vy, -ci * vx);
+  const float gjx = fmaf(sj, vx, cj * vy), gjy = fmaf(sj, vy, -cj * vx);
+  const float tx = fmaf(gix, pti, a), ty = fmaf(giy, pti, b);
+  ax += tx + fmaf(gjx, ptj, a);
+  ay += ty + fmaf(gjy, ptj, b);
+  at = fmaf(gix, tx, fmaf(giy, ty, at));
+}
+
+struct Quad7 {
+  float4 q[NSTG];
+  unsigned int v;
+};
+
+__device__ __forceinline__ void read_quad7(const WideSmem& sm, int row, int lane, Quad7& o) {
+  const int c = 4 + 4 * lane;
+#pragma unroll
+  for (int k = 0; k < NSTG; ++k) o.q[k] = *reinterpret_cast<const float4*>(&sm.stg[k][row][c]);
+  o.v = sm.v[row][1 + lane];
+}
+
+template <bool MASK>
+__global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __restrict__ probs,
+                                                           const Chunk* __restrict__ chunks,
+                                                           const int* __restrict__ tiles,
+                                                           double* __restrict__ part,
+                                                           const float* __restrict__ p_in_override,
+                                                           int par, int update) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  WideSmem& sm = *reinterpret_cast<WideSmem*>(dyn_smem);
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  Scalars* s = pr.s;
+  if (s->done || !s->pcg_active) return;
+  const int pl = (int)pr.plane;
+  const float w = pr.w_reg, wfit = pr.w_fit;
+  const float beta = s->beta_f;
+  const int use_beta = beta != 0.0f;
+  const float lam = pr.lm ? s->lambda_f : 0.0f;
+  const float* __restrict__ pin = p_in_override ? p_in_override : pr.p + (long long)(par & 1) * 3 * pl;
+  float* __restrict__ pout = pr.p + (long long)((par + 1) & 1) * 3 * pl;
+  WidePlanes pp;
+  pp.src[0] = update ? pr.r : nullptr;
+  pp.src[1] = update ? pr.r + pl : nullptr;
+  pp.src[2] = update ? pr.r + 2 * pl : nullptr;
+  pp.src[3] = update ? pr.m : nullptr;
+  pp.src[4] = update ? pr.m + pl : nullptr;
+  pp.src[5] = (!update || use_beta) ? pin : nullptr;
+  pp.src[6] = (!update || use_beta) ? pin + pl : nullptr;
+  pp.src[7] = (!update || use_beta) ? pin + 2 * pl : nullptr;
+  pp.src[8] = pr.csn;
+  pp.src[9] = pr.csn + pl;
+  pp.src[10] = pr.c;
+  pp.src[11] = pr.c + pl;
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  float acc = 0.f;
+  int tc = tiles[ch.begin];
+  wide_issue<MASK>(sm, pp, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+  for (int t = ch.begin; t < ch.end; ++t) {
+    const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
+    const int gx = x0 + 4 * lane, gy = y0 + ty;
+    const int tcur = tc;
+    cp_async_wait_all();
+    __syncthreads();
+    // phase 2: staged direction and geometry
+    float4 opx, opy, opt;
+    wide_stage_quad<MASK>(sm, ty + 1, lane, pr, gx, gy, update, use_beta, beta, &opx, &opy, &opt);
+    if (tid < 64) {
+      const int row = tid < 32 ? 0 : HH - 1;
+      wide_stage_quad<MASK>(sm, row, lane, pr, gx, y0 - 1 + row, update, use_beta, beta, nullptr, nullptr, nullptr);
+    } else if (tid < 64 + 2 * TH) {
+      const int h = tid - 64;
+      const int row = 1 + (h % TH), side = h / TH;
+      const int col = side ? 4 + W4 : 3;
+      float a, b, c;
+      if (update) {
+        a = sm.raw[3][row][col] * sm.raw[0][row][col];
+        b = sm.raw[3][row][col] * sm.raw[1][row][col];
+        c = sm.raw[4][row][col] * sm.raw[2][row][col];
+        if (use_beta) {
+          a = fmaf(beta, sm.raw[5][row][col], a);
+          b = fmaf(beta, sm.raw[6][row][col], b);
+          c = fmaf(beta, sm.raw[7][row][col], c);
+        }
+      } else {
+        a = sm.raw[5][row][col]; b = sm.raw[6][row][col]; c = sm.raw[7][row][col];
+      }
+      sm.stg[0][row][col] = a; sm.stg[1][row][col] = b; sm.stg[2][row][col] = c;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sm.stg[3 + k][row][col] = sm.raw[8 + k][row][col];
+      const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
+      const bool ok = hy < pr.H && hx >= 0 && hx < pr.W;
+      sm.vc[row][side] = (unsigned char)(ok && (!MASK || __ldg(pr.mask + (long long)hy * pr.P + hx) == 0));
+    }
+    __syncthreads();
+    // the raw buffer is free: start the next tile's copies
+    if (t + 1 < ch.end) {
+      tc = tiles[t + 1];
+      wide_issue<MASK>(sm, pp, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+    }
+    if (gy < pr.H) {                          // warp-uniform: one warp per row
+      const long long i = (long long)gy * pr.P + gx;
+      if (update) {
+        *reinterpret_cast<float4*>(pout + i) = opx;
+        *reinterpret_cast<float4*>(pout + pl + i) = opy;
+        *reinterpret_cast<float4*>(pout + 2 * pl + i) = opt;
+      }
+      Quad7 O;
+      read_quad7(sm, ty + 1, lane, O);
+      float L[NSTG], R[NSTG];
+#pragma unroll
+      for (int k = 0; k < NSTG; ++k) {
+        L[k] = __shfl_up_sync(0xffffffffu, O.q[k].w, 1);
+        R[k] = __shfl_down_sync(0xffffffffu, O.q[k].x, 1);
+      }
+      unsigned int lv = (__shfl_up_sync(0xffffffffu, O.v, 1) >> 3) & 1u;
+      unsigned int rv = __shfl_down_sync(0xffffffffu, O.v, 1) & 1u;
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NSTG; ++k) L[k] = sm.stg[k][ty + 1][3];
+        lv = sm.vc[ty + 1][0];
+      }
+      if (lane == 31) {
+#pragma unroll
+        for (int k = 0; k < NSTG; ++k) R[k] = sm.stg[k][ty + 1][4 + W4];
+        rv = sm.vc[ty + 1][1];
+      }
+      Quad7 Up, Dn;
+      read_quad7(sm, ty, lane, Up);
+      read_quad7(sm, ty + 2, lane, Dn);
+      float qx[4], qy[4], qt[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float ax = 0.f, ay = 0.f, at = 0.f;
+        const float pxi = cmp(O.q[0], k), pyi = cmp(O.q[1], k), pti = cmp(O.q[2], k);
+        const float ci = cmp(O.q[3], k), si = cmp(O.q[4], k), uxi = cmp(O.q[5], k), uyi = cmp(O.q[6], k);
+        if ((O.v >> k) & 1u) {
+          if (k == 0 ? lv : ((O.v >> (k - 1)) & 1u)) {
+            if (k == 0)
+              pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, L[0], L[1], L[2], L[3], L[4], L[5], L[6], ax, ay, at);
+            else
+              pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, cmp(O.q[0], k - 1), cmp(O.q[1], k - 1), cmp(O.q[2], k - 1),
+                         cmp(O.q[3], k - 1), cmp(O.q[4], k - 1), cmp(O.q[5], k - 1), cmp(O.q[6], k - 1), ax, ay, at);
+          }
+          if (k == 3 ? rv : ((O.v >> (k + 1)) & 1u)) {
+            if (k == 3)
+              pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, R[0], R[1], R[2], R[3], R[4], R[5], R[6], ax, ay, at);
+            else
+              pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, cmp(O.q[0], k + 1), cmp(O.q[1], k + 1), cmp(O.q[2], k + 1),
+                         cmp(O.q[3], k + 1), cmp(O.q[4], k + 1), cmp(O.q[5], k + 1), cmp(O.q[6], k + 1), ax, ay, at);
+          }
+          if ((Up.v >> k) & 1u)
+            pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, cmp(Up.q[0], k), cmp(Up.q[1], k), cmp(Up.q[2], k),
+                       cmp(Up.q[3], k), cmp(Up.q[4], k), cmp(Up.q[5], k), cmp(Up.q[6], k), ax, ay, at);
+          if ((Dn.v >> k) & 1u)
+            pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, cmp(Dn.q[0], k), cmp(Dn.q[1], k), cmp(Dn.q[2], k),
+                       cmp(Dn.q[3], k), cmp(Dn.q[4], k), cmp(Dn.q[5], k), cmp(Dn.q[6], k), ax, ay, at);
+        }
+        qx[k] = w * ax;
+        qy[k] = w * ay;
+        qt[k] = w * at;
+      }
+      const int tid_ = tile_id(pr, tcur);
+      for (int h = pr.hbeg[tid_]; h < pr.hbeg[tid_ + 1]; ++h) {
+        const long long k = pr.hpix[h] - i;
+        if (k >= 0 && k < 4 && ((O.v >> k) & 1u)) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            if (kk == k) { qx[kk] += wfit * cmp(O.q[0], kk); qy[kk] += wfit * cmp(O.q[1], kk); }
+        }
+      }
+      if (pr.lm) {
+        const float4 dd = ld4(pr.dc + i), dt = ld4(pr.dc + pl + i);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (!((O.v >> k) & 1u)) continue;
+          qx[k] += lam * cmp(dd, k) * cmp(O.q[0], k);
+          qy[k] += lam * cmp(dd, k) * cmp(O.q[1], k);
+          qt[k] += lam * cmp(dt, k) * cmp(O.q[2], k);
+        }
+      }
+      *reinterpret_cast<float4*>(pr.q + i) = make_float4(qx[0], qx[1], qx[2], qx[3]);
+      *reinterpret_cast<float4*>(pr.q + pl + i) = make_float4(qy[0], qy[1], qy[2], qy[3]);
+      *reinterpret_cast<float4*>(pr.q + 2 * pl + i) = make_float4(qt[0], qt[1], qt[2], qt[3]);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        acc += cmp(O.q[0], k) * qx[k] + cmp(O.q[1], k) * qy[k] + cmp(O.q[2], k) * qt[k];
+    }
+  }
+  cp_async_wait_all();
+  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+    double pq, unused;
+    gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, pq, unused);
+    if (threadIdx.x == 0) {
+      s->pq = pq;
+      if (pq > 0.0 && isfinite(pq)) {
+        s->alpha_f = (float)(s->rz / pq);
+      } else {
+        s->alpha_f = 0.f;
+        s->pcg_active = 0;
+        if (!isfinite(pq)) s->nonfinite = 1;
+      }
+    }
+  }
+}
+
+// Wide-tile warp PCGInit (tw = 128), staged with asynchronous copies like the
+// wide apply: raw planes (dx, dy, theta, UrShape) of the halo-extended tile are
+// copied global -> shared, phase 2 evaluates cos / sin of theta once per staged
+// pixel, then the next tile's copies overlap phase 3.  Per valid neighbour
+// pair (i, j), with a = d_i - d_j, v = U_i - U_j, e_k = v - R(theta_k) v and
+// G_i = -R'(theta_i) v:
+//   own residual       r_(i,j) =  s_w (a + e_i)
+//   incoming residual  r_(j,i) = -s_w (a + e_j)
+//   J^T F (d rows)  += w (2 a + e_i + e_j),   J^T F (theta row) += w G_i . (a + e_i)
+//   diag (d rows)   += 2 w,                   diag (theta row)  += w |G_i|^2
+//   E               += w |a + e_i|^2   (own residuals only)
+// Writes r = b = -J^T F, M^-1, delta = 0, the LM diagonal, cos / sin of theta.
+constexpr int NRAW_I = 5;        // dx dy theta ux uy
+constexpr int NSTG_I = 6;        // dx dy cos sin ux uy
+
+struct InitSmem {
+  float raw[NRAW_I][HH][SP];
+  float stg[NSTG_I][HH][SP];
+  unsigned int v[HH][SP / 4];
+  unsigned char mk[HH][SPB];
+  unsigned char vc[HH][2];
+};
+
+template <bool MASK>
+__device__ __forceinline__ void init_issue(InitSmem& sm, const GridProb& pr, int x0, int y0, int tid) {
+  const int lane = tid & 31, ty = tid >> 5;
+  const int gx = x0 + 4 * lane;
+  const int pl = (int)pr.plane;
+  const float* src[NRAW_I] = {pr.x, pr.x + pl, pr.x + 2 * pl, pr.c, pr.c + pl};
+  {
+    const int gy = y0 + ty;
+    const bool ok = gy < pr.H;
+    const long long i = ok ? (long long)gy * pr.P + gx : 0;
+#pragma unroll
+    for (int k = 0; k < NRAW_I; ++k) cp_async16(&sm.raw[k][ty + 1][4 + 4 * lane], src[k] + i, ok);
+    if (MASK) cp_async4(&sm.mk[ty + 1][16 + 4 * lane], pr.mask + i, ok);
+  }
+  if (tid < 64) {
+    const int row = tid < 32 ? 0 : HH - 1;
+    const int gy = y0 - 1 + row;
+    const bool ok = gy >= 0 && gy < pr.H;
+    const long long i = ok ? (long long)gy * pr.P + gx : 0;
+#pragma unroll
+    for (int k = 0; k < NRAW_I; ++k) cp_async16(&sm.raw[k][row][4 + 4 * lane], src[k] + i, ok);
+    if (MASK) cp_async4(&sm.mk[row][16 + 4 * lane], pr.mask + i, ok);
+  } else if (tid < 64 + 2 * TH) {
+    const int h = tid - 64;
+    const int row = 1 + (h % TH), side = h / TH;
+    const int gy = y0 + row - 1, cx = side ? x0 + W4 : x0 - 1;
+    const bool ok = gy < pr.H && cx >= 0 && cx < pr.W;
+    const long long i = ok ? (long long)gy * pr.P + cx : 0;
+    const int col = side ? 4 + W4 : 3;
+#pragma unroll
+    for (int k = 0; k < NRAW_I; ++k) cp_async4(&sm.raw[k][row][col], src[k] + i, ok);
+  }
+  cp_async_commit();
+}
+
+// Phase 2 for one staged quad: cos / sin, copied values, validity bits.
+template <bool MASK>
+__device__ __forceinline__ void init_stage_quad(InitSmem& sm, int row, int lane, const GridProb& pr, int gx, int gy) {
+  const int c = 4 + 4 * lane;
+  const float4 th = *reinterpret_cast<const float4*>(&sm.raw[2][row][c]);
+  float4 cs, sn;
+  sincosf(th.x, &sn.x, &cs.x);
+  sincosf(th.y, &sn.y, &cs.y);
+  sincosf(th.z, &sn.z, &cs.z);
+  sincosf(th.w, &sn.w, &cs.w);
+  *reinterpret_cast<float4*>(&sm.stg[0][row][c]) = *reinterpret_cast<const float4*>(&sm.raw[0][row][c]);
+  *reinterpret_cast<float4*>(&sm.stg[1][row][c]) = *reinterpret_cast<const float4*>(&sm.raw[1][row][c]);
+  *reinterpret_cast<float4*>(&sm.stg[2][row][c]) = cs;
+  *reinterpret_cast<float4*>(&sm.stg[3][row][c]) = sn;
+  *reinterpret_cast<float4*>(&sm.stg[4][row][c]) = *reinterpret_cast<const float4*>(&sm.raw[3][row][c]);
+  *reinterpret_cast<float4*>(&sm.stg[5][row][c]) = *reinterpret_cast<const float4*>(&sm.raw[4][row][c]);
+  unsigned int v = 0u;
+  if (gy >= 0 && gy < pr.H) {
+    const unsigned int m4 = MASK ? *reinterpret_cast<const unsigned int*>(&sm.mk[row][16 + 4 * lane]) : 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (gx + k < pr.W && (!MASK || ((m4 >> (8 * k)) & 0xffu) == 0u)) v |= 1u << k;
+  }
+  sm.v[row][1 + lane] = v;
+}
+
+// Grouped J^T F / diag / energy terms of the pair (i, j).
+__device__ __forceinline__ void init_pair(float dxi, float dyi, float ci, float si, float uxi, float uyi, float dxj,
+                                          float dyj, float cj, float sj, float uxj, float uyj, float& gx, float& gy,
+                                          float& gt, float& dt, float& e, float& npair) {
+  const float vx = uxi - uxj, vy = uyi - uyj;
+  const float ax = dxi - dxj, ay = dyi - dyj;
+  // e_k = v - R(theta_k) v
+  const float eix = vx - fmaf(ci, vx, -si * vy), eiy = vy - fmaf(si, vx, ci * vy);
+  const float ejx = vx - fmaf(cj, vx, -sj * vy), ejy = vy - fmaf(sj, vx, cj * vy);
+  const float gix = fmaf(si, vx, ci * vy), giy = fmaf(si, vy, -ci * vx);
+  const float ox = ax + eix, oy = ay + eiy;       // own residual / s_w
+  gx += ox + (ax + ejx);
+  gy += oy + (ay + ejy);
+  gt = fmaf(gix, ox, fmaf(giy, oy, gt));
+  dt = fmaf(gix, gix, fmaf(giy, giy, dt));
+  e = fmaf(ox, ox, fmaf(oy, oy, e));
+  npair += 1.f;
+}
+
+struct Quad6 {
+  float4 q[NSTG_I];
+  unsigned int v;
+};
+
+__device__ __forceinline__ void read_quad6(const InitSmem& sm, int row, int lane, Quad6& o) {
+  const int c = 4 + 4 * lane;
+#pragma unroll
+  for (int k = 0; k < NSTG_I; ++k) o.q[k] = *reinterpret_cast<const float4*>(&sm.stg[k][row][c]);
+  o.v = sm.v[row][1 + lane];
+}
+
+template <bool MASK>
+__global__ void __launch_bounds__(NT, 2) k_warp_init_wide(const GridProb* __restrict__ probs,
+                                                          const Chunk* __restrict__ chunks,
+                                                          const int* __restrict__ tiles,
+                                                          double* __restrict__ part, int k_outer,
+                                                          float dmin, float dmax) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  InitSmem& sm = *reinterpret_cast<InitSmem*>(dyn_smem);
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  Scalars* s = pr.s;
+  if (s->done) return;
+  const int pl = (int)pr.plane;
+  const float w = pr.w_reg, wfit = pr.w_fit;
+  const float lam = pr.lm ? s->lambda_f : 0.0f;
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  float acc_rz = 0.f, acc_E = 0.f;
+  int tc = tiles[ch.begin];
+  init_issue<MASK>(sm, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+  for (int t = ch.begin; t < ch.end; ++t) {
+    const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
+    const int gx = x0 + 4 * lane, gy = y0 + ty;
+    const int tcur = tc;
+    cp_async_wait_all();
+    __syncthreads();
+    init_stage_quad<MASK>(sm, ty + 1, lane, pr, gx, gy);
+    if (tid < 64) {
+      const int row = tid < 32 ? 0 : HH - 1;
+      init_stage_quad<MASK>(sm, row, lane, pr, gx, y0 - 1 + row);
+    } else if (tid < 64 + 2 * TH) {
+      const int h = tid - 64;
+      const int row = 1 + (h % TH), side = h / TH;
+      const int col = side ? 4 + W4 : 3;
+      float sn, cs;
+      sincosf(sm.raw[2][row][col], &sn, &cs);
+      sm.stg[0][row][col] = sm.raw[0][row][col];
+      sm.stg[1][row][col] = sm.raw[1][row][col];
+      sm.stg[2][row][col] = cs;
+      sm.stg[3][row][col] = sn;
+      sm.stg[4][row][col] = sm.raw[3][row][col];
+      sm.stg[5][row][col] = sm.raw[4][row][col];
+      const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
+      const bool ok = hy < pr.H && hx >= 0 && hx < pr.W;
+      sm.vc[row][side] = (unsigned char)(ok && (!MASK || __ldg(pr.mask + (long long)hy * pr.P + hx) == 0));
+    }
+    __syncthreads();
+    if (t + 1 < ch.end) {
+      tc = tiles[t + 1];
+      init_issue<MASK>(sm, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+    }
+    if (gy < pr.H) {
+      Quad6 O;
+      read_quad6(sm, ty + 1, lane, O);
+      float L[NSTG_I], R[NSTG_I];
+#pragma unroll
+      for (int k = 0; k < NSTG_I; ++k) {
+        L[k] = __shfl_up_sync(0xffffffffu, O.q[k].w, 1);
+        R[k] = __shfl_down_sync(0xffffffffu, O.q[k].x, 1);
+      }
+      unsigned int lv = (__shfl_up_sync(0xffffffffu, O.v, 1) >> 3) & 1u;
+      unsigned int rv = __shfl_down_sync(0xffffffffu, O.v, 1) & 1u;
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NSTG_I; ++k) L[k] = sm.stg[k][ty + 1][3];
+        lv = sm.vc[ty + 1][0];
+      }
+      if (lane == 31) {
+#pragma unroll
+        for (int k = 0; k < NSTG_I; ++k) R[k] = sm.stg[k][ty + 1][4 + W4];
+        rv = sm.vc[ty + 1][1];
+      }
+      Quad6 Up, Dn;
+      read_quad6(sm, ty, lane, Up);
+      read_quad6(sm, ty + 2, lane, Dn);
+      float gxv[4], gyv[4], gtv[4], ddv[4], dtv[4], ev[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float gxx = 0.f, gyy = 0.f, gt = 0.f, dt = 0.f, e = 0.f, np = 0.f;
+        const float dxi = cmp(O.q[0], k), dyi = cmp(O.q[1], k), ci = cmp(O.q[2], k), si = cmp(O.q[3], k);
+        const float uxi = cmp(O.q[4], k), uyi = cmp(O.q[5], k);
+        if ((O.v >> k) & 1u) {
+          if (k == 0 ? lv : ((O.v >> (k - 1)) & 1u)) {
+            if (k == 0) init_pair(dxi, dyi, ci, si, uxi, uyi, L[0], L[1], L[2], L[3], L[4], L[5], gxx, gyy, gt, dt, e, np);
+            else init_pair(dxi, dyi, ci, si, uxi, uyi, cmp(O.q[0], k - 1), cmp(O.q[1], k - 1), cmp(O.q[2], k - 1),
+                           cmp(O.q[3], k - 1), cmp(O.q[4], k - 1), cmp(O.q[5], k - 1), gxx, gyy, gt, dt, e, np);
+          }
+          if (k == 3 ? rv : ((O.v >> (k + 1)) & 1u)) {
+            if (k == 3) init_pair(dxi, dyi, ci, si, uxi, uyi, R[0], R[1], R[2], R[3], R[4], R[5], gxx, gyy, gt, dt, e, np);
+            else init_pair(dxi, dyi, ci, si, uxi, uyi, cmp(O.q[0], k + 1), cmp(O.q[1], k + 1), cmp(O.q[2], k + 1),
+                           cmp(O.q[3], k + 1), cmp(O.q[4], k + 1), cmp(O.q[5], k + 1), gxx, gyy, gt, dt, e, np);
+          }
+          if ((Up.v >> k) & 1u)
+            init_pair(dxi, dyi, ci, si, uxi, uyi, cmp(Up.q[0], k), cmp(Up.q[1], k), cmp(Up.q[2], k), cmp(Up.q[3], k),
+                      cmp(Up.q[4], k), cmp(Up.q[5], k), gxx, gyy, gt, dt, e, np);
+          if ((Dn.v >> k) & 1u)
+            init_pair(dxi, dyi, ci, si, uxi, uyi, cmp(Dn.q[0], k), cmp(Dn.q[1], k), cmp(Dn.q[2], k), cmp(Dn.q[3], k),
+                      cmp(Dn.q[4], k), cmp(Dn.q[5], k), gxx, gyy, gt, dt, e, np);
+        }
+        gxv[k] = w * gxx;
+        gyv[k] = w * gyy;
+        gtv[k] = w * gt;
+        ddv[k] = 2.f * w * np;
+        dtv[k] = w * dt;
+        ev[k] = w * e;
+      }
+      const long long i = (long long)gy * pr.P + gx;
+      const int tid_ = tile_id(pr, tcur);
+      for (int h = pr.hbeg[tid_]; h < pr.hbeg[tid_ + 1]; ++h) {
+        const long long k = pr.hpix[h] - i;
+        if (k >= 0 && k < 4 && ((O.v >> k) & 1u)) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            if (kk == k) {
+              const float rx = cmp(O.q[0], kk) - pr.htgt[2 * h], ry = cmp(O.q[1], kk) - pr.htgt[2 * h + 1];
+              gxv[kk] += wfit * rx;
+              gyv[kk] += wfit * ry;
+              ddv[kk] += wfit;
+              ev[kk] += wfit * (rx * rx + ry * ry);
+            }
+        }
+      }
+      float md[4], mt[4], cd[4], ct[4], bx[4], by[4], bt[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        md[k] = minv_entry(ddv[k], lam, dmin, dmax, pr.use_precond, &cd[k]);
+        mt[k] = minv_entry(dtv[k], lam, dmin, dmax, pr.use_precond, &ct[k]);
+        bx[k] = -gxv[k];
+        by[k] = -gyv[k];
+        bt[k] = -gtv[k];
+        acc_rz += md[k] * (bx[k] * bx[k] + by[k] * by[k]) + mt[k] * bt[k] * bt[k];
+        acc_E += ev[k];
+      }
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(pr.r + i) = make_float4(bx[0], bx[1], bx[2], bx[3]);
+      *reinterpret_cast<float4*>(pr.r + pl + i) = make_float4(by[0], by[1], by[2], by[3]);
+      *reinterpret_cast<float4*>(pr.r + 2 * pl + i) = make_float4(bt[0], bt[1], bt[2], bt[3]);
+      *reinterpret_cast<float4*>(pr.m + i) = make_float4(md[0], md[1], md[2], md[3]);
+      *reinterpret_cast<float4*>(pr.m + pl + i) = make_float4(mt[0], mt[1], mt[2], mt[3]);
+      *reinterpret_cast<float4*>(pr.d + i) = z;
+      *reinterpret_cast<float4*>(pr.d + pl + i) = z;
+      *reinterpret_cast<float4*>(pr.d + 2 * pl + i) = z;
+      *reinterpret_cast<float4*>(pr.csn + i) = O.q[2];
+      *reinterpret_cast<float4*>(pr.csn + pl + i) = O.q[3];
+      if (pr.lm) {
+        *reinterpret_cast<float4*>(pr.dc + i) = make_float4(cd[0], cd[1], cd[2], cd[3]);
+        *reinterpret_cast<float4*>(pr.dc + pl + i) = make_float4(ct[0], ct[1], ct[2], ct[3]);
+      }
+      if (pr.jtf_out) {
+        *reinterpret_cast<float4*>(pr.jtf_out + i) = make_float4(gxv[0], gxv[1], gxv[2], gxv[3]);
+        *reinterpret_cast<float4*>(pr.jtf_out + pl + i) = make_float4(gyv[0], gyv[1], gyv[2], gyv[3]);
+        *reinterpret_cast<float4*>(pr.jtf_out + 2 * pl + i) = make_float4(gtv[0], gtv[1], gtv[2], gtv[3]);
+      }
+      if (pr.diag_out) {
+        *reinterpret_cast<float4*>(pr.diag_out + i) = make_float4(ddv[0], ddv[1], ddv[2], ddv[3]);
+        *reinterpret_cast<float4*>(pr.diag_out + pl + i) = make_float4(dtv[0], dtv[1], dtv[2], dtv[3]);
+      }
+    }
+  }
+  cp_async_wait_all();
+  if (publish_partials(part, blockIdx.x, acc_rz, acc_E, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+    double rz, E;
+    gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, rz, E);
+    if (threadIdx.x == 0) {
+      s->rz = rz;
+      s->E = E;
+      if (pr.Ehist && k_outer >= 0) pr.Ehist[k_outer] = E;
+      s->beta_f = 0.f;
+      s->pcg_active = (rz != 0.0) && isfinite(rz);
+      if (!isfinite(rz) || !isfinite(E)) s->nonfinite = 1;
+    }
+  }
+}
+
 // E(x) (mode 0) or E(x + delta) and |F(x) + J(x) delta|^2 (mode 1).
 __global__ void __launch_bounds__(NT) k_warp_energy(const GridProb* __restrict__ probs,
                                                     const Chunk* __restrict__ chunks,
@@ -376,9 +1013,10 @@ __global__ void __launch_bounds__(NT) k_warp_energy(const GridProb* __restrict__
   const float sw = pr.s_w, sf = pr.s_f;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   float acc0 = 0.f, acc1 = 0.f;
-  for (int t = ch.begin; t < ch.end; ++t) {
-    const int tc = tiles[t];
-    const int x0 = tile_x0(tc), y0 = tile_y0(tc);
+  const int nsub = pr.tw / TW;
+  for (int ts = ch.begin * nsub; ts < ch.end * nsub; ++ts) {
+    const int tc = tiles[ts / nsub];
+    const int x0 = tile_x0(tc, pr.tw) + TW * (ts % nsub), y0 = tile_y0(tc);
     for (int hc = threadIdx.x; hc < HW * HH; hc += NT) {
       const int hy = hc / HW, hx = hc - hy * HW;
       const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
@@ -496,9 +1134,10 @@ __global__ void __launch_bounds__(NT) k_poisson_init(const GridProb* __restrict_
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   float acc_rz = 0.f, acc_E = 0.f;
-  for (int t = ch.begin; t < ch.end; ++t) {
-    const int tc = tiles[t];
-    const int x0 = tile_x0(tc), y0 = tile_y0(tc);
+  const int nsub = pr.tw / TW;
+  for (int ts = ch.begin * nsub; ts < ch.end * nsub; ++ts) {
+    const int tc = tiles[ts / nsub];
+    const int x0 = tile_x0(tc, pr.tw) + TW * (ts % nsub), y0 = tile_y0(tc);
     for (int hc = threadIdx.x; hc < HW * HH; hc += NT) {
       const int hy = hc / HW, hx = hc - hy * HW;
       const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
@@ -648,10 +1287,10 @@ __global__ void __launch_bounds__(NT, 3) k_poisson_apply(const GridProb* __restr
   float acc = 0.f;
   PoisCell A, B;
   int tc = tiles[ch.begin];
-  pois_cell_load(A, pr, pin, tile_x0(tc) + tx, tile_y0(tc) + ty, update, use_beta);
-  if (has_halo) pois_cell_load(B, pr, pin, tile_x0(tc) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
+  pois_cell_load(A, pr, pin, tile_x0(tc, 32) + tx, tile_y0(tc) + ty, update, use_beta);
+  if (has_halo) pois_cell_load(B, pr, pin, tile_x0(tc, 32) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
   for (int t = ch.begin; t < ch.end; ++t) {
-    const int x0 = tile_x0(tc), y0 = tile_y0(tc);
+    const int x0 = tile_x0(tc, 32), y0 = tile_y0(tc);
     const int gx = x0 + tx, gy = y0 + ty;
     const long long i = (long long)gy * P + gx;
     __syncthreads();
@@ -660,8 +1299,8 @@ __global__ void __launch_bounds__(NT, 3) k_poisson_apply(const GridProb* __restr
     __syncthreads();
     if (t + 1 < ch.end) {
       tc = tiles[t + 1];
-      pois_cell_load(A, pr, pin, tile_x0(tc) + tx, tile_y0(tc) + ty, update, use_beta);
-      if (has_halo) pois_cell_load(B, pr, pin, tile_x0(tc) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
+      pois_cell_load(A, pr, pin, tile_x0(tc, 32) + tx, tile_y0(tc) + ty, update, use_beta);
+      if (has_halo) pois_cell_load(B, pr, pin, tile_x0(tc, 32) - 1 + hhx, tile_y0(tc) - 1 + hhy, update, use_beta);
     }
     if (gx < W && gy < H) {
       const int lx = tx + 1, ly = ty + 1;
@@ -719,9 +1358,10 @@ __global__ void __launch_bounds__(NT) k_poisson_energy(const GridProb* __restric
   const int P = pr.P, W = pr.W, H = pr.H;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   float acc0 = 0.f, acc1 = 0.f;
-  for (int t = ch.begin; t < ch.end; ++t) {
-    const int tc = tiles[t];
-    const int x0 = tile_x0(tc), y0 = tile_y0(tc);
+  const int nsub = pr.tw / TW;
+  for (int ts = ch.begin * nsub; ts < ch.end * nsub; ++ts) {
+    const int tc = tiles[ts / nsub];
+    const int x0 = tile_x0(tc, pr.tw) + TW * (ts % nsub), y0 = tile_y0(tc);
     for (int hc = threadIdx.x; hc < HW * HH; hc += NT) {
       const int hy = hc / HW, hx = hc - hy * HW;
       const int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
@@ -792,7 +1432,6 @@ __global__ void __launch_bounds__(NT) k_grid_update(const GridProb* __restrict__
                                                     const int* __restrict__ tiles,
                                                     double* __restrict__ part, int par) {
   constexpr int NM = NX == 3 ? 2 : 1;
-  constexpr int QPT = TW / 4 * TH;   // float4 quads per tile
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -806,13 +1445,15 @@ __global__ void __launch_bounds__(NT) k_grid_update(const GridProb* __restrict__
   float4* __restrict__ d4 = reinterpret_cast<float4*>(pr.d);
   float4* __restrict__ r4 = reinterpret_cast<float4*>(pr.r);
   float acc = 0.f;
+  const int qrow = pr.tw / 4;        // float4 quads per tile row
+  const int QPT = qrow * TH;         // float4 quads per tile
   const int nq = (ch.end - ch.begin) * QPT;
   for (int k = threadIdx.x; k < nq; k += NT) {
     const int tc = tiles[ch.begin + k / QPT];
     const int w = k % QPT;
-    const int y = tile_y0(tc) + w / (TW / 4);
+    const int y = tile_y0(tc) + w / qrow;
     if (y >= pr.H) continue;
-    const long long j = (long long)y * P4 + tile_x0(tc) / 4 + w % (TW / 4);
+    const long long j = (long long)y * P4 + tile_x0(tc, pr.tw) / 4 + w % qrow;
     float4 pv[NX], qv[NX], dv[NX], rv[NX], mv[NM];
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
@@ -864,11 +1505,14 @@ __global__ void __launch_bounds__(NT) k_grid_step(const GridProb* __restrict__ p
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int t = ch.begin; t < ch.end; ++t) {
     const int tc = tiles[t];
-    const int gx = tile_x0(tc) + tx, gy = tile_y0(tc) + ty;
-    if (gx >= pr.W || gy >= pr.H) continue;
-    const long long i = (long long)gy * pr.P + gx;
+    const int gy = tile_y0(tc) + ty;
+    for (int sx = tx; sx < pr.tw; sx += TW) {
+      const int gx = tile_x0(tc, pr.tw) + sx;
+      if (gx >= pr.W || gy >= pr.H) continue;
+      const long long i = (long long)gy * pr.P + gx;
 #pragma unroll
-    for (int c = 0; c < NX; ++c) pr.x[c * pl + i] += pr.d[c * pl + i];
+      for (int c = 0; c < NX; ++c) pr.x[c * pl + i] += pr.d[c * pl + i];
+    }
   }
 }
 
@@ -877,15 +1521,53 @@ __global__ void __launch_bounds__(NT) k_grid_step(const GridProb* __restrict__ p
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+cudaError_t grid_kernels_prepare() {
+  static cudaError_t status = cudaErrorNotReady;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const int bytes = (int)sizeof(WideSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_warp_apply_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_apply_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_apply_wide<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_apply_wide<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    const int ibytes = (int)sizeof(InitSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_init_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ibytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_init_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ibytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_init_wide<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_init_wide<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    status = e;
+  });
+  return status;
+}
+
 void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, float dmax) {
-  if (kind == K_WARP)
+  if (kind == K_WARP && L.tw == 128 && L.masked)
+    k_warp_init_wide<true><<<L.nchunks, NT, sizeof(InitSmem), L.stream>>>(L.probs, L.chunks, L.tiles, L.part, k_outer,
+                                                                        dmin, dmax);
+  else if (kind == K_WARP && L.tw == 128)
+    k_warp_init_wide<false><<<L.nchunks, NT, sizeof(InitSmem), L.stream>>>(L.probs, L.chunks, L.tiles, L.part,
+                                                                         k_outer, dmin, dmax);
+  else if (kind == K_WARP)
     k_warp_init<<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
   else
     k_poisson_init<<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
 }
 
 void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, int par, int update) {
-  if (kind == K_WARP)
+  if (kind == K_WARP && L.tw == 128 && L.masked)
+    k_warp_apply_wide<true><<<L.nchunks, NT, sizeof(WideSmem), L.stream>>>(L.probs, L.chunks, L.tiles, L.part,
+                                                                         p_override, par, update);
+  else if (kind == K_WARP && L.tw == 128)
+    k_warp_apply_wide<false><<<L.nchunks, NT, sizeof(WideSmem), L.stream>>>(L.probs, L.chunks, L.tiles, L.part,
+                                                                          p_override, par, update);
+  else if (kind == K_WARP)
     k_warp_apply<<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, p_override, par, update);
   else
     k_poisson_apply<<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, p_override, par, update);

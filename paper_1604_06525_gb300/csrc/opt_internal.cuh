@@ -1,8 +1,10 @@
 // Internal definitions shared by the CUDA translation units of the solver.
 //
 // Data layout in HBM (struct of arrays, float32):
-//  * grid problems keep every plane pitched: row pitch P = W rounded up to 32
-//    floats (128 B), plane stride P*H; tiles are TW x TH = 32 x 8 pixels;
+//  * grid problems keep every plane pitched: row pitch P = W rounded up to the
+//    tile width (32 or 128 floats), plane stride P*H; tiles are tw x TH pixels
+//    (tw = 32, or 128 for wide warps); the 32-wide kernels walk a 128-wide
+//    tile as four 32 x 8 sub-tiles;
 //  * graph problems keep vertex planes of stride Vp = V rounded up to 32;
 //  * the PCG vectors delta, r, p, q have one plane per unknown component; the
 //    inverse Jacobi preconditioner M^-1 (and the LM damping diagonal D) keep
@@ -71,6 +73,7 @@ struct Chunk {
 // Grid problem (image warping, Poisson).  Pointers are device pointers.
 struct GridProb {
   int kind, W, H, P;
+  int tw;                       // tile width: 32 or 128 pixels (tiles are tw x TH)
   int ntx, nty;                 // tiles per row / column
   long long plane;              // P * H
   int chunk_begin, chunk_end;   // this problem's chunks (for the final reduction)
@@ -81,6 +84,7 @@ struct GridProb {
   const uint8_t* mask;          // pitched mask, NULL = none
   float *d, *r, *p, *q;         // PCG vectors
   float *m, *dc;                // M^-1 and LM diagonal (distinct-diagonal planes)
+  float* csn;                   // warp, tw = 128: cos / sin of theta (2 planes, written by PCGInit)
   const int* hbeg;              // per tile id: first handle (ntx*nty + 1 entries)
   const int* hpix;              // handle pixel index y*P + x, sorted by tile
   const float* htgt;            // handle target displacement (2 per handle)
@@ -105,6 +109,7 @@ struct MeshProb {
   float *d, *r, *p, *q;         // 6 planes each
   float *m, *dc;                // 4 planes: displacement, ax, ay, az
   float* acc;                   // 3 planes: angle-diagonal accumulators (PCGInit)
+  float* csn;                   // 6 planes: cos ax, sin ax, cos ay, sin ay, cos az, sin az (PCGInit)
   const int* hbeg;              // per vertex tile: first handle
   const int* hpix;              // handle vertex, sorted
   const float* htgt;            // 3 per handle
@@ -164,6 +169,7 @@ __device__ __forceinline__ void gather_partials(const double* part, int cb, int 
   __threadfence();
   a = 0.0;
   b = 0.0;
+#pragma unroll 4
   for (int c = cb + (int)threadIdx.x; c < ce; c += NT) {
     a += __ldcg(&part[2 * c]);
     b += __ldcg(&part[2 * c + 1]);
@@ -221,6 +227,30 @@ __device__ __forceinline__ RotV rot_apply(float ax, float ay, float az, float vx
   o.g[1][1] = sc * yb0;
   o.g[1][2] = yb2;
   // dR/daz v = dRz Ry Rx v = dRz y
+  o.g[2][0] = -sc * y0 - cc * y1;
+  o.g[2][1] = cc * y0 - sc * y1;
+  o.g[2][2] = 0.f;
+  return o;
+}
+
+// Same as rot_apply with the angles' cos / sin given.
+__device__ __forceinline__ RotV rot_apply_cs(float ca, float sa, float cb, float sb, float cc, float sc, float vx,
+                                             float vy, float vz) {
+  const float w0 = vx, w1 = ca * vy - sa * vz, w2 = sa * vy + ca * vz;
+  const float wd1 = -sa * vy - ca * vz, wd2 = ca * vy - sa * vz;
+  const float y0 = cb * w0 + sb * w2, y1 = w1, y2 = -sb * w0 + cb * w2;
+  const float yb0 = -sb * w0 + cb * w2, yb2 = -cb * w0 - sb * w2;
+  const float ya0 = sb * wd2, ya1 = wd1, ya2 = cb * wd2;
+  RotV o;
+  o.rv[0] = cc * y0 - sc * y1;
+  o.rv[1] = sc * y0 + cc * y1;
+  o.rv[2] = y2;
+  o.g[0][0] = cc * ya0 - sc * ya1;
+  o.g[0][1] = sc * ya0 + cc * ya1;
+  o.g[0][2] = ya2;
+  o.g[1][0] = cc * yb0;
+  o.g[1][1] = sc * yb0;
+  o.g[1][2] = yb2;
   o.g[2][0] = -sc * y0 - cc * y1;
   o.g[2][1] = cc * y0 - sc * y1;
   o.g[2][2] = 0.f;

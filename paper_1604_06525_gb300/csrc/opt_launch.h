@@ -12,6 +12,8 @@ struct GridLaunch {
   double* part;
   int nchunks;
   cudaStream_t stream;
+  int tw;        // tile width of every problem in the launch (32 or 128)
+  int masked;    // every problem in the launch has a mask (wide warp kernel variant)
 };
 
 struct MeshLaunch {
@@ -25,6 +27,7 @@ struct MeshLaunch {
 };
 
 // grid_kernels.cu
+cudaError_t grid_kernels_prepare();   // one-time kernel attributes (call outside capture)
 void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, float dmax);
 void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, int par, int update);
 void launch_grid_update(int kind, const GridLaunch& L, int par);

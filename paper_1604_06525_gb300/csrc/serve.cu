@@ -61,15 +61,17 @@ __global__ void k_serve_reset(Scalars* s, double lambda0) {
 size_t round32(size_t v) { return (v + 31) / 32 * 32; }
 
 // Device bytes a planned problem allocates (planes, tables, reduction slots).
-size_t estimate_grid(const opt_grid_desc& d) {
-  const size_t pl = round32((size_t)d.W) * (size_t)d.H;
-  const size_t planes = d.kind == OPT_ARAP_WARP_2D ? 24 : 30;
-  const size_t tiles = ((size_t)(d.W + 31) / 32) * ((size_t)(d.H + 7) / 8);
+size_t estimate_grid(const opt_grid_desc& d, int tile_w) {
+  const bool warp = d.kind == OPT_ARAP_WARP_2D;
+  const size_t tw = !warp ? 32 : (tile_w ? tile_w : (d.W >= 256 ? 128 : 32));
+  const size_t pl = ((size_t)d.W + tw - 1) / tw * tw * (size_t)d.H;
+  const size_t planes = warp ? (tw == 128 ? 26 : 24) : 30;
+  const size_t tiles = ((size_t)d.W + tw - 1) / tw * ((size_t)(d.H + 7) / 8);
   return planes * pl * 4 + (d.mask ? pl : 0) + tiles * 64 + (size_t)d.n_handles * 16 + (1 << 16);
 }
 size_t estimate_graph(const opt_graph_desc& d) {
   const size_t pl = round32((size_t)d.V);
-  return 51 * pl * 4 + (size_t)d.E * 8 + (size_t)d.n_handles * 16 + (1 << 16);
+  return 57 * pl * 4 + (size_t)d.E * 8 + (size_t)d.n_handles * 16 + (1 << 16);
 }
 
 }  // namespace
@@ -176,7 +178,7 @@ opt_status opt_server_submit_grid(opt_server* s, const opt_grid_desc* d, uint64_
   if (!s || !d || d->W < 1 || d->H < 1) return OPT_ERR_INVALID_ARG;
   ServeReq* r = new ServeReq();
   r->gd = *d;
-  r->est_bytes = estimate_grid(*d);
+  r->est_bytes = estimate_grid(*d, s->prm.tile_w);
   const opt_status st = submit(s, r, ticket);
   if (st != OPT_OK) delete r;
   return st;

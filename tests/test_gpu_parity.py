@@ -63,6 +63,8 @@ def random_direction(prob, seed):
 GRID_CASES = [
     ("warp", 64, 64, 0.0), ("warp", 37, 29, 0.0), ("warp", 37, 29, 0.25), ("warp", 1, 1, 0.0),
     ("warp", 1, 45, 0.0), ("warp", 70, 1, 0.0), ("warp", 100, 70, 0.1),
+    # 128-pixel tiles (float4 rows): exact, ragged and masked widths
+    ("warp", 256, 24, 0.0), ("warp", 300, 41, 0.0), ("warp", 301, 17, 0.2), ("warp", 520, 9, 0.0),
     ("poisson", 64, 48, None), ("poisson", 45, 33, None), ("poisson", 1, 17, None), ("poisson", 96, 80, None),
 ]
 
@@ -379,3 +381,53 @@ def test_materialized_solve_matches_oracle_and_matrix_free(api, case):
     a.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
     rm2 = solve(a, materialized=1)
     assert rm2["E_history"] == rm["E_history"] or all(relE(x, y) <= 1e-6 for x, y in zip(rm2["E_history"], rm["E_history"]))
+
+
+@pytest.mark.parametrize("W,H,mf", [(100, 30, 0.0), (33, 20, 0.3), (5, 7, 0.0)])
+def test_wide_tiles_forced_on_narrow_grids(api, W, H, mf):
+    """128-wide tiles on grids narrower than a tile (pitch padding, halo
+    columns outside the image) give the same products as 32-wide tiles."""
+    import torch
+    prob = make_grid("warp", W, H, mf, seed=131)
+    p = random_direction(prob, 2)
+    a = api.Problem(prob, tile_w=128)
+    b = api.Problem(prob, tile_w=32)
+    for lam in (0.0, 0.3):
+        qa, pqa = a.apply_jtj(torch.as_tensor(p, device="cuda"), lam)
+        qb, pqb = b.apply_jtj(torch.as_tensor(p, device="cuda"), lam)
+        assert rel(qa.cpu().numpy(), qb.cpu().numpy()) <= 1e-6
+        assert relE(pqa, pqb) <= 1e-6
+    ra = a.solve_gn(3, 6)
+    rb = b.solve_gn(3, 6)
+    for x, y in zip(ra["E_history"], rb["E_history"]):
+        assert relE(x, y) <= 1e-5
+
+
+def test_gn_wide_tiles_match_oracle(api):
+    """A 320 x 64 warp (128-wide tiles, ragged last tile) through GN 4 x 10."""
+    prob = synth.warp_problem(320, 64, 12, seed=141)
+    e = oracle.make_energy(prob)
+    ref = oracle.gauss_newton(e, prob.x0.reshape(-1), 4, 10)
+    gp = api.Problem(prob)
+    rep = gp.solve_gn(4, 10)
+    for a, b in zip(rep["E_history"], ref.E_history):
+        assert relE(a, b) <= TOL_ENERGY
+
+
+@pytest.mark.parametrize("kind", ["warp", "mesh"])
+def test_chunking_and_autotune_keep_results(api, kind):
+    prob = synth.warp_problem(300, 90, 9, seed=151) if kind == "warp" else synth.mesh_problem(3, seed=152)
+    a = api.Problem(prob)
+    ref = a.solve_gn(3, 8)
+    for per in (1, 5, -3, 0):
+        a.set_chunking(per)
+        a.x.copy_(__import__("torch").as_tensor(prob.x0, device="cuda"))
+        r = a.solve_gn(3, 8)
+        for x, y in zip(r["E_history"], ref["E_history"]):
+            assert relE(x, y) <= 1e-6
+    chosen, ms = a.autotune()
+    assert chosen in (-1, -2, -3, -4, -6, -8, 1, 4) and ms > 0
+    a.x.copy_(__import__("torch").as_tensor(prob.x0, device="cuda"))
+    r = a.solve_gn(3, 8)
+    for x, y in zip(r["E_history"], ref["E_history"]):
+        assert relE(x, y) <= 1e-6
