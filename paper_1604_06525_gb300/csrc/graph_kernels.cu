@@ -69,6 +69,7 @@ __device__ __forceinline__ int handle_of(const MeshProb& pr, int v) {
 __global__ void __launch_bounds__(NT) k_mesh_init_v(const MeshProb* __restrict__ probs,
                                                     const Chunk* __restrict__ chunks,
                                                     double* __restrict__ part) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_v(const MeshProb* __restrict__
       pr.csn[(2 * m + 1) * pl + v] = sn;
     }
   }
+  pdl_trigger();
   if (publish_partials(part, blockIdx.x, e, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double a, b;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, a, b);
@@ -106,6 +108,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_v(const MeshProb* __restrict__
 __global__ void __launch_bounds__(NT) k_mesh_init_e(const MeshProb* __restrict__ probs,
                                                     const Chunk* __restrict__ chunks,
                                                     double* __restrict__ part) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -155,6 +158,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_e(const MeshProb* __restrict__
       atomicAdd(&pr.q[2 * pl + b], rb2);
     }
   }
+  pdl_trigger();
   if (publish_partials(part, blockIdx.x, e, 0.0, &s->counter, pr.echunk_end - pr.echunk_begin)) {
     double a, b;
     gather_partials(part, pr.echunk_begin, pr.echunk_end, &s->counter, a, b);
@@ -166,6 +170,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_f(const MeshProb* __restrict__
                                                     const Chunk* __restrict__ chunks,
                                                     double* __restrict__ part, int k_outer,
                                                     float dmin, float dmax) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -196,6 +201,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_f(const MeshProb* __restrict__
       rz += b * (mv[c < 3 ? 0 : c - 2] * b);
     }
   }
+  pdl_trigger();
   if (publish_partials(part, blockIdx.x, rz, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double a, b;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, a, b);
@@ -228,6 +234,7 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_v(const MeshProb* __restrict_
                                                      double* __restrict__ part,
                                                      const float* __restrict__ p_override, int par,
                                                      int update) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -293,6 +300,7 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_v(const MeshProb* __restrict_
       for (int k = 0; k < 4; ++k) acc += c4(pv[c], k) * q[c][k];
     }
   }
+  pdl_trigger();
   if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double a, b;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, a, b);
@@ -305,6 +313,7 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_e(const MeshProb* __restrict_
                                                      const Chunk* __restrict__ chunks,
                                                      double* __restrict__ part,
                                                      const float* __restrict__ p_override, int par) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -358,6 +367,7 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_e(const MeshProb* __restrict_
       atomicAdd(&pr.q[2 * pl + b], jb2);
     }
   }
+  pdl_trigger();
   if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.echunk_end - pr.echunk_begin)) {
     double a, b;
     gather_partials(part, pr.echunk_begin, pr.echunk_end, &s->counter, a, b);
@@ -380,6 +390,7 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_e(const MeshProb* __restrict_
 __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__ probs,
                                                     const Chunk* __restrict__ chunks,
                                                     double* __restrict__ part, int par) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -414,6 +425,7 @@ __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__
       *reinterpret_cast<float4*>(pr.r + c * pl + v0) = rv[c];
     }
   }
+  pdl_trigger();
   if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double rz, unused;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, rz, unused);
@@ -435,6 +447,7 @@ __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__
 __global__ void __launch_bounds__(NT) k_mesh_energy_v(const MeshProb* __restrict__ probs,
                                                       const Chunk* __restrict__ chunks,
                                                       double* __restrict__ part, int mode) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -452,6 +465,7 @@ __global__ void __launch_bounds__(NT) k_mesh_energy_v(const MeshProb* __restrict
       e += f * f;
     }
   }
+  pdl_trigger();
   if (publish_partials(part, blockIdx.x, e, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double a, b;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, a, b);
@@ -463,6 +477,7 @@ __global__ void __launch_bounds__(NT) k_mesh_energy_e(const MeshProb* __restrict
                                                       const Chunk* __restrict__ chunks,
                                                       double* __restrict__ part, int mode,
                                                       int hist_idx) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -498,6 +513,7 @@ __global__ void __launch_bounds__(NT) k_mesh_energy_e(const MeshProb* __restrict
       e1 += l0 * l0 + l1 * l1 + l2 * l2;
     }
   }
+  pdl_trigger();
   if (publish_partials(part, blockIdx.x, e0, e1, &s->counter, pr.echunk_end - pr.echunk_begin)) {
     double a, b;
     gather_partials(part, pr.echunk_begin, pr.echunk_end, &s->counter, a, b);
@@ -518,6 +534,7 @@ __global__ void __launch_bounds__(NT) k_mesh_energy_e(const MeshProb* __restrict
 
 __global__ void __launch_bounds__(NT) k_mesh_step(const MeshProb* __restrict__ probs,
                                                   const Chunk* __restrict__ chunks, int cond) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   if (cond && !pr.s->accept) return;
@@ -535,27 +552,27 @@ __global__ void __launch_bounds__(NT) k_mesh_step(const MeshProb* __restrict__ p
 // launchers
 // ---------------------------------------------------------------------------
 void launch_mesh_init(const MeshLaunch& L, int k_outer, float dmin, float dmax) {
-  k_mesh_init_v<<<L.nvchunks, NT, 0, L.stream>>>(L.probs, L.vchunks, L.part);
-  k_mesh_init_e<<<L.nechunks, NT, 0, L.stream>>>(L.probs, L.echunks, L.part);
-  k_mesh_init_f<<<L.nvchunks, NT, 0, L.stream>>>(L.probs, L.vchunks, L.part, k_outer, dmin, dmax);
+  launch_pdl(k_mesh_init_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
+  launch_pdl(k_mesh_init_e, L.nechunks, NT, 0, L.stream, L.probs, L.echunks, L.part);
+  launch_pdl(k_mesh_init_f, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, k_outer, dmin, dmax);
 }
 
 void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, int update) {
-  k_mesh_apply_v<<<L.nvchunks, NT, 0, L.stream>>>(L.probs, L.vchunks, L.part, p_override, par, update);
-  k_mesh_apply_e<<<L.nechunks, NT, 0, L.stream>>>(L.probs, L.echunks, L.part, p_override, par);
+  launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, p_override, par, update);
+  launch_pdl(k_mesh_apply_e, L.nechunks, NT, 0, L.stream, L.probs, L.echunks, L.part, p_override, par);
 }
 
 void launch_mesh_update(const MeshLaunch& L, int par) {
-  k_mesh_update<<<L.nvchunks, NT, 0, L.stream>>>(L.probs, L.vchunks, L.part, par);
+  launch_pdl(k_mesh_update, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, par);
 }
 
 void launch_mesh_energy(const MeshLaunch& L, int mode, int hist_idx) {
-  k_mesh_energy_v<<<L.nvchunks, NT, 0, L.stream>>>(L.probs, L.vchunks, L.part, mode);
-  k_mesh_energy_e<<<L.nechunks, NT, 0, L.stream>>>(L.probs, L.echunks, L.part, mode, hist_idx);
+  launch_pdl(k_mesh_energy_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, mode);
+  launch_pdl(k_mesh_energy_e, L.nechunks, NT, 0, L.stream, L.probs, L.echunks, L.part, mode, hist_idx);
 }
 
 void launch_mesh_step(const MeshLaunch& L, int cond) {
-  k_mesh_step<<<L.nvchunks, NT, 0, L.stream>>>(L.probs, L.vchunks, cond);
+  launch_pdl(k_mesh_step, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, cond);
 }
 
 }  // namespace optgb

@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(NT) k_warp_init(const GridProb* __restrict__ p
                                                   const int* __restrict__ tiles,
                                                   double* __restrict__ part, int k_outer,
                                                   float dmin, float dmax) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(NT, 3) k_warp_apply(const GridProb* __restrict
                                                       double* __restrict__ part,
                                                       const float* __restrict__ p_in_override,
                                                       int par, int update) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -383,14 +385,12 @@ constexpr int W4 = 128;          // wide tile width
 constexpr int SP = W4 + 8;       // staged row pitch (floats): columns -1..128 live at 3..132
 constexpr int SPB = W4 + 32;     // mask row pitch (bytes): columns 0..127 live at 16..143
 constexpr int NRAW = 12;         // r0 r1 r2 m0 m1 p0 p1 p2 cos sin ux uy
-constexpr int NSTG = 7;          // px py pt cos sin ux uy
+constexpr int NSTG = 8;          // px py pt cos sin ux uy valid, each quad stored as pixels 0 2 1 3
 
 struct WideSmem {
   float raw[NRAW][HH][SP];
-  float stg[NSTG][HH][SP];
-  unsigned int v[HH][SP / 4];    // validity bits of each staged quad (bit k = pixel k)
+  float stg[NSTG][HH][SP];       // halo columns -1 / 128 live at 3 / 132, in plain order
   unsigned char mk[HH][SPB];
-  unsigned char vc[HH][2];       // validity of the halo columns -1 and 128
 };
 
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
@@ -461,67 +461,90 @@ __device__ __forceinline__ void wide_issue(WideSmem& sm, const WidePlanes& pp, c
   cp_async_commit();
 }
 
-// Phase 2 for one staged quad: direction, copied geometry, validity bits.
+// Packed float32 pairs (one instruction for two lanes of a float2).  All are
+// correctly rounded IEEE operations, so results do not depend on the packing.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ float4 mul4p(const float4& a, const float4& b) {
+  return cat4(mul2(lo2(a), lo2(b)), mul2(hi2(a), hi2(b)));
+}
+__device__ __forceinline__ float4 fma4p(float2 a, const float4& x, const float4& y) {
+  return cat4(fma2(a, lo2(x), lo2(y)), fma2(a, hi2(x), hi2(y)));
+}
+// pixel order 0 1 2 3 <-> 0 2 1 3 (its own inverse)
+__device__ __forceinline__ float4 swz4(const float4& v) { return make_float4(v.x, v.z, v.y, v.w); }
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void sts4(float* p, const float4& v) { *reinterpret_cast<float4*>(p) = v; }
+
+// Phase 2 for one staged quad: direction, copied geometry and validity (1 / 0),
+// stored in the staged order 0 2 1 3 so that pixels {0, 2} and {1, 3} form the
+// two float2 packs of the stencil.
 template <bool MASK>
 __device__ __forceinline__ void wide_stage_quad(WideSmem& sm, int row, int lane, const GridProb& pr, int gx, int gy,
-                                                int update, int use_beta, float beta, float4* px, float4* py,
-                                                float4* pt) {
+                                                int update, int use_beta, float2 beta2) {
   const int c = 4 + 4 * lane;
-  auto R = [&](int k) { return *reinterpret_cast<const float4*>(&sm.raw[k][row][c]); };
+  auto R = [&](int k) { return lds4(&sm.raw[k][row][c]); };
   float4 a, b, t;
   if (update) {
     const float4 m0 = R(3), m1 = R(4);
-    a = mul4(m0, R(0));
-    b = mul4(m0, R(1));
-    t = mul4(m1, R(2));
+    a = mul4p(m0, R(0));
+    b = mul4p(m0, R(1));
+    t = mul4p(m1, R(2));
     if (use_beta) {
-      a = fma4(beta, R(5), a);
-      b = fma4(beta, R(6), b);
-      t = fma4(beta, R(7), t);
+      a = fma4p(beta2, R(5), a);
+      b = fma4p(beta2, R(6), b);
+      t = fma4p(beta2, R(7), t);
     }
   } else {
     a = R(5); b = R(6); t = R(7);
   }
-  *reinterpret_cast<float4*>(&sm.stg[0][row][c]) = a;
-  *reinterpret_cast<float4*>(&sm.stg[1][row][c]) = b;
-  *reinterpret_cast<float4*>(&sm.stg[2][row][c]) = t;
+  sts4(&sm.stg[0][row][c], swz4(a));
+  sts4(&sm.stg[1][row][c], swz4(b));
+  sts4(&sm.stg[2][row][c], swz4(t));
 #pragma unroll
-  for (int k = 0; k < 4; ++k) *reinterpret_cast<float4*>(&sm.stg[3 + k][row][c]) = R(8 + k);
-  unsigned int v = 0u;
+  for (int k = 0; k < 4; ++k) sts4(&sm.stg[3 + k][row][c], swz4(R(8 + k)));
+  float vk[4] = {0.f, 0.f, 0.f, 0.f};
   if (gy >= 0 && gy < pr.H) {
     const unsigned int m4 = MASK ? *reinterpret_cast<const unsigned int*>(&sm.mk[row][16 + 4 * lane]) : 0u;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (gx + k < pr.W && (!MASK || ((m4 >> (8 * k)) & 0xffu) == 0u)) v |= 1u << k;
+      vk[k] = (gx + k < pr.W && (!MASK || ((m4 >> (8 * k)) & 0xffu) == 0u)) ? 1.f : 0.f;
   }
-  sm.v[row][1 + lane] = v;
-  if (px) { *px = a; *py = b; *pt = t; }
+  sts4(&sm.stg[7][row][c], make_float4(vk[0], vk[2], vk[1], vk[3]));
 }
 
-// Adds the grouped own + incoming rows of the pair (i, j) to the accumulators.
-__device__ __forceinline__ void pair_terms(float pxi, float pyi, float pti, float ci, float si, float uxi,
-                                           float uyi, float pxj, float pyj, float ptj, float cj, float sj,
-                                           float uxj, float uyj, float& ax, float& ay, float& at) {
-  const float vx = uxi - uxj, vy = uyi - uyj;
-  const float a = pxi - pxj, b = pyi - pyj;
-  const float gix = fmaf(si, vx, ci * vy), giy = fmaf(si, vy, -ci * vx);
-  const float gjx = fmaf(sj, vx, cj * vy), gjy = fmaf(sj, vy, -cj * vx);
-  const float tx = fmaf(gix, pti, a), ty = fmaf(giy, pti, b);
-  ax += tx + fmaf(gjx, ptj, a);
-  ay += ty + fmaf(gjy, ptj, b);
-  at = fmaf(gix, tx, fmaf(giy, ty, at));
-}
-
-struct Quad7 {
-  float4 q[NSTG];
-  unsigned int v;
+// Own values of one float2 pack of pixels.
+struct Own2 {
+  float2 px, py, pt, c, s, ux, uy;
 };
 
-__device__ __forceinline__ void read_quad7(const WideSmem& sm, int row, int lane, Quad7& o) {
-  const int c = 4 + 4 * lane;
-#pragma unroll
-  for (int k = 0; k < NSTG; ++k) o.q[k] = *reinterpret_cast<const float4*>(&sm.stg[k][row][c]);
-  o.v = sm.v[row][1 + lane];
+// Adds the grouped own + incoming rows of the pairs (i, j) of one pack (two
+// pixels i, each with its neighbour j in the same direction), scaled by the
+// validity m_j of the neighbour.  With v = U_i - U_j, a = p_i - p_j and
+// G_k = (s_k v_x + c_k v_y, s_k v_y - c_k v_x):
+//   q_d,i += m_j [2 a + G_i p_t,i + G_j p_t,j],  q_t,i += m_j G_i . (a + G_i p_t,i).
+__device__ __forceinline__ void pair2(const Own2& o, float2 pxj, float2 pyj, float2 ptj, float2 cj, float2 sj,
+                                      float2 uxj, float2 uyj, float2 mj, float2& ax, float2& ay, float2& at) {
+  const float2 vx = sub2(o.ux, uxj), vy = sub2(o.uy, uyj), nvx = sub2(uxj, o.ux);
+  const float2 a = sub2(o.px, pxj), b = sub2(o.py, pyj);
+  const float2 gix = fma2(o.s, vx, mul2(o.c, vy)), giy = fma2(o.c, nvx, mul2(o.s, vy));
+  const float2 gjx = fma2(sj, vx, mul2(cj, vy)), gjy = fma2(cj, nvx, mul2(sj, vy));
+  const float2 tx = fma2(gix, o.pt, a), ty = fma2(giy, o.pt, b);
+  ax = fma2(mj, add2(tx, fma2(gjx, ptj, a)), ax);
+  ay = fma2(mj, add2(ty, fma2(gjy, ptj, b)), ay);
+  at = fma2(mj, fma2(gix, tx, mul2(giy, ty)), at);
 }
 
 template <bool MASK>
@@ -531,6 +554,7 @@ __global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __res
                                                            double* __restrict__ part,
                                                            const float* __restrict__ p_in_override,
                                                            int par, int update) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   WideSmem& sm = *reinterpret_cast<WideSmem*>(dyn_smem);
   const Chunk ch = chunks[blockIdx.x];
@@ -538,8 +562,10 @@ __global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __res
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
   const int pl = (int)pr.plane;
-  const float w = pr.w_reg, wfit = pr.w_fit;
+  const float wfit = pr.w_fit;
+  const float2 w2 = make_float2(pr.w_reg, pr.w_reg);
   const float beta = s->beta_f;
+  const float2 beta2 = make_float2(beta, beta);
   const int use_beta = beta != 0.0f;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const float* __restrict__ pin = p_in_override ? p_in_override : pr.p + (long long)(par & 1) * 3 * pl;
@@ -559,20 +585,24 @@ __global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __res
   pp.src[11] = pr.c + pl;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   float acc = 0.f;
+  // the tile index one tile ahead and the handle range of the current tile
+  // are loaded an iteration early: the inline-assembly copies order all
+  // memory accesses, so a late load would stall the warp at its use
   int tc = tiles[ch.begin];
+  int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
+  int hb0 = pr.hbeg[tile_id(pr, tc)], hb1 = pr.hbeg[tile_id(pr, tc) + 1];
   wide_issue<MASK>(sm, pp, pr, tile_x0(tc, W4), tile_y0(tc), tid);
   for (int t = ch.begin; t < ch.end; ++t) {
     const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
     const int gx = x0 + 4 * lane, gy = y0 + ty;
-    const int tcur = tc;
+    const int hcur0 = hb0, hcur1 = hb1;
     cp_async_wait_all();
     __syncthreads();
-    // phase 2: staged direction and geometry
-    float4 opx, opy, opt;
-    wide_stage_quad<MASK>(sm, ty + 1, lane, pr, gx, gy, update, use_beta, beta, &opx, &opy, &opt);
+    // phase 2: staged direction, geometry and validity
+    wide_stage_quad<MASK>(sm, ty + 1, lane, pr, gx, gy, update, use_beta, beta2);
     if (tid < 64) {
       const int row = tid < 32 ? 0 : HH - 1;
-      wide_stage_quad<MASK>(sm, row, lane, pr, gx, y0 - 1 + row, update, use_beta, beta, nullptr, nullptr, nullptr);
+      wide_stage_quad<MASK>(sm, row, lane, pr, gx, y0 - 1 + row, update, use_beta, beta2);
     } else if (tid < 64 + 2 * TH) {
       const int h = tid - 64;
       const int row = 1 + (h % TH), side = h / TH;
@@ -595,101 +625,104 @@ __global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __res
       for (int k = 0; k < 4; ++k) sm.stg[3 + k][row][col] = sm.raw[8 + k][row][col];
       const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
       const bool ok = hy < pr.H && hx >= 0 && hx < pr.W;
-      sm.vc[row][side] = (unsigned char)(ok && (!MASK || __ldg(pr.mask + (long long)hy * pr.P + hx) == 0));
+      sm.stg[7][row][col] = (ok && (!MASK || __ldg(pr.mask + (long long)hy * pr.P + hx) == 0)) ? 1.f : 0.f;
     }
     __syncthreads();
     // the raw buffer is free: start the next tile's copies
     if (t + 1 < ch.end) {
-      tc = tiles[t + 1];
+      tc = tn;
       wide_issue<MASK>(sm, pp, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+      const int tidn = tile_id(pr, tc);
+      hb0 = pr.hbeg[tidn];
+      hb1 = pr.hbeg[tidn + 1];
+      if (t + 2 < ch.end) tn = tiles[t + 2];
     }
     if (gy < pr.H) {                          // warp-uniform: one warp per row
       const long long i = (long long)gy * pr.P + gx;
+      // phase 3: the stencil on two packs, A = pixels {0, 2}, B = pixels {1, 3}
+      const int c = 4 + 4 * lane;
+      float4 O[NSTG];
+#pragma unroll
+      for (int k = 0; k < NSTG; ++k) O[k] = lds4(&sm.stg[k][ty + 1][c]);
       if (update) {
-        *reinterpret_cast<float4*>(pout + i) = opx;
-        *reinterpret_cast<float4*>(pout + pl + i) = opy;
-        *reinterpret_cast<float4*>(pout + 2 * pl + i) = opt;
+        *reinterpret_cast<float4*>(pout + i) = swz4(O[0]);
+        *reinterpret_cast<float4*>(pout + pl + i) = swz4(O[1]);
+        *reinterpret_cast<float4*>(pout + 2 * pl + i) = swz4(O[2]);
       }
-      Quad7 O;
-      read_quad7(sm, ty + 1, lane, O);
-      float L[NSTG], R[NSTG];
+      float2 axA = make_float2(0.f, 0.f), ayA = axA, atA = axA, axB = axA, ayB = axA, atB = axA;
+      const Own2 oa = {lo2(O[0]), lo2(O[1]), lo2(O[2]), lo2(O[3]), lo2(O[4]), lo2(O[5]), lo2(O[6])};
+      const Own2 ob = {hi2(O[0]), hi2(O[1]), hi2(O[2]), hi2(O[3]), hi2(O[4]), hi2(O[5]), hi2(O[6])};
+      {
+        // horizontal neighbours: pixel -1 / 4 from the neighbouring lanes
+        // (staged order: pixel 3 is .w, pixel 0 is .x) or the halo columns
+        float L[NSTG], R[NSTG];
 #pragma unroll
-      for (int k = 0; k < NSTG; ++k) {
-        L[k] = __shfl_up_sync(0xffffffffu, O.q[k].w, 1);
-        R[k] = __shfl_down_sync(0xffffffffu, O.q[k].x, 1);
-      }
-      unsigned int lv = (__shfl_up_sync(0xffffffffu, O.v, 1) >> 3) & 1u;
-      unsigned int rv = __shfl_down_sync(0xffffffffu, O.v, 1) & 1u;
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < NSTG; ++k) L[k] = sm.stg[k][ty + 1][3];
-        lv = sm.vc[ty + 1][0];
-      }
-      if (lane == 31) {
-#pragma unroll
-        for (int k = 0; k < NSTG; ++k) R[k] = sm.stg[k][ty + 1][4 + W4];
-        rv = sm.vc[ty + 1][1];
-      }
-      Quad7 Up, Dn;
-      read_quad7(sm, ty, lane, Up);
-      read_quad7(sm, ty + 2, lane, Dn);
-      float qx[4], qy[4], qt[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        float ax = 0.f, ay = 0.f, at = 0.f;
-        const float pxi = cmp(O.q[0], k), pyi = cmp(O.q[1], k), pti = cmp(O.q[2], k);
-        const float ci = cmp(O.q[3], k), si = cmp(O.q[4], k), uxi = cmp(O.q[5], k), uyi = cmp(O.q[6], k);
-        if ((O.v >> k) & 1u) {
-          if (k == 0 ? lv : ((O.v >> (k - 1)) & 1u)) {
-            if (k == 0)
-              pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, L[0], L[1], L[2], L[3], L[4], L[5], L[6], ax, ay, at);
-            else
-              pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, cmp(O.q[0], k - 1), cmp(O.q[1], k - 1), cmp(O.q[2], k - 1),
-                         cmp(O.q[3], k - 1), cmp(O.q[4], k - 1), cmp(O.q[5], k - 1), cmp(O.q[6], k - 1), ax, ay, at);
-          }
-          if (k == 3 ? rv : ((O.v >> (k + 1)) & 1u)) {
-            if (k == 3)
-              pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, R[0], R[1], R[2], R[3], R[4], R[5], R[6], ax, ay, at);
-            else
-              pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, cmp(O.q[0], k + 1), cmp(O.q[1], k + 1), cmp(O.q[2], k + 1),
-                         cmp(O.q[3], k + 1), cmp(O.q[4], k + 1), cmp(O.q[5], k + 1), cmp(O.q[6], k + 1), ax, ay, at);
-          }
-          if ((Up.v >> k) & 1u)
-            pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, cmp(Up.q[0], k), cmp(Up.q[1], k), cmp(Up.q[2], k),
-                       cmp(Up.q[3], k), cmp(Up.q[4], k), cmp(Up.q[5], k), cmp(Up.q[6], k), ax, ay, at);
-          if ((Dn.v >> k) & 1u)
-            pair_terms(pxi, pyi, pti, ci, si, uxi, uyi, cmp(Dn.q[0], k), cmp(Dn.q[1], k), cmp(Dn.q[2], k),
-                       cmp(Dn.q[3], k), cmp(Dn.q[4], k), cmp(Dn.q[5], k), cmp(Dn.q[6], k), ax, ay, at);
+        for (int k = 0; k < NSTG; ++k) {
+          L[k] = __shfl_up_sync(0xffffffffu, O[k].w, 1);
+          R[k] = __shfl_down_sync(0xffffffffu, O[k].x, 1);
         }
-        qx[k] = w * ax;
-        qy[k] = w * ay;
-        qt[k] = w * at;
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < NSTG; ++k) L[k] = sm.stg[k][ty + 1][3];
+        }
+        if (lane == 31) {
+#pragma unroll
+          for (int k = 0; k < NSTG; ++k) R[k] = sm.stg[k][ty + 1][4 + W4];
+        }
+        // A: left neighbours {-1, 1}, right neighbours {1, 3} = B
+        pair2(oa, make_float2(L[0], O[0].z), make_float2(L[1], O[1].z), make_float2(L[2], O[2].z),
+              make_float2(L[3], O[3].z), make_float2(L[4], O[4].z), make_float2(L[5], O[5].z),
+              make_float2(L[6], O[6].z), make_float2(L[7], O[7].z), axA, ayA, atA);
+        pair2(oa, ob.px, ob.py, ob.pt, ob.c, ob.s, ob.ux, ob.uy, hi2(O[7]), axA, ayA, atA);
+        // B: left neighbours {0, 2} = A, right neighbours {2, 4}
+        pair2(ob, oa.px, oa.py, oa.pt, oa.c, oa.s, oa.ux, oa.uy, lo2(O[7]), axB, ayB, atB);
+        pair2(ob, make_float2(O[0].y, R[0]), make_float2(O[1].y, R[1]), make_float2(O[2].y, R[2]),
+              make_float2(O[3].y, R[3]), make_float2(O[4].y, R[4]), make_float2(O[5].y, R[5]),
+              make_float2(O[6].y, R[6]), make_float2(O[7].y, R[7]), axB, ayB, atB);
       }
-      const int tid_ = tile_id(pr, tcur);
-      for (int h = pr.hbeg[tid_]; h < pr.hbeg[tid_ + 1]; ++h) {
+#pragma unroll 1
+      for (int dr = 0; dr < 2; ++dr) {        // rows above and below
+        float4 U[NSTG];
+        const int row = dr ? ty + 2 : ty;
+#pragma unroll
+        for (int k = 0; k < NSTG; ++k) U[k] = lds4(&sm.stg[k][row][c]);
+        pair2(oa, lo2(U[0]), lo2(U[1]), lo2(U[2]), lo2(U[3]), lo2(U[4]), lo2(U[5]), lo2(U[6]), lo2(U[7]), axA,
+              ayA, atA);
+        pair2(ob, hi2(U[0]), hi2(U[1]), hi2(U[2]), hi2(U[3]), hi2(U[4]), hi2(U[5]), hi2(U[6]), hi2(U[7]), axB,
+              ayB, atB);
+      }
+      // scale by w and the own validity, back to plain pixel order
+      const float2 wa = mul2(w2, lo2(O[7])), wb = mul2(w2, hi2(O[7]));
+      axA = mul2(wa, axA); ayA = mul2(wa, ayA); atA = mul2(wa, atA);
+      axB = mul2(wb, axB); ayB = mul2(wb, ayB); atB = mul2(wb, atB);
+      float qx[4] = {axA.x, axB.x, axA.y, axB.y};
+      float qy[4] = {ayA.x, ayB.x, ayA.y, ayB.y};
+      float qt[4] = {atA.x, atB.x, atA.y, atB.y};
+      const float vf[4] = {O[7].x, O[7].z, O[7].y, O[7].w};
+      const float4 opx = swz4(O[0]), opy = swz4(O[1]), opt = swz4(O[2]);
+      for (int h = hcur0; h < hcur1; ++h) {
         const long long k = pr.hpix[h] - i;
-        if (k >= 0 && k < 4 && ((O.v >> k) & 1u)) {
+        if (k >= 0 && k < 4) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            if (kk == k) { qx[kk] += wfit * cmp(O.q[0], kk); qy[kk] += wfit * cmp(O.q[1], kk); }
+            if (kk == k && vf[kk] != 0.f) { qx[kk] += wfit * cmp(opx, kk); qy[kk] += wfit * cmp(opy, kk); }
         }
       }
       if (pr.lm) {
         const float4 dd = ld4(pr.dc + i), dt = ld4(pr.dc + pl + i);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          if (!((O.v >> k) & 1u)) continue;
-          qx[k] += lam * cmp(dd, k) * cmp(O.q[0], k);
-          qy[k] += lam * cmp(dd, k) * cmp(O.q[1], k);
-          qt[k] += lam * cmp(dt, k) * cmp(O.q[2], k);
+          if (vf[k] == 0.f) continue;
+          qx[k] += lam * cmp(dd, k) * cmp(opx, k);
+          qy[k] += lam * cmp(dd, k) * cmp(opy, k);
+          qt[k] += lam * cmp(dt, k) * cmp(opt, k);
         }
       }
       *reinterpret_cast<float4*>(pr.q + i) = make_float4(qx[0], qx[1], qx[2], qx[3]);
       *reinterpret_cast<float4*>(pr.q + pl + i) = make_float4(qy[0], qy[1], qy[2], qy[3]);
       *reinterpret_cast<float4*>(pr.q + 2 * pl + i) = make_float4(qt[0], qt[1], qt[2], qt[3]);
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        acc += cmp(O.q[0], k) * qx[k] + cmp(O.q[1], k) * qy[k] + cmp(O.q[2], k) * qt[k];
+      for (int k = 0; k < 4; ++k) acc += cmp(opx, k) * qx[k] + cmp(opy, k) * qy[k] + cmp(opt, k) * qt[k];
     }
   }
   cp_async_wait_all();
@@ -830,6 +863,7 @@ __global__ void __launch_bounds__(NT, 2) k_warp_init_wide(const GridProb* __rest
                                                           const int* __restrict__ tiles,
                                                           double* __restrict__ part, int k_outer,
                                                           float dmin, float dmax) {
+  pdl_begin();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   InitSmem& sm = *reinterpret_cast<InitSmem*>(dyn_smem);
   const Chunk ch = chunks[blockIdx.x];
@@ -1003,6 +1037,7 @@ __global__ void __launch_bounds__(NT) k_warp_energy(const GridProb* __restrict__
                                                     const int* __restrict__ tiles,
                                                     double* __restrict__ part, int mode,
                                                     int hist_idx) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -1124,6 +1159,7 @@ __global__ void __launch_bounds__(NT) k_poisson_init(const GridProb* __restrict_
                                                      const int* __restrict__ tiles,
                                                      double* __restrict__ part, int k_outer,
                                                      float dmin, float dmax) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -1268,6 +1304,7 @@ __global__ void __launch_bounds__(NT, 3) k_poisson_apply(const GridProb* __restr
                                                          double* __restrict__ part,
                                                          const float* __restrict__ p_in_override,
                                                          int par, int update) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -1349,6 +1386,7 @@ __global__ void __launch_bounds__(NT) k_poisson_energy(const GridProb* __restric
                                                        const int* __restrict__ tiles,
                                                        double* __restrict__ part, int mode,
                                                        int hist_idx) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -1431,6 +1469,7 @@ __global__ void __launch_bounds__(NT) k_grid_update(const GridProb* __restrict__
                                                     const Chunk* __restrict__ chunks,
                                                     const int* __restrict__ tiles,
                                                     double* __restrict__ part, int par) {
+  pdl_begin();
   constexpr int NM = NX == 3 ? 2 : 1;
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
@@ -1497,6 +1536,7 @@ template <int NX>
 __global__ void __launch_bounds__(NT) k_grid_step(const GridProb* __restrict__ probs,
                                                   const Chunk* __restrict__ chunks,
                                                   const int* __restrict__ tiles, int cond) {
+  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   if (cond && !pr.s->accept) return;
@@ -1549,49 +1589,49 @@ cudaError_t grid_kernels_prepare() {
 
 void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, float dmax) {
   if (kind == K_WARP && L.tw == 128 && L.masked)
-    k_warp_init_wide<true><<<L.nchunks, NT, sizeof(InitSmem), L.stream>>>(L.probs, L.chunks, L.tiles, L.part, k_outer,
+    launch_pdl(k_warp_init_wide<true>, L.nchunks, NT, sizeof(InitSmem), L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer,
                                                                         dmin, dmax);
   else if (kind == K_WARP && L.tw == 128)
-    k_warp_init_wide<false><<<L.nchunks, NT, sizeof(InitSmem), L.stream>>>(L.probs, L.chunks, L.tiles, L.part,
+    launch_pdl(k_warp_init_wide<false>, L.nchunks, NT, sizeof(InitSmem), L.stream, L.probs, L.chunks, L.tiles, L.part,
                                                                          k_outer, dmin, dmax);
   else if (kind == K_WARP)
-    k_warp_init<<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
+    launch_pdl(k_warp_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
   else
-    k_poisson_init<<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
+    launch_pdl(k_poisson_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
 }
 
 void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, int par, int update) {
   if (kind == K_WARP && L.tw == 128 && L.masked)
-    k_warp_apply_wide<true><<<L.nchunks, NT, sizeof(WideSmem), L.stream>>>(L.probs, L.chunks, L.tiles, L.part,
+    launch_pdl(k_warp_apply_wide<true>, L.nchunks, NT, sizeof(WideSmem), L.stream, L.probs, L.chunks, L.tiles, L.part,
                                                                          p_override, par, update);
   else if (kind == K_WARP && L.tw == 128)
-    k_warp_apply_wide<false><<<L.nchunks, NT, sizeof(WideSmem), L.stream>>>(L.probs, L.chunks, L.tiles, L.part,
+    launch_pdl(k_warp_apply_wide<false>, L.nchunks, NT, sizeof(WideSmem), L.stream, L.probs, L.chunks, L.tiles, L.part,
                                                                           p_override, par, update);
   else if (kind == K_WARP)
-    k_warp_apply<<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, p_override, par, update);
+    launch_pdl(k_warp_apply, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, p_override, par, update);
   else
-    k_poisson_apply<<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, p_override, par, update);
+    launch_pdl(k_poisson_apply, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, p_override, par, update);
 }
 
 void launch_grid_update(int kind, const GridLaunch& L, int par) {
   if (kind == K_WARP)
-    k_grid_update<3><<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, par);
+    launch_pdl(k_grid_update<3>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, par);
   else
-    k_grid_update<4><<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, par);
+    launch_pdl(k_grid_update<4>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, par);
 }
 
 void launch_grid_energy(int kind, const GridLaunch& L, int mode, int hist_idx) {
   if (kind == K_WARP)
-    k_warp_energy<<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, mode, hist_idx);
+    launch_pdl(k_warp_energy, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, mode, hist_idx);
   else
-    k_poisson_energy<<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, L.part, mode, hist_idx);
+    launch_pdl(k_poisson_energy, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, mode, hist_idx);
 }
 
 void launch_grid_step(int kind, const GridLaunch& L, int cond) {
   if (kind == K_WARP)
-    k_grid_step<3><<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, cond);
+    launch_pdl(k_grid_step<3>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, cond);
   else
-    k_grid_step<4><<<L.nchunks, NT, 0, L.stream>>>(L.probs, L.chunks, L.tiles, cond);
+    launch_pdl(k_grid_step<4>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, cond);
 }
 
 }  // namespace optgb

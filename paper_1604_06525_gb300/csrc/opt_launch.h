@@ -26,6 +26,24 @@ struct MeshLaunch {
   cudaStream_t stream;
 };
 
+// Launches kernel k with programmatic stream serialization (the kernel must
+// begin with pdl_begin()).  Works inside stream capture as well.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // grid_kernels.cu
 cudaError_t grid_kernels_prepare();   // one-time kernel attributes (call outside capture)
 void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, float dmax);
