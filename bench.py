@@ -37,6 +37,8 @@ W_BENCH, H_BENCH, HANDLES, OUTER, INNER = 1024, 1024, 64, 20, 20
 # algorithmic bytes per pixel (float32 planes, each touched once per launch)
 BYTES_APPLY_WARP = 72      # read r 12, M^-1 8, p_old 12, cos/sin 8, UrShape 8; write p 12, q 12
 BYTES_UPDATE_WARP = 80     # read delta 12, p 12, r 12, q 12, M^-1 8; write delta 12, r 12
+BYTES_INIT_WARP = 60       # read x 12, UrShape 8; write r 12, M^-1 8, delta 12, cos/sin 8 (GN)
+KERNEL_SOURCES = ("grid_kernels.cu", "opt_internal.cuh", "opt_launch.h")
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -50,10 +52,13 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
-    """sha256[:16] of the grid kernel source (the traffic figure is dropped
-    when it changes)."""
-    with open(os.path.join(ROOT, "paper_1604_06525_gb300", "csrc", "grid_kernels.cu"), "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """sha256[:16] of the grid kernel sources (the traffic figure is dropped
+    when they change)."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1604_06525_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str, workload: str):
@@ -86,7 +91,7 @@ class ClockSampler:
         try:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.tmp, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -194,9 +199,14 @@ def roofline_for(api, synth, torch, W, H, peak, iters=20):
     ms_init, ms_apply, ms_update = gp.profile_pcg(iters)
     px = W * H
     out = {}
-    for name, ms, bpp in (("k_warp_apply", ms_apply, BYTES_APPLY_WARP), ("k_grid_update", ms_update, BYTES_UPDATE_WARP)):
+    wide = W >= 256                      # 128-pixel tiles (k_warp_*_wide) from 256 pixels up
+    for name, ms, bpp, per_solve in (
+            ("k_warp_apply_wide" if wide else "k_warp_apply", ms_apply, BYTES_APPLY_WARP, OUTER * INNER),
+            ("k_grid_update<3>", ms_update, BYTES_UPDATE_WARP, OUTER * INNER),
+            ("k_warp_init_wide" if wide else "k_warp_init", ms_init, BYTES_INIT_WARP, OUTER)):
         ach = bpp * px / (ms * 1e-3) / 1e9
-        out[name] = {"ms": ms, "bytes": bpp * px, "achieved": ach, "frac": ach / peak}
+        out[name] = {"ms": ms, "bytes": bpp * px, "achieved": ach, "frac": ach / peak,
+                     "launches_per_solve": per_solve}
     gp.close()
     del prob
     torch.cuda.empty_cache()
@@ -401,11 +411,13 @@ def run_ours(args):
         torch.distributed.barrier()
     reps = []
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
         t0 = time.perf_counter()
         for _ in range(args.steps):
             reps.append(one_step())
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        torch.cuda.nvtx.range_pop()
     if world > 1:
         torch.distributed.barrier()
     dev_ms = sum(r["ms"] for r in reps)
@@ -433,54 +445,55 @@ def run_ours(args):
 
     # roofline of the dominant kernel, timed live at the bench size and beyond L2
     roof, _ = roofline_for(api, synth, torch, W_BENCH, H_BENCH, peak)
-    dom = max(roof, key=lambda k: roof[k]["ms"] * (1 if k == "k_warp_apply" else 1))
-    roof_big, _ = roofline_for(api, synth, torch, 4096, 4096, peak)
+    dom = max(roof, key=lambda k: roof[k]["ms"] * roof[k]["launches_per_solve"])   # largest share of a solve
+    roof_big, extra = {}, {}
+    if not args.no_extras:
+        roof_big, _ = roofline_for(api, synth, torch, 4096, 4096, peak)
 
-    # secondary workloads: matrix-free vs materialized J (Sec. 8.3) on the
-    # warp and on Poisson editing at 1024 x 1024, then the mesh under LM
-    extra = {}
+        # secondary workloads: matrix-free vs materialized J (Sec. 8.3) on the
+        # warp and on Poisson editing at 1024 x 1024, then the mesh under LM
 
-    def timed(g, x_init, fn, n=3, **kw):
-        out = []
-        for _ in range(n + 1):
-            flush.zero_()
-            g.x.copy_(x_init)
-            out.append(fn(OUTER, INNER, **kw))
-        return out[1:]
+        def timed(g, x_init, fn, n=3, **kw):
+            out = []
+            for _ in range(n + 1):
+                flush.zero_()
+                g.x.copy_(x_init)
+                out.append(fn(OUTER, INNER, **kw))
+            return out[1:]
 
-    rr_mat = timed(gp, x0, gp.solve_gn, materialized=1)
-    ms_mat = statistics.median(r_["ms"] for r_ in rr_mat)
-    extra["warp_1024x1024_materialized_gn20x20"] = {
-        "pcg_iters_per_s": OUTER * INNER / (ms_mat / 1e3), "ms_per_solve": ms_mat,
-        "matrix_free_speedup": ms_mat / ms_per_step, "E_final": rr_mat[-1]["E_final"],
-        "E_final_matrix_free": E_final}
-    pp = synth.poisson_problem(W_BENCH, H_BENCH, seed=synth.BASE_SEED)
-    gpp = api.Problem(pp)
-    xp0 = gpp.x.clone()
-    rr = timed(gpp, xp0, gpp.solve_gn)
-    rrm = timed(gpp, xp0, gpp.solve_gn, materialized=1)
-    msp = statistics.median(r_["ms"] for r_ in rr)
-    mspm = statistics.median(r_["ms"] for r_ in rrm)
-    extra["poisson_1024x1024x4_gn20x20"] = {"pcg_iters_per_s": OUTER * INNER / (msp / 1e3), "ms_per_solve": msp,
-                                           "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
-    extra["poisson_1024x1024x4_materialized_gn20x20"] = {
-        "pcg_iters_per_s": OUTER * INNER / (mspm / 1e3), "ms_per_solve": mspm,
-        "matrix_free_speedup": mspm / msp, "E_final": rrm[-1]["E_final"]}
-    gpp.close()
-    mp = synth.mesh_problem(7, seed=synth.BASE_SEED)
-    gmp = api.Problem(mp)
-    x0m = gmp.x.clone()
-    rr = []
-    for _ in range(3):
-        gmp.x.copy_(x0m)
-        rr.append(gmp.solve_lm(15, 30, lambda0=1e-3))
-    msm = statistics.median(r_["ms"] for r_ in rr)
-    extra["mesh_icosphere7_lm15x30"] = {"pcg_iters_per_s": rr[-1]["pcg_done"] / (msm / 1e3), "ms_per_solve": msm,
-                                       "accepted": rr[-1]["accepted"], "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
-    gmp.close()
+        rr_mat = timed(gp, x0, gp.solve_gn, materialized=1)
+        ms_mat = statistics.median(r_["ms"] for r_ in rr_mat)
+        extra["warp_1024x1024_materialized_gn20x20"] = {
+            "pcg_iters_per_s": OUTER * INNER / (ms_mat / 1e3), "ms_per_solve": ms_mat,
+            "matrix_free_speedup": ms_mat / ms_per_step, "E_final": rr_mat[-1]["E_final"],
+            "E_final_matrix_free": E_final}
+        pp = synth.poisson_problem(W_BENCH, H_BENCH, seed=synth.BASE_SEED)
+        gpp = api.Problem(pp)
+        xp0 = gpp.x.clone()
+        rr = timed(gpp, xp0, gpp.solve_gn)
+        rrm = timed(gpp, xp0, gpp.solve_gn, materialized=1)
+        msp = statistics.median(r_["ms"] for r_ in rr)
+        mspm = statistics.median(r_["ms"] for r_ in rrm)
+        extra["poisson_1024x1024x4_gn20x20"] = {"pcg_iters_per_s": OUTER * INNER / (msp / 1e3), "ms_per_solve": msp,
+                                               "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
+        extra["poisson_1024x1024x4_materialized_gn20x20"] = {
+            "pcg_iters_per_s": OUTER * INNER / (mspm / 1e3), "ms_per_solve": mspm,
+            "matrix_free_speedup": mspm / msp, "E_final": rrm[-1]["E_final"]}
+        gpp.close()
+        mp = synth.mesh_problem(7, seed=synth.BASE_SEED)
+        gmp = api.Problem(mp)
+        x0m = gmp.x.clone()
+        rr = []
+        for _ in range(3):
+            gmp.x.copy_(x0m)
+            rr.append(gmp.solve_lm(15, 30, lambda0=1e-3))
+        msm = statistics.median(r_["ms"] for r_ in rr)
+        extra["mesh_icosphere7_lm15x30"] = {"pcg_iters_per_s": rr[-1]["pcg_done"] / (msm / 1e3), "ms_per_solve": msm,
+                                           "accepted": rr[-1]["accepted"], "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
+        gmp.close()
 
-    extra["batched_512_warps_gn10x10"] = bench_batched(api, synth, torch, flush)
-    extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch)
+        extra["batched_512_warps_gn10x10"] = bench_batched(api, synth, torch, flush)
+        extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch)
 
     launches_per_step = 2 + OUTER * (2 + 2 * INNER)
     line = {
@@ -504,7 +517,7 @@ def run_ours(args):
         "clocks": clk.summary(),
         "also": extra,
     }
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_extras:
         line["cpu_baseline"] = oracle_sample()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -517,9 +530,12 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline workload only: skip the secondary workloads and the CPU baseline "
+                         "(for profiler runs; the timed region is unchanged)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

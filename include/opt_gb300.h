@@ -130,6 +130,13 @@ typedef struct {
     int32_t use_graph;        /* 1 = replay the solve as one CUDA graph (default) */
     int32_t tile_w;           /* grid planning only: tile width 32 or 128 (warp), 0 = automatic
                                  (128 for warps at least 256 pixels wide, else 32) */
+    int32_t persistent;       /* 1 = run each outer iteration's PCG loop as one cooperative
+                                 launch with grid-wide barriers when the problem is a wide-tile
+                                 warp, matrix-free, and all its blocks fit on the device at once;
+                                 0 (default) = one launch per PCG kernel, measured faster on
+                                 GB300 (a barrier costs more than a kernel boundary with
+                                 programmatic dependent launch).  Same arithmetic either way.  A
+                                 barrier wait is bounded (1 s): OPT_ERR_TIMEOUT. */
     void* stream;             /* cudaStream_t; NULL = legacy default stream */
 } opt_solve_params;
 
@@ -340,6 +347,16 @@ opt_status opt_warp_apply_jtj_noalloc(int32_t W, int32_t H, const float* x, cons
                                       const uint8_t* mask, const int32_t* handle_idx, int32_t n_handles,
                                       float w_reg, float w_fit, const float* p, float* q, double* pq,
                                       void* stream);
+
+/* Self-test of the bounded grid-wide barrier used by the persistent PCG loop
+ * (opt_solve_params.persistent).  Runs one cooperative launch of 2 blocks that
+ * meet at the barrier `rounds` times while the barrier awaits 2 + extra
+ * blocks.  extra = 0: a working barrier, *timed_out = 0.  extra > 0: the wait
+ * cannot complete; every block gives up after 50 ms, the launch ends and
+ * *timed_out = 1 (the bounded wait leaves the context usable).  Synchronous.
+ * OPT_ERR_INVALID_ARG for extra outside [0, 64], rounds outside [1, 1000] or a
+ * NULL pointer. */
+opt_status opt_selftest_grid_barrier(int32_t extra, int32_t rounds, int32_t* timed_out);
 
 /* Human-readable name of a status code; never NULL. */
 const char* opt_status_str(opt_status s);

@@ -41,7 +41,7 @@ class SolveParams(ctypes.Structure):
                 ("lambda_min", c_double), ("lambda_max", c_double), ("diag_min", c_double),
                 ("diag_max", c_double), ("eta", c_double), ("rel_tol", c_double),
                 ("use_precond", c_int32), ("materialized", c_int32), ("use_graph", c_int32),
-                ("tile_w", c_int32), ("stream", c_void_p)]
+                ("tile_w", c_int32), ("persistent", c_int32), ("stream", c_void_p)]
 
 
 class Report(ctypes.Structure):
@@ -83,6 +83,7 @@ _SIGNATURES = [
     ("opt_warp_apply_jtj_noalloc", c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                              c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p,
                                              c_void_p]),
+    ("opt_selftest_grid_barrier", c_int32, [c_int32, c_int32, POINTER(c_int32)]),
     ("opt_status_str", ctypes.c_char_p, [c_int32]),
     ("opt_last_error", ctypes.c_char_p, []),
 ]

@@ -258,17 +258,33 @@ opt_status check_params(const opt_solve_params& p, bool lm) {
 }
 
 // The whole solve as stream-ordered work (captured into a graph or run directly).
+// The PCG loop runs as one cooperative launch per outer iteration when asked
+// for, matrix-free, on wide warp tiles, and every chunk's block fits on the
+// device at once.
+bool use_persistent(const opt_problem* pb, const opt_solve_params& p) {
+  return p.persistent && !p.materialized && p.inner > 0 && pb->d_gbar && pb->nchunks <= pb->coop_cap;
+}
+
 opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cudaStream_t st) {
   const float dmin = (float)p.diag_min, dmax = (float)p.diag_max;
   CKS(copy_planes_in(pb, pb->x, pb->user_x, pb->nx, st));
   k_reset<<<1, 32, 0, st>>>(pb->d_s, 1, lm ? p.lambda0 : 0.0);
+  const bool coop = use_persistent(pb, p);
+  if (coop) CK(cudaMemsetAsync(pb->d_gbar, 0, sizeof(GridBarrier), st));
   for (int k = 0; k < p.outer; ++k) {
     st_init(pb, st, k, dmin, dmax);
     if (p.materialized) csr_evalj(pb, st);
-    for (int i = 0; i < p.inner; ++i) {
-      if (p.materialized) csr_apply(pb, st, i);
-      else st_apply(pb, st, nullptr, i, 1);
-      st_update(pb, st, i);
+    if (coop) {
+      // the barrier's counter restarts at 0 (a timed-out launch may leave it
+      // mid-count); its timeout flag accumulates over the solve
+      CK(cudaMemsetAsync(&pb->d_gbar->count, 0, sizeof(unsigned int), st));
+      CK(launch_grid_pcg_coop(grid_launch(pb, st), pb->d_gbar, 0, p.inner));
+    } else {
+      for (int i = 0; i < p.inner; ++i) {
+        if (p.materialized) csr_apply(pb, st, i);
+        else st_apply(pb, st, nullptr, i, 1);
+        st_update(pb, st, i);
+      }
     }
     if (!lm) {
       st_step(pb, st, 0);
@@ -286,7 +302,7 @@ opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cu
 
 std::vector<double> graph_key(const opt_solve_params& p, bool lm, cudaStream_t) {
   return {double(p.outer), double(p.inner), double(lm), double(p.use_precond), p.lambda0, p.lambda_min,
-          p.lambda_max, p.diag_min, p.diag_max, p.eta, p.rel_tol, double(p.materialized)};
+          p.lambda_max, p.diag_min, p.diag_max, p.eta, p.rel_tol, double(p.materialized), double(p.persistent)};
 }
 
 opt_status ensure_ehist(opt_problem* pb, int n) {
@@ -365,6 +381,11 @@ opt_status run_solve(opt_problem* pb, const opt_solve_params* prm_in, opt_report
     CK(cudaEventElapsedTime(&ms, pb->ev0, pb->ev1));
     rep->ms = ms;
   }
+  if (use_persistent(pb, p)) {
+    GridBarrier gb;
+    CK(cudaMemcpy(&gb, pb->d_gbar, sizeof(gb), cudaMemcpyDeviceToHost));
+    if (gb.timeout) return OPT_ERR_TIMEOUT;
+  }
   if (s.nonfinite) return OPT_ERR_NUMERIC;
   return OPT_OK;
 }
@@ -413,7 +434,23 @@ opt_status opt_solve_params_default(opt_solve_params* p) {
   p->use_precond = 1;
   p->materialized = 0;
   p->use_graph = 1;
+  p->persistent = 0;
   p->stream = nullptr;
+  return OPT_OK;
+}
+
+opt_status opt_selftest_grid_barrier(int32_t extra, int32_t rounds, int32_t* timed_out) {
+  if (!timed_out || extra < 0 || extra > 64 || rounds < 1 || rounds > 1000) return OPT_ERR_INVALID_ARG;
+  GridBarrier* gb = nullptr;
+  CK(cudaMalloc(&gb, sizeof(GridBarrier)));
+  GridBarrier h{};
+  cudaError_t e = cudaMemset(gb, 0, sizeof(GridBarrier));
+  if (e == cudaSuccess) e = launch_barrier_selftest(gb, 2, 2u + (unsigned)extra, rounds, 50000000ull, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, gb, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(gb);
+  if (e != cudaSuccess) return cuda_fail(e, "opt_selftest_grid_barrier");
+  *timed_out = h.timeout ? 1 : 0;
   return OPT_OK;
 }
 
@@ -542,7 +579,11 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   CKS(dalloc(q, &m, nm * pl));
   CKS(dalloc(q, &dc, nm * pl));
   float* csn = nullptr;
-  if (warp && tw == 128) CKS(dalloc(q, &csn, 2 * pl));
+  if (warp && tw == 128) {
+    CKS(dalloc(q, &csn, 2 * pl));
+    CKS(dalloc(q, &q->d_gbar, 1));
+    q->coop_cap = grid_coop_capacity(d->mask != nullptr);
+  }
   if (d->mask) {
     CKS(dalloc(q, &dmask, pl));
     CK(cudaMemcpy2D(dmask, P, d->mask, W, W, H, cudaMemcpyDeviceToDevice));

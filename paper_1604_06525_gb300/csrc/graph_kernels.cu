@@ -540,9 +540,14 @@ __global__ void __launch_bounds__(NT) k_mesh_step(const MeshProb* __restrict__ p
   if (cond && !pr.s->accept) return;
   if (!cond && pr.s->done) return;
   const long long pl = pr.Vp;
+  float* __restrict__ x = pr.x;
+  const float* __restrict__ d = pr.d;
   for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
+    float xv[6], dv[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) pr.x[c * pl + v] += pr.d[c * pl + v];
+    for (int c = 0; c < 6; ++c) { xv[c] = x[c * pl + v]; dv[c] = __ldg(d + c * pl + v); }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) x[c * pl + v] = xv[c] + dv[c];
   }
 }
 

@@ -448,15 +448,18 @@ __device__ __forceinline__ void wide_issue(WideSmem& sm, const WidePlanes& pp, c
       if (pp.src[k]) cp_async16(&sm.raw[k][row][4 + 4 * lane], pp.src[k] + i, ok);
     if (MASK) cp_async4(&sm.mk[row][16 + 4 * lane], pr.mask + i, ok);
   } else if (tid < 64 + 2 * TH) {
+    // halo columns: the aligned quad holding column -1 (x0-4 .. x0-1, staged
+    // at 0..3) or column 128 (x0+128 .. x0+131, staged at 132..135); x0 is a
+    // multiple of 128, so both quads lie inside the pitched row when valid
     const int h = tid - 64;
     const int row = 1 + (h % TH), side = h / TH;
-    const int gy = y0 + row - 1, cx = side ? x0 + W4 : x0 - 1;
-    const bool ok = gy < pr.H && cx >= 0 && cx < pr.W;
+    const int gy = y0 + row - 1, cx = side ? x0 + W4 : x0 - 4;
+    const bool ok = gy < pr.H && (side ? x0 + W4 < pr.W : x0 > 0);
     const long long i = ok ? (long long)gy * pr.P + cx : 0;
-    const int col = side ? 4 + W4 : 3;
+    const int col = side ? 4 + W4 : 0;
 #pragma unroll
     for (int k = 0; k < NRAW; ++k)
-      if (pp.src[k]) cp_async4(&sm.raw[k][row][col], pp.src[k] + i, ok);
+      if (pp.src[k]) cp_async16(&sm.raw[k][row][col], pp.src[k] + i, ok);
   }
   cp_async_commit();
 }
@@ -547,18 +550,12 @@ __device__ __forceinline__ void pair2(const Own2& o, float2 pxj, float2 pyj, flo
   at = fma2(mj, fma2(gix, tx, mul2(giy, ty)), at);
 }
 
+// One applyJTJ pass of the block's chunk (shared by the per-step kernel and
+// the persistent PCG kernel).
 template <bool MASK>
-__global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __restrict__ probs,
-                                                           const Chunk* __restrict__ chunks,
-                                                           const int* __restrict__ tiles,
-                                                           double* __restrict__ part,
-                                                           const float* __restrict__ p_in_override,
-                                                           int par, int update) {
-  pdl_begin();
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
-  WideSmem& sm = *reinterpret_cast<WideSmem*>(dyn_smem);
-  const Chunk ch = chunks[blockIdx.x];
-  const GridProb pr = probs[ch.prob];
+__device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, const GridProb& pr,
+                                                const int* __restrict__ tiles, double* __restrict__ part,
+                                                const float* __restrict__ p_in_override, int par, int update) {
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
   const int pl = (int)pr.plane;
@@ -740,6 +737,21 @@ __global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __res
       }
     }
   }
+}
+
+template <bool MASK>
+__global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __restrict__ probs,
+                                                           const Chunk* __restrict__ chunks,
+                                                           const int* __restrict__ tiles,
+                                                           double* __restrict__ part,
+                                                           const float* __restrict__ p_in_override,
+                                                           int par, int update) {
+  pdl_begin();
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  WideSmem& sm = *reinterpret_cast<WideSmem*>(dyn_smem);
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  apply_wide_body<MASK>(sm, ch, pr, tiles, part, p_in_override, par, update);
 }
 
 // Wide-tile warp PCGInit (tw = 128), staged with asynchronous copies like the
@@ -1464,15 +1476,14 @@ __global__ void __launch_bounds__(NT) k_poisson_energy(const GridProb* __restric
 // Float4 stream over the tile rows (a tile row is 32 floats = 128 B of each
 // plane; the pitch keeps rows 16-byte aligned and the pitch padding holds
 // zeros in every vector).  All loads of a quad are issued before any use.
+// One vector-update pass of the block's chunk (shared by the per-step kernel
+// and the persistent PCG kernel).  p and q were written earlier in the same
+// persistent launch, so they are read through L2 (ld.global.cg), not the
+// read-only path.
 template <int NX>
-__global__ void __launch_bounds__(NT) k_grid_update(const GridProb* __restrict__ probs,
-                                                    const Chunk* __restrict__ chunks,
-                                                    const int* __restrict__ tiles,
-                                                    double* __restrict__ part, int par) {
-  pdl_begin();
+__device__ __forceinline__ void update_body(const Chunk& ch, const GridProb& pr, const int* __restrict__ tiles,
+                                            double* __restrict__ part, int par) {
   constexpr int NM = NX == 3 ? 2 : 1;
-  const Chunk ch = chunks[blockIdx.x];
-  const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
   const long long pl4 = pr.plane / 4;
@@ -1487,8 +1498,11 @@ __global__ void __launch_bounds__(NT) k_grid_update(const GridProb* __restrict__
   const int qrow = pr.tw / 4;        // float4 quads per tile row
   const int QPT = qrow * TH;         // float4 quads per tile
   const int nq = (ch.end - ch.begin) * QPT;
+  // the tile index of the thread's next quad is loaded one step ahead
+  int tc_next = threadIdx.x < nq ? tiles[ch.begin + threadIdx.x / QPT] : 0;
   for (int k = threadIdx.x; k < nq; k += NT) {
-    const int tc = tiles[ch.begin + k / QPT];
+    const int tc = tc_next;
+    if (k + NT < nq) tc_next = tiles[ch.begin + (k + NT) / QPT];
     const int w = k % QPT;
     const int y = tile_y0(tc) + w / qrow;
     if (y >= pr.H) continue;
@@ -1496,8 +1510,8 @@ __global__ void __launch_bounds__(NT) k_grid_update(const GridProb* __restrict__
     float4 pv[NX], qv[NX], dv[NX], rv[NX], mv[NM];
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
-      pv[c] = __ldg(pn + c * pl4 + j);
-      qv[c] = __ldg(q4 + c * pl4 + j);
+      pv[c] = __ldcg(pn + c * pl4 + j);
+      qv[c] = __ldcg(q4 + c * pl4 + j);
       dv[c] = d4[c * pl4 + j];
       rv[c] = r4[c * pl4 + j];
     }
@@ -1533,6 +1547,41 @@ __global__ void __launch_bounds__(NT) k_grid_update(const GridProb* __restrict__
 
 // x += delta over the owned pixels (cond: 0 always, 1 only if s->accept).
 template <int NX>
+__global__ void __launch_bounds__(NT) k_grid_update(const GridProb* __restrict__ probs,
+                                                    const Chunk* __restrict__ chunks,
+                                                    const int* __restrict__ tiles,
+                                                    double* __restrict__ part, int par) {
+  pdl_begin();
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  update_body<NX>(ch, pr, tiles, part, par);
+}
+
+// Persistent PCG loop of the wide warp (tw = 128): n_inner iterations of
+// applyJTJ + vector update in one cooperative launch (every block resident),
+// separated by grid-wide barriers instead of kernel boundaries.  Block b
+// keeps chunk b for the whole loop, so the reductions are the same as those
+// of the per-step kernels.  A barrier that times out ends the launch early
+// with the barrier's timeout flag set.
+template <bool MASK>
+__global__ void __launch_bounds__(NT, 2) k_warp_pcg_coop(const GridProb* __restrict__ probs,
+                                                         const Chunk* __restrict__ chunks,
+                                                         const int* __restrict__ tiles,
+                                                         double* __restrict__ part, GridBarrier* gb,
+                                                         int par0, int n_inner) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  WideSmem& sm = *reinterpret_cast<WideSmem*>(dyn_smem);
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  for (int it = 0; it < n_inner; ++it) {
+    apply_wide_body<MASK>(sm, ch, pr, tiles, part, nullptr, par0 + it, 1);
+    if (!grid_sync(gb, gridDim.x)) return;
+    update_body<3>(ch, pr, tiles, part, par0 + it);
+    if (it + 1 < n_inner && !grid_sync(gb, gridDim.x)) return;
+  }
+}
+
+template <int NX>
 __global__ void __launch_bounds__(NT) k_grid_step(const GridProb* __restrict__ probs,
                                                   const Chunk* __restrict__ chunks,
                                                   const int* __restrict__ tiles, int cond) {
@@ -1542,17 +1591,28 @@ __global__ void __launch_bounds__(NT) k_grid_step(const GridProb* __restrict__ p
   if (cond && !pr.s->accept) return;
   if (!cond && pr.s->done) return;
   const long long pl = pr.plane;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  for (int t = ch.begin; t < ch.end; ++t) {
-    const int tc = tiles[t];
-    const int gy = tile_y0(tc) + ty;
-    for (int sx = tx; sx < pr.tw; sx += TW) {
-      const int gx = tile_x0(tc, pr.tw) + sx;
-      if (gx >= pr.W || gy >= pr.H) continue;
-      const long long i = (long long)gy * pr.P + gx;
+  float* __restrict__ x = pr.x;
+  const float* __restrict__ d = pr.d;
+  // float4 quads of the chunk's tiles; the pitched padding columns hold zeros
+  // in both planes, so only rows past H are skipped
+  const int qrow = pr.tw / 4, qpt = qrow * TH;
+  const int nq = (ch.end - ch.begin) * qpt;
+  for (int u = threadIdx.x; u < nq; u += NT) {
+    const int tc = tiles[ch.begin + u / qpt];
+    const int q = u % qpt;
+    const int gy = tile_y0(tc) + q / qrow;
+    if (gy >= pr.H) continue;
+    const long long i = (long long)gy * pr.P + tile_x0(tc, pr.tw) + 4 * (q % qrow);
+    float4 xv[NX], dv[NX];
 #pragma unroll
-      for (int c = 0; c < NX; ++c) pr.x[c * pl + i] += pr.d[c * pl + i];
+    for (int c = 0; c < NX; ++c) {
+      xv[c] = *reinterpret_cast<const float4*>(x + c * pl + i);
+      dv[c] = __ldg(reinterpret_cast<const float4*>(d + c * pl + i));
     }
+#pragma unroll
+    for (int c = 0; c < NX; ++c)
+      *reinterpret_cast<float4*>(x + c * pl + i) =
+          make_float4(xv[c].x + dv[c].x, xv[c].y + dv[c].y, xv[c].z + dv[c].z, xv[c].w + dv[c].w);
   }
 }
 
@@ -1582,6 +1642,14 @@ cudaError_t grid_kernels_prepare() {
       e = cudaFuncSetAttribute(k_warp_init_wide<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_warp_init_wide<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_pcg_coop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_pcg_coop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_pcg_coop<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_pcg_coop<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     status = e;
   });
   return status;
@@ -1632,6 +1700,57 @@ void launch_grid_step(int kind, const GridLaunch& L, int cond) {
     launch_pdl(k_grid_step<3>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, cond);
   else
     launch_pdl(k_grid_step<4>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, cond);
+}
+
+int grid_coop_capacity(int masked) {
+  if (grid_kernels_prepare() != cudaSuccess) return 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cudaError_t e = masked ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_warp_pcg_coop<true>, NT,
+                                                                          sizeof(WideSmem))
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_warp_pcg_coop<false>, NT,
+                                                                          sizeof(WideSmem));
+  return e == cudaSuccess ? per_sm * sms : 0;
+}
+
+cudaError_t launch_grid_pcg_coop(const GridLaunch& L, GridBarrier* gb, int par0, int n_inner) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(L.nchunks);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = sizeof(WideSmem);
+  cfg.stream = L.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return L.masked ? cudaLaunchKernelEx(&cfg, k_warp_pcg_coop<true>, L.probs, L.chunks, L.tiles, L.part, gb, par0,
+                                       n_inner)
+                  : cudaLaunchKernelEx(&cfg, k_warp_pcg_coop<false>, L.probs, L.chunks, L.tiles, L.part, gb, par0,
+                                       n_inner);
+}
+
+// Barrier self-test: `rounds` barriers among gridDim.x blocks that await
+// `expected` arrivals each; a block that times out stops.
+__global__ void k_barrier_selftest(GridBarrier* gb, unsigned int expected, int rounds,
+                                   unsigned long long limit_ns) {
+  for (int r = 0; r < rounds; ++r)
+    if (!grid_sync(gb, expected, limit_ns)) return;
+}
+
+cudaError_t launch_barrier_selftest(GridBarrier* gb, int nblocks, unsigned int expected, int rounds,
+                                    unsigned long long limit_ns, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(NT);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_barrier_selftest, gb, expected, rounds, limit_ns);
 }
 
 }  // namespace optgb

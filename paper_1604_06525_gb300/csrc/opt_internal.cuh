@@ -141,6 +141,69 @@ __device__ __forceinline__ void pdl_begin() {
 }
 
 // ---------------------------------------------------------------------------
+// grid-wide barrier of a cooperative launch (all blocks co-resident)
+// ---------------------------------------------------------------------------
+// Every wait is bounded: a block that has waited longer than limit_ns sets
+// `timeout` and the barrier reports failure, so the kernel returns instead
+// of hanging; the host turns the flag into OPT_ERR_TIMEOUT.  count returns to
+// 0 at every completed barrier; the host clears the struct before a launch.
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+  int timeout;
+  int pad;
+};
+
+constexpr unsigned long long kBarrierLimitNs = 1000000000ull;   // 1 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Must be called by every thread of every block of the launch; `expected` is
+// the number of blocks that take part (gridDim.x).  Returns false on timeout.
+__device__ __forceinline__ bool grid_sync(GridBarrier* gb, unsigned int expected,
+                                          unsigned long long limit_ns = kBarrierLimitNs) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int g = ld_acquire_u32(&gb->gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&gb->count, 1u) + 1u;
+    if (arrived == expected) {
+      gb->count = 0u;
+      __threadfence();
+      st_release_u32(&gb->gen, g + 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_u32(&gb->gen) == g) {
+        if (global_ns() - t0 > limit_ns) {
+          atomicExch(&gb->timeout, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {

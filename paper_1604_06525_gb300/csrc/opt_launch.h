@@ -51,6 +51,13 @@ void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, i
 void launch_grid_update(int kind, const GridLaunch& L, int par);
 void launch_grid_energy(int kind, const GridLaunch& L, int mode, int hist_idx);
 void launch_grid_step(int kind, const GridLaunch& L, int cond);
+// Persistent PCG loop (wide warp tiles only): the largest chunk count whose
+// blocks are all resident at once (0 if unknown), and the cooperative launch
+// of n_inner PCG iterations (applyJTJ + update) starting at parity par0.
+int grid_coop_capacity(int masked);
+cudaError_t launch_grid_pcg_coop(const GridLaunch& L, GridBarrier* gb, int par0, int n_inner);
+cudaError_t launch_barrier_selftest(GridBarrier* gb, int nblocks, unsigned int expected, int rounds,
+                                    unsigned long long limit_ns, cudaStream_t st);
 
 // graph_kernels.cu
 void launch_mesh_init(const MeshLaunch& L, int k_outer, float dmin, float dmax);

@@ -74,6 +74,10 @@ struct opt_problem {
   float* qvec = nullptr;
   std::vector<void*> allocs;
   int pcg_par = 0;
+  // persistent PCG loop (wide warps): grid barrier state and the number of
+  // blocks that can be resident at once (0 = not available)
+  optgb::GridBarrier* d_gbar = nullptr;
+  int coop_cap = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<double> gkey;

@@ -431,3 +431,26 @@ def test_chunking_and_autotune_keep_results(api, kind):
     r = a.solve_gn(3, 8)
     for x, y in zip(r["E_history"], ref["E_history"]):
         assert relE(x, y) <= 1e-6
+
+
+@pytest.mark.parametrize("W,H,mf,method,graph", [(1024, 1024, 0.0, "gn", 1), (700, 300, 0.2, "lm", 1),
+                                                 (260, 20, 0.0, "lm", 0)])
+def test_persistent_pcg_equals_per_step_launches(api, W, H, mf, method, graph):
+    """The persistent PCG loop (one cooperative launch per outer iteration,
+    grid-wide barriers) runs the same arithmetic in the same order as one
+    launch per PCG kernel: identical energies, PCG counts and unknowns."""
+    mask = synth.random_mask(W, H, mf, 3) if mf else None
+    prob = synth.warp_problem(W, H, synth.warp_handle_count(W, H), seed=161, mask=mask)
+    a, b = api.Problem(prob), api.Problem(prob)
+    ra = getattr(a, f"solve_{method}")(4, 12, persistent=1, use_graph=graph)
+    rb = getattr(b, f"solve_{method}")(4, 12, persistent=0, use_graph=graph)
+    assert ra["status"] == rb["status"] == "OPT_OK"
+    assert ra["E_history"] == rb["E_history"]
+    assert ra["pcg_done"] == rb["pcg_done"] and ra["accepted"] == rb["accepted"]
+    assert np.array_equal(a.x.cpu().numpy(), b.x.cpu().numpy())
+    # and against the oracle
+    e = oracle.make_energy(prob)
+    x0 = prob.x0.reshape(-1)
+    ref = (oracle.gauss_newton(e, x0, 4, 12) if method == "gn" else oracle.levenberg_marquardt(e, x0, 4, 12))
+    for x, y in zip(ra["E_history"], ref.E_history):
+        assert relE(x, y) <= TOL_ENERGY
