@@ -38,6 +38,17 @@ W_BENCH, H_BENCH, HANDLES, OUTER, INNER = 1024, 1024, 64, 20, 20
 BYTES_APPLY_WARP = 72      # read r 12, M^-1 8, p_old 12, cos/sin 8, UrShape 8; write p 12, q 12
 BYTES_UPDATE_WARP = 80     # read delta 12, p 12, r 12, q 12, M^-1 8; write delta 12, r 12
 BYTES_INIT_WARP = 60       # read x 12, UrShape 8; write r 12, M^-1 8, delta 12, cos/sin 8 (GN)
+# Poisson, per free pixel (4 channels, one M^-1 plane)
+BYTES_APPLY_POISSON = 69   # read r 16, M^-1 4, p_old 16, mask 1; write p 16, q 16
+BYTES_UPDATE_POISSON = 100  # read delta 16, p 16, r 16, q 16, M^-1 4; write delta 16, r 16
+BYTES_INIT_POISSON = 69    # read X 16, T 16, mask 1; write r 16, M^-1 4, delta 16 (GN)
+# ARAP mesh, per vertex (6 unknowns, 6 directed edges per vertex on an icosphere)
+BYTES_APPLY_MESH = 268     # vertex pass: read r 24, M^-1 16, p_old 24; write p 24, q 24 (112);
+#                            edge pass: (v0, v1) 6 x 8, U 12, cos/sin 24, p 24, q read + write 48 (156)
+BYTES_UPDATE_MESH = 160    # read delta 24, p 24, r 24, q 24, M^-1 16; write delta 24, r 24
+BYTES_INIT_MESH = 356      # vertex pass: read angles 12; write JtF 24, acc 12, cos/sin 24 (72);
+#                            edge pass: (v0, v1) 48, U 12, x 24, cos/sin 24, JtF and acc read + write 72 (180);
+#                            final pass: read degree 4, acc 12, JtF 24; write M^-1 16, r 24, delta 24 (104)
 KERNEL_SOURCES = ("grid_kernels.cu", "opt_internal.cuh", "opt_launch.h")
 L2_FLUSH_BYTES = 512 << 20
 
@@ -189,28 +200,65 @@ def run_reference(args):
     return 0
 
 
-def roofline_for(api, synth, torch, W, H, peak, iters=20):
-    """Live timing of the matrix-free kernels on a W x H warp (CUDA events on
-    the launching stream, mean over `iters` launches)."""
-    prob = synth.warp_problem(W, H, max(8, int(round(64.0 * W * H / 2 ** 20))), seed=synth.BASE_SEED)
-    gp = api.Problem(prob)
+def kernel_roofline(gp, kernels, units, peak, iters=20):
+    """Live timing of a problem's PCG kernels (CUDA events on the launching
+    stream, mean over `iters` launches) after autotuning its granularity.
+    kernels: (name, algorithmic bytes per unit, launches per solve) for the
+    init, apply and update passes, in that order."""
     gp.autotune()
     gp.profile_pcg(3)
-    ms_init, ms_apply, ms_update = gp.profile_pcg(iters)
-    px = W * H
+    times = gp.profile_pcg(iters)
     out = {}
-    wide = W >= 256                      # 128-pixel tiles (k_warp_*_wide) from 256 pixels up
-    for name, ms, bpp, per_solve in (
-            ("k_warp_apply_wide" if wide else "k_warp_apply", ms_apply, BYTES_APPLY_WARP, OUTER * INNER),
-            ("k_grid_update<3>", ms_update, BYTES_UPDATE_WARP, OUTER * INNER),
-            ("k_warp_init_wide" if wide else "k_warp_init", ms_init, BYTES_INIT_WARP, OUTER)):
-        ach = bpp * px / (ms * 1e-3) / 1e9
-        out[name] = {"ms": ms, "bytes": bpp * px, "achieved": ach, "frac": ach / peak,
+    for (name, bpu, per_solve), ms in zip(kernels, times):
+        ach = bpu * units / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "bytes": bpu * units, "achieved": ach, "frac": ach / peak,
                      "launches_per_solve": per_solve}
+    return out
+
+
+def roofline_for(api, synth, torch, W, H, peak, iters=20):
+    """Per-kernel roofline of the matrix-free ARAP warp at W x H."""
+    prob = synth.warp_problem(W, H, max(8, int(round(64.0 * W * H / 2 ** 20))), seed=synth.BASE_SEED)
+    gp = api.Problem(prob)
+    wide = W >= 256                      # 128-pixel tiles (k_warp_*_wide) from 256 pixels up
+    out = kernel_roofline(gp, (("k_warp_init_wide" if wide else "k_warp_init", BYTES_INIT_WARP, OUTER),
+                               ("k_warp_apply_wide" if wide else "k_warp_apply", BYTES_APPLY_WARP, OUTER * INNER),
+                               ("k_grid_update<3>", BYTES_UPDATE_WARP, OUTER * INNER)), W * H, peak, iters)
     gp.close()
     del prob
     torch.cuda.empty_cache()
-    return out, ms_init
+    return out, out[next(iter(out))]["ms"]
+
+
+def roofline_beyond_l2(api, synth, torch, peak):
+    """The added sizes well beyond L2 (where the HBM-fraction target is
+    judged): ARAP warp 4096^2, Poisson 4096^2 x 4 (free pixels), icosphere
+    level 9 (vertices)."""
+    res = {}
+    warp, _ = roofline_for(api, synth, torch, 4096, 4096, peak)
+    res["warp_4096x4096"] = {"unit_of_work": "pixel", "units": 4096 * 4096, "kernels": warp}
+    pp = synth.poisson_problem(4096, 4096, seed=synth.BASE_SEED)
+    free = int((pp.mask == 0).sum())
+    gp = api.Problem(pp)
+    res["poisson_4096x4096x4"] = {
+        "unit_of_work": "free pixel", "units": free,
+        "kernels": kernel_roofline(gp, (("k_poisson_init", BYTES_INIT_POISSON, OUTER),
+                                        ("k_poisson_apply", BYTES_APPLY_POISSON, OUTER * INNER),
+                                        ("k_grid_update<4>", BYTES_UPDATE_POISSON, OUTER * INNER)), free, peak)}
+    gp.close()
+    del pp
+    torch.cuda.empty_cache()
+    mp = synth.mesh_problem(9, seed=synth.BASE_SEED)
+    gp = api.Problem(mp)
+    res["mesh_icosphere9"] = {
+        "unit_of_work": "vertex", "units": mp.V, "directed_edges": int(len(mp.v0)),
+        "kernels": kernel_roofline(gp, (("k_mesh_init_v+e+f", BYTES_INIT_MESH, 15),
+                                        ("k_mesh_apply_v+e", BYTES_APPLY_MESH, 15 * 30),
+                                        ("k_mesh_update", BYTES_UPDATE_MESH, 15 * 30)), mp.V, peak)}
+    gp.close()
+    del mp
+    torch.cuda.empty_cache()
+    return res
 
 
 def aggregate_replicas(dev_ms: float, pcg_done: int, world: int, device=None):
@@ -448,7 +496,7 @@ def run_ours(args):
     dom = max(roof, key=lambda k: roof[k]["ms"] * roof[k]["launches_per_solve"])   # largest share of a solve
     roof_big, extra = {}, {}
     if not args.no_extras:
-        roof_big, _ = roofline_for(api, synth, torch, 4096, 4096, peak)
+        roof_big = roofline_beyond_l2(api, synth, torch, peak)
 
         # secondary workloads: matrix-free vs materialized J (Sec. 8.3) on the
         # warp and on Poisson editing at 1024 x 1024, then the mesh under LM
@@ -511,7 +559,8 @@ def run_ours(args):
                      "traffic": ncu_traffic(dom, "warp1024"),
                      "algorithmic_bytes_per_launch": roof[dom]["bytes"], "ms_per_launch": roof[dom]["ms"],
                      "peak_source": f"{peak_src} hbm_gbs", "kernels": roof},
-        "roofline_4096": {"bound": "hbm", "peak": peak, "unit": "GB/s", "kernels": roof_big},
+        "roofline_beyond_l2": {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": f"{peak_src} hbm_gbs",
+                               "workloads": roof_big},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
@@ -527,6 +576,36 @@ def run_ours(args):
     return 0
 
 
+PROFILE_CASES = {
+    # name: (builder, description); small enough for ncu --set full (a few GB
+    # on the device at most) and larger than L2
+    "warp2048": (lambda synth: synth.warp_problem(2048, 2048, 256, seed=synth.BASE_SEED), "ARAP warp 2048^2"),
+    "poisson2048": (lambda synth: synth.poisson_problem(2048, 2048, seed=synth.BASE_SEED), "Poisson 2048^2 x 4"),
+    "mesh8": (lambda synth: synth.mesh_problem(8, seed=synth.BASE_SEED), "ARAP mesh, icosphere level 8"),
+}
+
+
+def run_profile_case(name):
+    """One autotuned problem, its PCGInit once and three PCG iterations (the
+    launches an ncu capture selects from); prints the per-kernel times."""
+    import torch
+    from paper_1604_06525_gb300 import build, api, synth
+    build.build()
+    api.load_library()
+    builder, desc = PROFILE_CASES[name]
+    gp = api.Problem(builder(synth))
+    chunking, _ = gp.autotune()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("profile")
+    ms = gp.profile_pcg(3)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_case": name, "workload": desc, "chunking": chunking,
+                      "ms_init_apply_update": ms}), flush=True)
+    gp.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -536,7 +615,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="headline workload only: skip the secondary workloads and the CPU baseline "
                          "(for profiler runs; the timed region is unchanged)")
+    ap.add_argument("--profile", choices=sorted(PROFILE_CASES),
+                    help="run one small profiling workload (for ncu captures) instead of the benchmark")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile_case(args.profile)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
