@@ -169,7 +169,8 @@ class PoissonEnergy(_Energy):
         self.W, self.H, self.n = W, H, W * H
         self.N = 4 * self.n
         self.T = prob.guide.reshape(4, -1).astype(np.float64)
-        free = prob.mask.reshape(-1) == 0
+        # no mask: nothing is excluded, every pixel is free
+        free = np.ones(self.n, bool) if prob.mask is None else prob.mask.reshape(-1) == 0
         self.free = free
         ys, xs = np.mgrid[0:H, 0:W]
         ks, js = [], []

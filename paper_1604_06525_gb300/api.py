@@ -167,7 +167,7 @@ def make_descriptor(prob, device):
         else:
             d.kind = OPT_POISSON_2D
             consts = f32(prob.guide)
-            mask = torch.as_tensor(prob.mask, dtype=torch.uint8, device=dev)
+            mask = None if prob.mask is None else torch.as_tensor(prob.mask, dtype=torch.uint8, device=dev)
             d.n_handles = 0
             nx, nc = 4, 4
         for c in range(nx):

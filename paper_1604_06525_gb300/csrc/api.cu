@@ -478,11 +478,11 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   if (d->W < 1 || d->H < 1 || d->W >= 32768 || d->H >= 32768) return OPT_ERR_INVALID_ARG;
   const bool warp = d->kind == OPT_ARAP_WARP_2D;
   const int nx = warp ? 3 : 4, nc = warp ? 2 : 4, nm = warp ? 2 : 1;
-  // tile width: 128-pixel tiles (float4 rows) for warps at least 256 wide,
-  // 32-pixel tiles otherwise; Poisson always uses 32
+  // tile width: 128-pixel tiles (float4 rows) for grids at least 256 wide,
+  // 32-pixel tiles otherwise
   const int req_tw = prm ? prm->tile_w : 0;
   if (req_tw != 0 && req_tw != 32 && req_tw != 128) return OPT_ERR_INVALID_ARG;
-  const int tw = !warp ? 32 : (req_tw ? req_tw : (d->W >= 256 ? 128 : 32));
+  const int tw = req_tw ? req_tw : (d->W >= 256 ? 128 : 32);
   for (int c = 0; c < nx; ++c)
     if (!d->unknowns[c]) return OPT_ERR_INVALID_ARG;
   for (int c = 0; c < nc; ++c)
@@ -493,7 +493,7 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   if (warp && (!std::isfinite(d->w_reg) || !std::isfinite(d->w_fit) || d->w_reg < 0.f || d->w_fit < 0.f))
     return OPT_ERR_INVALID_ARG;
 
-  if (warp && tw == 128) CK(grid_kernels_prepare());
+  if (tw == 128) CK(grid_kernels_prepare());
   std::unique_ptr<opt_problem> pb(new opt_problem());
   pb->kind = warp ? K_WARP : K_POISSON;
   pb->nx = nx;

@@ -421,22 +421,29 @@ struct WidePlanes {
   const float* src[NRAW];        // plane base pointers (nullptr: not needed this launch)
 };
 
-// Issues the copies of one tile: quads (own rows by every thread, the two
-// halo rows by threads 0..63) and the halo columns (threads 64..79).
-template <bool MASK>
-__device__ __forceinline__ void wide_issue(WideSmem& sm, const WidePlanes& pp, const GridProb& pr, int x0, int y0,
-                                           int tid) {
+// Issues the copies of one 128 x 8 tile with its halo into raw[NR][HH][SP]
+// (column x0 + k at 4 + k): quads of the own rows by every thread, of the two
+// halo rows by threads 0..63, and the halo columns by threads 64..79 as the
+// aligned quad holding column -1 (x0-4 .. x0-1, staged at 0..3) or column
+// 128 (x0+128 .. x0+131, staged at 132..135); x0 is a multiple of 128, so
+// both quads lie inside the pitched row when valid.  Rows / columns outside
+// the grid are zero-filled.  src[k] == nullptr skips plane k.  The mask bytes
+// of the own / halo rows land at mk[row][16 + k], those of the halo columns
+// as the aligned 4-byte words around them (column -1 at mk[row][15], column
+// 128 at mk[row][144]).
+template <int NR, bool MASK>
+__device__ __forceinline__ void tile_issue(float (*raw)[HH][SP], unsigned char (*mk)[SPB],
+                                           const float* const* src, const GridProb& pr, int x0, int y0, int tid) {
   const int lane = tid & 31, ty = tid >> 5;
   const int gx = x0 + 4 * lane;
-  // own row
   {
     const int gy = y0 + ty;
     const bool ok = gy < pr.H;
     const long long i = ok ? (long long)gy * pr.P + gx : 0;
 #pragma unroll
-    for (int k = 0; k < NRAW; ++k)
-      if (pp.src[k]) cp_async16(&sm.raw[k][ty + 1][4 + 4 * lane], pp.src[k] + i, ok);
-    if (MASK) cp_async4(&sm.mk[ty + 1][16 + 4 * lane], pr.mask + i, ok);
+    for (int k = 0; k < NR; ++k)
+      if (src[k]) cp_async16(&raw[k][ty + 1][4 + 4 * lane], src[k] + i, ok);
+    if (MASK) cp_async4(&mk[ty + 1][16 + 4 * lane], pr.mask + i, ok);
   }
   if (tid < 64) {
     const int row = tid < 32 ? 0 : HH - 1;
@@ -444,13 +451,10 @@ __device__ __forceinline__ void wide_issue(WideSmem& sm, const WidePlanes& pp, c
     const bool ok = gy >= 0 && gy < pr.H;
     const long long i = ok ? (long long)gy * pr.P + gx : 0;
 #pragma unroll
-    for (int k = 0; k < NRAW; ++k)
-      if (pp.src[k]) cp_async16(&sm.raw[k][row][4 + 4 * lane], pp.src[k] + i, ok);
-    if (MASK) cp_async4(&sm.mk[row][16 + 4 * lane], pr.mask + i, ok);
+    for (int k = 0; k < NR; ++k)
+      if (src[k]) cp_async16(&raw[k][row][4 + 4 * lane], src[k] + i, ok);
+    if (MASK) cp_async4(&mk[row][16 + 4 * lane], pr.mask + i, ok);
   } else if (tid < 64 + 2 * TH) {
-    // halo columns: the aligned quad holding column -1 (x0-4 .. x0-1, staged
-    // at 0..3) or column 128 (x0+128 .. x0+131, staged at 132..135); x0 is a
-    // multiple of 128, so both quads lie inside the pitched row when valid
     const int h = tid - 64;
     const int row = 1 + (h % TH), side = h / TH;
     const int gy = y0 + row - 1, cx = side ? x0 + W4 : x0 - 4;
@@ -458,10 +462,22 @@ __device__ __forceinline__ void wide_issue(WideSmem& sm, const WidePlanes& pp, c
     const long long i = ok ? (long long)gy * pr.P + cx : 0;
     const int col = side ? 4 + W4 : 0;
 #pragma unroll
-    for (int k = 0; k < NRAW; ++k)
-      if (pp.src[k]) cp_async16(&sm.raw[k][row][col], pp.src[k] + i, ok);
+    for (int k = 0; k < NR; ++k)
+      if (src[k]) cp_async16(&raw[k][row][col], src[k] + i, ok);
+    if (MASK) cp_async4(&mk[row][side ? 16 + W4 : 12], pr.mask + i, ok);
   }
   cp_async_commit();
+}
+
+// mask byte of the staged halo column (side 0: column -1, side 1: column 128)
+__device__ __forceinline__ unsigned char halo_mask(const unsigned char (*mk)[SPB], int row, int side) {
+  return mk[row][side ? 16 + W4 : 15];
+}
+
+template <bool MASK>
+__device__ __forceinline__ void wide_issue(WideSmem& sm, const WidePlanes& pp, const GridProb& pr, int x0, int y0,
+                                           int tid) {
+  tile_issue<NRAW, MASK>(sm.raw, sm.mk, pp.src, pr, x0, y0, tid);
 }
 
 // Packed float32 pairs (one instruction for two lanes of a float2).  All are
@@ -622,7 +638,7 @@ __device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, c
       for (int k = 0; k < 4; ++k) sm.stg[3 + k][row][col] = sm.raw[8 + k][row][col];
       const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
       const bool ok = hy < pr.H && hx >= 0 && hx < pr.W;
-      sm.stg[7][row][col] = (ok && (!MASK || __ldg(pr.mask + (long long)hy * pr.P + hx) == 0)) ? 1.f : 0.f;
+      sm.stg[7][row][col] = (ok && (!MASK || halo_mask(sm.mk, row, side) == 0)) ? 1.f : 0.f;
     }
     __syncthreads();
     // the raw buffer is free: start the next tile's copies
@@ -777,39 +793,14 @@ struct InitSmem {
   unsigned char vc[HH][2];
 };
 
+struct InitPlanes {
+  const float* src[NRAW_I];      // dx, dy, theta, UrShape x, y
+};
+
 template <bool MASK>
-__device__ __forceinline__ void init_issue(InitSmem& sm, const GridProb& pr, int x0, int y0, int tid) {
-  const int lane = tid & 31, ty = tid >> 5;
-  const int gx = x0 + 4 * lane;
-  const int pl = (int)pr.plane;
-  const float* src[NRAW_I] = {pr.x, pr.x + pl, pr.x + 2 * pl, pr.c, pr.c + pl};
-  {
-    const int gy = y0 + ty;
-    const bool ok = gy < pr.H;
-    const long long i = ok ? (long long)gy * pr.P + gx : 0;
-#pragma unroll
-    for (int k = 0; k < NRAW_I; ++k) cp_async16(&sm.raw[k][ty + 1][4 + 4 * lane], src[k] + i, ok);
-    if (MASK) cp_async4(&sm.mk[ty + 1][16 + 4 * lane], pr.mask + i, ok);
-  }
-  if (tid < 64) {
-    const int row = tid < 32 ? 0 : HH - 1;
-    const int gy = y0 - 1 + row;
-    const bool ok = gy >= 0 && gy < pr.H;
-    const long long i = ok ? (long long)gy * pr.P + gx : 0;
-#pragma unroll
-    for (int k = 0; k < NRAW_I; ++k) cp_async16(&sm.raw[k][row][4 + 4 * lane], src[k] + i, ok);
-    if (MASK) cp_async4(&sm.mk[row][16 + 4 * lane], pr.mask + i, ok);
-  } else if (tid < 64 + 2 * TH) {
-    const int h = tid - 64;
-    const int row = 1 + (h % TH), side = h / TH;
-    const int gy = y0 + row - 1, cx = side ? x0 + W4 : x0 - 1;
-    const bool ok = gy < pr.H && cx >= 0 && cx < pr.W;
-    const long long i = ok ? (long long)gy * pr.P + cx : 0;
-    const int col = side ? 4 + W4 : 3;
-#pragma unroll
-    for (int k = 0; k < NRAW_I; ++k) cp_async4(&sm.raw[k][row][col], src[k] + i, ok);
-  }
-  cp_async_commit();
+__device__ __forceinline__ void init_issue(InitSmem& sm, const InitPlanes& pp, const GridProb& pr, int x0, int y0,
+                                           int tid) {
+  tile_issue<NRAW_I, MASK>(sm.raw, sm.mk, pp.src, pr, x0, y0, tid);
 }
 
 // Phase 2 for one staged quad: cos / sin, copied values, validity bits.
@@ -887,8 +878,13 @@ __global__ void __launch_bounds__(NT, 2) k_warp_init_wide(const GridProb* __rest
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   float acc_rz = 0.f, acc_E = 0.f;
+  InitPlanes ip;
+  {
+    const int ipl = (int)pr.plane;
+    ip.src[0] = pr.x; ip.src[1] = pr.x + ipl; ip.src[2] = pr.x + 2 * ipl; ip.src[3] = pr.c; ip.src[4] = pr.c + ipl;
+  }
   int tc = tiles[ch.begin];
-  init_issue<MASK>(sm, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+  init_issue<MASK>(sm, ip, pr, tile_x0(tc, W4), tile_y0(tc), tid);
   for (int t = ch.begin; t < ch.end; ++t) {
     const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
     const int gx = x0 + 4 * lane, gy = y0 + ty;
@@ -913,12 +909,12 @@ __global__ void __launch_bounds__(NT, 2) k_warp_init_wide(const GridProb* __rest
       sm.stg[5][row][col] = sm.raw[4][row][col];
       const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
       const bool ok = hy < pr.H && hx >= 0 && hx < pr.W;
-      sm.vc[row][side] = (unsigned char)(ok && (!MASK || __ldg(pr.mask + (long long)hy * pr.P + hx) == 0));
+      sm.vc[row][side] = (unsigned char)(ok && (!MASK || halo_mask(sm.mk, row, side) == 0));
     }
     __syncthreads();
     if (t + 1 < ch.end) {
       tc = tiles[t + 1];
-      init_issue<MASK>(sm, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+      init_issue<MASK>(sm, ip, pr, tile_x0(tc, W4), tile_y0(tc), tid);
     }
     if (gy < pr.H) {
       Quad6 O;
@@ -1393,6 +1389,369 @@ __global__ void __launch_bounds__(NT, 3) k_poisson_apply(const GridProb* __restr
   }
 }
 
+// ---------------------------------------------------------------------------
+// Wide-tile Poisson kernels (tw = 128), staged like the wide warp apply.
+// Per channel the J^T J row of a free pixel i is q_i = sum_j w_j (p_i - p_j)
+// with w_j = 2 for a free neighbour (own + incoming residual), 1 for a fixed
+// one (own residual only; p_j = 0 there) and 0 outside the grid, i.e.
+// q_i = S_i p_i - sum_j w_j p_j with S_i = sum_j w_j = diag(J^T J)_i.  With
+// Y = X - T every residual is r_(i,j) = Y_i - Y_j, so PCGInit is the same
+// stencil on Y: J^T F_i = S_i Y_i - sum_j w_j Y_j, E += sum_(j in grid)
+// (Y_i - Y_j)^2 over free i.  The staged weight plane holds w (0 / 1 / 2).
+// ---------------------------------------------------------------------------
+constexpr int NRAW_PA = 9;       // r0..r3, M^-1, p_old0..p_old3
+constexpr int NRAW_PI = 8;       // X0..X3, T0..T3
+constexpr int NSTG_P = 5;        // 4 channels + weight, quads stored as pixels 0 2 1 3
+
+struct PoisWideSmem {
+  float raw[NRAW_PA][HH][SP];
+  float stg[NSTG_P][HH][SP];
+  unsigned char mk[HH][SPB];
+};
+
+// weight of the staged pixel (gx, gy): 0 outside the grid, 1 fixed, 2 free
+template <bool MASK>
+__device__ __forceinline__ float4 pois_weights(const PoisWideSmem& sm, int row, int lane, const GridProb& pr,
+                                               int gx, int gy) {
+  float w[4] = {0.f, 0.f, 0.f, 0.f};
+  if (gy >= 0 && gy < pr.H) {
+    const unsigned int m4 = MASK ? *reinterpret_cast<const unsigned int*>(&sm.mk[row][16 + 4 * lane]) : 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (gx + k < pr.W) w[k] = (!MASK || ((m4 >> (8 * k)) & 0xffu) == 0u) ? 2.f : 1.f;
+  }
+  return make_float4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ float4 free01(const float4& w) {
+  return make_float4(w.x > 1.5f ? 1.f : 0.f, w.y > 1.5f ? 1.f : 0.f, w.z > 1.5f ? 1.f : 0.f, w.w > 1.5f ? 1.f : 0.f);
+}
+
+// Weighted neighbour sums of one float2 pack for the 4 channels:
+// out_c = S p_c - sum_j w_j p_(j,c), with (w_j, p_j) of the 4 neighbours.
+struct Nb5 {
+  float2 v[NSTG_P];
+};
+
+// Phase 3 of the wide Poisson kernels: the stencil on the own quad of the
+// warp's row.  O: own staged values (swizzled), lane 0 / 31 take the halo
+// columns.  Returns, per pack (A = pixels {0, 2}, B = {1, 3}) and channel,
+// S v_i - sum_j w_j v_j, and (init only) the own-residual energy sum.
+template <bool ENERGY>
+__device__ __forceinline__ void pois_stencil(const PoisWideSmem& sm, int ty, int lane, const float4 (&O)[NSTG_P],
+                                             float2 (&outA)[4], float2 (&outB)[4], float2& SA, float2& SB,
+                                             float2& eA, float2& eB) {
+  const int c = 4 + 4 * lane;
+  float L[NSTG_P], R[NSTG_P];
+#pragma unroll
+  for (int k = 0; k < NSTG_P; ++k) {
+    L[k] = __shfl_up_sync(0xffffffffu, O[k].w, 1);
+    R[k] = __shfl_down_sync(0xffffffffu, O[k].x, 1);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NSTG_P; ++k) L[k] = sm.stg[k][ty + 1][3];
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int k = 0; k < NSTG_P; ++k) R[k] = sm.stg[k][ty + 1][4 + W4];
+  }
+  float4 U[NSTG_P], D[NSTG_P];
+#pragma unroll
+  for (int k = 0; k < NSTG_P; ++k) {
+    U[k] = lds4(&sm.stg[k][ty][c]);
+    D[k] = lds4(&sm.stg[k][ty + 2][c]);
+  }
+  // neighbour packs: A left {-1, 1}, right {1, 3}; B left {0, 2}, right {2, 4}
+  Nb5 aL, aR, bL, bR, aU, aD, bU, bD;
+#pragma unroll
+  for (int k = 0; k < NSTG_P; ++k) {
+    aL.v[k] = make_float2(L[k], O[k].z);
+    aR.v[k] = hi2(O[k]);
+    bL.v[k] = lo2(O[k]);
+    bR.v[k] = make_float2(O[k].y, R[k]);
+    aU.v[k] = lo2(U[k]);
+    aD.v[k] = lo2(D[k]);
+    bU.v[k] = hi2(U[k]);
+    bD.v[k] = hi2(D[k]);
+  }
+  SA = add2(add2(aL.v[4], aR.v[4]), add2(aU.v[4], aD.v[4]));
+  SB = add2(add2(bL.v[4], bR.v[4]), add2(bU.v[4], bD.v[4]));
+#pragma unroll
+  for (int ch = 0; ch < 4; ++ch) {
+    const float2 nA = fma2(aL.v[4], aL.v[ch], fma2(aR.v[4], aR.v[ch], fma2(aU.v[4], aU.v[ch], mul2(aD.v[4], aD.v[ch]))));
+    const float2 nB = fma2(bL.v[4], bL.v[ch], fma2(bR.v[4], bR.v[ch], fma2(bU.v[4], bU.v[ch], mul2(bD.v[4], bD.v[ch]))));
+    outA[ch] = sub2(mul2(SA, lo2(O[ch])), nA);
+    outB[ch] = sub2(mul2(SB, hi2(O[ch])), nB);
+  }
+  if (ENERGY) {
+    // own residuals towards every in-grid neighbour (weight > 0)
+    eA = make_float2(0.f, 0.f);
+    eB = make_float2(0.f, 0.f);
+    const Nb5* na[4] = {&aL, &aR, &aU, &aD};
+    const Nb5* nb[4] = {&bL, &bR, &bU, &bD};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const float2 ma = make_float2(na[d]->v[4].x > 0.5f ? 1.f : 0.f, na[d]->v[4].y > 0.5f ? 1.f : 0.f);
+      const float2 mb = make_float2(nb[d]->v[4].x > 0.5f ? 1.f : 0.f, nb[d]->v[4].y > 0.5f ? 1.f : 0.f);
+      float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) {
+        const float2 da = sub2(lo2(O[ch]), na[d]->v[ch]);
+        const float2 db = sub2(hi2(O[ch]), nb[d]->v[ch]);
+        sa = fma2(da, da, sa);
+        sb = fma2(db, db, sb);
+      }
+      eA = fma2(ma, sa, eA);
+      eB = fma2(mb, sb, eB);
+    }
+  }
+}
+
+template <bool MASK>
+__global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __restrict__ probs,
+                                                              const Chunk* __restrict__ chunks,
+                                                              const int* __restrict__ tiles,
+                                                              double* __restrict__ part,
+                                                              const float* __restrict__ p_in_override,
+                                                              int par, int update) {
+  pdl_begin();
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  PoisWideSmem& sm = *reinterpret_cast<PoisWideSmem*>(dyn_smem);
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  Scalars* s = pr.s;
+  if (s->done || !s->pcg_active) return;
+  const int pl = (int)pr.plane;
+  const float beta = s->beta_f;
+  const float2 beta2 = make_float2(beta, beta);
+  const int use_beta = beta != 0.0f;
+  const float lam = pr.lm ? s->lambda_f : 0.0f;
+  const float* __restrict__ pin = p_in_override ? p_in_override : pr.p + (long long)(par & 1) * 4 * pl;
+  float* __restrict__ pout = pr.p + (long long)((par + 1) & 1) * 4 * pl;
+  const float* src[NRAW_PA];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    src[k] = update ? pr.r + k * pl : nullptr;
+    src[5 + k] = (!update || use_beta) ? pin + k * pl : nullptr;
+  }
+  src[4] = update ? pr.m : nullptr;
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  float acc = 0.f;
+  int tc = tiles[ch.begin];
+  int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
+  tile_issue<NRAW_PA, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+  // phase 2 of one staged quad: p = (M^-1 r + beta p_old) on free pixels, 0
+  // elsewhere; weights
+  auto stage = [&](int row, int gx, int gy) {
+    const int c = 4 + 4 * lane;
+    const float4 w = pois_weights<MASK>(sm, row, lane, pr, gx, gy);
+    const float4 f = free01(w);
+    const float4 m = update ? lds4(&sm.raw[4][row][c]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float4 v;
+      if (update) {
+        v = mul4p(m, lds4(&sm.raw[k][row][c]));
+        if (use_beta) v = fma4p(beta2, lds4(&sm.raw[5 + k][row][c]), v);
+      } else {
+        v = lds4(&sm.raw[5 + k][row][c]);
+      }
+      sts4(&sm.stg[k][row][c], swz4(mul4p(f, v)));
+    }
+    sts4(&sm.stg[4][row][c], swz4(w));
+  };
+  for (int t = ch.begin; t < ch.end; ++t) {
+    const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
+    const int gx = x0 + 4 * lane, gy = y0 + ty;
+    cp_async_wait_all();
+    __syncthreads();
+    stage(ty + 1, gx, gy);
+    if (tid < 64) {
+      const int row = tid < 32 ? 0 : HH - 1;
+      stage(row, gx, y0 - 1 + row);
+    } else if (tid < 64 + 2 * TH) {
+      const int h = tid - 64;
+      const int row = 1 + (h % TH), side = h / TH;
+      const int col = side ? 4 + W4 : 3;
+      const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
+      const bool inb = hy < pr.H && hx >= 0 && hx < pr.W;
+      const bool fr = inb && (!MASK || halo_mask(sm.mk, row, side) == 0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float v;
+        if (update) {
+          v = sm.raw[4][row][col] * sm.raw[k][row][col];
+          if (use_beta) v = fmaf(beta, sm.raw[5 + k][row][col], v);
+        } else {
+          v = sm.raw[5 + k][row][col];
+        }
+        sm.stg[k][row][col] = fr ? v : 0.f;
+      }
+      sm.stg[4][row][col] = inb ? (fr ? 2.f : 1.f) : 0.f;
+    }
+    __syncthreads();
+    if (t + 1 < ch.end) {
+      tc = tn;
+      tile_issue<NRAW_PA, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+      if (t + 2 < ch.end) tn = tiles[t + 2];
+    }
+    if (gy < pr.H) {
+      const long long i = (long long)gy * pr.P + gx;
+      const int c = 4 + 4 * lane;
+      float4 O[NSTG_P];
+#pragma unroll
+      for (int k = 0; k < NSTG_P; ++k) O[k] = lds4(&sm.stg[k][ty + 1][c]);
+      if (update) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) *reinterpret_cast<float4*>(pout + k * pl + i) = swz4(O[k]);
+      }
+      float2 qA[4], qB[4], SA, SB, eA, eB;
+      pois_stencil<false>(sm, ty, lane, O, qA, qB, SA, SB, eA, eB);
+      const float4 fo = free01(O[4]);                 // own pixels free (staged order)
+      float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (pr.lm) dd = swz4(ld4(pr.dc + i));
+      const float2 lam2 = make_float2(lam, lam);
+      const float2 dA = mul2(lam2, lo2(dd)), dB = mul2(lam2, hi2(dd));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 a = mul2(lo2(fo), fma2(dA, lo2(O[k]), qA[k]));
+        const float2 b = mul2(hi2(fo), fma2(dB, hi2(O[k]), qB[k]));
+        *reinterpret_cast<float4*>(pr.q + k * pl + i) = swz4(cat4(a, b));
+        acc += O[k].x * a.x + O[k].y * a.y + O[k].z * b.x + O[k].w * b.y;
+      }
+    }
+  }
+  cp_async_wait_all();
+  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+    double pq, unused;
+    gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, pq, unused);
+    if (threadIdx.x == 0) {
+      s->pq = pq;
+      if (pq > 0.0 && isfinite(pq)) {
+        s->alpha_f = (float)(s->rz / pq);
+      } else {
+        s->alpha_f = 0.f;
+        s->pcg_active = 0;
+        if (!isfinite(pq)) s->nonfinite = 1;
+      }
+    }
+  }
+}
+
+template <bool MASK>
+__global__ void __launch_bounds__(NT, 2) k_poisson_init_wide(const GridProb* __restrict__ probs,
+                                                             const Chunk* __restrict__ chunks,
+                                                             const int* __restrict__ tiles,
+                                                             double* __restrict__ part, int k_outer,
+                                                             float dmin, float dmax) {
+  pdl_begin();
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  PoisWideSmem& sm = *reinterpret_cast<PoisWideSmem*>(dyn_smem);
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  Scalars* s = pr.s;
+  if (s->done) return;
+  const int pl = (int)pr.plane;
+  const float lam = pr.lm ? s->lambda_f : 0.0f;
+  const float* src[NRAW_PI];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    src[k] = pr.x + k * pl;
+    src[4 + k] = pr.c + k * pl;
+  }
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  float acc_rz = 0.f, acc_E = 0.f;
+  int tc = tiles[ch.begin];
+  int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
+  tile_issue<NRAW_PI, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+  // phase 2: Y = X - T (staged order) and weights
+  auto stage = [&](int row, int gx, int gy) {
+    const int c = 4 + 4 * lane;
+    const float4 w = pois_weights<MASK>(sm, row, lane, pr, gx, gy);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float4 x = lds4(&sm.raw[k][row][c]), g = lds4(&sm.raw[4 + k][row][c]);
+      sts4(&sm.stg[k][row][c], swz4(cat4(sub2(lo2(x), lo2(g)), sub2(hi2(x), hi2(g)))));
+    }
+    sts4(&sm.stg[4][row][c], swz4(w));
+  };
+  for (int t = ch.begin; t < ch.end; ++t) {
+    const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
+    const int gx = x0 + 4 * lane, gy = y0 + ty;
+    cp_async_wait_all();
+    __syncthreads();
+    stage(ty + 1, gx, gy);
+    if (tid < 64) {
+      const int row = tid < 32 ? 0 : HH - 1;
+      stage(row, gx, y0 - 1 + row);
+    } else if (tid < 64 + 2 * TH) {
+      const int h = tid - 64;
+      const int row = 1 + (h % TH), side = h / TH;
+      const int col = side ? 4 + W4 : 3;
+      const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
+      const bool inb = hy < pr.H && hx >= 0 && hx < pr.W;
+      const bool fr = inb && (!MASK || halo_mask(sm.mk, row, side) == 0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sm.stg[k][row][col] = sm.raw[k][row][col] - sm.raw[4 + k][row][col];
+      sm.stg[4][row][col] = inb ? (fr ? 2.f : 1.f) : 0.f;
+    }
+    __syncthreads();
+    if (t + 1 < ch.end) {
+      tc = tn;
+      tile_issue<NRAW_PI, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+      if (t + 2 < ch.end) tn = tiles[t + 2];
+    }
+    if (gy < pr.H) {
+      const long long i = (long long)gy * pr.P + gx;
+      const int c = 4 + 4 * lane;
+      float4 O[NSTG_P];
+#pragma unroll
+      for (int k = 0; k < NSTG_P; ++k) O[k] = lds4(&sm.stg[k][ty + 1][c]);
+      float2 gA[4], gB[4], SA, SB, eA, eB;
+      pois_stencil<true>(sm, ty, lane, O, gA, gB, SA, SB, eA, eB);
+      const float4 fo = free01(O[4]);
+      // diagonal S on free pixels (0 elsewhere), M^-1, LM damping diagonal
+      const float4 dg = swz4(cat4(mul2(lo2(fo), SA), mul2(hi2(fo), SB)));   // plain order
+      float4 mv, dcv;
+      mv.x = minv_entry(dg.x, lam, dmin, dmax, pr.use_precond, &dcv.x);
+      mv.y = minv_entry(dg.y, lam, dmin, dmax, pr.use_precond, &dcv.y);
+      mv.z = minv_entry(dg.z, lam, dmin, dmax, pr.use_precond, &dcv.z);
+      mv.w = minv_entry(dg.w, lam, dmin, dmax, pr.use_precond, &dcv.w);
+      *reinterpret_cast<float4*>(pr.m + i) = mv;
+      if (pr.lm) *reinterpret_cast<float4*>(pr.dc + i) = dcv;
+      if (pr.diag_out) *reinterpret_cast<float4*>(pr.diag_out + i) = dg;
+      const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+      float rz = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float4 g = swz4(cat4(mul2(lo2(fo), gA[k]), mul2(hi2(fo), gB[k])));   // J^T F, plain order
+        const float4 b = make_float4(-g.x, -g.y, -g.z, -g.w);
+        *reinterpret_cast<float4*>(pr.r + k * pl + i) = b;
+        *reinterpret_cast<float4*>(pr.d + k * pl + i) = zero;
+        if (pr.jtf_out) *reinterpret_cast<float4*>(pr.jtf_out + k * pl + i) = g;
+        rz += mv.x * b.x * b.x + mv.y * b.y * b.y + mv.z * b.z * b.z + mv.w * b.w * b.w;
+      }
+      acc_rz += rz;
+      const float2 ea = mul2(lo2(fo), eA), eb = mul2(hi2(fo), eB);
+      acc_E += (ea.x + ea.y) + (eb.x + eb.y);
+    }
+  }
+  cp_async_wait_all();
+  if (publish_partials(part, blockIdx.x, acc_rz, acc_E, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+    double rz, E;
+    gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, rz, E);
+    if (threadIdx.x == 0) {
+      s->rz = rz;
+      s->E = E;
+      if (pr.Ehist && k_outer >= 0) pr.Ehist[k_outer] = E;
+      s->beta_f = 0.f;
+      s->pcg_active = (rz != 0.0) && isfinite(rz);
+      if (!isfinite(rz) || !isfinite(E)) s->nonfinite = 1;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(NT) k_poisson_energy(const GridProb* __restrict__ probs,
                                                        const Chunk* __restrict__ chunks,
                                                        const int* __restrict__ tiles,
@@ -1642,6 +2001,15 @@ cudaError_t grid_kernels_prepare() {
       e = cudaFuncSetAttribute(k_warp_init_wide<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_warp_init_wide<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    const int pbytes = (int)sizeof(PoisWideSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_poisson_apply_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_poisson_apply_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_poisson_init_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_poisson_init_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_warp_pcg_coop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
@@ -1665,7 +2033,14 @@ void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, fl
   else if (kind == K_WARP)
     launch_pdl(k_warp_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
   else
-    launch_pdl(k_poisson_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
+    if (L.tw == W4 && L.masked)
+      launch_pdl(k_poisson_init_wide<true>, L.nchunks, NT, sizeof(PoisWideSmem), L.stream, L.probs, L.chunks, L.tiles,
+                 L.part, k_outer, dmin, dmax);
+    else if (L.tw == W4)
+      launch_pdl(k_poisson_init_wide<false>, L.nchunks, NT, sizeof(PoisWideSmem), L.stream, L.probs, L.chunks,
+                 L.tiles, L.part, k_outer, dmin, dmax);
+    else
+      launch_pdl(k_poisson_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
 }
 
 void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, int par, int update) {
@@ -1678,7 +2053,15 @@ void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, i
   else if (kind == K_WARP)
     launch_pdl(k_warp_apply, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, p_override, par, update);
   else
-    launch_pdl(k_poisson_apply, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, p_override, par, update);
+    if (L.tw == W4 && L.masked)
+      launch_pdl(k_poisson_apply_wide<true>, L.nchunks, NT, sizeof(PoisWideSmem), L.stream, L.probs, L.chunks,
+                 L.tiles, L.part, p_override, par, update);
+    else if (L.tw == W4)
+      launch_pdl(k_poisson_apply_wide<false>, L.nchunks, NT, sizeof(PoisWideSmem), L.stream, L.probs, L.chunks,
+                 L.tiles, L.part, p_override, par, update);
+    else
+      launch_pdl(k_poisson_apply, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, p_override, par,
+                 update);
 }
 
 void launch_grid_update(int kind, const GridLaunch& L, int par) {

@@ -31,7 +31,8 @@ def mixed_problems():
     # wide warps run the 128-pixel-tile kernel group (with and without a mask)
     probs.append(synth.warp_problem(260, 20, 6, seed=221))
     probs.append(synth.warp_problem(300, 16, 6, seed=222, mask=synth.random_mask(300, 16, 0.1, 5)))
-    probs += [synth.poisson_problem(64, 40, seed=230), synth.poisson_problem(37, 70, seed=231)]
+    probs += [synth.poisson_problem(64, 40, seed=230), synth.poisson_problem(37, 70, seed=231),
+              synth.poisson_problem(300, 24, seed=232)]      # 128-pixel Poisson tiles
     probs += [synth.mesh_problem(1, seed=240, handle_frac=0.1), synth.mesh_problem(2, seed=241, handle_frac=0.05)]
     return probs
 
@@ -58,7 +59,7 @@ def test_batch_matches_solo_and_oracle(api, method):
             # members scatter with float32 atomics -> rounding-level differences
             assert relE(a, b) <= (0.0 if p.kind != "mesh" else 1e-5)
     # a few members against the oracle
-    for i in (0, 9, 10, 11, 12):
+    for i in (0, 9, 10, 11, 12, 14):
         e = oracle.make_energy(probs[i])
         x0 = probs[i].x0.reshape(-1)
         ref = (oracle.gauss_newton(e, x0, outer, inner) if method == "gn"

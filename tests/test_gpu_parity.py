@@ -44,7 +44,7 @@ def perturbed(prob, scale, seed):
     rng = np.random.default_rng(seed)
     x = prob.x0.astype(np.float32).copy()
     if prob.kind == "poisson":
-        free = prob.mask == 0
+        free = np.ones((prob.H, prob.W), bool) if prob.mask is None else prob.mask == 0
         x[:, free] += rng.uniform(-scale, scale, size=(4, int(free.sum()))).astype(np.float32)
     else:
         x += rng.uniform(-scale, scale, size=x.shape).astype(np.float32)
@@ -55,7 +55,7 @@ def perturbed(prob, scale, seed):
 def random_direction(prob, seed):
     rng = np.random.default_rng(seed)
     p = rng.standard_normal(prob.n_unknowns).astype(np.float32)
-    if prob.kind == "poisson":
+    if prob.kind == "poisson" and prob.mask is not None:
         p.reshape(4, -1)[:, prob.mask.reshape(-1) != 0] = 0.0
     return p
 
@@ -66,6 +66,9 @@ GRID_CASES = [
     # 128-pixel tiles (float4 rows): exact, ragged and masked widths
     ("warp", 256, 24, 0.0), ("warp", 300, 41, 0.0), ("warp", 301, 17, 0.2), ("warp", 520, 9, 0.0),
     ("poisson", 64, 48, None), ("poisson", 45, 33, None), ("poisson", 1, 17, None), ("poisson", 96, 80, None),
+    # Poisson on 128-pixel tiles: exact, ragged widths, and no mask at all (every pixel free)
+    ("poisson", 256, 24, None), ("poisson", 300, 41, None), ("poisson", 301, 17, None), ("poisson", 520, 9, None),
+    ("poisson", 290, 20, "nomask"),
 ]
 
 
@@ -75,6 +78,8 @@ def make_grid(kind, W, H, mask_frac, seed=11):
         prob = synth.warp_problem(W, H, max(1, (W * H) // 200), seed=seed, mask=mask)
         return perturbed(prob, 0.5, seed + 2)
     prob = synth.poisson_problem(W, H, seed=seed)
+    if mask_frac == "nomask":
+        prob.mask = None
     return perturbed(prob, 0.2, seed + 2)
 
 
@@ -388,7 +393,13 @@ def test_wide_tiles_forced_on_narrow_grids(api, W, H, mf):
     """128-wide tiles on grids narrower than a tile (pitch padding, halo
     columns outside the image) give the same products as 32-wide tiles."""
     import torch
-    prob = make_grid("warp", W, H, mf, seed=131)
+    for kind in ("warp", "poisson"):
+        _forced_tiles_case(api, kind, W, H, mf)
+
+
+def _forced_tiles_case(api, kind, W, H, mf):
+    import torch
+    prob = make_grid(kind, W, H, mf if kind == "warp" else None, seed=131)
     p = random_direction(prob, 2)
     a = api.Problem(prob, tile_w=128)
     b = api.Problem(prob, tile_w=32)
