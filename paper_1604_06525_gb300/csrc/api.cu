@@ -103,6 +103,44 @@ __global__ void k_lm_decide(Scalars* s, int n, double eta, double lmin, double l
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+// Locality order of graph vertices: ascending Morton (Z-order) code of the
+// rest positions quantised to 10 bits per axis inside their bounding box,
+// ties by caller index.  Neighbouring vertices of a surface mesh end up close
+// in memory, so the gather kernels find most neighbour records in cache.
+std::vector<int> morton_order(const std::vector<float>* U, int V) {
+  float lo[3], hi[3];
+  for (int c = 0; c < 3; ++c) {
+    lo[c] = hi[c] = V ? U[c][0] : 0.f;
+    for (int v = 1; v < V; ++v) {
+      lo[c] = std::min(lo[c], U[c][v]);
+      hi[c] = std::max(hi[c], U[c][v]);
+    }
+  }
+  auto spread = [](uint32_t x) {   // 10 bits -> every third bit
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+  };
+  std::vector<std::pair<uint32_t, int>> key((size_t)V);
+  for (int v = 0; v < V; ++v) {
+    uint32_t code = 0;
+    for (int c = 0; c < 3; ++c) {
+      const float ext = hi[c] - lo[c];
+      const float t = ext > 0.f ? (U[c][v] - lo[c]) / ext : 0.f;
+      const uint32_t qv = (uint32_t)std::min(1023.f, std::max(0.f, t * 1023.f));
+      code |= spread(qv) << c;
+    }
+    key[v] = {code, v};
+  }
+  std::sort(key.begin(), key.end());
+  std::vector<int> perm((size_t)V);
+  for (int k = 0; k < V; ++k) perm[k] = key[k].second;
+  return perm;
+}
+
 }  // namespace
 
 
@@ -162,32 +200,55 @@ opt_status common_setup(opt_problem* pb) {
   return OPT_OK;
 }
 
-// copy between caller dense planes and internal pitched planes
+// Graph problems keep their vertices in a locality order (internal vertex k
+// is the caller's vertex perm[k]); these move one plane between the orders.
+__global__ void k_gather_vertices(float* __restrict__ dst, const float* __restrict__ src, const int* __restrict__ perm,
+                                  int V) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < V) dst[k] = src[perm[k]];
+}
+__global__ void k_scatter_vertices(float* __restrict__ dst, const float* __restrict__ src,
+                                   const int* __restrict__ perm, int V) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < V) dst[perm[k]] = src[k];
+}
+
+}  // namespace
+
+namespace optgb {
+
+// copy between caller dense planes (caller order) and internal planes
+// (pitched rows for grids, locality order for graphs)
 opt_status copy_planes_in(const opt_problem* pb, float* internal, float* const* user, int n,
                           cudaStream_t st) {
   for (int c = 0; c < n; ++c) {
-    if (is_grid(pb))
+    if (is_grid(pb)) {
       CK(cudaMemcpy2DAsync(internal + c * pb->plane, (size_t)pb->P * 4, user[c], (size_t)pb->W * 4,
                            (size_t)pb->W * 4, pb->H, cudaMemcpyDeviceToDevice, st));
-    else
-      CK(cudaMemcpyAsync(internal + c * pb->plane, user[c], (size_t)pb->V * 4,
-                         cudaMemcpyDeviceToDevice, st));
+    } else {
+      k_gather_vertices<<<(pb->V + 255) / 256, 256, 0, st>>>(internal + c * pb->plane, user[c], pb->d_perm, pb->V);
+      CK(cudaGetLastError());
+    }
+  }
+  return OPT_OK;
+}
+opt_status copy_planes_out(const opt_problem* pb, float* const* user, const float* internal, int n,
+                           cudaStream_t st) {
+  for (int c = 0; c < n; ++c) {
+    if (is_grid(pb)) {
+      CK(cudaMemcpy2DAsync(user[c], (size_t)pb->W * 4, internal + c * pb->plane, (size_t)pb->P * 4,
+                           (size_t)pb->W * 4, pb->H, cudaMemcpyDeviceToDevice, st));
+    } else {
+      k_scatter_vertices<<<(pb->V + 255) / 256, 256, 0, st>>>(user[c], internal + c * pb->plane, pb->d_perm, pb->V);
+      CK(cudaGetLastError());
+    }
   }
   return OPT_OK;
 }
 
-opt_status copy_planes_out(const opt_problem* pb, float* const* user, const float* internal, int n,
-                           cudaStream_t st) {
-  for (int c = 0; c < n; ++c) {
-    if (is_grid(pb))
-      CK(cudaMemcpy2DAsync(user[c], (size_t)pb->W * 4, internal + c * pb->plane, (size_t)pb->P * 4,
-                           (size_t)pb->W * 4, pb->H, cudaMemcpyDeviceToDevice, st));
-    else
-      CK(cudaMemcpyAsync(user[c], internal + c * pb->plane, (size_t)pb->V * 4,
-                         cudaMemcpyDeviceToDevice, st));
-  }
-  return OPT_OK;
-}
+}  // namespace optgb
+
+namespace {
 
 void dense_planes(const opt_problem* pb, const float* base, float** out, int n) {
   for (int c = 0; c < n; ++c) out[c] = const_cast<float*>(base) + c * pb->ulen;
@@ -198,7 +259,7 @@ GridLaunch grid_launch(const opt_problem* pb, cudaStream_t st) {
                     pb->hg.mask != nullptr};
 }
 MeshLaunch mesh_launch(const opt_problem* pb, cudaStream_t st) {
-  return MeshLaunch{pb->dm, pb->d_vchunks, pb->d_echunks, pb->d_part, pb->d_acc, pb->nvchunks,
+  return MeshLaunch{pb->dm, pb->d_vchunks, pb->d_echunks, pb->d_part, pb->nvchunks,
                     pb->nechunks, st};
 }
 
@@ -668,6 +729,17 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   CKS(download(e1, d->v1, (size_t)E));
   for (int e = 0; e < E; ++e)
     if (e0[e] < 0 || e0[e] >= V || e1[e] < 0 || e1[e] >= V || e0[e] == e1[e]) return OPT_ERR_INVALID_ARG;
+  std::vector<float> Uh[3];
+  for (int c = 0; c < 3; ++c) {
+    CKS(download(Uh[c], d->urshape[c], (size_t)V));
+    if (!all_finite(Uh[c])) return OPT_ERR_INVALID_ARG;
+  }
+  // internal vertex order: internal k = caller perm[k]; edges and handles are
+  // renumbered before sorting
+  const std::vector<int> perm = morton_order(Uh, V);
+  std::vector<int> iperm((size_t)V);
+  for (int k = 0; k < V; ++k) iperm[perm[k]] = k;
+  for (int e = 0; e < E; ++e) { e0[e] = iperm[e0[e]]; e1[e] = iperm[e1[e]]; }
   bool sorted = true;
   for (int e = 1; e < E && sorted; ++e)
     if (e0[e] < e0[e - 1] || (e0[e] == e0[e - 1] && e1[e] < e1[e - 1])) sorted = false;
@@ -677,18 +749,16 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
     std::sort(key.begin(), key.end());
     for (int e = 0; e < E; ++e) { e0[e] = (int)(key[e] / V); e1[e] = (int)(key[e] % V); }
   }
-  std::vector<float> U3;
-  for (int c = 0; c < 3; ++c) {
-    std::vector<float> tmp;
-    CKS(download(tmp, d->urshape[c], (size_t)V));
-    if (!all_finite(tmp)) return OPT_ERR_INVALID_ARG;
-  }
   std::vector<int> hidx;
   std::vector<float> htgt;
   if (nh > 0) {
     CKS(download(hidx, d->handle_idx, (size_t)nh));
     CKS(download(htgt, d->handle_target, (size_t)nh * 3));
     if (!all_finite(htgt)) return OPT_ERR_INVALID_ARG;
+    for (int& h : hidx) {
+      if (h < 0 || h >= V) return OPT_ERR_INVALID_ARG;
+      h = iperm[h];
+    }
   }
   std::vector<int> order(nh);
   std::iota(order.begin(), order.end(), 0);
@@ -710,6 +780,21 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
     degw[e0[e]] += d->w_reg;
     degw[e1[e]] += d->w_reg;
   }
+  // out-edge rows of the sorted list, and the in-edges of every vertex
+  // (sources ascending, as the sorted list visits them)
+  std::vector<int> orow((size_t)V + 1, 0), irow((size_t)V + 1, 0), isrc((size_t)E);
+  for (int e = 0; e < E; ++e) {
+    orow[(size_t)e0[e] + 1] += 1;
+    irow[(size_t)e1[e] + 1] += 1;
+  }
+  for (int v = 0; v < V; ++v) {
+    orow[(size_t)v + 1] += orow[v];
+    irow[(size_t)v + 1] += irow[v];
+  }
+  {
+    std::vector<int> fill(irow.begin(), irow.end() - 1);
+    for (int e = 0; e < E; ++e) isrc[(size_t)fill[e1[e]]++] = e0[e];
+  }
 
   const int target = std::max(1, q->sms * 8);
   std::vector<Chunk> vch = make_chunks_balanced(nvt, target, 0);
@@ -728,11 +813,23 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   CKS(dalloc(q, &q->pbuf, 12 * pl));
   CKS(dalloc(q, &m, 4 * pl));
   CKS(dalloc(q, &dc, 4 * pl));
-  CKS(dalloc(q, &q->d_acc, 3 * pl));
-  float* mcsn = nullptr;
-  CKS(dalloc(q, &mcsn, 6 * pl));
-  for (int c = 0; c < 3; ++c)
-    CK(cudaMemcpy(U + c * pl, d->urshape[c], (size_t)V * 4, cudaMemcpyDeviceToDevice));
+  float4 *grec = nullptr, *vrec = nullptr;
+  CKS(dalloc(q, &grec, 3 * (size_t)V));
+  CKS(dalloc(q, &vrec, 2 * (size_t)V));
+  int *dorow = nullptr, *dirow = nullptr, *disrc = nullptr;
+  CKS(dalloc(q, &dorow, orow.size()));
+  CKS(upload(dorow, orow));
+  CKS(dalloc(q, &dirow, irow.size()));
+  CKS(upload(dirow, irow));
+  CKS(dalloc(q, &disrc, std::max<size_t>(1, isrc.size())));
+  if (E > 0) CKS(upload(disrc, isrc));
+  for (int c = 0; c < 3; ++c) {
+    std::vector<float> Ui((size_t)V);
+    for (int k = 0; k < V; ++k) Ui[k] = Uh[c][perm[k]];
+    CKS(upload(U + c * pl, Ui));
+  }
+  CKS(dalloc(q, &q->d_perm, (size_t)V));
+  CKS(upload(q->d_perm, perm));
   CKS(upload(dgw, degw));
   CKS(dalloc(q, &de0, (size_t)E));
   CKS(upload(de0, e0));
@@ -766,8 +863,8 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   g.use_precond = 1; g.lm = 0;
   g.x = q->x; g.U = U; g.degw = dgw; g.e0 = de0; g.e1 = de1;
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
-  g.acc = q->d_acc;
-  g.csn = mcsn;
+  g.orow = dorow; g.irow = dirow; g.isrc = disrc;
+  g.grec = grec; g.vrec = vrec;
   g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;
   g.jtf_out = nullptr; g.diag_out = nullptr;
   g.s = q->d_s;

@@ -44,6 +44,9 @@ struct PlaneCopy {
   float* dst;
   int rows, cols;
   int src_pitch, dst_pitch;   // in floats
+  const int* perm;            // graphs (one row): internal vertex k = caller vertex perm[k]
+  int to_caller;              // with perm: 1 = internal -> caller order, 0 = caller -> internal
+  int pad;
 };
 
 __global__ void k_copy_planes(const PlaneCopy* __restrict__ tab, int n) {
@@ -51,6 +54,12 @@ __global__ void k_copy_planes(const PlaneCopy* __restrict__ tab, int n) {
   const long long total = (long long)c.rows * c.cols;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
        k += (long long)gridDim.x * blockDim.x) {
+    if (c.perm) {
+      const int v = c.perm[k];
+      if (c.to_caller) c.dst[v] = c.src[k];
+      else c.dst[k] = c.src[v];
+      continue;
+    }
     const int r = (int)(k / c.cols), col = (int)(k - (long long)r * c.cols);
     c.dst[(long long)r * c.dst_pitch + col] = c.src[(long long)r * c.src_pitch + col];
   }
@@ -261,7 +270,7 @@ GridLaunch gl(const GridGroup& g, cudaStream_t st) {
   return GridLaunch{g.d_probs, g.d_chunks, g.d_tiles, g.d_part, g.nchunks, st, g.tw, g.masked};
 }
 MeshLaunch ml(const MeshGroup& g, cudaStream_t st) {
-  return MeshLaunch{g.d_probs, g.d_vch, g.d_ech, g.d_part, nullptr, g.nv, g.ne, st};
+  return MeshLaunch{g.d_probs, g.d_vch, g.d_ech, g.d_part, g.nv, g.ne, st};
 }
 
 // Uploads the members' descriptors with the solve's flags (outside any capture).
@@ -476,11 +485,11 @@ opt_status opt_batch_create(opt_problem* const* probs, int32_t n, opt_batch** ou
     stab.push_back(pb->d_s);
     for (int c = 0; c < pb->nx; ++c) {
       if (is_grid_kind(pb->kind)) {
-        cin.push_back(PlaneCopy{pb->user_x[c], pb->x + c * pb->plane, pb->H, pb->W, pb->W, pb->P});
-        cout_.push_back(PlaneCopy{pb->x + c * pb->plane, pb->user_x[c], pb->H, pb->W, pb->P, pb->W});
+        cin.push_back(PlaneCopy{pb->user_x[c], pb->x + c * pb->plane, pb->H, pb->W, pb->W, pb->P, nullptr, 0, 0});
+        cout_.push_back(PlaneCopy{pb->x + c * pb->plane, pb->user_x[c], pb->H, pb->W, pb->P, pb->W, nullptr, 0, 0});
       } else {
-        cin.push_back(PlaneCopy{pb->user_x[c], pb->x + c * pb->plane, 1, pb->V, pb->V, pb->V});
-        cout_.push_back(PlaneCopy{pb->x + c * pb->plane, pb->user_x[c], 1, pb->V, pb->V, pb->V});
+        cin.push_back(PlaneCopy{pb->user_x[c], pb->x + c * pb->plane, 1, pb->V, pb->V, pb->V, pb->d_perm, 0, 0});
+        cout_.push_back(PlaneCopy{pb->x + c * pb->plane, pb->user_x[c], 1, pb->V, pb->V, pb->V, pb->d_perm, 1, 0});
       }
       maxp = std::max<int>(maxp, (int)pb->ulen);
     }

@@ -1,60 +1,38 @@
 // Matrix-free graph kernels (Sec. 4.1 "Graph-based Array Access", Sec. 5.3.2).
 //
-// As in the paper, one thread owns one edge residual and scatters its
-// contributions to the rows of the two vertices it touches (Fig. 11: a row of
-// J p per residual, then J^T times it).  Edges are kept sorted by (v0, v1), so
-// the v0-side contributions of a warp are first summed over each run of equal
-// v0 (segmented shuffle reduction) and only the run head issues the atomic
-// add; the v1 side issues one float32 atomic add per component.
+// The paper maps one thread to one edge residual and scatters its
+// contributions to the rows of the two vertices with atomics (Fig. 11).  Here
+// every row of J^T F, diag(J^T J) and J^T J p is gathered instead: one thread
+// owns one vertex i and walks
+//   * its out-edges (i, j) (edges sorted by (v0, v1) -> CSR rows): the
+//     residual's own rows at i (displacement and angles), and
+//   * its in-edges (j, i) (a transposed list built at planning): the
+//     residual's rows at its far end, the displacement rows of i,
+// so each edge residual is evaluated twice (once from each end) and no
+// atomic or cross-thread sum is needed; every row is summed in a fixed
+// order.  What a thread reads of a neighbour sits in two per-vertex records
+// (array of structures, a few 32-byte sectors per gather instead of one
+// sector per plane):
+//   grec[v] = (U_x, U_y, U_z, cos a_x), (sin a_x, cos a_y, sin a_y, cos a_z),
+//             (sin a_z, 0, 0, 0)          written by PCGInit's vertex pass
+//   vrec[v] = the vertex's 6-vector (x in PCGInit, p in applyJTJ), 2 float4
 //
 // ARAP mesh algebra per edge e = (a, b), v = U_a - U_b, d = O - U:
 //   r_e       = s_w [(d_a - d_b) + (v - R(A_a) v)]              (= Fig. 25)
 //   dr/dd_a   = s_w I,  dr/dd_b = -s_w I,
 //   dr/dA_a,m = g_m = -s_w (dR/dA_m)(A_a) v,  R = Rz(az) Ry(ay) Rx(ax).
 //
-// Per outer iteration (PCGInit): k_mesh_init_v (fit rows, zero accumulators),
-// k_mesh_init_e (edge rows of J^T F, angle diagonal, energy), k_mesh_init_f
-// (b, M^-1, r, delta, float64 r.z).  Per PCG iteration: k_mesh_apply_v
-// (p = z + beta p, fit + damping rows of q), k_mesh_apply_e (edge rows of
-// J^T J p, float64 p.q -> alpha), k_mesh_update (vector update -> beta).
+// Per outer iteration (PCGInit): k_mesh_init_v (cos / sin of the angles, the
+// records), k_mesh_init_pull (J^T F, diag, M^-1, r, delta, float64 r.z and E).
+// Per PCG iteration: k_mesh_apply_v (p = z + beta p into the planes and the
+// records), k_mesh_apply_pull (J^T J p + fit + damping, float64 p.q -> alpha),
+// k_mesh_update (vector update -> beta).
 #include "opt_internal.cuh"
 #include "opt_launch.h"
 
 namespace optgb {
 
 namespace {
-
-// Segment structure of a warp whose lanes hold sorted keys.
-struct Seg {
-  unsigned flags;   // bit k: lane + 2^k is in this lane's segment
-  bool head;        // first lane of its segment within the warp
-};
-
-__device__ __forceinline__ Seg seg_info(int key) {
-  const int lane = threadIdx.x & 31;
-  Seg sg;
-  sg.flags = 0u;
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const int off = 1 << k;
-    const int other = __shfl_down_sync(0xffffffffu, key, off);
-    if (lane + off < 32 && other == key) sg.flags |= 1u << k;
-  }
-  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-  sg.head = (lane == 0) || (prev != key);
-  return sg;
-}
-
-// Sum of v over the lanes of this lane's segment at or after this lane
-// (the full segment sum at the head lane).
-__device__ __forceinline__ float seg_sum(float v, unsigned flags) {
-#pragma unroll
-  for (int k = 0; k < 5; ++k) {
-    const float o = __shfl_down_sync(0xffffffffu, v, 1 << k);
-    if (flags & (1u << k)) v += o;
-  }
-  return v;
-}
 
 __device__ __forceinline__ int handle_of(const MeshProb& pr, int v) {
   const int t = v / VT;
@@ -63,51 +41,74 @@ __device__ __forceinline__ int handle_of(const MeshProb& pr, int v) {
   return -1;
 }
 
+constexpr int KB = 6;             // neighbour indices fetched ahead per vertex (icosphere degree 5 / 6)
+#ifndef MESH_PULL_MIN_BLOCKS
+#define MESH_PULL_MIN_BLOCKS 4    // resident blocks per SM the gather apply is compiled for
+#endif
+
+__device__ __forceinline__ float4 ld4g(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float c4(const float4& a, int k) {
+  return k == 0 ? a.x : (k == 1 ? a.y : (k == 2 ? a.z : a.w));
+}
+
+// A vertex's geometry record and 6-vector record.
+struct GeoRec {
+  float U[3];
+  float cs[6];      // cos ax, sin ax, cos ay, sin ay, cos az, sin az
+};
+__device__ __forceinline__ GeoRec load_geo(const float4* __restrict__ grec, int v) {
+  const float4 a = __ldg(grec + 3 * v), b = __ldg(grec + 3 * v + 1), c = __ldg(grec + 3 * v + 2);
+  GeoRec g;
+  g.U[0] = a.x; g.U[1] = a.y; g.U[2] = a.z;
+  g.cs[0] = a.w; g.cs[1] = b.x; g.cs[2] = b.y; g.cs[3] = b.z; g.cs[4] = b.w; g.cs[5] = c.x;
+  return g;
+}
+// 6-vector record written in the same launch chain (plain loads, not the
+// read-only path)
+__device__ __forceinline__ void load_vec(const float4* vrec, int v, float (&o)[6]) {
+  const float4 a = vrec[2 * v], b = vrec[2 * v + 1];
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y;
+}
+__device__ __forceinline__ void load_vec3(const float4* vrec, int v, float (&o)[3]) {
+  const float4 a = vrec[2 * v];
+  o[0] = a.x; o[1] = a.y; o[2] = a.z;
+}
+
 // ---------------------------------------------------------------------------
 // PCGInit
 // ---------------------------------------------------------------------------
+// Vertex pass: cos / sin of the angles and both records of every vertex.
 __global__ void __launch_bounds__(NT) k_mesh_init_v(const MeshProb* __restrict__ probs,
-                                                    const Chunk* __restrict__ chunks,
-                                                    double* __restrict__ part) {
+                                                    const Chunk* __restrict__ chunks) {
   pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
-  Scalars* s = pr.s;
-  if (s->done) return;
+  if (pr.s->done) return;
   const long long pl = pr.Vp;
-  float e = 0.f;
   for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    const int h = handle_of(pr, v);
-    if (h >= 0) {
-      const float f0 = pr.s_f * (pr.x[v] - pr.htgt[3 * h]);
-      const float f1 = pr.s_f * (pr.x[pl + v] - pr.htgt[3 * h + 1]);
-      const float f2 = pr.s_f * (pr.x[2 * pl + v] - pr.htgt[3 * h + 2]);
-      g0 = pr.s_f * f0; g1 = pr.s_f * f1; g2 = pr.s_f * f2;
-      e += f0 * f0 + f1 * f1 + f2 * f2;
-    }
-    pr.q[v] = g0; pr.q[pl + v] = g1; pr.q[2 * pl + v] = g2;
-    pr.q[3 * pl + v] = 0.f; pr.q[4 * pl + v] = 0.f; pr.q[5 * pl + v] = 0.f;
-    pr.acc[v] = 0.f; pr.acc[pl + v] = 0.f; pr.acc[2 * pl + v] = 0.f;
+    float x[6], U[3], cs[6];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      float sn, cs;
-      sincosf(pr.x[(3 + m) * pl + v], &sn, &cs);
-      pr.csn[(2 * m) * pl + v] = cs;
-      pr.csn[(2 * m + 1) * pl + v] = sn;
-    }
-  }
-  pdl_trigger();
-  if (publish_partials(part, blockIdx.x, e, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
-    double a, b;
-    gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, a, b);
-    if (threadIdx.x == 0) s->part0 = a;
+    for (int c = 0; c < 6; ++c) x[c] = pr.x[c * pl + v];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) U[c] = __ldg(pr.U + c * pl + v);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) sincosf(x[3 + m], &cs[2 * m + 1], &cs[2 * m]);
+    pr.grec[3 * v] = make_float4(U[0], U[1], U[2], cs[0]);
+    pr.grec[3 * v + 1] = make_float4(cs[1], cs[2], cs[3], cs[4]);
+    pr.grec[3 * v + 2] = make_float4(cs[5], 0.f, 0.f, 0.f);
+    pr.vrec[2 * v] = make_float4(x[0], x[1], x[2], x[3]);
+    pr.vrec[2 * v + 1] = make_float4(x[4], x[5], 0.f, 0.f);
   }
 }
 
-__global__ void __launch_bounds__(NT) k_mesh_init_e(const MeshProb* __restrict__ probs,
-                                                    const Chunk* __restrict__ chunks,
-                                                    double* __restrict__ part) {
+// Gather pass: per vertex i the rows of J^T F (fit, own edge residuals with
+// their angle rows, incoming edge residuals), diag(J^T J) (displacement:
+// planned w_reg * degree + w_fit; angles: sum |g_m|^2 over the out-edges),
+// the energy of the own residuals, then b = -J^T F, M^-1, r = b, delta = 0.
+__global__ void __launch_bounds__(NT) k_mesh_init_pull(const MeshProb* __restrict__ probs,
+                                                       const Chunk* __restrict__ chunks,
+                                                       double* __restrict__ part, int k_outer, float dmin,
+                                                       float dmax) {
   pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
@@ -115,104 +116,89 @@ __global__ void __launch_bounds__(NT) k_mesh_init_e(const MeshProb* __restrict__
   if (s->done) return;
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
-  float e = 0.f;
-  for (int base = ch.begin; base < ch.end; base += NT) {
-    const int ei = base + (int)threadIdx.x;
-    const bool ok = ei < ch.end;
-    const int a = ok ? pr.e0[ei] : -1;
-    float c[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int b = 0;
-    float rb0 = 0.f, rb1 = 0.f, rb2 = 0.f;
-    if (ok) {
-      b = pr.e1[ei];
-      const float vx = pr.U[a] - pr.U[b];
-      const float vy = pr.U[pl + a] - pr.U[pl + b];
-      const float vz = pr.U[2 * pl + a] - pr.U[2 * pl + b];
-      const RotV R = rot_apply_cs(pr.csn[a], pr.csn[pl + a], pr.csn[2 * pl + a], pr.csn[3 * pl + a],
-                                    pr.csn[4 * pl + a], pr.csn[5 * pl + a], vx, vy, vz);
-      const float r0 = sw * ((pr.x[a] - pr.x[b]) + (vx - R.rv[0]));
-      const float r1 = sw * ((pr.x[pl + a] - pr.x[pl + b]) + (vy - R.rv[1]));
-      const float r2 = sw * ((pr.x[2 * pl + a] - pr.x[2 * pl + b]) + (vz - R.rv[2]));
-      c[0] = sw * r0; c[1] = sw * r1; c[2] = sw * r2;
+  const float lam = pr.lm ? s->lambda_f : 0.0f;
+  float acc_rz = 0.f, acc_E = 0.f;
+  for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
+    float xi[6];
+    load_vec(pr.vrec, i, xi);
+    const GeoRec gi = load_geo(pr.grec, i);
+    float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // J^T F
+    float da[3] = {0.f, 0.f, 0.f};                 // angle diagonal
+    float e = 0.f;
+    const int h = handle_of(pr, i);
+    if (h >= 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float f = pr.s_f * (xi[c] - pr.htgt[3 * h + c]);
+        g[c] += pr.s_f * f;
+        e += f * f;
+      }
+    }
+    const int o0 = pr.orow[i], o1 = pr.orow[i + 1];
+    for (int k = o0; k < o1; ++k) {
+      const int j = pr.e1[k];
+      float xj[3];
+      load_vec3(pr.vrec, j, xj);
+      const float4 uj = __ldg(pr.grec + 3 * j);
+      const float vx = gi.U[0] - uj.x, vy = gi.U[1] - uj.y, vz = gi.U[2] - uj.z;
+      const RotV R = rot_apply_cs(gi.cs[0], gi.cs[1], gi.cs[2], gi.cs[3], gi.cs[4], gi.cs[5], vx, vy, vz);
+      const float r0 = sw * ((xi[0] - xj[0]) + (vx - R.rv[0]));
+      const float r1 = sw * ((xi[1] - xj[1]) + (vy - R.rv[1]));
+      const float r2 = sw * ((xi[2] - xj[2]) + (vz - R.rv[2]));
+      g[0] += sw * r0; g[1] += sw * r1; g[2] += sw * r2;
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         const float g0 = -sw * R.g[m][0], g1 = -sw * R.g[m][1], g2 = -sw * R.g[m][2];
-        c[3 + m] = g0 * r0 + g1 * r1 + g2 * r2;
-        c[6 + m] = g0 * g0 + g1 * g1 + g2 * g2;
+        g[3 + m] += g0 * r0 + g1 * r1 + g2 * r2;
+        da[m] += g0 * g0 + g1 * g1 + g2 * g2;
       }
-      rb0 = -sw * r0; rb1 = -sw * r1; rb2 = -sw * r2;
       e += r0 * r0 + r1 * r1 + r2 * r2;
     }
-    const Seg sg = seg_info(a);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) c[k] = seg_sum(c[k], sg.flags);
-    if (ok && sg.head) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) atomicAdd(&pr.q[k * pl + a], c[k]);
-#pragma unroll
-      for (int k = 0; k < 3; ++k) atomicAdd(&pr.acc[k * pl + a], c[6 + k]);
+    const int n0 = pr.irow[i], n1 = pr.irow[i + 1];
+    for (int k = n0; k < n1; ++k) {
+      const int j = pr.isrc[k];
+      float xj[3];
+      load_vec3(pr.vrec, j, xj);
+      const GeoRec gj = load_geo(pr.grec, j);
+      const float vx = gj.U[0] - gi.U[0], vy = gj.U[1] - gi.U[1], vz = gj.U[2] - gi.U[2];
+      const RotV R = rot_apply_cs(gj.cs[0], gj.cs[1], gj.cs[2], gj.cs[3], gj.cs[4], gj.cs[5], vx, vy, vz);
+      g[0] -= sw * (sw * ((xj[0] - xi[0]) + (vx - R.rv[0])));
+      g[1] -= sw * (sw * ((xj[1] - xi[1]) + (vy - R.rv[1])));
+      g[2] -= sw * (sw * ((xj[2] - xi[2]) + (vz - R.rv[2])));
     }
-    if (ok) {
-      atomicAdd(&pr.q[b], rb0);
-      atomicAdd(&pr.q[pl + b], rb1);
-      atomicAdd(&pr.q[2 * pl + b], rb2);
-    }
-  }
-  pdl_trigger();
-  if (publish_partials(part, blockIdx.x, e, 0.0, &s->counter, pr.echunk_end - pr.echunk_begin)) {
-    double a, b;
-    gather_partials(part, pr.echunk_begin, pr.echunk_end, &s->counter, a, b);
-    if (threadIdx.x == 0) s->part1 = a;
-  }
-}
-
-__global__ void __launch_bounds__(NT) k_mesh_init_f(const MeshProb* __restrict__ probs,
-                                                    const Chunk* __restrict__ chunks,
-                                                    double* __restrict__ part, int k_outer,
-                                                    float dmin, float dmax) {
-  pdl_begin();
-  const Chunk ch = chunks[blockIdx.x];
-  const MeshProb pr = probs[ch.prob];
-  Scalars* s = pr.s;
-  if (s->done) return;
-  const long long pl = pr.Vp;
-  const float lam = pr.lm ? s->lambda_f : 0.0f;
-  float rz = 0.f;
-  for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
-    float dg[4];
-    dg[0] = pr.degw[v];
-    dg[1] = pr.acc[v]; dg[2] = pr.acc[pl + v]; dg[3] = pr.acc[2 * pl + v];
+    const float dg[4] = {pr.degw[i], da[0], da[1], da[2]};
     float mv[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       float dcv;
       mv[k] = minv_entry(dg[k], lam, dmin, dmax, pr.use_precond, &dcv);
-      pr.m[k * pl + v] = mv[k];
-      if (pr.lm) pr.dc[k * pl + v] = dcv;
-      if (pr.diag_out) pr.diag_out[k * pl + v] = dg[k];
+      pr.m[k * pl + i] = mv[k];
+      if (pr.lm) pr.dc[k * pl + i] = dcv;
+      if (pr.diag_out) pr.diag_out[k * pl + i] = dg[k];
     }
+    float rz = 0.f;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      const float g = pr.q[c * pl + v];
-      const float b = -g;
-      pr.r[c * pl + v] = b;
-      pr.d[c * pl + v] = 0.f;
-      if (pr.jtf_out) pr.jtf_out[c * pl + v] = g;
+      const float b = -g[c];
+      pr.r[c * pl + i] = b;
+      pr.d[c * pl + i] = 0.f;
+      if (pr.jtf_out) pr.jtf_out[c * pl + i] = g[c];
       rz += b * (mv[c < 3 ? 0 : c - 2] * b);
     }
+    acc_rz += rz;
+    acc_E += e;
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, rz, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
-    double a, b;
-    gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, a, b);
+  if (publish_partials(part, blockIdx.x, acc_rz, acc_E, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+    double rz, E;
+    gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, rz, E);
     if (threadIdx.x == 0) {
-      const double E = s->part0 + s->part1;
-      s->rz = a;
+      s->rz = rz;
       s->E = E;
       if (pr.Ehist && k_outer >= 0) pr.Ehist[k_outer] = E;
       s->beta_f = 0.f;
-      s->pcg_active = (a != 0.0) && isfinite(a);
-      if (!isfinite(a) || !isfinite(E)) s->nonfinite = 1;
+      s->pcg_active = (rz != 0.0) && isfinite(rz);
+      if (!isfinite(rz) || !isfinite(E)) s->nonfinite = 1;
     }
   }
 }
@@ -220,18 +206,13 @@ __global__ void __launch_bounds__(NT) k_mesh_init_f(const MeshProb* __restrict__
 // ---------------------------------------------------------------------------
 // PCGStep: applyJTJ
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float4 ld4g(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-__device__ __forceinline__ float c4(const float4& a, int k) {
-  return k == 0 ? a.x : (k == 1 ? a.y : (k == 2 ? a.z : a.w));
-}
-
-// Direction update and the vertex rows of q (fit + damping), four vertices per
-// thread: every load of a quad is issued before any store.  Vertex ranges
-// start at multiples of 256 and the planes are padded to 32 (zeros), so a quad
-// never leaves the plane.
+// Direction update p = z + beta p (or p = p_override), four vertices per
+// thread from the planes (every load of a quad before any store), written to
+// the planes and to the 6-vector records.  Vertex ranges start at multiples
+// of 256 and the planes are padded to 32 (zeros), so a quad never leaves the
+// plane; records are written for real vertices only.
 __global__ void __launch_bounds__(NT) k_mesh_apply_v(const MeshProb* __restrict__ probs,
                                                      const Chunk* __restrict__ chunks,
-                                                     double* __restrict__ part,
                                                      const float* __restrict__ p_override, int par,
                                                      int update) {
   pdl_begin();
@@ -241,10 +222,8 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_v(const MeshProb* __restrict_
   if (s->done || !s->pcg_active) return;
   const long long pl = pr.Vp;
   const float beta = s->beta_f;
-  const float lam = pr.lm ? s->lambda_f : 0.0f;
   const float* __restrict__ pin = p_override ? p_override : pr.p + (long long)(par & 1) * 6 * pl;
   float* __restrict__ pout = pr.p + (long long)((par + 1) & 1) * 6 * pl;
-  float acc = 0.f;
   const int q0 = ch.begin / 4, q1 = (ch.end + 3) / 4;
   for (int qi = q0 + threadIdx.x; qi < q1; qi += NT) {
     const int v0 = 4 * qi;
@@ -274,45 +253,28 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_v(const MeshProb* __restrict_
 #pragma unroll
       for (int c = 0; c < 6; ++c) pv[c] = ld4g(pin + c * pl + v0);
     }
-    float4 dc[4];
-    if (pr.lm) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) dc[k] = ld4g(pr.dc + k * pl + v0);
-    }
-    float q[6][4];
-#pragma unroll
-    for (int c = 0; c < 6; ++c)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) q[c][k] = pr.lm ? lam * c4(dc[c < 3 ? 0 : c - 2], k) * c4(pv[c], k) : 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int v = v0 + k;
-      if (v < pr.V && handle_of(pr, v) >= 0) {
-        q[0][k] += pr.w_fit * c4(pv[0], k);
-        q[1][k] += pr.w_fit * c4(pv[1], k);
-        q[2][k] += pr.w_fit * c4(pv[2], k);
+      if (v < pr.V) {
+        pr.vrec[2 * v] = make_float4(c4(pv[0], k), c4(pv[1], k), c4(pv[2], k), c4(pv[3], k));
+        pr.vrec[2 * v + 1] = make_float4(c4(pv[4], k), c4(pv[5], k), 0.f, 0.f);
       }
     }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      *reinterpret_cast<float4*>(pr.q + c * pl + v0) = make_float4(q[c][0], q[c][1], q[c][2], q[c][3]);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc += c4(pv[c], k) * q[c][k];
-    }
-  }
-  pdl_trigger();
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
-    double a, b;
-    gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, a, b);
-    if (threadIdx.x == 0) s->part0 = a;
   }
 }
 
-// Edge rows of J^T J p; p.q = p^T (fit + damping) p + sum_e |J_e p|^2.
-__global__ void __launch_bounds__(NT) k_mesh_apply_e(const MeshProb* __restrict__ probs,
-                                                     const Chunk* __restrict__ chunks,
-                                                     double* __restrict__ part,
-                                                     const float* __restrict__ p_override, int par) {
+// Gather pass: q_i = (fit + damping) p_i + sum over out-edges (i, j) of the
+// own rows s_w J_e p (displacement) and g_m . J_e p (angles) + sum over
+// in-edges (j, i) of -s_w J_e p (displacement), with
+//   J_e p = s_w (p_a,d - p_b,d) + sum_m g_m p_a,m   for e = (a, b);
+// float64 p.q -> alpha.  The neighbour indices of the first KB out- and
+// in-edges are loaded together before any record is needed; the kernel is
+// bound by these dependent load chains, so it is compiled for
+// MESH_PULL_MIN_BLOCKS resident blocks per SM (measured best at 4).
+__global__ void __launch_bounds__(NT, MESH_PULL_MIN_BLOCKS) k_mesh_apply_pull(const MeshProb* __restrict__ probs,
+                                                                             const Chunk* __restrict__ chunks,
+                                                                             double* __restrict__ part) {
   pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
@@ -320,59 +282,81 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_e(const MeshProb* __restrict_
   if (s->done || !s->pcg_active) return;
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
-  const float* __restrict__ p = p_override ? p_override : pr.p + (long long)((par + 1) & 1) * 6 * pl;
+  const float lam = pr.lm ? s->lambda_f : 0.0f;
   float acc = 0.f;
-  for (int base = ch.begin; base < ch.end; base += NT) {
-    const int ei = base + (int)threadIdx.x;
-    const bool ok = ei < ch.end;
-    const int a = ok ? pr.e0[ei] : -1;
-    float c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    int b = 0;
-    float jb0 = 0.f, jb1 = 0.f, jb2 = 0.f;
-    if (ok) {
-      b = pr.e1[ei];
-      const float vx = pr.U[a] - pr.U[b];
-      const float vy = pr.U[pl + a] - pr.U[pl + b];
-      const float vz = pr.U[2 * pl + a] - pr.U[2 * pl + b];
-      const RotV R = rot_apply_cs(pr.csn[a], pr.csn[pl + a], pr.csn[2 * pl + a], pr.csn[3 * pl + a],
-                                    pr.csn[4 * pl + a], pr.csn[5 * pl + a], vx, vy, vz);
-      const float pa3 = p[3 * pl + a], pa4 = p[4 * pl + a], pa5 = p[5 * pl + a];
-      float j0 = sw * (p[a] - p[b]);
-      float j1 = sw * (p[pl + a] - p[pl + b]);
-      float j2 = sw * (p[2 * pl + a] - p[2 * pl + b]);
-      float g[3][3];
+  for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
+    const int o0 = pr.orow[i], o1 = pr.orow[i + 1];
+    const int n0 = pr.irow[i], n1 = pr.irow[i + 1];
+    int jo[KB], ji[KB];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        g[m][0] = -sw * R.g[m][0]; g[m][1] = -sw * R.g[m][1]; g[m][2] = -sw * R.g[m][2];
+    for (int t = 0; t < KB; ++t) {
+      jo[t] = o0 + t < o1 ? pr.e1[o0 + t] : 0;
+      ji[t] = n0 + t < n1 ? pr.isrc[n0 + t] : 0;
+    }
+    float pi[6];
+    load_vec(pr.vrec, i, pi);
+    const GeoRec gi = load_geo(pr.grec, i);
+    float q[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) q[c] = pr.lm ? lam * pr.dc[(c < 3 ? 0 : c - 2) * pl + i] * pi[c] : 0.f;
+    if (handle_of(pr, i) >= 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) q[c] += pr.w_fit * pi[c];
+    }
+#pragma unroll
+    for (int t = 0; t < KB + 1; ++t) {
+      // t < KB: one prefetched out-edge (if the row has it); t == KB: the rest of a longer row
+      const int kb = t < KB ? o0 + t : o0 + KB, ke = t < KB ? min(o0 + t + 1, o1) : o1;
+      for (int k = kb; k < ke; ++k) {
+        const int j = t < KB ? jo[t] : pr.e1[k];
+        float pj[3];
+        load_vec3(pr.vrec, j, pj);
+        const float4 uj = __ldg(pr.grec + 3 * j);
+        const float vx = gi.U[0] - uj.x, vy = gi.U[1] - uj.y, vz = gi.U[2] - uj.z;
+        const RotV R = rot_apply_cs(gi.cs[0], gi.cs[1], gi.cs[2], gi.cs[3], gi.cs[4], gi.cs[5], vx, vy, vz);
+        float j0 = sw * (pi[0] - pj[0]), j1 = sw * (pi[1] - pj[1]), j2 = sw * (pi[2] - pj[2]);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          j0 -= sw * R.g[m][0] * pi[3 + m];
+          j1 -= sw * R.g[m][1] * pi[3 + m];
+          j2 -= sw * R.g[m][2] * pi[3 + m];
+        }
+        q[0] += sw * j0; q[1] += sw * j1; q[2] += sw * j2;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) q[3 + m] -= sw * (R.g[m][0] * j0 + R.g[m][1] * j1 + R.g[m][2] * j2);
       }
-      j0 += g[0][0] * pa3 + g[1][0] * pa4 + g[2][0] * pa5;
-      j1 += g[0][1] * pa3 + g[1][1] * pa4 + g[2][1] * pa5;
-      j2 += g[0][2] * pa3 + g[1][2] * pa4 + g[2][2] * pa5;
-      c[0] = sw * j0; c[1] = sw * j1; c[2] = sw * j2;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) c[3 + m] = g[m][0] * j0 + g[m][1] * j1 + g[m][2] * j2;
-      jb0 = -sw * j0; jb1 = -sw * j1; jb2 = -sw * j2;
-      acc += j0 * j0 + j1 * j1 + j2 * j2;
     }
-    const Seg sg = seg_info(a);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) c[k] = seg_sum(c[k], sg.flags);
-    if (ok && sg.head) {
+    for (int t = 0; t < KB + 1; ++t) {
+      const int kb = t < KB ? n0 + t : n0 + KB, ke = t < KB ? min(n0 + t + 1, n1) : n1;
+      for (int k = kb; k < ke; ++k) {
+        const int j = t < KB ? ji[t] : pr.isrc[k];
+        float pj[6];
+        load_vec(pr.vrec, j, pj);
+        const GeoRec gj = load_geo(pr.grec, j);
+        const float vx = gj.U[0] - gi.U[0], vy = gj.U[1] - gi.U[1], vz = gj.U[2] - gi.U[2];
+        const RotV R = rot_apply_cs(gj.cs[0], gj.cs[1], gj.cs[2], gj.cs[3], gj.cs[4], gj.cs[5], vx, vy, vz);
+        float j0 = sw * (pj[0] - pi[0]), j1 = sw * (pj[1] - pi[1]), j2 = sw * (pj[2] - pi[2]);
 #pragma unroll
-      for (int k = 0; k < 6; ++k) atomicAdd(&pr.q[k * pl + a], c[k]);
+        for (int m = 0; m < 3; ++m) {
+          j0 -= sw * R.g[m][0] * pj[3 + m];
+          j1 -= sw * R.g[m][1] * pj[3 + m];
+          j2 -= sw * R.g[m][2] * pj[3 + m];
+        }
+        q[0] -= sw * j0; q[1] -= sw * j1; q[2] -= sw * j2;
+      }
     }
-    if (ok) {
-      atomicAdd(&pr.q[b], jb0);
-      atomicAdd(&pr.q[pl + b], jb1);
-      atomicAdd(&pr.q[2 * pl + b], jb2);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      pr.q[c * pl + i] = q[c];
+      acc += pi[c] * q[c];
     }
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.echunk_end - pr.echunk_begin)) {
-    double a, b;
-    gather_partials(part, pr.echunk_begin, pr.echunk_end, &s->counter, a, b);
+  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+    double pq, unused;
+    gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
-      const double pq = s->part0 + a;
       s->pq = pq;
       if (pq > 0.0 && isfinite(pq)) {
         s->alpha_f = (float)(s->rz / pq);
@@ -557,14 +541,13 @@ __global__ void __launch_bounds__(NT) k_mesh_step(const MeshProb* __restrict__ p
 // launchers
 // ---------------------------------------------------------------------------
 void launch_mesh_init(const MeshLaunch& L, int k_outer, float dmin, float dmax) {
-  launch_pdl(k_mesh_init_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
-  launch_pdl(k_mesh_init_e, L.nechunks, NT, 0, L.stream, L.probs, L.echunks, L.part);
-  launch_pdl(k_mesh_init_f, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, k_outer, dmin, dmax);
+  launch_pdl(k_mesh_init_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks);
+  launch_pdl(k_mesh_init_pull, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, k_outer, dmin, dmax);
 }
 
 void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, int update) {
-  launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, p_override, par, update);
-  launch_pdl(k_mesh_apply_e, L.nechunks, NT, 0, L.stream, L.probs, L.echunks, L.part, p_override, par);
+  launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, p_override, par, update);
+  launch_pdl(k_mesh_apply_pull, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
 }
 
 void launch_mesh_update(const MeshLaunch& L, int par) {

@@ -108,10 +108,13 @@ struct MeshProb {
   const float* degw;            // w_reg * (outdeg + indeg) + w_fit[handle]
   const int* e0;                // edges sorted by (v0, v1)
   const int* e1;
+  const int* orow;              // V + 1: out-edges of v are e1[orow[v] .. orow[v+1])
+  const int* irow;              // V + 1: in-edges of v come from isrc[irow[v] .. irow[v+1])
+  const int* isrc;              // E: sources of the in-edges, ascending per vertex
   float *d, *r, *p, *q;         // 6 planes each
   float *m, *dc;                // 4 planes: displacement, ax, ay, az
-  float* acc;                   // 3 planes: angle-diagonal accumulators (PCGInit)
-  float* csn;                   // 6 planes: cos ax, sin ax, cos ay, sin ay, cos az, sin az (PCGInit)
+  float4* grec;                 // 3 float4 per vertex: U, cos / sin of the angles (PCGInit)
+  float4* vrec;                 // 2 float4 per vertex: x (PCGInit) or p (applyJTJ)
   const int* hbeg;              // per vertex tile: first handle
   const int* hpix;              // handle vertex, sorted
   const float* htgt;            // 3 per handle

@@ -21,7 +21,6 @@ struct MeshLaunch {
   const Chunk* vchunks;
   const Chunk* echunks;
   double* part;
-  float* acc;
   int nvchunks, nechunks;
   cudaStream_t stream;
 };

@@ -52,11 +52,11 @@ struct opt_problem {
   optgb::Chunk* d_vchunks = nullptr;
   optgb::Chunk* d_echunks = nullptr;
   int nvchunks = 0, nechunks = 0;
-  float* d_acc = nullptr;
   // host copies kept for building the materialized Jacobian
   std::vector<unsigned char> h_mask;    // grid mask (empty = none)
   std::vector<int> h_hpix;              // grid handles (pitched index) / mesh handles (vertex)
-  std::vector<int> h_e0, h_e1;          // sorted edges
+  std::vector<int> h_e0, h_e1;          // sorted edges (internal vertex order)
+  int* d_perm = nullptr;                // graphs: internal vertex k is the caller's vertex d_perm[k]
   CsrJ csr;
   // common
   double* d_part = nullptr;
@@ -99,6 +99,11 @@ namespace optgb {
 opt_status batch_prepare_round(opt_batch* b, const opt_solve_params& p);
 void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_t st);
 opt_status batch_read_scalars(opt_batch* b, Scalars* host_out, cudaStream_t st);
+// api.cu: caller planes (dense rows for grids, caller vertex order for
+// graphs) <-> internal planes
+opt_status copy_planes_in(const opt_problem* pb, float* internal, float* const* user, int n, cudaStream_t st);
+opt_status copy_planes_out(const opt_problem* pb, float* const* user, const float* internal, int n,
+                           cudaStream_t st);
 // materialize.cu
 opt_status csr_build(opt_problem* pb);
 void csr_evalj(opt_problem* pb, cudaStream_t st);

@@ -71,7 +71,9 @@ size_t estimate_grid(const opt_grid_desc& d, int tile_w) {
 }
 size_t estimate_graph(const opt_graph_desc& d) {
   const size_t pl = round32((size_t)d.V);
-  return 57 * pl * 4 + (size_t)d.E * 8 + (size_t)d.n_handles * 16 + (1 << 16);
+  // 48 planes + the 3 + 2 float4 records per vertex, edges (sorted copy and
+  // in-edge sources), row pointers
+  return 68 * pl * 4 + (size_t)d.E * 12 + 8 * pl + (size_t)d.n_handles * 16 + (1 << 16);
 }
 
 }  // namespace
@@ -121,29 +123,11 @@ void finish(opt_server* s, ServeReq* r, opt_status st) {
 
 // Copies the member's working unknowns back to the caller's planes.
 opt_status write_back(opt_problem* pb, cudaStream_t st) {
-  for (int c = 0; c < pb->nx; ++c) {
-    cudaError_t e;
-    if (pb->kind == K_MESH)
-      e = cudaMemcpyAsync(pb->user_x[c], pb->x + c * pb->plane, (size_t)pb->V * 4, cudaMemcpyDeviceToDevice, st);
-    else
-      e = cudaMemcpy2DAsync(pb->user_x[c], (size_t)pb->W * 4, pb->x + c * pb->plane, (size_t)pb->P * 4,
-                            (size_t)pb->W * 4, pb->H, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return OPT_ERR_CUDA;
-  }
-  return OPT_OK;
+  return copy_planes_out(pb, pb->user_x, pb->x, pb->nx, st);
 }
 
 opt_status copy_in(opt_problem* pb, cudaStream_t st) {
-  for (int c = 0; c < pb->nx; ++c) {
-    cudaError_t e;
-    if (pb->kind == K_MESH)
-      e = cudaMemcpyAsync(pb->x + c * pb->plane, pb->user_x[c], (size_t)pb->V * 4, cudaMemcpyDeviceToDevice, st);
-    else
-      e = cudaMemcpy2DAsync(pb->x + c * pb->plane, (size_t)pb->P * 4, pb->user_x[c], (size_t)pb->W * 4,
-                            (size_t)pb->W * 4, pb->H, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return OPT_ERR_CUDA;
-  }
-  return OPT_OK;
+  return copy_planes_in(pb, pb->x, pb->user_x, pb->nx, st);
 }
 
 }  // namespace

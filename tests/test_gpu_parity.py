@@ -155,6 +155,38 @@ def test_mesh_eval_jtf(api, level, noise):
     gp.close()
 
 
+@pytest.mark.parametrize("keep", [0.6, 1.0])
+def test_mesh_one_way_edges_and_isolated_vertices(api, keep):
+    """Directed edge lists need not be symmetric: drop a random part of the
+    directed edges (some vertices lose all in- or out-edges) and duplicate a
+    few; J^T J p, J^T F, diag and E still match the oracle."""
+    import torch
+    prob = make_mesh(2, 0.25, seed=61)
+    rng = np.random.default_rng(5)
+    sel = rng.random(prob.v0.size) < keep
+    v0, v1 = prob.v0[sel], prob.v1[sel]
+    dup = rng.choice(v0.size, size=7, replace=False)
+    v0 = np.concatenate([v0, v0[dup]]).astype(np.int32)
+    v1 = np.concatenate([v1, v1[dup]]).astype(np.int32)
+    order = np.lexsort((v1, v0))
+    prob = synth.MeshProblem(prob.V, prob.urshape, v0[order], v1[order], prob.x0, prob.handle_idx,
+                             prob.handle_target)
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    gp = api.Problem(prob)
+    p = random_direction(prob, 4)
+    for lam in (0.0, 0.4):
+        q, pq = gp.apply_jtj(torch.as_tensor(p, device="cuda"), lam)
+        jtf, diag, E = oracle.jtf_diag(e, x)
+        qref = oracle.apply_jtj(e, x, p.astype(np.float64), lam, np.clip(diag, 1e-6, 1e32))
+        assert rel(q.cpu().numpy(), qref) <= TOL_PRODUCT
+        assert relE(pq, float(p.astype(np.float64) @ qref)) <= TOL_PRODUCT
+    g, d, Eg = gp.eval_jtf()
+    assert rel(g.cpu().numpy(), jtf) <= TOL_PRODUCT
+    assert rel(d.cpu().numpy(), diag) <= TOL_PRODUCT
+    assert relE(Eg, E) <= TOL_PRODUCT
+
+
 def test_mesh_unsorted_edges_are_sorted_by_the_library(api):
     import torch
     prob = make_mesh(2, 0.2, seed=51)
