@@ -783,14 +783,12 @@ __global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __res
 //   E               += w |a + e_i|^2   (own residuals only)
 // Writes r = b = -J^T F, M^-1, delta = 0, the LM diagonal, cos / sin of theta.
 constexpr int NRAW_I = 5;        // dx dy theta ux uy
-constexpr int NSTG_I = 6;        // dx dy cos sin ux uy
+constexpr int NSTG_I = 7;        // dx dy cos sin ux uy valid, quads stored as pixels 0 2 1 3
 
 struct InitSmem {
   float raw[NRAW_I][HH][SP];
-  float stg[NSTG_I][HH][SP];
-  unsigned int v[HH][SP / 4];
+  float stg[NSTG_I][HH][SP];     // halo columns -1 / 128 live at 3 / 132, in plain order
   unsigned char mk[HH][SPB];
-  unsigned char vc[HH][2];
 };
 
 struct InitPlanes {
@@ -803,61 +801,62 @@ __device__ __forceinline__ void init_issue(InitSmem& sm, const InitPlanes& pp, c
   tile_issue<NRAW_I, MASK>(sm.raw, sm.mk, pp.src, pr, x0, y0, tid);
 }
 
-// Phase 2 for one staged quad: cos / sin, copied values, validity bits.
+// Phase 2 for one staged quad: cos / sin of theta, copied values, validity,
+// in the staged order 0 2 1 3.
 template <bool MASK>
 __device__ __forceinline__ void init_stage_quad(InitSmem& sm, int row, int lane, const GridProb& pr, int gx, int gy) {
   const int c = 4 + 4 * lane;
-  const float4 th = *reinterpret_cast<const float4*>(&sm.raw[2][row][c]);
+  const float4 th = lds4(&sm.raw[2][row][c]);
   float4 cs, sn;
   sincosf(th.x, &sn.x, &cs.x);
   sincosf(th.y, &sn.y, &cs.y);
   sincosf(th.z, &sn.z, &cs.z);
   sincosf(th.w, &sn.w, &cs.w);
-  *reinterpret_cast<float4*>(&sm.stg[0][row][c]) = *reinterpret_cast<const float4*>(&sm.raw[0][row][c]);
-  *reinterpret_cast<float4*>(&sm.stg[1][row][c]) = *reinterpret_cast<const float4*>(&sm.raw[1][row][c]);
-  *reinterpret_cast<float4*>(&sm.stg[2][row][c]) = cs;
-  *reinterpret_cast<float4*>(&sm.stg[3][row][c]) = sn;
-  *reinterpret_cast<float4*>(&sm.stg[4][row][c]) = *reinterpret_cast<const float4*>(&sm.raw[3][row][c]);
-  *reinterpret_cast<float4*>(&sm.stg[5][row][c]) = *reinterpret_cast<const float4*>(&sm.raw[4][row][c]);
-  unsigned int v = 0u;
+  sts4(&sm.stg[0][row][c], swz4(lds4(&sm.raw[0][row][c])));
+  sts4(&sm.stg[1][row][c], swz4(lds4(&sm.raw[1][row][c])));
+  sts4(&sm.stg[2][row][c], swz4(cs));
+  sts4(&sm.stg[3][row][c], swz4(sn));
+  sts4(&sm.stg[4][row][c], swz4(lds4(&sm.raw[3][row][c])));
+  sts4(&sm.stg[5][row][c], swz4(lds4(&sm.raw[4][row][c])));
+  float vk[4] = {0.f, 0.f, 0.f, 0.f};
   if (gy >= 0 && gy < pr.H) {
     const unsigned int m4 = MASK ? *reinterpret_cast<const unsigned int*>(&sm.mk[row][16 + 4 * lane]) : 0u;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (gx + k < pr.W && (!MASK || ((m4 >> (8 * k)) & 0xffu) == 0u)) v |= 1u << k;
+      vk[k] = (gx + k < pr.W && (!MASK || ((m4 >> (8 * k)) & 0xffu) == 0u)) ? 1.f : 0.f;
   }
-  sm.v[row][1 + lane] = v;
+  sts4(&sm.stg[6][row][c], make_float4(vk[0], vk[2], vk[1], vk[3]));
 }
 
-// Grouped J^T F / diag / energy terms of the pair (i, j).
-__device__ __forceinline__ void init_pair(float dxi, float dyi, float ci, float si, float uxi, float uyi, float dxj,
-                                          float dyj, float cj, float sj, float uxj, float uyj, float& gx, float& gy,
-                                          float& gt, float& dt, float& e, float& npair) {
-  const float vx = uxi - uxj, vy = uyi - uyj;
-  const float ax = dxi - dxj, ay = dyi - dyj;
-  // e_k = v - R(theta_k) v
-  const float eix = vx - fmaf(ci, vx, -si * vy), eiy = vy - fmaf(si, vx, ci * vy);
-  const float ejx = vx - fmaf(cj, vx, -sj * vy), ejy = vy - fmaf(sj, vx, cj * vy);
-  const float gix = fmaf(si, vx, ci * vy), giy = fmaf(si, vy, -ci * vx);
-  const float ox = ax + eix, oy = ay + eiy;       // own residual / s_w
-  gx += ox + (ax + ejx);
-  gy += oy + (ay + ejy);
-  gt = fmaf(gix, ox, fmaf(giy, oy, gt));
-  dt = fmaf(gix, gix, fmaf(giy, giy, dt));
-  e = fmaf(ox, ox, fmaf(oy, oy, e));
-  npair += 1.f;
-}
-
-struct Quad6 {
-  float4 q[NSTG_I];
-  unsigned int v;
+// Own values of one float2 pack for PCGInit.
+struct OwnI2 {
+  float2 dx, dy, c, s, ux, uy;
+};
+struct AccI2 {
+  float2 gx, gy, gt, dt, e, np;
 };
 
-__device__ __forceinline__ void read_quad6(const InitSmem& sm, int row, int lane, Quad6& o) {
-  const int c = 4 + 4 * lane;
-#pragma unroll
-  for (int k = 0; k < NSTG_I; ++k) o.q[k] = *reinterpret_cast<const float4*>(&sm.stg[k][row][c]);
-  o.v = sm.v[row][1 + lane];
+// Grouped J^T F / diag / energy terms of the pairs (i, j) of one pack, scaled
+// by the neighbour's validity m_j.  With v = U_i - U_j, a = d_i - d_j and
+// G_k = (s_k v_x + c_k v_y, s_k v_y - c_k v_x), the rotation residual part is
+// e_k = v - R(theta_k) v = (v_x + G_k,y, v_y - G_k,x), own residual / s_w
+// o = a + e_i:
+//   J^T F_d += o + (a + e_j),  J^T F_t += G_i . o,  diag_t += |G_i|^2,
+//   E += |o|^2,  np += 1 (diag_d = 2 w np).
+__device__ __forceinline__ void init_pair2(const OwnI2& o, float2 dxj, float2 dyj, float2 cj, float2 sj, float2 uxj,
+                                           float2 uyj, float2 mj, AccI2& A) {
+  const float2 vx = sub2(o.ux, uxj), vy = sub2(o.uy, uyj), nvx = sub2(uxj, o.ux);
+  const float2 ax = sub2(o.dx, dxj), ay = sub2(o.dy, dyj);
+  const float2 gix = fma2(o.s, vx, mul2(o.c, vy)), giy = fma2(o.s, vy, mul2(o.c, nvx));
+  const float2 gjx = fma2(sj, vx, mul2(cj, vy)), gjy = fma2(sj, vy, mul2(cj, nvx));
+  const float2 ox = add2(ax, add2(vx, giy)), oy = add2(ay, sub2(vy, gix));
+  const float2 fx = add2(ox, add2(ax, add2(vx, gjy))), fy = add2(oy, add2(ay, sub2(vy, gjx)));
+  A.gx = fma2(mj, fx, A.gx);
+  A.gy = fma2(mj, fy, A.gy);
+  A.gt = fma2(mj, fma2(gix, ox, mul2(giy, oy)), A.gt);
+  A.dt = fma2(mj, fma2(gix, gix, mul2(giy, giy)), A.dt);
+  A.e = fma2(mj, fma2(ox, ox, mul2(oy, oy)), A.e);
+  A.np = add2(A.np, mj);
 }
 
 template <bool MASK>
@@ -875,20 +874,20 @@ __global__ void __launch_bounds__(NT, 2) k_warp_init_wide(const GridProb* __rest
   if (s->done) return;
   const int pl = (int)pr.plane;
   const float w = pr.w_reg, wfit = pr.w_fit;
+  const float2 w2 = make_float2(w, w);
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   float acc_rz = 0.f, acc_E = 0.f;
   InitPlanes ip;
-  {
-    const int ipl = (int)pr.plane;
-    ip.src[0] = pr.x; ip.src[1] = pr.x + ipl; ip.src[2] = pr.x + 2 * ipl; ip.src[3] = pr.c; ip.src[4] = pr.c + ipl;
-  }
+  ip.src[0] = pr.x; ip.src[1] = pr.x + pl; ip.src[2] = pr.x + 2 * pl; ip.src[3] = pr.c; ip.src[4] = pr.c + pl;
   int tc = tiles[ch.begin];
+  int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
+  int hb0 = pr.hbeg[tile_id(pr, tc)], hb1 = pr.hbeg[tile_id(pr, tc) + 1];
   init_issue<MASK>(sm, ip, pr, tile_x0(tc, W4), tile_y0(tc), tid);
   for (int t = ch.begin; t < ch.end; ++t) {
     const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
     const int gx = x0 + 4 * lane, gy = y0 + ty;
-    const int tcur = tc;
+    const int hcur0 = hb0, hcur1 = hb1;
     cp_async_wait_all();
     __syncthreads();
     init_stage_quad<MASK>(sm, ty + 1, lane, pr, gx, gy);
@@ -909,77 +908,81 @@ __global__ void __launch_bounds__(NT, 2) k_warp_init_wide(const GridProb* __rest
       sm.stg[5][row][col] = sm.raw[4][row][col];
       const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
       const bool ok = hy < pr.H && hx >= 0 && hx < pr.W;
-      sm.vc[row][side] = (unsigned char)(ok && (!MASK || halo_mask(sm.mk, row, side) == 0));
+      sm.stg[6][row][col] = (ok && (!MASK || halo_mask(sm.mk, row, side) == 0)) ? 1.f : 0.f;
     }
     __syncthreads();
     if (t + 1 < ch.end) {
-      tc = tiles[t + 1];
+      tc = tn;
       init_issue<MASK>(sm, ip, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+      const int tidn = tile_id(pr, tc);
+      hb0 = pr.hbeg[tidn];
+      hb1 = pr.hbeg[tidn + 1];
+      if (t + 2 < ch.end) tn = tiles[t + 2];
     }
     if (gy < pr.H) {
-      Quad6 O;
-      read_quad6(sm, ty + 1, lane, O);
-      float L[NSTG_I], R[NSTG_I];
+      const int c = 4 + 4 * lane;
+      float4 O[NSTG_I];
 #pragma unroll
-      for (int k = 0; k < NSTG_I; ++k) {
-        L[k] = __shfl_up_sync(0xffffffffu, O.q[k].w, 1);
-        R[k] = __shfl_down_sync(0xffffffffu, O.q[k].x, 1);
-      }
-      unsigned int lv = (__shfl_up_sync(0xffffffffu, O.v, 1) >> 3) & 1u;
-      unsigned int rv = __shfl_down_sync(0xffffffffu, O.v, 1) & 1u;
-      if (lane == 0) {
+      for (int k = 0; k < NSTG_I; ++k) O[k] = lds4(&sm.stg[k][ty + 1][c]);
+      const OwnI2 oa = {lo2(O[0]), lo2(O[1]), lo2(O[2]), lo2(O[3]), lo2(O[4]), lo2(O[5])};
+      const OwnI2 ob = {hi2(O[0]), hi2(O[1]), hi2(O[2]), hi2(O[3]), hi2(O[4]), hi2(O[5])};
+      const float2 z2 = make_float2(0.f, 0.f);
+      AccI2 A = {z2, z2, z2, z2, z2, z2}, B = A;
+      {
+        float L[NSTG_I], R[NSTG_I];
 #pragma unroll
-        for (int k = 0; k < NSTG_I; ++k) L[k] = sm.stg[k][ty + 1][3];
-        lv = sm.vc[ty + 1][0];
-      }
-      if (lane == 31) {
-#pragma unroll
-        for (int k = 0; k < NSTG_I; ++k) R[k] = sm.stg[k][ty + 1][4 + W4];
-        rv = sm.vc[ty + 1][1];
-      }
-      Quad6 Up, Dn;
-      read_quad6(sm, ty, lane, Up);
-      read_quad6(sm, ty + 2, lane, Dn);
-      float gxv[4], gyv[4], gtv[4], ddv[4], dtv[4], ev[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        float gxx = 0.f, gyy = 0.f, gt = 0.f, dt = 0.f, e = 0.f, np = 0.f;
-        const float dxi = cmp(O.q[0], k), dyi = cmp(O.q[1], k), ci = cmp(O.q[2], k), si = cmp(O.q[3], k);
-        const float uxi = cmp(O.q[4], k), uyi = cmp(O.q[5], k);
-        if ((O.v >> k) & 1u) {
-          if (k == 0 ? lv : ((O.v >> (k - 1)) & 1u)) {
-            if (k == 0) init_pair(dxi, dyi, ci, si, uxi, uyi, L[0], L[1], L[2], L[3], L[4], L[5], gxx, gyy, gt, dt, e, np);
-            else init_pair(dxi, dyi, ci, si, uxi, uyi, cmp(O.q[0], k - 1), cmp(O.q[1], k - 1), cmp(O.q[2], k - 1),
-                           cmp(O.q[3], k - 1), cmp(O.q[4], k - 1), cmp(O.q[5], k - 1), gxx, gyy, gt, dt, e, np);
-          }
-          if (k == 3 ? rv : ((O.v >> (k + 1)) & 1u)) {
-            if (k == 3) init_pair(dxi, dyi, ci, si, uxi, uyi, R[0], R[1], R[2], R[3], R[4], R[5], gxx, gyy, gt, dt, e, np);
-            else init_pair(dxi, dyi, ci, si, uxi, uyi, cmp(O.q[0], k + 1), cmp(O.q[1], k + 1), cmp(O.q[2], k + 1),
-                           cmp(O.q[3], k + 1), cmp(O.q[4], k + 1), cmp(O.q[5], k + 1), gxx, gyy, gt, dt, e, np);
-          }
-          if ((Up.v >> k) & 1u)
-            init_pair(dxi, dyi, ci, si, uxi, uyi, cmp(Up.q[0], k), cmp(Up.q[1], k), cmp(Up.q[2], k), cmp(Up.q[3], k),
-                      cmp(Up.q[4], k), cmp(Up.q[5], k), gxx, gyy, gt, dt, e, np);
-          if ((Dn.v >> k) & 1u)
-            init_pair(dxi, dyi, ci, si, uxi, uyi, cmp(Dn.q[0], k), cmp(Dn.q[1], k), cmp(Dn.q[2], k), cmp(Dn.q[3], k),
-                      cmp(Dn.q[4], k), cmp(Dn.q[5], k), gxx, gyy, gt, dt, e, np);
+        for (int k = 0; k < NSTG_I; ++k) {
+          L[k] = __shfl_up_sync(0xffffffffu, O[k].w, 1);
+          R[k] = __shfl_down_sync(0xffffffffu, O[k].x, 1);
         }
-        gxv[k] = w * gxx;
-        gyv[k] = w * gyy;
-        gtv[k] = w * gt;
-        ddv[k] = 2.f * w * np;
-        dtv[k] = w * dt;
-        ev[k] = w * e;
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < NSTG_I; ++k) L[k] = sm.stg[k][ty + 1][3];
+        }
+        if (lane == 31) {
+#pragma unroll
+          for (int k = 0; k < NSTG_I; ++k) R[k] = sm.stg[k][ty + 1][4 + W4];
+        }
+        // A = pixels {0, 2}: left {-1, 1}, right {1, 3} = B
+        init_pair2(oa, make_float2(L[0], O[0].z), make_float2(L[1], O[1].z), make_float2(L[2], O[2].z),
+                   make_float2(L[3], O[3].z), make_float2(L[4], O[4].z), make_float2(L[5], O[5].z),
+                   make_float2(L[6], O[6].z), A);
+        init_pair2(oa, ob.dx, ob.dy, ob.c, ob.s, ob.ux, ob.uy, hi2(O[6]), A);
+        // B = pixels {1, 3}: left {0, 2} = A, right {2, 4}
+        init_pair2(ob, oa.dx, oa.dy, oa.c, oa.s, oa.ux, oa.uy, lo2(O[6]), B);
+        init_pair2(ob, make_float2(O[0].y, R[0]), make_float2(O[1].y, R[1]), make_float2(O[2].y, R[2]),
+                   make_float2(O[3].y, R[3]), make_float2(O[4].y, R[4]), make_float2(O[5].y, R[5]),
+                   make_float2(O[6].y, R[6]), B);
       }
+#pragma unroll 1
+      for (int dr = 0; dr < 2; ++dr) {
+        float4 U[NSTG_I];
+        const int row = dr ? ty + 2 : ty;
+#pragma unroll
+        for (int k = 0; k < NSTG_I; ++k) U[k] = lds4(&sm.stg[k][row][c]);
+        init_pair2(oa, lo2(U[0]), lo2(U[1]), lo2(U[2]), lo2(U[3]), lo2(U[4]), lo2(U[5]), lo2(U[6]), A);
+        init_pair2(ob, hi2(U[0]), hi2(U[1]), hi2(U[2]), hi2(U[3]), hi2(U[4]), hi2(U[5]), hi2(U[6]), B);
+      }
+      // scale by w and the own validity, back to plain pixel order
+      const float2 wa = mul2(w2, lo2(O[6])), wb = mul2(w2, hi2(O[6]));
+      const float2 wa2 = add2(wa, wa), wb2 = add2(wb, wb);
+      auto plain = [](float2 a, float2 b) { return make_float4(a.x, b.x, a.y, b.y); };
+      const float4 gx4 = plain(mul2(wa, A.gx), mul2(wb, B.gx)), gy4 = plain(mul2(wa, A.gy), mul2(wb, B.gy));
+      const float4 gt4 = plain(mul2(wa, A.gt), mul2(wb, B.gt)), dt4 = plain(mul2(wa, A.dt), mul2(wb, B.dt));
+      const float4 e4 = plain(mul2(wa, A.e), mul2(wb, B.e)), dd4 = plain(mul2(wa2, A.np), mul2(wb2, B.np));
+      float gxv[4] = {gx4.x, gx4.y, gx4.z, gx4.w}, gyv[4] = {gy4.x, gy4.y, gy4.z, gy4.w};
+      float gtv[4] = {gt4.x, gt4.y, gt4.z, gt4.w}, dtv[4] = {dt4.x, dt4.y, dt4.z, dt4.w};
+      float ev[4] = {e4.x, e4.y, e4.z, e4.w}, ddv[4] = {dd4.x, dd4.y, dd4.z, dd4.w};
+      const float vf[4] = {O[6].x, O[6].z, O[6].y, O[6].w};
+      const float4 dxp = swz4(O[0]), dyp = swz4(O[1]);
       const long long i = (long long)gy * pr.P + gx;
-      const int tid_ = tile_id(pr, tcur);
-      for (int h = pr.hbeg[tid_]; h < pr.hbeg[tid_ + 1]; ++h) {
+      for (int h = hcur0; h < hcur1; ++h) {
         const long long k = pr.hpix[h] - i;
-        if (k >= 0 && k < 4 && ((O.v >> k) & 1u)) {
+        if (k >= 0 && k < 4) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            if (kk == k) {
-              const float rx = cmp(O.q[0], kk) - pr.htgt[2 * h], ry = cmp(O.q[1], kk) - pr.htgt[2 * h + 1];
+            if (kk == k && vf[kk] != 0.f) {
+              const float rx = cmp(dxp, kk) - pr.htgt[2 * h], ry = cmp(dyp, kk) - pr.htgt[2 * h + 1];
               gxv[kk] += wfit * rx;
               gyv[kk] += wfit * ry;
               ddv[kk] += wfit;
@@ -1007,8 +1010,8 @@ __global__ void __launch_bounds__(NT, 2) k_warp_init_wide(const GridProb* __rest
       *reinterpret_cast<float4*>(pr.d + i) = z;
       *reinterpret_cast<float4*>(pr.d + pl + i) = z;
       *reinterpret_cast<float4*>(pr.d + 2 * pl + i) = z;
-      *reinterpret_cast<float4*>(pr.csn + i) = O.q[2];
-      *reinterpret_cast<float4*>(pr.csn + pl + i) = O.q[3];
+      *reinterpret_cast<float4*>(pr.csn + i) = swz4(O[2]);
+      *reinterpret_cast<float4*>(pr.csn + pl + i) = swz4(O[3]);
       if (pr.lm) {
         *reinterpret_cast<float4*>(pr.dc + i) = make_float4(cd[0], cd[1], cd[2], cd[3]);
         *reinterpret_cast<float4*>(pr.dc + pl + i) = make_float4(ct[0], ct[1], ct[2], ct[3]);
