@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -124,20 +125,29 @@ std::vector<int> morton_order(const std::vector<float>* U, int V) {
     x = (x | (x << 2)) & 0x09249249u;
     return x;
   };
-  std::vector<std::pair<uint32_t, int>> key((size_t)V);
+  std::vector<uint32_t> code((size_t)V);
   for (int v = 0; v < V; ++v) {
-    uint32_t code = 0;
+    uint32_t cv = 0;
     for (int c = 0; c < 3; ++c) {
       const float ext = hi[c] - lo[c];
       const float t = ext > 0.f ? (U[c][v] - lo[c]) / ext : 0.f;
       const uint32_t qv = (uint32_t)std::min(1023.f, std::max(0.f, t * 1023.f));
-      code |= spread(qv) << c;
+      cv |= spread(qv) << c;
     }
-    key[v] = {code, v};
+    code[v] = cv;
   }
-  std::sort(key.begin(), key.end());
-  std::vector<int> perm((size_t)V);
-  for (int k = 0; k < V; ++k) perm[k] = key[k].second;
+  // stable least-significant-digit radix sort of the 30-bit codes (3 x 10
+  // bits): equal codes keep the caller order
+  std::vector<int> perm((size_t)V), tmp((size_t)V);
+  for (int v = 0; v < V; ++v) perm[v] = v;
+  for (int pass = 0; pass < 3; ++pass) {
+    const int shift = 10 * pass;
+    std::vector<int> cnt(1025, 0);
+    for (int v = 0; v < V; ++v) cnt[((code[perm[v]] >> shift) & 1023u) + 1] += 1;
+    for (int b = 0; b < 1024; ++b) cnt[b + 1] += cnt[b];
+    for (int v = 0; v < V; ++v) tmp[(size_t)cnt[(code[perm[v]] >> shift) & 1023u]++] = perm[v];
+    perm.swap(tmp);
+  }
   return perm;
 }
 
@@ -146,15 +156,48 @@ std::vector<int> morton_order(const std::vector<float>* U, int V) {
 
 namespace {
 
+// Problem memory comes from a library-owned stream-ordered pool per device
+// that keeps freed blocks: planning and tearing down problems (the server
+// does both continuously) then neither goes back to the driver nor waits for
+// the device.  nullptr if the pool cannot be made (plain cudaMalloc then).
+cudaMemPool_t problem_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[128] = {};
+  static bool failed[128] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev] && !failed[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&pools[dev], &props) != cudaSuccess) {
+      pools[dev] = nullptr;
+      failed[dev] = true;
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  return pools[dev];
+}
+
+// Zero-filled device array owned by the problem (ordered on the legacy
+// stream; planning ends with a synchronising copy before any other stream
+// touches it).
 template <class T>
 opt_status dalloc(opt_problem* pb, T** ptr, size_t n) {
   void* p = nullptr;
   const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
-  cudaError_t e = cudaMalloc(&p, bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  cudaMemPool_t pool = problem_pool();
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, nullptr) : cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "device allocation");
   pb->allocs.push_back(p);
-  e = cudaMemset(p, 0, bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemset");
+  pb->pooled.push_back(pool != nullptr);
+  e = cudaMemsetAsync(p, 0, bytes, nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   *ptr = static_cast<T*>(p);
   return OPT_OK;
 }
@@ -744,10 +787,23 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   for (int e = 1; e < E && sorted; ++e)
     if (e0[e] < e0[e - 1] || (e0[e] == e0[e - 1] && e1[e] < e1[e - 1])) sorted = false;
   if (!sorted) {
-    std::vector<long long> key((size_t)E);
-    for (int e = 0; e < E; ++e) key[e] = (long long)e0[e] * V + e1[e];
-    std::sort(key.begin(), key.end());
-    for (int e = 0; e < E; ++e) { e0[e] = (int)(key[e] / V); e1[e] = (int)(key[e] % V); }
+    // counting sort by v0, then each (short) row by v1
+    std::vector<int> start((size_t)V + 1, 0), s1((size_t)E);
+    for (int e = 0; e < E; ++e) start[(size_t)e0[e] + 1] += 1;
+    for (int v = 0; v < V; ++v) start[(size_t)v + 1] += start[v];
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (int e = 0; e < E; ++e) s1[(size_t)fill[e0[e]]++] = e1[e];
+    for (int v = 0; v < V; ++v) {
+      const int b = start[v], e = start[(size_t)v + 1];
+      for (int k = b + 1; k < e; ++k) {   // rows are short: insertion sort
+        const int x = s1[k];
+        int m = k;
+        for (; m > b && s1[(size_t)m - 1] > x; --m) s1[m] = s1[(size_t)m - 1];
+        s1[m] = x;
+      }
+      for (int k = b; k < e; ++k) e0[k] = v;
+    }
+    e1.swap(s1);
   }
   std::vector<int> hidx;
   std::vector<float> htgt;

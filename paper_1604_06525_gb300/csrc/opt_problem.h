@@ -73,6 +73,7 @@ struct opt_problem {
   float* rvec = nullptr;
   float* qvec = nullptr;
   std::vector<void*> allocs;
+  std::vector<bool> pooled;             // allocs[k] came from the library's stream-ordered pool
   int pcg_par = 0;
   // persistent PCG loop (wide warps): grid barrier state and the number of
   // blocks that can be resident at once (0 = not available)
@@ -88,7 +89,10 @@ struct opt_problem {
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
-    for (void* p : allocs) cudaFree(p);
+    for (size_t k = 0; k < allocs.size(); ++k) {
+      if (pooled[k]) cudaFreeAsync(allocs[k], nullptr);
+      else cudaFree(allocs[k]);
+    }
   }
 };
 
