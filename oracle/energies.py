@@ -8,7 +8,8 @@ dense user buffers:
 * warp:    [dx (H*W), dy (H*W), theta (H*W)], each plane row-major;
 * poisson: [X_0, X_1, X_2, X_3] (each H*W), fixed pixels keep all-zero
            Jacobian columns (they are not solved for);
-* mesh:    [dx, dy, dz, A_x, A_y, A_z] (each V).
+* mesh:    [dx, dy, dz, A_x, A_y, A_z] (each V);
+* warp on a graph: [dx, dy, theta] (each V).
 
 Weights: the configured weights multiply the *squared* residual, so residuals
 carry their square roots (Fig. 3 caption: weights inside Energy() are square
@@ -154,6 +155,69 @@ class WarpEnergy(_Energy):
         return _csr(rows, cols, vals, (self.R, self.N))
 
 
+class WarpGraphEnergy(_Energy):
+    """ARAP image warping on an explicit graph (Sec. 4.1 "Graph-based Array
+    Access"; the explicit-graph form of Fig. 18).  Per vertex the unknowns are
+    (dx, dy, theta) and the rest position U; for every directed edge (a, b)
+        r_e = s_w * ((O_a - O_b) - R(theta_a) (U_a - U_b))
+    and for every handle h:  s_f * (O_h - C_h), O = U + displacement,
+    C = U + target.  With the stencil pairs of an image as edges this is the
+    energy of Fig. 24 (WarpEnergy) with its residuals in another order.
+    """
+
+    def __init__(self, prob):
+        self.prob = prob
+        self.V = self.n = prob.V
+        self.N = 3 * self.V
+        self.s_w = math.sqrt(prob.w_reg)
+        self.s_f = math.sqrt(prob.w_fit)
+        self.U = prob.urshape.astype(np.float64)
+        self.a = prob.v0.astype(np.int64)
+        self.b = prob.v1.astype(np.int64)
+        self.h = prob.handle_idx.astype(np.int64)
+        self.C = self.U[:, self.h] + prob.handle_target.astype(np.float64).T
+        self.R = 2 * self.a.size + 2 * self.h.size
+
+    def split(self, x):
+        x = np.asarray(x, np.float64).reshape(3, self.V)
+        return x[0:2], x[2]
+
+    def residuals(self, x):
+        d, th = self.split(x)
+        O = self.U + d
+        a, b = self.a, self.b
+        v = self.U[:, a] - self.U[:, b]
+        Rv = np.einsum('eij,je->ie', rot2d(th[a]).transpose(2, 0, 1), v)
+        reg = self.s_w * ((O[:, a] - O[:, b]) - Rv)
+        fit = self.s_f * (O[:, self.h] - self.C)
+        return np.concatenate([reg[0], reg[1], fit[0], fit[1]])
+
+    def jacobian(self, x):
+        d, th = self.split(x)
+        V, a, b, h = self.V, self.a, self.b, self.h
+        m = a.size
+        sw, sf = self.s_w, self.s_f
+        v = self.U[:, a] - self.U[:, b]
+        c, s = np.cos(th[a]), np.sin(th[a])
+        rows, cols, vals = [], [], []
+        for i in range(2):
+            rr = i * m + np.arange(m)
+            rows += [rr, rr]
+            cols += [i * V + a, i * V + b]
+            vals += [np.full(m, sw), np.full(m, -sw)]
+        # d r / d theta_a = -s_w R'(theta_a) v
+        dRv = np.stack([-s * v[0] - c * v[1], c * v[0] - s * v[1]])
+        for i in range(2):
+            rows.append(i * m + np.arange(m))
+            cols.append(2 * V + a)
+            vals.append(-sw * dRv[i])
+        for i in range(2):
+            rows.append(2 * m + i * h.size + np.arange(h.size))
+            cols.append(i * V + h)
+            vals.append(np.full(h.size, sf))
+        return _csr(rows, cols, vals, (self.R, self.N))
+
+
 class PoissonEnergy(_Energy):
     """Poisson image editing, Fig. 27 (4 channels, no weights).
 
@@ -268,4 +332,5 @@ class MeshEnergy(_Energy):
 
 def make_energy(prob):
     """Oracle energy object for a synth problem instance."""
-    return {"warp": WarpEnergy, "poisson": PoissonEnergy, "mesh": MeshEnergy}[prob.kind](prob)
+    return {"warp": WarpEnergy, "poisson": PoissonEnergy, "mesh": MeshEnergy,
+            "warp_graph": WarpGraphEnergy}[prob.kind](prob)

@@ -116,6 +116,39 @@ class MeshProblem:
         return 6 * self.V
 
 
+@dataclass
+class WarpGraphProblem:
+    """ARAP image warping written on an explicit graph (the explicit side of
+    the implicit-grid vs explicit-graph comparison, Fig. 18): one vertex per
+    pixel, the stencil neighbourhood as directed edges.
+
+    urshape: (2, V) float32 rest positions.
+    v0, v1: (E,) int32 directed edges, sorted by (v0, v1).
+    x0 planes: 0 = dx, 1 = dy, 2 = theta; (3, V) float32.
+    handle_idx: (n,) int32 vertex ids (distinct); handle_target: (n, 2)
+    float32 target displacements.
+    """
+    V: int
+    urshape: np.ndarray
+    v0: np.ndarray
+    v1: np.ndarray
+    x0: np.ndarray
+    handle_idx: np.ndarray
+    handle_target: np.ndarray
+    w_reg: float = 1.0
+    w_fit: float = 100.0
+    seed: int = BASE_SEED
+    kind: str = field(default="warp_graph", init=False)
+
+    @property
+    def E(self) -> int:
+        return int(self.v0.shape[0])
+
+    @property
+    def n_unknowns(self) -> int:
+        return 3 * self.V
+
+
 # ----------------------------------------------------------------------------
 # image warping
 # ----------------------------------------------------------------------------
@@ -148,6 +181,34 @@ def random_mask(W: int, H: int, frac: float, seed: int) -> np.ndarray:
     """Bernoulli(frac) mask of excluded pixels (tests of the masked stencil)."""
     rng = np.random.default_rng(seed)
     return (rng.random((H, W)) < frac).astype(np.uint8)
+
+
+def warp_graph_from_grid(prob: WarpProblem) -> WarpGraphProblem:
+    """The same warp as an explicit graph: vertex y * W + x per pixel, a
+    directed edge (k, k + d) for every stencil direction d whose neighbour is
+    inside the image with both pixels unmasked; handles on masked pixels are
+    dropped (their pixels carry no unknowns in the grid form either)."""
+    W, H = prob.W, prob.H
+    mask = np.zeros((H, W), bool) if prob.mask is None else (prob.mask != 0)
+    ys, xs = np.mgrid[0:H, 0:W]
+    a, b = [], []
+    for ox, oy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+        nx, ny = xs + ox, ys + oy
+        inb = (nx >= 0) & (nx < W) & (ny >= 0) & (ny < H)
+        nxc, nyc = np.clip(nx, 0, W - 1), np.clip(ny, 0, H - 1)
+        ok = inb & ~mask & ~mask[nyc, nxc]
+        a.append((ys * W + xs)[ok])
+        b.append((nyc * W + nxc)[ok])
+    v0 = np.concatenate(a).astype(np.int64)
+    v1 = np.concatenate(b).astype(np.int64)
+    order = np.lexsort((v1, v0))
+    keep = ~mask.reshape(-1)[prob.handle_idx]
+    return WarpGraphProblem(V=W * H, urshape=prob.urshape.reshape(2, -1).astype(np.float32).copy(),
+                            v0=v0[order].astype(np.int32), v1=v1[order].astype(np.int32),
+                            x0=prob.x0.reshape(3, -1).astype(np.float32).copy(),
+                            handle_idx=prob.handle_idx[keep].astype(np.int32).copy(),
+                            handle_target=prob.handle_target[keep].astype(np.float32).copy(),
+                            w_reg=prob.w_reg, w_fit=prob.w_fit, seed=prob.seed)
 
 
 def warp_handle_count(W: int, H: int) -> int:

@@ -214,14 +214,61 @@ def test_mesh_on_grid_graph_reduces_to_image_warp():
     assert en.MeshEnergy(mp).energy(xm) == pytest.approx(en.WarpEnergy(wp).energy(xw.reshape(-1)), rel=1e-12)
 
 
+@pytest.mark.parametrize("mask_frac", [0.0, 0.3])
+def test_warp_on_explicit_graph_equals_grid_warp(mask_frac):
+    # The explicit-graph form of the warp (Fig. 18's comparison) has the grid
+    # energy's residuals in another order: equal E, J^T F and J^T J.
+    wp = tiny_warp(W=6, H=5, n_handles=4, seed=21, mask_frac=mask_frac, noise=0.4)
+    if mask_frac:
+        wp.handle_idx[0] = int(np.flatnonzero(wp.mask.reshape(-1))[0])   # a handle on a masked pixel is dropped
+    gp = synth.warp_graph_from_grid(wp)
+    eg, ew = en.make_energy(gp), en.WarpEnergy(wp)
+    x = wp.x0.reshape(-1).astype(np.float64) + np.random.default_rng(2).uniform(-0.3, 0.3, wp.n_unknowns)
+    assert eg.energy(x) == pytest.approx(ew.energy(x), rel=1e-13)
+    Jg, Jw = eg.jacobian(x), ew.jacobian(x)
+    np.testing.assert_allclose(Jg.T @ eg.residuals(x), Jw.T @ ew.residuals(x), rtol=0, atol=1e-11)
+    np.testing.assert_allclose((Jg.T @ Jg).toarray(), (Jw.T @ Jw).toarray(), rtol=0, atol=1e-11)
+
+
+def test_warp_graph_rigid_motion_has_zero_regularizer():
+    # O = R(phi) U + t with theta = phi on every vertex: every edge residual vanishes
+    rng = np.random.default_rng(4)
+    V = 9
+    U = rng.uniform(-3, 3, (2, V)).astype(np.float32)
+    a = rng.integers(0, V, 30)
+    b = (a + rng.integers(1, V, 30)) % V
+    order = np.lexsort((b, a))
+    phi, t = 0.7, np.array([[1.5], [-0.25]])
+    O = en.rot2d(phi) @ U.astype(np.float64) + t
+    gp = synth.WarpGraphProblem(V=V, urshape=U, v0=a[order].astype(np.int32), v1=b[order].astype(np.int32),
+                                x0=np.zeros((3, V), np.float32), handle_idx=np.zeros(0, np.int32),
+                                handle_target=np.zeros((0, 2), np.float32))
+    x = np.concatenate([O - U, np.full((1, V), phi)]).reshape(-1)
+    assert en.make_energy(gp).energy(x) == pytest.approx(0.0, abs=1e-20)
+
+
 # --------------------------------------------------------------------------
 # Jacobian: central finite differences; gradient = 2 J^T F
 # --------------------------------------------------------------------------
+def random_warp_graph(seed=6):
+    rng = np.random.default_rng(seed)
+    V = 7
+    a = rng.integers(0, V, 16)
+    b = (a + rng.integers(1, V, 16)) % V
+    order = np.lexsort((b, a))
+    return synth.WarpGraphProblem(V=V, urshape=rng.uniform(-2, 2, (2, V)).astype(np.float32),
+                                  v0=a[order].astype(np.int32), v1=b[order].astype(np.int32),
+                                  x0=rng.uniform(-0.5, 0.5, (3, V)).astype(np.float32),
+                                  handle_idx=np.array([1, 4], np.int32),
+                                  handle_target=rng.uniform(-1, 1, (2, 2)).astype(np.float32))
+
+
 @pytest.mark.parametrize("make", [
     lambda: (tiny_warp(), None),
     lambda: (tiny_warp(mask_frac=0.3, seed=9), None),
     lambda: (tiny_mesh(), None),
     lambda: (synth.poisson_problem(6, 5, seed=2), None),
+    lambda: (random_warp_graph(), None),
 ])
 def test_jacobian_matches_central_differences(make):
     prob, _ = make()
