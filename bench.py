@@ -540,6 +540,22 @@ def run_ours(args):
                                            "accepted": rr[-1]["accepted"], "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
         gmp.close()
 
+        # implicit grid vs explicit graph for the same warp (Fig. 18: 8 outer x 100 PCG)
+        gwp = synth.warp_graph_from_grid(prob)
+        ggp = api.Problem(gwp)
+        xg0 = ggp.x.clone()
+        rr_graph = timed(ggp, xg0, lambda o, i: ggp.solve_gn(8, 100))
+        rr_grid = timed(gp, x0, lambda o, i: gp.solve_gn(8, 100))
+        msg = statistics.median(r_["ms"] for r_ in rr_graph)
+        msw = statistics.median(r_["ms"] for r_ in rr_grid)
+        extra["warp_1024x1024_grid_vs_graph_gn8x100"] = {
+            "grid_ms_per_solve": msw, "graph_ms_per_solve": msg, "graph_over_grid_time": msg / msw,
+            "grid_pcg_iters_per_s": 800 / (msw / 1e3), "graph_pcg_iters_per_s": 800 / (msg / 1e3),
+            "directed_edges": int(gwp.E), "E_final_grid": rr_grid[-1]["E_final"],
+            "E_final_graph": rr_graph[-1]["E_final"]}
+        ggp.close()
+        del gwp
+
         extra["batched_512_warps_gn10x10"] = bench_batched(api, synth, torch, flush)
         extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch)
 

@@ -53,7 +53,8 @@ typedef enum {
 typedef enum {
     OPT_ARAP_WARP_2D = 0,     /* Fig. 24: unknowns dx, dy, theta per pixel */
     OPT_POISSON_2D = 1,       /* Fig. 27: unknowns X (4 channels) per pixel */
-    OPT_ARAP_MESH = 2         /* Fig. 25: unknowns dx, dy, dz, ax, ay, az per vertex */
+    OPT_ARAP_MESH = 2,        /* Fig. 25: unknowns dx, dy, dz, ax, ay, az per vertex */
+    OPT_ARAP_WARP_GRAPH = 3   /* Fig. 24 on an explicit graph (Fig. 18): dx, dy, theta per vertex */
 } opt_energy;
 
 typedef struct opt_problem opt_problem;
@@ -167,9 +168,27 @@ opt_status opt_problem_create_grid(const opt_grid_desc* desc, const opt_solve_pa
                                    opt_problem** out);
 
 /* Plan a graph problem (edges: 0 <= v0, v1 < V, v0 != v1, else
- * OPT_ERR_INVALID_ARG).  Same ownership rules as opt_problem_create_grid. */
+ * OPT_ERR_INVALID_ARG).  Same ownership rules as opt_problem_create_grid.
+ * The library keeps its vertices in its own (locality) order; the caller's
+ * planes stay in the caller's order. */
 opt_status opt_problem_create_graph(const opt_graph_desc* desc, const opt_solve_params* params,
                                     opt_problem** out);
+
+/* Plan ARAP image warping written on an explicit graph (OPT_ARAP_WARP_GRAPH:
+ * Sec. 4.1 "Graph-based Array Access", the explicit side of the implicit
+ * grid vs explicit graph comparison of Fig. 18), with opt_graph_desc read as
+ *   unknowns[0..2] = dx, dy, theta per vertex (unknowns[3..5] unused);
+ *   urshape[0..1]  = rest positions x, y (urshape[2] unused);
+ *   handle_target  = n_handles (tx, ty) target displacements, interleaved.
+ *   Residuals: for every edge (a, b),
+ *     sqrt(w_reg) * ((O_a - O_b) - R(theta_a) (U_a - U_b)), R counter-clockwise;
+ *   for every handle, sqrt(w_fit) * (O_h - C_h), C_h = U_h + target.
+ * With the stencil neighbour pairs of an image as edges this is the
+ * OPT_ARAP_WARP_2D energy.  Solves as a graph problem; there is no
+ * materialized form (params.materialized = 1 gives OPT_ERR_INVALID_ARG at
+ * solve time).  Errors as opt_problem_create_graph. */
+opt_status opt_problem_create_graph2d(const opt_graph_desc* desc, const opt_solve_params* params,
+                                      opt_problem** out);
 
 /* Frees everything the problem owns.  NULL is accepted. */
 opt_status opt_problem_destroy(opt_problem* prob);

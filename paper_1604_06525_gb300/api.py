@@ -55,6 +55,7 @@ _SIGNATURES = [
     ("opt_solve_params_default", c_int32, [POINTER(SolveParams)]),
     ("opt_problem_create_grid", c_int32, [POINTER(GridDesc), POINTER(SolveParams), POINTER(c_void_p)]),
     ("opt_problem_create_graph", c_int32, [POINTER(GraphDesc), POINTER(SolveParams), POINTER(c_void_p)]),
+    ("opt_problem_create_graph2d", c_int32, [POINTER(GraphDesc), POINTER(SolveParams), POINTER(c_void_p)]),
     ("opt_problem_destroy", c_int32, [c_void_p]),
     ("opt_solve_gn", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report)]),
     ("opt_solve_lm", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report)]),
@@ -177,8 +178,9 @@ def make_descriptor(prob, device):
         d.mask = _ptr(mask) if mask is not None else None
         keep += [consts, mask, x]
         return d, x, keep
-    if prob.kind == "mesh":
-        x = f32(prob.x0).reshape(6, prob.V).clone()
+    if prob.kind in ("mesh", "warp_graph"):
+        nxg, dim = (6, 3) if prob.kind == "mesh" else (3, 2)
+        x = f32(prob.x0).reshape(nxg, prob.V).clone()
         U = f32(prob.urshape)
         v0, v1 = i32(prob.v0), i32(prob.v1)
         hidx = i32(prob.handle_idx)
@@ -186,9 +188,9 @@ def make_descriptor(prob, device):
         d = GraphDesc()
         d.V, d.E = prob.V, int(prob.v0.size)
         d.v0, d.v1 = _ptr(v0), _ptr(v1)
-        for c in range(6):
+        for c in range(nxg):
             d.unknowns[c] = _ptr(x[c])
-        for c in range(3):
+        for c in range(dim):
             d.urshape[c] = _ptr(U[c])
         d.n_handles = int(prob.handle_idx.size)
         d.handle_idx = _ptr(hidx) if d.n_handles else None
@@ -231,8 +233,9 @@ class Problem:
                    "opt_problem_create_grid")
         else:
             self.V = prob.V
-            _check(self.lib.opt_problem_create_graph(ctypes.byref(d), None, ctypes.byref(h)),
-                   "opt_problem_create_graph")
+            create = (self.lib.opt_problem_create_graph if prob.kind == "mesh"
+                      else self.lib.opt_problem_create_graph2d)
+            _check(create(ctypes.byref(d), None, ctypes.byref(h)), "opt_problem_create_graph")
         self.h = h
 
     # ------------------------------------------------------------------
@@ -430,6 +433,8 @@ class Server:
             pass
 
     def submit(self, prob, x=None) -> int:
+        if prob.kind not in ("warp", "poisson", "mesh"):
+            raise ValueError(f"the server takes warp, poisson and mesh requests, not {prob.kind}")
         d, xt, keep = make_descriptor(prob, self.device)
         if x is not None:
             xt.copy_(x)

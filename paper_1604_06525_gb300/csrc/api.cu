@@ -227,7 +227,7 @@ bool is_grid(const opt_problem* pb) { return pb->kind == K_WARP || pb->kind == K
 
 // distinct-diagonal plane of unknown component c
 int mplane_of(int kind, int c) {
-  if (kind == K_WARP) return c == 2 ? 1 : 0;
+  if (kind == K_WARP || kind == K_WARPG) return c == 2 ? 1 : 0;
   if (kind == K_POISSON) return 0;
   return c < 3 ? 0 : c - 2;
 }
@@ -303,7 +303,7 @@ GridLaunch grid_launch(const opt_problem* pb, cudaStream_t st) {
 }
 MeshLaunch mesh_launch(const opt_problem* pb, cudaStream_t st) {
   return MeshLaunch{pb->dm, pb->d_vchunks, pb->d_echunks, pb->d_part, pb->nvchunks,
-                    pb->nechunks, st};
+                    pb->nechunks, st, pb->kind == K_WARPG ? 2 : 3};
 }
 
 opt_status upload_desc(opt_problem* pb, cudaStream_t st) {
@@ -430,6 +430,7 @@ opt_status run_solve(opt_problem* pb, const opt_solve_params* prm_in, opt_report
   else opt_solve_params_default(&p);
   CKS(check_params(p, lm));
   if (p.materialized != 0 && p.materialized != 1) return OPT_ERR_INVALID_ARG;
+  if (p.materialized && pb->kind == K_WARPG) return OPT_ERR_INVALID_ARG;   // no materialized form
   if (p.materialized) CKS(csr_build(pb));
   cudaStream_t st = (cudaStream_t)p.stream;
   CK(cudaStreamSynchronize(st));
@@ -739,16 +740,19 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   return OPT_OK;
 }
 
-opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_params* prm, opt_problem** out) {
-  (void)prm;
+// Graph planning for dimension D: D = 3 is the ARAP mesh (unknowns dx, dy, dz,
+// ax, ay, az; rest positions and targets in 3-D), D = 2 the warp on a graph
+// (unknowns dx, dy, theta; rest positions and targets in 2-D).
+static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem** out) {
+  const int NXg = D == 3 ? 6 : 3, NMg = D == 3 ? 4 : 2, NGR = D == 3 ? 3 : 1, NVR = D == 3 ? 2 : 1;
   if (!out) return OPT_ERR_INVALID_ARG;
   *out = nullptr;
   if (!d) return OPT_ERR_INVALID_ARG;
   if (d->V < 1 || d->E < 0 || d->n_handles < 0) return OPT_ERR_INVALID_ARG;
   if (d->E > 0 && (!d->v0 || !d->v1)) return OPT_ERR_INVALID_ARG;
-  for (int c = 0; c < 6; ++c)
+  for (int c = 0; c < NXg; ++c)
     if (!d->unknowns[c]) return OPT_ERR_INVALID_ARG;
-  for (int c = 0; c < 3; ++c)
+  for (int c = 0; c < D; ++c)
     if (!d->urshape[c]) return OPT_ERR_INVALID_ARG;
   if (d->n_handles > 0 && (!d->handle_idx || !d->handle_target)) return OPT_ERR_INVALID_ARG;
   if (!std::isfinite(d->w_reg) || !std::isfinite(d->w_fit) || d->w_reg < 0.f || d->w_fit < 0.f)
@@ -756,9 +760,9 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
 
   std::unique_ptr<opt_problem> pb(new opt_problem());
   opt_problem* q = pb.get();
-  q->kind = K_MESH;
-  q->nx = 6;
-  q->nm = 4;
+  q->kind = D == 3 ? K_MESH : K_WARPG;
+  q->nx = NXg;
+  q->nm = NMg;
   q->V = d->V;
   q->E = d->E;
   const int V = d->V, E = d->E, nh = d->n_handles;
@@ -773,7 +777,8 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   for (int e = 0; e < E; ++e)
     if (e0[e] < 0 || e0[e] >= V || e1[e] < 0 || e1[e] >= V || e0[e] == e1[e]) return OPT_ERR_INVALID_ARG;
   std::vector<float> Uh[3];
-  for (int c = 0; c < 3; ++c) {
+  Uh[2].assign((size_t)V, 0.f);             // a graph warp lies in the plane z = 0
+  for (int c = 0; c < D; ++c) {
     CKS(download(Uh[c], d->urshape[c], (size_t)V));
     if (!all_finite(Uh[c])) return OPT_ERR_INVALID_ARG;
   }
@@ -809,7 +814,7 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   std::vector<float> htgt;
   if (nh > 0) {
     CKS(download(hidx, d->handle_idx, (size_t)nh));
-    CKS(download(htgt, d->handle_target, (size_t)nh * 3));
+    CKS(download(htgt, d->handle_target, (size_t)nh * D));
     if (!all_finite(htgt)) return OPT_ERR_INVALID_ARG;
     for (int& h : hidx) {
       if (h < 0 || h >= V) return OPT_ERR_INVALID_ARG;
@@ -821,13 +826,13 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   std::sort(order.begin(), order.end(), [&](int a, int b) { return hidx[a] < hidx[b]; });
   const int nvt = (V + VT - 1) / VT;
   std::vector<int> hbeg((size_t)nvt + 1, 0), hpix(nh);
-  std::vector<float> hts((size_t)nh * 3);
+  std::vector<float> hts((size_t)nh * D);
   std::vector<float> degw((size_t)V, 0.f);
   for (int k = 0; k < nh; ++k) {
     const int i = order[k], v = hidx[i];
     if (v < 0 || v >= V || (k && hpix[k - 1] == v)) return OPT_ERR_INVALID_ARG;
     hpix[k] = v;
-    for (int c = 0; c < 3; ++c) hts[3 * k + c] = htgt[3 * i + c];
+    for (int c = 0; c < D; ++c) hts[(size_t)D * k + c] = htgt[(size_t)D * i + c];
     hbeg[v / VT + 1] += 1;
     degw[v] += d->w_fit;
   }
@@ -860,18 +865,18 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   const size_t pl = (size_t)Vp;
   float *U = nullptr, *dgw = nullptr, *m = nullptr, *dc = nullptr, *dhtgt = nullptr;
   int *de0 = nullptr, *de1 = nullptr, *dhbeg = nullptr, *dhpix = nullptr;
-  CKS(dalloc(q, &q->x, 6 * pl));
-  CKS(dalloc(q, &U, 3 * pl));
+  CKS(dalloc(q, &q->x, NXg * pl));
+  CKS(dalloc(q, &U, D * pl));
   CKS(dalloc(q, &dgw, pl));
-  CKS(dalloc(q, &q->dvec, 6 * pl));
-  CKS(dalloc(q, &q->rvec, 6 * pl));
-  CKS(dalloc(q, &q->qvec, 6 * pl));
-  CKS(dalloc(q, &q->pbuf, 12 * pl));
-  CKS(dalloc(q, &m, 4 * pl));
-  CKS(dalloc(q, &dc, 4 * pl));
+  CKS(dalloc(q, &q->dvec, NXg * pl));
+  CKS(dalloc(q, &q->rvec, NXg * pl));
+  CKS(dalloc(q, &q->qvec, NXg * pl));
+  CKS(dalloc(q, &q->pbuf, 2 * NXg * pl));
+  CKS(dalloc(q, &m, NMg * pl));
+  CKS(dalloc(q, &dc, NMg * pl));
   float4 *grec = nullptr, *vrec = nullptr;
-  CKS(dalloc(q, &grec, 3 * (size_t)V));
-  CKS(dalloc(q, &vrec, 2 * (size_t)V));
+  CKS(dalloc(q, &grec, (size_t)NGR * V));
+  CKS(dalloc(q, &vrec, (size_t)NVR * V));
   int *dorow = nullptr, *dirow = nullptr, *disrc = nullptr;
   CKS(dalloc(q, &dorow, orow.size()));
   CKS(upload(dorow, orow));
@@ -879,7 +884,7 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   CKS(upload(dirow, irow));
   CKS(dalloc(q, &disrc, std::max<size_t>(1, isrc.size())));
   if (E > 0) CKS(upload(disrc, isrc));
-  for (int c = 0; c < 3; ++c) {
+  for (int c = 0; c < D; ++c) {
     std::vector<float> Ui((size_t)V);
     for (int k = 0; k < V; ++k) Ui[k] = Uh[c][perm[k]];
     CKS(upload(U + c * pl, Ui));
@@ -905,7 +910,7 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   q->nechunks = (int)ech.size();
   CKS(dalloc(q, &q->d_part, 2 * std::max(vch.size(), ech.size())));
   CKS(dalloc(q, &q->dm, 1));
-  for (int k = 0; k < 6; ++k) q->user_x[k] = d->unknowns[k];
+  for (int k = 0; k < NXg; ++k) q->user_x[k] = d->unknowns[k];
   q->h_e0 = e0;
   q->h_e1 = e1;
   q->h_hpix = hpix;
@@ -928,6 +933,16 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
   CKS(upload_desc(q, nullptr));
   *out = pb.release();
   return OPT_OK;
+}
+
+opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_params* prm, opt_problem** out) {
+  (void)prm;
+  return create_graph_impl(d, 3, out);
+}
+
+opt_status opt_problem_create_graph2d(const opt_graph_desc* d, const opt_solve_params* prm, opt_problem** out) {
+  (void)prm;
+  return create_graph_impl(d, 2, out);
 }
 
 opt_status opt_problem_destroy(opt_problem* prob) {

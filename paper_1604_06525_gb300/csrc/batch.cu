@@ -150,6 +150,7 @@ struct GridGroup {
 };
 
 struct MeshGroup {
+  int dim = 3;                         // 3: ARAP mesh, 2: warp on a graph
   std::vector<int> members;
   MeshProb* d_probs = nullptr;
   Chunk* d_vch = nullptr;
@@ -163,7 +164,7 @@ struct MeshGroup {
 struct opt_batch {
   std::vector<opt_problem*> probs;
   std::vector<GridGroup> grids;
-  MeshGroup mesh;
+  MeshGroup graphs[2];               // [0]: ARAP meshes (dim 3), [1]: warps on graphs (dim 2)
   int tiles_per_chunk = 0;          // 0 = per-problem default
   std::vector<void*> table_allocs;  // rebuilt with the chunking
   std::vector<void*> allocs;        // fixed for the batch's life
@@ -236,8 +237,8 @@ opt_status build_tables(opt_batch* b, int tpc) {
     if ((s = balloc(b->table_allocs, &g.d_part, 2 * chunks.size())) != OPT_OK) return s;
     g.nchunks = (int)chunks.size();
   }
-  if (!b->mesh.members.empty()) {
-    MeshGroup& g = b->mesh;
+  for (MeshGroup& g : b->graphs) {
+    if (g.members.empty()) continue;
     std::vector<MeshProb> mp;
     std::vector<Chunk> vch, ech;
     for (size_t mi = 0; mi < g.members.size(); ++mi) {
@@ -270,7 +271,7 @@ GridLaunch gl(const GridGroup& g, cudaStream_t st) {
   return GridLaunch{g.d_probs, g.d_chunks, g.d_tiles, g.d_part, g.nchunks, st, g.tw, g.masked};
 }
 MeshLaunch ml(const MeshGroup& g, cudaStream_t st) {
-  return MeshLaunch{g.d_probs, g.d_vch, g.d_ech, g.d_part, g.nv, g.ne, st};
+  return MeshLaunch{g.d_probs, g.d_vch, g.d_ech, g.d_part, g.nv, g.ne, st, g.dim};
 }
 
 // Uploads the members' descriptors with the solve's flags (outside any capture).
@@ -304,8 +305,8 @@ opt_status refresh_descriptors(opt_batch* b, int lm, int use_precond, int outer)
     }
     BCK(cudaMemcpy(g.d_probs, gp.data(), gp.size() * sizeof(GridProb), cudaMemcpyHostToDevice));
   }
-  if (!b->mesh.members.empty()) {
-    MeshGroup& g = b->mesh;
+  for (MeshGroup& g : b->graphs) {
+    if (g.members.empty()) continue;
     std::vector<MeshProb> mp(g.members.size());
     BCK(cudaMemcpy(mp.data(), g.d_probs, mp.size() * sizeof(MeshProb), cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < mp.size(); ++i) {
@@ -338,26 +339,26 @@ void enqueue_batch(opt_batch* b, const opt_solve_params& p, bool lm, cudaStream_
   k_reset_tab<<<(n + 127) / 128, 128, 0, st>>>(b->d_stab, n, lm ? p.lambda0 : 0.0);
   for (int k = 0; k < outer; ++k) {
     for (GridGroup& g : b->grids) launch_grid_init(g.kind, gl(g, st), k, dmin, dmax);
-    if (!b->mesh.members.empty()) launch_mesh_init(ml(b->mesh, st), k, dmin, dmax);
+    for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_init(ml(g, st), k, dmin, dmax);
     for (int i = 0; i < p.inner; ++i) {
       for (GridGroup& g : b->grids) launch_grid_apply(g.kind, gl(g, st), nullptr, i, 1);
-      if (!b->mesh.members.empty()) launch_mesh_apply(ml(b->mesh, st), nullptr, i, 1);
+      for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_apply(ml(g, st), nullptr, i, 1);
       for (GridGroup& g : b->grids) launch_grid_update(g.kind, gl(g, st), i);
-      if (!b->mesh.members.empty()) launch_mesh_update(ml(b->mesh, st), i);
+      for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_update(ml(g, st), i);
     }
     if (!lm) {
       for (GridGroup& g : b->grids) launch_grid_step(g.kind, gl(g, st), 0);
-      if (!b->mesh.members.empty()) launch_mesh_step(ml(b->mesh, st), 0);
+      for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_step(ml(g, st), 0);
     } else {
       for (GridGroup& g : b->grids) launch_grid_energy(g.kind, gl(g, st), 1, -2);
-      if (!b->mesh.members.empty()) launch_mesh_energy(ml(b->mesh, st), 1, -2);
+      for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_energy(ml(g, st), 1, -2);
       k_lm_decide_tab<<<(n + 127) / 128, 128, 0, st>>>(b->d_stab, n, p.eta, p.lambda_min, p.lambda_max, p.rel_tol);
       for (GridGroup& g : b->grids) launch_grid_step(g.kind, gl(g, st), 1);
-      if (!b->mesh.members.empty()) launch_mesh_step(ml(b->mesh, st), 1);
+      for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_step(ml(g, st), 1);
     }
   }
   for (GridGroup& g : b->grids) launch_grid_energy(g.kind, gl(g, st), 0, lm ? -1 : outer);
-  if (!b->mesh.members.empty()) launch_mesh_energy(ml(b->mesh, st), 0, lm ? -1 : outer);
+  for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_energy(ml(g, st), 0, lm ? -1 : outer);
   if (write_back) enqueue_copies(b, b->d_copy_out, st);
 }
 
@@ -472,8 +473,11 @@ opt_status opt_batch_create(opt_problem* const* probs, int32_t n, opt_batch** ou
             g.members.push_back(i);
         if (!g.members.empty()) b->grids.push_back(g);
       }
-  for (int i = 0; i < n; ++i)
-    if (probs[i]->kind == K_MESH) b->mesh.members.push_back(i);
+  b->graphs[1].dim = 2;
+  for (int i = 0; i < n; ++i) {
+    if (probs[i]->kind == K_MESH) b->graphs[0].members.push_back(i);
+    if (probs[i]->kind == K_WARPG) b->graphs[1].members.push_back(i);
+  }
   BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
   BCK(cudaEventCreate(&b->ev0));
   BCK(cudaEventCreate(&b->ev1));
@@ -576,18 +580,18 @@ void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_
   const float dmin = (float)p.diag_min, dmax = (float)p.diag_max;
   const int n = (int)b->probs.size();
   for (GridGroup& g : b->grids) launch_grid_init(g.kind, gl(g, st), -2, dmin, dmax);
-  if (!b->mesh.members.empty()) launch_mesh_init(ml(b->mesh, st), -2, dmin, dmax);
+  for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_init(ml(g, st), -2, dmin, dmax);
   for (int i = 0; i < p.inner; ++i) {
     for (GridGroup& g : b->grids) launch_grid_apply(g.kind, gl(g, st), nullptr, i, 1);
-    if (!b->mesh.members.empty()) launch_mesh_apply(ml(b->mesh, st), nullptr, i, 1);
+    for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_apply(ml(g, st), nullptr, i, 1);
     for (GridGroup& g : b->grids) launch_grid_update(g.kind, gl(g, st), i);
-    if (!b->mesh.members.empty()) launch_mesh_update(ml(b->mesh, st), i);
+    for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_update(ml(g, st), i);
   }
   for (GridGroup& g : b->grids) launch_grid_energy(g.kind, gl(g, st), 1, -2);
-  if (!b->mesh.members.empty()) launch_mesh_energy(ml(b->mesh, st), 1, -2);
+  for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_energy(ml(g, st), 1, -2);
   k_lm_decide_tab<<<(n + 127) / 128, 128, 0, st>>>(b->d_stab, n, p.eta, p.lambda_min, p.lambda_max, p.rel_tol);
   for (GridGroup& g : b->grids) launch_grid_step(g.kind, gl(g, st), 1);
-  if (!b->mesh.members.empty()) launch_mesh_step(ml(b->mesh, st), 1);
+  for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_step(ml(g, st), 1);
   k_gather_results<<<n, 128, 0, st>>>(b->d_stab, b->d_htab, n, 0, b->d_sout, b->d_hout);
 }
 

@@ -541,25 +541,30 @@ __global__ void __launch_bounds__(NT) k_mesh_step(const MeshProb* __restrict__ p
 // launchers
 // ---------------------------------------------------------------------------
 void launch_mesh_init(const MeshLaunch& L, int k_outer, float dmin, float dmax) {
+  if (L.dim == 2) return launch_wg_init(L, k_outer, dmin, dmax);
   launch_pdl(k_mesh_init_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks);
   launch_pdl(k_mesh_init_pull, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, k_outer, dmin, dmax);
 }
 
 void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, int update) {
+  if (L.dim == 2) return launch_wg_apply(L, p_override, par, update);
   launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, p_override, par, update);
   launch_pdl(k_mesh_apply_pull, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
 }
 
 void launch_mesh_update(const MeshLaunch& L, int par) {
+  if (L.dim == 2) return launch_wg_update(L, par);
   launch_pdl(k_mesh_update, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, par);
 }
 
 void launch_mesh_energy(const MeshLaunch& L, int mode, int hist_idx) {
+  if (L.dim == 2) return launch_wg_energy(L, mode, hist_idx);
   launch_pdl(k_mesh_energy_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, mode);
   launch_pdl(k_mesh_energy_e, L.nechunks, NT, 0, L.stream, L.probs, L.echunks, L.part, mode, hist_idx);
 }
 
 void launch_mesh_step(const MeshLaunch& L, int cond) {
+  if (L.dim == 2) return launch_wg_step(L, cond);
   launch_pdl(k_mesh_step, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, cond);
 }
 

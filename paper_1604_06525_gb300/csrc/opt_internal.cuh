@@ -29,7 +29,7 @@
 
 namespace optgb {
 
-enum Kind : int { K_WARP = 0, K_POISSON = 1, K_MESH = 2 };
+enum Kind : int { K_WARP = 0, K_POISSON = 1, K_MESH = 2, K_WARPG = 3 };   // K_WARPG: warp on a graph
 
 constexpr int TW = 32;            // grid tile width  (pixels)
 constexpr int TH = 8;             // grid tile height (pixels)

@@ -23,6 +23,7 @@ struct MeshLaunch {
   double* part;
   int nvchunks, nechunks;
   cudaStream_t stream;
+  int dim;       // 3: ARAP mesh (6 unknowns per vertex); 2: warp on a graph (3 unknowns)
 };
 
 // Launches kernel k with programmatic stream serialization (the kernel must
@@ -64,5 +65,12 @@ void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, in
 void launch_mesh_update(const MeshLaunch& L, int par);
 void launch_mesh_energy(const MeshLaunch& L, int mode, int hist_idx);
 void launch_mesh_step(const MeshLaunch& L, int cond);
+
+// graph2d_kernels.cu (dim == 2; reached through the launch_mesh_* functions)
+void launch_wg_init(const MeshLaunch& L, int k_outer, float dmin, float dmax);
+void launch_wg_apply(const MeshLaunch& L, const float* p_override, int par, int update);
+void launch_wg_update(const MeshLaunch& L, int par);
+void launch_wg_energy(const MeshLaunch& L, int mode, int hist_idx);
+void launch_wg_step(const MeshLaunch& L, int cond);
 
 }  // namespace optgb
