@@ -9,7 +9,8 @@ dense user buffers:
 * poisson: [X_0, X_1, X_2, X_3] (each H*W), fixed pixels keep all-zero
            Jacobian columns (they are not solved for);
 * mesh:    [dx, dy, dz, A_x, A_y, A_z] (each V);
-* warp on a graph: [dx, dy, theta] (each V).
+* warp on a graph: [dx, dy, theta] (each V);
+* volume:  [dx, dy, dz, A_x, A_y, A_z] (each W*H*D voxels, index (z*H + y)*W + x).
 
 Weights: the configured weights multiply the *squared* residual, so residuals
 carry their square roots (Fig. 3 caption: weights inside Energy() are square
@@ -330,7 +331,84 @@ class MeshEnergy(_Energy):
         return _csr(rows, cols, vals, (self.R, self.N))
 
 
+class VolumeEnergy(_Energy):
+    """Volumetric ARAP deformation, Fig. 31, on the W x H x D voxel array.
+
+    For every voxel k and stencil direction d in {+-x, +-y, +-z} with k+d
+    inside the grid (InBounds):
+        r_{k,d} = s_w * ((O_k - O_{k+d}) - Rotate3D(A_k) (U_k - U_{k+d}))
+    and for every constrained voxel h:  s_f * (O_h - C_h).
+    O = UrShape + displacement; C = UrShape + target.  The stencil is walked
+    on the 3-D array (shifted slices), not through an edge list.
+    """
+
+    def __init__(self, prob):
+        self.prob = prob
+        W, H, D = prob.W, prob.H, prob.D
+        self.shape = (D, H, W)
+        self.V = self.n = W * H * D
+        self.N = 6 * self.V
+        self.s_w = math.sqrt(prob.w_reg)
+        self.s_f = math.sqrt(prob.w_fit)
+        self.U = prob.urshape.astype(np.float64)
+        idx = np.arange(self.V).reshape(D, H, W)
+        ks, js = [], []
+        for axis in range(3):                    # numpy axes: 0 = z, 1 = y, 2 = x
+            for step in (1, -1):
+                src = [slice(None)] * 3
+                dst = [slice(None)] * 3
+                if step == 1:
+                    src[axis], dst[axis] = slice(0, -1), slice(1, None)
+                else:
+                    src[axis], dst[axis] = slice(1, None), slice(0, -1)
+                ks.append(idx[tuple(src)].reshape(-1))
+                js.append(idx[tuple(dst)].reshape(-1))
+        self.a = np.concatenate(ks)
+        self.b = np.concatenate(js)
+        self.h = prob.handle_idx.astype(np.int64)
+        self.C = self.U[:, self.h] + prob.handle_target.astype(np.float64).T
+        self.R = 3 * self.a.size + 3 * self.h.size
+
+    def split(self, x):
+        x = np.asarray(x, np.float64).reshape(6, self.V)
+        return x[0:3], x[3:6]
+
+    def residuals(self, x):
+        d, A = self.split(x)
+        O = self.U + d
+        a, b = self.a, self.b
+        v = (self.U[:, a] - self.U[:, b]).T
+        R, _ = euler_rotation(A[:, a].T)
+        Rv = np.einsum('eij,ej->ie', R, v)
+        reg = self.s_w * ((O[:, a] - O[:, b]) - Rv)
+        fit = self.s_f * (O[:, self.h] - self.C)
+        return np.concatenate([reg.reshape(-1), fit.reshape(-1)])
+
+    def jacobian(self, x):
+        d, A = self.split(x)
+        V, a, b, h = self.V, self.a, self.b, self.h
+        m = a.size
+        sw, sf = self.s_w, self.s_f
+        v = (self.U[:, a] - self.U[:, b]).T
+        _, dR = euler_rotation(A[:, a].T)
+        rows, cols, vals = [], [], []
+        for i in range(3):
+            rr = i * m + np.arange(m)
+            rows += [rr, rr]
+            cols += [i * V + a, i * V + b]
+            vals += [np.full(m, sw), np.full(m, -sw)]
+            for mm in range(3):
+                rows.append(rr)
+                cols.append((3 + mm) * V + a)
+                vals.append(-sw * np.einsum('ej,ej->e', dR[mm][:, i, :], v))
+        for i in range(3):
+            rows.append(3 * m + i * h.size + np.arange(h.size))
+            cols.append(i * V + h)
+            vals.append(np.full(h.size, sf))
+        return _csr(rows, cols, vals, (self.R, self.N))
+
+
 def make_energy(prob):
     """Oracle energy object for a synth problem instance."""
     return {"warp": WarpEnergy, "poisson": PoissonEnergy, "mesh": MeshEnergy,
-            "warp_graph": WarpGraphEnergy}[prob.kind](prob)
+            "warp_graph": WarpGraphEnergy, "volume": VolumeEnergy}[prob.kind](prob)

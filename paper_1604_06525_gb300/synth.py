@@ -149,6 +149,37 @@ class WarpGraphProblem:
         return 3 * self.V
 
 
+@dataclass
+class VolumeProblem:
+    """Volumetric ARAP deformation instance (Fig. 31): a W x H x D voxel grid,
+    7-point stencil.  Voxel index (z * H + y) * W + x.
+
+    urshape: (3, V) float32 rest positions (read as an array).
+    x0 planes: 0..2 = displacement, 3..5 = Euler angles; (6, V) float32.
+    handle_idx: (n,) int32 voxel ids (distinct); handle_target: (n, 3)
+    float32 target displacements (the constrained voxels of Fig. 31).
+    """
+    W: int
+    H: int
+    D: int
+    urshape: np.ndarray
+    x0: np.ndarray
+    handle_idx: np.ndarray
+    handle_target: np.ndarray
+    w_reg: float = 1.0
+    w_fit: float = 100.0
+    seed: int = BASE_SEED
+    kind: str = field(default="volume", init=False)
+
+    @property
+    def V(self) -> int:
+        return self.W * self.H * self.D
+
+    @property
+    def n_unknowns(self) -> int:
+        return 6 * self.V
+
+
 # ----------------------------------------------------------------------------
 # image warping
 # ----------------------------------------------------------------------------
@@ -359,6 +390,43 @@ def graph_problem(urshape: np.ndarray, v0: np.ndarray, v1: np.ndarray, n_handles
         x0[:] = rng.uniform(-x0_noise, x0_noise, size=x0.shape).astype(np.float32)
     return MeshProblem(V, np.ascontiguousarray(urshape, np.float32), np.asarray(v0, np.int32),
                        np.asarray(v1, np.int32), x0, hidx, htgt, 1.0, 100.0, -1, seed)
+
+
+# ----------------------------------------------------------------------------
+# volumetric deformation
+# ----------------------------------------------------------------------------
+def volume_problem(W: int, H: int, D: int, n_handles: int, seed: int = BASE_SEED, spacing: float = 1.0,
+                   max_off: float = 2.0, w_reg: float = 1.0, w_fit: float = 100.0,
+                   x0_noise: float = 0.0) -> VolumeProblem:
+    """Volumetric ARAP on a W x H x D grid with rest positions at the voxel
+    centres (spacing apart), `n_handles` distinct seeded constrained voxels
+    displaced uniformly in [-max_off, max_off]^3."""
+    zs, ys, xs = np.mgrid[0:D, 0:H, 0:W]
+    urshape = (spacing * np.stack([xs, ys, zs]).reshape(3, -1)).astype(np.float32)
+    V = W * H * D
+    rng = np.random.default_rng(seed)
+    hidx = np.sort(rng.choice(V, size=n_handles, replace=False)).astype(np.int32)
+    htgt = rng.uniform(-max_off, max_off, size=(n_handles, 3)).astype(np.float32)
+    x0 = np.zeros((6, V), np.float32)
+    if x0_noise > 0:
+        x0[:] = rng.uniform(-x0_noise, x0_noise, size=x0.shape).astype(np.float32)
+    return VolumeProblem(W, H, D, urshape, x0, hidx, htgt, float(w_reg), float(w_fit), seed)
+
+
+def volume_edges(W: int, H: int, D: int):
+    """The 7-point stencil of a W x H x D grid as directed edges (k, k + d)
+    with both voxels inside the grid, sorted by (v0, v1)."""
+    zs, ys, xs = np.mgrid[0:D, 0:H, 0:W]
+    a, b = [], []
+    for ox, oy, oz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+        nx, ny, nz = xs + ox, ys + oy, zs + oz
+        ok = (nx >= 0) & (nx < W) & (ny >= 0) & (ny < H) & (nz >= 0) & (nz < D)
+        a.append(((zs * H + ys) * W + xs)[ok])
+        b.append(((nz * H + ny) * W + nx)[ok])
+    v0 = np.concatenate(a)
+    v1 = np.concatenate(b)
+    order = np.lexsort((v1, v0))
+    return v0[order].astype(np.int32), v1[order].astype(np.int32)
 
 
 # ----------------------------------------------------------------------------

@@ -247,6 +247,35 @@ def test_warp_graph_rigid_motion_has_zero_regularizer():
     assert en.make_energy(gp).energy(x) == pytest.approx(0.0, abs=1e-20)
 
 
+def test_volume_stencil_count_and_equals_mesh_on_the_voxel_graph():
+    # Fig. 31: the 7-point stencil on a W x H x D array; as an explicit graph of
+    # the same neighbour pairs it is the Fig. 25 energy (Rotate3D at the centre)
+    W, H, D = 4, 3, 5
+    vp = synth.volume_problem(W, H, D, 6, seed=2, x0_noise=0.3)
+    ev = en.make_energy(vp)
+    assert ev.a.size == 2 * ((W - 1) * H * D + W * (H - 1) * D + W * H * (D - 1))
+    v0, v1 = synth.volume_edges(W, H, D)
+    em = en.MeshEnergy(synth.MeshProblem(vp.V, vp.urshape, v0, v1, vp.x0, vp.handle_idx, vp.handle_target))
+    x = vp.x0.reshape(-1).astype(np.float64) + np.random.default_rng(3).uniform(-0.2, 0.2, vp.n_unknowns)
+    assert ev.energy(x) == pytest.approx(em.energy(x), rel=1e-13)
+    Jv, Jm = ev.jacobian(x), em.jacobian(x)
+    np.testing.assert_allclose(Jv.T @ ev.residuals(x), Jm.T @ em.residuals(x), rtol=0, atol=1e-11)
+    np.testing.assert_allclose((Jv.T @ Jv).toarray(), (Jm.T @ Jm).toarray(), rtol=0, atol=1e-11)
+
+
+def test_volume_rigid_motion_has_zero_regularizer():
+    from scipy.spatial.transform import Rotation
+    vp = synth.volume_problem(3, 4, 3, 1, seed=5)
+    ang = np.array([0.3, -0.5, 0.9])
+    R = Rotation.from_euler("xyz", ang).as_matrix()      # = Rz Ry Rx (extrinsic xyz)
+    U = vp.urshape.astype(np.float64)
+    O = R @ U + np.array([[1.0], [2.0], [-0.5]])
+    x = np.concatenate([O - U, np.repeat(ang[:, None], vp.V, 1)]).reshape(-1)
+    vp.handle_idx = np.zeros(0, np.int32)
+    vp.handle_target = np.zeros((0, 3), np.float32)
+    assert en.make_energy(vp).energy(x) == pytest.approx(0.0, abs=1e-18)
+
+
 # --------------------------------------------------------------------------
 # Jacobian: central finite differences; gradient = 2 J^T F
 # --------------------------------------------------------------------------
@@ -269,6 +298,7 @@ def random_warp_graph(seed=6):
     lambda: (tiny_mesh(), None),
     lambda: (synth.poisson_problem(6, 5, seed=2), None),
     lambda: (random_warp_graph(), None),
+    lambda: (synth.volume_problem(3, 2, 3, 2, seed=4, x0_noise=0.3), None),
 ])
 def test_jacobian_matches_central_differences(make):
     prob, _ = make()
