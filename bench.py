@@ -49,6 +49,12 @@ BYTES_UPDATE_MESH = 160    # read delta 24, p 24, r 24, q 24, M^-1 16; write del
 BYTES_INIT_MESH = 356      # vertex pass: read angles 12; write JtF 24, acc 12, cos/sin 24 (72);
 #                            edge pass: (v0, v1) 48, U 12, x 24, cos/sin 24, JtF and acc read + write 72 (180);
 #                            final pass: read degree 4, acc 12, JtF 24; write M^-1 16, r 24, delta 24 (104)
+# volumetric ARAP, per voxel (the gather form: neighbour records hit cache)
+BYTES_APPLY_VOLUME = 224   # direction pass: read r 24, M^-1 16, p_old 24; write p 24, p record 32 (120);
+#                            gather pass: read own records 32 + 48; write q 24 (104)
+BYTES_UPDATE_VOLUME = 160  # as the mesh
+BYTES_INIT_VOLUME = 264    # vertex pass: read x 24, U 12; write records 80 (116); gather pass: read
+#                            records 80, degree 4; write r 24, M^-1 16, delta 24 (148)
 KERNEL_SOURCES = ("grid_kernels.cu", "opt_internal.cuh", "opt_launch.h")
 L2_FLUSH_BYTES = 512 << 20
 
@@ -257,6 +263,16 @@ def roofline_beyond_l2(api, synth, torch, peak):
                                         ("k_mesh_update", BYTES_UPDATE_MESH, 15 * 30)), mp.V, peak)}
     gp.close()
     del mp
+    torch.cuda.empty_cache()
+    vp = synth.volume_problem(128, 128, 128, 2048, seed=synth.BASE_SEED)
+    gp = api.Problem(vp)
+    res["volume_128x128x128"] = {
+        "unit_of_work": "voxel", "units": vp.V,
+        "kernels": kernel_roofline(gp, (("k_mesh_init_v+pull<grid>", BYTES_INIT_VOLUME, 10),
+                                        ("k_mesh_apply_v+pull<grid>", BYTES_APPLY_VOLUME, 10 * 10),
+                                        ("k_mesh_update", BYTES_UPDATE_VOLUME, 10 * 10)), vp.V, peak)}
+    gp.close()
+    del vp
     torch.cuda.empty_cache()
     return res
 
@@ -555,6 +571,21 @@ def run_ours(args):
             "E_final_graph": rr_graph[-1]["E_final"]}
         ggp.close()
         del gwp
+
+        # volumetric deformation at the paper's size (4,961 voxels, Appendix A.2.5)
+        vp = synth.volume_problem(11, 11, 41, 40, seed=synth.BASE_SEED)
+        gv = api.Problem(vp)
+        xv0 = gv.x.clone()
+        rr = []
+        for _ in range(4):
+            gv.x.copy_(xv0)
+            rr.append(gv.solve_lm(10, 10))
+        msv = statistics.median(r_["ms"] for r_ in rr[1:])
+        extra["volume_11x11x41_lm10x10"] = {"ms_per_solve": msv, "voxels_per_s": vp.V / (msv / 1e3),
+                                            "pcg_iters_per_s": rr[-1]["pcg_done"] / (msv / 1e3),
+                                            "accepted": rr[-1]["accepted"], "E0": rr[-1]["E0"],
+                                            "E_final": rr[-1]["E_final"]}
+        gv.close()
 
         extra["batched_512_warps_gn10x10"] = bench_batched(api, synth, torch, flush)
         extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch)

@@ -54,7 +54,8 @@ typedef enum {
     OPT_ARAP_WARP_2D = 0,     /* Fig. 24: unknowns dx, dy, theta per pixel */
     OPT_POISSON_2D = 1,       /* Fig. 27: unknowns X (4 channels) per pixel */
     OPT_ARAP_MESH = 2,        /* Fig. 25: unknowns dx, dy, dz, ax, ay, az per vertex */
-    OPT_ARAP_WARP_GRAPH = 3   /* Fig. 24 on an explicit graph (Fig. 18): dx, dy, theta per vertex */
+    OPT_ARAP_WARP_GRAPH = 3,  /* Fig. 24 on an explicit graph (Fig. 18): dx, dy, theta per vertex */
+    OPT_ARAP_VOLUME = 4       /* Fig. 31: dx, dy, dz, ax, ay, az per voxel of a 3-D grid */
 } opt_energy;
 
 typedef struct opt_problem opt_problem;
@@ -112,6 +113,26 @@ typedef struct {
     int32_t n_handles;
     float w_reg, w_fit;
 } opt_graph_desc;
+
+/* Volumetric ARAP deformation (Fig. 31, Appendix A.2.5): a W x H x D voxel
+ * grid, voxel index (z*H + y)*W + x, every plane W*H*D float32 values.
+ *   unknowns[6] = dx, dy, dz (Offset - UrShape) and Euler angles ax, ay, az
+ *                 (device).
+ *   urshape[3]  = rest positions x, y, z (device).
+ *   handle_idx / handle_target = n_handles distinct constrained voxels and
+ *                 their (x, y, z) target displacements, interleaved (device).
+ *   Residuals: for every voxel k and direction d in {+-x, +-y, +-z} with k+d
+ *   in the grid, sqrt(w_reg) * ((O_k - O_{k+d}) - Rz Ry Rx(A_k) (U_k - U_{k+d}));
+ *   for every constrained voxel, sqrt(w_fit) * (O_h - C_h), C_h = U_h + target. */
+typedef struct {
+    int32_t W, H, D;
+    float* unknowns[6];
+    const float* urshape[3];
+    const int32_t* handle_idx;
+    const float* handle_target;
+    int32_t n_handles;
+    float w_reg, w_fit;
+} opt_volume_desc;
 
 /* Solver parameters (Sec. 4, Sec. 7 "LM vs. GN", "Matrix-free vs.
  * Materialized").  opt_solve_params_default fills the values used by the
@@ -189,6 +210,15 @@ opt_status opt_problem_create_graph(const opt_graph_desc* desc, const opt_solve_
  * solve time).  Errors as opt_problem_create_graph. */
 opt_status opt_problem_create_graph2d(const opt_graph_desc* desc, const opt_solve_params* params,
                                       opt_problem** out);
+
+/* Plan a volumetric ARAP problem (OPT_ARAP_VOLUME).  The voxel grid is the
+ * implicit structure: the kernels take each voxel's neighbours from the
+ * 7-point stencil (the mesh energy's gather kernels otherwise).  W, H, D >= 1
+ * with W*H*D <= 2^27, same validation and ownership as
+ * opt_problem_create_graph.  Solves like a graph problem, including the
+ * materialized form. */
+opt_status opt_problem_create_volume(const opt_volume_desc* desc, const opt_solve_params* params,
+                                     opt_problem** out);
 
 /* Frees everything the problem owns.  NULL is accepted. */
 opt_status opt_problem_destroy(opt_problem* prob);

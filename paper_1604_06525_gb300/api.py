@@ -36,6 +36,12 @@ class GraphDesc(ctypes.Structure):
                 ("w_reg", c_float), ("w_fit", c_float)]
 
 
+class VolumeDesc(ctypes.Structure):
+    _fields_ = [("W", c_int32), ("H", c_int32), ("D", c_int32), ("unknowns", c_void_p * 6),
+                ("urshape", c_void_p * 3), ("handle_idx", c_void_p), ("handle_target", c_void_p),
+                ("n_handles", c_int32), ("w_reg", c_float), ("w_fit", c_float)]
+
+
 class SolveParams(ctypes.Structure):
     _fields_ = [("outer", c_int32), ("inner", c_int32), ("lambda0", c_double),
                 ("lambda_min", c_double), ("lambda_max", c_double), ("diag_min", c_double),
@@ -56,6 +62,7 @@ _SIGNATURES = [
     ("opt_problem_create_grid", c_int32, [POINTER(GridDesc), POINTER(SolveParams), POINTER(c_void_p)]),
     ("opt_problem_create_graph", c_int32, [POINTER(GraphDesc), POINTER(SolveParams), POINTER(c_void_p)]),
     ("opt_problem_create_graph2d", c_int32, [POINTER(GraphDesc), POINTER(SolveParams), POINTER(c_void_p)]),
+    ("opt_problem_create_volume", c_int32, [POINTER(VolumeDesc), POINTER(SolveParams), POINTER(c_void_p)]),
     ("opt_problem_destroy", c_int32, [c_void_p]),
     ("opt_solve_gn", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report)]),
     ("opt_solve_lm", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report)]),
@@ -198,6 +205,23 @@ def make_descriptor(prob, device):
         d.w_reg, d.w_fit = prob.w_reg, prob.w_fit
         keep += [U, v0, v1, hidx, htgt, x]
         return d, x, keep
+    if prob.kind == "volume":
+        x = f32(prob.x0).reshape(6, prob.V).clone()
+        U = f32(prob.urshape)
+        hidx = i32(prob.handle_idx)
+        htgt = f32(prob.handle_target.reshape(-1))
+        d = VolumeDesc()
+        d.W, d.H, d.D = prob.W, prob.H, prob.D
+        for c in range(6):
+            d.unknowns[c] = _ptr(x[c])
+        for c in range(3):
+            d.urshape[c] = _ptr(U[c])
+        d.n_handles = int(prob.handle_idx.size)
+        d.handle_idx = _ptr(hidx) if d.n_handles else None
+        d.handle_target = _ptr(htgt) if d.n_handles else None
+        d.w_reg, d.w_fit = prob.w_reg, prob.w_fit
+        keep += [U, hidx, htgt, x]
+        return d, x, keep
     raise ValueError(prob.kind)
 
 
@@ -233,8 +257,8 @@ class Problem:
                    "opt_problem_create_grid")
         else:
             self.V = prob.V
-            create = (self.lib.opt_problem_create_graph if prob.kind == "mesh"
-                      else self.lib.opt_problem_create_graph2d)
+            create = {"mesh": self.lib.opt_problem_create_graph, "warp_graph": self.lib.opt_problem_create_graph2d,
+                      "volume": self.lib.opt_problem_create_volume}[prob.kind]
             _check(create(ctypes.byref(d), None, ctypes.byref(h)), "opt_problem_create_graph")
         self.h = h
 

@@ -227,7 +227,7 @@ bool is_grid(const opt_problem* pb) { return pb->kind == K_WARP || pb->kind == K
 
 // distinct-diagonal plane of unknown component c
 int mplane_of(int kind, int c) {
-  if (kind == K_WARP || kind == K_WARPG) return c == 2 ? 1 : 0;
+  if (kind == K_WARP || kind == K_WARPG) return c == 2 ? 1 : 0;   // K_MESH / K_VOLUME below
   if (kind == K_POISSON) return 0;
   return c < 3 ? 0 : c - 2;
 }
@@ -303,7 +303,7 @@ GridLaunch grid_launch(const opt_problem* pb, cudaStream_t st) {
 }
 MeshLaunch mesh_launch(const opt_problem* pb, cudaStream_t st) {
   return MeshLaunch{pb->dm, pb->d_vchunks, pb->d_echunks, pb->d_part, pb->nvchunks,
-                    pb->nechunks, st, pb->kind == K_WARPG ? 2 : 3};
+                    pb->nechunks, st, pb->kind == K_WARPG ? 2 : 3, pb->kind == K_VOLUME ? 1 : 0};
 }
 
 opt_status upload_desc(opt_problem* pb, cudaStream_t st) {
@@ -743,13 +743,18 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
 // Graph planning for dimension D: D = 3 is the ARAP mesh (unknowns dx, dy, dz,
 // ax, ay, az; rest positions and targets in 3-D), D = 2 the warp on a graph
 // (unknowns dx, dy, theta; rest positions and targets in 2-D).
-static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem** out) {
+// grid3 (volumetric problems): the W x H x D voxel grid whose 7-point stencil
+// the host edge lists hold; vertices then keep the caller's order (already
+// local) and the gather kernels take neighbours from the stencil.
+static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem** out,
+                                    const std::vector<int>* host_e0 = nullptr,
+                                    const std::vector<int>* host_e1 = nullptr, const int* grid3 = nullptr) {
   const int NXg = D == 3 ? 6 : 3, NMg = D == 3 ? 4 : 2, NGR = D == 3 ? 3 : 1, NVR = D == 3 ? 2 : 1;
   if (!out) return OPT_ERR_INVALID_ARG;
   *out = nullptr;
   if (!d) return OPT_ERR_INVALID_ARG;
   if (d->V < 1 || d->E < 0 || d->n_handles < 0) return OPT_ERR_INVALID_ARG;
-  if (d->E > 0 && (!d->v0 || !d->v1)) return OPT_ERR_INVALID_ARG;
+  if (d->E > 0 && !host_e0 && (!d->v0 || !d->v1)) return OPT_ERR_INVALID_ARG;
   for (int c = 0; c < NXg; ++c)
     if (!d->unknowns[c]) return OPT_ERR_INVALID_ARG;
   for (int c = 0; c < D; ++c)
@@ -760,7 +765,7 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
 
   std::unique_ptr<opt_problem> pb(new opt_problem());
   opt_problem* q = pb.get();
-  q->kind = D == 3 ? K_MESH : K_WARPG;
+  q->kind = grid3 ? K_VOLUME : (D == 3 ? K_MESH : K_WARPG);
   q->nx = NXg;
   q->nm = NMg;
   q->V = d->V;
@@ -772,8 +777,13 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   CKS(common_setup(q));
 
   std::vector<int> e0, e1;
-  CKS(download(e0, d->v0, (size_t)E));
-  CKS(download(e1, d->v1, (size_t)E));
+  if (host_e0) {
+    e0 = *host_e0;
+    e1 = *host_e1;
+  } else {
+    CKS(download(e0, d->v0, (size_t)E));
+    CKS(download(e1, d->v1, (size_t)E));
+  }
   for (int e = 0; e < E; ++e)
     if (e0[e] < 0 || e0[e] >= V || e1[e] < 0 || e1[e] >= V || e0[e] == e1[e]) return OPT_ERR_INVALID_ARG;
   std::vector<float> Uh[3];
@@ -784,7 +794,13 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   }
   // internal vertex order: internal k = caller perm[k]; edges and handles are
   // renumbered before sorting
-  const std::vector<int> perm = morton_order(Uh, V);
+  std::vector<int> perm;
+  if (grid3) {
+    perm.resize((size_t)V);
+    std::iota(perm.begin(), perm.end(), 0);
+  } else {
+    perm = morton_order(Uh, V);
+  }
   std::vector<int> iperm((size_t)V);
   for (int k = 0; k < V; ++k) iperm[perm[k]] = k;
   for (int e = 0; e < E; ++e) { e0[e] = iperm[e0[e]]; e1[e] = iperm[e1[e]]; }
@@ -925,6 +941,7 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   g.x = q->x; g.U = U; g.degw = dgw; g.e0 = de0; g.e1 = de1;
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
   g.orow = dorow; g.irow = dirow; g.isrc = disrc;
+  g.gw = grid3 ? grid3[0] : 0; g.gh = grid3 ? grid3[1] : 0; g.gd = grid3 ? grid3[2] : 0; g.gpad = 0;
   g.grec = grec; g.vrec = vrec;
   g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;
   g.jtf_out = nullptr; g.diag_out = nullptr;
@@ -943,6 +960,44 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
 opt_status opt_problem_create_graph2d(const opt_graph_desc* d, const opt_solve_params* prm, opt_problem** out) {
   (void)prm;
   return create_graph_impl(d, 2, out);
+}
+
+opt_status opt_problem_create_volume(const opt_volume_desc* d, const opt_solve_params* prm, opt_problem** out) {
+  (void)prm;
+  if (!out) return OPT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d || d->W < 1 || d->H < 1 || d->D < 1) return OPT_ERR_INVALID_ARG;
+  const long long V = (long long)d->W * d->H * d->D;
+  if (V > (1ll << 27)) return OPT_ERR_INVALID_ARG;
+  const int W = d->W, H = d->H, Dz = d->D;
+  // the 7-point stencil as directed edges, sorted by (v0, v1)
+  std::vector<int> e0, e1;
+  e0.reserve((size_t)V * 6);
+  e1.reserve((size_t)V * 6);
+  for (int z = 0; z < Dz; ++z)
+    for (int y = 0; y < H; ++y)
+      for (int x = 0; x < W; ++x) {
+        const int i = (z * H + y) * W + x;
+        const int WH = W * H;
+        if (z > 0) { e0.push_back(i); e1.push_back(i - WH); }
+        if (y > 0) { e0.push_back(i); e1.push_back(i - W); }
+        if (x > 0) { e0.push_back(i); e1.push_back(i - 1); }
+        if (x + 1 < W) { e0.push_back(i); e1.push_back(i + 1); }
+        if (y + 1 < H) { e0.push_back(i); e1.push_back(i + W); }
+        if (z + 1 < Dz) { e0.push_back(i); e1.push_back(i + WH); }
+      }
+  opt_graph_desc g = {};
+  g.V = (int32_t)V;
+  g.E = (int32_t)e0.size();
+  for (int c = 0; c < 6; ++c) g.unknowns[c] = d->unknowns[c];
+  for (int c = 0; c < 3; ++c) g.urshape[c] = d->urshape[c];
+  g.handle_idx = d->handle_idx;
+  g.handle_target = d->handle_target;
+  g.n_handles = d->n_handles;
+  g.w_reg = d->w_reg;
+  g.w_fit = d->w_fit;
+  const int dims[3] = {W, H, Dz};
+  return create_graph_impl(&g, 3, out, &e0, &e1, dims);
 }
 
 opt_status opt_problem_destroy(opt_problem* prob) {

@@ -151,6 +151,7 @@ struct GridGroup {
 
 struct MeshGroup {
   int dim = 3;                         // 3: ARAP mesh, 2: warp on a graph
+  int grid3 = 0;                       // volumetric problems (7-point stencil)
   std::vector<int> members;
   MeshProb* d_probs = nullptr;
   Chunk* d_vch = nullptr;
@@ -164,7 +165,7 @@ struct MeshGroup {
 struct opt_batch {
   std::vector<opt_problem*> probs;
   std::vector<GridGroup> grids;
-  MeshGroup graphs[2];               // [0]: ARAP meshes (dim 3), [1]: warps on graphs (dim 2)
+  MeshGroup graphs[3];               // [0]: ARAP meshes, [1]: warps on graphs, [2]: volumes
   int tiles_per_chunk = 0;          // 0 = per-problem default
   std::vector<void*> table_allocs;  // rebuilt with the chunking
   std::vector<void*> allocs;        // fixed for the batch's life
@@ -271,7 +272,7 @@ GridLaunch gl(const GridGroup& g, cudaStream_t st) {
   return GridLaunch{g.d_probs, g.d_chunks, g.d_tiles, g.d_part, g.nchunks, st, g.tw, g.masked};
 }
 MeshLaunch ml(const MeshGroup& g, cudaStream_t st) {
-  return MeshLaunch{g.d_probs, g.d_vch, g.d_ech, g.d_part, g.nv, g.ne, st, g.dim};
+  return MeshLaunch{g.d_probs, g.d_vch, g.d_ech, g.d_part, g.nv, g.ne, st, g.dim, g.grid3};
 }
 
 // Uploads the members' descriptors with the solve's flags (outside any capture).
@@ -474,9 +475,11 @@ opt_status opt_batch_create(opt_problem* const* probs, int32_t n, opt_batch** ou
         if (!g.members.empty()) b->grids.push_back(g);
       }
   b->graphs[1].dim = 2;
+  b->graphs[2].grid3 = 1;
   for (int i = 0; i < n; ++i) {
     if (probs[i]->kind == K_MESH) b->graphs[0].members.push_back(i);
     if (probs[i]->kind == K_WARPG) b->graphs[1].members.push_back(i);
+    if (probs[i]->kind == K_VOLUME) b->graphs[2].members.push_back(i);
   }
   BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
   BCK(cudaEventCreate(&b->ev0));

@@ -51,6 +51,26 @@ __device__ __forceinline__ float c4(const float4& a, int k) {
   return k == 0 ? a.x : (k == 1 ? a.y : (k == 2 ? a.z : a.w));
 }
 
+// The 7-point stencil of a W x H x D voxel grid (volumetric problems): the
+// six neighbour offsets in ascending order -- the order the sorted edge lists
+// give -- and which of them lie inside the grid.
+struct Stencil3 {
+  int off[6];
+  bool ok[6];
+};
+__device__ __forceinline__ Stencil3 stencil3(const MeshProb& pr, int i) {
+  const int W = pr.gw, H = pr.gh, WH = W * H;
+  const int x = i % W, y = (i / W) % H, z = i / WH;
+  Stencil3 st;
+  st.off[0] = -WH; st.ok[0] = z > 0;
+  st.off[1] = -W;  st.ok[1] = y > 0;
+  st.off[2] = -1;  st.ok[2] = x > 0;
+  st.off[3] = 1;   st.ok[3] = x + 1 < W;
+  st.off[4] = W;   st.ok[4] = y + 1 < H;
+  st.off[5] = WH;  st.ok[5] = z + 1 < pr.gd;
+  return st;
+}
+
 // A vertex's geometry record and 6-vector record.
 struct GeoRec {
   float U[3];
@@ -105,6 +125,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_v(const MeshProb* __restrict__
 // their angle rows, incoming edge residuals), diag(J^T J) (displacement:
 // planned w_reg * degree + w_fit; angles: sum |g_m|^2 over the out-edges),
 // the energy of the own residuals, then b = -J^T F, M^-1, r = b, delta = 0.
+template <bool G3>
 __global__ void __launch_bounds__(NT) k_mesh_init_pull(const MeshProb* __restrict__ probs,
                                                        const Chunk* __restrict__ chunks,
                                                        double* __restrict__ part, int k_outer, float dmin,
@@ -134,9 +155,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_pull(const MeshProb* __restric
         e += f * f;
       }
     }
-    const int o0 = pr.orow[i], o1 = pr.orow[i + 1];
-    for (int k = o0; k < o1; ++k) {
-      const int j = pr.e1[k];
+    auto own_edge = [&](int j) {
       float xj[3];
       load_vec3(pr.vrec, j, xj);
       const float4 uj = __ldg(pr.grec + 3 * j);
@@ -153,10 +172,8 @@ __global__ void __launch_bounds__(NT) k_mesh_init_pull(const MeshProb* __restric
         da[m] += g0 * g0 + g1 * g1 + g2 * g2;
       }
       e += r0 * r0 + r1 * r1 + r2 * r2;
-    }
-    const int n0 = pr.irow[i], n1 = pr.irow[i + 1];
-    for (int k = n0; k < n1; ++k) {
-      const int j = pr.isrc[k];
+    };
+    auto in_edge = [&](int j) {
       float xj[3];
       load_vec3(pr.vrec, j, xj);
       const GeoRec gj = load_geo(pr.grec, j);
@@ -165,6 +182,18 @@ __global__ void __launch_bounds__(NT) k_mesh_init_pull(const MeshProb* __restric
       g[0] -= sw * (sw * ((xj[0] - xi[0]) + (vx - R.rv[0])));
       g[1] -= sw * (sw * ((xj[1] - xi[1]) + (vy - R.rv[1])));
       g[2] -= sw * (sw * ((xj[2] - xi[2]) + (vz - R.rv[2])));
+    };
+    if (G3) {
+      const Stencil3 st = stencil3(pr, i);
+#pragma unroll
+      for (int t = 0; t < 6; ++t)
+        if (st.ok[t]) own_edge(i + st.off[t]);
+#pragma unroll
+      for (int t = 0; t < 6; ++t)
+        if (st.ok[t]) in_edge(i + st.off[t]);
+    } else {
+      for (int k = pr.orow[i]; k < pr.orow[i + 1]; ++k) own_edge(pr.e1[k]);
+      for (int k = pr.irow[i]; k < pr.irow[i + 1]; ++k) in_edge(pr.isrc[k]);
     }
     const float dg[4] = {pr.degw[i], da[0], da[1], da[2]};
     float mv[4];
@@ -272,6 +301,7 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_v(const MeshProb* __restrict_
 // in-edges are loaded together before any record is needed; the kernel is
 // bound by these dependent load chains, so it is compiled for
 // MESH_PULL_MIN_BLOCKS resident blocks per SM (measured best at 4).
+template <bool G3>
 __global__ void __launch_bounds__(NT, MESH_PULL_MIN_BLOCKS) k_mesh_apply_pull(const MeshProb* __restrict__ probs,
                                                                              const Chunk* __restrict__ chunks,
                                                                              double* __restrict__ part) {
@@ -285,13 +315,16 @@ __global__ void __launch_bounds__(NT, MESH_PULL_MIN_BLOCKS) k_mesh_apply_pull(co
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   float acc = 0.f;
   for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
-    const int o0 = pr.orow[i], o1 = pr.orow[i + 1];
-    const int n0 = pr.irow[i], n1 = pr.irow[i + 1];
+    int o0 = 0, o1 = 0, n0 = 0, n1 = 0;
     int jo[KB], ji[KB];
+    if (!G3) {
+      o0 = pr.orow[i]; o1 = pr.orow[i + 1];
+      n0 = pr.irow[i]; n1 = pr.irow[i + 1];
 #pragma unroll
-    for (int t = 0; t < KB; ++t) {
-      jo[t] = o0 + t < o1 ? pr.e1[o0 + t] : 0;
-      ji[t] = n0 + t < n1 ? pr.isrc[n0 + t] : 0;
+      for (int t = 0; t < KB; ++t) {
+        jo[t] = o0 + t < o1 ? pr.e1[o0 + t] : 0;
+        ji[t] = n0 + t < n1 ? pr.isrc[n0 + t] : 0;
+      }
     }
     float pi[6];
     load_vec(pr.vrec, i, pi);
@@ -303,47 +336,57 @@ __global__ void __launch_bounds__(NT, MESH_PULL_MIN_BLOCKS) k_mesh_apply_pull(co
 #pragma unroll
       for (int c = 0; c < 3; ++c) q[c] += pr.w_fit * pi[c];
     }
+    auto own_edge = [&](int j) {
+      float pj[3];
+      load_vec3(pr.vrec, j, pj);
+      const float4 uj = __ldg(pr.grec + 3 * j);
+      const float vx = gi.U[0] - uj.x, vy = gi.U[1] - uj.y, vz = gi.U[2] - uj.z;
+      const RotV R = rot_apply_cs(gi.cs[0], gi.cs[1], gi.cs[2], gi.cs[3], gi.cs[4], gi.cs[5], vx, vy, vz);
+      float j0 = sw * (pi[0] - pj[0]), j1 = sw * (pi[1] - pj[1]), j2 = sw * (pi[2] - pj[2]);
 #pragma unroll
-    for (int t = 0; t < KB + 1; ++t) {
-      // t < KB: one prefetched out-edge (if the row has it); t == KB: the rest of a longer row
-      const int kb = t < KB ? o0 + t : o0 + KB, ke = t < KB ? min(o0 + t + 1, o1) : o1;
-      for (int k = kb; k < ke; ++k) {
-        const int j = t < KB ? jo[t] : pr.e1[k];
-        float pj[3];
-        load_vec3(pr.vrec, j, pj);
-        const float4 uj = __ldg(pr.grec + 3 * j);
-        const float vx = gi.U[0] - uj.x, vy = gi.U[1] - uj.y, vz = gi.U[2] - uj.z;
-        const RotV R = rot_apply_cs(gi.cs[0], gi.cs[1], gi.cs[2], gi.cs[3], gi.cs[4], gi.cs[5], vx, vy, vz);
-        float j0 = sw * (pi[0] - pj[0]), j1 = sw * (pi[1] - pj[1]), j2 = sw * (pi[2] - pj[2]);
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          j0 -= sw * R.g[m][0] * pi[3 + m];
-          j1 -= sw * R.g[m][1] * pi[3 + m];
-          j2 -= sw * R.g[m][2] * pi[3 + m];
-        }
-        q[0] += sw * j0; q[1] += sw * j1; q[2] += sw * j2;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) q[3 + m] -= sw * (R.g[m][0] * j0 + R.g[m][1] * j1 + R.g[m][2] * j2);
+      for (int m = 0; m < 3; ++m) {
+        j0 -= sw * R.g[m][0] * pi[3 + m];
+        j1 -= sw * R.g[m][1] * pi[3 + m];
+        j2 -= sw * R.g[m][2] * pi[3 + m];
       }
-    }
+      q[0] += sw * j0; q[1] += sw * j1; q[2] += sw * j2;
 #pragma unroll
-    for (int t = 0; t < KB + 1; ++t) {
-      const int kb = t < KB ? n0 + t : n0 + KB, ke = t < KB ? min(n0 + t + 1, n1) : n1;
-      for (int k = kb; k < ke; ++k) {
-        const int j = t < KB ? ji[t] : pr.isrc[k];
-        float pj[6];
-        load_vec(pr.vrec, j, pj);
-        const GeoRec gj = load_geo(pr.grec, j);
-        const float vx = gj.U[0] - gi.U[0], vy = gj.U[1] - gi.U[1], vz = gj.U[2] - gi.U[2];
-        const RotV R = rot_apply_cs(gj.cs[0], gj.cs[1], gj.cs[2], gj.cs[3], gj.cs[4], gj.cs[5], vx, vy, vz);
-        float j0 = sw * (pj[0] - pi[0]), j1 = sw * (pj[1] - pi[1]), j2 = sw * (pj[2] - pi[2]);
+      for (int m = 0; m < 3; ++m) q[3 + m] -= sw * (R.g[m][0] * j0 + R.g[m][1] * j1 + R.g[m][2] * j2);
+    };
+    auto in_edge = [&](int j) {
+      float pj[6];
+      load_vec(pr.vrec, j, pj);
+      const GeoRec gj = load_geo(pr.grec, j);
+      const float vx = gj.U[0] - gi.U[0], vy = gj.U[1] - gi.U[1], vz = gj.U[2] - gi.U[2];
+      const RotV R = rot_apply_cs(gj.cs[0], gj.cs[1], gj.cs[2], gj.cs[3], gj.cs[4], gj.cs[5], vx, vy, vz);
+      float j0 = sw * (pj[0] - pi[0]), j1 = sw * (pj[1] - pi[1]), j2 = sw * (pj[2] - pi[2]);
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          j0 -= sw * R.g[m][0] * pj[3 + m];
-          j1 -= sw * R.g[m][1] * pj[3 + m];
-          j2 -= sw * R.g[m][2] * pj[3 + m];
-        }
-        q[0] -= sw * j0; q[1] -= sw * j1; q[2] -= sw * j2;
+      for (int m = 0; m < 3; ++m) {
+        j0 -= sw * R.g[m][0] * pj[3 + m];
+        j1 -= sw * R.g[m][1] * pj[3 + m];
+        j2 -= sw * R.g[m][2] * pj[3 + m];
+      }
+      q[0] -= sw * j0; q[1] -= sw * j1; q[2] -= sw * j2;
+    };
+    if (G3) {
+      const Stencil3 st = stencil3(pr, i);
+#pragma unroll
+      for (int t = 0; t < 6; ++t)
+        if (st.ok[t]) own_edge(i + st.off[t]);
+#pragma unroll
+      for (int t = 0; t < 6; ++t)
+        if (st.ok[t]) in_edge(i + st.off[t]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < KB + 1; ++t) {
+        // t < KB: one prefetched out-edge (if the row has it); t == KB: the rest of a longer row
+        const int kb = t < KB ? o0 + t : o0 + KB, ke = t < KB ? min(o0 + t + 1, o1) : o1;
+        for (int k = kb; k < ke; ++k) own_edge(t < KB ? jo[t] : pr.e1[k]);
+      }
+#pragma unroll
+      for (int t = 0; t < KB + 1; ++t) {
+        const int kb = t < KB ? n0 + t : n0 + KB, ke = t < KB ? min(n0 + t + 1, n1) : n1;
+        for (int k = kb; k < ke; ++k) in_edge(t < KB ? ji[t] : pr.isrc[k]);
       }
     }
 #pragma unroll
@@ -543,13 +586,20 @@ __global__ void __launch_bounds__(NT) k_mesh_step(const MeshProb* __restrict__ p
 void launch_mesh_init(const MeshLaunch& L, int k_outer, float dmin, float dmax) {
   if (L.dim == 2) return launch_wg_init(L, k_outer, dmin, dmax);
   launch_pdl(k_mesh_init_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks);
-  launch_pdl(k_mesh_init_pull, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, k_outer, dmin, dmax);
+  if (L.grid3)
+    launch_pdl(k_mesh_init_pull<true>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, k_outer, dmin, dmax);
+  else
+    launch_pdl(k_mesh_init_pull<false>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, k_outer, dmin,
+               dmax);
 }
 
 void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, int update) {
   if (L.dim == 2) return launch_wg_apply(L, p_override, par, update);
   launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, p_override, par, update);
-  launch_pdl(k_mesh_apply_pull, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
+  if (L.grid3)
+    launch_pdl(k_mesh_apply_pull<true>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
+  else
+    launch_pdl(k_mesh_apply_pull<false>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
 }
 
 void launch_mesh_update(const MeshLaunch& L, int par) {

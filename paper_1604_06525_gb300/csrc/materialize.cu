@@ -291,9 +291,10 @@ void csr_apply(opt_problem* pb, cudaStream_t st, int par) {
   const long long pl = pb->plane;
   const float* pin = pb->pbuf + (long long)(par & 1) * pb->nx * pl;
   float* pout = pb->pbuf + (long long)((par + 1) & 1) * pb->nx * pl;
-  const float* m = pb->kind == K_MESH ? pb->hm.m : pb->hg.m;
-  const float* dc = pb->kind == K_MESH ? pb->hm.dc : pb->hg.dc;
-  const int lm = pb->kind == K_MESH ? pb->hm.lm : pb->hg.lm;
+  const bool graph = pb->kind == K_MESH || pb->kind == K_VOLUME;   // the mesh energy (K_WARPG has no CSR form)
+  const float* m = graph ? pb->hm.m : pb->hg.m;
+  const float* dc = graph ? pb->hm.dc : pb->hg.dc;
+  const int lm = graph ? pb->hm.lm : pb->hg.lm;
   k_csr_direction<<<blocks_for(J.nT, cap), NT, 0, st>>>(J.nT, J.t_unk, pl, cm, m, pb->rvec, pin, pout, pb->d_s);
   k_csr_jp<<<blocks_for(J.R, cap), NT, 0, st>>>(J.R, J.rp, J.col, J.val, pout, J.tvec, pb->d_s);
   k_csr_jtt<<<J.nblk_t, NT, 0, st>>>(J.nT, J.t_unk, J.t_ptr, J.t_row, J.t_val, J.tvec, pout, pb->qvec, dc, lm, pl,

@@ -29,7 +29,8 @@
 
 namespace optgb {
 
-enum Kind : int { K_WARP = 0, K_POISSON = 1, K_MESH = 2, K_WARPG = 3 };   // K_WARPG: warp on a graph
+// K_WARPG: the warp on a graph; K_VOLUME: volumetric ARAP (the mesh energy on a voxel grid)
+enum Kind : int { K_WARP = 0, K_POISSON = 1, K_MESH = 2, K_WARPG = 3, K_VOLUME = 4 };
 
 constexpr int TW = 32;            // grid tile width  (pixels)
 constexpr int TH = 8;             // grid tile height (pixels)
@@ -99,6 +100,7 @@ struct GridProb {
 // Graph problem (ARAP mesh).
 struct MeshProb {
   int V, E, Vp, pad;
+  int gw, gh, gd, gpad;         // volumetric problems: voxel grid W x H x D (0 for graphs)
   int vchunk_begin, vchunk_end;
   int echunk_begin, echunk_end;
   float s_w, s_f, w_reg, w_fit;

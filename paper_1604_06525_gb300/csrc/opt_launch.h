@@ -24,6 +24,7 @@ struct MeshLaunch {
   int nvchunks, nechunks;
   cudaStream_t stream;
   int dim;       // 3: ARAP mesh (6 unknowns per vertex); 2: warp on a graph (3 unknowns)
+  int grid3;     // dim 3 on a W x H x D voxel grid: neighbours from the 7-point stencil, not the lists
 };
 
 // Launches kernel k with programmatic stream serialization (the kernel must
