@@ -283,6 +283,7 @@ opt_status refresh_descriptors(opt_batch* b, int lm, int use_precond, int outer)
       void* p = nullptr;
       BCK(cudaMalloc(&p, sizeof(double) * (outer + 1)));
       pb->allocs.push_back(p);
+      pb->pooled.push_back(false);
       e = static_cast<double*>(p);
       pb->d_Ehist = e;
       pb->Ehist_cap = outer + 1;

@@ -162,6 +162,7 @@ bool upload_vec(opt_problem* pb, T** dst, const std::vector<T>& v) {
   const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
   if (cudaMalloc(&ptr, bytes) != cudaSuccess) return false;
   pb->allocs.push_back(ptr);
+  pb->pooled.push_back(false);
   if (!v.empty() && cudaMemcpy(ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
     return false;
   *dst = static_cast<T*>(ptr);

@@ -90,7 +90,7 @@ struct opt_problem {
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     for (size_t k = 0; k < allocs.size(); ++k) {
-      if (pooled[k]) cudaFreeAsync(allocs[k], nullptr);
+      if (k < pooled.size() && pooled[k]) cudaFreeAsync(allocs[k], nullptr);
       else cudaFree(allocs[k]);
     }
   }
