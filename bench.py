@@ -531,11 +531,17 @@ def run_ours(args):
             "pcg_iters_per_s": OUTER * INNER / (ms_mat / 1e3), "ms_per_solve": ms_mat,
             "matrix_free_speedup": ms_mat / ms_per_step, "E_final": rr_mat[-1]["E_final"],
             "E_final_matrix_free": E_final}
+        rr_jtj = timed(gp, x0, gp.solve_gn, materialized=2)
+        ms_jtj = statistics.median(r_["ms"] for r_ in rr_jtj)
+        extra["warp_1024x1024_assembled_jtj_gn20x20"] = {
+            "pcg_iters_per_s": OUTER * INNER / (ms_jtj / 1e3), "ms_per_solve": ms_jtj,
+            "matrix_free_speedup": ms_jtj / ms_per_step, "E_final": rr_jtj[-1]["E_final"]}
         pp = synth.poisson_problem(W_BENCH, H_BENCH, seed=synth.BASE_SEED)
         gpp = api.Problem(pp)
         xp0 = gpp.x.clone()
         rr = timed(gpp, xp0, gpp.solve_gn)
         rrm = timed(gpp, xp0, gpp.solve_gn, materialized=1)
+        rra = timed(gpp, xp0, gpp.solve_gn, materialized=2)
         msp = statistics.median(r_["ms"] for r_ in rr)
         mspm = statistics.median(r_["ms"] for r_ in rrm)
         extra["poisson_1024x1024x4_gn20x20"] = {"pcg_iters_per_s": OUTER * INNER / (msp / 1e3), "ms_per_solve": msp,
@@ -543,6 +549,10 @@ def run_ours(args):
         extra["poisson_1024x1024x4_materialized_gn20x20"] = {
             "pcg_iters_per_s": OUTER * INNER / (mspm / 1e3), "ms_per_solve": mspm,
             "matrix_free_speedup": mspm / msp, "E_final": rrm[-1]["E_final"]}
+        mspa = statistics.median(r_["ms"] for r_ in rra)
+        extra["poisson_1024x1024x4_assembled_jtj_gn20x20"] = {
+            "pcg_iters_per_s": OUTER * INNER / (mspa / 1e3), "ms_per_solve": mspa,
+            "matrix_free_speedup": mspa / msp, "E_final": rra[-1]["E_final"]}
         gpp.close()
         mp = synth.mesh_problem(7, seed=synth.BASE_SEED)
         gmp = api.Problem(mp)

@@ -148,7 +148,10 @@ typedef struct {
     double eta;               /* LM acceptance threshold on the gain ratio (default 1e-3) */
     double rel_tol;           /* LM: stop after an accepted step with |dE|/E < rel_tol (0 = off) */
     int32_t use_precond;      /* 1 = Jacobi preconditioner (default), 0 = plain CG */
-    int32_t materialized;     /* 1 = materialized CSR J, q = J^T (J p) (Sec. 7) */
+    int32_t materialized;     /* 0 = matrix-free (default); 1 = materialized CSR J, q = J^T (J p)
+                                 (Sec. 7); 2 = J^T J assembled once per outer iteration, q = A p
+                                 (the paper's materialized form, Fig. 16).  Grid warp, Poisson,
+                                 mesh and volume problems. */
     int32_t use_graph;        /* 1 = replay the solve as one CUDA graph (default) */
     int32_t tile_w;           /* grid planning only: tile width 32 or 128, 0 = automatic
                                  (128 for grids at least 256 pixels wide, else 32) */

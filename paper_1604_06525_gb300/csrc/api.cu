@@ -377,7 +377,7 @@ opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cu
   if (coop) CK(cudaMemsetAsync(pb->d_gbar, 0, sizeof(GridBarrier), st));
   for (int k = 0; k < p.outer; ++k) {
     st_init(pb, st, k, dmin, dmax);
-    if (p.materialized) csr_evalj(pb, st);
+    if (p.materialized) csr_evalj(pb, st, p.materialized);
     if (coop) {
       // the barrier's counter restarts at 0 (a timed-out launch may leave it
       // mid-count); its timeout flag accumulates over the solve
@@ -385,7 +385,7 @@ opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cu
       CK(launch_grid_pcg_coop(grid_launch(pb, st), pb->d_gbar, 0, p.inner));
     } else {
       for (int i = 0; i < p.inner; ++i) {
-        if (p.materialized) csr_apply(pb, st, i);
+        if (p.materialized) csr_apply(pb, st, i, p.materialized);
         else st_apply(pb, st, nullptr, i, 1);
         st_update(pb, st, i);
       }
@@ -429,9 +429,9 @@ opt_status run_solve(opt_problem* pb, const opt_solve_params* prm_in, opt_report
   if (prm_in) p = *prm_in;
   else opt_solve_params_default(&p);
   CKS(check_params(p, lm));
-  if (p.materialized != 0 && p.materialized != 1) return OPT_ERR_INVALID_ARG;
+  if (p.materialized < 0 || p.materialized > 2) return OPT_ERR_INVALID_ARG;
   if (p.materialized && pb->kind == K_WARPG) return OPT_ERR_INVALID_ARG;   // no materialized form
-  if (p.materialized) CKS(csr_build(pb));
+  if (p.materialized) CKS(csr_build(pb, p.materialized));
   cudaStream_t st = (cudaStream_t)p.stream;
   CK(cudaStreamSynchronize(st));
   CKS(ensure_ehist(pb, p.outer + 1));

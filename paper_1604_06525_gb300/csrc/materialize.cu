@@ -146,6 +146,75 @@ __global__ void __launch_bounds__(NT) k_csr_jtt(int nT, const int* __restrict__ 
   }
 }
 
+// A = J^T J, one thread per row u (a non-empty unknown): for every residual
+// row r with an entry J[r,u] (the J^T row of u), every entry J[r,v] of that
+// row adds J[r,u] J[r,v] to A[u,v] (v found in u's short sorted column
+// list).  The row is owned by one thread, so the sums need no atomics and
+// follow a fixed order.
+__global__ void __launch_bounds__(NT) k_jtj_assemble(int nT, const int* __restrict__ t_ptr,
+                                                     const int* __restrict__ t_row, const float* __restrict__ t_val,
+                                                     const int* __restrict__ rp, const int* __restrict__ col,
+                                                     const float* __restrict__ val, const int* __restrict__ a_ptr,
+                                                     const int* __restrict__ a_col, float* __restrict__ a_val,
+                                                     const Scalars* __restrict__ s) {
+  if (s->done) return;
+  for (int k = blockIdx.x * NT + threadIdx.x; k < nT; k += gridDim.x * NT) {
+    const int a0 = a_ptr[k], a1 = a_ptr[k + 1];
+    for (int n = a0; n < a1; ++n) a_val[n] = 0.f;
+    for (int e = t_ptr[k]; e < t_ptr[k + 1]; ++e) {
+      const int r = t_row[e];
+      const float ju = t_val[e];
+      for (int f = rp[r]; f < rp[r + 1]; ++f) {
+        const int v = col[f];
+        int lo = a0, hi = a1 - 1;
+        while (lo < hi) {                 // the row's columns are sorted
+          const int mid = (lo + hi) >> 1;
+          if (a_col[mid] < v) lo = mid + 1;
+          else hi = mid;
+        }
+        a_val[lo] += ju * val[f];
+      }
+    }
+  }
+}
+
+// q = A p (+ lambda D p) over the non-empty unknowns; float64 p.q -> alpha.
+__global__ void __launch_bounds__(NT) k_jtj_spmv(int nT, const int* __restrict__ t_unk, const int* __restrict__ a_ptr,
+                                                 const int* __restrict__ a_col, const float* __restrict__ a_val,
+                                                 const float* __restrict__ p, float* __restrict__ q,
+                                                 const float* __restrict__ dc, int lm, long long pl, CompMap cm,
+                                                 Scalars* __restrict__ s, double* __restrict__ part) {
+  if (s->done || !s->pcg_active) return;
+  const float lam = lm ? s->lambda_f : 0.f;
+  float acc = 0.f;
+  for (int k = blockIdx.x * NT + threadIdx.x; k < nT; k += gridDim.x * NT) {
+    const int u = t_unk[k];
+    float v = 0.f;
+    for (int n = a_ptr[k]; n < a_ptr[k + 1]; ++n) v += a_val[n] * p[a_col[n]];
+    const float pu = p[u];
+    if (lm) {
+      const int c = (int)(u / pl);
+      v += lam * dc[cm.mp[c] * pl + (u - c * pl)] * pu;
+    }
+    q[u] = v;
+    acc += pu * v;
+  }
+  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, gridDim.x)) {
+    double pq, unused;
+    gather_partials(part, 0, gridDim.x, &s->counter, pq, unused);
+    if (threadIdx.x == 0) {
+      s->pq = pq;
+      if (pq > 0.0 && isfinite(pq)) {
+        s->alpha_f = (float)(s->rz / pq);
+      } else {
+        s->alpha_f = 0.f;
+        s->pcg_active = 0;
+        if (!isfinite(pq)) s->nonfinite = 1;
+      }
+    }
+  }
+}
+
 int blocks_for(long long n, int cap) {
   return (int)std::max<long long>(1, std::min<long long>((n + NT - 1) / NT, cap));
 }
@@ -172,7 +241,7 @@ bool upload_vec(opt_problem* pb, T** dst, const std::vector<T>& v) {
 }  // namespace
 
 // Builds the CSR structure of J and J^T (host, once per problem).
-opt_status csr_build(opt_problem* pb) {
+static opt_status csr_build_j(opt_problem* pb) {
   CsrJ& J = pb->csr;
   if (J.rp) return OPT_OK;
   const long long pl = pb->plane;
@@ -269,11 +338,58 @@ opt_status csr_build(opt_problem* pb) {
   return OPT_OK;
 }
 
-// evalJ (once per outer iteration): values that depend on x, then J^T's copy.
-void csr_evalj(opt_problem* pb, cudaStream_t st) {
+// Pattern of A = J^T J (host, once, for mode 2): the columns of every row that
+// shares a residual with unknown t_unk[k], sorted and unique.
+static opt_status csr_build_a(opt_problem* pb) {
+  CsrJ& J = pb->csr;
+  if (J.a_ptr) return OPT_OK;
+  std::vector<int> rp((size_t)J.R + 1), col((size_t)J.nnz), t_ptr((size_t)J.nT + 1), t_row((size_t)J.nnz);
+  if (cudaMemcpy(rp.data(), J.rp, rp.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(col.data(), J.col, col.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(t_ptr.data(), J.t_ptr, t_ptr.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(t_row.data(), J.t_row, t_row.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return OPT_ERR_CUDA;
+  }
+  // pattern of A = J^T J: the columns of every row that shares a residual
+  // with unknown t_unk[k], sorted and unique
+  std::vector<int> a_ptr(1, 0), a_col, scratch;
+  a_col.reserve((size_t)J.nT * 16);
+  for (int k = 0; k < J.nT; ++k) {
+    scratch.clear();
+    for (int e = t_ptr[k]; e < t_ptr[(size_t)k + 1]; ++e) {
+      const int r = t_row[e];
+      for (int f = rp[r]; f < rp[(size_t)r + 1]; ++f) scratch.push_back(col[f]);
+    }
+    std::sort(scratch.begin(), scratch.end());
+    scratch.erase(std::unique(scratch.begin(), scratch.end()), scratch.end());
+    a_col.insert(a_col.end(), scratch.begin(), scratch.end());
+    a_ptr.push_back((int)a_col.size());
+  }
+  J.nnz_a = (long long)a_col.size();
+  std::vector<float> a_zero(a_col.size(), 0.f);
+  if (!upload_vec(pb, &J.a_ptr, a_ptr) || !upload_vec(pb, &J.a_col, a_col) || !upload_vec(pb, &J.a_val, a_zero))
+    return OPT_ERR_OOM;
+  return OPT_OK;
+}
+
+opt_status csr_build(opt_problem* pb, int mode) {
+  opt_status st = csr_build_j(pb);
+  if (st == OPT_OK && mode == 2) st = csr_build_a(pb);
+  return st;
+}
+
+// evalJ (once per outer iteration): values that depend on x, then J^T's copy
+// and, for the assembled form (mode 2), A = J^T J.
+void csr_evalj(opt_problem* pb, cudaStream_t st, int mode) {
   CsrJ& J = pb->csr;
   const int cap = pb->sms * 8;
-  if (pb->kind == K_POISSON) return;   // constant J
+  if (pb->kind == K_POISSON) {          // constant J (A is still rebuilt once per PCG solve, as in the paper)
+    if (mode == 2)
+      k_jtj_assemble<<<blocks_for(J.nT, cap), NT, 0, st>>>(J.nT, J.t_ptr, J.t_row, J.t_val, J.rp, J.col, J.val,
+                                                           J.a_ptr, J.a_col, J.a_val, pb->d_s);
+    return;
+  }
   if (pb->kind == K_WARP) {
     k_evalj_warp<<<blocks_for(J.ngroups, cap), NT, 0, st>>>(J.ngroups, J.col, J.val, pb->x, pb->hg.c, pb->plane,
                                                              pb->hg.s_w, pb->d_s);
@@ -282,10 +398,14 @@ void csr_evalj(opt_problem* pb, cudaStream_t st) {
                                                              pb->hm.U, pb->plane, pb->hm.s_w, pb->d_s);
   }
   k_gather_vals<<<blocks_for(J.nnz, cap), NT, 0, st>>>(J.nnz, J.t_perm, J.val, J.t_val, pb->d_s);
+  if (mode == 2)
+    k_jtj_assemble<<<blocks_for(J.nT, cap), NT, 0, st>>>(J.nT, J.t_ptr, J.t_row, J.t_val, J.rp, J.col, J.val,
+                                                         J.a_ptr, J.a_col, J.a_val, pb->d_s);
 }
 
-// One materialized applyJTJ: direction update, t = J p, q = J^T t (+ damping).
-void csr_apply(opt_problem* pb, cudaStream_t st, int par) {
+// One materialized applyJTJ: direction update, then t = J p, q = J^T t
+// (mode 1) or q = A p (mode 2), plus damping.
+void csr_apply(opt_problem* pb, cudaStream_t st, int par, int mode) {
   CsrJ& J = pb->csr;
   const int cap = pb->sms * 8;
   const CompMap cm = comp_map(pb->kind);
@@ -297,6 +417,11 @@ void csr_apply(opt_problem* pb, cudaStream_t st, int par) {
   const float* dc = graph ? pb->hm.dc : pb->hg.dc;
   const int lm = graph ? pb->hm.lm : pb->hg.lm;
   k_csr_direction<<<blocks_for(J.nT, cap), NT, 0, st>>>(J.nT, J.t_unk, pl, cm, m, pb->rvec, pin, pout, pb->d_s);
+  if (mode == 2) {
+    k_jtj_spmv<<<J.nblk_t, NT, 0, st>>>(J.nT, J.t_unk, J.a_ptr, J.a_col, J.a_val, pout, pb->qvec, dc, lm, pl, cm,
+                                        pb->d_s, J.part);
+    return;
+  }
   k_csr_jp<<<blocks_for(J.R, cap), NT, 0, st>>>(J.R, J.rp, J.col, J.val, pout, J.tvec, pb->d_s);
   k_csr_jtt<<<J.nblk_t, NT, 0, st>>>(J.nT, J.t_unk, J.t_ptr, J.t_row, J.t_val, J.tvec, pout, pb->qvec, dc, lm, pl,
                                      cm, pb->d_s, J.part);

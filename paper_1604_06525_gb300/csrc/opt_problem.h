@@ -28,6 +28,12 @@ struct CsrJ {
   float* tvec = nullptr;     // R: t = J p
   double* part = nullptr;    // reduction partials of the J^T pass
   int nblk_t = 0;            // blocks of the J^T pass
+  // assembled A = J^T J over the non-empty unknowns (materialized = 2): row k
+  // is unknown t_unk[k], columns in the internal unknown index space
+  int* a_ptr = nullptr;      // nT + 1
+  int* a_col = nullptr;      // nnz_a
+  float* a_val = nullptr;    // nnz_a, refreshed once per outer iteration
+  long long nnz_a = 0;
 };
 
 struct opt_problem {
@@ -109,7 +115,7 @@ opt_status copy_planes_in(const opt_problem* pb, float* internal, float* const* 
 opt_status copy_planes_out(const opt_problem* pb, float* const* user, const float* internal, int n,
                            cudaStream_t st);
 // materialize.cu
-opt_status csr_build(opt_problem* pb);
-void csr_evalj(opt_problem* pb, cudaStream_t st);
-void csr_apply(opt_problem* pb, cudaStream_t st, int par);
+opt_status csr_build(opt_problem* pb, int mode);   // mode 1: J and J^T; mode 2: also the pattern of J^T J
+void csr_evalj(opt_problem* pb, cudaStream_t st, int mode);
+void csr_apply(opt_problem* pb, cudaStream_t st, int par, int mode);
 }  // namespace optgb

@@ -388,10 +388,12 @@ def test_full_size_mesh_apply(api):
     assert rel(jtf.cpu().numpy(), J.T @ e.residuals(x)) <= TOL_PRODUCT
 
 
-@pytest.mark.parametrize("case", ["warp", "warp_masked", "poisson", "mesh"])
-def test_materialized_solve_matches_oracle_and_matrix_free(api, case):
-    """Materialized CSR J, q = J^T (J p) (Sec. 7), against the oracle and the
-    matrix-free path on the same problem."""
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("case", ["warp", "warp_masked", "poisson", "mesh", "volume"])
+def test_materialized_solve_matches_oracle_and_matrix_free(api, case, mode):
+    """Materialized forms (Sec. 7): CSR J with q = J^T (J p) (mode 1) and J^T J
+    assembled once per outer iteration with q = A p (mode 2, Fig. 16),
+    against the oracle and the matrix-free path on the same problem."""
     import torch
     if case == "warp":
         prob, lm, outer, inner = synth.warp_problem(70, 45, 6, seed=101), False, 4, 10
@@ -400,14 +402,16 @@ def test_materialized_solve_matches_oracle_and_matrix_free(api, case):
         lm, outer, inner = False, 3, 10
     elif case == "poisson":
         prob, lm, outer, inner = synth.poisson_problem(96, 80, seed=103), False, 3, 20
-    else:
+    elif case == "mesh":
         prob, lm, outer, inner = synth.mesh_problem(3, seed=104, handle_frac=0.02), True, 5, 15
+    else:
+        prob, lm, outer, inner = synth.volume_problem(7, 6, 8, 12, seed=105), True, 4, 15
     e = oracle.make_energy(prob)
     x0 = prob.x0.reshape(-1)
     ref = (oracle.levenberg_marquardt(e, x0, outer, inner) if lm else oracle.gauss_newton(e, x0, outer, inner))
     a, b = api.Problem(prob), api.Problem(prob)
     solve = (lambda g, **kw: g.solve_lm(outer, inner, **kw)) if lm else (lambda g, **kw: g.solve_gn(outer, inner, **kw))
-    rm = solve(a, materialized=1)
+    rm = solve(a, materialized=mode)
     rf = solve(b, materialized=0)
     assert rm["outer_done"] == rf["outer_done"] == (ref.outer_done if lm else outer)
     for x, y, z in zip(rm["E_history"], rf["E_history"], ref.E_history):
@@ -416,7 +420,7 @@ def test_materialized_solve_matches_oracle_and_matrix_free(api, case):
     assert rel(a.x.cpu().numpy(), b.x.cpu().numpy()) <= 1e-4
     # a second materialized solve from the same start replays the cached graph
     a.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
-    rm2 = solve(a, materialized=1)
+    rm2 = solve(a, materialized=mode)
     assert rm2["E_history"] == rm["E_history"] or all(relE(x, y) <= 1e-6 for x, y in zip(rm2["E_history"], rm["E_history"]))
 
 
