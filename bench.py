@@ -55,6 +55,12 @@ BYTES_APPLY_VOLUME = 224   # direction pass: read r 24, M^-1 16, p_old 24; write
 BYTES_UPDATE_VOLUME = 160  # as the mesh
 BYTES_INIT_VOLUME = 264    # vertex pass: read x 24, U 12; write records 80 (116); gather pass: read
 #                            records 80, degree 4; write r 24, M^-1 16, delta 24 (148)
+# float64 solver: algorithmic flops of applyJTJ per unit in the scatter form of
+# Fig. 10 / 11 (every residual's J p evaluated once; an FMA counts 2), the
+# numerators of the float64 arithmetic roofline
+FLOPS_APPLY_WARP_F64 = 119     # 4 residuals x (v 2, R'v 6, J p 6, J^T scatter 12) + p = z + beta p 9 + p.q 6
+FLOPS_APPLY_POISSON_F64 = 68   # 4 channels x 4 residuals x (J p 1, J^T scatter 2) + p update 12 + p.q 8
+FLOPS_APPLY_MESH_F64 = 594     # 6 edges x (v 3, dR/dA v 40, J p 21, J^T scatter 30) + p update 18 + p.q 12
 KERNEL_SOURCES = ("grid_kernels.cu", "opt_internal.cuh", "opt_launch.h")
 L2_FLUSH_BYTES = 512 << 20
 
@@ -294,6 +300,43 @@ def aggregate_replicas(dev_ms: float, pcg_done: int, world: int, device=None):
 def pct(v, q):
     v = sorted(v)
     return v[min(len(v) - 1, max(0, int(round(q / 100.0 * (len(v) - 1)))))]
+
+
+def bench_fp64(api, synth, torch, flush, ms_f32_warp):
+    """The full float64 solver (Sec. 7 "Numerical Precision", Fig. 14's float
+    vs double comparison) on the 1024^2 warp and Poisson (GN 20 x 20) and the
+    level-7 mesh (LM 15 x 30), with the applyJTJ kernel's float64 arithmetic
+    rate against the measured float64 FMA peak of the device."""
+    fma = max(api.fp64_fma_rate() for _ in range(3))
+    out = {"fp64_fma_peak_gflops": fma, "peak_source": "measured (opt_measure_fp64_fma_rate)"}
+    cases = [("warp_1024x1024_gn20x20", lambda: synth.warp_problem(W_BENCH, H_BENCH, HANDLES, seed=synth.BASE_SEED),
+              lambda g: g.solve_gn(OUTER, INNER), FLOPS_APPLY_WARP_F64),
+             ("poisson_1024x1024x4_gn20x20", lambda: synth.poisson_problem(W_BENCH, H_BENCH, seed=synth.BASE_SEED),
+              lambda g: g.solve_gn(OUTER, INNER), FLOPS_APPLY_POISSON_F64),
+             ("mesh_icosphere7_lm15x30", lambda: synth.mesh_problem(7, seed=synth.BASE_SEED),
+              lambda g: g.solve_lm(15, 30, lambda0=1e-3), FLOPS_APPLY_MESH_F64)]
+    for name, mk, solve, flops in cases:
+        prob = mk()
+        g = api.ProblemF64(prob)
+        x0 = g.x.clone()
+        rr = []
+        for _ in range(4):
+            flush.zero_()
+            g.x.copy_(x0)
+            rr.append(solve(g))
+        ms = statistics.median(r["ms"] for r in rr[1:])
+        k = g.profile_pcg(10)
+        units = prob.W * prob.H if prob.kind != "mesh" else prob.V
+        if prob.kind == "poisson":
+            units = int((prob.mask == 0).sum())
+        achieved = flops * units / (k[1] * 1e-3) * 1e-9
+        out[name] = {"ms_per_solve": ms, "pcg_iters_per_s": rr[-1]["pcg_done"] / (ms / 1e3),
+                     "E_final": rr[-1]["E_final"], "ms_init_apply_update": k,
+                     "apply_roofline": {"bound": "alu", "achieved": achieved, "peak": fma, "unit": "GFLOP/s",
+                                        "frac": achieved / fma, "flops_per_unit": flops}}
+        g.close()
+    out["warp_f64_over_f32_time"] = out["warp_1024x1024_gn20x20"]["ms_per_solve"] / ms_f32_warp
+    return out
 
 
 def bench_batched(api, synth, torch, flush, n=512, outer=10, inner=10):
@@ -596,6 +639,8 @@ def run_ours(args):
                                             "accepted": rr[-1]["accepted"], "E0": rr[-1]["E0"],
                                             "E_final": rr[-1]["E_final"]}
         gv.close()
+
+        extra["float64_variant"] = bench_fp64(api, synth, torch, flush, ms_per_step)
 
         extra["batched_512_warps_gn10x10"] = bench_batched(api, synth, torch, flush)
         extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch)

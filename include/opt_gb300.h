@@ -400,6 +400,83 @@ opt_status opt_warp_apply_jtj_noalloc(int32_t W, int32_t H, const float* x, cons
                                       float w_reg, float w_fit, const float* p, float* q, double* pq,
                                       void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Full float64 solver (Sec. 7 "Numerical Precision": the solver runs in
+ * single or double precision; Fig. 14 compares the two).  Same energies,
+ * conventions and algorithm as the float32 calls above (matrix-free GN / LM
+ * with Jacobi PCG, the whole solve one CUDA graph), with every quantity in
+ * float64: unknowns, constants, residuals, J^T J p, PCG vectors, dot
+ * products, energies.  Planes are dense: grid index y*W + x, graph index =
+ * vertex.  The grid energies are OPT_ARAP_WARP_2D and OPT_POISSON_2D, the
+ * graph energy is OPT_ARAP_MESH.  Not supported here: materialized forms
+ * (params.materialized must be 0), batches and the server.
+ * ------------------------------------------------------------------------- */
+typedef struct opt_problem_f64 opt_problem_f64;
+
+/* As opt_grid_desc with float64 planes, handle targets and weights. */
+typedef struct {
+    int32_t kind;                 /* OPT_ARAP_WARP_2D or OPT_POISSON_2D */
+    int32_t W, H;
+    double* unknowns[4];          /* device: warp dx, dy, theta; Poisson X (4 channels) */
+    const double* consts[4];      /* device: warp UrShape x, y; Poisson guidance T (4) */
+    const uint8_t* mask;          /* device W*H bytes or NULL (as opt_grid_desc) */
+    const int32_t* handle_idx;    /* device, warp only */
+    const double* handle_target;  /* device, 2 per handle, warp only */
+    int32_t n_handles;
+    double w_reg, w_fit;          /* warp only */
+} opt_grid_desc_f64;
+
+/* As opt_graph_desc (ARAP mesh, Fig. 25) with float64 planes. */
+typedef struct {
+    int32_t V, E;
+    const int32_t* v0;            /* device, E directed edges, 0 <= v < V, v0 != v1 */
+    const int32_t* v1;
+    double* unknowns[6];          /* device: dx, dy, dz, ax, ay, az (V each) */
+    const double* urshape[3];     /* device: rest positions x, y, z */
+    const int32_t* handle_idx;    /* device, distinct vertices */
+    const double* handle_target;  /* device, 3 per handle */
+    int32_t n_handles;
+    double w_reg, w_fit;
+} opt_graph_desc_f64;
+
+/* Planning: validates (OPT_ERR_INVALID_ARG on a bad kind, size, null plane,
+ * handle index out of range or repeated, edge out of range or a loop,
+ * non-finite constant or weight), copies the constants and allocates the
+ * float64 scratch (about 8 * (8 nx + 2) bytes per pixel / vertex).  params
+ * is unused (may be NULL).  *out stays NULL on error. */
+opt_status opt_problem_create_grid_f64(const opt_grid_desc_f64* desc, const opt_solve_params* params,
+                                       opt_problem_f64** out);
+opt_status opt_problem_create_graph_f64(const opt_graph_desc_f64* desc, const opt_solve_params* params,
+                                        opt_problem_f64** out);
+opt_status opt_problem_destroy_f64(opt_problem_f64* prob);
+
+/* GN / LM exactly as opt_solve_gn / opt_solve_lm (params->materialized must
+ * be 0; tile_w and persistent are ignored). */
+opt_status opt_solve_gn_f64(opt_problem_f64* prob, const opt_solve_params* params, opt_report* report);
+opt_status opt_solve_lm_f64(opt_problem_f64* prob, const opt_solve_params* params, opt_report* report);
+
+/* Hooks as opt_apply_jtj / opt_eval_jtf / opt_eval_energy, synchronous, on
+ * the legacy default stream.  p, q, jtf, diag: device, nx dense planes
+ * (diag: one entry per unknown). */
+opt_status opt_apply_jtj_f64(opt_problem_f64* prob, const double* p, double* q, double lambda, double* pq);
+opt_status opt_eval_jtf_f64(opt_problem_f64* prob, double* jtf, double* diag, double* energy);
+opt_status opt_eval_energy_f64(opt_problem_f64* prob, double* energy);
+
+/* Measurement hook as opt_profile_pcg: ms[0] PCGInit, ms[1] applyJTJ,
+ * ms[2] vector update (mean device ms per launch). */
+opt_status opt_profile_pcg_f64(opt_problem_f64* prob, int32_t n_iters, void* stream, float* ms);
+
+/* Number of unknowns, planes and plane length. */
+opt_status opt_problem_info_f64(const opt_problem_f64* prob, int64_t* n_unknowns, int32_t* n_planes,
+                                int64_t* plane_len);
+
+/* Measured float64 fused multiply-add throughput of the current device in
+ * GFLOP/s (2 flops per FMA): one launch of independent FMA chains on every
+ * SM, timed with CUDA events on `stream` (cudaStream_t, NULL = legacy
+ * default stream).  The denominator of the float64 kernels' arithmetic
+ * roofline.  Synchronises the stream. */
+opt_status opt_measure_fp64_fma_rate(void* stream, double* gflops);
+
 /* Self-test of the bounded grid-wide barrier used by the persistent PCG loop
  * (opt_solve_params.persistent).  Runs one cooperative launch of 2 blocks that
  * meet at the barrier `rounds` times while the barrier awaits 2 + extra

@@ -42,6 +42,20 @@ class VolumeDesc(ctypes.Structure):
                 ("n_handles", c_int32), ("w_reg", c_float), ("w_fit", c_float)]
 
 
+class GridDescF64(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("W", c_int32), ("H", c_int32),
+                ("unknowns", c_void_p * 4), ("consts", c_void_p * 4), ("mask", c_void_p),
+                ("handle_idx", c_void_p), ("handle_target", c_void_p), ("n_handles", c_int32),
+                ("w_reg", c_double), ("w_fit", c_double)]
+
+
+class GraphDescF64(ctypes.Structure):
+    _fields_ = [("V", c_int32), ("E", c_int32), ("v0", c_void_p), ("v1", c_void_p),
+                ("unknowns", c_void_p * 6), ("urshape", c_void_p * 3),
+                ("handle_idx", c_void_p), ("handle_target", c_void_p), ("n_handles", c_int32),
+                ("w_reg", c_double), ("w_fit", c_double)]
+
+
 class SolveParams(ctypes.Structure):
     _fields_ = [("outer", c_int32), ("inner", c_int32), ("lambda0", c_double),
                 ("lambda_min", c_double), ("lambda_max", c_double), ("diag_min", c_double),
@@ -92,6 +106,17 @@ _SIGNATURES = [
                                              c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p,
                                              c_void_p]),
     ("opt_selftest_grid_barrier", c_int32, [c_int32, c_int32, POINTER(c_int32)]),
+    ("opt_problem_create_grid_f64", c_int32, [POINTER(GridDescF64), POINTER(SolveParams), POINTER(c_void_p)]),
+    ("opt_problem_create_graph_f64", c_int32, [POINTER(GraphDescF64), POINTER(SolveParams), POINTER(c_void_p)]),
+    ("opt_problem_destroy_f64", c_int32, [c_void_p]),
+    ("opt_solve_gn_f64", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report)]),
+    ("opt_solve_lm_f64", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report)]),
+    ("opt_apply_jtj_f64", c_int32, [c_void_p, c_void_p, c_void_p, c_double, POINTER(c_double)]),
+    ("opt_eval_jtf_f64", c_int32, [c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
+    ("opt_eval_energy_f64", c_int32, [c_void_p, POINTER(c_double)]),
+    ("opt_profile_pcg_f64", c_int32, [c_void_p, c_int32, c_void_p, POINTER(c_float)]),
+    ("opt_problem_info_f64", c_int32, [c_void_p, POINTER(c_int64), POINTER(c_int32), POINTER(c_int64)]),
+    ("opt_measure_fp64_fma_rate", c_int32, [c_void_p, POINTER(c_double)]),
     ("opt_status_str", ctypes.c_char_p, [c_int32]),
     ("opt_last_error", ctypes.c_char_p, []),
 ]
@@ -358,6 +383,146 @@ class Problem:
         _check(self.lib.opt_pcg_get_state(self.h, _ptr(dl), _ptr(r), _ptr(p), ctypes.byref(it)),
                "opt_pcg_get_state")
         return dl, r, p, it.value
+
+
+def make_descriptor_f64(prob, device):
+    """float64 device tensors and the C descriptor of a synth warp / Poisson /
+    mesh instance.  Returns (descriptor, unknown tensor, tensors to keep alive)."""
+    import torch
+    dev = torch.device(device)
+
+    def f64(a):
+        return torch.as_tensor(np.ascontiguousarray(a, np.float64), device=dev)
+
+    def i32(a):
+        return torch.as_tensor(np.ascontiguousarray(a, np.int32), device=dev)
+
+    keep = []
+    if prob.kind in ("warp", "poisson"):
+        x = f64(prob.x0).reshape(-1, prob.H, prob.W).clone()
+        d = GridDescF64()
+        d.W, d.H = prob.W, prob.H
+        mask = None if prob.mask is None else torch.as_tensor(prob.mask, dtype=torch.uint8, device=dev)
+        if prob.kind == "warp":
+            d.kind = OPT_ARAP_WARP_2D
+            consts = f64(prob.urshape)
+            hidx = i32(prob.handle_idx)
+            htgt = f64(prob.handle_target.reshape(-1))
+            d.n_handles = int(prob.handle_idx.size)
+            d.handle_idx = _ptr(hidx) if d.n_handles else None
+            d.handle_target = _ptr(htgt) if d.n_handles else None
+            d.w_reg, d.w_fit = prob.w_reg, prob.w_fit
+            keep += [hidx, htgt]
+            nx, nc = 3, 2
+        else:
+            d.kind = OPT_POISSON_2D
+            consts = f64(prob.guide)
+            d.n_handles = 0
+            nx, nc = 4, 4
+        for c in range(nx):
+            d.unknowns[c] = _ptr(x[c])
+        for c in range(nc):
+            d.consts[c] = _ptr(consts[c])
+        d.mask = _ptr(mask) if mask is not None else None
+        keep += [consts, mask, x]
+        return d, x, keep
+    if prob.kind == "mesh":
+        x = f64(prob.x0).reshape(6, prob.V).clone()
+        U = f64(prob.urshape)
+        v0, v1 = i32(prob.v0), i32(prob.v1)
+        hidx = i32(prob.handle_idx)
+        htgt = f64(prob.handle_target.reshape(-1))
+        d = GraphDescF64()
+        d.V, d.E = prob.V, int(prob.v0.size)
+        d.v0, d.v1 = _ptr(v0), _ptr(v1)
+        for c in range(6):
+            d.unknowns[c] = _ptr(x[c])
+        for c in range(3):
+            d.urshape[c] = _ptr(U[c])
+        d.n_handles = int(prob.handle_idx.size)
+        d.handle_idx = _ptr(hidx) if d.n_handles else None
+        d.handle_target = _ptr(htgt) if d.n_handles else None
+        d.w_reg, d.w_fit = prob.w_reg, prob.w_fit
+        keep += [U, v0, v1, hidx, htgt, x]
+        return d, x, keep
+    raise ValueError(f"no float64 variant for {prob.kind}")
+
+
+class ProblemF64(Problem):
+    """The full float64 solver (opt_*_f64 in the C ABI) on a synth warp,
+    Poisson or mesh instance; the same methods as Problem, float64 tensors."""
+
+    def __init__(self, prob, device: str = "cuda"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.lib = load_library()
+        self.kind = prob.kind
+        self.device = torch.device(device)
+        h = c_void_p()
+        d, self.x, self._keep = make_descriptor_f64(prob, self.device)
+        if prob.kind in ("warp", "poisson"):
+            self.W, self.H = prob.W, prob.H
+            _check(self.lib.opt_problem_create_grid_f64(ctypes.byref(d), None, ctypes.byref(h)),
+                   "opt_problem_create_grid_f64")
+        else:
+            self.V = prob.V
+            _check(self.lib.opt_problem_create_graph_f64(ctypes.byref(d), None, ctypes.byref(h)),
+                   "opt_problem_create_graph_f64")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.opt_problem_destroy_f64(self.h)
+            self.h = c_void_p()
+
+    def solve_gn(self, outer: int, inner: int, **kw) -> dict:
+        return self._solve(self.lib.opt_solve_gn_f64, outer, inner, **kw)
+
+    def solve_lm(self, outer: int, inner: int, **kw) -> dict:
+        return self._solve(self.lib.opt_solve_lm_f64, outer, inner, **kw)
+
+    def apply_jtj(self, p, lam: float = 0.0):
+        import torch
+        p = torch.as_tensor(p, dtype=torch.float64, device=self.device).contiguous()
+        q = torch.empty_like(p)
+        pq = c_double()
+        _check(self.lib.opt_apply_jtj_f64(self.h, _ptr(p), _ptr(q), lam, ctypes.byref(pq)), "opt_apply_jtj_f64")
+        return q, pq.value
+
+    def eval_jtf(self):
+        import torch
+        jtf = torch.empty_like(self.x)
+        diag = torch.empty_like(self.x)
+        E = c_double()
+        _check(self.lib.opt_eval_jtf_f64(self.h, _ptr(jtf), _ptr(diag), ctypes.byref(E)), "opt_eval_jtf_f64")
+        return jtf, diag, E.value
+
+    def energy(self) -> float:
+        E = c_double()
+        _check(self.lib.opt_eval_energy_f64(self.h, ctypes.byref(E)), "opt_eval_energy_f64")
+        return E.value
+
+    def profile_pcg(self, n_iters: int) -> tuple:
+        import torch
+        ms = (c_float * 3)()
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        _check(self.lib.opt_profile_pcg_f64(self.h, n_iters, st, ms), "opt_profile_pcg_f64")
+        return ms[0], ms[1], ms[2]
+
+    def _unsupported(self, *a, **k):
+        raise NotImplementedError("not part of the float64 solver")
+
+    pcg_init = pcg_step = set_chunking = autotune = pcg_state = _unsupported
+
+
+def fp64_fma_rate() -> float:
+    """Measured float64 FMA throughput of the current device, GFLOP/s."""
+    import torch
+    g = c_double()
+    _check(load_library().opt_measure_fp64_fma_rate(torch.cuda.current_stream().cuda_stream, ctypes.byref(g)),
+           "opt_measure_fp64_fma_rate")
+    return g.value
 
 
 class Batch:

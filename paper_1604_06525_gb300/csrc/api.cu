@@ -28,14 +28,17 @@
 using namespace optgb;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
 
-opt_status cuda_fail(cudaError_t e, const char* what) {
+// Records the failed call for opt_last_error and clears the sticky error.
+opt_status optgb::cuda_fail(cudaError_t e, const char* what) {
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
   (void)cudaGetLastError();
   return e == cudaErrorMemoryAllocation ? OPT_ERR_OOM : OPT_ERR_CUDA;
 }
+
+namespace {
 
 #define CK(call)                                         \
   do {                                                   \
@@ -51,13 +54,7 @@ opt_status cuda_fail(cudaError_t e, const char* what) {
 
 __global__ void k_reset(Scalars* s, int n, double lambda0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  Scalars z;
-  memset(&z, 0, sizeof(z));
-  z.lambda = lambda0;
-  z.lambda_f = (float)lambda0;
-  z.nu = 2.0;
-  s[i] = z;
+  if (i < n) scalars_reset(s + i, lambda0);
 }
 
 __global__ void k_force_active(Scalars* s, int n) {
@@ -70,36 +67,7 @@ __global__ void k_force_active(Scalars* s, int n) {
 // LM decision (Sec. 4; Nielsen's damping update), one thread per problem.
 __global__ void k_lm_decide(Scalars* s, int n, double eta, double lmin, double lmax, double rel_tol) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  Scalars* t = s + i;
-  if (t->done) {
-    t->accept = 0;
-    return;
-  }
-  const double E = t->E, Et = t->E_trial;
-  const double pred = E - t->model;
-  const double rho = pred > 0.0 ? (E - Et) / pred : -INFINITY;
-  double lam = t->lambda;
-  t->outer_done += 1;
-  if (rho > eta) {
-    const double u = 2.0 * rho - 1.0;
-    lam *= fmax(1.0 / 3.0, 1.0 - u * u * u);
-    t->nu = 2.0;
-    t->accept = 1;
-    t->accepted_total += 1;
-    if (rel_tol > 0.0 && (Et == 0.0 || fabs(E - Et) / E < rel_tol)) {
-      t->done = 1;
-      t->converged = 1;
-    }
-  } else {
-    lam *= t->nu;
-    t->nu *= 2.0;
-    t->accept = 0;
-  }
-  lam = fmin(fmax(lam, lmin), lmax);
-  t->lambda = lam;
-  t->lambda_f = (float)lam;
-  if (!isfinite(Et) && t->accept) t->nonfinite = 1;
+  if (i < n) lm_decide(s + i, eta, lmin, lmax, rel_tol);
 }
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }

@@ -67,48 +67,13 @@ __global__ void k_copy_planes(const PlaneCopy* __restrict__ tab, int n) {
 
 __global__ void k_reset_tab(Scalars* const* __restrict__ tab, int n, double lambda0) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  Scalars z;
-  memset(&z, 0, sizeof(z));
-  z.lambda = lambda0;
-  z.lambda_f = (float)lambda0;
-  z.nu = 2.0;
-  *tab[i] = z;
+  if (i < n) scalars_reset(tab[i], lambda0);
 }
 
 __global__ void k_lm_decide_tab(Scalars* const* __restrict__ tab, int n, double eta, double lmin, double lmax,
                                 double rel_tol) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  Scalars* t = tab[i];
-  if (t->done) {
-    t->accept = 0;
-    return;
-  }
-  const double E = t->E, Et = t->E_trial;
-  const double pred = E - t->model;
-  const double rho = pred > 0.0 ? (E - Et) / pred : -INFINITY;
-  double lam = t->lambda;
-  t->outer_done += 1;
-  if (rho > eta) {
-    const double u = 2.0 * rho - 1.0;
-    lam *= fmax(1.0 / 3.0, 1.0 - u * u * u);
-    t->nu = 2.0;
-    t->accept = 1;
-    t->accepted_total += 1;
-    if (rel_tol > 0.0 && (Et == 0.0 || fabs(E - Et) / E < rel_tol)) {
-      t->done = 1;
-      t->converged = 1;
-    }
-  } else {
-    lam *= t->nu;
-    t->nu *= 2.0;
-    t->accept = 0;
-  }
-  lam = fmin(fmax(lam, lmin), lmax);
-  t->lambda = lam;
-  t->lambda_f = (float)lam;
-  if (!isfinite(Et) && t->accept) t->nonfinite = 1;
+  if (i < n) lm_decide(tab[i], eta, lmin, lmax, rel_tol);
 }
 
 // Copies every member's scalars and energy history into contiguous buffers.

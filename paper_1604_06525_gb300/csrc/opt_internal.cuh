@@ -65,6 +65,8 @@ struct __align__(16) Scalars {
   int nonfinite;      // a non-finite scalar was produced
   unsigned int counter;   // last-block counter
   unsigned int pad1[3];
+  double alpha_d;     // float64 solver: alpha = rz / pq
+  double beta_d;      // float64 solver: beta  = rz' / rz
 };
 
 struct Chunk {
@@ -294,6 +296,54 @@ __device__ __forceinline__ void gather_partials(const double* part, int cb, int 
 
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
 
+// Fresh scalars for a solve: zero iterates and counters, LM damping lambda0,
+// growth factor 2.
+__device__ __forceinline__ void scalars_reset(Scalars* s, double lambda0) {
+  Scalars z;
+  memset(&z, 0, sizeof(z));
+  z.lambda = lambda0;
+  z.lambda_f = (float)lambda0;
+  z.nu = 2.0;
+  *s = z;
+}
+
+// LM decision after the trial energy (Sec. 4 LM; Nielsen's damping update,
+// Madsen, Nielsen & Tingleff 2004, Sec. 3.2): gain ratio rho = (E - E') /
+// (E - |F + J d|^2); accept if rho > eta with lambda *= max(1/3, 1 - (2 rho -
+// 1)^3) and nu = 2, else lambda *= nu and nu *= 2; lambda clamped to
+// [lmin, lmax].  An accepted step whose relative energy change is below
+// rel_tol (> 0) ends the solve.  Every decision counts as an outer iteration.
+__device__ __forceinline__ void lm_decide(Scalars* t, double eta, double lmin, double lmax, double rel_tol) {
+  if (t->done) {
+    t->accept = 0;
+    return;
+  }
+  const double E = t->E, Et = t->E_trial;
+  const double pred = E - t->model;
+  const double rho = pred > 0.0 ? (E - Et) / pred : -INFINITY;
+  double lam = t->lambda;
+  t->outer_done += 1;
+  if (rho > eta) {
+    const double u = 2.0 * rho - 1.0;
+    lam *= fmax(1.0 / 3.0, 1.0 - u * u * u);
+    t->nu = 2.0;
+    t->accept = 1;
+    t->accepted_total += 1;
+    if (rel_tol > 0.0 && (Et == 0.0 || fabs(E - Et) / E < rel_tol)) {
+      t->done = 1;
+      t->converged = 1;
+    }
+  } else {
+    lam *= t->nu;
+    t->nu *= 2.0;
+    t->accept = 0;
+  }
+  lam = fmin(fmax(lam, lmin), lmax);
+  t->lambda = lam;
+  t->lambda_f = (float)lam;
+  if (!isfinite(Et) && t->accept) t->nonfinite = 1;
+}
+
 // Inverse Jacobi preconditioner entry for diagonal `dg` with LM damping
 // lambda * clamp(dg): 1 / (dg + lambda * Dc); rows with a zero diagonal get 1.
 __device__ __forceinline__ float minv_entry(float dg, float lam, float dmin, float dmax,
@@ -309,11 +359,13 @@ __device__ __forceinline__ float minv_entry(float dg, float lam, float dmin, flo
 // ARAP mesh rotation (Fig. 25 Rotate3D, read as Rz(az) Ry(ay) Rx(ax))
 // ---------------------------------------------------------------------------
 // Rotation R = Rz(c) Ry(b) Rx(a) applied to v, and its three angle
-// derivatives applied to v.
-struct RotV {
-  float rv[3];
-  float g[3][3];    // g[m] = dR/dA_m v
+// derivatives applied to v (float32 kernels: RotV; float64 solver: RotVT<double>).
+template <typename T>
+struct RotVT {
+  T rv[3];
+  T g[3][3];        // g[m] = dR/dA_m v
 };
+using RotV = RotVT<float>;
 
 __device__ __forceinline__ RotV rot_apply(float ax, float ay, float az, float vx, float vy, float vz) {
   float sa, ca, sb, cb, sc, cc;
@@ -348,14 +400,14 @@ __device__ __forceinline__ RotV rot_apply(float ax, float ay, float az, float vx
 }
 
 // Same as rot_apply with the angles' cos / sin given.
-__device__ __forceinline__ RotV rot_apply_cs(float ca, float sa, float cb, float sb, float cc, float sc, float vx,
-                                             float vy, float vz) {
-  const float w0 = vx, w1 = ca * vy - sa * vz, w2 = sa * vy + ca * vz;
-  const float wd1 = -sa * vy - ca * vz, wd2 = ca * vy - sa * vz;
-  const float y0 = cb * w0 + sb * w2, y1 = w1, y2 = -sb * w0 + cb * w2;
-  const float yb0 = -sb * w0 + cb * w2, yb2 = -cb * w0 - sb * w2;
-  const float ya0 = sb * wd2, ya1 = wd1, ya2 = cb * wd2;
-  RotV o;
+template <typename T>
+__device__ __forceinline__ RotVT<T> rot_apply_cs(T ca, T sa, T cb, T sb, T cc, T sc, T vx, T vy, T vz) {
+  const T w0 = vx, w1 = ca * vy - sa * vz, w2 = sa * vy + ca * vz;
+  const T wd1 = -sa * vy - ca * vz, wd2 = ca * vy - sa * vz;
+  const T y0 = cb * w0 + sb * w2, y1 = w1, y2 = -sb * w0 + cb * w2;
+  const T yb0 = -sb * w0 + cb * w2, yb2 = -cb * w0 - sb * w2;
+  const T ya0 = sb * wd2, ya1 = wd1, ya2 = cb * wd2;
+  RotVT<T> o;
   o.rv[0] = cc * y0 - sc * y1;
   o.rv[1] = sc * y0 + cc * y1;
   o.rv[2] = y2;
@@ -367,7 +419,7 @@ __device__ __forceinline__ RotV rot_apply_cs(float ca, float sa, float cb, float
   o.g[1][2] = yb2;
   o.g[2][0] = -sc * y0 - cc * y1;
   o.g[2][1] = cc * y0 - sc * y1;
-  o.g[2][2] = 0.f;
+  o.g[2][2] = T(0);
   return o;
 }
 

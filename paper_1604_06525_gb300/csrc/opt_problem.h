@@ -105,6 +105,8 @@ struct opt_problem {
 struct opt_batch;
 
 namespace optgb {
+// api.cu: records a failed CUDA call for opt_last_error (OOM or CUDA status)
+opt_status cuda_fail(cudaError_t e, const char* what);
 // batch.cu (serving engine interface)
 opt_status batch_prepare_round(opt_batch* b, const opt_solve_params& p);
 void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_t st);

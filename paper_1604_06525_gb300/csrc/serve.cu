@@ -49,14 +49,7 @@ struct ServeReq {
   int state = 0;   // 0 queued, 1 active, 2 finished
 };
 
-__global__ void k_serve_reset(Scalars* s, double lambda0) {
-  Scalars z;
-  memset(&z, 0, sizeof(z));
-  z.lambda = lambda0;
-  z.lambda_f = (float)lambda0;
-  z.nu = 2.0;
-  *s = z;
-}
+__global__ void k_serve_reset(Scalars* s, double lambda0) { scalars_reset(s, lambda0); }
 
 size_t round32(size_t v) { return (v + 31) / 32 * 32; }
 
