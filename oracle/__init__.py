@@ -11,7 +11,9 @@ Contents
 energies.py   residual vectors F(x) and explicitly assembled sparse Jacobians
               J(x) for the three energy templates of the paper
               (ARAP image warping, Fig. 24; ARAP mesh deformation, Fig. 25;
-              Poisson image editing, Fig. 27), in float64.
+              Poisson image editing, Fig. 27), the warp written on a graph
+              (Fig. 18), volumetric ARAP (Fig. 31) and embedded deformation
+              (Fig. 28), in float64.
 solver.py     textbook Jacobi-preconditioned CG, Gauss-Newton (Sec. 4) and
               Levenberg-Marquardt (Sec. 4, Nielsen's damping update), run step
               by step on the assembled J, in float64.

@@ -10,7 +10,8 @@ dense user buffers:
            Jacobian columns (they are not solved for);
 * mesh:    [dx, dy, dz, A_x, A_y, A_z] (each V);
 * warp on a graph: [dx, dy, theta] (each V);
-* volume:  [dx, dy, dz, A_x, A_y, A_z] (each W*H*D voxels, index (z*H + y)*W + x).
+* volume:  [dx, dy, dz, A_x, A_y, A_z] (each W*H*D voxels, index (z*H + y)*W + x);
+* embedded deformation: [dx, dy, dz, R00, R01, ..., R22] (each V; R row-major).
 
 Weights: the configured weights multiply the *squared* residual, so residuals
 carry their square roots (Fig. 3 caption: weights inside Energy() are square
@@ -408,7 +409,98 @@ class VolumeEnergy(_Energy):
         return _csr(rows, cols, vals, (self.R, self.N))
 
 
+class EmbeddedEnergy(_Energy):
+    """Embedded deformation, Fig. 28 (Appendix A.2.1): every vertex carries a
+    position and a full 3x3 matrix R (row-major, R[3r + c]) instead of Euler
+    angles; soft constraints keep R a rotation.
+
+    Unknowns: [dx, dy, dz, R00, R01, R02, R10, R11, R12, R20, R21, R22] (each
+    V); the position is UrShape + (dx, dy, dz).  Residuals:
+      * for every directed edge (a, b):
+            s_w * ((O_a - O_b) - R_a (U_a - U_b))
+        (Fig. 28 writes (O_b - O_a) - R_a (U_b - U_a), the negation of this
+        residual: the same energy);
+      * for every vertex, with the columns c_k = (R[k], R[3 + k], R[6 + k]):
+            s_r * (c0 . c1), s_r * (c0 . c2), s_r * (c1 . c2),
+            s_r * (c0 . c0 - 1), s_r * (c1 . c1 - 1), s_r * (c2 . c2 - 1);
+      * for every handle h:  s_f * (O_h - C_h), C_h = UrShape_h + target.
+    s_w = sqrt(w_reg), s_r = sqrt(w_rot), s_f = sqrt(w_fit).
+    """
+
+    PAIRS = ((0, 1), (0, 2), (1, 2), (0, 0), (1, 1), (2, 2))
+
+    def __init__(self, prob):
+        self.prob = prob
+        self.V = self.n = prob.V
+        self.N = 12 * self.V
+        self.s_w = math.sqrt(prob.w_reg)
+        self.s_r = math.sqrt(prob.w_rot)
+        self.s_f = math.sqrt(prob.w_fit)
+        self.U = prob.urshape.astype(np.float64)
+        self.a = prob.v0.astype(np.int64)
+        self.b = prob.v1.astype(np.int64)
+        self.h = prob.handle_idx.astype(np.int64)
+        self.C = self.U[:, self.h] + prob.handle_target.astype(np.float64).T
+        self.R = 3 * self.a.size + 6 * self.V + 3 * self.h.size
+
+    def split(self, x):
+        x = np.asarray(x, np.float64).reshape(12, self.V)
+        return x[0:3], x[3:12].reshape(3, 3, self.V)        # Rm[r, c, v] = R_v[3r + c]
+
+    def residuals(self, x):
+        d, Rm = self.split(x)
+        O = self.U + d
+        a, b = self.a, self.b
+        v = self.U[:, a] - self.U[:, b]                       # (3, E)
+        Rv = np.einsum('rce,ce->re', Rm[:, :, a], v)
+        reg = self.s_w * ((O[:, a] - O[:, b]) - Rv)
+        col = [Rm[:, k, :] for k in range(3)]                 # c_k as (3, V)
+        rot = [self.s_r * (np.sum(col[i] * col[j], axis=0) - (1.0 if i == j else 0.0)) for i, j in self.PAIRS]
+        fit = self.s_f * (O[:, self.h] - self.C)
+        return np.concatenate([reg.reshape(-1), np.concatenate(rot), fit.reshape(-1)])
+
+    def jacobian(self, x):
+        d, Rm = self.split(x)
+        V, a, b, h = self.V, self.a, self.b, self.h
+        m = a.size
+        sw, sr, sf = self.s_w, self.s_r, self.s_f
+        v = self.U[:, a] - self.U[:, b]
+        rows, cols, vals = [], [], []
+        # edge rows: d/dO_a = s_w I, d/dO_b = -s_w I, d/dR_a[3i + c] = -s_w v_c (row i only)
+        for i in range(3):
+            rr = i * m + np.arange(m)
+            rows += [rr, rr]
+            cols += [i * V + a, i * V + b]
+            vals += [np.full(m, sw), np.full(m, -sw)]
+            for c in range(3):
+                rows.append(rr)
+                cols.append((3 + 3 * i + c) * V + a)
+                vals.append(-sw * v[c])
+        # rotation rows: d(c_i . c_j)/d c_i = c_j and d/d c_j = c_i (2 c_i when i == j);
+        # column k entry r is the unknown R[3r + k]
+        base = 3 * m
+        vid = np.arange(V)
+        for t, (i, j) in enumerate(self.PAIRS):
+            rr = base + t * V + vid
+            for r in range(3):
+                if i == j:
+                    rows.append(rr)
+                    cols.append((3 + 3 * r + i) * V + vid)
+                    vals.append(2.0 * sr * Rm[r, i])
+                else:
+                    rows += [rr, rr]
+                    cols += [(3 + 3 * r + i) * V + vid, (3 + 3 * r + j) * V + vid]
+                    vals += [sr * Rm[r, j], sr * Rm[r, i]]
+        base += 6 * V
+        for i in range(3):
+            rows.append(base + i * h.size + np.arange(h.size))
+            cols.append(i * V + h)
+            vals.append(np.full(h.size, sf))
+        return _csr(rows, cols, vals, (self.R, self.N))
+
+
 def make_energy(prob):
     """Oracle energy object for a synth problem instance."""
     return {"warp": WarpEnergy, "poisson": PoissonEnergy, "mesh": MeshEnergy,
-            "warp_graph": WarpGraphEnergy, "volume": VolumeEnergy}[prob.kind](prob)
+            "warp_graph": WarpGraphEnergy, "volume": VolumeEnergy,
+            "embedded": EmbeddedEnergy}[prob.kind](prob)

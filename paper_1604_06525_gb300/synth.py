@@ -356,6 +356,55 @@ def directed_edges(faces: np.ndarray, n_vertices: int):
     return v0[order].astype(np.int32), v1[order].astype(np.int32)
 
 
+@dataclass
+class EmbeddedProblem:
+    """Embedded deformation instance (Fig. 28): a mesh whose vertices carry a
+    displacement and a full 3x3 matrix.
+
+    urshape: (3, V) float32 rest positions; v0, v1: (E,) int32 directed edges
+    sorted by (v0, v1).  x0 planes: 0..2 = displacement, 3..11 = the matrix
+    row-major (R00, R01, R02, R10, ..., R22); (12, V) float32, identity
+    matrices at the start.  handle_idx / handle_target as MeshProblem.
+    """
+    V: int
+    urshape: np.ndarray
+    v0: np.ndarray
+    v1: np.ndarray
+    x0: np.ndarray
+    handle_idx: np.ndarray
+    handle_target: np.ndarray
+    w_reg: float = 1.0
+    w_fit: float = 100.0
+    w_rot: float = 1.0
+    level: int = -1
+    seed: int = BASE_SEED
+    kind: str = field(default="embedded", init=False)
+
+    @property
+    def E(self) -> int:
+        return int(self.v0.shape[0])
+
+    @property
+    def n_unknowns(self) -> int:
+        return 12 * self.V
+
+
+def embedded_problem(level: int, seed: int = BASE_SEED, handle_frac: float = 0.01, max_off: float = 0.1,
+                     w_reg: float = 1.0, w_fit: float = 100.0, w_rot: float = 1.0,
+                     x0_noise: float = 0.0) -> EmbeddedProblem:
+    """Embedded deformation on a level-`level` icosphere: the handles of
+    mesh_problem(level, seed, handle_frac, max_off), displacement 0 and
+    identity matrices at the start (optionally perturbed by x0_noise)."""
+    m = mesh_problem(level, seed=seed, handle_frac=handle_frac, max_off=max_off, w_reg=w_reg, w_fit=w_fit)
+    x0 = np.zeros((12, m.V), np.float32)
+    x0[3] = x0[7] = x0[11] = 1.0
+    if x0_noise > 0:
+        rng = np.random.default_rng(seed + 7)
+        x0 += rng.uniform(-x0_noise, x0_noise, size=x0.shape).astype(np.float32)
+    return EmbeddedProblem(m.V, m.urshape, m.v0, m.v1, x0, m.handle_idx, m.handle_target, float(w_reg),
+                           float(w_fit), float(w_rot), level, seed)
+
+
 def mesh_problem(level: int, seed: int = BASE_SEED, handle_frac: float = 0.01,
                  max_off: float = 0.1, w_reg: float = 1.0, w_fit: float = 100.0,
                  x0_noise: float = 0.0) -> MeshProblem:

@@ -279,6 +279,81 @@ def test_volume_rigid_motion_has_zero_regularizer():
 # --------------------------------------------------------------------------
 # Jacobian: central finite differences; gradient = 2 J^T F
 # --------------------------------------------------------------------------
+# --------------------------------------------------------------------------
+# embedded deformation (Fig. 28)
+# --------------------------------------------------------------------------
+def embedded_from(U, v0, v1, x, handle_idx=(), handle_target=None, w_rot=1.0):
+    U = np.asarray(U, np.float32)
+    hidx = np.asarray(handle_idx, np.int32)
+    htgt = np.zeros((hidx.size, 3), np.float32) if handle_target is None else np.asarray(handle_target, np.float32)
+    return synth.EmbeddedProblem(U.shape[1], U, np.asarray(v0, np.int32), np.asarray(v1, np.int32),
+                                 np.asarray(x, np.float32), hidx, htgt, w_rot=w_rot)
+
+
+def test_golden_embedded_2v():
+    g = _golden("embedded_2v.json")
+    prob = embedded_from(g["urshape"], g["v0"], g["v1"], g["x"])
+    e = en.EmbeddedEnergy(prob)
+    jtf, diag, E = so.jtf_diag(e, np.array(g["x"], np.float64).reshape(-1))
+    assert E == pytest.approx(g["E"], abs=1e-12)
+    np.testing.assert_allclose(jtf, np.array(g["jtf"]).reshape(-1), atol=1e-12)
+    np.testing.assert_allclose(diag, np.array(g["diag"]).reshape(-1), atol=1e-12)
+
+
+def test_embedded_rest_state_and_fit_closed_form():
+    prob = synth.embedded_problem(1, seed=3)
+    e = en.EmbeddedEnergy(prob)
+    t = prob.handle_target.astype(np.float64)
+    assert e.energy(prob.x0.reshape(-1)) == pytest.approx(prob.w_fit * float((t * t).sum()), rel=1e-13)
+    prob.handle_target[:] = 0
+    jtf, _, E = so.jtf_diag(en.EmbeddedEnergy(prob), prob.x0.reshape(-1))
+    assert E == 0.0 and np.abs(jtf).max() == 0.0
+
+
+def test_embedded_rigid_motion_is_free_and_scaling_closed_form():
+    prob = synth.embedded_problem(2, seed=4, w_rot=2.5)
+    prob.handle_idx = prob.handle_idx[:0]
+    prob.handle_target = prob.handle_target[:0]
+    e = en.EmbeddedEnergy(prob)
+    U = prob.urshape.astype(np.float64)
+    Q = Rotation.from_euler("zyx", [0.7, -0.4, 1.9]).as_matrix()
+    O = Q @ U + np.array([[0.5], [1.0], [-2.0]])
+    x = np.concatenate([(O - U).reshape(-1), np.repeat(Q.reshape(-1), prob.V)])
+    assert e.energy(x) < 1e-20
+    # R = s I, O = U: edge residuals (1 - s)(U_a - U_b), three constraints s^2 - 1 per vertex
+    s_ = 1.3
+    x2 = np.concatenate([np.zeros(3 * prob.V), np.repeat((s_ * np.eye(3)).reshape(-1), prob.V)])
+    dU = U[:, prob.v0] - U[:, prob.v1]
+    ref = prob.w_reg * (1 - s_) ** 2 * float((dU * dU).sum()) + prob.w_rot * prob.V * 3 * (s_ * s_ - 1) ** 2
+    assert e.energy(x2) == pytest.approx(ref, rel=1e-12)
+
+
+def test_embedded_constraints_act_on_columns():
+    """The six constraints use the columns of R (Fig. 28 builds c0 from
+    R(0), R(3), R(6)).  For R = [[1,1,1],[0,1,0],[0,0,1]] the column dots are
+    (1, 1, 1) and the squared column norms (1, 2, 2): E = w_rot (3 + 0 + 1 + 1)
+    = 5 w_rot (the rows would give 6 w_rot)."""
+    R = np.array([[1.0, 1.0, 1.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    x = np.concatenate([np.zeros(3), R.reshape(-1)]).reshape(12, 1)
+    prob = embedded_from(np.zeros((3, 1)), [], [], x, w_rot=0.7)
+    assert en.EmbeddedEnergy(prob).energy(x.reshape(-1)) == pytest.approx(5 * 0.7, rel=1e-14)
+
+
+def test_embedded_with_rotation_matrices_equals_arap_mesh():
+    """With R_v the rotation Rz Ry Rx(A_v) the edge term is the ARAP mesh
+    residual and the column constraints vanish: the two energies agree."""
+    m = synth.mesh_problem(1, seed=9, handle_frac=0.2, x0_noise=0.4)
+    ed = synth.embedded_problem(1, seed=9, handle_frac=0.2)
+    x_mesh = m.x0.reshape(-1).astype(np.float64)
+    A = m.x0[3:6].astype(np.float64)
+    R, _ = en.euler_rotation(A.T)                            # (V, 3, 3)
+    x_ed = np.concatenate([m.x0[0:3].astype(np.float64).reshape(-1),
+                           np.transpose(R, (1, 2, 0)).reshape(-1)])
+    Em = en.MeshEnergy(m).energy(x_mesh)
+    Ee = en.EmbeddedEnergy(ed).energy(x_ed)
+    assert Ee == pytest.approx(Em, rel=1e-12)
+
+
 def random_warp_graph(seed=6):
     rng = np.random.default_rng(seed)
     V = 7
@@ -299,6 +374,7 @@ def random_warp_graph(seed=6):
     lambda: (synth.poisson_problem(6, 5, seed=2), None),
     lambda: (random_warp_graph(), None),
     lambda: (synth.volume_problem(3, 2, 3, 2, seed=4, x0_noise=0.3), None),
+    lambda: (synth.embedded_problem(0, seed=5, handle_frac=0.2, x0_noise=0.3), None),
 ])
 def test_jacobian_matches_central_differences(make):
     prob, _ = make()
@@ -332,10 +408,11 @@ def test_gradient_is_twice_jtf():
 # --------------------------------------------------------------------------
 # J^T J: symmetry, PSD, closed-form stencils, null space, diagonals
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("kind", ["warp", "mesh", "poisson"])
+@pytest.mark.parametrize("kind", ["warp", "mesh", "poisson", "embedded"])
 def test_jtj_symmetric_psd_and_matrix_free_equals_dense(kind):
     prob = {"warp": lambda: tiny_warp(5, 4, 3, seed=21),
             "mesh": lambda: tiny_mesh(seed=22),
+            "embedded": lambda: synth.embedded_problem(0, seed=24, handle_frac=0.2, x0_noise=0.3),
             "poisson": lambda: synth.poisson_problem(7, 6, seed=23)}[kind]()
     e = en.make_energy(prob)
     x = prob.x0.reshape(-1).astype(np.float64)
