@@ -55,6 +55,12 @@ BYTES_APPLY_VOLUME = 224   # direction pass: read r 24, M^-1 16, p_old 24; write
 BYTES_UPDATE_VOLUME = 160  # as the mesh
 BYTES_INIT_VOLUME = 264    # vertex pass: read x 24, U 12; write records 80 (116); gather pass: read
 #                            records 80, degree 4; write r 24, M^-1 16, delta 24 (148)
+# embedded deformation, per vertex (12 unknowns, 10 diagonal planes, 6 directed edges)
+BYTES_APPLY_ED = 380       # direction pass: read r 48, M^-1 40, p_old 48; write p 48, records 48 (232);
+#                            gather pass: read own records 48 + 16, matrix at x 36; write q 48 (148)
+BYTES_UPDATE_ED = 328      # read delta 48, p 48, r 48, q 48, M^-1 40; write delta 48, r 48
+BYTES_INIT_ED = 328        # vertex pass: read x 48, U 12; write records 64 (124); gather pass: read
+#                            own records 64, degree 4; write r 48, M^-1 40, delta 48 (204)
 # float64 solver: algorithmic flops of applyJTJ per unit in the scatter form of
 # Fig. 10 / 11 (every residual's J p evaluated once; an FMA counts 2), the
 # numerators of the float64 arithmetic roofline
@@ -245,7 +251,7 @@ def roofline_for(api, synth, torch, W, H, peak, iters=20):
 def roofline_beyond_l2(api, synth, torch, peak):
     """The added sizes well beyond L2 (where the HBM-fraction target is
     judged): ARAP warp 4096^2, Poisson 4096^2 x 4 (free pixels), icosphere
-    level 9 (vertices)."""
+    level 9 (vertices: ARAP mesh and embedded deformation), 128^3 voxels."""
     res = {}
     warp, _ = roofline_for(api, synth, torch, 4096, 4096, peak)
     res["warp_4096x4096"] = {"unit_of_work": "pixel", "units": 4096 * 4096, "kernels": warp}
@@ -269,6 +275,16 @@ def roofline_beyond_l2(api, synth, torch, peak):
                                         ("k_mesh_update", BYTES_UPDATE_MESH, 15 * 30)), mp.V, peak)}
     gp.close()
     del mp
+    torch.cuda.empty_cache()
+    ep = synth.embedded_problem(9, seed=synth.BASE_SEED)
+    gp = api.Problem(ep)
+    res["embedded_icosphere9"] = {
+        "unit_of_work": "vertex", "units": ep.V, "directed_edges": int(len(ep.v0)),
+        "kernels": kernel_roofline(gp, (("k_ed_init_v+pull", BYTES_INIT_ED, 15),
+                                        ("k_ed_apply_v+pull", BYTES_APPLY_ED, 15 * 30),
+                                        ("k_ed_update", BYTES_UPDATE_ED, 15 * 30)), ep.V, peak)}
+    gp.close()
+    del ep
     torch.cuda.empty_cache()
     vp = synth.volume_problem(128, 128, 128, 2048, seed=synth.BASE_SEED)
     gp = api.Problem(vp)
@@ -639,6 +655,23 @@ def run_ours(args):
                                             "accepted": rr[-1]["accepted"], "E0": rr[-1]["E0"],
                                             "E_final": rr[-1]["E_final"]}
         gv.close()
+
+        # embedded deformation (Fig. 28) at the size class of the paper's 12k-vertex example and at level 7
+        for lev in (5, 7):
+            ep = synth.embedded_problem(lev, seed=synth.BASE_SEED)
+            ge = api.Problem(ep)
+            xe0 = ge.x.clone()
+            rr = []
+            for _ in range(4):
+                flush.zero_()
+                ge.x.copy_(xe0)
+                rr.append(ge.solve_lm(15, 30, lambda0=1e-3))
+            mse = statistics.median(r_["ms"] for r_ in rr[1:])
+            extra[f"embedded_icosphere{lev}_lm15x30"] = {
+                "vertices": ep.V, "ms_per_solve": mse, "solves_per_s": 1e3 / mse,
+                "pcg_iters_per_s": rr[-1]["pcg_done"] / (mse / 1e3), "accepted": rr[-1]["accepted"],
+                "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
+            ge.close()
 
         extra["float64_variant"] = bench_fp64(api, synth, torch, flush, ms_per_step)
 

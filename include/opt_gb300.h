@@ -6,7 +6,9 @@
  * (Fig. 4 and Sec. 3 "API": compile, allocate and run are separate calls so
  * that set-up is amortised over many solves).  The energy templates are fixed
  * and hand-derived (no DSL): ARAP image warping (Fig. 24), Poisson image
- * editing (Fig. 27) and ARAP mesh deformation (Fig. 25).
+ * editing (Fig. 27), ARAP mesh deformation (Fig. 25), the warp on an
+ * explicit graph (Fig. 18), volumetric ARAP (Fig. 31) and embedded
+ * deformation (Fig. 28).
  *
  * Conventions for every call:
  *  - Pointers named "device" point to CUDA global memory on the current
@@ -55,7 +57,8 @@ typedef enum {
     OPT_POISSON_2D = 1,       /* Fig. 27: unknowns X (4 channels) per pixel */
     OPT_ARAP_MESH = 2,        /* Fig. 25: unknowns dx, dy, dz, ax, ay, az per vertex */
     OPT_ARAP_WARP_GRAPH = 3,  /* Fig. 24 on an explicit graph (Fig. 18): dx, dy, theta per vertex */
-    OPT_ARAP_VOLUME = 4       /* Fig. 31: dx, dy, dz, ax, ay, az per voxel of a 3-D grid */
+    OPT_ARAP_VOLUME = 4,      /* Fig. 31: dx, dy, dz, ax, ay, az per voxel of a 3-D grid */
+    OPT_EMBEDDED_DEFORMATION = 5  /* Fig. 28: dx, dy, dz and a 3x3 matrix per vertex */
 } opt_energy;
 
 typedef struct opt_problem opt_problem;
@@ -133,6 +136,31 @@ typedef struct {
     int32_t n_handles;
     float w_reg, w_fit;
 } opt_volume_desc;
+
+/* Embedded deformation (Fig. 28, Appendix A.2.1): per vertex a displacement
+ * and a full 3x3 matrix R instead of Euler angles, with soft constraints
+ * that keep R a rotation.
+ *   v0, v1       = E directed edges (device, any order; as opt_graph_desc).
+ *   unknowns[12] = dx, dy, dz (Offset - UrShape), then R row-major R00, R01,
+ *                  R02, R10, ..., R22, V floats each (device).  Identity
+ *                  matrices and zero displacement are the rest state.
+ *   urshape[3], handle_idx, handle_target: as opt_graph_desc.
+ *   Residuals: for every edge (a, b),
+ *     sqrt(w_reg) * ((O_a - O_b) - R_a (U_a - U_b));
+ *   for every vertex, with c_k = (R[k], R[3+k], R[6+k]) the columns of R,
+ *     sqrt(w_rot) * (c0.c1), (c0.c2), (c1.c2), (c0.c0 - 1), (c1.c1 - 1), (c2.c2 - 1);
+ *   for every handle, sqrt(w_fit) * (O_h - C_h), C_h = U_h + target. */
+typedef struct {
+    int32_t V, E;
+    const int32_t* v0;
+    const int32_t* v1;
+    float* unknowns[12];
+    const float* urshape[3];
+    const int32_t* handle_idx;
+    const float* handle_target;
+    int32_t n_handles;
+    float w_reg, w_fit, w_rot;
+} opt_embedded_desc;
 
 /* Solver parameters (Sec. 4, Sec. 7 "LM vs. GN", "Matrix-free vs.
  * Materialized").  opt_solve_params_default fills the values used by the
@@ -222,6 +250,15 @@ opt_status opt_problem_create_graph2d(const opt_graph_desc* desc, const opt_solv
  * materialized form. */
 opt_status opt_problem_create_volume(const opt_volume_desc* desc, const opt_solve_params* params,
                                      opt_problem** out);
+
+/* Plan an embedded deformation problem (OPT_EMBEDDED_DEFORMATION).  Same
+ * validation (plus a finite w_rot >= 0), ownership and vertex ordering as
+ * opt_problem_create_graph.  Solves as a graph problem, also in batches;
+ * there is no materialized form (params.materialized != 0 gives
+ * OPT_ERR_INVALID_ARG at solve time).  The paper solves this energy with
+ * LM: GN is not robust on it (Appendix A.2.1). */
+opt_status opt_problem_create_embedded(const opt_embedded_desc* desc, const opt_solve_params* params,
+                                       opt_problem** out);
 
 /* Frees everything the problem owns.  NULL is accepted. */
 opt_status opt_problem_destroy(opt_problem* prob);

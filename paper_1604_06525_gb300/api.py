@@ -20,6 +20,7 @@ OPT_OK = 0
 STATUS = {0: "OPT_OK", 1: "OPT_ERR_INVALID_ARG", 2: "OPT_ERR_OOM", 3: "OPT_ERR_CUDA",
           4: "OPT_ERR_NUMERIC", 5: "OPT_ERR_TIMEOUT", 6: "OPT_ERR_BUDGET", 7: "OPT_ERR_NOT_READY"}
 OPT_ARAP_WARP_2D, OPT_POISSON_2D, OPT_ARAP_MESH = 0, 1, 2
+OPT_ARAP_WARP_GRAPH, OPT_ARAP_VOLUME, OPT_EMBEDDED_DEFORMATION = 3, 4, 5
 
 
 class GridDesc(ctypes.Structure):
@@ -40,6 +41,13 @@ class VolumeDesc(ctypes.Structure):
     _fields_ = [("W", c_int32), ("H", c_int32), ("D", c_int32), ("unknowns", c_void_p * 6),
                 ("urshape", c_void_p * 3), ("handle_idx", c_void_p), ("handle_target", c_void_p),
                 ("n_handles", c_int32), ("w_reg", c_float), ("w_fit", c_float)]
+
+
+class EmbeddedDesc(ctypes.Structure):
+    _fields_ = [("V", c_int32), ("E", c_int32), ("v0", c_void_p), ("v1", c_void_p),
+                ("unknowns", c_void_p * 12), ("urshape", c_void_p * 3),
+                ("handle_idx", c_void_p), ("handle_target", c_void_p), ("n_handles", c_int32),
+                ("w_reg", c_float), ("w_fit", c_float), ("w_rot", c_float)]
 
 
 class GridDescF64(ctypes.Structure):
@@ -77,6 +85,7 @@ _SIGNATURES = [
     ("opt_problem_create_graph", c_int32, [POINTER(GraphDesc), POINTER(SolveParams), POINTER(c_void_p)]),
     ("opt_problem_create_graph2d", c_int32, [POINTER(GraphDesc), POINTER(SolveParams), POINTER(c_void_p)]),
     ("opt_problem_create_volume", c_int32, [POINTER(VolumeDesc), POINTER(SolveParams), POINTER(c_void_p)]),
+    ("opt_problem_create_embedded", c_int32, [POINTER(EmbeddedDesc), POINTER(SolveParams), POINTER(c_void_p)]),
     ("opt_problem_destroy", c_int32, [c_void_p]),
     ("opt_solve_gn", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report)]),
     ("opt_solve_lm", c_int32, [c_void_p, POINTER(SolveParams), POINTER(Report)]),
@@ -230,6 +239,25 @@ def make_descriptor(prob, device):
         d.w_reg, d.w_fit = prob.w_reg, prob.w_fit
         keep += [U, v0, v1, hidx, htgt, x]
         return d, x, keep
+    if prob.kind == "embedded":
+        x = f32(prob.x0).reshape(12, prob.V).clone()
+        U = f32(prob.urshape)
+        v0, v1 = i32(prob.v0), i32(prob.v1)
+        hidx = i32(prob.handle_idx)
+        htgt = f32(prob.handle_target.reshape(-1))
+        d = EmbeddedDesc()
+        d.V, d.E = prob.V, int(prob.v0.size)
+        d.v0, d.v1 = _ptr(v0), _ptr(v1)
+        for c in range(12):
+            d.unknowns[c] = _ptr(x[c])
+        for c in range(3):
+            d.urshape[c] = _ptr(U[c])
+        d.n_handles = int(prob.handle_idx.size)
+        d.handle_idx = _ptr(hidx) if d.n_handles else None
+        d.handle_target = _ptr(htgt) if d.n_handles else None
+        d.w_reg, d.w_fit, d.w_rot = prob.w_reg, prob.w_fit, prob.w_rot
+        keep += [U, v0, v1, hidx, htgt, x]
+        return d, x, keep
     if prob.kind == "volume":
         x = f32(prob.x0).reshape(6, prob.V).clone()
         U = f32(prob.urshape)
@@ -283,7 +311,8 @@ class Problem:
         else:
             self.V = prob.V
             create = {"mesh": self.lib.opt_problem_create_graph, "warp_graph": self.lib.opt_problem_create_graph2d,
-                      "volume": self.lib.opt_problem_create_volume}[prob.kind]
+                      "volume": self.lib.opt_problem_create_volume,
+                      "embedded": self.lib.opt_problem_create_embedded}[prob.kind]
             _check(create(ctypes.byref(d), None, ctypes.byref(h)), "opt_problem_create_graph")
         self.h = h
 

@@ -18,7 +18,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 BUILDDIR = os.path.join(ROOT, "_build")
 LIBNAME = "libopt_gb300.so"
 SOURCES = ["api.cu", "batch.cu", "grid_kernels.cu", "graph_kernels.cu", "graph2d_kernels.cu", "materialize.cu",
-           "noalloc.cu", "serve.cu", "fp64.cu"]
+           "noalloc.cu", "serve.cu", "fp64.cu",
+           "embedded_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

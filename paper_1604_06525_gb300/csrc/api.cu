@@ -271,7 +271,8 @@ GridLaunch grid_launch(const opt_problem* pb, cudaStream_t st) {
 }
 MeshLaunch mesh_launch(const opt_problem* pb, cudaStream_t st) {
   return MeshLaunch{pb->dm, pb->d_vchunks, pb->d_echunks, pb->d_part, pb->nvchunks,
-                    pb->nechunks, st, pb->kind == K_WARPG ? 2 : 3, pb->kind == K_VOLUME ? 1 : 0};
+                    pb->nechunks, st, pb->kind == K_WARPG ? 2 : (pb->kind == K_EMBED ? 12 : 3),
+                    pb->kind == K_VOLUME ? 1 : 0};
 }
 
 opt_status upload_desc(opt_problem* pb, cudaStream_t st) {
@@ -398,7 +399,7 @@ opt_status run_solve(opt_problem* pb, const opt_solve_params* prm_in, opt_report
   else opt_solve_params_default(&p);
   CKS(check_params(p, lm));
   if (p.materialized < 0 || p.materialized > 2) return OPT_ERR_INVALID_ARG;
-  if (p.materialized && pb->kind == K_WARPG) return OPT_ERR_INVALID_ARG;   // no materialized form
+  if (p.materialized && (pb->kind == K_WARPG || pb->kind == K_EMBED)) return OPT_ERR_INVALID_ARG;   // no CSR form
   if (p.materialized) CKS(csr_build(pb, p.materialized));
   cudaStream_t st = (cudaStream_t)p.stream;
   CK(cudaStreamSynchronize(st));
@@ -714,26 +715,38 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
 // grid3 (volumetric problems): the W x H x D voxel grid whose 7-point stencil
 // the host edge lists hold; vertices then keep the caller's order (already
 // local) and the gather kernels take neighbours from the stencil.
+// Embedded deformation: the 12 unknown planes and the constraint weight
+// (the rest of the problem is an opt_graph_desc).
+struct EmbedExtra {
+  float* unknowns[12];
+  float w_rot;
+};
+
 static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem** out,
                                     const std::vector<int>* host_e0 = nullptr,
-                                    const std::vector<int>* host_e1 = nullptr, const int* grid3 = nullptr) {
-  const int NXg = D == 3 ? 6 : 3, NMg = D == 3 ? 4 : 2, NGR = D == 3 ? 3 : 1, NVR = D == 3 ? 2 : 1;
+                                    const std::vector<int>* host_e1 = nullptr, const int* grid3 = nullptr,
+                                    const EmbedExtra* ed = nullptr) {
+  // unknown planes, distinct-diagonal planes, geometry and vector records per vertex
+  const int NXg = ed ? 12 : (D == 3 ? 6 : 3), NMg = ed ? 10 : (D == 3 ? 4 : 2);
+  const int NGR = ed ? 1 : (D == 3 ? 3 : 1), NVR = ed ? 3 : (D == 3 ? 2 : 1);
+  float* const* ux = ed ? ed->unknowns : d ? d->unknowns : nullptr;
   if (!out) return OPT_ERR_INVALID_ARG;
   *out = nullptr;
   if (!d) return OPT_ERR_INVALID_ARG;
   if (d->V < 1 || d->E < 0 || d->n_handles < 0) return OPT_ERR_INVALID_ARG;
   if (d->E > 0 && !host_e0 && (!d->v0 || !d->v1)) return OPT_ERR_INVALID_ARG;
   for (int c = 0; c < NXg; ++c)
-    if (!d->unknowns[c]) return OPT_ERR_INVALID_ARG;
+    if (!ux[c]) return OPT_ERR_INVALID_ARG;
   for (int c = 0; c < D; ++c)
     if (!d->urshape[c]) return OPT_ERR_INVALID_ARG;
+  if (ed && (!std::isfinite(ed->w_rot) || ed->w_rot < 0.f)) return OPT_ERR_INVALID_ARG;
   if (d->n_handles > 0 && (!d->handle_idx || !d->handle_target)) return OPT_ERR_INVALID_ARG;
   if (!std::isfinite(d->w_reg) || !std::isfinite(d->w_fit) || d->w_reg < 0.f || d->w_fit < 0.f)
     return OPT_ERR_INVALID_ARG;
 
   std::unique_ptr<opt_problem> pb(new opt_problem());
   opt_problem* q = pb.get();
-  q->kind = grid3 ? K_VOLUME : (D == 3 ? K_MESH : K_WARPG);
+  q->kind = ed ? K_EMBED : (grid3 ? K_VOLUME : (D == 3 ? K_MESH : K_WARPG));
   q->nx = NXg;
   q->nm = NMg;
   q->V = d->V;
@@ -894,7 +907,7 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   q->nechunks = (int)ech.size();
   CKS(dalloc(q, &q->d_part, 2 * std::max(vch.size(), ech.size())));
   CKS(dalloc(q, &q->dm, 1));
-  for (int k = 0; k < NXg; ++k) q->user_x[k] = d->unknowns[k];
+  for (int k = 0; k < NXg; ++k) q->user_x[k] = ux[k];
   q->h_e0 = e0;
   q->h_e1 = e1;
   q->h_hpix = hpix;
@@ -905,6 +918,7 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   g.echunk_begin = 0; g.echunk_end = q->nechunks;
   g.w_reg = d->w_reg; g.w_fit = d->w_fit;
   g.s_w = std::sqrt(d->w_reg); g.s_f = std::sqrt(d->w_fit);
+  g.w_rot = ed ? ed->w_rot : 0.f; g.s_r = std::sqrt(g.w_rot);
   g.use_precond = 1; g.lm = 0;
   g.x = q->x; g.U = U; g.degw = dgw; g.e0 = de0; g.e1 = de1;
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
@@ -928,6 +942,28 @@ opt_status opt_problem_create_graph(const opt_graph_desc* d, const opt_solve_par
 opt_status opt_problem_create_graph2d(const opt_graph_desc* d, const opt_solve_params* prm, opt_problem** out) {
   (void)prm;
   return create_graph_impl(d, 2, out);
+}
+
+opt_status opt_problem_create_embedded(const opt_embedded_desc* d, const opt_solve_params* prm, opt_problem** out) {
+  (void)prm;
+  if (!out) return OPT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d) return OPT_ERR_INVALID_ARG;
+  opt_graph_desc g = {};
+  g.V = d->V;
+  g.E = d->E;
+  g.v0 = d->v0;
+  g.v1 = d->v1;
+  for (int c = 0; c < 3; ++c) g.urshape[c] = d->urshape[c];
+  g.handle_idx = d->handle_idx;
+  g.handle_target = d->handle_target;
+  g.n_handles = d->n_handles;
+  g.w_reg = d->w_reg;
+  g.w_fit = d->w_fit;
+  EmbedExtra ex;
+  for (int c = 0; c < 12; ++c) ex.unknowns[c] = d->unknowns[c];
+  ex.w_rot = d->w_rot;
+  return create_graph_impl(&g, 3, out, nullptr, nullptr, nullptr, &ex);
 }
 
 opt_status opt_problem_create_volume(const opt_volume_desc* d, const opt_solve_params* prm, opt_problem** out) {
@@ -1056,7 +1092,7 @@ opt_status opt_pcg_step(opt_problem* prob, int32_t n_iters) {
 
 opt_status opt_pcg_get_state(opt_problem* prob, float* delta, float* r, float* p, int32_t* iters_done) {
   if (!prob) return OPT_ERR_INVALID_ARG;
-  float* planes[6];
+  float* planes[12];
   if (delta) {
     dense_planes(prob, delta, planes, prob->nx);
     CKS(copy_planes_out(prob, planes, prob->dvec, prob->nx, nullptr));
@@ -1087,7 +1123,7 @@ opt_status opt_apply_jtj(opt_problem* prob, const float* p, float* q, double lam
   if (!prob || !p || !q || !(lambda >= 0.0) || !std::isfinite(lambda)) return OPT_ERR_INVALID_ARG;
   CKS(hook_prepare(prob, lambda, false));
   CKS(hook_init(prob, lambda));
-  float* planes[6];
+  float* planes[12];
   dense_planes(prob, p, planes, prob->nx);
   CKS(copy_planes_in(prob, prob->d_tmp, planes, prob->nx, nullptr));
   k_force_active<<<1, 32>>>(prob->d_s, 1);
@@ -1107,7 +1143,7 @@ opt_status opt_eval_jtf(opt_problem* prob, float* jtf, float* diag, double* ener
   if (!prob) return OPT_ERR_INVALID_ARG;
   CKS(hook_prepare(prob, 0.0, true));
   CKS(hook_init(prob, 0.0));
-  float* planes[6];
+  float* planes[12];
   if (jtf) {
     dense_planes(prob, jtf, planes, prob->nx);
     CKS(copy_planes_out(prob, planes, prob->d_jtf, prob->nx, nullptr));

@@ -115,7 +115,7 @@ struct GridGroup {
 };
 
 struct MeshGroup {
-  int dim = 3;                         // 3: ARAP mesh, 2: warp on a graph
+  int dim = 3;                         // 3: ARAP mesh, 2: warp on a graph, 12: embedded deformation
   int grid3 = 0;                       // volumetric problems (7-point stencil)
   std::vector<int> members;
   MeshProb* d_probs = nullptr;
@@ -130,7 +130,8 @@ struct MeshGroup {
 struct opt_batch {
   std::vector<opt_problem*> probs;
   std::vector<GridGroup> grids;
-  MeshGroup graphs[3];               // [0]: ARAP meshes, [1]: warps on graphs, [2]: volumes
+  MeshGroup graphs[4];               // [0]: ARAP meshes, [1]: warps on graphs, [2]: volumes,
+                                     // [3]: embedded deformation
   int tiles_per_chunk = 0;          // 0 = per-problem default
   std::vector<void*> table_allocs;  // rebuilt with the chunking
   std::vector<void*> allocs;        // fixed for the batch's life
@@ -442,10 +443,12 @@ opt_status opt_batch_create(opt_problem* const* probs, int32_t n, opt_batch** ou
       }
   b->graphs[1].dim = 2;
   b->graphs[2].grid3 = 1;
+  b->graphs[3].dim = 12;
   for (int i = 0; i < n; ++i) {
     if (probs[i]->kind == K_MESH) b->graphs[0].members.push_back(i);
     if (probs[i]->kind == K_WARPG) b->graphs[1].members.push_back(i);
     if (probs[i]->kind == K_VOLUME) b->graphs[2].members.push_back(i);
+    if (probs[i]->kind == K_EMBED) b->graphs[3].members.push_back(i);
   }
   BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
   BCK(cudaEventCreate(&b->ev0));

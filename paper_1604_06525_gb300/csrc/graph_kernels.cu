@@ -585,6 +585,7 @@ __global__ void __launch_bounds__(NT) k_mesh_step(const MeshProb* __restrict__ p
 // ---------------------------------------------------------------------------
 void launch_mesh_init(const MeshLaunch& L, int k_outer, float dmin, float dmax) {
   if (L.dim == 2) return launch_wg_init(L, k_outer, dmin, dmax);
+  if (L.dim == 12) return launch_ed_init(L, k_outer, dmin, dmax);
   launch_pdl(k_mesh_init_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks);
   if (L.grid3)
     launch_pdl(k_mesh_init_pull<true>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, k_outer, dmin, dmax);
@@ -595,6 +596,7 @@ void launch_mesh_init(const MeshLaunch& L, int k_outer, float dmin, float dmax) 
 
 void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, int update) {
   if (L.dim == 2) return launch_wg_apply(L, p_override, par, update);
+  if (L.dim == 12) return launch_ed_apply(L, p_override, par, update);
   launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, p_override, par, update);
   if (L.grid3)
     launch_pdl(k_mesh_apply_pull<true>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
@@ -604,17 +606,20 @@ void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, in
 
 void launch_mesh_update(const MeshLaunch& L, int par) {
   if (L.dim == 2) return launch_wg_update(L, par);
+  if (L.dim == 12) return launch_ed_update(L, par);
   launch_pdl(k_mesh_update, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, par);
 }
 
 void launch_mesh_energy(const MeshLaunch& L, int mode, int hist_idx) {
   if (L.dim == 2) return launch_wg_energy(L, mode, hist_idx);
+  if (L.dim == 12) return launch_ed_energy(L, mode, hist_idx);
   launch_pdl(k_mesh_energy_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, mode);
   launch_pdl(k_mesh_energy_e, L.nechunks, NT, 0, L.stream, L.probs, L.echunks, L.part, mode, hist_idx);
 }
 
 void launch_mesh_step(const MeshLaunch& L, int cond) {
   if (L.dim == 2) return launch_wg_step(L, cond);
+  if (L.dim == 12) return launch_ed_step(L, cond);
   launch_pdl(k_mesh_step, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, cond);
 }
 

@@ -29,8 +29,9 @@
 
 namespace optgb {
 
-// K_WARPG: the warp on a graph; K_VOLUME: volumetric ARAP (the mesh energy on a voxel grid)
-enum Kind : int { K_WARP = 0, K_POISSON = 1, K_MESH = 2, K_WARPG = 3, K_VOLUME = 4 };
+// K_WARPG: the warp on a graph; K_VOLUME: volumetric ARAP (the mesh energy on a voxel grid);
+// K_EMBED: embedded deformation (12 unknowns per vertex)
+enum Kind : int { K_WARP = 0, K_POISSON = 1, K_MESH = 2, K_WARPG = 3, K_VOLUME = 4, K_EMBED = 5 };
 
 constexpr int TW = 32;            // grid tile width  (pixels)
 constexpr int TH = 8;             // grid tile height (pixels)
@@ -106,8 +107,9 @@ struct MeshProb {
   int vchunk_begin, vchunk_end;
   int echunk_begin, echunk_end;
   float s_w, s_f, w_reg, w_fit;
+  float s_r, w_rot;             // embedded deformation: column constraint weight
   int use_precond, lm;
-  float* x;                     // 6 planes: displacement, angles
+  float* x;                     // 6 planes: displacement, angles (embedded deformation: 12)
   const float* U;               // 3 planes
   const float* degw;            // w_reg * (outdeg + indeg) + w_fit[handle]
   const int* e0;                // edges sorted by (v0, v1)

@@ -23,7 +23,8 @@ struct MeshLaunch {
   double* part;
   int nvchunks, nechunks;
   cudaStream_t stream;
-  int dim;       // 3: ARAP mesh (6 unknowns per vertex); 2: warp on a graph (3 unknowns)
+  int dim;       // 3: ARAP mesh (6 unknowns per vertex); 2: warp on a graph (3 unknowns);
+                 // 12: embedded deformation (12 unknowns)
   int grid3;     // dim 3 on a W x H x D voxel grid: neighbours from the 7-point stencil, not the lists
 };
 
@@ -73,5 +74,12 @@ void launch_wg_apply(const MeshLaunch& L, const float* p_override, int par, int 
 void launch_wg_update(const MeshLaunch& L, int par);
 void launch_wg_energy(const MeshLaunch& L, int mode, int hist_idx);
 void launch_wg_step(const MeshLaunch& L, int cond);
+
+// embedded_kernels.cu (dim == 12; reached through the launch_mesh_* functions)
+void launch_ed_init(const MeshLaunch& L, int k_outer, float dmin, float dmax);
+void launch_ed_apply(const MeshLaunch& L, const float* p_override, int par, int update);
+void launch_ed_update(const MeshLaunch& L, int par);
+void launch_ed_energy(const MeshLaunch& L, int mode, int hist_idx);
+void launch_ed_step(const MeshLaunch& L, int cond);
 
 }  // namespace optgb

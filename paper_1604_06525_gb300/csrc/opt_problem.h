@@ -69,7 +69,7 @@ struct opt_problem {
   optgb::Scalars* d_s = nullptr;
   double* d_Ehist = nullptr;
   int Ehist_cap = 0;
-  float* user_x[6] = {};
+  float* user_x[12] = {};
   float* d_tmp = nullptr;     // nx planes: caller p (apply hook)
   float* d_jtf = nullptr;     // nx planes: J^T F (hook)
   float* d_diag = nullptr;    // nm planes: diag (hook)
