@@ -645,23 +645,29 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   int *dhbeg = nullptr, *dhpix = nullptr;
   float* dhtgt = nullptr;
   CKS(dalloc(q, &q->x, nx * pl));
-  CKS(dalloc(q, &c, nc * pl));
-  CKS(dalloc(q, &q->dvec, nx * pl));
-  CKS(dalloc(q, &q->rvec, nx * pl));
-  CKS(dalloc(q, &q->qvec, nx * pl));
-  CKS(dalloc(q, &q->pbuf, 2 * nx * pl));
-  CKS(dalloc(q, &m, nm * pl));
   CKS(dalloc(q, &dc, nm * pl));
-  float* csn = nullptr;
-  if (warp && tw == 128) {
-    CKS(dalloc(q, &csn, 2 * pl));
+  // one slab for every plane the PCG launches touch, in the order r, M^-1,
+  // p (two), q, delta, cos / sin, constants, mask (planes are multiples of
+  // 32 floats, so every plane stays 128-byte aligned)
+  const bool has_csn = warp && tw == 128;
+  const size_t nslab = (size_t)(nx + nm + 2 * nx + nx + nx + (has_csn ? 2 : 0) + nc) * pl + (d->mask ? pl / 4 : 0);
+  float* slab = nullptr;
+  CKS(dalloc(q, &slab, nslab));
+  float* cur = slab;
+  auto take = [&](size_t n) { float* r = cur; cur += n; return r; };
+  q->rvec = take(nx * pl);
+  m = take(nm * pl);
+  q->pbuf = take(2 * nx * pl);
+  q->qvec = take(nx * pl);
+  q->dvec = take(nx * pl);
+  float* csn = has_csn ? take(2 * pl) : nullptr;
+  c = take(nc * pl);
+  if (d->mask) dmask = reinterpret_cast<uint8_t*>(take(pl / 4));
+  if (has_csn) {
     CKS(dalloc(q, &q->d_gbar, 1));
     q->coop_cap = grid_coop_capacity(d->mask != nullptr);
   }
-  if (d->mask) {
-    CKS(dalloc(q, &dmask, pl));
-    CK(cudaMemcpy2D(dmask, P, d->mask, W, W, H, cudaMemcpyDeviceToDevice));
-  }
+  if (d->mask) CK(cudaMemcpy2D(dmask, P, d->mask, W, W, H, cudaMemcpyDeviceToDevice));
   for (int k = 0; k < nc; ++k)
     CK(cudaMemcpy2D(c + k * pl, (size_t)P * 4, d->consts[k], (size_t)W * 4, (size_t)W * 4, H,
                     cudaMemcpyDeviceToDevice));
