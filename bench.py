@@ -712,11 +712,18 @@ def run_ours(args):
 
 
 PROFILE_CASES = {
-    # name: (builder, description); small enough for ncu --set full (a few GB
-    # on the device at most) and larger than L2
-    "warp2048": (lambda synth: synth.warp_problem(2048, 2048, 256, seed=synth.BASE_SEED), "ARAP warp 2048^2"),
-    "poisson2048": (lambda synth: synth.poisson_problem(2048, 2048, seed=synth.BASE_SEED), "Poisson 2048^2 x 4"),
-    "mesh8": (lambda synth: synth.mesh_problem(8, seed=synth.BASE_SEED), "ARAP mesh, icosphere level 8"),
+    # name: (builder, description, float64 solver); small enough for ncu --set
+    # full (a few GB on the device at most) and larger than L2
+    "warp2048": (lambda synth: synth.warp_problem(2048, 2048, 256, seed=synth.BASE_SEED), "ARAP warp 2048^2", False),
+    "poisson2048": (lambda synth: synth.poisson_problem(2048, 2048, seed=synth.BASE_SEED), "Poisson 2048^2 x 4",
+                    False),
+    "mesh8": (lambda synth: synth.mesh_problem(8, seed=synth.BASE_SEED), "ARAP mesh, icosphere level 8", False),
+    "embedded8": (lambda synth: synth.embedded_problem(8, seed=synth.BASE_SEED),
+                  "embedded deformation, icosphere level 8", False),
+    "warp2048_f64": (lambda synth: synth.warp_problem(2048, 2048, 256, seed=synth.BASE_SEED),
+                     "ARAP warp 2048^2, float64 solver", True),
+    "mesh8_f64": (lambda synth: synth.mesh_problem(8, seed=synth.BASE_SEED),
+                  "ARAP mesh, icosphere level 8, float64 solver", True),
 }
 
 
@@ -727,9 +734,13 @@ def run_profile_case(name):
     from paper_1604_06525_gb300 import build, api, synth
     build.build()
     api.load_library()
-    builder, desc = PROFILE_CASES[name]
-    gp = api.Problem(builder(synth))
-    chunking, _ = gp.autotune()
+    builder, desc, f64 = PROFILE_CASES[name]
+    if f64:
+        gp = api.ProblemF64(builder(synth))
+        chunking = None
+    else:
+        gp = api.Problem(builder(synth))
+        chunking, _ = gp.autotune()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("profile")
     ms = gp.profile_pcg(3)

@@ -499,8 +499,9 @@ opt_status opt_apply_jtj_f64(opt_problem_f64* prob, const double* p, double* q, 
 opt_status opt_eval_jtf_f64(opt_problem_f64* prob, double* jtf, double* diag, double* energy);
 opt_status opt_eval_energy_f64(opt_problem_f64* prob, double* energy);
 
-/* Measurement hook as opt_profile_pcg: ms[0] PCGInit, ms[1] applyJTJ,
- * ms[2] vector update (mean device ms per launch). */
+/* Measurement hook as opt_profile_pcg: ms[0] PCGInit (with the cos / sin
+ * pass), ms[1] applyJTJ with the direction update (two launches from the
+ * second PCG iteration on), ms[2] vector update (mean device ms). */
 opt_status opt_profile_pcg_f64(opt_problem_f64* prob, int32_t n_iters, void* stream, float* ms);
 
 /* Number of unknowns, planes and plane length. */

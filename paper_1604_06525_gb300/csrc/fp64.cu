@@ -13,14 +13,20 @@
 // issues at a small fraction of the float32 rate, while a float64 operand is
 // only twice the bytes.  The float64 kernels are therefore bound by float64
 // arithmetic, not by memory, and are written for the fewest float64
-// operations rather than for the fewest bytes: one thread per pixel / vertex
-// (grid-stride over a fixed grid of blocks), operands straight from global
-// memory through L1 (no shared-memory staging: the bytes are not the limit),
-// cos / sin of the rotation angles computed once per outer iteration into
-// planes, the direction p = M^-1 r + beta p_old re-formed where a neighbour's
-// value is needed.  Reductions are float64 throughout: per thread, per block
-// (fixed shuffle tree), then across blocks in block order by the last block
-// to arrive, so results do not depend on scheduling.
+// operations rather than for the fewest bytes:
+//  * the Jacobian entries that depend on x and are not constants -- the angle
+//    columns (warp: R'(theta_i) v per residual; mesh: dR/dA_m (U_a - U_b) per
+//    directed edge) -- are evaluated once per outer iteration by PCGInit and
+//    read by every applyJTJ of the PCG solve (the rest of J is +-s_w);
+//  * the direction update p = M^-1 r + beta p is its own streaming pass, so
+//    applyJTJ reads p at the neighbours instead of re-forming it;
+//  * the own and the incoming residual of a stencil pair are folded into one
+//    expression (the same p differences feed both);
+//  * one thread per pixel / vertex (grid-stride over a fixed grid of blocks),
+//    operands straight from global memory through L1.
+// Reductions are float64 throughout: per thread, per block (fixed shuffle
+// tree), then across blocks in block order by the last block to arrive, so
+// results do not depend on scheduling.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,9 +61,13 @@ struct P64 {
   const int* oe1;
   const int* irow;              // graph: in-edges of v come from isrc[irow[v] .. irow[v+1])
   const int* isrc;
+  const int* ieid;              // graph: out-edge index (into oe1) of each in-edge
+  long long ne;                 // graph: directed edges
   double *d, *r, *q, *m, *dc;   // nx planes each
-  double* p[2];                 // direction, ping-pong between PCG iterations
+  double* p;                    // PCG direction (nx planes)
   double* cs;                   // cos / sin planes of the angles (warp 2, mesh 6)
+  double* G;                    // angle columns of J at x: warp 8 planes of n (R'(theta) v per
+                                // direction, x / y), mesh 9 planes of ne (dR/dA_m w, m-major)
   const double* pin;            // apply hook: caller direction (NULL in a solve)
   double* jtf_out;              // hook outputs (nx planes each) or NULL
   double* diag_out;
@@ -102,15 +112,6 @@ __device__ __forceinline__ double minv64(double dg, double lam, double dmin, dou
   return mm != 0.0 ? 1.0 / mm : 1.0;
 }
 
-// Direction component c at element j: the caller's p (apply hook) or
-// p = M^-1 r + beta p_old (the fused direction update).
-__device__ __forceinline__ double dir64(const P64& P, const double* __restrict__ po, double beta, int c,
-                                        long long j) {
-  const long long k = c * P.n + j;
-  if (P.pin) return P.pin[k];
-  return P.m[k] * P.r[k] + beta * po[k];
-}
-
 // Writes the PCGInit outputs of element i from its J^T F (g) and diag (dg).
 template <int NX>
 __device__ __forceinline__ double init_store(const P64& P, long long i, const double* g, const double* dg,
@@ -126,7 +127,7 @@ __device__ __forceinline__ double init_store(const P64& P, long long i, const do
     P.m[k] = mi;
     P.dc[k] = dcv;
     P.d[k] = 0.0;
-    P.p[0][k] = 0.0;
+    P.p[k] = mi * b;            // first direction p = z = M^-1 r
     rz += b * mi * b;
     if (P.jtf_out) P.jtf_out[k] = g[c];
     if (P.diag_out) P.diag_out[k] = dg[c];
@@ -214,14 +215,30 @@ __global__ void __launch_bounds__(NT) k64_rot(P64 P) {
   }
 }
 
+// Direction update (Sec. 4.1 PCGStep): p = z + beta p, z = M^-1 r (every
+// PCG iteration after the first; PCGInit writes the first direction).
+template <int NX>
+__global__ void __launch_bounds__(NT) k64_direction(P64 P) {
+  const Scalars* s = P.s;
+  if (s->done || !s->pcg_active) return;
+  const double beta = s->beta_d;
+  FOR_ELEMENTS(P, i) {
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+      const long long k = c * P.n + i;
+      P.p[k] = fma(beta, P.p[k], P.m[k] * P.r[k]);
+    }
+  }
+}
+
 // PCG vector update (Sec. 4.1 PCGStep): delta += alpha p, r -= alpha q,
 // z = M^-1 r, r.z -> beta = r.z / r.z_old.
 template <int NX>
-__global__ void __launch_bounds__(NT) k64_update(P64 P, int par) {
+__global__ void __launch_bounds__(NT) k64_update(P64 P) {
   Scalars* s = P.s;
   if (s->done || !s->pcg_active) return;
   const double alpha = s->alpha_d;
-  const double* __restrict__ pn = P.p[(par + 1) & 1];
+  const double* __restrict__ pn = P.p;
   double rz = 0.0;
   FOR_ELEMENTS(P, i) {
 #pragma unroll
@@ -275,6 +292,8 @@ __global__ void __launch_bounds__(NT) k64_warp_init(P64 P, int k_outer, double d
       const double ci = P.cs[i], si = P.cs[n + i];
       const double uxi = P.c[i], uyi = P.c[n + i];
       for (int k = 0; k < 4; ++k) {
+        P.G[(2 * k) * n + i] = 0.0;
+        P.G[(2 * k + 1) * n + i] = 0.0;
         const int nx_ = gx + ddx(k), ny_ = gy + ddy(k);
         if (nx_ < 0 || nx_ >= P.W || ny_ < 0 || ny_ >= P.H) continue;
         const long long j = (long long)ny_ * P.W + nx_;
@@ -285,6 +304,8 @@ __global__ void __launch_bounds__(NT) k64_warp_init(P64 P, int k_outer, double d
         const double fx = sw * ((xi - xj) + vx - (ci * vx - si * vy));
         const double fy = sw * ((yi - yj) + vy - (si * vx + ci * vy));
         const double rpx = -si * vx - ci * vy, rpy = ci * vx - si * vy;   // R'(theta_i) v
+        P.G[(2 * k) * n + i] = rpx;
+        P.G[(2 * k + 1) * n + i] = rpy;
         E += fx * fx + fy * fy;
         g[0] += sw * fx;
         g[1] += sw * fy;
@@ -317,54 +338,45 @@ __global__ void __launch_bounds__(NT) k64_warp_init(P64 P, int k_outer, double d
   init_finish(P, rz, E, k_outer);
 }
 
-// q = (J^T J + lambda D) p, p formed on the fly (direction update fused);
-// writes p (unless the caller gave p) and q; p.q -> alpha.
-__global__ void __launch_bounds__(NT) k64_warp_apply(P64 P, int par) {
+// q = (J^T J + lambda D) p with the angle columns of J from PCGInit; p.q ->
+// alpha.  Per stencil pair (i, j = i + d), both residuals exist together
+// (both pixels valid); with dp = p_i - p_j (x, y), a = dp - R'_i v pt_i the
+// own row's J p / s_w and b = -dp - R'_j (-v) pt_j the incoming one's:
+//   q_O += w (a - b) = w (a + dp + R'_j(-v) pt_j),   q_t -= w R'_i v . a.
+__global__ void __launch_bounds__(NT) k64_warp_apply(P64 P) {
   Scalars* s = P.s;
   if (s->done || !s->pcg_active) return;
-  const double beta = P.pin ? 0.0 : s->beta_d;
   const double lam = P.lm ? s->lambda : 0.0;
-  const double* __restrict__ po = P.p[par & 1];
-  double* __restrict__ pn = P.p[(par + 1) & 1];
+  const double* __restrict__ pp = P.pin ? P.pin : P.p;
   const long long n = P.n;
-  const double sw = P.s_w;
+  const double w = P.w_reg;
   double pq = 0.0;
   FOR_ELEMENTS(P, i) {
     // rows without residuals (excluded pixels) carry only the damping term
-    const double pxi = dir64(P, po, beta, 0, i), pyi = dir64(P, po, beta, 1, i);
-    const double pti = dir64(P, po, beta, 2, i);
-    double qx = 0.0, qy = 0.0, qt = 0.0;
+    const double pxi = pp[i], pyi = pp[n + i], pti = pp[2 * n + i];
+    double ax_ = 0.0, ay_ = 0.0, at_ = 0.0;
     if (elem_valid(P, i)) {
       const int gx = (int)(i % P.W), gy = (int)(i / P.W);
-      const double ci = P.cs[i], si = P.cs[n + i];
-      const double uxi = P.c[i], uyi = P.c[n + i];
       for (int k = 0; k < 4; ++k) {
         const int nx_ = gx + ddx(k), ny_ = gy + ddy(k);
         if (nx_ < 0 || nx_ >= P.W || ny_ < 0 || ny_ >= P.H) continue;
         const long long j = (long long)ny_ * P.W + nx_;
         if (!elem_valid(P, j)) continue;
-        const double pxj = dir64(P, po, beta, 0, j), pyj = dir64(P, po, beta, 1, j);
-        const double ptj = dir64(P, po, beta, 2, j);
-        const double vx = uxi - P.c[j], vy = uyi - P.c[n + j];
-        // own residual (i, d): J p = s_w ((pO_i - pO_j) - R'(theta_i) v pt_i)
-        const double rpx = -si * vx - ci * vy, rpy = ci * vx - si * vy;
-        const double ax = sw * ((pxi - pxj) - rpx * pti);
-        const double ay = sw * ((pyi - pyj) - rpy * pti);
-        qx += sw * ax;
-        qy += sw * ay;
-        qt -= sw * (rpx * ax + rpy * ay);
-        // incoming residual (j, -d) with w = -v
-        const double cj = P.cs[j], sj = P.cs[n + j];
-        const double qpx = sj * vx + cj * vy, qpy = -cj * vx + sj * vy;   // R'(theta_j) (-v)
-        const double bx = sw * ((pxj - pxi) - qpx * ptj);
-        const double by = sw * ((pyj - pyi) - qpy * ptj);
-        qx -= sw * bx;
-        qy -= sw * by;
+        const int ko = k ^ 1;                                   // the opposite direction, seen from j
+        const double rpx = P.G[(2 * k) * n + i], rpy = P.G[(2 * k + 1) * n + i];
+        const double qpx = P.G[(2 * ko) * n + j], qpy = P.G[(2 * ko + 1) * n + j];
+        const double ptj = pp[2 * n + j];
+        const double dx = pxi - pp[j], dy = pyi - pp[n + j];
+        const double ax = fma(-rpx, pti, dx), ay = fma(-rpy, pti, dy);
+        at_ = fma(rpx, ax, fma(rpy, ay, at_));
+        ax_ += fma(qpx, ptj, ax + dx);
+        ay_ += fma(qpy, ptj, ay + dy);
       }
-      if (P.hslot[i] >= 0) {
-        qx += P.w_fit * pxi;
-        qy += P.w_fit * pyi;
-      }
+    }
+    double qx = w * ax_, qy = w * ay_, qt = -w * at_;
+    if (P.hslot[i] >= 0) {
+      qx = fma(P.w_fit, pxi, qx);
+      qy = fma(P.w_fit, pyi, qy);
     }
     if (lam != 0.0) {
       qx += lam * P.dc[i] * pxi;
@@ -374,11 +386,6 @@ __global__ void __launch_bounds__(NT) k64_warp_apply(P64 P, int par) {
     P.q[i] = qx;
     P.q[n + i] = qy;
     P.q[2 * n + i] = qt;
-    if (!P.pin) {
-      pn[i] = pxi;
-      pn[n + i] = pyi;
-      pn[2 * n + i] = pti;
-    }
     pq += pxi * qx + pyi * qy + pti * qt;
   }
   apply_finish(P, pq);
@@ -473,38 +480,36 @@ __global__ void __launch_bounds__(NT) k64_poisson_init(P64 P, int k_outer, doubl
   init_finish(P, rz, E, k_outer);
 }
 
-__global__ void __launch_bounds__(NT) k64_poisson_apply(P64 P, int par) {
+__global__ void __launch_bounds__(NT) k64_poisson_apply(P64 P) {
   Scalars* s = P.s;
   if (s->done || !s->pcg_active) return;
-  const double beta = P.pin ? 0.0 : s->beta_d;
   const double lam = P.lm ? s->lambda : 0.0;
-  const double* __restrict__ po = P.p[par & 1];
-  double* __restrict__ pn = P.p[(par + 1) & 1];
+  const double* __restrict__ pp = P.pin ? P.pin : P.p;
   const long long n = P.n;
   double pq = 0.0;
   FOR_ELEMENTS(P, i) {
     // fixed pixels carry only the damping term (their p is 0 in a solve)
     double pv[4], qv[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int c = 0; c < 4; ++c) pv[c] = dir64(P, po, beta, c, i);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) pv[c] = pp[c * n + i];
     if (elem_valid(P, i)) {
       const int gx = (int)(i % P.W), gy = (int)(i / P.W);
       for (int k = 0; k < 4; ++k) {
         const int nx_ = gx + ddx(k), ny_ = gy + ddy(k);
         if (nx_ < 0 || nx_ >= P.W || ny_ < 0 || ny_ >= P.H) continue;
         const long long j = (long long)ny_ * P.W + nx_;
+        // own residual: J p = p_i - p_j (p_j = 0 on a fixed pixel); the
+        // incoming one of a free neighbour adds the same again
         const bool fj = elem_valid(P, j);
-        for (int c = 0; c < 4; ++c) {
-          const double pj = fj ? dir64(P, po, beta, c, j) : 0.0;   // p = 0 on fixed pixels
-          const double a = pv[c] - pj;                              // own residual: J p
-          qv[c] += fj ? 2.0 * a : a;                                // incoming one: -(pj - pi)
-        }
+        const double f = fj ? 2.0 : 1.0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) qv[c] = fma(f, pv[c] - (fj ? pp[c * n + j] : 0.0), qv[c]);
       }
     }
-    if (lam != 0.0)
-      for (int c = 0; c < 4; ++c) qv[c] += lam * P.dc[c * n + i] * pv[c];
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
+      if (lam != 0.0) qv[c] += lam * P.dc[c * n + i] * pv[c];
       P.q[c * n + i] = qv[c];
-      if (!P.pin) pn[c * n + i] = pv[c];
       pq += pv[c] * qv[c];
     }
   }
@@ -568,6 +573,8 @@ __global__ void __launch_bounds__(NT) k64_mesh_init(P64 P, int k_outer, double d
       const int b = P.oe1[e];
       const double wv[3] = {uv[0] - P.c[b], uv[1] - P.c[n + b], uv[2] - P.c[2 * n + b]};
       const RotVT<double> R = rot_at(P, v, wv[0], wv[1], wv[2]);
+      for (int m = 0; m < 3; ++m)
+        for (int c = 0; c < 3; ++c) P.G[(3 * m + c) * P.ne + e] = R.g[m][c];
       double f[3];
       for (int c = 0; c < 3; ++c) f[c] = sw * ((xv[c] - P.x[c * n + b]) + wv[c] - R.rv[c]);
       E += f[0] * f[0] + f[1] * f[1] + f[2] * f[2];
@@ -604,48 +611,56 @@ __global__ void __launch_bounds__(NT) k64_mesh_init(P64 P, int k_outer, double d
   init_finish(P, rz, E, k_outer);
 }
 
-__global__ void __launch_bounds__(NT) k64_mesh_apply(P64 P, int par) {
+// q = (J^T J + lambda D) p with every edge's angle columns g_m = dR/dA_m w
+// (w = U_a - U_b) from PCGInit: J_e p / s_w = (pd_a - pd_b) - sum_m g_m pA_m(a);
+// own edges add w J_e p / s_w to q_d and -w g_m . (J_e p / s_w) to q_A, in-edges
+// subtract w J_e p / s_w from q_d.
+__global__ void __launch_bounds__(NT) k64_mesh_apply(P64 P) {
   Scalars* s = P.s;
   if (s->done || !s->pcg_active) return;
-  const double beta = P.pin ? 0.0 : s->beta_d;
   const double lam = P.lm ? s->lambda : 0.0;
-  const double* __restrict__ po = P.p[par & 1];
-  double* __restrict__ pn = P.p[(par + 1) & 1];
-  const long long n = P.n;
-  const double sw = P.s_w;
+  const double* __restrict__ pp = P.pin ? P.pin : P.p;
+  const long long n = P.n, ne = P.ne;
+  const double w = P.w_reg;
   double pq = 0.0;
   FOR_ELEMENTS(P, v) {
-    double pv[6], qv[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int c = 0; c < 6; ++c) pv[c] = dir64(P, po, beta, c, v);
-    const double uv[3] = {P.c[v], P.c[n + v], P.c[2 * n + v]};
+    double pv[6], qd[3] = {0.0, 0.0, 0.0}, qa[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) pv[c] = pp[c * n + v];
     for (int e = P.orow[v]; e < P.orow[v + 1]; ++e) {
       const int b = P.oe1[e];
-      const RotVT<double> R = rot_at(P, v, uv[0] - P.c[b], uv[1] - P.c[n + b], uv[2] - P.c[2 * n + b]);
+      double g[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) g[k] = P.G[k * ne + e];
       double jp[3];
-      for (int c = 0; c < 3; ++c)
-        jp[c] = sw * ((pv[c] - dir64(P, po, beta, c, b)) -
-                      (R.g[0][c] * pv[3] + R.g[1][c] * pv[4] + R.g[2][c] * pv[5]));
-      for (int c = 0; c < 3; ++c) qv[c] += sw * jp[c];
-      for (int m = 0; m < 3; ++m) qv[3 + m] -= sw * (R.g[m][0] * jp[0] + R.g[m][1] * jp[1] + R.g[m][2] * jp[2]);
-    }
-    for (int e = P.irow[v]; e < P.irow[v + 1]; ++e) {
-      const int a = P.isrc[e];
-      const RotVT<double> R = rot_at(P, a, P.c[a] - uv[0], P.c[n + a] - uv[1], P.c[2 * n + a] - uv[2]);
-      const double pa3 = dir64(P, po, beta, 3, a), pa4 = dir64(P, po, beta, 4, a);
-      const double pa5 = dir64(P, po, beta, 5, a);
+#pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const double jp = sw * ((dir64(P, po, beta, c, a) - pv[c]) -
-                                (R.g[0][c] * pa3 + R.g[1][c] * pa4 + R.g[2][c] * pa5));
-        qv[c] -= sw * jp;
+        const double t = fma(g[c], pv[3], fma(g[3 + c], pv[4], g[6 + c] * pv[5]));
+        jp[c] = (pv[c] - pp[c * n + b]) - t;
+        qd[c] += jp[c];
+      }
+#pragma unroll
+      for (int m = 0; m < 3; ++m) qa[m] = fma(g[3 * m], jp[0], fma(g[3 * m + 1], jp[1], fma(g[3 * m + 2], jp[2], qa[m])));
+    }
+    for (int k = P.irow[v]; k < P.irow[v + 1]; ++k) {
+      const int a = P.isrc[k], e = P.ieid[k];
+      const double pa3 = pp[3 * n + a], pa4 = pp[4 * n + a], pa5 = pp[5 * n + a];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double t = fma(P.G[c * ne + e], pa3, fma(P.G[(3 + c) * ne + e], pa4, P.G[(6 + c) * ne + e] * pa5));
+        qd[c] -= (pp[c * n + a] - pv[c]) - t;
       }
     }
+    double qv[6] = {w * qd[0], w * qd[1], w * qd[2], -w * qa[0], -w * qa[1], -w * qa[2]};
     if (P.hslot[v] >= 0)
-      for (int c = 0; c < 3; ++c) qv[c] += P.w_fit * pv[c];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) qv[c] = fma(P.w_fit, pv[c], qv[c]);
     if (lam != 0.0)
+#pragma unroll
       for (int c = 0; c < 6; ++c) qv[c] += lam * P.dc[c * n + v] * pv[c];
+#pragma unroll
     for (int c = 0; c < 6; ++c) {
       P.q[c * n + v] = qv[c];
-      if (!P.pin) pn[c * n + v] = pv[c];
       pq += pv[c] * qv[c];
     }
   }
@@ -820,15 +835,13 @@ opt_status plan_common(opt_problem_f64* pb, const std::vector<double>& consts, c
   CKS64(alloc64(pb, &P.q, n * P.nx));
   CKS64(alloc64(pb, &P.m, n * P.nx));
   CKS64(alloc64(pb, &P.dc, n * P.nx));
-  CKS64(alloc64(pb, &P.p[0], n * P.nx));
-  CKS64(alloc64(pb, &P.p[1], n * P.nx));
+  CKS64(alloc64(pb, &P.p, n * P.nx));
   CKS64(alloc64(pb, &pb->d_pin, n * P.nx));
   if (ncs) CKS64(alloc64(pb, &P.cs, n * ncs));
   CKS64(alloc64(pb, &P.part, 2 * (size_t)pb->nblk));
   CKS64(alloc64(pb, &pb->d_s, 1));
   CK64(cudaMemset(pb->d_s, 0, sizeof(Scalars)));
-  CK64(cudaMemset(P.p[0], 0, n * P.nx * sizeof(double)));
-  CK64(cudaMemset(P.p[1], 0, n * P.nx * sizeof(double)));
+  CK64(cudaMemset(P.p, 0, n * P.nx * sizeof(double)));
   P.s = pb->d_s;
   CK64(cudaStreamCreateWithFlags(&pb->cap_stream, cudaStreamNonBlocking));
   CK64(cudaEventCreate(&pb->ev0));
@@ -861,15 +874,22 @@ void k_init(opt_problem_f64* pb, const P64& P, cudaStream_t st, int k, double dm
   else if (pb->kind == F64_POISSON) k64_poisson_init<<<pb->nblk, NT, 0, st>>>(P, k, dmin, dmax);
   else k64_mesh_init<<<pb->nblk, NT, 0, st>>>(P, k, dmin, dmax);
 }
-void k_apply(opt_problem_f64* pb, const P64& P, cudaStream_t st, int par) {
-  if (pb->kind == F64_WARP) k64_warp_apply<<<pb->nblk, NT, 0, st>>>(P, par);
-  else if (pb->kind == F64_POISSON) k64_poisson_apply<<<pb->nblk, NT, 0, st>>>(P, par);
-  else k64_mesh_apply<<<pb->nblk, NT, 0, st>>>(P, par);
+// applyJTJ of PCG iteration i: the direction update (from the second
+// iteration on; PCGInit writes the first direction), then q = A p
+void k_apply(opt_problem_f64* pb, const P64& P, cudaStream_t st, int i) {
+  if (i > 0 && !P.pin) {
+    if (pb->kind == F64_WARP) k64_direction<3><<<pb->nblk, NT, 0, st>>>(P);
+    else if (pb->kind == F64_POISSON) k64_direction<4><<<pb->nblk, NT, 0, st>>>(P);
+    else k64_direction<6><<<pb->nblk, NT, 0, st>>>(P);
+  }
+  if (pb->kind == F64_WARP) k64_warp_apply<<<pb->nblk, NT, 0, st>>>(P);
+  else if (pb->kind == F64_POISSON) k64_poisson_apply<<<pb->nblk, NT, 0, st>>>(P);
+  else k64_mesh_apply<<<pb->nblk, NT, 0, st>>>(P);
 }
-void k_update(opt_problem_f64* pb, const P64& P, cudaStream_t st, int par) {
-  if (pb->kind == F64_WARP) k64_update<3><<<pb->nblk, NT, 0, st>>>(P, par);
-  else if (pb->kind == F64_POISSON) k64_update<4><<<pb->nblk, NT, 0, st>>>(P, par);
-  else k64_update<6><<<pb->nblk, NT, 0, st>>>(P, par);
+void k_update(opt_problem_f64* pb, const P64& P, cudaStream_t st) {
+  if (pb->kind == F64_WARP) k64_update<3><<<pb->nblk, NT, 0, st>>>(P);
+  else if (pb->kind == F64_POISSON) k64_update<4><<<pb->nblk, NT, 0, st>>>(P);
+  else k64_update<6><<<pb->nblk, NT, 0, st>>>(P);
 }
 void k_energy(opt_problem_f64* pb, const P64& P, cudaStream_t st, int mode, int hist) {
   if (pb->kind == F64_WARP) k64_warp_energy<<<pb->nblk, NT, 0, st>>>(P, mode, hist);
@@ -913,7 +933,7 @@ opt_status enqueue_solve64(opt_problem_f64* pb, const opt_solve_params& p, bool 
     k_init(pb, P, st, k, p.diag_min, p.diag_max);
     for (int i = 0; i < p.inner; ++i) {
       k_apply(pb, P, st, i);
-      k_update(pb, P, st, i);
+      k_update(pb, P, st);
     }
     if (!lm) {
       k64_step<<<pb->nblk, NT, 0, st>>>(P, 0);
@@ -1078,6 +1098,7 @@ opt_status opt_problem_create_grid_f64(const opt_grid_desc_f64* d, const opt_sol
     hslot.assign((size_t)n, -1);
   }
   CKS64(plan_common(pb.get(), consts, hslot, htgt, warp ? d->w_reg : 1.0, warp ? d->w_fit : 0.0));
+  if (warp) CKS64(alloc64(pb.get(), &P.G, 8 * (size_t)n));   // R'(theta) v per direction
   if (d->mask) {
     uint8_t* mk = nullptr;
     CKS64(alloc64(pb.get(), &mk, (size_t)n));
@@ -1107,6 +1128,7 @@ opt_status opt_problem_create_graph_f64(const opt_graph_desc_f64* d, const opt_s
     if (e0[e] < 0 || e0[e] >= V || e1[e] < 0 || e1[e] >= V || e0[e] == e1[e]) return OPT_ERR_INVALID_ARG;
   // out-edges sorted by (v0, v1): counting sort by v1, then stable by v0
   std::vector<int> orow(V + 1, 0), irow(V + 1, 0), tmpo((size_t)E), oe1((size_t)E), isrc((size_t)E);
+  std::vector<int> ieid((size_t)E);
   {
     std::vector<int> cnt(V + 1, 0);
     for (int e = 0; e < E; ++e) cnt[e1[e] + 1]++;
@@ -1124,7 +1146,11 @@ opt_status opt_problem_create_graph_f64(const opt_graph_desc_f64* d, const opt_s
     for (int v = 0; v < V; ++v) irow[v + 1] += irow[v];
     std::vector<int> ipos(irow.begin(), irow.end() - 1);
     for (int a = 0; a < V; ++a)
-      for (int k = orow[a]; k < orow[a + 1]; ++k) isrc[ipos[oe1[k]]++] = a;
+      for (int k = orow[a]; k < orow[a + 1]; ++k) {
+        const int slot = ipos[oe1[k]]++;
+        isrc[slot] = a;
+        ieid[slot] = k;
+      }
   }
   std::unique_ptr<opt_problem_f64> pb(new opt_problem_f64());
   pb->kind = F64_MESH;
@@ -1135,6 +1161,7 @@ opt_status opt_problem_create_graph_f64(const opt_graph_desc_f64* d, const opt_s
   P.H = 0;
   P.nx = 6;
   P.n = V;
+  P.ne = E;
   for (int c = 0; c < 6; ++c) pb->user_x[c] = d->unknowns[c];
   std::vector<double> consts((size_t)V * 3), tmp;
   for (int c = 0; c < 3; ++c) {
@@ -1151,15 +1178,18 @@ opt_status opt_problem_create_graph_f64(const opt_graph_desc_f64* d, const opt_s
     if (!all_finite(htgt)) return OPT_ERR_INVALID_ARG;
   }
   CKS64(plan_common(pb.get(), consts, hslot, htgt, d->w_reg, d->w_fit));
-  int *a = nullptr, *b = nullptr, *c2 = nullptr, *d2 = nullptr;
+  int *a = nullptr, *b = nullptr, *c2 = nullptr, *d2 = nullptr, *e2 = nullptr;
   CKS64(upload64(pb.get(), &a, orow));
   CKS64(upload64(pb.get(), &b, oe1));
   CKS64(upload64(pb.get(), &c2, irow));
   CKS64(upload64(pb.get(), &d2, isrc));
+  CKS64(upload64(pb.get(), &e2, ieid));
+  CKS64(alloc64(pb.get(), &P.G, 9 * (size_t)E));            // dR/dA_m w per directed edge
   P.orow = a;
   P.oe1 = b;
   P.irow = c2;
   P.isrc = d2;
+  P.ieid = e2;
   return finish_create64(pb, out);
 }
 
@@ -1231,8 +1261,8 @@ opt_status opt_profile_pcg_f64(opt_problem_f64* pb, int32_t n_iters, void* strea
   std::vector<cudaEvent_t> ev(2 + 4 * (size_t)n_iters);
   for (auto& e : ev) CK64(cudaEventCreate(&e));
   k64_reset<<<1, 1, 0, st>>>(pb->d_s, 0.0);
-  k_rot(pb, st);
   CK64(cudaEventRecord(ev[0], st));
+  k_rot(pb, st);
   k_init(pb, P, st, -1, 1e-6, 1e32);
   CK64(cudaEventRecord(ev[1], st));
   for (int i = 0; i < n_iters; ++i) {
@@ -1240,7 +1270,7 @@ opt_status opt_profile_pcg_f64(opt_problem_f64* pb, int32_t n_iters, void* strea
     k_apply(pb, P, st, i);
     CK64(cudaEventRecord(ev[3 + 4 * i], st));
     CK64(cudaEventRecord(ev[4 + 4 * i], st));
-    k_update(pb, P, st, i);
+    k_update(pb, P, st);
     CK64(cudaEventRecord(ev[5 + 4 * i], st));
   }
   CK64(cudaGetLastError());
