@@ -247,16 +247,25 @@ __global__ void __launch_bounds__(NT) k_ed_apply_v(const MeshProb* __restrict__ 
   const float beta = s->beta_f;
   const float* __restrict__ pin = p_override ? p_override : pr.p + (long long)(par & 1) * NXE * pl;
   float* __restrict__ pout = pr.p + (long long)((par + 1) & 1) * NXE * pl;
+  const float* __restrict__ rr = pr.r;
+  const float* __restrict__ mm = pr.m;
   for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
     float pv[NXE];
     if (update) {
+      // every load before any store (the planes may not alias, but the
+      // compiler cannot know: stores first would serialise the loads)
+      float rv[NXE], mv[NME], po[NXE];
 #pragma unroll
       for (int c = 0; c < NXE; ++c) {
-        float pc = pr.m[mplane_e(c) * pl + v] * pr.r[c * pl + v];
-        if (beta != 0.0f) pc = fmaf(beta, pin[c * pl + v], pc);
-        pv[c] = pc;
-        pout[c * pl + v] = pc;
+        rv[c] = __ldcg(rr + c * pl + v);
+        po[c] = beta != 0.0f ? __ldcg(pin + c * pl + v) : 0.f;
       }
+#pragma unroll
+      for (int k = 0; k < NME; ++k) mv[k] = __ldg(mm + k * pl + v);
+#pragma unroll
+      for (int c = 0; c < NXE; ++c) pv[c] = fmaf(beta, po[c], mv[mplane_e(c)] * rv[c]);
+#pragma unroll
+      for (int c = 0; c < NXE; ++c) pout[c * pl + v] = pv[c];
     } else {
 #pragma unroll
       for (int c = 0; c < NXE; ++c) pv[c] = pin[c * pl + v];
@@ -361,15 +370,33 @@ __global__ void __launch_bounds__(NT) k_ed_update(const MeshProb* __restrict__ p
   const long long pl = pr.Vp;
   const float alpha = s->alpha_f;
   const float* __restrict__ pn = pr.p + (long long)((par + 1) & 1) * NXE * pl;
+  float* __restrict__ dd = pr.d;
+  float* __restrict__ rr = pr.r;
+  const float* __restrict__ qq = pr.q;
+  const float* __restrict__ mm = pr.m;
   float acc = 0.f;
   for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
+    // every load before any store
+    float pv[NXE], qv[NXE], dv[NXE], rv[NXE], mv[NME];
 #pragma unroll
     for (int c = 0; c < NXE; ++c) {
-      const long long k = c * pl + v;
-      pr.d[k] += alpha * __ldcg(pn + k);
-      const float rv = pr.r[k] - alpha * __ldcg(pr.q + k);
-      pr.r[k] = rv;
-      acc += rv * (__ldg(pr.m + mplane_e(c) * pl + v) * rv);
+      pv[c] = __ldcg(pn + c * pl + v);
+      qv[c] = __ldcg(qq + c * pl + v);
+      dv[c] = dd[c * pl + v];
+      rv[c] = rr[c * pl + v];
+    }
+#pragma unroll
+    for (int k = 0; k < NME; ++k) mv[k] = __ldg(mm + k * pl + v);
+#pragma unroll
+    for (int c = 0; c < NXE; ++c) {
+      dv[c] = fmaf(alpha, pv[c], dv[c]);
+      rv[c] = fmaf(-alpha, qv[c], rv[c]);
+      acc += rv[c] * (mv[mplane_e(c)] * rv[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < NXE; ++c) {
+      dd[c * pl + v] = dv[c];
+      rr[c * pl + v] = rv[c];
     }
   }
   pdl_trigger();
@@ -485,9 +512,17 @@ __global__ void __launch_bounds__(NT) k_ed_step(const MeshProb* __restrict__ pro
   if (cond && !pr.s->accept) return;
   if (!cond && pr.s->done) return;
   const long long pl = pr.Vp;
+  float* __restrict__ x = pr.x;
+  const float* __restrict__ dd = pr.d;
   for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
+    float xv[NXE], dv[NXE];
 #pragma unroll
-    for (int c = 0; c < NXE; ++c) pr.x[c * pl + v] += __ldg(pr.d + c * pl + v);
+    for (int c = 0; c < NXE; ++c) {
+      xv[c] = x[c * pl + v];
+      dv[c] = __ldg(dd + c * pl + v);
+    }
+#pragma unroll
+    for (int c = 0; c < NXE; ++c) x[c * pl + v] = xv[c] + dv[c];
   }
 }
 

@@ -222,12 +222,19 @@ __global__ void __launch_bounds__(NT) k64_direction(P64 P) {
   const Scalars* s = P.s;
   if (s->done || !s->pcg_active) return;
   const double beta = s->beta_d;
+  double* __restrict__ pp = P.p;
+  const double* __restrict__ mm = P.m;
+  const double* __restrict__ rr = P.r;
   FOR_ELEMENTS(P, i) {
+    double pv[NX], mv[NX], rv[NX];   // every load before any store
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
-      const long long k = c * P.n + i;
-      P.p[k] = fma(beta, P.p[k], P.m[k] * P.r[k]);
+      pv[c] = pp[c * P.n + i];
+      mv[c] = mm[c * P.n + i];
+      rv[c] = rr[c * P.n + i];
     }
+#pragma unroll
+    for (int c = 0; c < NX; ++c) pp[c * P.n + i] = fma(beta, pv[c], mv[c] * rv[c]);
   }
 }
 
@@ -239,15 +246,29 @@ __global__ void __launch_bounds__(NT) k64_update(P64 P) {
   if (s->done || !s->pcg_active) return;
   const double alpha = s->alpha_d;
   const double* __restrict__ pn = P.p;
+  const double* __restrict__ qq = P.q;
+  const double* __restrict__ mm = P.m;
+  double* __restrict__ dd = P.d;
+  double* __restrict__ rr = P.r;
   double rz = 0.0;
   FOR_ELEMENTS(P, i) {
+    double pv[NX], qv[NX], mv[NX], dv[NX], rv[NX];   // every load before any store
 #pragma unroll
     for (int c = 0; c < NX; ++c) {
       const long long k = c * P.n + i;
-      P.d[k] += alpha * pn[k];
-      const double rv = P.r[k] - alpha * P.q[k];
-      P.r[k] = rv;
-      rz += rv * P.m[k] * rv;
+      pv[c] = pn[k];
+      qv[c] = qq[k];
+      mv[c] = mm[k];
+      dv[c] = dd[k];
+      rv[c] = rr[k];
+    }
+#pragma unroll
+    for (int c = 0; c < NX; ++c) {
+      const long long k = c * P.n + i;
+      dd[k] = fma(alpha, pv[c], dv[c]);
+      const double r2 = fma(-alpha, qv[c], rv[c]);
+      rr[k] = r2;
+      rz += r2 * mv[c] * r2;
     }
   }
   if (publish64(P.part, rz, 0.0, &s->counter)) {
