@@ -29,6 +29,21 @@ namespace {
 
 constexpr int NXE = 12;   // unknowns per vertex
 constexpr int NME = 10;   // distinct-diagonal planes
+constexpr int KBE = 6;    // neighbour indices fetched ahead per vertex (icosphere degree 5 / 6)
+
+// Visits the out-edge targets e1[o0 .. o1) (or in-edge sources) of a vertex:
+// the first KBE indices are loaded together before any neighbour record is
+// needed, the rest of a longer row one by one.
+template <typename F>
+__device__ __forceinline__ void for_neighbours(const int* __restrict__ idx, int o0, int o1, F&& f) {
+  int j[KBE];
+#pragma unroll
+  for (int t = 0; t < KBE; ++t) j[t] = o0 + t < o1 ? __ldg(idx + o0 + t) : 0;
+#pragma unroll
+  for (int t = 0; t < KBE; ++t)
+    if (o0 + t < o1) f(j[t]);
+  for (int k = o0 + KBE; k < o1; ++k) f(__ldg(idx + k));
+}
 
 __device__ __forceinline__ int mplane_e(int c) { return c < 3 ? 0 : c - 2; }
 
@@ -141,8 +156,7 @@ __global__ void __launch_bounds__(NT) k_ed_init_pull(const MeshProb* __restrict_
         e += f * f;
       }
     }
-    for (int k = pr.orow[i]; k < pr.orow[i + 1]; ++k) {
-      const int j = pr.e1[k];
+    for_neighbours(pr.e1, pr.orow[i], pr.orow[i + 1], [&](int j) {
       const float4 dj = pr.vrec[3 * j];
       const float4 uj = __ldg(pr.grec + j);
       const float wv[3] = {ui.x - uj.x, ui.y - uj.y, ui.z - uj.z};
@@ -161,9 +175,8 @@ __global__ void __launch_bounds__(NT) k_ed_init_pull(const MeshProb* __restrict_
         const float wc2 = w * wv[c] * wv[c];
         dR[c] += wc2; dR[3 + c] += wc2; dR[6 + c] += wc2;
       }
-    }
-    for (int k = pr.irow[i]; k < pr.irow[i + 1]; ++k) {
-      const int j = pr.isrc[k];
+    });
+    for_neighbours(pr.isrc, pr.irow[i], pr.irow[i + 1], [&](int j) {
       float xj[NXE];
       load12(pr.vrec, j, xj);
       const float4 uj = __ldg(pr.grec + j);
@@ -173,7 +186,7 @@ __global__ void __launch_bounds__(NT) k_ed_init_pull(const MeshProb* __restrict_
         const float rw = xj[3 + 3 * r] * wv[0] + xj[4 + 3 * r] * wv[1] + xj[5 + 3 * r] * wv[2];
         g[r] -= sw * (sw * (((xj[r] - xi[r]) + wv[r]) - rw));
       }
-    }
+    });
     {
       float f[6];
       col_constraints(xi + 3, f);
@@ -298,6 +311,8 @@ __global__ void __launch_bounds__(NT) k_ed_apply_pull(const MeshProb* __restrict
 #pragma unroll
       for (int c = 0; c < 3; ++c) q[c] += pr.w_fit * pi[c];
     }
+    // (plain loops: prefetching the indices as PCGInit does costs this
+    // kernel occupancy -- 100 instead of 80 registers -- and was measured slower)
     for (int k = pr.orow[i]; k < pr.orow[i + 1]; ++k) {
       const int j = pr.e1[k];
       const float4 pj = pr.vrec[3 * j];
