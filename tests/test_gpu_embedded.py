@@ -181,3 +181,15 @@ def test_embedded_invalid_arguments(api):
     with pytest.raises(api.OptError):
         gp.solve_lm(2, 2, materialized=1)
     gp.close()
+
+
+def test_embedded_plain_cg_lm(api):
+    """use_precond = 0 (M^-1 = 1) under LM, against the oracle's."""
+    prob = synth.embedded_problem(2, seed=95, handle_frac=0.05)
+    e = oracle.make_energy(prob)
+    ref = oracle.levenberg_marquardt(e, prob.x0.reshape(-1), 4, 10, use_precond=False)
+    gp = api.Problem(prob)
+    rep = gp.solve_lm(4, 10, use_precond=0)
+    assert rep["accepted"] == int(sum(ref.accepted))
+    for a, b in zip(rep["E_history"], ref.E_history):
+        assert relE(a, b) <= TOL_ENERGY

@@ -268,3 +268,20 @@ def test_invalid_arguments_f64(api):
 def test_fp64_fma_rate_is_measured(api):
     g = api.fp64_fma_rate()
     assert 10.0 < g < 1e6   # GFLOP/s
+
+
+@pytest.mark.parametrize("kind", ["warp", "poisson", "mesh"])
+def test_plain_cg_f64(api, kind):
+    """use_precond = 0: unpreconditioned CG (M^-1 = 1), against the oracle's.
+    Without the Jacobi scaling the warp's system is badly conditioned (the
+    fit rows weigh 100 against rows of 4 .. 8), and CG carries the different
+    summation orders of the two sides further: the bar is 1e-6, not 1e-9."""
+    prob = {"warp": lambda: synth.warp_problem(40, 30, 5, seed=17),
+            "poisson": lambda: synth.poisson_problem(48, 40, seed=18),
+            "mesh": lambda: synth.mesh_problem(2, seed=19, handle_frac=0.05)}[kind]()
+    e = oracle.make_energy(prob)
+    ref = oracle.gauss_newton(e, prob.x0.reshape(-1), 3, 10, use_precond=False)
+    gp = api.ProblemF64(prob)
+    rep = gp.solve_gn(3, 10, use_precond=0)
+    assert rep["pcg_done"] == ref.pcg_done
+    trajectory_close(rep, ref.E_history, 1e-6)

@@ -501,3 +501,24 @@ def test_persistent_pcg_equals_per_step_launches(api, W, H, mf, method, graph):
     ref = (oracle.gauss_newton(e, x0, 4, 12) if method == "gn" else oracle.levenberg_marquardt(e, x0, 4, 12))
     for x, y in zip(ra["E_history"], ref.E_history):
         assert relE(x, y) <= TOL_ENERGY
+
+
+@pytest.mark.parametrize("kind,inner", [("poisson", 10), ("mesh", 10), ("warp", 3)])
+def test_plain_cg_matches_oracle(api, kind, inner):
+    """use_precond = 0 (M^-1 = 1).  Poisson and the mesh follow the oracle
+    over 10 CG iterations; on the warp, whose fit rows weigh 100 against
+    stencil rows of 4 .. 8, unpreconditioned CG amplifies rounding about
+    100-fold per iteration (float32 vs float64: 7e-7 after 3 iterations, 5e-2
+    after 8), so it is checked over 3 -- the Jacobi preconditioner removes
+    this (float32 within 1e-7 at any count)."""
+    prob = {"warp": lambda: synth.warp_problem(40, 30, 5, seed=17),
+            "poisson": lambda: synth.poisson_problem(48, 40, seed=18),
+            "mesh": lambda: synth.mesh_problem(2, seed=19, handle_frac=0.05)}[kind]()
+    e = oracle.make_energy(prob)
+    ref = oracle.gauss_newton(e, prob.x0.reshape(-1), 2, inner, use_precond=False)
+    gp = api.Problem(prob)
+    rep = gp.solve_gn(2, inner, use_precond=0)
+    assert rep["pcg_done"] == ref.pcg_done
+    for a, b in zip(rep["E_history"], ref.E_history):
+        assert relE(a, b) <= TOL_ENERGY
+    gp.close()
