@@ -622,13 +622,13 @@ __device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, c
       const int col = side ? 4 + W4 : 3;
       float a, b, c;
       if (update) {
-        a = sm.raw[3][row][col] * sm.raw[0][row][col];
-        b = sm.raw[3][row][col] * sm.raw[1][row][col];
-        c = sm.raw[4][row][col] * sm.raw[2][row][col];
+        a = __fmul_rn(sm.raw[3][row][col], sm.raw[0][row][col]);
+        b = __fmul_rn(sm.raw[3][row][col], sm.raw[1][row][col]);
+        c = __fmul_rn(sm.raw[4][row][col], sm.raw[2][row][col]);
         if (use_beta) {
-          a = fmaf(beta, sm.raw[5][row][col], a);
-          b = fmaf(beta, sm.raw[6][row][col], b);
-          c = fmaf(beta, sm.raw[7][row][col], c);
+          a = __fmaf_rn(beta, sm.raw[5][row][col], a);
+          b = __fmaf_rn(beta, sm.raw[6][row][col], b);
+          c = __fmaf_rn(beta, sm.raw[7][row][col], c);
         }
       } else {
         a = sm.raw[5][row][col]; b = sm.raw[6][row][col]; c = sm.raw[7][row][col];
@@ -713,12 +713,17 @@ __device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, c
       float qt[4] = {atA.x, atB.x, atA.y, atB.y};
       const float vf[4] = {O[7].x, O[7].z, O[7].y, O[7].w};
       const float4 opx = swz4(O[0]), opy = swz4(O[1]), opt = swz4(O[2]);
+      // explicit roundings (no contraction left to the compiler), so that
+      // every kernel instantiating this body computes the same bits
       for (int h = hcur0; h < hcur1; ++h) {
         const long long k = pr.hpix[h] - i;
         if (k >= 0 && k < 4) {
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
-            if (kk == k && vf[kk] != 0.f) { qx[kk] += wfit * cmp(opx, kk); qy[kk] += wfit * cmp(opy, kk); }
+            if (kk == k && vf[kk] != 0.f) {
+              qx[kk] = __fmaf_rn(wfit, cmp(opx, kk), qx[kk]);
+              qy[kk] = __fmaf_rn(wfit, cmp(opy, kk), qy[kk]);
+            }
         }
       }
       if (pr.lm) {
@@ -726,16 +731,17 @@ __device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, c
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           if (vf[k] == 0.f) continue;
-          qx[k] += lam * cmp(dd, k) * cmp(opx, k);
-          qy[k] += lam * cmp(dd, k) * cmp(opy, k);
-          qt[k] += lam * cmp(dt, k) * cmp(opt, k);
+          qx[k] = __fmaf_rn(__fmul_rn(lam, cmp(dd, k)), cmp(opx, k), qx[k]);
+          qy[k] = __fmaf_rn(__fmul_rn(lam, cmp(dd, k)), cmp(opy, k), qy[k]);
+          qt[k] = __fmaf_rn(__fmul_rn(lam, cmp(dt, k)), cmp(opt, k), qt[k]);
         }
       }
       *reinterpret_cast<float4*>(pr.q + i) = make_float4(qx[0], qx[1], qx[2], qx[3]);
       *reinterpret_cast<float4*>(pr.q + pl + i) = make_float4(qy[0], qy[1], qy[2], qy[3]);
       *reinterpret_cast<float4*>(pr.q + 2 * pl + i) = make_float4(qt[0], qt[1], qt[2], qt[3]);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc += cmp(opx, k) * qx[k] + cmp(opy, k) * qy[k] + cmp(opt, k) * qt[k];
+      for (int k = 0; k < 4; ++k)
+        acc = __fmaf_rn(cmp(opt, k), qt[k], __fmaf_rn(cmp(opy, k), qy[k], __fmaf_rn(cmp(opx, k), qx[k], acc)));
     }
   }
   cp_async_wait_all();
@@ -1883,12 +1889,16 @@ __device__ __forceinline__ void update_body(const Chunk& ch, const GridProb& pr,
     for (int c = 0; c < NX; ++c) {
       // distinct-diagonal plane: warp (x, y) -> 0, theta -> 1; Poisson -> 0
       const float4 m = mv[NX == 3 ? (c == 2 ? 1 : 0) : 0];
-      dv[c].x += alpha * pv[c].x; dv[c].y += alpha * pv[c].y;
-      dv[c].z += alpha * pv[c].z; dv[c].w += alpha * pv[c].w;
-      rv[c].x -= alpha * qv[c].x; rv[c].y -= alpha * qv[c].y;
-      rv[c].z -= alpha * qv[c].z; rv[c].w -= alpha * qv[c].w;
-      acc += rv[c].x * (m.x * rv[c].x) + rv[c].y * (m.y * rv[c].y) +
-             rv[c].z * (m.z * rv[c].z) + rv[c].w * (m.w * rv[c].w);
+      // explicit roundings: the same bits in every kernel using this body
+      dv[c].x = __fmaf_rn(alpha, pv[c].x, dv[c].x); dv[c].y = __fmaf_rn(alpha, pv[c].y, dv[c].y);
+      dv[c].z = __fmaf_rn(alpha, pv[c].z, dv[c].z); dv[c].w = __fmaf_rn(alpha, pv[c].w, dv[c].w);
+      rv[c].x = __fmaf_rn(-alpha, qv[c].x, rv[c].x); rv[c].y = __fmaf_rn(-alpha, qv[c].y, rv[c].y);
+      rv[c].z = __fmaf_rn(-alpha, qv[c].z, rv[c].z); rv[c].w = __fmaf_rn(-alpha, qv[c].w, rv[c].w);
+      float t = __fmul_rn(rv[c].x, __fmul_rn(m.x, rv[c].x));
+      t = __fmaf_rn(rv[c].y, __fmul_rn(m.y, rv[c].y), t);
+      t = __fmaf_rn(rv[c].z, __fmul_rn(m.z, rv[c].z), t);
+      t = __fmaf_rn(rv[c].w, __fmul_rn(m.w, rv[c].w), t);
+      acc = __fadd_rn(acc, t);
       d4[c * pl4 + j] = dv[c];
       r4[c * pl4 + j] = rv[c];
     }
