@@ -238,7 +238,7 @@ def roofline_for(api, synth, torch, W, H, peak, iters=20):
     """Per-kernel roofline of the matrix-free ARAP warp at W x H."""
     prob = synth.warp_problem(W, H, max(8, int(round(64.0 * W * H / 2 ** 20))), seed=synth.BASE_SEED)
     gp = api.Problem(prob)
-    wide = W >= 256                      # 128-pixel tiles (k_warp_*_wide) from 256 pixels up
+    wide = W >= 128                      # 128-pixel tiles (k_warp_*_wide) from 128 pixels up
     out = kernel_roofline(gp, (("k_warp_init_wide" if wide else "k_warp_init", BYTES_INIT_WARP, OUTER),
                                ("k_warp_apply_wide" if wide else "k_warp_apply", BYTES_APPLY_WARP, OUTER * INNER),
                                ("k_grid_update<3>", BYTES_UPDATE_WARP, OUTER * INNER)), W * H, peak, iters)

@@ -182,7 +182,7 @@ typedef struct {
                                  mesh and volume problems. */
     int32_t use_graph;        /* 1 = replay the solve as one CUDA graph (default) */
     int32_t tile_w;           /* grid planning only: tile width 32 or 128, 0 = automatic
-                                 (128 for grids at least 256 pixels wide, else 32) */
+                                 (128 for grids at least 128 pixels wide, else 32) */
     int32_t persistent;       /* 1 = run each outer iteration's PCG loop as one cooperative
                                  launch with grid-wide barriers when the problem is a wide-tile
                                  warp, matrix-free, and all its blocks fit on the device at once;

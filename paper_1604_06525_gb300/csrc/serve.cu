@@ -56,7 +56,7 @@ size_t round32(size_t v) { return (v + 31) / 32 * 32; }
 // Device bytes a planned problem allocates (planes, tables, reduction slots).
 size_t estimate_grid(const opt_grid_desc& d, int tile_w) {
   const bool warp = d.kind == OPT_ARAP_WARP_2D;
-  const size_t tw = tile_w ? tile_w : (d.W >= 256 ? 128 : 32);
+  const size_t tw = tile_w ? tile_w : (d.W >= 128 ? 128 : 32);
   const size_t pl = ((size_t)d.W + tw - 1) / tw * tw * (size_t)d.H;
   const size_t planes = warp ? (tw == 128 ? 26 : 24) : 30;
   const size_t tiles = ((size_t)d.W + tw - 1) / tw * ((size_t)(d.H + 7) / 8);
