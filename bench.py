@@ -720,6 +720,10 @@ PROFILE_CASES = {
     "mesh8": (lambda synth: synth.mesh_problem(8, seed=synth.BASE_SEED), "ARAP mesh, icosphere level 8", False),
     "embedded8": (lambda synth: synth.embedded_problem(8, seed=synth.BASE_SEED),
                   "embedded deformation, icosphere level 8", False),
+    "volume128": (lambda synth: synth.volume_problem(128, 128, 128, 2048, seed=synth.BASE_SEED),
+                  "volumetric ARAP, 128^3 voxels", False),
+    "warpgraph1024": (lambda synth: synth.warp_graph_from_grid(synth.warp_problem(1024, 1024, 64, seed=synth.BASE_SEED)),
+                      "ARAP warp 1024^2 written on an explicit graph", False),
     "warp2048_f64": (lambda synth: synth.warp_problem(2048, 2048, 256, seed=synth.BASE_SEED),
                      "ARAP warp 2048^2, float64 solver", True),
     "mesh8_f64": (lambda synth: synth.mesh_problem(8, seed=synth.BASE_SEED),
