@@ -165,8 +165,10 @@ def dist_env():
 
 
 def oracle_sample(seconds_hint: float = 15.0):
-    """The FP64 oracle as it stands on a bounded sample of the workload: one GN
-    outer iteration (J assembly + 20 PCG iterations) of the 1024 x 1024 warp."""
+    """The FP64 oracle as it stands on a bounded sample of the workload: the
+    first GN outer iterations (J assembly + 20 PCG iterations each) of the
+    1024 x 1024 warp, from the bench's start point.  Also returns the oracle's
+    energies E(x_0) .. E(x_n) of those iterations (compared with the GPU's)."""
     import numpy as np
     import oracle
     from paper_1604_06525_gb300 import synth
@@ -174,16 +176,19 @@ def oracle_sample(seconds_hint: float = 15.0):
     e = oracle.make_energy(prob)
     x = prob.x0.reshape(-1).astype(np.float64)
     n_outer = 0
+    hist = []
     t0 = time.perf_counter()
     while True:
-        oracle.gauss_newton(e, x, 1, INNER)
+        res = oracle.gauss_newton(e, x, 1, INNER)
+        x = res.x
+        hist = hist[:-1] + res.E_history if hist else list(res.E_history)
         n_outer += 1
         if time.perf_counter() - t0 >= seconds_hint or n_outer >= 4:
             break
     dt = time.perf_counter() - t0
     return {"value": n_outer * INNER / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n_outer} GN outer iteration(s) (explicit CSR J assembly + {INNER} PCG) of the "
-                      f"{W_BENCH}x{H_BENCH} ARAP warp, float64, numpy/scipy single thread"}
+                      f"{W_BENCH}x{H_BENCH} ARAP warp, float64, numpy/scipy single thread"}, hist
 
 
 def run_reference(args):
@@ -702,7 +707,13 @@ def run_ours(args):
         "also": extra,
     }
     if rank == 0 and world == 1 and not args.no_extras:
-        line["cpu_baseline"] = oracle_sample()
+        line["cpu_baseline"], e_ref = oracle_sample()
+        # the error of the bench's own solve against the float64 oracle over the
+        # outer iterations the oracle sample ran (same start point)
+        e_gpu = reps[-1]["E_history"][:len(e_ref)]
+        line["oracle_check"] = {"outer_iterations": len(e_ref) - 1, "E_oracle": e_ref, "E_gpu": e_gpu,
+                                "E_rel_err_max": max(abs(a - b) / max(abs(b), 1e-30) for a, b in zip(e_gpu, e_ref)),
+                                "tolerance": 1e-4}
     if rank == 0:
         print(json.dumps(line), flush=True)
     gp.close()
