@@ -530,7 +530,11 @@ def run_ours(args):
 
     prob = synth.warp_problem(W_BENCH, H_BENCH, HANDLES, seed=synth.BASE_SEED)
     gp = api.Problem(prob)
-    chunking, _ = gp.autotune()          # work granularity (outside the timed region)
+    if args.chunking is None:
+        chunking, _ = gp.autotune()      # work granularity (outside the timed region)
+    else:
+        chunking = args.chunking         # fixed (profiler runs: ncu's serialised timing misleads the autotuner)
+        gp.set_chunking(chunking)
     x0 = gp.x.clone()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -699,7 +703,8 @@ def run_ours(args):
                                f"GN {OUTER} outer x {INNER} PCG, Jacobi, matrix-free, one CUDA graph per solve",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed between steps (512 MB write)", "precision": "f32 vectors, f64 dots/energies",
-                   "tiles_per_block": chunking,
+                   "chunking": chunking,
+                   "chunking_meaning": "n > 0: n tiles per block; n < 0: balanced over -n blocks per SM",
                    "E_final": E_final, "wall_s": wall},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": roof[dom]["achieved"], "peak": peak,
                      "unit": "GB/s", "frac": roof[dom]["frac"],
@@ -783,6 +788,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="headline workload only: skip the secondary workloads and the CPU baseline "
                          "(for profiler runs; the timed region is unchanged)")
+    ap.add_argument("--chunking", type=int, default=None,
+                    help="work granularity of the headline problem (as opt_problem_set_chunking) instead of "
+                         "autotuning it; for ncu captures, pass the value the plain run chose")
     ap.add_argument("--profile", choices=sorted(PROFILE_CASES),
                     help="run one small profiling workload (for ncu captures) instead of the benchmark")
     args = ap.parse_args()

@@ -313,7 +313,8 @@ opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, flo
 /* Work granularity of the problem's kernels.  units_per_block > 0: that many
  * consecutive tiles (grid) or 256-vertex tiles and units_per_block * 256 edges
  * (graph) per block; units_per_block < 0: the work split into
- * (-units_per_block) x (number of SMs) balanced blocks (grid; graph: 4x that);
+ * (-units_per_block) x (number of SMs) balanced blocks (grid; graph: 4x that;
+ * sizes differ by at most one unit, the larger blocks first);
  * 0 restores the default (balanced, 2 blocks per SM for grids, 8 for graphs).
  * Drops the cached solve graph.  Synchronises the device. */
 opt_status opt_problem_set_chunking(opt_problem* prob, int32_t units_per_block);
