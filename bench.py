@@ -432,7 +432,7 @@ def bench_batched(api, synth, torch, flush, n=512, outer=10, inner=10):
             "max_rel_diff_E_final_default_chunking_vs_plain": rel0}
 
 
-def bench_serving(api, synth, torch, n_req=400, rate=2000.0, budget=120 << 30):
+def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30):
     """Serving form: Poisson arrivals (mean `rate` per second), 50/50 mix of
     ARAP warps (square, side log-uniform in [64, 1024]) and icosphere mesh
     deformations (levels 4-6, 2.5k-41k vertices), each LM <= 10 outer x 10 PCG
@@ -692,7 +692,7 @@ def run_ours(args):
         extra["float64_variant"] = bench_fp64(api, synth, torch, flush, ms_per_step)
 
         extra["batched_512_warps_gn10x10"] = bench_batched(api, synth, torch, flush)
-        extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch)
+        extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch, n_req=args.serving_requests)
 
     launches_per_step = 2 + OUTER * (2 + 2 * INNER)
     line = {
@@ -788,6 +788,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="headline workload only: skip the secondary workloads and the CPU baseline "
                          "(for profiler runs; the timed region is unchanged)")
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="requests in the serving workload (Poisson arrivals at 2,000 / s; 2,000 = 1 s of arrivals)")
     ap.add_argument("--chunking", type=int, default=None,
                     help="work granularity of the headline problem (as opt_problem_set_chunking) instead of "
                          "autotuning it; for ncu captures, pass the value the plain run chose")
