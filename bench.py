@@ -272,8 +272,8 @@ def roofline_beyond_l2(api, synth, torch, peak):
     gp = api.Problem(pp)
     res["poisson_4096x4096x4"] = {
         "unit_of_work": "free pixel", "units": free,
-        "kernels": kernel_roofline(gp, (("k_poisson_init", BYTES_INIT_POISSON, OUTER),
-                                        ("k_poisson_apply", BYTES_APPLY_POISSON, OUTER * INNER),
+        "kernels": kernel_roofline(gp, (("k_poisson_init_wide", BYTES_INIT_POISSON, OUTER),
+                                        ("k_poisson_apply_wide", BYTES_APPLY_POISSON, OUTER * INNER),
                                         ("k_grid_update<4>", BYTES_UPDATE_POISSON, OUTER * INNER)), free, peak)}
     gp.close()
     del pp
