@@ -432,14 +432,16 @@ def bench_batched(api, synth, torch, flush, n=512, outer=10, inner=10):
             "max_rel_diff_E_final_default_chunking_vs_plain": rel0}
 
 
-def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30):
+def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, max_active=256):
     """Serving form: Poisson arrivals (mean `rate` per second), 50/50 mix of
     ARAP warps (square, side log-uniform in [64, 1024]) and icosphere mesh
     deformations (levels 4-6, 2.5k-41k vertices), each LM <= 10 outer x 10 PCG
     to relative energy change 1e-6, admission by an HBM budget of 120 GB.
     Requests reuse a pool of 24 warp templates and 3 meshes (fresh unknowns per
-    request).  Served = continuous batching (opt_server_*); plain = one
-    request at a time in arrival order (opt_solve_lm, direct launches)."""
+    request).  Served = continuous batching (opt_server_*), admission by the
+    budget alone and, second, with at most `max_active` requests admitted at
+    once; plain = one request at a time in arrival order (opt_solve_lm, direct
+    launches)."""
     import numpy as np
     rng = np.random.default_rng(synth.BASE_SEED + 5)
     sides = synth.batch_sides(24, 64, 1024, seed=synth.BASE_SEED + 6)
@@ -452,40 +454,44 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30):
     arrivals = synth.arrival_times(n_req, rate, seed=synth.BASE_SEED + 7)
     OUT, INN, TOL = 10, 10, 1e-6
 
-    srv = api.Server(budget, outer=OUT, inner=INN, rel_tol=TOL)
-    # warm-up: one request of each template kind
-    for t in (0, len(warps)):
-        tk = srv.submit_template(templates[t])
-        while srv.poll(tk) is None:
-            srv.step()
-    torch.cuda.synchronize()
-    done, lat, nxt, rounds = {}, {}, 0, 0
-    pending = {}
-    t0 = time.perf_counter()
-    while len(done) < n_req:
-        now = time.perf_counter() - t0
-        while nxt < n_req and arrivals[nxt] <= now:
-            pending[srv.submit_template(templates[pick[nxt]])] = nxt
-            nxt += 1
-        if pending:
-            srv.step()
-            rounds += 1
-            tnow = time.perf_counter() - t0
-            for tk in list(pending):
-                r = srv.poll(tk)
-                if r is not None:
-                    i = pending.pop(tk)
-                    done[i] = r[0]
-                    lat[i] = tnow - arrivals[i]
-        else:
-            time.sleep(max(0.0, min(1e-3, arrivals[nxt] - now)))
-    span_served = max(arrivals[i] + lat[i] for i in range(n_req)) - arrivals[0]
-    srv.close()
+    def served(cap):
+        srv = api.Server(budget, outer=OUT, inner=INN, rel_tol=TOL, max_active=cap)
+        # warm-up: one request of each template kind
+        for t in (0, len(warps)):
+            tk = srv.submit_template(templates[t])
+            while srv.poll(tk) is None:
+                srv.step()
+        torch.cuda.synchronize()
+        done, lat, nxt, rounds = {}, {}, 0, 0
+        pending = {}
+        t0 = time.perf_counter()
+        while len(done) < n_req:
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrivals[nxt] <= now:
+                pending[srv.submit_template(templates[pick[nxt]])] = nxt
+                nxt += 1
+            if pending:
+                srv.step()
+                rounds += 1
+                tnow = time.perf_counter() - t0
+                for tk in list(pending):
+                    r = srv.poll(tk)
+                    if r is not None:
+                        i = pending.pop(tk)
+                        done[i] = r[0]
+                        lat[i] = tnow - arrivals[i]
+            else:
+                time.sleep(max(0.0, min(1e-3, arrivals[nxt] - now)))
+        span = max(arrivals[i] + lat[i] for i in range(n_req)) - arrivals[0]
+        srv.close()
+        return done, list(lat.values()), span, rounds
+
+    done, L, span_served, rounds = served(0)
+    done_c, LC, span_capped, rounds_c = served(max_active)
 
     # plain: a single worker, requests in arrival order
     plain_lat, plain_done = {}, {}
     probs = warps + meshes
-    solvers = {}
     t0 = time.perf_counter()
     for i in range(n_req):
         now = time.perf_counter() - t0
@@ -497,10 +503,13 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30):
         plain_done[i] = r
         plain_lat[i] = time.perf_counter() - t0 - arrivals[i]
     span_plain = max(arrivals[i] + plain_lat[i] for i in range(n_req)) - arrivals[0]
-    diff = max(abs(done[i]["E_final"] - plain_done[i]["E_final"]) / max(abs(plain_done[i]["E_final"]), 1e-30)
-               for i in range(n_req))
+
+    def maxdiff(d):
+        return max(abs(d[i]["E_final"] - plain_done[i]["E_final"]) / max(abs(plain_done[i]["E_final"]), 1e-30)
+                   for i in range(n_req))
+
     same_outer = sum(done[i]["outer_done"] == plain_done[i]["outer_done"] for i in range(n_req))
-    L = list(lat.values())
+    same_outer_c = sum(done_c[i]["outer_done"] == plain_done[i]["outer_done"] for i in range(n_req))
     PL = list(plain_lat.values())
     for tpl in templates:
         del tpl
@@ -508,10 +517,16 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30):
     return {"requests": n_req, "rate_per_s": rate, "budget_gb": budget / 2 ** 30, "rounds": rounds,
             "served_solves_per_s": n_req / span_served, "served_p50_ms": 1e3 * pct(L, 50),
             "served_p99_ms": 1e3 * pct(L, 99),
+            "capped_max_active": max_active, "capped_rounds": rounds_c,
+            "capped_solves_per_s": n_req / span_capped, "capped_p50_ms": 1e3 * pct(LC, 50),
+            "capped_p99_ms": 1e3 * pct(LC, 99),
             "plain_solves_per_s": n_req / span_plain, "plain_p50_ms": 1e3 * pct(PL, 50),
             "plain_p99_ms": 1e3 * pct(PL, 99),
             "speedup_solves_per_s": span_plain / span_served,
-            "max_rel_diff_E_final_served_vs_plain": diff, "same_outer_count": same_outer}
+            "capped_speedup_solves_per_s": span_plain / span_capped,
+            "max_rel_diff_E_final_served_vs_plain": maxdiff(done),
+            "max_rel_diff_E_final_capped_vs_plain": maxdiff(done_c),
+            "same_outer_count": same_outer, "capped_same_outer_count": same_outer_c}
 
 
 def run_ours(args):
@@ -692,7 +707,8 @@ def run_ours(args):
         extra["float64_variant"] = bench_fp64(api, synth, torch, flush, ms_per_step)
 
         extra["batched_512_warps_gn10x10"] = bench_batched(api, synth, torch, flush)
-        extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch, n_req=args.serving_requests)
+        extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch, n_req=args.serving_requests,
+                                                          max_active=args.serving_max_active)
 
     launches_per_step = 2 + OUTER * (2 + 2 * INNER)
     line = {
@@ -790,6 +806,8 @@ def main():
                          "(for profiler runs; the timed region is unchanged)")
     ap.add_argument("--serving-requests", type=int, default=2000,
                     help="requests in the serving workload (Poisson arrivals at 2,000 / s; 2,000 = 1 s of arrivals)")
+    ap.add_argument("--serving-max-active", type=int, default=256,
+                    help="cap on requests admitted at once for the capped serving run")
     ap.add_argument("--chunking", type=int, default=None,
                     help="work granularity of the headline problem (as opt_problem_set_chunking) instead of "
                          "autotuning it; for ncu captures, pass the value the plain run chose")

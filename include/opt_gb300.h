@@ -400,6 +400,14 @@ opt_status opt_server_submit_graph(opt_server* server, const opt_graph_desc* des
  * (host, may be NULL) receive the counts after the step. */
 opt_status opt_server_step(opt_server* server, int32_t* n_active, int32_t* n_queued);
 
+/* Caps the number of requests admitted at once (0, the default: admission by
+ * the budget alone).  Admission stays in arrival order; under a cap, requests
+ * that arrive faster than they are served wait in the queue instead of all
+ * sharing the device, so the early ones finish first (a FIFO of batches).
+ * Takes effect at the next opt_server_step.  OPT_ERR_INVALID_ARG on a NULL
+ * server or a negative cap. */
+opt_status opt_server_set_max_active(opt_server* server, int32_t max_active);
+
 /* OPT_OK and the report (E_history, if not NULL, receives outer_done + 1
  * values) once the request finished; the ticket is then forgotten.
  * OPT_ERR_NOT_READY while queued or running; OPT_ERR_INVALID_ARG for an

@@ -111,6 +111,7 @@ _SIGNATURES = [
     ("opt_server_submit_graph", c_int32, [c_void_p, POINTER(GraphDesc), POINTER(ctypes.c_uint64)]),
     ("opt_server_step", c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
     ("opt_server_poll", c_int32, [c_void_p, ctypes.c_uint64, POINTER(Report)]),
+    ("opt_server_set_max_active", c_int32, [c_void_p, c_int32]),
     ("opt_warp_apply_jtj_noalloc", c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                              c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p,
                                              c_void_p]),
@@ -623,10 +624,11 @@ class Server:
     """Continuous-batching LM server (opt_server_* in the C ABI).  submit()
     takes a synth problem instance, uploads its arrays and queues it; step()
     admits under the HBM budget and advances every admitted request by one LM
-    outer iteration; poll() returns the report once the request finished."""
+    outer iteration; poll() returns the report once the request finished.
+    max_active > 0 caps the requests admitted at once (opt_server_set_max_active)."""
 
     def __init__(self, hbm_budget_bytes: int, outer: int = 10, inner: int = 10, rel_tol: float = 1e-6,
-                 device: str = "cuda", **kw):
+                 device: str = "cuda", max_active: int = 0, **kw):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -638,6 +640,11 @@ class Server:
         _check(self.lib.opt_server_create(hbm_budget_bytes, ctypes.byref(p), ctypes.byref(h)), "opt_server_create")
         self.h = h
         self.inflight = {}
+        if max_active:
+            self.set_max_active(max_active)
+
+    def set_max_active(self, max_active: int):
+        _check(self.lib.opt_server_set_max_active(self.h, max_active), "opt_server_set_max_active")
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

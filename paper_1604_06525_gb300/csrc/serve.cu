@@ -73,6 +73,7 @@ size_t estimate_graph(const opt_graph_desc& d) {
 
 struct opt_server {
   size_t budget = 0, used = 0;
+  int max_active = 0;                // 0: admission by the budget alone
   opt_solve_params prm{};
   cudaStream_t st = nullptr;
   std::mutex mu;
@@ -178,7 +179,8 @@ opt_status opt_server_step(opt_server* s, int32_t* n_active, int32_t* n_queued) 
   std::vector<ServeReq*> admit;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    while (!s->queue.empty() && s->used + s->queue.front()->est_bytes <= s->budget) {
+    while (!s->queue.empty() && s->used + s->queue.front()->est_bytes <= s->budget &&
+           (s->max_active <= 0 || s->active.size() + admit.size() < (size_t)s->max_active)) {
       ServeReq* r = s->queue.front();
       s->queue.pop_front();
       s->used += r->est_bytes;
@@ -258,6 +260,13 @@ opt_status opt_server_step(opt_server* s, int32_t* n_active, int32_t* n_queued) 
     std::lock_guard<std::mutex> lk(s->mu);
     *n_queued = (int32_t)s->queue.size();
   }
+  return OPT_OK;
+}
+
+opt_status opt_server_set_max_active(opt_server* s, int32_t max_active) {
+  if (!s || max_active < 0) return OPT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->max_active = max_active;
   return OPT_OK;
 }
 

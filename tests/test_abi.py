@@ -66,6 +66,7 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert lib.opt_solve_lm_f64(None, None, None) == 1
     assert lib.opt_apply_jtj_f64(None, None, None, ctypes.c_double(0.0), None) == 1
     assert lib.opt_problem_destroy_f64(None) == 0
+    assert lib.opt_server_set_max_active(None, 4) == 1
 
 
 def test_library_is_built_for_sm103a():

@@ -114,6 +114,40 @@ def test_serve_budget_limits_admission(api):
     srv.close()
 
 
+def test_serve_max_active_caps_admission_in_arrival_order(api):
+    """max_active = 3 under an ample budget: never more than three requests
+    admitted, admission in arrival order (the requests admitted so far, done
+    or active, are always the first ones submitted), every result equal to
+    its solo solve."""
+    probs = requests()
+    refs = [solo(api, p) for p in probs]
+    srv = api.Server(4 << 30, outer=OUTER, inner=INNER, rel_tol=REL_TOL, max_active=3)
+    tickets = [srv.submit(p) for p in probs]
+    done, max_active = {}, 0
+    for _ in range(400):
+        active, queued = srv.step()
+        max_active = max(max_active, active)
+        for t in tickets:
+            if t not in done:
+                r = srv.poll(t)
+                if r is not None:
+                    done[t] = r
+        admitted = len(tickets) - queued
+        assert len(done) + active == admitted
+        assert all(tickets.index(t) < admitted for t in done)
+        if len(done) == len(tickets):
+            break
+    assert len(done) == len(tickets)
+    assert max_active == 3
+    for p, t, (ref, xref) in zip(probs, tickets, refs):
+        rep, x = done[t]
+        check_same(p, rep, x, ref, xref)
+    with pytest.raises(api.OptError) as ei:
+        srv.set_max_active(-1)
+    assert ei.value.status == 1
+    srv.close()
+
+
 def test_serve_rejects_oversize_and_reports_planning_errors(api):
     srv = api.Server(1 << 20, outer=OUTER, inner=INNER)
     with pytest.raises(api.OptError) as ei:
