@@ -261,7 +261,7 @@ def roofline_for(api, synth, torch, W, H, peak, iters=20):
 
 
 def roofline_beyond_l2(api, synth, torch, peak):
-    """The added sizes well beyond L2 (where the HBM-fraction target is
+    """The added sizes well beyond L2 (where the HBM-fraction target
     applies): ARAP warp 4096^2, Poisson 4096^2 x 4 (free pixels), icosphere
     level 9 (vertices: ARAP mesh and embedded deformation), 128^3 voxels."""
     res = {}
