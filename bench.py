@@ -767,6 +767,12 @@ PROFILE_CASES = {
                      "ARAP warp 2048^2, float64 solver", True),
     "mesh8_f64": (lambda synth: synth.mesh_problem(8, seed=synth.BASE_SEED),
                   "ARAP mesh, icosphere level 8, float64 solver", True),
+    # materialized forms: one GN outer iteration with 3 PCG iterations (evalJ,
+    # J^T values / J^T J assembly, then the sparse products)
+    "warp1024_csr": (lambda synth: synth.warp_problem(1024, 1024, 64, seed=synth.BASE_SEED),
+                     "ARAP warp 1024^2, CSR J and J^T (materialized = 1)", False, 1),
+    "warp1024_jtj": (lambda synth: synth.warp_problem(1024, 1024, 64, seed=synth.BASE_SEED),
+                     "ARAP warp 1024^2, J^T J assembled (materialized = 2)", False, 2),
 }
 
 
@@ -777,20 +783,29 @@ def run_profile_case(name):
     from paper_1604_06525_gb300 import build, api, synth
     build.build()
     api.load_library()
-    builder, desc, f64 = PROFILE_CASES[name]
+    builder, desc, f64 = PROFILE_CASES[name][:3]
+    materialized = PROFILE_CASES[name][3] if len(PROFILE_CASES[name]) > 3 else 0
     if f64:
         gp = api.ProblemF64(builder(synth))
         chunking = None
     else:
         gp = api.Problem(builder(synth))
         chunking, _ = gp.autotune()
+    if materialized:
+        x0 = gp.x.clone()
+        gp.solve_gn(1, 3, materialized=materialized)          # structure built, graph captured
+        gp.x.copy_(x0)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("profile")
-    ms = gp.profile_pcg(3)
+    if materialized:
+        rep = gp.solve_gn(1, 3, materialized=materialized)
+        ms = rep["ms"]
+    else:
+        ms = gp.profile_pcg(3)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     print(json.dumps({"profile_case": name, "workload": desc, "chunking": chunking,
-                      "ms_init_apply_update": ms}), flush=True)
+                      "ms_solve" if materialized else "ms_init_apply_update": ms}), flush=True)
     gp.close()
     return 0
 
