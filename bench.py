@@ -601,7 +601,9 @@ def run_ours(args):
     roof, _ = roofline_for(api, synth, torch, W_BENCH, H_BENCH, peak)
     dom = max(roof, key=lambda k: roof[k]["ms"] * roof[k]["launches_per_solve"])   # largest share of a solve
     roof_big, extra = {}, {}
-    if not args.no_extras:
+    # the secondary workloads are single-GPU measurements: taken at N = 1 only,
+    # so a replica run holds its GPUs for the headline alone
+    if not args.no_extras and world == 1:
         roof_big = roofline_beyond_l2(api, synth, torch, peak)
 
         # secondary workloads: matrix-free vs materialized J (Sec. 8.3) on the
