@@ -775,7 +775,39 @@ PROFILE_CASES = {
                      "ARAP warp 1024^2, CSR J and J^T (materialized = 1)", False, 1),
     "warp1024_jtj": (lambda synth: synth.warp_problem(1024, 1024, 64, seed=synth.BASE_SEED),
                      "ARAP warp 1024^2, J^T J assembled (materialized = 2)", False, 2),
+    # the batched form: 512 uneven warps (sides 32..512), one autotuned batch,
+    # one GN outer iteration x 3 PCG iterations in the range (run_profile_batch)
+    "batch512": (None, "512 warps, sides log-uniform in [32, 512], batched", False),
 }
+
+
+def run_profile_batch():
+    """The batched form's launches: 512 uneven warps in one autotuned batch,
+    one GN outer iteration with 3 PCG iterations inside the NVTX range."""
+    import torch
+    from paper_1604_06525_gb300 import build, api, synth
+    build.build()
+    api.load_library()
+    probs = synth.batch_warps(512, 32, 512, seed=synth.BASE_SEED)
+    members = [api.Problem(p) for p in probs]
+    x0s = [m.x.clone() for m in members]
+    batch = api.Batch(members)
+    chosen, _ = batch.autotune(inner=4)
+    for m, x in zip(members, x0s):
+        m.x.copy_(x)
+    batch.solve_gn(1, 3)                      # graph captured
+    for m, x in zip(members, x0s):
+        m.x.copy_(x)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("profile")
+    _, ms = batch.solve_gn(1, 3)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_case": "batch512", "problems": len(probs),
+                      "pixels": int(sum(p.W * p.H for p in probs)), "tiles_per_chunk": chosen,
+                      "ms_solve": ms}), flush=True)
+    batch.close()
+    return 0
 
 
 def run_profile_case(name):
@@ -785,6 +817,8 @@ def run_profile_case(name):
     from paper_1604_06525_gb300 import build, api, synth
     build.build()
     api.load_library()
+    if name == "batch512":
+        return run_profile_batch()
     builder, desc, f64 = PROFILE_CASES[name][:3]
     materialized = PROFILE_CASES[name][3] if len(PROFILE_CASES[name]) > 3 else 0
     if f64:
