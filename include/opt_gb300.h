@@ -397,8 +397,18 @@ opt_status opt_server_submit_graph(opt_server* server, const opt_graph_desc* des
 
 /* Admits, runs one LM outer iteration of every admitted request, retires the
  * finished ones (synchronises the server's stream).  n_active / n_queued
- * (host, may be NULL) receive the counts after the step. */
+ * (host, may be NULL) receive the counts after the step.  If rebuilding the
+ * batch after an admission or a retirement fails (e.g. OPT_ERR_OOM), or the
+ * round itself fails, every request active at that moment ends with that
+ * status (opt_server_poll returns it), its memory returns to the budget, the
+ * step returns the status, and later steps go on with the queue. */
 opt_status opt_server_step(opt_server* server, int32_t* n_active, int32_t* n_queued);
+
+/* Failure-path test hook (host only, no device work): the next batch rebuild
+ * of opt_server_step fails with `status` instead of planning the batch, as an
+ * allocation failure would.  OPT_ERR_INVALID_ARG for a NULL server or
+ * status == OPT_OK. */
+opt_status opt_server_inject_rebuild_failure(opt_server* server, opt_status status);
 
 /* Caps the number of requests admitted at once (0, the default: admission by
  * the budget alone).  Admission stays in arrival order; under a cap, requests
@@ -420,14 +430,22 @@ opt_status opt_server_poll(opt_server* server, uint64_t ticket, opt_report* repo
  * budget that must not stall on an allocation, and host applications or
  * plug-in hosts that own all device memory and hand a component only its
  * buffers.  Computes q = J^T J p (lambda = 0) for an OPT_ARAP_WARP_2D energy
- * at x, exactly as opt_apply_jtj does, and p.q in float64, without any
+ * at x -- the product opt_apply_jtj computes, equal to it within 1e-5
+ * relative error but not bitwise (cos / sin are evaluated per call and the
+ * sums are rounded in another order) -- and p.q in float64, without any
  * allocation: its only scratch (float64 reduction partials, an arrival
  * counter) is a file-scope device array of 262,400 bytes that every device
  * loading the library holds until the process exits.
  *   x        device, 3*W*H floats: dx, dy, theta planes (row-major, y*W + x)
  *   urshape  device, 2*W*H floats: UrShape x, y planes
  *   mask     device, W*H bytes (nonzero = excluded) or NULL
- *   handle_idx device, n_handles pixel indices (may be NULL if n_handles = 0)
+ *   handle_idx device, n_handles pixel indices y*W + x in any order (may be
+ *            NULL if n_handles = 0).  Unlike opt_problem_create_grid, repeated
+ *            indices are not rejected: each entry adds its own fit residual
+ *            (a pixel listed twice gets twice the fit weight).  Every block
+ *            scans the whole list, so the cost grows as tiles x n_handles:
+ *            cheap for the few handles of an interactive warp, about 0.7 G
+ *            index loads per call at 2048 x 2048 with 40k handles.
  *   p        device, 3*W*H floats (input direction)
  *   q        device, 3*W*H floats (output)
  *   pq       device, one double (output p.q) or NULL

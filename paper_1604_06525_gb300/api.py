@@ -112,6 +112,7 @@ _SIGNATURES = [
     ("opt_server_step", c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
     ("opt_server_poll", c_int32, [c_void_p, ctypes.c_uint64, POINTER(Report)]),
     ("opt_server_set_max_active", c_int32, [c_void_p, c_int32]),
+    ("opt_server_inject_rebuild_failure", c_int32, [c_void_p, c_int32]),
     ("opt_warp_apply_jtj_noalloc", c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                              c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p,
                                              c_void_p]),
@@ -645,6 +646,16 @@ class Server:
 
     def set_max_active(self, max_active: int):
         _check(self.lib.opt_server_set_max_active(self.h, max_active), "opt_server_set_max_active")
+
+    def inject_rebuild_failure(self, status: int):
+        """Test hook: the next batch rebuild fails with `status` (host only)."""
+        _check(self.lib.opt_server_inject_rebuild_failure(self.h, status), "opt_server_inject_rebuild_failure")
+
+    def step_status(self):
+        """As step(), but returns the status code instead of raising."""
+        a, q = c_int32(), c_int32()
+        st = self.lib.opt_server_step(self.h, ctypes.byref(a), ctypes.byref(q))
+        return st, a.value, q.value
 
     def close(self):
         if getattr(self, "h", None) and self.h.value:

@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(NT) k_warp_apply_noalloc(
   unsigned int* counter = reinterpret_cast<unsigned int*>(scratch);
   double* part = reinterpret_cast<double*>(scratch + kHeaderBytes);
   __shared__ float sp[3][HH][HW], scs[HH][HW], ssn[HH][HW], sux[HH][HW], suy[HH][HW];
-  __shared__ unsigned char sv[HH][HW], sfit[TH][TW];
+  __shared__ unsigned char sv[HH][HW];
+  __shared__ int sfit[TH][TW];      // handle entries on each pixel of the tile
   const long long pl = (long long)W * H;
   const int ntx = (W + TW - 1) / TW;
   const int x0 = (blockIdx.x % ntx) * TW, y0 = (blockIdx.x / ntx) * TH;
@@ -79,10 +80,12 @@ __global__ void __launch_bounds__(NT) k_warp_apply_noalloc(
     scs[hy][hx] = cs; ssn[hy][hx] = sn; sux[hy][hx] = ux; suy[hy][hx] = uy; sv[hy][hx] = v;
   }
   __syncthreads();
+  // every block scans the whole handle list (O(tiles x n_handles) loads);
+  // a repeated index counts once per entry, as a sum of squares over entries
   for (int h = threadIdx.x; h < nh; h += NT) {
     const int pix = hidx[h];
     const int hx = pix % W - x0, hy = pix / W - y0;
-    if (hx >= 0 && hx < TW && hy >= 0 && hy < TH) sfit[hy][hx] = 1;
+    if (hx >= 0 && hx < TW && hy >= 0 && hy < TH) atomicAdd(&sfit[hy][hx], 1);
   }
   __syncthreads();
   float acc = 0.f;
@@ -110,7 +113,11 @@ __global__ void __launch_bounds__(NT) k_warp_apply_noalloc(
         qx -= sw * (sw * (pxj - pxi) + hx_ * ptj);
         qy -= sw * (sw * (pyj - pyi) + hy_ * ptj);
       }
-      if (sfit[ty][tx]) { qx += wfit * pxi; qy += wfit * pyi; }
+      if (sfit[ty][tx]) {
+        const float wf = wfit * (float)sfit[ty][tx];
+        qx += wf * pxi;
+        qy += wf * pyi;
+      }
     }
     q[i] = qx; q[pl + i] = qy; q[2 * pl + i] = qt;
     acc = pxi * qx + pyi * qy + pti * qt;

@@ -83,6 +83,7 @@ struct opt_server {
   uint64_t next_ticket = 1;
   opt_batch* batch = nullptr;
   bool dirty = true;
+  opt_status inject = OPT_OK;        // test hook: the next batch rebuild fails with this status
   std::vector<Scalars> sbuf;
 
   ~opt_server() {
@@ -122,6 +123,23 @@ opt_status write_back(opt_problem* pb, cudaStream_t st) {
 
 opt_status copy_in(opt_problem* pb, cudaStream_t st) {
   return copy_planes_in(pb, pb->x, pb->user_x, pb->nx, st);
+}
+
+// A rebuild or a round failed: every active request ends with `st` (its
+// memory returns to the budget) and the batch is dropped, so the next step
+// starts over from the queue instead of retrying the same rebuild forever.
+opt_status fail_active(opt_server* s, opt_status st) {
+  cudaStreamSynchronize(s->st);
+  (void)cudaGetLastError();
+  if (s->batch) {
+    opt_batch_destroy(s->batch);
+    s->batch = nullptr;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (ServeReq* r : s->active) finish(s, r, st);
+  s->active.clear();
+  s->dirty = true;
+  return st;
 }
 
 }  // namespace
@@ -175,6 +193,14 @@ opt_status opt_server_submit_graph(opt_server* s, const opt_graph_desc* d, uint6
 
 opt_status opt_server_step(opt_server* s, int32_t* n_active, int32_t* n_queued) {
   if (!s) return OPT_ERR_INVALID_ARG;
+  auto counts = [&](opt_status st) {
+    if (n_active) *n_active = (int32_t)s->active.size();
+    if (n_queued) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      *n_queued = (int32_t)s->queue.size();
+    }
+    return st;
+  };
   // 1. admission in arrival order under the budget
   std::vector<ServeReq*> admit;
   {
@@ -215,17 +241,18 @@ opt_status opt_server_step(opt_server* s, int32_t* n_active, int32_t* n_queued) 
       }
       std::vector<opt_problem*> ps;
       for (ServeReq* r : s->active) ps.push_back(r->pb);
-      opt_status st = opt_batch_create(ps.data(), (int)ps.size(), &s->batch);
-      if (st != OPT_OK) return st;
-      st = batch_prepare_round(s->batch, s->prm);
-      if (st != OPT_OK) return st;
+      opt_status st = s->inject;
+      s->inject = OPT_OK;
+      if (st == OPT_OK) st = opt_batch_create(ps.data(), (int)ps.size(), &s->batch);
+      if (st == OPT_OK) st = batch_prepare_round(s->batch, s->prm);
+      if (st != OPT_OK) return counts(fail_active(s, st));
       s->dirty = false;
     }
     batch_enqueue_lm_round(s->batch, s->prm, s->st);
-    if (cudaGetLastError() != cudaSuccess) return OPT_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return counts(fail_active(s, OPT_ERR_CUDA));
     s->sbuf.resize(s->active.size());
     opt_status st = batch_read_scalars(s->batch, s->sbuf.data(), s->st);
-    if (st != OPT_OK) return st;
+    if (st != OPT_OK) return counts(fail_active(s, st));
     // 3. retire converged / capped members
     std::vector<ServeReq*> keep;
     for (size_t i = 0; i < s->active.size(); ++i) {
@@ -255,11 +282,13 @@ opt_status opt_server_step(opt_server* s, int32_t* n_active, int32_t* n_queued) 
     }
     s->active.swap(keep);
   }
-  if (n_active) *n_active = (int32_t)s->active.size();
-  if (n_queued) {
-    std::lock_guard<std::mutex> lk(s->mu);
-    *n_queued = (int32_t)s->queue.size();
-  }
+  return counts(OPT_OK);
+}
+
+opt_status opt_server_inject_rebuild_failure(opt_server* s, opt_status status) {
+  if (!s || status == OPT_OK) return OPT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->inject = status;
   return OPT_OK;
 }
 

@@ -163,3 +163,42 @@ def test_serve_rejects_oversize_and_reports_planning_errors(api):
         srv.poll(t)
     assert ei.value.status == 1
     srv.close()
+
+
+def test_serve_failed_rebuild_ends_active_requests_and_keeps_serving(api):
+    """A batch rebuild that fails (an out-of-memory made on the host through
+    the server's test hook, no device fault) ends every request active at
+    that moment with the error; their budget is returned, and requests queued
+    afterwards are served normally, equal to their solo solves."""
+    probs = requests()
+    srv = api.Server(4 << 30, outer=OUTER, inner=INNER, rel_tol=REL_TOL)
+    first = [srv.submit(p) for p in probs[:3]]
+    srv.step()                                        # admitted, one outer iteration done
+    srv.inject_rebuild_failure(2)                     # OPT_ERR_OOM at the next rebuild
+    late = srv.submit(probs[3])                       # its admission forces the rebuild
+    st, active, queued = srv.step_status()
+    assert st == 2 and active == 0 and queued == 0
+    for t in first + [late]:
+        with pytest.raises(api.OptError) as ei:
+            srv.poll(t)
+        assert ei.value.status == 2
+    # the server goes on with new requests
+    refs = [solo(api, p) for p in probs[4:7]]
+    tickets = [srv.submit(p) for p in probs[4:7]]
+    done = {}
+    for _ in range(200):
+        srv.step()
+        for t in tickets:
+            if t not in done:
+                r = srv.poll(t)
+                if r is not None:
+                    done[t] = r
+        if len(done) == len(tickets):
+            break
+    assert len(done) == len(tickets)
+    for p, t, (ref, xref) in zip(probs[4:7], tickets, refs):
+        rep, x = done[t]
+        check_same(p, rep, x, ref, xref)
+    with pytest.raises(api.OptError):
+        srv.inject_rebuild_failure(0)
+    srv.close()

@@ -66,3 +66,37 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     assert st == 1
     st = lib.opt_warp_apply_jtj_noalloc(0, 10, 1, 1, None, None, 0, 1.0, 100.0, 1, 1, None, None)
     assert st == 1
+
+
+def test_noalloc_repeated_handles_count_per_entry():
+    """Repeated handle indices (which the planned entry point rejects) each
+    add their own fit residual, as the float64 oracle does with one fit row
+    per handle entry."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import oracle
+    from paper_1604_06525_gb300 import build, api
+    build.build()
+    lib = api.load_library()
+    W, H = 45, 19
+    prob = synth.warp_problem(W, H, 5, seed=8, x0_noise=0.3)
+    prob.handle_idx = np.concatenate([prob.handle_idx, prob.handle_idx[:2], prob.handle_idx[:1]]).astype(np.int32)
+    prob.handle_target = np.concatenate([prob.handle_target, prob.handle_target[:2],
+                                         prob.handle_target[:1]]).astype(np.float32)
+    e = oracle.make_energy(prob)
+    x64 = prob.x0.reshape(-1).astype(np.float64)
+    dev = torch.device("cuda")
+    x = torch.as_tensor(prob.x0, device=dev).contiguous()
+    U = torch.as_tensor(prob.urshape, device=dev).contiguous()
+    hidx = torch.as_tensor(prob.handle_idx, dtype=torch.int32, device=dev)
+    p_np = np.random.default_rng(3).standard_normal(3 * W * H).astype(np.float32)
+    p = torch.as_tensor(p_np, device=dev)
+    q = torch.empty(3 * W * H, dtype=torch.float32, device=dev)
+    st = lib.opt_warp_apply_jtj_noalloc(W, H, x.data_ptr(), U.data_ptr(), None, hidx.data_ptr(),
+                                        int(hidx.numel()), prob.w_reg, prob.w_fit, p.data_ptr(), q.data_ptr(),
+                                        None, None)
+    assert st == 0, api.STATUS.get(st, st)
+    torch.cuda.synchronize()
+    qref = oracle.apply_jtj(e, x64, p_np.astype(np.float64))
+    assert _rel(q.cpu().numpy(), qref) <= TOL
