@@ -131,6 +131,9 @@ class LMResult:
     outer_done: int
     pcg_done: int
     lambda_final: float = 0.0    # damping after the last update
+    E_trial: list = None         # per outer iteration: E(x + d)
+    pred: list = None            # per outer iteration: predicted decrease E - |F + J d|^2
+    rho: list = None             # per outer iteration: gain ratio
 
 
 def levenberg_marquardt(energy, x0, outer: int, inner: int, prm: LMParams = LMParams(),
@@ -143,6 +146,7 @@ def levenberg_marquardt(energy, x0, outer: int, inner: int, prm: LMParams = LMPa
     x = np.asarray(x0, np.float64).reshape(-1).copy()
     lam, nu = prm.lambda0, 2.0
     hist, acc, lams = [], [], []
+    trials, preds, rhos = [], [], []
     total = 0
     k = 0
     while k < outer:
@@ -161,6 +165,9 @@ def levenberg_marquardt(energy, x0, outer: int, inner: int, prm: LMParams = LMPa
         Fl = F + J @ d                          # linear model of the residuals
         pred = E - float(Fl @ Fl)
         rho = (E - E_new) / pred if pred > 0.0 else -np.inf
+        trials.append(E_new)
+        preds.append(pred)
+        rhos.append(rho)
         k += 1
         if rho > prm.eta:
             x = x + d
@@ -176,4 +183,4 @@ def levenberg_marquardt(energy, x0, outer: int, inner: int, prm: LMParams = LMPa
             acc.append(False)
             lam = min(max(lam, prm.lambda_min), prm.lambda_max)
     hist.append(energy.energy(x))
-    return LMResult(x, hist, acc, lams, k, total, lam)
+    return LMResult(x, hist, acc, lams, k, total, lam, trials, preds, rhos)

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(NT) k_ed_init_pull(const MeshProb* __restrict_
   const long long pl = pr.Vp;
   const float sw = pr.s_w, sr = pr.s_r, w = pr.w_reg;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
-  float acc_rz = 0.f, acc_E = 0.f;
+  F2 acc_rz = f2_zero(), acc_E = f2_zero();
   for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
     float xi[NXE];
     load12(pr.vrec, i, xi);
@@ -216,17 +216,15 @@ __global__ void __launch_bounds__(NT) k_ed_init_pull(const MeshProb* __restrict_
       if (pr.lm) pr.dc[k * pl + i] = dcv;
       if (pr.diag_out) pr.diag_out[k * pl + i] = dg;
     }
-    float rz = 0.f;
 #pragma unroll
     for (int c = 0; c < NXE; ++c) {
       const float b = -g[c];
       pr.r[c * pl + i] = b;
       pr.d[c * pl + i] = 0.f;
       if (pr.jtf_out) pr.jtf_out[c * pl + i] = g[c];
-      rz += b * (mv[mplane_e(c)] * b);
+      f2_add_prod(acc_rz, b, __fmul_rn(mv[mplane_e(c)], b));
     }
-    acc_rz += rz;
-    acc_E += e;
+    f2_add(acc_E, e);
   }
   pdl_trigger();
   if (publish_partials(part, blockIdx.x, acc_rz, acc_E, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
@@ -300,7 +298,7 @@ __global__ void __launch_bounds__(NT) k_ed_apply_pull(const MeshProb* __restrict
   const long long pl = pr.Vp;
   const float wreg = pr.w_reg;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
-  float acc = 0.f;
+  F2 acc = f2_zero();
   for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
     float pi[NXE], q[NXE];
     load12(pr.vrec, i, pi);
@@ -353,11 +351,11 @@ __global__ void __launch_bounds__(NT) k_ed_apply_pull(const MeshProb* __restrict
 #pragma unroll
     for (int c = 0; c < NXE; ++c) {
       pr.q[c * pl + i] = q[c];
-      acc += pi[c] * q[c];
+      f2_add_prod(acc, pi[c], q[c]);
     }
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double pq, unused;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
@@ -389,7 +387,7 @@ __global__ void __launch_bounds__(NT) k_ed_update(const MeshProb* __restrict__ p
   float* __restrict__ rr = pr.r;
   const float* __restrict__ qq = pr.q;
   const float* __restrict__ mm = pr.m;
-  float acc = 0.f;
+  F2 acc = f2_zero();
   for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
     // every load before any store
     float pv[NXE], qv[NXE], dv[NXE], rv[NXE], mv[NME];
@@ -406,7 +404,7 @@ __global__ void __launch_bounds__(NT) k_ed_update(const MeshProb* __restrict__ p
     for (int c = 0; c < NXE; ++c) {
       dv[c] = fmaf(alpha, pv[c], dv[c]);
       rv[c] = fmaf(-alpha, qv[c], rv[c]);
-      acc += rv[c] * (mv[mplane_e(c)] * rv[c]);
+      f2_add_prod(acc, rv[c], __fmul_rn(mv[mplane_e(c)], rv[c]));
     }
 #pragma unroll
     for (int c = 0; c < NXE; ++c) {
@@ -415,7 +413,7 @@ __global__ void __launch_bounds__(NT) k_ed_update(const MeshProb* __restrict__ p
     }
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double rz, unused;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, rz, unused);
     if (threadIdx.x == 0) {
@@ -444,8 +442,9 @@ __global__ void __launch_bounds__(NT) k_ed_energy(const MeshProb* __restrict__ p
   if (mode == 1 && s->done) return;
   const long long pl = pr.Vp;
   const float sw = pr.s_w, sr = pr.s_r;
-  float e0 = 0.f, e1 = 0.f;
+  F2 acc0 = f2_zero(), acc1 = f2_zero();
   for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
+    float e0 = 0.f, e1 = 0.f;           // this vertex's residuals
     float xi[NXE], di[NXE];
 #pragma unroll
     for (int c = 0; c < NXE; ++c) {
@@ -500,9 +499,11 @@ __global__ void __launch_bounds__(NT) k_ed_energy(const MeshProb* __restrict__ p
         e1 += l * l;
       }
     }
+    f2_add(acc0, e0);
+    f2_add(acc1, e1);
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, e0, e1, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc0, acc1, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double a, b;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, a, b);
     if (threadIdx.x == 0) {

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(NT) k_wg_init_pull(const MeshProb* __restrict_
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
-  float acc_rz = 0.f, acc_E = 0.f;
+  F2 acc_rz = f2_zero(), acc_E = f2_zero();
   for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
     const float4 xi = pr.vrec[i];
     const float4 gi = __ldg(pr.grec + i);
@@ -114,8 +114,10 @@ __global__ void __launch_bounds__(NT) k_wg_init_pull(const MeshProb* __restrict_
     pr.r[i] = -g0; pr.r[pl + i] = -g1; pr.r[2 * pl + i] = -gt;
     pr.d[i] = 0.f; pr.d[pl + i] = 0.f; pr.d[2 * pl + i] = 0.f;
     if (pr.jtf_out) { pr.jtf_out[i] = g0; pr.jtf_out[pl + i] = g1; pr.jtf_out[2 * pl + i] = gt; }
-    acc_rz += md * (g0 * g0 + g1 * g1) + mt * gt * gt;
-    acc_E += e;
+    f2_add_prod(acc_rz, g0, __fmul_rn(md, g0));
+    f2_add_prod(acc_rz, g1, __fmul_rn(md, g1));
+    f2_add_prod(acc_rz, gt, __fmul_rn(mt, gt));
+    f2_add(acc_E, e);
   }
   pdl_trigger();
   if (publish_partials(part, blockIdx.x, acc_rz, acc_E, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(NT) k_wg_apply_pull(const MeshProb* __restrict
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
-  float acc = 0.f;
+  F2 acc = f2_zero();
   for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
     const float4 pi = pr.vrec[i];
     const float4 gi = __ldg(pr.grec + i);
@@ -231,10 +233,12 @@ __global__ void __launch_bounds__(NT) k_wg_apply_pull(const MeshProb* __restrict
       q1 -= sw * sw * fmaf(Gy, pj.z, pj.y - pi.y);
     }
     pr.q[i] = q0; pr.q[pl + i] = q1; pr.q[2 * pl + i] = qt;
-    acc += pi.x * q0 + pi.y * q1 + pi.z * qt;
+    f2_add_prod(acc, pi.x, q0);
+    f2_add_prod(acc, pi.y, q1);
+    f2_add_prod(acc, pi.z, qt);
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double pq, unused;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
@@ -263,7 +267,7 @@ __global__ void __launch_bounds__(NT) k_wg_update(const MeshProb* __restrict__ p
   const long long pl = pr.Vp;
   const float alpha = s->alpha_f;
   const float* __restrict__ pn = pr.p + (long long)((par + 1) & 1) * 3 * pl;
-  float acc = 0.f;
+  F2 acc = f2_zero();
   const int q0 = ch.begin / 4, q1 = (ch.end + 3) / 4;
   for (int qi = q0 + threadIdx.x; qi < q1; qi += NT) {
     const int v0 = 4 * qi;
@@ -283,14 +287,16 @@ __global__ void __launch_bounds__(NT) k_wg_update(const MeshProb* __restrict__ p
       dv[c].z += alpha * pv[c].z; dv[c].w += alpha * pv[c].w;
       rv[c].x -= alpha * qv[c].x; rv[c].y -= alpha * qv[c].y;
       rv[c].z -= alpha * qv[c].z; rv[c].w -= alpha * qv[c].w;
-      acc += rv[c].x * (m.x * rv[c].x) + rv[c].y * (m.y * rv[c].y) + rv[c].z * (m.z * rv[c].z) +
-             rv[c].w * (m.w * rv[c].w);
+      f2_add_prod(acc, rv[c].x, __fmul_rn(m.x, rv[c].x));
+      f2_add_prod(acc, rv[c].y, __fmul_rn(m.y, rv[c].y));
+      f2_add_prod(acc, rv[c].z, __fmul_rn(m.z, rv[c].z));
+      f2_add_prod(acc, rv[c].w, __fmul_rn(m.w, rv[c].w));
       *reinterpret_cast<float4*>(pr.d + c * pl + v0) = dv[c];
       *reinterpret_cast<float4*>(pr.r + c * pl + v0) = rv[c];
     }
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double rz, unused;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, rz, unused);
     if (threadIdx.x == 0) {
@@ -317,20 +323,22 @@ __global__ void __launch_bounds__(NT) k_wg_energy_v(const MeshProb* __restrict__
   Scalars* s = pr.s;
   if (mode == 1 && s->done) return;
   const long long pl = pr.Vp;
-  float e = 0.f;
+  F2 e = f2_zero();
   for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
     const int h = handle_of2(pr, v);
     if (h < 0) continue;
+    float ev = 0.f;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       float dv = pr.x[c * pl + v];
       if (mode == 1) dv += pr.d[c * pl + v];
       const float f = pr.s_f * (dv - pr.htgt[2 * h + c]);
-      e += f * f;
+      ev += f * f;
     }
+    f2_add(e, ev);
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, e, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+  if (publish_partials(part, blockIdx.x, e, f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double a, b;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, a, b);
     if (threadIdx.x == 0) s->part0 = a;
@@ -348,7 +356,7 @@ __global__ void __launch_bounds__(NT) k_wg_energy_e(const MeshProb* __restrict__
   if (mode == 1 && s->done) return;
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
-  float e0 = 0.f, e1 = 0.f;
+  F2 e0 = f2_zero(), e1 = f2_zero();
   for (int ei = ch.begin + threadIdx.x; ei < ch.end; ei += NT) {
     const int a = pr.e0[ei], b = pr.e1[ei];
     const float vx = pr.U[a] - pr.U[b], vy = pr.U[pl + a] - pr.U[pl + b];
@@ -359,16 +367,16 @@ __global__ void __launch_bounds__(NT) k_wg_energy_e(const MeshProb* __restrict__
     const float Gx = fmaf(sn, vx, cs * vy), Gy = fmaf(sn, vy, -cs * vx);
     const float r0 = sw * (dd0 + (vx + Gy)), r1 = sw * (dd1 + (vy - Gx));
     if (mode == 0) {
-      e0 += r0 * r0 + r1 * r1;
+      f2_add(e0, r0 * r0 + r1 * r1);
     } else {
       const float ea0 = pr.d[a] - pr.d[b], ea1 = pr.d[pl + a] - pr.d[pl + b], t = pr.d[2 * pl + a];
       float sn2, cs2;
       sincosf(th + t, &sn2, &cs2);
       const float G2x = fmaf(sn2, vx, cs2 * vy), G2y = fmaf(sn2, vy, -cs2 * vx);
       const float u0 = sw * ((dd0 + ea0) + (vx + G2y)), u1 = sw * ((dd1 + ea1) + (vy - G2x));
-      e0 += u0 * u0 + u1 * u1;
+      f2_add(e0, u0 * u0 + u1 * u1);
       const float l0 = r0 + sw * fmaf(Gx, t, ea0), l1 = r1 + sw * fmaf(Gy, t, ea1);
-      e1 += l0 * l0 + l1 * l1;
+      f2_add(e1, l0 * l0 + l1 * l1);
     }
   }
   pdl_trigger();

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(NT) k_mesh_init_pull(const MeshProb* __restric
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
-  float acc_rz = 0.f, acc_E = 0.f;
+  F2 acc_rz = f2_zero(), acc_E = f2_zero();
   for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
     float xi[6];
     load_vec(pr.vrec, i, xi);
@@ -205,17 +205,15 @@ __global__ void __launch_bounds__(NT) k_mesh_init_pull(const MeshProb* __restric
       if (pr.lm) pr.dc[k * pl + i] = dcv;
       if (pr.diag_out) pr.diag_out[k * pl + i] = dg[k];
     }
-    float rz = 0.f;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       const float b = -g[c];
       pr.r[c * pl + i] = b;
       pr.d[c * pl + i] = 0.f;
       if (pr.jtf_out) pr.jtf_out[c * pl + i] = g[c];
-      rz += b * (mv[c < 3 ? 0 : c - 2] * b);
+      f2_add_prod(acc_rz, b, __fmul_rn(mv[c < 3 ? 0 : c - 2], b));
     }
-    acc_rz += rz;
-    acc_E += e;
+    f2_add(acc_E, e);
   }
   pdl_trigger();
   if (publish_partials(part, blockIdx.x, acc_rz, acc_E, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
@@ -313,7 +311,7 @@ __global__ void __launch_bounds__(NT, MESH_PULL_MIN_BLOCKS) k_mesh_apply_pull(co
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
-  float acc = 0.f;
+  F2 acc = f2_zero();
   for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
     int o0 = 0, o1 = 0, n0 = 0, n1 = 0;
     int jo[KB], ji[KB];
@@ -392,11 +390,11 @@ __global__ void __launch_bounds__(NT, MESH_PULL_MIN_BLOCKS) k_mesh_apply_pull(co
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       pr.q[c * pl + i] = q[c];
-      acc += pi[c] * q[c];
+      f2_add_prod(acc, pi[c], q[c]);
     }
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double pq, unused;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
@@ -425,7 +423,7 @@ __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__
   const long long pl = pr.Vp;
   const float alpha = s->alpha_f;
   const float* __restrict__ pn = pr.p + (long long)((par + 1) & 1) * 6 * pl;
-  float acc = 0.f;
+  F2 acc = f2_zero();
   const int q0 = ch.begin / 4, q1 = (ch.end + 3) / 4;
   for (int qi = q0 + threadIdx.x; qi < q1; qi += NT) {
     const int v0 = 4 * qi;
@@ -446,14 +444,16 @@ __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__
       dv[c].z += alpha * pv[c].z; dv[c].w += alpha * pv[c].w;
       rv[c].x -= alpha * qv[c].x; rv[c].y -= alpha * qv[c].y;
       rv[c].z -= alpha * qv[c].z; rv[c].w -= alpha * qv[c].w;
-      acc += rv[c].x * (m.x * rv[c].x) + rv[c].y * (m.y * rv[c].y) + rv[c].z * (m.z * rv[c].z) +
-             rv[c].w * (m.w * rv[c].w);
+      f2_add_prod(acc, rv[c].x, __fmul_rn(m.x, rv[c].x));
+      f2_add_prod(acc, rv[c].y, __fmul_rn(m.y, rv[c].y));
+      f2_add_prod(acc, rv[c].z, __fmul_rn(m.z, rv[c].z));
+      f2_add_prod(acc, rv[c].w, __fmul_rn(m.w, rv[c].w));
       *reinterpret_cast<float4*>(pr.d + c * pl + v0) = dv[c];
       *reinterpret_cast<float4*>(pr.r + c * pl + v0) = rv[c];
     }
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double rz, unused;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, rz, unused);
     if (threadIdx.x == 0) {
@@ -480,20 +480,22 @@ __global__ void __launch_bounds__(NT) k_mesh_energy_v(const MeshProb* __restrict
   Scalars* s = pr.s;
   if (mode == 1 && s->done) return;
   const long long pl = pr.Vp;
-  float e = 0.f;
+  F2 e = f2_zero();
   for (int v = ch.begin + threadIdx.x; v < ch.end; v += NT) {
     const int h = handle_of(pr, v);
     if (h < 0) continue;
+    float ev = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       float dv = pr.x[c * pl + v];
       if (mode == 1) dv += pr.d[c * pl + v];
       const float f = pr.s_f * (dv - pr.htgt[3 * h + c]);
-      e += f * f;
+      ev += f * f;
     }
+    f2_add(e, ev);
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, e, 0.0, &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+  if (publish_partials(part, blockIdx.x, e, f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double a, b;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, a, b);
     if (threadIdx.x == 0) s->part0 = a;
@@ -511,7 +513,7 @@ __global__ void __launch_bounds__(NT) k_mesh_energy_e(const MeshProb* __restrict
   if (mode == 1 && s->done) return;
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
-  float e0 = 0.f, e1 = 0.f;
+  F2 e0 = f2_zero(), e1 = f2_zero();
   for (int ei = ch.begin + threadIdx.x; ei < ch.end; ei += NT) {
     const int a = pr.e0[ei], b = pr.e1[ei];
     const float vx = pr.U[a] - pr.U[b];
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(NT) k_mesh_energy_e(const MeshProb* __restrict
     const float r1 = sw * (dd1 + (vy - R.rv[1]));
     const float r2 = sw * (dd2 + (vz - R.rv[2]));
     if (mode == 0) {
-      e0 += r0 * r0 + r1 * r1 + r2 * r2;
+      f2_add(e0, r0 * r0 + r1 * r1 + r2 * r2);
     } else {
       const float ea0 = pr.d[a] - pr.d[b], ea1 = pr.d[pl + a] - pr.d[pl + b];
       const float ea2 = pr.d[2 * pl + a] - pr.d[2 * pl + b];
@@ -533,11 +535,11 @@ __global__ void __launch_bounds__(NT) k_mesh_energy_e(const MeshProb* __restrict
       const float u0 = sw * ((dd0 + ea0) + (vx - R2.rv[0]));
       const float u1 = sw * ((dd1 + ea1) + (vy - R2.rv[1]));
       const float u2 = sw * ((dd2 + ea2) + (vz - R2.rv[2]));
-      e0 += u0 * u0 + u1 * u1 + u2 * u2;
+      f2_add(e0, u0 * u0 + u1 * u1 + u2 * u2);
       const float l0 = r0 + sw * ea0 - sw * (R.g[0][0] * t3 + R.g[1][0] * t4 + R.g[2][0] * t5);
       const float l1 = r1 + sw * ea1 - sw * (R.g[0][1] * t3 + R.g[1][1] * t4 + R.g[2][1] * t5);
       const float l2 = r2 + sw * ea2 - sw * (R.g[0][2] * t3 + R.g[1][2] * t4 + R.g[2][2] * t5);
-      e1 += l0 * l0 + l1 * l1 + l2 * l2;
+      f2_add(e1, l0 * l0 + l1 * l1 + l2 * l2);
     }
   }
   pdl_trigger();

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(NT) k_warp_init(const GridProb* __restrict__ p
   const float sw = pr.s_w, sf = pr.s_f, wreg = pr.w_reg, wfit = pr.w_fit;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  float acc_rz = 0.f, acc_E = 0.f;
+  F2 acc_rz = f2_zero(), acc_E = f2_zero();
   const int nsub = pr.tw / TW;
   for (int ts = ch.begin * nsub; ts < ch.end * nsub; ++ts) {
     const int tc = tiles[ts / nsub];
@@ -154,8 +154,10 @@ __global__ void __launch_bounds__(NT) k_warp_init(const GridProb* __restrict__ p
       if (pr.csn) { pr.csn[i] = ci; pr.csn[pl + i] = si; }
       if (pr.jtf_out) { pr.jtf_out[i] = gdx; pr.jtf_out[pl + i] = gdy; pr.jtf_out[2 * pl + i] = gt; }
       if (pr.diag_out) { pr.diag_out[i] = diag_d; pr.diag_out[pl + i] = diag_t; }
-      acc_rz += md * (bx * bx + by * by) + mt * bt * bt;
-      acc_E += e;
+      f2_add_prod(acc_rz, bx, __fmul_rn(md, bx));
+      f2_add_prod(acc_rz, by, __fmul_rn(md, by));
+      f2_add_prod(acc_rz, bt, __fmul_rn(mt, bt));
+      f2_add(acc_E, e);
     }
     __syncthreads();
   }
@@ -286,7 +288,7 @@ __global__ void __launch_bounds__(NT, 3) k_warp_apply(const GridProb* __restrict
   const bool has_halo = tid < NHALO;
   int hhy = 0, hhx = 0;
   if (has_halo) halo_cell(tid, hhy, hhx);
-  float acc = 0.f;
+  F2 acc = f2_zero();
   WarpCell A, B;
   int tc = tiles[ch.begin];
   warp_cell_load(A, pr, pin, tile_x0(tc, 32) + tx, tile_y0(tc) + ty, update, use_beta);
@@ -347,10 +349,12 @@ __global__ void __launch_bounds__(NT, 3) k_warp_apply(const GridProb* __restrict
         }
       }
       pr.q[i] = qx; pr.q[pl + i] = qy; pr.q[2 * pl + i] = qt;
-      acc += pxi * qx + pyi * qy + pti * qt;
+      f2_add_prod(acc, pxi, qx);
+      f2_add_prod(acc, pyi, qy);
+      f2_add_prod(acc, pti, qt);
     }
   }
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double pq, unused;
     gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
@@ -591,7 +595,7 @@ __device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, c
   pp.src[10] = pr.c;
   pp.src[11] = pr.c + pl;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  float acc = 0.f;
+  F2 acc = f2_zero();
   // the tile index one tile ahead and the handle range of the current tile
   // are loaded an iteration early: the inline-assembly copies order all
   // memory accesses, so a late load would stall the warp at its use
@@ -734,12 +738,15 @@ __device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, c
       *reinterpret_cast<float4*>(pr.q + pl + i) = make_float4(qy[0], qy[1], qy[2], qy[3]);
       *reinterpret_cast<float4*>(pr.q + 2 * pl + i) = make_float4(qt[0], qt[1], qt[2], qt[3]);
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        acc = __fmaf_rn(cmp(opt, k), qt[k], __fmaf_rn(cmp(opy, k), qy[k], __fmaf_rn(cmp(opx, k), qx[k], acc)));
+      for (int k = 0; k < 4; ++k) {
+        f2_add_prod(acc, cmp(opx, k), qx[k]);
+        f2_add_prod(acc, cmp(opy, k), qy[k]);
+        f2_add_prod(acc, cmp(opt, k), qt[k]);
+      }
     }
   }
   cp_async_wait_all();
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double pq, unused;
     gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
@@ -877,7 +884,7 @@ __global__ void __launch_bounds__(NT, 2) k_warp_init_wide(const GridProb* __rest
   const float2 w2 = make_float2(w, w);
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  float acc_rz = 0.f, acc_E = 0.f;
+  F2 acc_rz = f2_zero(), acc_E = f2_zero();
   InitPlanes ip;
   ip.src[0] = pr.x; ip.src[1] = pr.x + pl; ip.src[2] = pr.x + 2 * pl; ip.src[3] = pr.c; ip.src[4] = pr.c + pl;
   int tc = tiles[ch.begin];
@@ -998,8 +1005,10 @@ __global__ void __launch_bounds__(NT, 2) k_warp_init_wide(const GridProb* __rest
         bx[k] = -gxv[k];
         by[k] = -gyv[k];
         bt[k] = -gtv[k];
-        acc_rz += md[k] * (bx[k] * bx[k] + by[k] * by[k]) + mt[k] * bt[k] * bt[k];
-        acc_E += ev[k];
+        f2_add_prod(acc_rz, bx[k], __fmul_rn(md[k], bx[k]));
+        f2_add_prod(acc_rz, by[k], __fmul_rn(md[k], by[k]));
+        f2_add_prod(acc_rz, bt[k], __fmul_rn(mt[k], bt[k]));
+        f2_add(acc_E, ev[k]);
       }
       const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
       *reinterpret_cast<float4*>(pr.r + i) = make_float4(bx[0], bx[1], bx[2], bx[3]);
@@ -1058,7 +1067,7 @@ __global__ void __launch_bounds__(NT) k_warp_energy(const GridProb* __restrict__
   const int P = pr.P, W = pr.W, H = pr.H;
   const float sw = pr.s_w, sf = pr.s_f;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  float acc0 = 0.f, acc1 = 0.f;
+  F2 acc0 = f2_zero(), acc1 = f2_zero();
   const int nsub = pr.tw / TW;
   for (int ts = ch.begin * nsub; ts < ch.end * nsub; ++ts) {
     const int tc = tiles[ts / nsub];
@@ -1129,8 +1138,8 @@ __global__ void __launch_bounds__(NT) k_warp_energy(const GridProb* __restrict__
           }
         }
       }
-      acc0 += e0;
-      acc1 += e1;
+      f2_add(acc0, e0);
+      f2_add(acc1, e1);
     }
     __syncthreads();
   }
@@ -1180,7 +1189,7 @@ __global__ void __launch_bounds__(NT) k_poisson_init(const GridProb* __restrict_
   const int P = pr.P, W = pr.W, H = pr.H;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  float acc_rz = 0.f, acc_E = 0.f;
+  F2 acc_rz = f2_zero(), acc_E = f2_zero();
   const int nsub = pr.tw / TW;
   for (int ts = ch.begin * nsub; ts < ch.end * nsub; ++ts) {
     const int tc = tiles[ts / nsub];
@@ -1225,20 +1234,18 @@ __global__ void __launch_bounds__(NT) k_poisson_init(const GridProb* __restrict_
       }
       float dcv;
       const float mv = minv_entry(dg, lam, dmin, dmax, pr.use_precond, &dcv);
-      float rz = 0.f;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const float b = -gr[c];
         pr.r[c * pl + i] = b;
         pr.d[c * pl + i] = 0.f;
         if (pr.jtf_out) pr.jtf_out[c * pl + i] = gr[c];
-        rz += b * b;
+        f2_add_prod(acc_rz, b, __fmul_rn(mv, b));
       }
       pr.m[i] = mv;
       if (pr.lm) pr.dc[i] = dcv;
       if (pr.diag_out) pr.diag_out[i] = dg;
-      acc_rz += mv * rz;
-      acc_E += e;
+      f2_add(acc_E, e);
     }
     __syncthreads();
   }
@@ -1332,7 +1339,7 @@ __global__ void __launch_bounds__(NT, 3) k_poisson_apply(const GridProb* __restr
   const bool has_halo = tid < NHALO;
   int hhy = 0, hhx = 0;
   if (has_halo) halo_cell(tid, hhy, hhx);
-  float acc = 0.f;
+  F2 acc = f2_zero();
   PoisCell A, B;
   int tc = tiles[ch.begin];
   pois_cell_load(A, pr, pin, tile_x0(tc, 32) + tx, tile_y0(tc) + ty, update, use_beta);
@@ -1372,11 +1379,11 @@ __global__ void __launch_bounds__(NT, 3) k_poisson_apply(const GridProb* __restr
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         pr.q[c * pl + i] = q[c];
-        acc += st.p[c][ly][lx] * q[c];
+        f2_add_prod(acc, st.p[c][ly][lx], q[c]);
       }
     }
   }
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double pq, unused;
     gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
@@ -1540,7 +1547,7 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __
   }
   src[4] = update ? pr.m : nullptr;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  float acc = 0.f;
+  F2 acc = f2_zero();
   int tc = tiles[ch.begin];
   int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
   tile_issue<NRAW_PA, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
@@ -1621,12 +1628,15 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __
         const float2 a = mul2(lo2(fo), fma2(dA, lo2(O[k]), qA[k]));
         const float2 b = mul2(hi2(fo), fma2(dB, hi2(O[k]), qB[k]));
         *reinterpret_cast<float4*>(pr.q + k * pl + i) = swz4(cat4(a, b));
-        acc += O[k].x * a.x + O[k].y * a.y + O[k].z * b.x + O[k].w * b.y;
+        f2_add_prod(acc, O[k].x, a.x);
+        f2_add_prod(acc, O[k].y, a.y);
+        f2_add_prod(acc, O[k].z, b.x);
+        f2_add_prod(acc, O[k].w, b.y);
       }
     }
   }
   cp_async_wait_all();
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double pq, unused;
     gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
@@ -1664,7 +1674,7 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_init_wide(const GridProb* __r
     src[4 + k] = pr.c + k * pl;
   }
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  float acc_rz = 0.f, acc_E = 0.f;
+  F2 acc_rz = f2_zero(), acc_E = f2_zero();
   int tc = tiles[ch.begin];
   int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
   tile_issue<NRAW_PI, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
@@ -1725,7 +1735,6 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_init_wide(const GridProb* __r
       if (pr.lm) *reinterpret_cast<float4*>(pr.dc + i) = dcv;
       if (pr.diag_out) *reinterpret_cast<float4*>(pr.diag_out + i) = dg;
       const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-      float rz = 0.f;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const float4 g = swz4(cat4(mul2(lo2(fo), gA[k]), mul2(hi2(fo), gB[k])));   // J^T F, plain order
@@ -1733,11 +1742,16 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_init_wide(const GridProb* __r
         *reinterpret_cast<float4*>(pr.r + k * pl + i) = b;
         *reinterpret_cast<float4*>(pr.d + k * pl + i) = zero;
         if (pr.jtf_out) *reinterpret_cast<float4*>(pr.jtf_out + k * pl + i) = g;
-        rz += mv.x * b.x * b.x + mv.y * b.y * b.y + mv.z * b.z * b.z + mv.w * b.w * b.w;
+        f2_add_prod(acc_rz, b.x, __fmul_rn(mv.x, b.x));
+        f2_add_prod(acc_rz, b.y, __fmul_rn(mv.y, b.y));
+        f2_add_prod(acc_rz, b.z, __fmul_rn(mv.z, b.z));
+        f2_add_prod(acc_rz, b.w, __fmul_rn(mv.w, b.w));
       }
-      acc_rz += rz;
       const float2 ea = mul2(lo2(fo), eA), eb = mul2(hi2(fo), eB);
-      acc_E += (ea.x + ea.y) + (eb.x + eb.y);
+      f2_add(acc_E, ea.x);
+      f2_add(acc_E, ea.y);
+      f2_add(acc_E, eb.x);
+      f2_add(acc_E, eb.y);
     }
   }
   cp_async_wait_all();
@@ -1769,7 +1783,7 @@ __global__ void __launch_bounds__(NT) k_poisson_energy(const GridProb* __restric
   const long long pl = pr.plane;
   const int P = pr.P, W = pr.W, H = pr.H;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  float acc0 = 0.f, acc1 = 0.f;
+  F2 acc0 = f2_zero(), acc1 = f2_zero();
   const int nsub = pr.tw / TW;
   for (int ts = ch.begin * nsub; ts < ch.end * nsub; ++ts) {
     const int tc = tiles[ts / nsub];
@@ -1809,8 +1823,8 @@ __global__ void __launch_bounds__(NT) k_poisson_energy(const GridProb* __restric
           e0 += r * r;
         }
       }
-      acc0 += e0;
-      acc1 += e0;
+      f2_add(acc0, e0);
+      f2_add(acc1, e0);
     }
     __syncthreads();
   }
@@ -1856,7 +1870,7 @@ __device__ __forceinline__ void update_body(const Chunk& ch, const GridProb& pr,
   const float4* __restrict__ m4 = reinterpret_cast<const float4*>(pr.m);
   float4* __restrict__ d4 = reinterpret_cast<float4*>(pr.d);
   float4* __restrict__ r4 = reinterpret_cast<float4*>(pr.r);
-  float acc = 0.f;
+  F2 acc = f2_zero();
   const int qrow = pr.tw / 4;        // float4 quads per tile row
   const int QPT = qrow * TH;         // float4 quads per tile
   const int nq = (ch.end - ch.begin) * QPT;
@@ -1888,16 +1902,15 @@ __device__ __forceinline__ void update_body(const Chunk& ch, const GridProb& pr,
       dv[c].z = __fmaf_rn(alpha, pv[c].z, dv[c].z); dv[c].w = __fmaf_rn(alpha, pv[c].w, dv[c].w);
       rv[c].x = __fmaf_rn(-alpha, qv[c].x, rv[c].x); rv[c].y = __fmaf_rn(-alpha, qv[c].y, rv[c].y);
       rv[c].z = __fmaf_rn(-alpha, qv[c].z, rv[c].z); rv[c].w = __fmaf_rn(-alpha, qv[c].w, rv[c].w);
-      float t = __fmul_rn(rv[c].x, __fmul_rn(m.x, rv[c].x));
-      t = __fmaf_rn(rv[c].y, __fmul_rn(m.y, rv[c].y), t);
-      t = __fmaf_rn(rv[c].z, __fmul_rn(m.z, rv[c].z), t);
-      t = __fmaf_rn(rv[c].w, __fmul_rn(m.w, rv[c].w), t);
-      acc = __fadd_rn(acc, t);
+      f2_add_prod(acc, rv[c].x, __fmul_rn(m.x, rv[c].x));
+      f2_add_prod(acc, rv[c].y, __fmul_rn(m.y, rv[c].y));
+      f2_add_prod(acc, rv[c].z, __fmul_rn(m.z, rv[c].z));
+      f2_add_prod(acc, rv[c].w, __fmul_rn(m.w, rv[c].w));
       d4[c * pl4 + j] = dv[c];
       r4[c * pl4 + j] = rv[c];
     }
   }
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double rz, unused;
     gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, rz, unused);
     if (threadIdx.x == 0) {

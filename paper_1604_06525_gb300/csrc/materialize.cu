@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(NT) k_csr_jtt(int nT, const int* __restrict__ 
                                                 double* __restrict__ part) {
   if (s->done || !s->pcg_active) return;
   const float lam = lm ? s->lambda_f : 0.f;
-  float acc = 0.f;
+  F2 acc = f2_zero();
   for (int k = blockIdx.x * NT + threadIdx.x; k < nT; k += gridDim.x * NT) {
     const int u = t_unk[k];
     float v = 0.f;
@@ -128,9 +128,9 @@ __global__ void __launch_bounds__(NT) k_csr_jtt(int nT, const int* __restrict__ 
       v += lam * dc[cm.mp[c] * pl + (u - c * pl)] * pu;
     }
     q[u] = v;
-    acc += pu * v;
+    f2_add_prod(acc, pu, v);
   }
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, gridDim.x)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, gridDim.x)) {
     double pq, unused;
     gather_partials(part, 0, gridDim.x, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(NT) k_jtj_spmv(int nT, const int* __restrict__
                                                  Scalars* __restrict__ s, double* __restrict__ part) {
   if (s->done || !s->pcg_active) return;
   const float lam = lm ? s->lambda_f : 0.f;
-  float acc = 0.f;
+  F2 acc = f2_zero();
   for (int k = blockIdx.x * NT + threadIdx.x; k < nT; k += gridDim.x * NT) {
     const int u = t_unk[k];
     float v = 0.f;
@@ -197,9 +197,9 @@ __global__ void __launch_bounds__(NT) k_jtj_spmv(int nT, const int* __restrict__
       v += lam * dc[cm.mp[c] * pl + (u - c * pl)] * pu;
     }
     q[u] = v;
-    acc += pu * v;
+    f2_add_prod(acc, pu, v);
   }
-  if (publish_partials(part, blockIdx.x, acc, 0.0, &s->counter, gridDim.x)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, gridDim.x)) {
     double pq, unused;
     gather_partials(part, 0, gridDim.x, &s->counter, pq, unused);
     if (threadIdx.x == 0) {

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(NT) k_warp_apply_noalloc(
     if (hx >= 0 && hx < TW && hy >= 0 && hy < TH) atomicAdd(&sfit[hy][hx], 1);
   }
   __syncthreads();
-  float acc = 0.f;
+  F2 acc = f2_zero();
   const int gx = x0 + tx, gy = y0 + ty;
   if (gx < W && gy < H) {
     const int lx = tx + 1, ly = ty + 1;
@@ -120,9 +120,11 @@ __global__ void __launch_bounds__(NT) k_warp_apply_noalloc(
       }
     }
     q[i] = qx; q[pl + i] = qy; q[2 * pl + i] = qt;
-    acc = pxi * qx + pyi * qy + pti * qt;
+    f2_add_prod(acc, pxi, qx);
+    f2_add_prod(acc, pyi, qy);
+    f2_add_prod(acc, pti, qt);
   }
-  if (publish_partials(part, blockIdx.x, acc, 0.0, counter, gridDim.x)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), counter, gridDim.x)) {
     double pq, unused;
     gather_partials(part, 0, gridDim.x, counter, pq, unused);
     if (threadIdx.x == 0 && pq_out) *pq_out = pq;

@@ -15,13 +15,16 @@
 // run of tiles (grid) or of vertices / edges (graph) of ONE problem, so the
 // same kernels serve a single solve and a batch of uneven problems.
 //
-// Reductions (p.q, r.z, energies) end in float64: each block reduces its
-// chunk (float32 products accumulated per thread over a few terms, summed in
-// float32 within each warp in a fixed shuffle order, float64 across the warps:
-// the float64 pipe of this part is narrow), writes the partial to a per-chunk
-// slot, and the last block of a problem to arrive (atomic counter) sums the
-// problem's partials in chunk order in float64, so the result does not depend
-// on block scheduling.
+// Reductions (p.q, r.z, energies) carry float64 accuracy from the first term
+// on: each thread accumulates its terms as a compensated float32 pair (every
+// product split exactly by one FMA, every addition made error-free by TwoSum:
+// Ogita, Rump & Oishi's Dot2, see F2 below), warps combine the pairs in a fixed
+// shuffle order, each warp's pair becomes a float64 hi + lo, and float64 takes
+// over from there (the float64 pipe of this part is narrow, so it is kept to
+// the last levels).  Each block writes its partial to a per-chunk slot, and the
+// last block of a problem to arrive (atomic counter) sums the problem's
+// partials in chunk order in float64, so the result does not depend on block
+// scheduling.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -238,33 +241,83 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
   }
 }
 
-__device__ __forceinline__ float warp_sumf(float v) {
+// ---------------------------------------------------------------------------
+// compensated float32 accumulation (error-free transformations)
+// ---------------------------------------------------------------------------
+// A sum is held as the unevaluated pair hi + lo of float32 values.  A product
+// x * y enters exactly: p = fl(x * y) and e = fma(x, y, -p) satisfy p + e =
+// x * y (TwoProduct); an addend enters through Knuth's TwoSum, which returns
+// the rounded sum and its exact rounding error, and the errors are collected
+// in lo.  This is the Sum2 / Dot2 scheme of Ogita, Rump & Oishi ("Accurate sum
+// and dot product", SIAM J. Sci. Comput. 26(6), 2005): the result is as
+// accurate as if accumulated in twice the float32 precision (~48 bits), on
+// par with float64 accumulation, at float32 issue rates.  Every operation is
+// an explicitly rounded intrinsic, so the compiler can neither contract nor
+// reorder it (either would destroy the error terms).
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ F2 f2_zero() { return F2{0.f, 0.f}; }
+
+// hi += x exactly, the rounding error goes to lo (TwoSum, 6 additions)
+__device__ __forceinline__ void f2_add(F2& a, float x) {
+  const float s = __fadd_rn(a.hi, x);
+  const float z = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, z)), __fsub_rn(x, z));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, e);
+}
+
+// a += x * y with the product split exactly (TwoProduct) before the TwoSum
+__device__ __forceinline__ void f2_add_prod(F2& a, float x, float y) {
+  const float p = __fmul_rn(x, y);
+  const float e = __fmaf_rn(x, y, -p);
+  f2_add(a, p);
+  a.lo = __fadd_rn(a.lo, e);
+}
+
+// a += b for two pairs
+__device__ __forceinline__ void f2_add_f2(F2& a, F2 b) {
+  f2_add(a, b.hi);
+  a.lo = __fadd_rn(a.lo, b.lo);
+}
+
+__device__ __forceinline__ double f2_to_double(F2 a) { return (double)a.hi + (double)a.lo; }
+
+// Sum of a pair over the warp (fixed shuffle order); valid in lane 0.
+__device__ __forceinline__ F2 warp_sum_f2(F2 v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    F2 w;
+    w.hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+    f2_add_f2(v, w);
+  }
   return v;
 }
 
-// Block sum of per-thread float32 values: float32 within each warp, float64
+// Block sum of per-thread compensated pairs: pairs within each warp, float64
 // across the warps; the result is valid in thread 0.  Called once per kernel
 // (its shared slots are not reused).
-__device__ __forceinline__ void block_sum2f(float a, float b, double& ra, double& rb) {
-  __shared__ float sa[NT / 32], sb[NT / 32];
-  a = warp_sumf(a);
-  b = warp_sumf(b);
+__device__ __forceinline__ void block_sum2f(F2 a, F2 b, double& ra, double& rb) {
+  __shared__ double sa[NT / 32], sb[NT / 32];
+  a = warp_sum_f2(a);
+  b = warp_sum_f2(b);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { sa[w] = a; sb[w] = b; }
+  if (l == 0) { sa[w] = f2_to_double(a); sb[w] = f2_to_double(b); }
   __syncthreads();
   ra = 0.0;
   rb = 0.0;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NT / 32; ++k) { ra += (double)sa[k]; rb += (double)sb[k]; }
+    for (int k = 0; k < NT / 32; ++k) { ra += sa[k]; rb += sb[k]; }
   }
 }
 
 // Stores this chunk's two partial sums and reports whether this block is the
 // last of its problem to do so.  Must be called by every thread of the block.
-__device__ __forceinline__ bool publish_partials(double* part, int chunk, float fa, float fb,
+__device__ __forceinline__ bool publish_partials(double* part, int chunk, F2 fa, F2 fb,
                                                  unsigned int* counter, unsigned int nchunks) {
   __shared__ int s_last;
   double a, b;

@@ -117,7 +117,13 @@ def test_graph_without_edges(api, kind):
     rep = gp.solve_lm(2, 10)
     assert rep["accepted"] == int(sum(ref.accepted)) == 2
     assert relE(rep["E_history"][0], ref.E_history[0]) <= 1e-5
-    assert relE(rep["E_history"][1], ref.E_history[1]) <= 1e-3
+    # after one step E is ~1e-6 of E0 while the unknowns are not small: the
+    # residuals cancel, and the float32 (float64) rounding of x and delta
+    # allows the first-order bound of tests/lm_tolerance.py (~1e-3 here)
+    from lm_tolerance import energy_rounding_bound, U32, U64
+    x1 = oracle.levenberg_marquardt(e, x, 1, 10).x
+    bound = energy_rounding_bound(e, x, x1, u=U64 if f64 else U32)
+    assert relE(rep["E_history"][1], ref.E_history[1]) <= max(1e-4 if not f64 else 1e-12, bound)
     assert rep["E_final"] <= 1e-6 * ref.E_history[0]
     gp.close()
 

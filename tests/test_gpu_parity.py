@@ -267,19 +267,46 @@ def test_gn_graph_replay_equals_direct_launches(api):
     assert ra2["E_history"] == ra["E_history"]
 
 
+def check_lm_trajectory(rep, ref):
+    """Same outer count and accept / reject sequence as the oracle (a
+    rejected step leaves x, hence the next energy, bit for bit unchanged),
+    every energy within 1e-4, lambda_final within the bound its gain ratios
+    allow (tests/lm_tolerance.py)."""
+    from lm_tolerance import lambda_tolerance
+    E = rep["E_history"]
+    assert rep["outer_done"] == ref.outer_done
+    assert rep["accepted"] == sum(ref.accepted)
+    assert [E[k + 1] != E[k] for k in range(ref.outer_done)] == list(ref.accepted)
+    for k, (a, b) in enumerate(zip(E, ref.E_history)):
+        assert relE(a, b) <= TOL_ENERGY, (k, a, b)
+    tol = lambda_tolerance(ref, E)
+    assert relE(rep["lambda_final"], ref.lambda_final) <= tol, (rep["lambda_final"], ref.lambda_final, tol)
+
+
 def test_lm_mesh_small(api):
     prob = synth.mesh_problem(3, seed=91, handle_frac=0.02)
     e = oracle.make_energy(prob)
     ref = oracle.levenberg_marquardt(e, prob.x0.reshape(-1), 6, 15)
     gp = api.Problem(prob)
     rep = gp.solve_lm(6, 15, lambda0=1e-3)
-    assert rep["outer_done"] == ref.outer_done
-    assert rep["accepted"] == sum(ref.accepted)
-    for a, b in zip(rep["E_history"], ref.E_history):
-        assert relE(a, b) <= TOL_ENERGY
-    # lambda follows the gain ratio, a quotient of energy differences that
-    # carries the float32 rounding of the residuals (~1e-5 relative)
-    assert relE(rep["lambda_final"], ref.lambda_final) <= 1e-3
+    check_lm_trajectory(rep, ref)
+
+
+def test_lm_mesh_level7_configuration(api):
+    """The mesh configuration as specified: icosphere level 7 (163,842
+    vertices, 983,040 directed edges), 1% seeded handles with offsets in
+    [-0.1, 0.1]^3, LM from lambda0 = 1e-3, 15 outer x 30 PCG iterations, in
+    the launch configuration the benchmark times (autotuned granularity):
+    the whole trajectory against the float64 oracle."""
+    prob = synth.mesh_problem(7, seed=synth.BASE_SEED)
+    e = oracle.make_energy(prob)
+    ref = oracle.levenberg_marquardt(e, prob.x0.reshape(-1), 15, 30)
+    gp = api.Problem(prob)
+    gp.autotune()
+    rep = gp.solve_lm(15, 30, lambda0=1e-3)
+    check_lm_trajectory(rep, ref)
+    assert rep["pcg_done"] == ref.pcg_done
+    gp.close()
 
 
 def test_lm_rejections_follow_nielsen(api):
