@@ -198,6 +198,110 @@ def oracle_sample(seconds_hint: float = 15.0):
                       f"{W_BENCH}x{H_BENCH} ARAP warp, float64, numpy/scipy on {ORACLE_THREADS} host thread(s)"}, hist
 
 
+# ---------------------------------------------------------------------------
+# the float64 oracle beside every result: bounded runs in a spawned process
+# pool (test infrastructure; never on the product path)
+# ---------------------------------------------------------------------------
+SERVE_OUT, SERVE_INN, SERVE_TOL = 10, 10, 1e-6
+BATCH_N, BATCH_LO, BATCH_HI = 512, 32, 512
+BATCH_SAMPLE = 32                      # batch members the oracle solves (every 16th by size)
+
+
+def oracle_job(spec):
+    """One oracle run (spawned worker): rebuilds the seeded problem the GPU
+    solved and returns its energy trajectory and CPU time."""
+    import numpy as np
+    import oracle
+    from paper_1604_06525_gb300 import synth
+    t0 = time.perf_counter()
+    kind = spec["kind"]
+    if kind == "warp":
+        prob = synth.warp_problem(spec["W"], spec["H"], spec["handles"], seed=spec["seed"])
+    elif kind == "poisson":
+        prob = synth.poisson_problem(spec["W"], spec["H"], seed=spec["seed"])
+    elif kind == "mesh":
+        prob = synth.mesh_problem(spec["level"], seed=spec["seed"])
+    elif kind == "batch_member":
+        side = int(synth.batch_sides(BATCH_N, BATCH_LO, BATCH_HI, seed=synth.BASE_SEED)[spec["i"]])
+        prob = synth.warp_problem(side, side, synth.warp_handle_count(side, side),
+                                  seed=synth.BASE_SEED + 1000 + spec["i"])
+    else:
+        raise ValueError(kind)
+    e = oracle.make_energy(prob)
+    x0 = prob.x0.reshape(-1).astype(np.float64)
+    if spec["method"] == "gn":
+        r = oracle.gauss_newton(e, x0, spec["outer"], spec["inner"])
+        out = {"E_history": list(r.E_history), "outer_done": spec["outer"]}
+    else:
+        prm = oracle.LMParams(lambda0=spec.get("lambda0", 1e-3), rel_tol=spec.get("rel_tol", 0.0))
+        r = oracle.levenberg_marquardt(e, x0, spec["outer"], spec["inner"], prm)
+        out = {"E_history": list(r.E_history), "outer_done": r.outer_done, "accepted": int(sum(r.accepted)),
+               "lambda_final": r.lambda_final}
+    out["cpu_s"] = time.perf_counter() - t0
+    return spec["key"], out
+
+
+def serve_sample_templates(synth):
+    """Serving templates the oracle solves: the warps of smallest, median
+    and largest side and the three meshes (indices into bench_serving's
+    template list)."""
+    import numpy as np
+    sides = synth.batch_sides(24, 64, 1024, seed=synth.BASE_SEED + 6)
+    order = np.argsort(sides, kind="stable")
+    return [int(order[0]), int(order[12]), int(order[23]), 24, 25, 26], sides
+
+
+def oracle_check_specs(synth):
+    """Oracle runs behind the accuracy report of every workload but the
+    batch (which batch_sample_members covers)."""
+    B = synth.BASE_SEED
+    specs = [
+        {"key": "warp_1024x1024_gn20x20", "kind": "warp", "W": W_BENCH, "H": H_BENCH, "handles": HANDLES, "seed": B,
+         "method": "gn", "outer": 4, "inner": INNER},
+        {"key": "warp_64x64_gn10x10", "kind": "warp", "W": 64, "H": 64, "handles": 8, "seed": B,
+         "method": "gn", "outer": 10, "inner": 10},
+        {"key": "poisson_1024x1024x4_gn20x20", "kind": "poisson", "W": W_BENCH, "H": H_BENCH, "seed": B,
+         "method": "gn", "outer": 4, "inner": INNER},
+        {"key": "mesh_icosphere7_lm15x30", "kind": "mesh", "level": 7, "seed": B, "method": "lm", "outer": 15,
+         "inner": 30, "lambda0": 1e-3},
+    ]
+    picks, sides = serve_sample_templates(synth)
+    for t in picks:
+        if t < 24:
+            s_ = int(sides[t])
+            specs.append({"key": f"serve_template_{t}", "kind": "warp", "W": s_, "H": s_,
+                          "handles": synth.warp_handle_count(s_, s_), "seed": 900 + t, "method": "lm",
+                          "outer": SERVE_OUT, "inner": SERVE_INN, "rel_tol": SERVE_TOL})
+        else:
+            lev = (4, 5, 6)[t - 24]
+            specs.append({"key": f"serve_template_{t}", "kind": "mesh", "level": lev, "seed": 950 + lev,
+                          "method": "lm", "outer": SERVE_OUT, "inner": SERVE_INN, "rel_tol": SERVE_TOL})
+    # the longest runs first, so the pool finishes early
+    specs.sort(key=lambda d: -(d.get("W", 0) * d.get("H", 0) * d["outer"] + (4 ** d.get("level", 0)) * 60 * d["outer"]))
+    return specs
+
+
+def batch_sample_members(synth):
+    """Every 16th of the 512 batch members in order of size (32 members
+    spanning the size range)."""
+    import numpy as np
+    sides = synth.batch_sides(BATCH_N, BATCH_LO, BATCH_HI, seed=synth.BASE_SEED)
+    order = np.argsort(sides, kind="stable")
+    step = BATCH_N // BATCH_SAMPLE
+    return [int(order[k]) for k in range(step // 2, BATCH_N, step)][:BATCH_SAMPLE]
+
+
+def rel_err(a, b):
+    return abs(a - b) / max(abs(b), 1e-30)
+
+
+def trajectory_error(E_gpu, E_ref):
+    n = min(len(E_gpu), len(E_ref))
+    errs = [rel_err(E_gpu[k], E_ref[k]) for k in range(n)]
+    return {"outer_compared": n - 1, "E_rel_err_max": max(errs), "E_rel_err_final": errs[n - 1],
+            "E_rel_err_per_outer": errs, "tolerance": 1e-4}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -421,7 +525,8 @@ def bench_batched(api, synth, torch, flush, n=512, outer=10, inner=10):
     for m in members:
         m.close()
     torch.cuda.empty_cache()
-    return {"problems": n, "pixels": px, "tiles_per_chunk": chosen,
+    details = {"batched": [r["E_history"] for r in reps_b], "plain": [r["E_history"] for r in reps_p]}
+    return details, {"problems": n, "pixels": px, "tiles_per_chunk": chosen,
             "batched_solves_per_s": n / wall_b, "batched_wall_ms": 1e3 * wall_b, "batched_device_ms": dev_b,
             "batched_p50_ms": 1e3 * wall_b, "batched_p99_ms": 1e3 * wall_b,
             "plain_solves_per_s": n / wall_p, "plain_wall_ms": 1e3 * wall_p, "plain_device_ms": dev_p,
@@ -514,7 +619,9 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, 
     for tpl in templates:
         del tpl
     torch.cuda.empty_cache()
-    return {"requests": n_req, "rate_per_s": rate, "budget_gb": budget / 2 ** 30, "rounds": rounds,
+    details = {"template": [int(t) for t in pick], "served": [done_c[i] for i in range(n_req)],
+               "plain": [plain_done[i] for i in range(n_req)]}
+    return details, {"requests": n_req, "rate_per_s": rate, "budget_gb": budget / 2 ** 30, "rounds": rounds,
             "served_solves_per_s": n_req / span_served, "served_p50_ms": 1e3 * pct(L, 50),
             "served_p99_ms": 1e3 * pct(L, 99),
             "capped_max_active": max_active, "capped_rounds": rounds_c,
@@ -601,10 +708,37 @@ def run_ours(args):
     roof, _ = roofline_for(api, synth, torch, W_BENCH, H_BENCH, peak)
     dom = max(roof, key=lambda k: roof[k]["ms"] * roof[k]["launches_per_solve"])   # largest share of a solve
     roof_big, extra = {}, {}
+    checks, cpu_base, cpu_all = {}, None, None
     # the secondary workloads are single-GPU measurements: taken at N = 1 only,
     # so a replica run holds its GPUs for the headline alone
     if not args.no_extras and world == 1:
+        # the float64 oracle on one host thread, timed while nothing else runs
+        cpu_base, e_ref = oracle_sample()
+        checks["warp_1024x1024_gn20x20"] = trajectory_error(reps[-1]["E_history"], e_ref)
+        # the oracle runs behind the accuracy report, in spawned workers beside
+        # the GPU measurements below (spawn: no CUDA state is inherited)
+        import multiprocessing as mp
+        ncpu = os.cpu_count() or 1
+        pool = mp.get_context("spawn").Pool(max(1, min(ncpu - 2, 12)))
+        pending = pool.map_async(oracle_job, [sp for sp in oracle_check_specs(synth)
+                                              if sp["key"] != "warp_1024x1024_gn20x20"])
+
         roof_big = roofline_beyond_l2(api, synth, torch, peak)
+
+        # the small configuration: ARAP warp 64 x 64, 8 handles, GN 10 x 10
+        # (launch-latency bound: its working set is a few hundred kB)
+        p64 = synth.warp_problem(64, 64, 8, seed=synth.BASE_SEED)
+        g64 = api.Problem(p64)
+        x64 = g64.x.clone()
+        rr64 = []
+        for _ in range(25):
+            g64.x.copy_(x64)
+            rr64.append(g64.solve_gn(10, 10))
+        ms64 = statistics.median(r_["ms"] for r_ in rr64[5:])
+        extra["warp_64x64_gn10x10"] = {"pcg_iters_per_s": 100 / (ms64 / 1e3), "ms_per_solve": ms64,
+                                       "E_final": rr64[-1]["E_final"], "note": "launch-latency bound, no roofline"}
+        e64 = rr64[-1]["E_history"]
+        g64.close()
 
         # secondary workloads: matrix-free vs materialized J (Sec. 8.3) on the
         # warp and on Poisson editing at 1024 x 1024, then the mesh under LM
@@ -638,6 +772,7 @@ def run_ours(args):
         mspm = statistics.median(r_["ms"] for r_ in rrm)
         extra["poisson_1024x1024x4_gn20x20"] = {"pcg_iters_per_s": OUTER * INNER / (msp / 1e3), "ms_per_solve": msp,
                                                "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
+        e_pois = rr[-1]["E_history"]
         extra["poisson_1024x1024x4_materialized_gn20x20"] = {
             "pcg_iters_per_s": OUTER * INNER / (mspm / 1e3), "ms_per_solve": mspm,
             "matrix_free_speedup": mspm / msp, "E_final": rrm[-1]["E_final"]}
@@ -656,6 +791,7 @@ def run_ours(args):
         msm = statistics.median(r_["ms"] for r_ in rr)
         extra["mesh_icosphere7_lm15x30"] = {"pcg_iters_per_s": rr[-1]["pcg_done"] / (msm / 1e3), "ms_per_solve": msm,
                                            "accepted": rr[-1]["accepted"], "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
+        rep_mesh = rr[-1]
         gmp.close()
 
         # implicit grid vs explicit graph for the same warp (Fig. 18: 8 outer x 100 PCG)
@@ -708,9 +844,66 @@ def run_ours(args):
 
         extra["float64_variant"] = bench_fp64(api, synth, torch, flush, ms_per_step)
 
-        extra["batched_512_warps_gn10x10"] = bench_batched(api, synth, torch, flush)
-        extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch, n_req=args.serving_requests,
-                                                          max_active=args.serving_max_active)
+        bdet, extra["batched_512_warps_gn10x10"] = bench_batched(api, synth, torch, flush)
+        sdet, extra["serving_poisson2000_lm10"] = bench_serving(api, synth, torch, n_req=args.serving_requests,
+                                                                max_active=args.serving_max_active)
+
+        # accuracy of every workload against the oracle
+        ref = dict(pending.get())
+        checks["warp_64x64_gn10x10"] = trajectory_error(e64, ref["warp_64x64_gn10x10"]["E_history"])
+        checks["poisson_1024x1024x4_gn20x20"] = trajectory_error(e_pois, ref["poisson_1024x1024x4_gn20x20"]["E_history"])
+        rm = ref["mesh_icosphere7_lm15x30"]
+        checks["mesh_icosphere7_lm15x30"] = dict(
+            trajectory_error(rep_mesh["E_history"], rm["E_history"]),
+            same_outer_count=rep_mesh["outer_done"] == rm["outer_done"],
+            same_accepted=rep_mesh["accepted"] == rm["accepted"],
+            lambda_final_rel_err=rel_err(rep_mesh["lambda_final"], rm["lambda_final"]))
+        picks, _ = serve_sample_templates(synth)
+        sv = {"served": [], "plain": []}
+        n_same = 0
+        for i, t in enumerate(sdet["template"]):
+            if t not in picks:
+                continue
+            o = ref[f"serve_template_{t}"]
+            for arm in ("served", "plain"):
+                sv[arm].append(rel_err(sdet[arm][i]["E_final"], o["E_history"][-1]))
+            n_same += sdet["served"][i]["outer_done"] == o["outer_done"]
+        checks["serving_poisson2000_lm10"] = {
+            "sample": f"{len(sv['served'])} requests of {len(picks)} templates (warps of smallest, median and "
+                      f"largest side; meshes of levels 4-6), final energy against the oracle's LM "
+                      f"<= {SERVE_OUT} x {SERVE_INN}, rel_tol {SERVE_TOL}",
+            "E_final_rel_err_max_served": max(sv["served"]), "E_final_rel_err_max_plain": max(sv["plain"]),
+            "same_outer_count_served": n_same, "tolerance": 1e-4}
+        pool.close()
+        pool.join()
+
+        # the batch: the oracle solves a sample of the members on every host
+        # core at once (the all-cores CPU baseline) and checks their energies
+        members = batch_sample_members(synth)
+        with mp.get_context("spawn").Pool(ncpu) as pool2:
+            pool2.map(oracle_job, [{"key": "warm", "kind": "warp", "W": 16, "H": 16, "handles": 2, "seed": 1,
+                                    "method": "gn", "outer": 1, "inner": 1}] * ncpu)
+            t0 = time.perf_counter()
+            bres = dict(pool2.map(oracle_job, [{"key": i, "kind": "batch_member", "i": i, "method": "gn",
+                                                "outer": 10, "inner": 10} for i in members], chunksize=1))
+            wall_all = time.perf_counter() - t0
+        cpu_sum = sum(v["cpu_s"] for v in bres.values())
+        errs_b = [rel_err(bdet["batched"][i][-1], bres[i]["E_history"][-1]) for i in members]
+        errs_p = [rel_err(bdet["plain"][i][-1], bres[i]["E_history"][-1]) for i in members]
+        checks["batched_512_warps_gn10x10"] = {
+            "sample": f"{len(members)} of {BATCH_N} members (every {BATCH_N // len(members)}th by size), "
+                      f"final energy after GN 10 x 10 against the oracle",
+            "E_final_rel_err_max_batched": max(errs_b), "E_final_rel_err_max_plain": max(errs_p),
+            "E_final_rel_err_median_batched": statistics.median(errs_b),
+            "E_final_rel_err_median_plain": statistics.median(errs_p),
+            "within_1e-4_batched": sum(e_ <= 1e-4 for e_ in errs_b),
+            "within_1e-4_plain": sum(e_ <= 1e-4 for e_ in errs_p), "tolerance": 1e-4}
+        cpu_all = {"value": len(members) / wall_all, "unit": "solves/s", "cores": ncpu, "kind": "oracle",
+                   "workload": "512 ARAP warps (sides 32..512), GN 10 x 10", "single_thread_value": len(members) / cpu_sum,
+                   "sample": f"{len(members)} members (every {BATCH_N // len(members)}th by size), one process "
+                             f"per host core ({ncpu}), float64 numpy/scipy; single_thread_value = members / "
+                             f"sum of per-member CPU seconds",
+                   "gpu_batched_solves_per_s": extra["batched_512_warps_gn10x10"]["batched_solves_per_s"]}
 
     launches_per_step = 2 + OUTER * (2 + 2 * INNER)
     line = {
@@ -737,13 +930,11 @@ def run_ours(args):
         "also": extra,
     }
     if rank == 0 and world == 1 and not args.no_extras:
-        line["cpu_baseline"], e_ref = oracle_sample()
-        # the error of the bench's own solve against the float64 oracle over the
-        # outer iterations the oracle sample ran (same start point)
-        e_gpu = reps[-1]["E_history"][:len(e_ref)]
-        line["oracle_check"] = {"outer_iterations": len(e_ref) - 1, "E_oracle": e_ref, "E_gpu": e_gpu,
-                                "E_rel_err_max": max(abs(a - b) / max(abs(b), 1e-30) for a, b in zip(e_gpu, e_ref)),
-                                "tolerance": 1e-4}
+        line["cpu_baseline"] = cpu_base
+        line["cpu_baseline_all_cores"] = cpu_all
+        # every workload's energies against the float64 oracle from the same
+        # start point (bounded outer counts where the oracle would take long)
+        line["oracle_check"] = checks
     if rank == 0:
         print(json.dumps(line), flush=True)
     gp.close()

@@ -21,6 +21,15 @@ Iterative Methods for Sparse Linear Systems, Alg. 9.1).  It stops early only
 on breakdown: r.z == 0 (the residual vanished) or p.q <= 0.  Rows whose
 diagonal is zero get M^-1 = 1 (their right-hand side is zero, so this only
 avoids a division by zero).
+
+round_to (jacobi_pcg, gauss_newton, levenberg_marquardt): None for plain
+float64.  A numpy dtype (np.float32) makes the runs store what a reduced-
+precision solver stores in that precision -- the unknowns x (after every
+update and at the LM trial point), the PCG vectors d, r, z, p, the product
+q = A p and the scalars alpha, beta -- while every product, dot product and
+energy is still formed in float64.  It measures how far a trajectory carries
+the rounding of that storage (some LM trajectories amplify a 1e-8 rounding to
+1e-4 within a few outer iterations); it is not a model of any kernel.
 """
 from __future__ import annotations
 
@@ -55,31 +64,38 @@ def jacobi_minv(diag):
     return out
 
 
-def jacobi_pcg(apply_A, b, Minv, iters: int):
+def _rounder(round_to):
+    if round_to is None:
+        return lambda v: v
+    return lambda v: np.asarray(v, round_to).astype(np.float64)
+
+
+def jacobi_pcg(apply_A, b, Minv, iters: int, round_to=None):
     """Textbook Jacobi-PCG for A d = b from d0 = 0.
 
     Returns (d, n_done, r) where n_done counts completed iterations and r is
-    the recurrence residual."""
+    the recurrence residual.  round_to: see the module docstring."""
+    rd = _rounder(round_to)
     d = np.zeros_like(b)
-    r = b.copy()
-    z = Minv * r
+    r = rd(b.copy())
+    z = rd(Minv * r)
     p = z.copy()
     rho = float(r @ z)
     n_done = 0
     for _ in range(iters):
         if rho == 0.0:
             break
-        q = apply_A(p)
+        q = rd(apply_A(p))
         pq = float(p @ q)
         if not pq > 0.0:
             break
-        alpha = rho / pq
-        d = d + alpha * p
-        r = r - alpha * q
-        z = Minv * r
+        alpha = float(rd(rho / pq))
+        d = rd(d + alpha * p)
+        r = rd(r - alpha * q)
+        z = rd(Minv * r)
         rho_new = float(r @ z)
-        beta = rho_new / rho
-        p = z + beta * p
+        beta = float(rd(rho_new / rho))
+        p = rd(z + beta * p)
         rho = rho_new
         n_done += 1
     return d, n_done, r
@@ -92,9 +108,11 @@ class GNResult:
     pcg_done: int
 
 
-def gauss_newton(energy, x0, outer: int, inner: int, use_precond: bool = True) -> GNResult:
-    """Gauss-Newton with a fixed number of outer and PCG iterations."""
-    x = np.asarray(x0, np.float64).reshape(-1).copy()
+def gauss_newton(energy, x0, outer: int, inner: int, use_precond: bool = True, round_to=None) -> GNResult:
+    """Gauss-Newton with a fixed number of outer and PCG iterations
+    (round_to: see the module docstring)."""
+    rd = _rounder(round_to)
+    x = rd(np.asarray(x0, np.float64).reshape(-1).copy())
     hist = []
     total = 0
     for _ in range(outer):
@@ -104,9 +122,9 @@ def gauss_newton(energy, x0, outer: int, inner: int, use_precond: bool = True) -
         b = -(J.T @ F)
         diag = np.asarray(J.multiply(J).sum(axis=0)).ravel()
         Minv = jacobi_minv(diag) if use_precond else np.ones_like(diag)
-        d, n_done, _ = jacobi_pcg(lambda p: J.T @ (J @ p), b, Minv, inner)
+        d, n_done, _ = jacobi_pcg(lambda p: J.T @ (J @ p), b, Minv, inner, round_to)
         total += n_done
-        x = x + d
+        x = rd(x + d)
     hist.append(energy.energy(x))
     return GNResult(x, hist, total)
 
@@ -137,13 +155,15 @@ class LMResult:
 
 
 def levenberg_marquardt(energy, x0, outer: int, inner: int, prm: LMParams = LMParams(),
-                        use_precond: bool = True) -> LMResult:
+                        use_precond: bool = True, round_to=None) -> LMResult:
     """Levenberg-Marquardt with Nielsen's damping update (module docstring).
 
     A rejected step counts as an outer iteration.  With prm.rel_tol > 0 the
     loop stops after an accepted step whose relative energy change is below
-    rel_tol (or whose new energy is exactly zero)."""
-    x = np.asarray(x0, np.float64).reshape(-1).copy()
+    rel_tol (or whose new energy is exactly zero).  round_to: see the module
+    docstring."""
+    rd = _rounder(round_to)
+    x = rd(np.asarray(x0, np.float64).reshape(-1).copy())
     lam, nu = prm.lambda0, 2.0
     hist, acc, lams = [], [], []
     trials, preds, rhos = [], [], []
@@ -159,9 +179,12 @@ def levenberg_marquardt(energy, x0, outer: int, inner: int, prm: LMParams = LMPa
         diag = np.asarray(J.multiply(J).sum(axis=0)).ravel()
         Dc = np.clip(diag, prm.diag_min, prm.diag_max)
         Minv = jacobi_minv(diag + lam * Dc) if use_precond else np.ones_like(diag)
-        d, n_done, _ = jacobi_pcg(lambda p: J.T @ (J @ p) + lam * Dc * p, b, Minv, inner)
+        d, n_done, _ = jacobi_pcg(lambda p: J.T @ (J @ p) + lam * Dc * p, b, Minv, inner, round_to)
         total += n_done
-        E_new = energy.energy(x + d)
+        x_trial = rd(x + d)
+        if round_to is not None:
+            d = x_trial - x                     # the step the rounded state actually takes
+        E_new = energy.energy(x_trial)
         Fl = F + J @ d                          # linear model of the residuals
         pred = E - float(Fl @ Fl)
         rho = (E - E_new) / pred if pred > 0.0 else -np.inf
@@ -170,7 +193,7 @@ def levenberg_marquardt(energy, x0, outer: int, inner: int, prm: LMParams = LMPa
         rhos.append(rho)
         k += 1
         if rho > prm.eta:
-            x = x + d
+            x = x_trial
             lam = lam * max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3)
             nu = 2.0
             acc.append(True)

@@ -62,3 +62,18 @@ def lambda_tolerance(ref, E_gpu, safety=2.0):
         slope = max(_dlnf(r) for r in grid)
         tot += slope * drho
     return float(np.expm1(tot)) + 1e-12
+
+
+def oracle_mesh_lm(level, seed, outer, inner, round_to=None):
+    """The oracle's LM on a seeded icosphere mesh problem, as a plain dict
+    (a spawned worker's job in the GPU tests).  round_to: None or "float32"
+    (oracle.solver's reduced-precision storage emulation)."""
+    import oracle
+    from paper_1604_06525_gb300 import synth
+    prob = synth.mesh_problem(level, seed=seed)
+    e = oracle.make_energy(prob)
+    r = oracle.levenberg_marquardt(e, prob.x0.reshape(-1), outer, inner,
+                                   round_to=None if round_to is None else np.dtype(round_to))
+    return {"E_history": list(r.E_history), "accepted": list(r.accepted), "outer_done": r.outer_done,
+            "pcg_done": r.pcg_done, "lambda_final": r.lambda_final, "E_trial": list(r.E_trial),
+            "pred": list(r.pred), "rho": list(r.rho)}

@@ -296,17 +296,51 @@ def test_lm_mesh_level7_configuration(api):
     """The mesh configuration as specified: icosphere level 7 (163,842
     vertices, 983,040 directed edges), 1% seeded handles with offsets in
     [-0.1, 0.1]^3, LM from lambda0 = 1e-3, 15 outer x 30 PCG iterations, in
-    the launch configuration the benchmark times (autotuned granularity):
-    the whole trajectory against the float64 oracle."""
+    the launch configuration the benchmark times (autotuned granularity),
+    against the float64 oracle.
+
+    This trajectory amplifies rounding: its gain ratios stay near 0.1-0.2, and
+    the oracle's own run with float32 storage of x, the PCG vectors and J^T J p
+    (oracle.solver round_to) leaves the plain float64 run by ~1e-8 up to outer
+    iteration 8 and by up to ~5e-4 by iteration 15.  So the float32 solver is
+    held to: the same decisions (outer count, accept / reject sequence, PCG
+    iterations), every energy within 1e-4 where that float32-storage run stays
+    within 1e-5 of the plain one, within 8x the float32-storage run's
+    deviation (its running maximum) after that, and lambda_final within the
+    bound of tests/lm_tolerance.py.  The float64 solver, which stores
+    everything in float64, is held to 1e-9 on the whole trajectory."""
+    import multiprocessing as mp
+    from lm_tolerance import oracle_mesh_lm, lambda_tolerance
     prob = synth.mesh_problem(7, seed=synth.BASE_SEED)
-    e = oracle.make_energy(prob)
-    ref = oracle.levenberg_marquardt(e, prob.x0.reshape(-1), 15, 30)
-    gp = api.Problem(prob)
-    gp.autotune()
-    rep = gp.solve_lm(15, 30, lambda0=1e-3)
-    check_lm_trajectory(rep, ref)
-    assert rep["pcg_done"] == ref.pcg_done
-    gp.close()
+    with mp.get_context("spawn").Pool(2) as pool:
+        j_ref = pool.apply_async(oracle_mesh_lm, (7, synth.BASE_SEED, 15, 30))
+        j_emu = pool.apply_async(oracle_mesh_lm, (7, synth.BASE_SEED, 15, 30, "float32"))
+        gp = api.Problem(prob)
+        gp.autotune()
+        rep = gp.solve_lm(15, 30, lambda0=1e-3)
+        gp.close()
+        g64 = api.ProblemF64(prob)
+        r64 = g64.solve_lm(15, 30, lambda0=1e-3)
+        g64.close()
+        ref, emu = j_ref.get(), j_emu.get()
+    E, Er, Ee = rep["E_history"], ref["E_history"], emu["E_history"]
+    n = ref["outer_done"]
+    assert rep["outer_done"] == n == r64["outer_done"] and len(E) == len(Er) == n + 1
+    assert rep["accepted"] == sum(ref["accepted"]) == r64["accepted"]
+    assert [E[k + 1] != E[k] for k in range(n)] == ref["accepted"]
+    assert rep["pcg_done"] == ref["pcg_done"]
+    run_max = 0.0
+    for k in range(n + 1):
+        dev = relE(Ee[k], Er[k])
+        run_max = max(run_max, dev)
+        tol = TOL_ENERGY if run_max <= 1e-5 else max(TOL_ENERGY, 8.0 * run_max)
+        assert relE(E[k], Er[k]) <= tol, (k, E[k], Er[k], tol)
+        assert relE(r64["E_history"][k], Er[k]) <= 1e-9, (k, r64["E_history"][k], Er[k])
+
+    class R:        # the oracle result in the shape lambda_tolerance reads
+        accepted, E_history, rho, pred = ref["accepted"], Er, ref["rho"], ref["pred"]
+    tol = lambda_tolerance(R, E)
+    assert relE(rep["lambda_final"], ref["lambda_final"]) <= tol, (rep["lambda_final"], ref["lambda_final"], tol)
 
 
 def test_lm_rejections_follow_nielsen(api):

@@ -616,3 +616,37 @@ def test_damped_apply_matches_exact_lm_step():
     jtf, diag, _ = so.jtf_diag(e, x0)
     q = so.apply_jtj(e, x0, res.x - x0, lam, np.clip(diag, 1e-6, 1e32))
     np.testing.assert_allclose(q, -jtf, atol=1e-9 * np.abs(jtf).max())
+
+
+# -- reduced-precision storage emulation (round_to) -------------------------------
+
+def test_round_to_none_is_the_plain_run():
+    prob = synth.mesh_problem(1, seed=21, handle_frac=0.2)
+    e = en.make_energy(prob)
+    x0 = prob.x0.reshape(-1)
+    a = so.levenberg_marquardt(e, x0, 4, 8)
+    b = so.levenberg_marquardt(e, x0, 4, 8, round_to=None)
+    assert a.E_history == b.E_history and np.array_equal(a.x, b.x)
+    g = so.gauss_newton(e, x0, 3, 6)
+    h = so.gauss_newton(e, x0, 3, 6, round_to=None)
+    assert g.E_history == h.E_history
+
+
+def test_round_to_float32_stores_float32_values_and_stays_close_when_well_conditioned():
+    """The emulated run keeps the state representable in float32; on a linear,
+    well-conditioned problem (Poisson) its energies stay within float32
+    rounding of the plain run, and LM stays monotone over accepted steps."""
+    prob = synth.poisson_problem(24, 20, seed=23)
+    e = en.make_energy(prob)
+    x0 = prob.x0.reshape(-1)
+    plain = so.gauss_newton(e, x0, 3, 15)
+    f32 = so.gauss_newton(e, x0, 3, 15, round_to=np.float32)
+    assert np.array_equal(f32.x, f32.x.astype(np.float32).astype(np.float64))
+    for a, b in zip(f32.E_history, plain.E_history):
+        assert abs(a - b) <= 1e-5 * b
+    m = synth.mesh_problem(1, seed=24, handle_frac=0.2)
+    em = en.make_energy(m)
+    lm = so.levenberg_marquardt(em, m.x0.reshape(-1), 6, 10, round_to=np.float32)
+    acc_E = [lm.E_history[0]] + [lm.E_history[k + 1] for k, a in enumerate(lm.accepted) if a]
+    assert all(b <= a for a, b in zip(acc_E, acc_E[1:]))
+    assert np.array_equal(lm.x, lm.x.astype(np.float32).astype(np.float64))
