@@ -717,9 +717,9 @@ def run_ours(args):
         checks["warp_1024x1024_gn20x20"] = trajectory_error(reps[-1]["E_history"], e_ref)
         # the oracle runs behind the accuracy report, in spawned workers beside
         # the GPU measurements below (spawn: no CUDA state is inherited)
-        import multiprocessing as mp
+        import multiprocessing as mproc
         ncpu = os.cpu_count() or 1
-        pool = mp.get_context("spawn").Pool(max(1, min(ncpu - 2, 12)))
+        pool = mproc.get_context("spawn").Pool(max(1, min(ncpu - 2, 12)))
         pending = pool.map_async(oracle_job, [sp for sp in oracle_check_specs(synth)
                                               if sp["key"] != "warp_1024x1024_gn20x20"])
 
@@ -880,7 +880,7 @@ def run_ours(args):
         # the batch: the oracle solves a sample of the members on every host
         # core at once (the all-cores CPU baseline) and checks their energies
         members = batch_sample_members(synth)
-        with mp.get_context("spawn").Pool(ncpu) as pool2:
+        with mproc.get_context("spawn").Pool(ncpu) as pool2:
             pool2.map(oracle_job, [{"key": "warm", "kind": "warp", "W": 16, "H": 16, "handles": 2, "seed": 1,
                                     "method": "gn", "outer": 1, "inner": 1}] * ncpu)
             t0 = time.perf_counter()
