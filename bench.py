@@ -229,12 +229,13 @@ def oracle_job(spec):
         raise ValueError(kind)
     e = oracle.make_energy(prob)
     x0 = prob.x0.reshape(-1).astype(np.float64)
+    rt = np.float32 if spec.get("round_to") == "float32" else None
     if spec["method"] == "gn":
-        r = oracle.gauss_newton(e, x0, spec["outer"], spec["inner"])
+        r = oracle.gauss_newton(e, x0, spec["outer"], spec["inner"], round_to=rt)
         out = {"E_history": list(r.E_history), "outer_done": spec["outer"]}
     else:
         prm = oracle.LMParams(lambda0=spec.get("lambda0", 1e-3), rel_tol=spec.get("rel_tol", 0.0))
-        r = oracle.levenberg_marquardt(e, x0, spec["outer"], spec["inner"], prm)
+        r = oracle.levenberg_marquardt(e, x0, spec["outer"], spec["inner"], prm, round_to=rt)
         out = {"E_history": list(r.E_history), "outer_done": r.outer_done, "accepted": int(sum(r.accepted)),
                "lambda_final": r.lambda_final}
     out["cpu_s"] = time.perf_counter() - t0
@@ -276,6 +277,10 @@ def oracle_check_specs(synth):
             lev = (4, 5, 6)[t - 24]
             specs.append({"key": f"serve_template_{t}", "kind": "mesh", "level": lev, "seed": 950 + lev,
                           "method": "lm", "outer": SERVE_OUT, "inner": SERVE_INN, "rel_tol": SERVE_TOL})
+    # the LM runs again with float32 storage (oracle.solver round_to): how far
+    # the float64 algorithm itself moves when only its stored values are
+    # rounded to float32 -- the scale of error a float32 solver cannot avoid
+    specs += [dict(sp, key=sp["key"] + "@f32storage", round_to="float32") for sp in specs if sp["method"] == "lm"]
     # the longest runs first, so the pool finishes early
     specs.sort(key=lambda d: -(d.get("W", 0) * d.get("H", 0) * d["outer"] + (4 ** d.get("level", 0)) * 60 * d["outer"]))
     return specs
@@ -857,7 +862,9 @@ def run_ours(args):
             trajectory_error(rep_mesh["E_history"], rm["E_history"]),
             same_outer_count=rep_mesh["outer_done"] == rm["outer_done"],
             same_accepted=rep_mesh["accepted"] == rm["accepted"],
-            lambda_final_rel_err=rel_err(rep_mesh["lambda_final"], rm["lambda_final"]))
+            lambda_final_rel_err=rel_err(rep_mesh["lambda_final"], rm["lambda_final"]),
+            oracle_float32_storage_E_rel_err_per_outer=trajectory_error(
+                ref["mesh_icosphere7_lm15x30@f32storage"]["E_history"], rm["E_history"])["E_rel_err_per_outer"])
         picks, _ = serve_sample_templates(synth)
         sv = {"served": [], "plain": []}
         n_same = 0
@@ -868,11 +875,14 @@ def run_ours(args):
             for arm in ("served", "plain"):
                 sv[arm].append(rel_err(sdet[arm][i]["E_final"], o["E_history"][-1]))
             n_same += sdet["served"][i]["outer_done"] == o["outer_done"]
+        f32s = [rel_err(ref[f"serve_template_{t}@f32storage"]["E_history"][-1], ref[f"serve_template_{t}"]["E_history"][-1])
+                for t in picks]
         checks["serving_poisson2000_lm10"] = {
             "sample": f"{len(sv['served'])} requests of {len(picks)} templates (warps of smallest, median and "
                       f"largest side; meshes of levels 4-6), final energy against the oracle's LM "
                       f"<= {SERVE_OUT} x {SERVE_INN}, rel_tol {SERVE_TOL}",
             "E_final_rel_err_max_served": max(sv["served"]), "E_final_rel_err_max_plain": max(sv["plain"]),
+            "oracle_float32_storage_E_final_rel_err_max": max(f32s),
             "same_outer_count_served": n_same, "tolerance": 1e-4}
         pool.close()
         pool.join()
