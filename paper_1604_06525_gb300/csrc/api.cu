@@ -854,7 +854,7 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   }
   // out-edge rows of the sorted list, and the in-edges of every vertex
   // (sources ascending, as the sorted list visits them)
-  std::vector<int> orow((size_t)V + 1, 0), irow((size_t)V + 1, 0), isrc((size_t)E);
+  std::vector<int> orow((size_t)V + 1, 0), irow((size_t)V + 1, 0), isrc((size_t)E), itpos((size_t)E);
   for (int e = 0; e < E; ++e) {
     orow[(size_t)e0[e] + 1] += 1;
     irow[(size_t)e1[e] + 1] += 1;
@@ -865,7 +865,11 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   }
   {
     std::vector<int> fill(irow.begin(), irow.end() - 1);
-    for (int e = 0; e < E; ++e) isrc[(size_t)fill[e1[e]]++] = e0[e];
+    for (int e = 0; e < E; ++e) {
+      const size_t k = (size_t)fill[e1[e]]++;
+      isrc[k] = e0[e];
+      itpos[k] = e;            // the edge's position in the sorted list
+    }
   }
 
   const int target = std::max(1, q->sms * 8);
@@ -888,13 +892,15 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   float4 *grec = nullptr, *vrec = nullptr;
   CKS(dalloc(q, &grec, (size_t)NGR * V));
   CKS(dalloc(q, &vrec, (size_t)NVR * V));
-  int *dorow = nullptr, *dirow = nullptr, *disrc = nullptr;
+  int *dorow = nullptr, *dirow = nullptr, *disrc = nullptr, *ditpos = nullptr;
   CKS(dalloc(q, &dorow, orow.size()));
   CKS(upload(dorow, orow));
   CKS(dalloc(q, &dirow, irow.size()));
   CKS(upload(dirow, irow));
   CKS(dalloc(q, &disrc, std::max<size_t>(1, isrc.size())));
   if (E > 0) CKS(upload(disrc, isrc));
+  CKS(dalloc(q, &ditpos, std::max<size_t>(1, itpos.size())));
+  if (E > 0) CKS(upload(ditpos, itpos));
   for (int c = 0; c < D; ++c) {
     std::vector<float> Ui((size_t)V);
     for (int k = 0; k < V; ++k) Ui[k] = Uh[c][perm[k]];
@@ -936,7 +942,7 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   g.use_precond = 1; g.lm = 0;
   g.x = q->x; g.U = U; g.degw = dgw; g.e0 = de0; g.e1 = de1;
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
-  g.orow = dorow; g.irow = dirow; g.isrc = disrc;
+  g.orow = dorow; g.irow = dirow; g.isrc = disrc; g.itpos = ditpos;
   g.gw = grid3 ? grid3[0] : 0; g.gh = grid3 ? grid3[1] : 0; g.gd = grid3 ? grid3[2] : 0; g.gpad = 0;
   g.grec = grec; g.vrec = vrec;
   g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;

@@ -410,6 +410,236 @@ __global__ void __launch_bounds__(NT, MESH_PULL_MIN_BLOCKS) k_mesh_apply_pull(co
   }
 }
 
+// ---------------------------------------------------------------------------
+// PCGStep: applyJTJ fused with the direction update, ARAP mesh on a graph
+// ---------------------------------------------------------------------------
+// A block walks its chunk in vertex tiles of NT vertices, one vertex per
+// thread.  With R = R(A_i) and M_i = sum_m p_i,m dR/dA_m(A_i) formed once per
+// vertex (rot3 / rot3_dir below), the linearized residual of an out-edge
+// e = (i, j) is
+//   t_e = J_e p = s_w [(p_i,d - p_j,d) - M_i v],   v = U_i - U_j,
+// its displacement rows add s_w t_e at i, and its angle rows
+// -s_w (dR/dA_m v) . t_e = -s_w <dR/dA_m, t_e v^T> at i are summed through the
+// 3 x 3 matrix S_i = sum_e t_e v^T (one contraction per vertex, not three
+// derivative vectors per edge).  At j the edge subtracts s_w t_e from the
+// displacement rows: the thread of j reads t_e from shared memory when i lies
+// in the same tile, so each residual is evaluated once, and re-evaluates it
+// from i's data only across tile borders (a few percent of the edges after
+// the Morton renumbering).  The direction p = M^-1 r + beta p_old of the
+// tile's vertices is formed here and written once; a neighbour outside the
+// tile forms its own from (r, M^-1, p_old) with the same roundings.  Every
+// row is summed in a fixed order: results do not depend on scheduling.
+
+// Rotation R = Rz(az) Ry(ay) Rx(ax) from the angles' cos / sin, with
+// u' = dR_:0 / day; the angle derivatives are then
+//   dR/dax = [0 | R_:2 | -R_:1],  dR/day = [u' | sin ax R_:0 | cos ax R_:0],
+//   dR/daz = rows (-R_1:, R_0:, 0).
+struct Rot3 {
+  float r[3][3];
+  float ud[3];
+  float ca, sa;
+};
+__device__ __forceinline__ Rot3 rot3(const float cs[6]) {
+  const float ca = cs[0], sa = cs[1], cb = cs[2], sb = cs[3], cc = cs[4], sc = cs[5];
+  const float a1 = sa * sb, a2 = ca * sb;
+  Rot3 o;
+  o.r[0][0] = cb * cc; o.r[0][1] = fmaf(a1, cc, -ca * sc); o.r[0][2] = fmaf(a2, cc, sa * sc);
+  o.r[1][0] = cb * sc; o.r[1][1] = fmaf(a1, sc, ca * cc);  o.r[1][2] = fmaf(a2, sc, -sa * cc);
+  o.r[2][0] = -sb;     o.r[2][1] = sa * cb;                o.r[2][2] = ca * cb;
+  o.ud[0] = -sb * cc; o.ud[1] = -sb * sc; o.ud[2] = -cb;
+  o.ca = ca; o.sa = sa;
+  return o;
+}
+// M = pa dR/dax + pb dR/day + pc dR/daz
+__device__ __forceinline__ void rot3_dir(const Rot3& R, float pa, float pb, float pc, float (&M)[3][3]) {
+  const float dz[3][3] = {{-R.r[1][0], -R.r[1][1], -R.r[1][2]}, {R.r[0][0], R.r[0][1], R.r[0][2]}, {0.f, 0.f, 0.f}};
+  const float bs = pb * R.sa, bc = pb * R.ca;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    M[i][0] = fmaf(pb, R.ud[i], pc * dz[i][0]);
+    M[i][1] = fmaf(pa, R.r[i][2], fmaf(bs, R.r[i][0], pc * dz[i][1]));
+    M[i][2] = fmaf(-pa, R.r[i][1], fmaf(bc, R.r[i][0], pc * dz[i][2]));
+  }
+}
+// (<dR/dax, S>, <dR/day, S>, <dR/daz, S>)
+__device__ __forceinline__ void rot3_contract(const Rot3& R, const float (&S)[3][3], float (&o)[3]) {
+  float a = 0.f, b = 0.f, c = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    a = fmaf(R.r[i][2], S[i][1], fmaf(-R.r[i][1], S[i][2], a));
+    b = fmaf(R.ud[i], S[i][0], fmaf(R.r[i][0], fmaf(R.sa, S[i][1], R.ca * S[i][2]), b));
+    c = fmaf(-R.r[1][i], S[0][i], fmaf(R.r[0][i], S[1][i], c));
+  }
+  o[0] = a; o[1] = b; o[2] = c;
+}
+
+// The direction of vertex v, components [0, NC): p = M^-1 r + beta p_old
+// (update) or the given p; the same roundings wherever it is formed.
+template <int NC>
+__device__ __forceinline__ void mesh_direction(const MeshProb& pr, int v, long long pl, int update, float beta,
+                                               const float* __restrict__ pin, float (&o)[NC]) {
+  if (update) {
+    float m[NC < 4 ? 1 : 4];
+#pragma unroll
+    for (int k = 0; k < (NC < 4 ? 1 : 4); ++k) m[k] = __ldg(pr.m + k * pl + v);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      o[c] = __fmul_rn(m[c < 3 ? 0 : c - 2], pr.r[c * pl + v]);
+      if (beta != 0.0f) o[c] = __fmaf_rn(beta, pin[c * pl + v], o[c]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) o[c] = pin[c * pl + v];
+  }
+}
+
+constexpr int MESH_ECAP = 2048;   // tile edges whose J_e p is kept in shared memory
+
+__global__ void __launch_bounds__(NT) k_mesh_apply_fused(const MeshProb* __restrict__ probs,
+                                                         const Chunk* __restrict__ chunks,
+                                                         double* __restrict__ part,
+                                                         const float* __restrict__ p_override, int par,
+                                                         int update) {
+  pdl_begin();
+  const Chunk ch = chunks[blockIdx.x];
+  const MeshProb pr = probs[ch.prob];
+  Scalars* s = pr.s;
+  if (s->done || !s->pcg_active) return;
+  __shared__ float sp[3][NT], su[3][NT];
+  __shared__ float st[3][MESH_ECAP];
+  const long long pl = pr.Vp;
+  const float sw = pr.s_w;
+  const float beta = s->beta_f;
+  const float lam = pr.lm ? s->lambda_f : 0.0f;
+  const float* __restrict__ pin = p_override ? p_override : pr.p + (long long)(par & 1) * 6 * pl;
+  float* __restrict__ pout = pr.p + (long long)((par + 1) & 1) * 6 * pl;
+  const int tid = threadIdx.x;
+  F2 acc = f2_zero();
+  for (int vb = ch.begin; vb < ch.end; vb += NT) {
+    const int ve = min(vb + NT, ch.end);
+    const int i = vb + tid;
+    const bool own = i < ve;
+    float pi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float ui[3] = {0.f, 0.f, 0.f}, cs[6] = {1.f, 0.f, 1.f, 0.f, 1.f, 0.f};
+    int o0 = 0, o1 = 0;
+    if (own) {
+      o0 = pr.orow[i];
+      o1 = pr.orow[i + 1];
+      mesh_direction<6>(pr, i, pl, update, beta, pin, pi);
+      if (update) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) pout[c * pl + i] = pi[c];
+      }
+      const GeoRec g = load_geo(pr.grec, i);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ui[c] = g.U[c];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) cs[c] = g.cs[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { sp[c][tid] = pi[c]; su[c][tid] = ui[c]; }
+    const int ebase = pr.orow[vb];
+    const int ncap = min(pr.orow[ve] - ebase, MESH_ECAP);
+    __syncthreads();
+    float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (own) {
+      const Rot3 R = rot3(cs);
+      float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+      {
+        float M[3][3];
+        rot3_dir(R, pi[3], pi[4], pi[5], M);
+        for (int k = o0; k < o1; ++k) {
+          const int j = pr.e1[k];
+          float pj[3], uj[3];
+          if (j >= vb && j < ve) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) { pj[c] = sp[c][j - vb]; uj[c] = su[c][j - vb]; }
+          } else {
+            mesh_direction<3>(pr, j, pl, update, beta, pin, pj);
+            const float4 g = __ldg(pr.grec + 3 * j);
+            uj[0] = g.x; uj[1] = g.y; uj[2] = g.z;
+          }
+          const float v[3] = {ui[0] - uj[0], ui[1] - uj[1], ui[2] - uj[2]};
+          float t[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float mv = fmaf(M[a][0], v[0], fmaf(M[a][1], v[1], M[a][2] * v[2]));
+            t[a] = sw * ((pi[a] - pj[a]) - mv);
+            q[a] = fmaf(sw, t[a], q[a]);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) S[a][b] = fmaf(t[a], v[b], S[a][b]);
+          }
+          if (k - ebase < ncap) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) st[a][k - ebase] = t[a];
+          }
+        }
+      }
+      float ga[3];
+      rot3_contract(R, S, ga);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) q[3 + m] = -sw * ga[m];
+    }
+    __syncthreads();
+    if (own) {
+      for (int k = pr.irow[i]; k < pr.irow[i + 1]; ++k) {
+        const int pos = pr.itpos[k] - ebase;
+        float t[3];
+        if (pos >= 0 && pos < ncap) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) t[a] = st[a][pos];
+        } else {
+          // the edge (j, i) starts outside this tile: its residual from j's data
+          const int j = pr.isrc[k];
+          float pj[6];
+          mesh_direction<6>(pr, j, pl, update, beta, pin, pj);
+          const GeoRec gj = load_geo(pr.grec, j);
+          const Rot3 Rj = rot3(gj.cs);
+          float Mj[3][3];
+          rot3_dir(Rj, pj[3], pj[4], pj[5], Mj);
+          const float v[3] = {gj.U[0] - ui[0], gj.U[1] - ui[1], gj.U[2] - ui[2]};
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float mv = fmaf(Mj[a][0], v[0], fmaf(Mj[a][1], v[1], Mj[a][2] * v[2]));
+            t[a] = sw * ((pj[a] - pi[a]) - mv);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) q[a] = fmaf(-sw, t[a], q[a]);
+      }
+      if (handle_of(pr, i) >= 0) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[c] = fmaf(pr.w_fit, pi[c], q[c]);
+      }
+      if (pr.lm) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) q[c] = fmaf(lam * pr.dc[(c < 3 ? 0 : c - 2) * pl + i], pi[c], q[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        pr.q[c * pl + i] = q[c];
+        f2_add_prod(acc, pi[c], q[c]);
+      }
+    }
+    __syncthreads();   // the next tile reuses the shared arrays
+  }
+  pdl_trigger();
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+    double pq, unused;
+    gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, pq, unused);
+    if (threadIdx.x == 0) {
+      s->pq = pq;
+      if (pq > 0.0 && isfinite(pq)) {
+        s->alpha_f = (float)(s->rz / pq);
+      } else {
+        s->alpha_f = 0.f;
+        s->pcg_active = 0;
+        if (!isfinite(pq)) s->nonfinite = 1;
+      }
+    }
+  }
+}
+
 // delta += alpha p, r -= alpha q, z = M^-1 r, float64 r.z -> beta; four
 // vertices per thread, all loads first.
 __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__ probs,
@@ -599,11 +829,12 @@ void launch_mesh_init(const MeshLaunch& L, int k_outer, float dmin, float dmax) 
 void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, int update) {
   if (L.dim == 2) return launch_wg_apply(L, p_override, par, update);
   if (L.dim == 12) return launch_ed_apply(L, p_override, par, update);
+  if (!L.grid3) {
+    launch_pdl(k_mesh_apply_fused, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, p_override, par, update);
+    return;
+  }
   launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, p_override, par, update);
-  if (L.grid3)
-    launch_pdl(k_mesh_apply_pull<true>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
-  else
-    launch_pdl(k_mesh_apply_pull<false>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
+  launch_pdl(k_mesh_apply_pull<true>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
 }
 
 void launch_mesh_update(const MeshLaunch& L, int par) {

@@ -120,6 +120,7 @@ struct MeshProb {
   const int* orow;              // V + 1: out-edges of v are e1[orow[v] .. orow[v+1])
   const int* irow;              // V + 1: in-edges of v come from isrc[irow[v] .. irow[v+1])
   const int* isrc;              // E: sources of the in-edges, ascending per vertex
+  const int* itpos;             // E: position of each in-edge (irow order) in the sorted edge list
   float *d, *r, *p, *q;         // 6 planes each
   float *m, *dc;                // 4 planes: displacement, ax, ay, az
   float4* grec;                 // 3 float4 per vertex: U, cos / sin of the angles (PCGInit)

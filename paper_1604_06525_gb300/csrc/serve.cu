@@ -64,9 +64,9 @@ size_t estimate_grid(const opt_grid_desc& d, int tile_w) {
 }
 size_t estimate_graph(const opt_graph_desc& d) {
   const size_t pl = round32((size_t)d.V);
-  // 48 planes + the 3 + 2 float4 records per vertex, edges (sorted copy and
-  // in-edge sources), row pointers
-  return 68 * pl * 4 + (size_t)d.E * 12 + 8 * pl + (size_t)d.n_handles * 16 + (1 << 16);
+  // 48 planes + the 3 + 2 float4 records per vertex, edges (sorted copy,
+  // in-edge sources and positions), row pointers
+  return 68 * pl * 4 + (size_t)d.E * 16 + 8 * pl + (size_t)d.n_handles * 16 + (1 << 16);
 }
 
 }  // namespace
