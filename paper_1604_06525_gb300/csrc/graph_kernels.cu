@@ -493,7 +493,22 @@ __device__ __forceinline__ void mesh_direction(const MeshProb& pr, int v, long l
   }
 }
 
-constexpr int MESH_ECAP = 2048;   // tile edges whose J_e p is kept in shared memory
+constexpr int MESH_ECAP = 2048;   // general path: tile edges whose J_e p is kept in shared memory
+constexpr int MT_NV = VT + MT_HALO;
+// dynamic shared memory of k_mesh_apply_fused (the tiled layout; the general
+// path uses a smaller prefix of it)
+constexpr size_t MESH_FUSED_SMEM = (size_t)(15 * MT_NV + 3 * MT_SLOTS) * sizeof(float);
+static_assert((6 * NT + 3 * MESH_ECAP) * sizeof(float) <= MESH_FUSED_SMEM, "general-path layout must fit");
+
+// J_e p of an edge (a, b) from a's rotation-derivative matrix M_a: s_w [(p_a - p_b) - M_a v], v = U_a - U_b
+__device__ __forceinline__ void edge_jp(float sw, const float (&M)[3][3], const float* pa, const float* pb,
+                                        const float (&v)[3], float (&t)[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float mv = fmaf(M[a][0], v[0], fmaf(M[a][1], v[1], M[a][2] * v[2]));
+    t[a] = sw * ((pa[a] - pb[a]) - mv);
+  }
+}
 
 __global__ void __launch_bounds__(NT) k_mesh_apply_fused(const MeshProb* __restrict__ probs,
                                                          const Chunk* __restrict__ chunks,
@@ -505,8 +520,7 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_fused(const MeshProb* __restr
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
-  __shared__ float sp[3][NT], su[3][NT];
-  __shared__ float st[3][MESH_ECAP];
+  extern __shared__ float smem[];
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
   const float beta = s->beta_f;
@@ -514,82 +528,148 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_fused(const MeshProb* __restr
   const float* __restrict__ pin = p_override ? p_override : pr.p + (long long)(par & 1) * 6 * pl;
   float* __restrict__ pout = pr.p + (long long)((par + 1) & 1) * 6 * pl;
   const int tid = threadIdx.x;
+  const bool tiled = pr.hptr != nullptr;
   F2 acc = f2_zero();
   for (int vb = ch.begin; vb < ch.end; vb += NT) {
     const int ve = min(vb + NT, ch.end);
     const int i = vb + tid;
     const bool own = i < ve;
+    const int ebase = pr.orow[vb];
     float pi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float ui[3] = {0.f, 0.f, 0.f}, cs[6] = {1.f, 0.f, 1.f, 0.f, 1.f, 0.f};
-    int o0 = 0, o1 = 0;
-    if (own) {
-      o0 = pr.orow[i];
-      o1 = pr.orow[i + 1];
-      mesh_direction<6>(pr, i, pl, update, beta, pin, pi);
-      if (update) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) pout[c * pl + i] = pi[c];
-      }
-      const GeoRec g = load_geo(pr.grec, i);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) ui[c] = g.U[c];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) cs[c] = g.cs[c];
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) { sp[c][tid] = pi[c]; su[c][tid] = ui[c]; }
-    const int ebase = pr.orow[vb];
-    const int ncap = min(pr.orow[ve] - ebase, MESH_ECAP);
-    __syncthreads();
     float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    int ncap;
+    // shared layout, tiled: p[6][MT_NV] U[3][MT_NV] cs[6][MT_NV] t[3][MT_SLOTS];
+    // general: p[3][NT] U[3][NT] t[3][MESH_ECAP]
+    float* const sp = smem;
+    float* const su = smem + (tiled ? 6 * MT_NV : 3 * NT);
+    float* const scs = su + 3 * MT_NV;
+    float* const st = tiled ? smem + 15 * MT_NV : smem + 6 * NT;
+    const int LD = tiled ? MT_NV : NT;          // leading dimension of sp / su
+    const int SD = tiled ? MT_SLOTS : MESH_ECAP;
+    if (tiled) {
+      // A: the tile's vertices and its halo: direction, geometry
+      const int T = vb / VT;
+      const int h0 = pr.hptr[T], nh = pr.hptr[T + 1] - h0;
+      for (int l = tid; l < VT + nh; l += NT) {
+        const int v = l < VT ? vb + l : pr.hvtx[h0 + l - VT];
+        if (l < VT && v >= ve) continue;
+        float pv[6];
+        mesh_direction<6>(pr, v, pl, update, beta, pin, pv);
+        if (l < VT && update) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) pout[c * pl + v] = pv[c];
+        }
+        const GeoRec g = load_geo(pr.grec, v);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) { sp[c * MT_NV + l] = pv[c]; scs[c * MT_NV + l] = g.cs[c]; }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) su[c * MT_NV + l] = g.U[c];
+      }
+      ncap = MT_SLOTS;
+      __syncthreads();
+      if (own) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) { pi[c] = sp[c * MT_NV + tid]; cs[c] = scs[c * MT_NV + tid]; }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ui[c] = su[c * MT_NV + tid];
+      }
+    } else {
+      if (own) {
+        mesh_direction<6>(pr, i, pl, update, beta, pin, pi);
+        if (update) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) pout[c * pl + i] = pi[c];
+        }
+        const GeoRec g = load_geo(pr.grec, i);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ui[c] = g.U[c];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) cs[c] = g.cs[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { sp[c * NT + tid] = pi[c]; su[c * NT + tid] = ui[c]; }
+      ncap = min(pr.orow[ve] - ebase, MESH_ECAP);
+      __syncthreads();
+    }
+    // B: the vertex's own edges (displacement rows, S = sum t v^T), J_e p to shared memory
+    const Rot3 R = rot3(cs);
     if (own) {
-      const Rot3 R = rot3(cs);
-      float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-      {
-        float M[3][3];
-        rot3_dir(R, pi[3], pi[4], pi[5], M);
-        for (int k = o0; k < o1; ++k) {
+      float M[3][3];
+      rot3_dir(R, pi[3], pi[4], pi[5], M);
+      const int o0 = pr.orow[i], o1 = pr.orow[i + 1];
+      for (int k = o0; k < o1; ++k) {
+        float pj[3], uj[3];
+        if (tiled) {
+          const int l = pr.lnbr[k];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) { pj[c] = sp[c * MT_NV + l]; uj[c] = su[c * MT_NV + l]; }
+        } else {
           const int j = pr.e1[k];
-          float pj[3], uj[3];
           if (j >= vb && j < ve) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) { pj[c] = sp[c][j - vb]; uj[c] = su[c][j - vb]; }
+            for (int c = 0; c < 3; ++c) { pj[c] = sp[c * NT + j - vb]; uj[c] = su[c * NT + j - vb]; }
           } else {
             mesh_direction<3>(pr, j, pl, update, beta, pin, pj);
             const float4 g = __ldg(pr.grec + 3 * j);
             uj[0] = g.x; uj[1] = g.y; uj[2] = g.z;
           }
-          const float v[3] = {ui[0] - uj[0], ui[1] - uj[1], ui[2] - uj[2]};
-          float t[3];
+        }
+        const float v[3] = {ui[0] - uj[0], ui[1] - uj[1], ui[2] - uj[2]};
+        float t[3];
+        edge_jp(sw, M, pi, pj, v, t);
 #pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const float mv = fmaf(M[a][0], v[0], fmaf(M[a][1], v[1], M[a][2] * v[2]));
-            t[a] = sw * ((pi[a] - pj[a]) - mv);
-            q[a] = fmaf(sw, t[a], q[a]);
+        for (int a = 0; a < 3; ++a) {
+          q[a] = fmaf(sw, t[a], q[a]);
 #pragma unroll
-            for (int b = 0; b < 3; ++b) S[a][b] = fmaf(t[a], v[b], S[a][b]);
-          }
-          if (k - ebase < ncap) {
+          for (int b = 0; b < 3; ++b) S[a][b] = fmaf(t[a], v[b], S[a][b]);
+        }
+        if (k - ebase < ncap) {
 #pragma unroll
-            for (int a = 0; a < 3; ++a) st[a][k - ebase] = t[a];
-          }
+          for (int a = 0; a < 3; ++a) st[a * SD + k - ebase] = t[a];
         }
       }
+    }
+    if (tiled) {
+      // in-edges from outside the tile: J_e p from the staged halo vertex
+      const int T = vb / VT;
+      const int r0 = pr.rptr[T], nr = pr.rptr[T + 1] - r0;
+      const int nout = pr.orow[ve] - ebase;
+      for (int r = tid; r < nr; r += NT) {
+        const int w = pr.rin[r0 + r];
+        const int sl = w >> 16, dl = w & 0xffff;
+        float pj[6], csj[6], d[3], v[3];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) { pj[c] = sp[c * MT_NV + sl]; csj[c] = scs[c * MT_NV + sl]; }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          d[c] = sp[c * MT_NV + dl];
+          v[c] = su[c * MT_NV + sl] - su[c * MT_NV + dl];
+        }
+        const Rot3 Rj = rot3(csj);
+        float Mj[3][3], t[3];
+        rot3_dir(Rj, pj[3], pj[4], pj[5], Mj);
+        edge_jp(sw, Mj, pj, d, v, t);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) st[a * MT_SLOTS + nout + r] = t[a];
+      }
+    }
+    __syncthreads();
+    // C: angle rows, in-edge displacement rows, fit, damping
+    if (own) {
       float ga[3];
       rot3_contract(R, S, ga);
 #pragma unroll
       for (int m = 0; m < 3; ++m) q[3 + m] = -sw * ga[m];
-    }
-    __syncthreads();
-    if (own) {
       for (int k = pr.irow[i]; k < pr.irow[i + 1]; ++k) {
-        const int pos = pr.itpos[k] - ebase;
         float t[3];
-        if (pos >= 0 && pos < ncap) {
+        const int slot = tiled ? pr.itslot[k] : pr.itpos[k] - ebase;
+        if (slot >= 0 && slot < ncap) {
 #pragma unroll
-          for (int a = 0; a < 3; ++a) t[a] = st[a][pos];
+          for (int a = 0; a < 3; ++a) t[a] = st[a * SD + slot];
         } else {
-          // the edge (j, i) starts outside this tile: its residual from j's data
+          // general path, the edge (j, i) starts outside this tile: its residual from j's data
           const int j = pr.isrc[k];
           float pj[6];
           mesh_direction<6>(pr, j, pl, update, beta, pin, pj);
@@ -598,11 +678,7 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_fused(const MeshProb* __restr
           float Mj[3][3];
           rot3_dir(Rj, pj[3], pj[4], pj[5], Mj);
           const float v[3] = {gj.U[0] - ui[0], gj.U[1] - ui[1], gj.U[2] - ui[2]};
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const float mv = fmaf(Mj[a][0], v[0], fmaf(Mj[a][1], v[1], Mj[a][2] * v[2]));
-            t[a] = sw * ((pj[a] - pi[a]) - mv);
-          }
+          edge_jp(sw, Mj, pj, pi, v, t);
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a) q[a] = fmaf(-sw, t[a], q[a]);
@@ -830,7 +906,12 @@ void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, in
   if (L.dim == 2) return launch_wg_apply(L, p_override, par, update);
   if (L.dim == 12) return launch_ed_apply(L, p_override, par, update);
   if (!L.grid3) {
-    launch_pdl(k_mesh_apply_fused, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part, p_override, par, update);
+    static const bool smem_ok =
+        cudaFuncSetAttribute(k_mesh_apply_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)MESH_FUSED_SMEM) == cudaSuccess;
+    (void)smem_ok;
+    launch_pdl(k_mesh_apply_fused, L.nvchunks, NT, MESH_FUSED_SMEM, L.stream, L.probs, L.vchunks, L.part,
+               p_override, par, update);
     return;
   }
   launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, p_override, par, update);

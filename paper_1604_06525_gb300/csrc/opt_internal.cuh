@@ -42,6 +42,11 @@ constexpr int NT = 256;           // threads per block (grid and graph kernels)
 constexpr int HW = TW + 2;        // staged halo width
 constexpr int HH = TH + 2;        // staged halo height
 constexpr int VT = 256;           // vertices per vertex tile (graph)
+// capacities of the tiled ARAP-mesh apply (one tile of VT vertices per pass):
+// out-of-tile neighbours staged with the tile, and J_e p slots (the tile's
+// out-edges plus its in-edges that start outside the tile)
+constexpr int MT_HALO = 384;
+constexpr int MT_SLOTS = 2304;
 
 // Device-resident scalars of one problem.  Written only by the single
 // finishing block of a reduction or by the one-thread LM decision kernel.
@@ -121,6 +126,14 @@ struct MeshProb {
   const int* irow;              // V + 1: in-edges of v come from isrc[irow[v] .. irow[v+1])
   const int* isrc;              // E: sources of the in-edges, ascending per vertex
   const int* itpos;             // E: position of each in-edge (irow order) in the sorted edge list
+  // vertex-tile tables of the tiled apply (NULL: the problem exceeds the
+  // capacities above and uses the general path)
+  const int* hptr;              // tiles + 1: the halo of tile T is hvtx[hptr[T] .. hptr[T+1])
+  const int* hvtx;              // out-of-tile vertices adjacent to the tile, ascending
+  const int* lnbr;              // E: each edge's far end as an index into its tile's vertex + halo table
+  const int* rptr;              // tiles + 1: in-edges from outside tile T are rin[rptr[T] .. rptr[T+1])
+  const int* rin;               // (source table index << 16) | target index within the tile
+  const int* itslot;            // E: shared-memory slot of each in-edge's J_e p (irow order)
   float *d, *r, *p, *q;         // 6 planes each
   float *m, *dc;                // 4 planes: displacement, ax, ay, az
   float4* grec;                 // 3 float4 per vertex: U, cos / sin of the angles (PCGInit)

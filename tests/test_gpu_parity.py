@@ -187,6 +187,38 @@ def test_mesh_one_way_edges_and_isolated_vertices(api, keep):
     assert relE(Eg, E) <= TOL_PRODUCT
 
 
+@pytest.mark.parametrize("hub_edges", [600, 2600])
+def test_mesh_hub_vertex(api, hub_edges):
+    """A hub vertex joined to many others (both directions): its tile's halo
+    outgrows the tiled apply's 384 staged neighbours (600) or its edges
+    outgrow the 2,304 shared-memory slots (2600), so the product runs on the
+    general path; J^T J p, J^T F and the LM damping still match the oracle."""
+    import torch
+    base = synth.mesh_problem(4, seed=71, handle_frac=0.02)
+    rng = np.random.default_rng(3)
+    others = rng.choice(np.arange(1, base.V), size=hub_edges, replace=False).astype(np.int32)
+    v0 = np.concatenate([base.v0, np.zeros(hub_edges, np.int32), others]).astype(np.int32)
+    v1 = np.concatenate([base.v1, others, np.zeros(hub_edges, np.int32)]).astype(np.int32)
+    order = np.lexsort((v1, v0))
+    prob = synth.MeshProblem(base.V, base.urshape, v0[order], v1[order], base.x0, base.handle_idx,
+                             base.handle_target)
+    prob = perturbed(prob, 0.1, 4)
+    e = oracle.make_energy(prob)
+    x = prob.x0.reshape(-1).astype(np.float64)
+    gp = api.Problem(prob)
+    p = random_direction(prob, 6)
+    jtf, diag, E = oracle.jtf_diag(e, x)
+    for lam in (0.0, 0.3):
+        q, pq = gp.apply_jtj(torch.as_tensor(p, device="cuda"), lam)
+        qref = oracle.apply_jtj(e, x, p.astype(np.float64), lam, np.clip(diag, 1e-6, 1e32))
+        assert rel(q.cpu().numpy(), qref) <= TOL_PRODUCT
+        assert relE(pq, float(p.astype(np.float64) @ qref)) <= TOL_PRODUCT
+    g, d, Eg = gp.eval_jtf()
+    assert rel(g.cpu().numpy(), jtf) <= TOL_PRODUCT
+    assert relE(Eg, E) <= TOL_PRODUCT
+    gp.close()
+
+
 def test_mesh_unsorted_edges_are_sorted_by_the_library(api):
     import torch
     prob = make_mesh(2, 0.2, seed=51)
