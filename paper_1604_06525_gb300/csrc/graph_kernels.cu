@@ -497,7 +497,7 @@ constexpr int MESH_ECAP = 2048;   // general path: tile edges whose J_e p is kep
 constexpr int MT_NV = VT + MT_HALO;
 // dynamic shared memory of k_mesh_apply_fused (the tiled layout; the general
 // path uses a smaller prefix of it)
-constexpr size_t MESH_FUSED_SMEM = (size_t)(15 * MT_NV + 3 * MT_SLOTS) * sizeof(float);
+constexpr size_t MESH_FUSED_SMEM = (size_t)(15 * MT_NV + 5 * MT_SLOTS) * sizeof(float);
 static_assert((6 * NT + 3 * MESH_ECAP) * sizeof(float) <= MESH_FUSED_SMEM, "general-path layout must fit");
 
 // J_e p of an edge (a, b) from a's rotation-derivative matrix M_a: s_w [(p_a - p_b) - M_a v], v = U_a - U_b
@@ -540,18 +540,25 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_fused(const MeshProb* __restr
     float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     int ncap;
-    // shared layout, tiled: p[6][MT_NV] U[3][MT_NV] cs[6][MT_NV] t[3][MT_SLOTS];
+    // shared layout, tiled: p[6][MT_NV] U[3][MT_NV] cs[6][MT_NV] t[3][MT_SLOTS]
+    // out-edge table index[MT_SLOTS] in-edge slot[MT_SLOTS];
     // general: p[3][NT] U[3][NT] t[3][MESH_ECAP]
     float* const sp = smem;
     float* const su = smem + (tiled ? 6 * MT_NV : 3 * NT);
     float* const scs = su + 3 * MT_NV;
     float* const st = tiled ? smem + 15 * MT_NV : smem + 6 * NT;
-    const int LD = tiled ? MT_NV : NT;          // leading dimension of sp / su
     const int SD = tiled ? MT_SLOTS : MESH_ECAP;
+    int* const sln = reinterpret_cast<int*>(smem + 15 * MT_NV + 3 * MT_SLOTS);   // tiled only
+    int* const sis = sln + MT_SLOTS;
+    const int ibase = pr.irow[vb];
     if (tiled) {
       // A: the tile's vertices and its halo: direction, geometry
       const int T = vb / VT;
       const int h0 = pr.hptr[T], nh = pr.hptr[T + 1] - h0;
+      // the tile's edge tables, coalesced (the loops below then read shared memory only)
+      const int nout = pr.orow[ve] - ebase, nin = pr.irow[ve] - ibase;
+      for (int k = tid; k < nout; k += NT) sln[k] = pr.lnbr[ebase + k];
+      for (int k = tid; k < nin; k += NT) sis[k] = pr.itslot[ibase + k];
       for (int l = tid; l < VT + nh; l += NT) {
         const int v = l < VT ? vb + l : pr.hvtx[h0 + l - VT];
         if (l < VT && v >= ve) continue;
@@ -602,7 +609,7 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_fused(const MeshProb* __restr
       for (int k = o0; k < o1; ++k) {
         float pj[3], uj[3];
         if (tiled) {
-          const int l = pr.lnbr[k];
+          const int l = sln[k - ebase];
 #pragma unroll
           for (int c = 0; c < 3; ++c) { pj[c] = sp[c * MT_NV + l]; uj[c] = su[c * MT_NV + l]; }
         } else {
@@ -664,7 +671,7 @@ __global__ void __launch_bounds__(NT) k_mesh_apply_fused(const MeshProb* __restr
       for (int m = 0; m < 3; ++m) q[3 + m] = -sw * ga[m];
       for (int k = pr.irow[i]; k < pr.irow[i + 1]; ++k) {
         float t[3];
-        const int slot = tiled ? pr.itslot[k] : pr.itpos[k] - ebase;
+        const int slot = tiled ? sis[k - ibase] : pr.itpos[k] - ebase;
         if (slot >= 0 && slot < ncap) {
 #pragma unroll
           for (int a = 0; a < 3; ++a) t[a] = st[a * SD + slot];

@@ -194,7 +194,7 @@ def test_mesh_hub_vertex(api, hub_edges):
     outgrow the 2,304 shared-memory slots (2600), so the product runs on the
     general path; J^T J p, J^T F and the LM damping still match the oracle."""
     import torch
-    base = synth.mesh_problem(4, seed=71, handle_frac=0.02)
+    base = synth.mesh_problem(5, seed=71, handle_frac=0.02)
     rng = np.random.default_rng(3)
     others = rng.choice(np.arange(1, base.V), size=hub_edges, replace=False).astype(np.int32)
     v0 = np.concatenate([base.v0, np.zeros(hub_edges, np.int32), others]).astype(np.int32)
