@@ -272,7 +272,7 @@ GridLaunch grid_launch(const opt_problem* pb, cudaStream_t st) {
 MeshLaunch mesh_launch(const opt_problem* pb, cudaStream_t st) {
   return MeshLaunch{pb->dm, pb->d_vchunks, pb->d_echunks, pb->d_part, pb->nvchunks,
                     pb->nechunks, st, pb->kind == K_WARPG ? 2 : (pb->kind == K_EMBED ? 12 : 3),
-                    pb->kind == K_VOLUME ? 1 : 0};
+                    pb->kind == K_VOLUME ? 1 : 0, pb->d_tchunks, pb->ntchunks};
 }
 
 opt_status upload_desc(opt_problem* pb, cudaStream_t st) {
@@ -924,6 +924,9 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   std::vector<Chunk> vch = make_chunks_balanced(nvt, target, 0);
   for (Chunk& c : vch) { c.begin *= VT; c.end = std::min(V, c.end * VT); }
   std::vector<Chunk> ech = make_chunks_balanced(E, target, 0);
+  std::vector<Chunk> tch;
+  if (tiled)
+    for (int T = 0; T < nvt; ++T) tch.push_back(Chunk{0, T * VT, std::min(V, (T + 1) * VT), 0});
 
   const size_t pl = (size_t)Vp;
   float *U = nullptr, *dgw = nullptr, *m = nullptr, *dc = nullptr, *dhtgt = nullptr;
@@ -988,7 +991,12 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   CKS(upload(q->d_echunks, ech));
   q->nvchunks = (int)vch.size();
   q->nechunks = (int)ech.size();
-  CKS(dalloc(q, &q->d_part, 2 * std::max(vch.size(), ech.size())));
+  if (tiled) {
+    CKS(dalloc(q, &q->d_tchunks, tch.size()));
+    CKS(upload(q->d_tchunks, tch));
+    q->ntchunks = (int)tch.size();
+  }
+  CKS(dalloc(q, &q->d_part, 2 * std::max({vch.size(), ech.size(), tch.size()})));
   CKS(dalloc(q, &q->dm, 1));
   for (int k = 0; k < NXg; ++k) q->user_x[k] = ux[k];
   q->h_e0 = e0;
@@ -999,6 +1007,7 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   g.V = V; g.E = E; g.Vp = Vp;
   g.vchunk_begin = 0; g.vchunk_end = q->nvchunks;
   g.echunk_begin = 0; g.echunk_end = q->nechunks;
+  g.tchunk_begin = 0; g.tchunk_end = q->ntchunks;
   g.w_reg = d->w_reg; g.w_fit = d->w_fit;
   g.s_w = std::sqrt(d->w_reg); g.s_f = std::sqrt(d->w_fit);
   g.w_rot = ed ? ed->w_rot : 0.f; g.s_r = std::sqrt(g.w_rot);
@@ -1322,8 +1331,8 @@ static opt_status rechunk(opt_problem* pb, int per) {
     std::vector<Chunk> ech = per > 0 ? make_chunks(pb->E, per * VT, 0) : make_chunks_balanced(pb->E, target, 0);
     if ((int)vch.size() > pb->nvchunks) CKS(dalloc(pb, &pb->d_vchunks, vch.size()));
     if ((int)ech.size() > pb->nechunks) CKS(dalloc(pb, &pb->d_echunks, ech.size()));
-    const size_t need = 2 * std::max(vch.size(), ech.size());
-    if (need > 2 * (size_t)std::max(pb->nvchunks, pb->nechunks)) CKS(dalloc(pb, &pb->d_part, need));
+    const size_t need = 2 * std::max({vch.size(), ech.size(), (size_t)pb->ntchunks});
+    if (need > 2 * (size_t)std::max({pb->nvchunks, pb->nechunks, pb->ntchunks})) CKS(dalloc(pb, &pb->d_part, need));
     CKS(upload(pb->d_vchunks, vch));
     CKS(upload(pb->d_echunks, ech));
     pb->nvchunks = (int)vch.size();

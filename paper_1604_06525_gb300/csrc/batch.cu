@@ -121,8 +121,9 @@ struct MeshGroup {
   MeshProb* d_probs = nullptr;
   Chunk* d_vch = nullptr;
   Chunk* d_ech = nullptr;
+  Chunk* d_tch = nullptr;              // tile chunks of the tiled ARAP-mesh apply (NULL: some member untiled)
   double* d_part = nullptr;
-  int nv = 0, ne = 0;
+  int nv = 0, ne = 0, nt = 0;
 };
 
 }  // namespace
@@ -207,7 +208,9 @@ opt_status build_tables(opt_batch* b, int tpc) {
   for (MeshGroup& g : b->graphs) {
     if (g.members.empty()) continue;
     std::vector<MeshProb> mp;
-    std::vector<Chunk> vch, ech;
+    std::vector<Chunk> vch, ech, tch;
+    bool tiled = true;
+    for (size_t mi = 0; mi < g.members.size(); ++mi) tiled = tiled && b->probs[g.members[mi]]->d_tchunks;
     for (size_t mi = 0; mi < g.members.size(); ++mi) {
       opt_problem* pb = b->probs[g.members[mi]];
       std::vector<Chunk> v(pb->nvchunks), e(pb->nechunks);
@@ -220,15 +223,26 @@ opt_status build_tables(opt_batch* b, int tpc) {
       d.echunk_begin = (int)ech.size();
       for (Chunk c : e) { c.prob = (int)mi; ech.push_back(c); }
       d.echunk_end = (int)ech.size();
+      d.tchunk_begin = (int)tch.size();
+      if (tiled) {
+        std::vector<Chunk> t(pb->ntchunks);
+        BCK(cudaMemcpy(t.data(), pb->d_tchunks, t.size() * sizeof(Chunk), cudaMemcpyDeviceToHost));
+        for (Chunk c : t) { c.prob = (int)mi; tch.push_back(c); }
+      }
+      d.tchunk_end = (int)tch.size();
       mp.push_back(d);
     }
     opt_status s;
     if ((s = bupload(b->table_allocs, &g.d_probs, mp)) != OPT_OK) return s;
     if ((s = bupload(b->table_allocs, &g.d_vch, vch)) != OPT_OK) return s;
     if ((s = bupload(b->table_allocs, &g.d_ech, ech)) != OPT_OK) return s;
-    if ((s = balloc(b->table_allocs, &g.d_part, 2 * std::max(vch.size(), ech.size()))) != OPT_OK) return s;
+    g.d_tch = nullptr;
+    if (tiled && (s = bupload(b->table_allocs, &g.d_tch, tch)) != OPT_OK) return s;
+    if ((s = balloc(b->table_allocs, &g.d_part, 2 * std::max({vch.size(), ech.size(), tch.size()}))) != OPT_OK)
+      return s;
     g.nv = (int)vch.size();
     g.ne = (int)ech.size();
+    g.nt = tiled ? (int)tch.size() : 0;
   }
   b->tiles_per_chunk = tpc;
   return OPT_OK;
@@ -238,7 +252,7 @@ GridLaunch gl(const GridGroup& g, cudaStream_t st) {
   return GridLaunch{g.d_probs, g.d_chunks, g.d_tiles, g.d_part, g.nchunks, st, g.tw, g.masked};
 }
 MeshLaunch ml(const MeshGroup& g, cudaStream_t st) {
-  return MeshLaunch{g.d_probs, g.d_vch, g.d_ech, g.d_part, g.nv, g.ne, st, g.dim, g.grid3};
+  return MeshLaunch{g.d_probs, g.d_vch, g.d_ech, g.d_part, g.nv, g.ne, st, g.dim, g.grid3, g.d_tch, g.nt};
 }
 
 // Uploads the members' descriptors with the solve's flags (outside any capture).

@@ -411,24 +411,25 @@ __global__ void __launch_bounds__(NT, MESH_PULL_MIN_BLOCKS) k_mesh_apply_pull(co
 }
 
 // ---------------------------------------------------------------------------
-// PCGStep: applyJTJ fused with the direction update, ARAP mesh on a graph
+// PCGStep: applyJTJ fused with the direction update, ARAP mesh (tiled)
 // ---------------------------------------------------------------------------
-// A block walks its chunk in vertex tiles of NT vertices, one vertex per
-// thread.  With R = R(A_i) and M_i = sum_m p_i,m dR/dA_m(A_i) formed once per
-// vertex (rot3 / rot3_dir below), the linearized residual of an out-edge
-// e = (i, j) is
-//   t_e = J_e p = s_w [(p_i,d - p_j,d) - M_i v],   v = U_i - U_j,
-// its displacement rows add s_w t_e at i, and its angle rows
-// -s_w (dR/dA_m v) . t_e = -s_w <dR/dA_m, t_e v^T> at i are summed through the
-// 3 x 3 matrix S_i = sum_e t_e v^T (one contraction per vertex, not three
-// derivative vectors per edge).  At j the edge subtracts s_w t_e from the
-// displacement rows: the thread of j reads t_e from shared memory when i lies
-// in the same tile, so each residual is evaluated once, and re-evaluates it
-// from i's data only across tile borders (a few percent of the edges after
-// the Morton renumbering).  The direction p = M^-1 r + beta p_old of the
-// tile's vertices is formed here and written once; a neighbour outside the
-// tile forms its own from (r, M^-1, p_old) with the same roundings.  Every
-// row is summed in a fixed order: results do not depend on scheduling.
+// One block per vertex tile of VT vertices (the tile-chunk table), one vertex
+// per thread.  The block stages the tile's vertices and its halo (the
+// out-of-tile neighbours, a table built at planning) in shared memory: the
+// displacement rows of the direction p = M^-1 r + beta p_old (formed here,
+// halo included, with the same roundings everywhere) and the rest position U.
+// With M_i = sum_m p_i,m dR/dA_m(A_i) formed once per vertex (rot3 /
+// rot3_dir), the linearized residual of an out-edge e = (i, j) is
+//   t_e = J_e p = s_w [(p_i,d - p_j,d) - M_i v],   v = U_i - U_j;
+// it adds s_w t_e to i's displacement rows and its angle rows
+// -s_w (dR/dA_m v) . t_e are summed through S_i = sum_e t_e v^T, one
+// contraction per vertex (rot3_contract) instead of three derivative vectors
+// per edge.  Each t_e goes to a shared-memory slot; in-edges that start
+// outside the tile are evaluated edge-parallel from their source's data into
+// further slots; every vertex then subtracts s_w t_e of its in-edges, read
+// from their slots (a slot table built at planning).  So each residual is
+// evaluated once inside a tile and once more per tile border it crosses, no
+// atomic is used, and every row is summed in a fixed order.
 
 // Rotation R = Rz(az) Ry(ay) Rx(ax) from the angles' cos / sin, with
 // u' = dR_:0 / day; the angle derivatives are then
@@ -461,7 +462,7 @@ __device__ __forceinline__ void rot3_dir(const Rot3& R, float pa, float pb, floa
     M[i][2] = fmaf(-pa, R.r[i][1], fmaf(bc, R.r[i][0], pc * dz[i][2]));
   }
 }
-// (<dR/dax, S>, <dR/day, S>, <dR/daz, S>)
+// (<dR/dax, S>, <dR/day, S>, <dR/daz, S>), <A, B> = sum_ij A_ij B_ij
 __device__ __forceinline__ void rot3_contract(const Rot3& R, const float (&S)[3][3], float (&o)[3]) {
   float a = 0.f, b = 0.f, c = 0.f;
 #pragma unroll
@@ -493,14 +494,7 @@ __device__ __forceinline__ void mesh_direction(const MeshProb& pr, int v, long l
   }
 }
 
-constexpr int MESH_ECAP = 2048;   // general path: tile edges whose J_e p is kept in shared memory
-constexpr int MT_NV = VT + MT_HALO;
-// dynamic shared memory of k_mesh_apply_fused (the tiled layout; the general
-// path uses a smaller prefix of it)
-constexpr size_t MESH_FUSED_SMEM = (size_t)(15 * MT_NV + 5 * MT_SLOTS) * sizeof(float);
-static_assert((6 * NT + 3 * MESH_ECAP) * sizeof(float) <= MESH_FUSED_SMEM, "general-path layout must fit");
-
-// J_e p of an edge (a, b) from a's rotation-derivative matrix M_a: s_w [(p_a - p_b) - M_a v], v = U_a - U_b
+// J_e p of an edge (a, b) from a's matrix M_a: s_w [(p_a - p_b) - M_a v], v = U_a - U_b
 __device__ __forceinline__ void edge_jp(float sw, const float (&M)[3][3], const float* pa, const float* pb,
                                         const float (&v)[3], float (&t)[3]) {
 #pragma unroll
@@ -510,206 +504,148 @@ __device__ __forceinline__ void edge_jp(float sw, const float (&M)[3][3], const 
   }
 }
 
-__global__ void __launch_bounds__(NT) k_mesh_apply_fused(const MeshProb* __restrict__ probs,
-                                                         const Chunk* __restrict__ chunks,
-                                                         double* __restrict__ part,
-                                                         const float* __restrict__ p_override, int par,
-                                                         int update) {
+#ifndef MESH_TILED_MIN_BLOCKS
+#define MESH_TILED_MIN_BLOCKS 4   // resident blocks per SM the tiled apply is compiled for
+#endif
+
+__global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
+    const MeshProb* __restrict__ probs, const Chunk* __restrict__ tchunks, double* __restrict__ part,
+    const float* __restrict__ p_override, int par, int update) {
   pdl_begin();
-  const Chunk ch = chunks[blockIdx.x];
+  const Chunk ch = tchunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
-  extern __shared__ float smem[];
+  __shared__ float spu[6][VT + MT_HALO];   // the tile's vertices, then its halo: p_d (3), U (3)
+  __shared__ float st[3][MT_SLOTS];        // J_e p of the tile's out-edges, then of the remote in-edges
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
   const float beta = s->beta_f;
-  const float lam = pr.lm ? s->lambda_f : 0.0f;
   const float* __restrict__ pin = p_override ? p_override : pr.p + (long long)(par & 1) * 6 * pl;
   float* __restrict__ pout = pr.p + (long long)((par + 1) & 1) * 6 * pl;
   const int tid = threadIdx.x;
-  const bool tiled = pr.hptr != nullptr;
-  F2 acc = f2_zero();
-  for (int vb = ch.begin; vb < ch.end; vb += NT) {
-    const int ve = min(vb + NT, ch.end);
-    const int i = vb + tid;
-    const bool own = i < ve;
-    const int ebase = pr.orow[vb];
-    float pi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float ui[3] = {0.f, 0.f, 0.f}, cs[6] = {1.f, 0.f, 1.f, 0.f, 1.f, 0.f};
-    float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-    int ncap;
-    // shared layout, tiled: p[6][MT_NV] U[3][MT_NV] cs[6][MT_NV] t[3][MT_SLOTS]
-    // out-edge table index[MT_SLOTS] in-edge slot[MT_SLOTS];
-    // general: p[3][NT] U[3][NT] t[3][MESH_ECAP]
-    float* const sp = smem;
-    float* const su = smem + (tiled ? 6 * MT_NV : 3 * NT);
-    float* const scs = su + 3 * MT_NV;
-    float* const st = tiled ? smem + 15 * MT_NV : smem + 6 * NT;
-    const int SD = tiled ? MT_SLOTS : MESH_ECAP;
-    int* const sln = reinterpret_cast<int*>(smem + 15 * MT_NV + 3 * MT_SLOTS);   // tiled only
-    int* const sis = sln + MT_SLOTS;
-    const int ibase = pr.irow[vb];
-    if (tiled) {
-      // A: the tile's vertices and its halo: direction, geometry
-      const int T = vb / VT;
-      const int h0 = pr.hptr[T], nh = pr.hptr[T + 1] - h0;
-      // the tile's edge tables, coalesced (the loops below then read shared memory only)
-      const int nout = pr.orow[ve] - ebase, nin = pr.irow[ve] - ibase;
-      for (int k = tid; k < nout; k += NT) sln[k] = pr.lnbr[ebase + k];
-      for (int k = tid; k < nin; k += NT) sis[k] = pr.itslot[ibase + k];
-      for (int l = tid; l < VT + nh; l += NT) {
-        const int v = l < VT ? vb + l : pr.hvtx[h0 + l - VT];
-        if (l < VT && v >= ve) continue;
-        float pv[6];
-        mesh_direction<6>(pr, v, pl, update, beta, pin, pv);
-        if (l < VT && update) {
+  const int vb = ch.begin, ve = ch.end, T = vb / VT;
+  const int i = vb + tid;
+  const bool own = i < ve;
+  const int ebase = pr.orow[vb], nout = pr.orow[ve] - ebase;
+  const int ibase = pr.irow[vb];
+  // A: this vertex's direction and geometry, its edge tables fetched ahead
+  int o0 = 0, o1 = 0, n0 = 0, n1 = 0;
+  int ln[KB], sl[KB];
+  float pi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float ui[3] = {0.f, 0.f, 0.f}, cs[6] = {1.f, 0.f, 1.f, 0.f, 1.f, 0.f};
+  if (own) {
+    o0 = pr.orow[i]; o1 = pr.orow[i + 1];
+    n0 = pr.irow[i]; n1 = pr.irow[i + 1];
 #pragma unroll
-          for (int c = 0; c < 6; ++c) pout[c * pl + v] = pv[c];
-        }
-        const GeoRec g = load_geo(pr.grec, v);
-#pragma unroll
-        for (int c = 0; c < 6; ++c) { sp[c * MT_NV + l] = pv[c]; scs[c * MT_NV + l] = g.cs[c]; }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) su[c * MT_NV + l] = g.U[c];
-      }
-      ncap = MT_SLOTS;
-      __syncthreads();
-      if (own) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) { pi[c] = sp[c * MT_NV + tid]; cs[c] = scs[c * MT_NV + tid]; }
-#pragma unroll
-        for (int c = 0; c < 3; ++c) ui[c] = su[c * MT_NV + tid];
-      }
-    } else {
-      if (own) {
-        mesh_direction<6>(pr, i, pl, update, beta, pin, pi);
-        if (update) {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) pout[c * pl + i] = pi[c];
-        }
-        const GeoRec g = load_geo(pr.grec, i);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) ui[c] = g.U[c];
-#pragma unroll
-        for (int c = 0; c < 6; ++c) cs[c] = g.cs[c];
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) { sp[c * NT + tid] = pi[c]; su[c * NT + tid] = ui[c]; }
-      ncap = min(pr.orow[ve] - ebase, MESH_ECAP);
-      __syncthreads();
+    for (int t = 0; t < KB; ++t) {
+      ln[t] = o0 + t < o1 ? pr.lnbr[o0 + t] : 0;
+      sl[t] = n0 + t < n1 ? pr.itslot[n0 + t] : 0;
     }
-    // B: the vertex's own edges (displacement rows, S = sum t v^T), J_e p to shared memory
-    const Rot3 R = rot3(cs);
-    if (own) {
-      float M[3][3];
-      rot3_dir(R, pi[3], pi[4], pi[5], M);
-      const int o0 = pr.orow[i], o1 = pr.orow[i + 1];
-      for (int k = o0; k < o1; ++k) {
-        float pj[3], uj[3];
-        if (tiled) {
-          const int l = sln[k - ebase];
+    mesh_direction<6>(pr, i, pl, update, beta, pin, pi);
+    if (update) {
 #pragma unroll
-          for (int c = 0; c < 3; ++c) { pj[c] = sp[c * MT_NV + l]; uj[c] = su[c * MT_NV + l]; }
-        } else {
-          const int j = pr.e1[k];
-          if (j >= vb && j < ve) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) { pj[c] = sp[c * NT + j - vb]; uj[c] = su[c * NT + j - vb]; }
-          } else {
-            mesh_direction<3>(pr, j, pl, update, beta, pin, pj);
-            const float4 g = __ldg(pr.grec + 3 * j);
-            uj[0] = g.x; uj[1] = g.y; uj[2] = g.z;
-          }
-        }
-        const float v[3] = {ui[0] - uj[0], ui[1] - uj[1], ui[2] - uj[2]};
-        float t[3];
-        edge_jp(sw, M, pi, pj, v, t);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          q[a] = fmaf(sw, t[a], q[a]);
-#pragma unroll
-          for (int b = 0; b < 3; ++b) S[a][b] = fmaf(t[a], v[b], S[a][b]);
-        }
-        if (k - ebase < ncap) {
-#pragma unroll
-          for (int a = 0; a < 3; ++a) st[a * SD + k - ebase] = t[a];
-        }
-      }
+      for (int c = 0; c < 6; ++c) pout[c * pl + i] = pi[c];
     }
-    if (tiled) {
-      // in-edges from outside the tile: J_e p from the staged halo vertex
-      const int T = vb / VT;
-      const int r0 = pr.rptr[T], nr = pr.rptr[T + 1] - r0;
-      const int nout = pr.orow[ve] - ebase;
-      for (int r = tid; r < nr; r += NT) {
-        const int w = pr.rin[r0 + r];
-        const int sl = w >> 16, dl = w & 0xffff;
-        float pj[6], csj[6], d[3], v[3];
+    const GeoRec g = load_geo(pr.grec, i);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) { pj[c] = sp[c * MT_NV + sl]; csj[c] = scs[c * MT_NV + sl]; }
+    for (int c = 0; c < 3; ++c) ui[c] = g.U[c];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          d[c] = sp[c * MT_NV + dl];
-          v[c] = su[c * MT_NV + sl] - su[c * MT_NV + dl];
-        }
-        const Rot3 Rj = rot3(csj);
-        float Mj[3][3], t[3];
-        rot3_dir(Rj, pj[3], pj[4], pj[5], Mj);
-        edge_jp(sw, Mj, pj, d, v, t);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) st[a * MT_SLOTS + nout + r] = t[a];
-      }
-    }
-    __syncthreads();
-    // C: angle rows, in-edge displacement rows, fit, damping
-    if (own) {
-      float ga[3];
-      rot3_contract(R, S, ga);
-#pragma unroll
-      for (int m = 0; m < 3; ++m) q[3 + m] = -sw * ga[m];
-      for (int k = pr.irow[i]; k < pr.irow[i + 1]; ++k) {
-        float t[3];
-        const int slot = tiled ? sis[k - ibase] : pr.itpos[k] - ebase;
-        if (slot >= 0 && slot < ncap) {
-#pragma unroll
-          for (int a = 0; a < 3; ++a) t[a] = st[a * SD + slot];
-        } else {
-          // general path, the edge (j, i) starts outside this tile: its residual from j's data
-          const int j = pr.isrc[k];
-          float pj[6];
-          mesh_direction<6>(pr, j, pl, update, beta, pin, pj);
-          const GeoRec gj = load_geo(pr.grec, j);
-          const Rot3 Rj = rot3(gj.cs);
-          float Mj[3][3];
-          rot3_dir(Rj, pj[3], pj[4], pj[5], Mj);
-          const float v[3] = {gj.U[0] - ui[0], gj.U[1] - ui[1], gj.U[2] - ui[2]};
-          edge_jp(sw, Mj, pj, pi, v, t);
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) q[a] = fmaf(-sw, t[a], q[a]);
-      }
-      if (handle_of(pr, i) >= 0) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) q[c] = fmaf(pr.w_fit, pi[c], q[c]);
-      }
-      if (pr.lm) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) q[c] = fmaf(lam * pr.dc[(c < 3 ? 0 : c - 2) * pl + i], pi[c], q[c]);
-      }
-#pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        pr.q[c * pl + i] = q[c];
-        f2_add_prod(acc, pi[c], q[c]);
-      }
-    }
-    __syncthreads();   // the next tile reuses the shared arrays
+    for (int c = 0; c < 6; ++c) cs[c] = g.cs[c];
   }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) { spu[c][tid] = pi[c]; spu[3 + c][tid] = ui[c]; }
+  {
+    const int h0 = pr.hptr[T], nh = pr.hptr[T + 1] - h0;
+    for (int l = tid; l < nh; l += NT) {
+      const int j = pr.hvtx[h0 + l];
+      float pj[3];
+      mesh_direction<3>(pr, j, pl, update, beta, pin, pj);
+      const float4 g = __ldg(pr.grec + 3 * j);
+      spu[0][VT + l] = pj[0]; spu[1][VT + l] = pj[1]; spu[2][VT + l] = pj[2];
+      spu[3][VT + l] = g.x; spu[4][VT + l] = g.y; spu[5][VT + l] = g.z;
+    }
+  }
+  __syncthreads();
+  // B: own edges (displacement rows, S_i), their J_e p into the slots
+  float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  if (own) {
+    float M[3][3];
+    rot3_dir(rot3(cs), pi[3], pi[4], pi[5], M);
+    auto own_edge = [&](int k, int l) {
+      const float pj[3] = {spu[0][l], spu[1][l], spu[2][l]};
+      const float v[3] = {ui[0] - spu[3][l], ui[1] - spu[4][l], ui[2] - spu[5][l]};
+      float t[3];
+      edge_jp(sw, M, pi, pj, v, t);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        q[a] = fmaf(sw, t[a], q[a]);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) S[a][b] = fmaf(t[a], v[b], S[a][b]);
+        st[a][k - ebase] = t[a];
+      }
+    };
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (o0 + t < o1) own_edge(o0 + t, ln[t]);
+    for (int k = o0 + KB; k < o1; ++k) own_edge(k, pr.lnbr[k]);
+  }
+  {
+    // in-edges arriving from outside the tile, edge-parallel, from the source's data
+    const int r0 = pr.rptr[T], nr = pr.rptr[T + 1] - r0, h0 = pr.hptr[T];
+    for (int r = tid; r < nr; r += NT) {
+      const int w = pr.rin[r0 + r];
+      const int dl = w & 0xffff;
+      const int j = pr.hvtx[h0 + (w >> 16) - VT];
+      float pj[6];
+      mesh_direction<6>(pr, j, pl, update, beta, pin, pj);
+      const GeoRec gj = load_geo(pr.grec, j);
+      float Mj[3][3], t[3];
+      rot3_dir(rot3(gj.cs), pj[3], pj[4], pj[5], Mj);
+      const float d[3] = {spu[0][dl], spu[1][dl], spu[2][dl]};
+      const float v[3] = {gj.U[0] - spu[3][dl], gj.U[1] - spu[4][dl], gj.U[2] - spu[5][dl]};
+      edge_jp(sw, Mj, pj, d, v, t);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) st[a][nout + r] = t[a];
+    }
+  }
+  __syncthreads();
+  // C: angle rows, in-edge displacement rows, fit, damping; p.q
+  F2 acc = f2_zero();
+  if (own) {
+    float ga[3];
+    rot3_contract(rot3(cs), S, ga);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) q[3 + m] = -sw * ga[m];
+    auto in_edge = [&](int slot) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) q[a] = fmaf(-sw, st[a][slot], q[a]);
+    };
+#pragma unroll
+    for (int t = 0; t < KB; ++t)
+      if (n0 + t < n1) in_edge(sl[t]);
+    for (int k = n0 + KB; k < n1; ++k) in_edge(pr.itslot[k]);
+    if (handle_of(pr, i) >= 0) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) q[c] = fmaf(pr.w_fit, pi[c], q[c]);
+    }
+    if (pr.lm) {
+      const float lam = s->lambda_f;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) q[c] = fmaf(lam * pr.dc[(c < 3 ? 0 : c - 2) * pl + i], pi[c], q[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      pr.q[c * pl + i] = q[c];
+      f2_add_prod(acc, pi[c], q[c]);
+    }
+  }
+  (void)ibase;
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.tchunk_end - pr.tchunk_begin)) {
     double pq, unused;
-    gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, pq, unused);
+    gather_partials(part, pr.tchunk_begin, pr.tchunk_end, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
       s->pq = pq;
       if (pq > 0.0 && isfinite(pq)) {
@@ -912,17 +848,15 @@ void launch_mesh_init(const MeshLaunch& L, int k_outer, float dmin, float dmax) 
 void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, int update) {
   if (L.dim == 2) return launch_wg_apply(L, p_override, par, update);
   if (L.dim == 12) return launch_ed_apply(L, p_override, par, update);
-  if (!L.grid3) {
-    static const bool smem_ok =
-        cudaFuncSetAttribute(k_mesh_apply_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)MESH_FUSED_SMEM) == cudaSuccess;
-    (void)smem_ok;
-    launch_pdl(k_mesh_apply_fused, L.nvchunks, NT, MESH_FUSED_SMEM, L.stream, L.probs, L.vchunks, L.part,
-               p_override, par, update);
+  if (!L.grid3 && L.tchunks) {
+    launch_pdl(k_mesh_apply_tiled, L.ntchunks, NT, 0, L.stream, L.probs, L.tchunks, L.part, p_override, par, update);
     return;
   }
   launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, p_override, par, update);
-  launch_pdl(k_mesh_apply_pull<true>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
+  if (L.grid3)
+    launch_pdl(k_mesh_apply_pull<true>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
+  else
+    launch_pdl(k_mesh_apply_pull<false>, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, L.part);
 }
 
 void launch_mesh_update(const MeshLaunch& L, int par) {

@@ -114,6 +114,7 @@ struct MeshProb {
   int gw, gh, gd, gpad;         // volumetric problems: voxel grid W x H x D (0 for graphs)
   int vchunk_begin, vchunk_end;
   int echunk_begin, echunk_end;
+  int tchunk_begin, tchunk_end; // tiled apply: this problem's vertex tiles in the tile-chunk table
   float s_w, s_f, w_reg, w_fit;
   float s_r, w_rot;             // embedded deformation: column constraint weight
   int use_precond, lm;

@@ -26,6 +26,8 @@ struct MeshLaunch {
   int dim;       // 3: ARAP mesh (6 unknowns per vertex); 2: warp on a graph (3 unknowns);
                  // 12: embedded deformation (12 unknowns)
   int grid3;     // dim 3 on a W x H x D voxel grid: neighbours from the 7-point stencil, not the lists
+  const Chunk* tchunks;   // one chunk per vertex tile (tiled ARAP-mesh apply), NULL if not every problem is tiled
+  int ntchunks;
 };
 
 // Launches kernel k with programmatic stream serialization (the kernel must

@@ -58,6 +58,8 @@ struct opt_problem {
   optgb::Chunk* d_vchunks = nullptr;
   optgb::Chunk* d_echunks = nullptr;
   int nvchunks = 0, nechunks = 0;
+  optgb::Chunk* d_tchunks = nullptr;   // tiled ARAP-mesh apply: one chunk per vertex tile (NULL: untiled)
+  int ntchunks = 0;
   // host copies kept for building the materialized Jacobian
   std::vector<unsigned char> h_mask;    // grid mask (empty = none)
   std::vector<int> h_hpix;              // grid handles (pitched index) / mesh handles (vertex)
