@@ -874,50 +874,46 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
 
   // Vertex-tile tables of the tiled ARAP-mesh apply: per tile of VT vertices
   // the out-of-tile neighbours (halo), each edge's far end as an index into
-  // the tile's vertex + halo table, the in-edges arriving from outside the
-  // tile, and the shared-memory slot of every in-edge's J_e p (the edge's own
-  // slot when it starts inside the tile).  A tile over the kernel's
-  // capacities leaves the problem on the general path (no tables).
-  std::vector<int> hptr, hvtx, lnbr, rptr, rin, itslot;
+  // the tile's vertex + halo table, the shared-memory slot of every in-edge
+  // that starts in the same tile (its own out-edge slot), and for every edge
+  // that crosses into another tile an export slot, grouped by its far end
+  // (imp_row), through which the far end's vertex update receives J_e p.  A
+  // tile over the kernel's capacities leaves the problem on the general path.
+  std::vector<int> hptr, hvtx, lnbr, itslot, xpos, imp_row;
   bool tiled = !ed && !grid3 && D == 3;
   if (tiled) {
     hptr.assign((size_t)nvt + 1, 0);
-    rptr.assign((size_t)nvt + 1, 0);
     lnbr.assign((size_t)E, 0);
-    itslot.assign((size_t)E, 0);
+    itslot.assign((size_t)E, -1);
+    xpos.assign((size_t)E, -1);
+    imp_row.assign((size_t)V + 1, 0);
     std::vector<int> halo;
+    int ncross = 0;
     for (int T = 0; T < nvt && tiled; ++T) {
       const int vb = T * VT, ve = std::min(V, vb + VT);
       const int eb = orow[vb], ee = orow[ve];
+      if (ee - eb > MT_SLOTS) { tiled = false; break; }
       halo.clear();
       for (int k = eb; k < ee; ++k)
         if (e1[k] < vb || e1[k] >= ve) halo.push_back(e1[k]);
-      for (int k = irow[vb]; k < irow[ve]; ++k)
-        if (isrc[k] < vb || isrc[k] >= ve) halo.push_back(isrc[k]);
       std::sort(halo.begin(), halo.end());
       halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
       if ((int)halo.size() > MT_HALO) { tiled = false; break; }
-      auto local = [&](int v) {
-        if (v >= vb && v < ve) return v - vb;
-        return VT + (int)(std::lower_bound(halo.begin(), halo.end(), v) - halo.begin());
-      };
-      for (int k = eb; k < ee; ++k) lnbr[k] = local(e1[k]);
-      const int nout = ee - eb;
-      int nrin = 0;
-      for (int i = vb; i < ve; ++i)
+      for (int k = eb; k < ee; ++k)
+        lnbr[k] = (e1[k] >= vb && e1[k] < ve)
+                      ? e1[k] - vb
+                      : VT + (int)(std::lower_bound(halo.begin(), halo.end(), e1[k]) - halo.begin());
+      for (int i = vb; i < ve; ++i) {
+        imp_row[i] = ncross;
         for (int k = irow[i]; k < irow[(size_t)i + 1]; ++k) {
-          if (isrc[k] >= vb && isrc[k] < ve) {
-            itslot[k] = itpos[k] - eb;
-          } else {
-            itslot[k] = nout + nrin++;
-            rin.push_back((local(isrc[k]) << 16) | (i - vb));
-          }
+          if (isrc[k] >= vb && isrc[k] < ve) itslot[k] = itpos[k] - eb;
+          else xpos[itpos[k]] = ncross++;
         }
-      if (nout + nrin > MT_SLOTS) { tiled = false; break; }
+      }
       hvtx.insert(hvtx.end(), halo.begin(), halo.end());
       hptr[(size_t)T + 1] = (int)hvtx.size();
-      rptr[(size_t)T + 1] = (int)rin.size();
     }
+    imp_row[V] = ncross;
   }
 
   const int target = std::max(1, q->sms * 8);
@@ -952,7 +948,9 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   if (E > 0) CKS(upload(disrc, isrc));
   CKS(dalloc(q, &ditpos, std::max<size_t>(1, itpos.size())));
   if (E > 0) CKS(upload(ditpos, itpos));
-  int *dhptr = nullptr, *dhvtx = nullptr, *dlnbr = nullptr, *drptr = nullptr, *drin = nullptr, *ditslot = nullptr;
+  int *dhptr = nullptr, *dhvtx = nullptr, *dlnbr = nullptr, *ditslot = nullptr, *dxpos = nullptr,
+      *dimp = nullptr;
+  float4* dex = nullptr;
   if (tiled) {
     CKS(dalloc(q, &dhptr, hptr.size()));
     CKS(upload(dhptr, hptr));
@@ -960,12 +958,13 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
     if (!hvtx.empty()) CKS(upload(dhvtx, hvtx));
     CKS(dalloc(q, &dlnbr, std::max<size_t>(1, lnbr.size())));
     if (E > 0) CKS(upload(dlnbr, lnbr));
-    CKS(dalloc(q, &drptr, rptr.size()));
-    CKS(upload(drptr, rptr));
-    CKS(dalloc(q, &drin, std::max<size_t>(1, rin.size())));
-    if (!rin.empty()) CKS(upload(drin, rin));
     CKS(dalloc(q, &ditslot, std::max<size_t>(1, itslot.size())));
     if (E > 0) CKS(upload(ditslot, itslot));
+    CKS(dalloc(q, &dxpos, std::max<size_t>(1, xpos.size())));
+    if (E > 0) CKS(upload(dxpos, xpos));
+    CKS(dalloc(q, &dimp, imp_row.size()));
+    CKS(upload(dimp, imp_row));
+    CKS(dalloc(q, &dex, std::max<size_t>(1, (size_t)imp_row[V])));
   }
   for (int c = 0; c < D; ++c) {
     std::vector<float> Ui((size_t)V);
@@ -1015,7 +1014,8 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   g.x = q->x; g.U = U; g.degw = dgw; g.e0 = de0; g.e1 = de1;
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
   g.orow = dorow; g.irow = dirow; g.isrc = disrc; g.itpos = ditpos;
-  g.hptr = dhptr; g.hvtx = dhvtx; g.lnbr = dlnbr; g.rptr = drptr; g.rin = drin; g.itslot = ditslot;
+  g.hptr = dhptr; g.hvtx = dhvtx; g.lnbr = dlnbr; g.itslot = ditslot; g.xpos = dxpos; g.imp_row = dimp;
+  g.ex = dex;
   g.gw = grid3 ? grid3[0] : 0; g.gh = grid3 ? grid3[1] : 0; g.gd = grid3 ? grid3[2] : 0; g.gpad = 0;
   g.grec = grec; g.vrec = vrec;
   g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;

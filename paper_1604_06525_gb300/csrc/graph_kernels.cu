@@ -415,21 +415,22 @@ __global__ void __launch_bounds__(NT, MESH_PULL_MIN_BLOCKS) k_mesh_apply_pull(co
 // ---------------------------------------------------------------------------
 // One block per vertex tile of VT vertices (the tile-chunk table), one vertex
 // per thread.  The block stages the tile's vertices and its halo (the
-// out-of-tile neighbours, a table built at planning) in shared memory: the
-// displacement rows of the direction p = M^-1 r + beta p_old (formed here,
-// halo included, with the same roundings everywhere) and the rest position U.
-// With M_i = sum_m p_i,m dR/dA_m(A_i) formed once per vertex (rot3 /
-// rot3_dir), the linearized residual of an out-edge e = (i, j) is
+// out-of-tile far ends of its edges, a table built at planning) in shared
+// memory: the displacement rows of the direction p = M^-1 r + beta p_old
+// (formed here, halo included, with the same roundings everywhere) and the
+// rest position U.  With M_i = sum_m p_i,m dR/dA_m(A_i) formed once per vertex
+// (rot3 / rot3_dir), the linearized residual of an out-edge e = (i, j) is
 //   t_e = J_e p = s_w [(p_i,d - p_j,d) - M_i v],   v = U_i - U_j;
-// it adds s_w t_e to i's displacement rows and its angle rows
+// it adds s_w t_e to i's displacement rows, and its angle rows
 // -s_w (dR/dA_m v) . t_e are summed through S_i = sum_e t_e v^T, one
 // contraction per vertex (rot3_contract) instead of three derivative vectors
-// per edge.  Each t_e goes to a shared-memory slot; in-edges that start
-// outside the tile are evaluated edge-parallel from their source's data into
-// further slots; every vertex then subtracts s_w t_e of its in-edges, read
-// from their slots (a slot table built at planning).  So each residual is
-// evaluated once inside a tile and once more per tile border it crosses, no
-// atomic is used, and every row is summed in a fixed order.
+// per edge.  j's displacement rows subtract s_w t_e: from a shared-memory slot
+// when j is in the tile, else through an export slot that j's vector update
+// adds (the tile-crossing edges, grouped by far end at planning).  So every
+// residual is evaluated exactly once, no atomic is used, and every row is
+// summed in a fixed order.  p.q = sum_e |J_e p|^2 + p.(fit + damping) p, the
+// same quantity as p.(J^T J + lambda D) p, summed as each vertex's own edges
+// come (its q is only complete after the imports).
 
 // Rotation R = Rz(az) Ry(ay) Rx(ax) from the angles' cos / sin, with
 // u' = dR_:0 / day; the angle derivatives are then
@@ -517,7 +518,7 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
   __shared__ float spu[6][VT + MT_HALO];   // the tile's vertices, then its halo: p_d (3), U (3)
-  __shared__ float st[3][MT_SLOTS];        // J_e p of the tile's out-edges, then of the remote in-edges
+  __shared__ float st[3][MT_SLOTS];        // J_e p of the tile's out-edges
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
   const float beta = s->beta_f;
@@ -527,8 +528,7 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
   const int vb = ch.begin, ve = ch.end, T = vb / VT;
   const int i = vb + tid;
   const bool own = i < ve;
-  const int ebase = pr.orow[vb], nout = pr.orow[ve] - ebase;
-  const int ibase = pr.irow[vb];
+  const int ebase = pr.orow[vb];
   // A: this vertex's direction and geometry, its edge tables fetched ahead
   int o0 = 0, o1 = 0, n0 = 0, n1 = 0;
   int ln[KB], sl[KB];
@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
 #pragma unroll
     for (int t = 0; t < KB; ++t) {
       ln[t] = o0 + t < o1 ? pr.lnbr[o0 + t] : 0;
-      sl[t] = n0 + t < n1 ? pr.itslot[n0 + t] : 0;
+      sl[t] = n0 + t < n1 ? pr.itslot[n0 + t] : -1;
     }
     mesh_direction<6>(pr, i, pl, update, beta, pin, pi);
     if (update) {
@@ -567,9 +567,10 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
     }
   }
   __syncthreads();
-  // B: own edges (displacement rows, S_i), their J_e p into the slots
+  // B: own edges (displacement rows, S_i, |J_e p|^2), J_e p into its slot or export slot
   float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  float jj = 0.f;
   if (own) {
     float M[3][3];
     rot3_dir(rot3(cs), pi[3], pi[4], pi[5], M);
@@ -581,37 +582,21 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         q[a] = fmaf(sw, t[a], q[a]);
+        jj = fmaf(t[a], t[a], jj);
 #pragma unroll
         for (int b = 0; b < 3; ++b) S[a][b] = fmaf(t[a], v[b], S[a][b]);
         st[a][k - ebase] = t[a];
       }
+      if (l >= VT) pr.ex[pr.xpos[k]] = make_float4(t[0], t[1], t[2], 0.f);
     };
 #pragma unroll
     for (int t = 0; t < KB; ++t)
       if (o0 + t < o1) own_edge(o0 + t, ln[t]);
     for (int k = o0 + KB; k < o1; ++k) own_edge(k, pr.lnbr[k]);
   }
-  {
-    // in-edges arriving from outside the tile, edge-parallel, from the source's data
-    const int r0 = pr.rptr[T], nr = pr.rptr[T + 1] - r0, h0 = pr.hptr[T];
-    for (int r = tid; r < nr; r += NT) {
-      const int w = pr.rin[r0 + r];
-      const int dl = w & 0xffff;
-      const int j = pr.hvtx[h0 + (w >> 16) - VT];
-      float pj[6];
-      mesh_direction<6>(pr, j, pl, update, beta, pin, pj);
-      const GeoRec gj = load_geo(pr.grec, j);
-      float Mj[3][3], t[3];
-      rot3_dir(rot3(gj.cs), pj[3], pj[4], pj[5], Mj);
-      const float d[3] = {spu[0][dl], spu[1][dl], spu[2][dl]};
-      const float v[3] = {gj.U[0] - spu[3][dl], gj.U[1] - spu[4][dl], gj.U[2] - spu[5][dl]};
-      edge_jp(sw, Mj, pj, d, v, t);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) st[a][nout + r] = t[a];
-    }
-  }
   __syncthreads();
-  // C: angle rows, in-edge displacement rows, fit, damping; p.q
+  // C: angle rows, the displacement rows of the in-edges from this tile, fit,
+  // damping; p.q
   F2 acc = f2_zero();
   if (own) {
     float ga[3];
@@ -619,6 +604,7 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
 #pragma unroll
     for (int m = 0; m < 3; ++m) q[3 + m] = -sw * ga[m];
     auto in_edge = [&](int slot) {
+      if (slot < 0) return;                  // starts in another tile: arrives through the exports
 #pragma unroll
       for (int a = 0; a < 3; ++a) q[a] = fmaf(-sw, st[a][slot], q[a]);
     };
@@ -628,20 +614,24 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
     for (int k = n0 + KB; k < n1; ++k) in_edge(pr.itslot[k]);
     if (handle_of(pr, i) >= 0) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) q[c] = fmaf(pr.w_fit, pi[c], q[c]);
+      for (int c = 0; c < 3; ++c) {
+        q[c] = fmaf(pr.w_fit, pi[c], q[c]);
+        jj = fmaf(pr.w_fit * pi[c], pi[c], jj);
+      }
     }
     if (pr.lm) {
       const float lam = s->lambda_f;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) q[c] = fmaf(lam * pr.dc[(c < 3 ? 0 : c - 2) * pl + i], pi[c], q[c]);
+      for (int c = 0; c < 6; ++c) {
+        const float dl = lam * pr.dc[(c < 3 ? 0 : c - 2) * pl + i];
+        q[c] = fmaf(dl, pi[c], q[c]);
+        jj = fmaf(dl * pi[c], pi[c], jj);
+      }
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      pr.q[c * pl + i] = q[c];
-      f2_add_prod(acc, pi[c], q[c]);
-    }
+    for (int c = 0; c < 6; ++c) pr.q[c * pl + i] = q[c];
+    f2_add(acc, jj);
   }
-  (void)ibase;
   pdl_trigger();
   if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.tchunk_end - pr.tchunk_begin)) {
     double pq, unused;
@@ -655,6 +645,52 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
         s->pcg_active = 0;
         if (!isfinite(pq)) s->nonfinite = 1;
       }
+    }
+  }
+}
+
+// The imports of a tiled problem added into q (the parity hook's product;
+// within the PCG loop the vector update adds them as it reads q).
+__global__ void __launch_bounds__(NT) k_mesh_import(const MeshProb* __restrict__ probs,
+                                                    const Chunk* __restrict__ tchunks) {
+  pdl_begin();
+  const Chunk ch = tchunks[blockIdx.x];
+  const MeshProb pr = probs[ch.prob];
+  if (pr.s->done || !pr.s->pcg_active) return;
+  const long long pl = pr.Vp;
+  const int i = ch.begin + threadIdx.x;
+  if (i >= ch.end) return;
+  float m[3] = {0.f, 0.f, 0.f};
+  for (int c = pr.imp_row[i]; c < pr.imp_row[i + 1]; ++c) {
+    const float4 t = pr.ex[c];
+    m[0] += t.x;
+    m[1] += t.y;
+    m[2] += t.z;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) pr.q[a * pl + i] = fmaf(-pr.s_w, m[a], pr.q[a * pl + i]);
+}
+
+__device__ __forceinline__ float cmp4(const float4& a, int k) {
+  return k == 0 ? a.x : (k == 1 ? a.y : (k == 2 ? a.z : a.w));
+}
+__device__ __forceinline__ void add4(float4& a, int k, float x) {
+  if (k == 0) a.x += x; else if (k == 1) a.y += x; else if (k == 2) a.z += x; else a.w += x;
+}
+// Sums of the imported J_e p (tiled apply) of vertices v0 .. v0 + 3, one
+// float4 per displacement row (component k = vertex v0 + k).
+__device__ __forceinline__ void import_sums(const MeshProb& pr, int v0, float4 (&im)[3]) {
+  const int vq = min(v0 + 4, pr.V);
+  if (v0 >= vq) return;
+  int c = pr.imp_row[v0];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int ce = v0 + k < vq ? pr.imp_row[v0 + k + 1] : c;
+    for (; c < ce; ++c) {
+      const float4 t = pr.ex[c];
+      add4(im[0], k, t.x);
+      add4(im[1], k, t.y);
+      add4(im[2], k, t.z);
     }
   }
 }
@@ -676,6 +712,10 @@ __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__
   const int q0 = ch.begin / 4, q1 = (ch.end + 3) / 4;
   for (int qi = q0 + threadIdx.x; qi < q1; qi += NT) {
     const int v0 = 4 * qi;
+    // tiled apply: the sums of J_e p of the edges arriving from other tiles
+    float4 im[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
+                    make_float4(0.f, 0.f, 0.f, 0.f)};
+    if (pr.imp_row) import_sums(pr, v0, im);
     float4 pv[6], qv[6], dv[6], rv[6], mv[4];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -686,6 +726,15 @@ __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) mv[k] = ld4g(pr.m + k * pl + v0);
+    if (pr.imp_row) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float* qk[3] = {reinterpret_cast<float*>(&qv[0]) + k, reinterpret_cast<float*>(&qv[1]) + k,
+                        reinterpret_cast<float*>(&qv[2]) + k};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) *qk[a] = fmaf(-pr.s_w, cmp4(im[a], k), *qk[a]);
+      }
+    }
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       const float4 m = mv[c < 3 ? 0 : c - 2];
@@ -850,6 +899,9 @@ void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, in
   if (L.dim == 12) return launch_ed_apply(L, p_override, par, update);
   if (!L.grid3 && L.tchunks) {
     launch_pdl(k_mesh_apply_tiled, L.ntchunks, NT, 0, L.stream, L.probs, L.tchunks, L.part, p_override, par, update);
+    // a given direction (the parity hook): q complete at once; the PCG loop
+    // leaves the imports to the vector update
+    if (!update) launch_pdl(k_mesh_import, L.ntchunks, NT, 0, L.stream, L.probs, L.tchunks);
     return;
   }
   launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, p_override, par, update);
