@@ -42,8 +42,10 @@ def _stale(out: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link the library if a source changed; returns its path."""
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, defines=()) -> str:
+    """Compile and link the library if a source changed; returns its path.
+    defines: extra preprocessor definitions ("NAME=value"), for measuring
+    compile-time variants of a kernel (pass force=True)."""
     out = lib_path()
     if not force and not _stale(out):
         return out
@@ -53,6 +55,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
+    common += [f"-D{d}" for d in defines]
     procs = []
     objs = []
     for src in SOURCES:

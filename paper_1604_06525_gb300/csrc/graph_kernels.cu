@@ -649,8 +649,9 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
   }
 }
 
-// The imports of a tiled problem added into q (the parity hook's product;
-// within the PCG loop the vector update adds them as it reads q).
+// The imports of a tiled problem: J_e p of the edges arriving from other
+// tiles subtracted from the displacement rows of q (after the tiled apply,
+// before anything reads q); vertices without imports are not touched.
 __global__ void __launch_bounds__(NT) k_mesh_import(const MeshProb* __restrict__ probs,
                                                     const Chunk* __restrict__ tchunks) {
   pdl_begin();
@@ -660,8 +661,10 @@ __global__ void __launch_bounds__(NT) k_mesh_import(const MeshProb* __restrict__
   const long long pl = pr.Vp;
   const int i = ch.begin + threadIdx.x;
   if (i >= ch.end) return;
+  const int c0 = pr.imp_row[i], c1 = pr.imp_row[i + 1];
+  if (c0 == c1) return;
   float m[3] = {0.f, 0.f, 0.f};
-  for (int c = pr.imp_row[i]; c < pr.imp_row[i + 1]; ++c) {
+  for (int c = c0; c < c1; ++c) {
     const float4 t = pr.ex[c];
     m[0] += t.x;
     m[1] += t.y;
@@ -669,30 +672,6 @@ __global__ void __launch_bounds__(NT) k_mesh_import(const MeshProb* __restrict__
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) pr.q[a * pl + i] = fmaf(-pr.s_w, m[a], pr.q[a * pl + i]);
-}
-
-__device__ __forceinline__ float cmp4(const float4& a, int k) {
-  return k == 0 ? a.x : (k == 1 ? a.y : (k == 2 ? a.z : a.w));
-}
-__device__ __forceinline__ void add4(float4& a, int k, float x) {
-  if (k == 0) a.x += x; else if (k == 1) a.y += x; else if (k == 2) a.z += x; else a.w += x;
-}
-// Sums of the imported J_e p (tiled apply) of vertices v0 .. v0 + 3, one
-// float4 per displacement row (component k = vertex v0 + k).
-__device__ __forceinline__ void import_sums(const MeshProb& pr, int v0, float4 (&im)[3]) {
-  const int vq = min(v0 + 4, pr.V);
-  if (v0 >= vq) return;
-  int c = pr.imp_row[v0];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int ce = v0 + k < vq ? pr.imp_row[v0 + k + 1] : c;
-    for (; c < ce; ++c) {
-      const float4 t = pr.ex[c];
-      add4(im[0], k, t.x);
-      add4(im[1], k, t.y);
-      add4(im[2], k, t.z);
-    }
-  }
 }
 
 // delta += alpha p, r -= alpha q, z = M^-1 r, float64 r.z -> beta; four
@@ -712,10 +691,6 @@ __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__
   const int q0 = ch.begin / 4, q1 = (ch.end + 3) / 4;
   for (int qi = q0 + threadIdx.x; qi < q1; qi += NT) {
     const int v0 = 4 * qi;
-    // tiled apply: the sums of J_e p of the edges arriving from other tiles
-    float4 im[3] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f),
-                    make_float4(0.f, 0.f, 0.f, 0.f)};
-    if (pr.imp_row) import_sums(pr, v0, im);
     float4 pv[6], qv[6], dv[6], rv[6], mv[4];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -726,15 +701,6 @@ __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) mv[k] = ld4g(pr.m + k * pl + v0);
-    if (pr.imp_row) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        float* qk[3] = {reinterpret_cast<float*>(&qv[0]) + k, reinterpret_cast<float*>(&qv[1]) + k,
-                        reinterpret_cast<float*>(&qv[2]) + k};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) *qk[a] = fmaf(-pr.s_w, cmp4(im[a], k), *qk[a]);
-      }
-    }
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       const float4 m = mv[c < 3 ? 0 : c - 2];
@@ -899,9 +865,7 @@ void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, in
   if (L.dim == 12) return launch_ed_apply(L, p_override, par, update);
   if (!L.grid3 && L.tchunks) {
     launch_pdl(k_mesh_apply_tiled, L.ntchunks, NT, 0, L.stream, L.probs, L.tchunks, L.part, p_override, par, update);
-    // a given direction (the parity hook): q complete at once; the PCG loop
-    // leaves the imports to the vector update
-    if (!update) launch_pdl(k_mesh_import, L.ntchunks, NT, 0, L.stream, L.probs, L.tchunks);
+    launch_pdl(k_mesh_import, L.ntchunks, NT, 0, L.stream, L.probs, L.tchunks);
     return;
   }
   launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, p_override, par, update);
