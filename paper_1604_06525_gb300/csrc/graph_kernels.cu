@@ -517,8 +517,9 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
-  __shared__ float spu[6][VT + MT_HALO];   // the tile's vertices, then its halo: p_d (3), U (3)
-  __shared__ float st[3][MT_SLOTS];        // J_e p of the tile's out-edges
+  __shared__ float4 sp4[VT + MT_HALO];     // the tile's vertices, then its halo: s_w p_d, 0
+  __shared__ float4 su4[VT + MT_HALO];     //   and U, 0
+  __shared__ float4 st4[MT_SLOTS];         // J_e p of the tile's out-edges
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
   const float beta = s->beta_f;
@@ -531,17 +532,14 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
   const int ebase = pr.orow[vb];
   // A: this vertex's direction and geometry, its edge tables fetched ahead
   int o0 = 0, o1 = 0, n0 = 0, n1 = 0;
-  int ln[KB], sl[KB];
+  int ln[KB];
   float pi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float ui[3] = {0.f, 0.f, 0.f}, cs[6] = {1.f, 0.f, 1.f, 0.f, 1.f, 0.f};
   if (own) {
     o0 = pr.orow[i]; o1 = pr.orow[i + 1];
     n0 = pr.irow[i]; n1 = pr.irow[i + 1];
 #pragma unroll
-    for (int t = 0; t < KB; ++t) {
-      ln[t] = o0 + t < o1 ? pr.lnbr[o0 + t] : 0;
-      sl[t] = n0 + t < n1 ? pr.itslot[n0 + t] : -1;
-    }
+    for (int t = 0; t < KB; ++t) ln[t] = o0 + t < o1 ? pr.lnbr[o0 + t] : 0;
     mesh_direction<6>(pr, i, pl, update, beta, pin, pi);
     if (update) {
 #pragma unroll
@@ -553,8 +551,8 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
 #pragma unroll
     for (int c = 0; c < 6; ++c) cs[c] = g.cs[c];
   }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) { spu[c][tid] = pi[c]; spu[3 + c][tid] = ui[c]; }
+  sp4[tid] = make_float4(sw * pi[0], sw * pi[1], sw * pi[2], 0.f);
+  su4[tid] = make_float4(ui[0], ui[1], ui[2], 0.f);
   {
     const int h0 = pr.hptr[T], nh = pr.hptr[T + 1] - h0;
     for (int l = tid; l < nh; l += NT) {
@@ -562,8 +560,8 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
       float pj[3];
       mesh_direction<3>(pr, j, pl, update, beta, pin, pj);
       const float4 g = __ldg(pr.grec + 3 * j);
-      spu[0][VT + l] = pj[0]; spu[1][VT + l] = pj[1]; spu[2][VT + l] = pj[2];
-      spu[3][VT + l] = g.x; spu[4][VT + l] = g.y; spu[5][VT + l] = g.z;
+      sp4[VT + l] = make_float4(sw * pj[0], sw * pj[1], sw * pj[2], 0.f);
+      su4[VT + l] = make_float4(g.x, g.y, g.z, 0.f);
     }
   }
   __syncthreads();
@@ -572,22 +570,27 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
   float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
   float jj = 0.f;
   if (own) {
+    // s_w folded into M and p: t = s_w p_i - s_w p_j - (s_w M) v
     float M[3][3];
-    rot3_dir(rot3(cs), pi[3], pi[4], pi[5], M);
+    rot3_dir(rot3(cs), sw * pi[3], sw * pi[4], sw * pi[5], M);
+    const float4 spi = sp4[tid];
     auto own_edge = [&](int k, int l) {
-      const float pj[3] = {spu[0][l], spu[1][l], spu[2][l]};
-      const float v[3] = {ui[0] - spu[3][l], ui[1] - spu[4][l], ui[2] - spu[5][l]};
+      const float4 pj = sp4[l], uj = su4[l];
+      const float v[3] = {ui[0] - uj.x, ui[1] - uj.y, ui[2] - uj.z};
+      const float pd[3] = {spi.x - pj.x, spi.y - pj.y, spi.z - pj.z};
       float t[3];
-      edge_jp(sw, M, pi, pj, v, t);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) t[a] = pd[a] - fmaf(M[a][0], v[0], fmaf(M[a][1], v[1], M[a][2] * v[2]));
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        q[a] = fmaf(sw, t[a], q[a]);
+        q[a] += t[a];
         jj = fmaf(t[a], t[a], jj);
 #pragma unroll
         for (int b = 0; b < 3; ++b) S[a][b] = fmaf(t[a], v[b], S[a][b]);
-        st[a][k - ebase] = t[a];
       }
-      if (l >= VT) pr.ex[pr.xpos[k]] = make_float4(t[0], t[1], t[2], 0.f);
+      const float4 t4 = make_float4(t[0], t[1], t[2], 0.f);
+      st4[k - ebase] = t4;
+      if (l >= VT) pr.ex[pr.xpos[k]] = t4;
     };
 #pragma unroll
     for (int t = 0; t < KB; ++t)
@@ -599,19 +602,26 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
   // damping; p.q
   F2 acc = f2_zero();
   if (own) {
+    int sl[KB];
+#pragma unroll
+    for (int t = 0; t < KB; ++t) sl[t] = n0 + t < n1 ? pr.itslot[n0 + t] : -1;
     float ga[3];
     rot3_contract(rot3(cs), S, ga);
 #pragma unroll
     for (int m = 0; m < 3; ++m) q[3 + m] = -sw * ga[m];
     auto in_edge = [&](int slot) {
       if (slot < 0) return;                  // starts in another tile: arrives through the exports
-#pragma unroll
-      for (int a = 0; a < 3; ++a) q[a] = fmaf(-sw, st[a][slot], q[a]);
+      const float4 t = st4[slot];
+      q[0] -= t.x;
+      q[1] -= t.y;
+      q[2] -= t.z;
     };
 #pragma unroll
     for (int t = 0; t < KB; ++t)
       if (n0 + t < n1) in_edge(sl[t]);
     for (int k = n0 + KB; k < n1; ++k) in_edge(pr.itslot[k]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) q[c] *= sw;
     if (handle_of(pr, i) >= 0) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -653,25 +663,25 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
 // tiles subtracted from the displacement rows of q (after the tiled apply,
 // before anything reads q); vertices without imports are not touched.
 __global__ void __launch_bounds__(NT) k_mesh_import(const MeshProb* __restrict__ probs,
-                                                    const Chunk* __restrict__ tchunks) {
+                                                    const Chunk* __restrict__ vchunks) {
   pdl_begin();
-  const Chunk ch = tchunks[blockIdx.x];
+  const Chunk ch = vchunks[blockIdx.x];
   const MeshProb pr = probs[ch.prob];
   if (pr.s->done || !pr.s->pcg_active) return;
   const long long pl = pr.Vp;
-  const int i = ch.begin + threadIdx.x;
-  if (i >= ch.end) return;
-  const int c0 = pr.imp_row[i], c1 = pr.imp_row[i + 1];
-  if (c0 == c1) return;
-  float m[3] = {0.f, 0.f, 0.f};
-  for (int c = c0; c < c1; ++c) {
-    const float4 t = pr.ex[c];
-    m[0] += t.x;
-    m[1] += t.y;
-    m[2] += t.z;
-  }
+  for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
+    const int c0 = pr.imp_row[i], c1 = pr.imp_row[i + 1];
+    if (c0 == c1) continue;
+    float m[3] = {0.f, 0.f, 0.f};
+    for (int c = c0; c < c1; ++c) {
+      const float4 t = pr.ex[c];
+      m[0] += t.x;
+      m[1] += t.y;
+      m[2] += t.z;
+    }
 #pragma unroll
-  for (int a = 0; a < 3; ++a) pr.q[a * pl + i] = fmaf(-pr.s_w, m[a], pr.q[a * pl + i]);
+    for (int a = 0; a < 3; ++a) pr.q[a * pl + i] = fmaf(-pr.s_w, m[a], pr.q[a * pl + i]);
+  }
 }
 
 // delta += alpha p, r -= alpha q, z = M^-1 r, float64 r.z -> beta; four
@@ -865,7 +875,7 @@ void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, in
   if (L.dim == 12) return launch_ed_apply(L, p_override, par, update);
   if (!L.grid3 && L.tchunks) {
     launch_pdl(k_mesh_apply_tiled, L.ntchunks, NT, 0, L.stream, L.probs, L.tchunks, L.part, p_override, par, update);
-    launch_pdl(k_mesh_import, L.ntchunks, NT, 0, L.stream, L.probs, L.tchunks);
+    launch_pdl(k_mesh_import, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks);
     return;
   }
   launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, p_override, par, update);

@@ -45,8 +45,8 @@ constexpr int VT = 256;           // vertices per vertex tile (graph)
 // capacities of the tiled ARAP-mesh apply (one tile of VT vertices per pass):
 // out-of-tile neighbours staged with the tile, and J_e p slots (the tile's
 // out-edges plus its in-edges that start outside the tile)
-constexpr int MT_HALO = 384;
-constexpr int MT_SLOTS = 2304;
+constexpr int MT_HALO = 320;
+constexpr int MT_SLOTS = 1792;
 
 // Device-resident scalars of one problem.  Written only by the single
 // finishing block of a reduction or by the one-thread LM decision kernel.
