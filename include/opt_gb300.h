@@ -321,14 +321,39 @@ opt_status opt_problem_set_chunking(opt_problem* prob, int32_t units_per_block);
 
 /* Autotuner: times applyJTJ + vector update (opt_profile_pcg) for each
  * candidate granularity {-1, -2, -3, -4, -6, -8, 1, 4} (see
- * opt_problem_set_chunking), keeps the fastest and
- * returns it in *chosen and its per-iteration time in *best_ms (host, either
- * may be NULL).  Leaves the PCG state as opt_profile_pcg does. */
+ * opt_problem_set_chunking) and, beside it, each apply form of an ARAP mesh
+ * with tile tables and each tile width (32, 128) of a grid (see
+ * opt_problem_get_config); keeps the fastest combination and returns its
+ * granularity in *chosen and its per-iteration time in *best_ms (host, either
+ * may be NULL).  Leaves the PCG state as opt_profile_pcg does.  A grid whose
+ * other tile width wins is re-planned in place: autotune a problem before
+ * building a batch over it, not while a batch holds it. */
 opt_status opt_problem_autotune(opt_problem* prob, int32_t* chosen, float* best_ms);
 
 /* Number of unknowns (elements per plane x planes) and of planes. */
 opt_status opt_problem_info(const opt_problem* prob, int64_t* n_unknowns, int32_t* n_planes,
                             int64_t* plane_len);
+
+/* The launch configuration in use (host outputs, each may be NULL):
+ * tile_w = tile width of a grid problem (32 or 128 pixels; 0 for graphs),
+ * chunking = granularity as passed to opt_problem_set_chunking (0 = the
+ * default), apply_form = how an ARAP mesh forms J^T J p (1: one block per
+ * vertex tile with the tile's halo staged in shared memory, every residual of
+ * the tile evaluated once; 0: the two-pass vertex gather; -1: not an ARAP mesh
+ * with tile tables).  opt_problem_autotune chooses all three: the form and
+ * granularity of a mesh, the granularity and tile width of a grid (the other
+ * width is planned afresh from the creation descriptor, whose arrays must
+ * still be valid, and kept if faster).  Results agree across configurations
+ * to float rounding (the sums are compensated, see Sec. 4.1 PCG). */
+opt_status opt_problem_get_config(const opt_problem* prob, int32_t* tile_w, int32_t* chunking,
+                                  int32_t* apply_form);
+
+/* Forces the ARAP-mesh apply form (1 tiled, 0 two-pass gather; see
+ * opt_problem_get_config).  OPT_ERR_INVALID_ARG for other values, for a NULL
+ * problem or for form 1 on a problem without tile tables (graphs whose
+ * vertex tiles exceed 384 out-of-tile neighbours or 2,304 edge slots, other
+ * energies). */
+opt_status opt_problem_set_apply_form(opt_problem* prob, int32_t form);
 
 /* ---------------------------------------------------------------------------
  * Batched solves: many planned problems of uneven sizes advanced together,

@@ -112,6 +112,8 @@ _SIGNATURES = [
     ("opt_server_step", c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
     ("opt_server_poll", c_int32, [c_void_p, ctypes.c_uint64, POINTER(Report)]),
     ("opt_server_set_max_active", c_int32, [c_void_p, c_int32]),
+    ("opt_problem_get_config", c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
+    ("opt_problem_set_apply_form", c_int32, [c_void_p, c_int32]),
     ("opt_server_inject_rebuild_failure", c_int32, [c_void_p, c_int32]),
     ("opt_warp_apply_jtj_noalloc", c_int32, [c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p,
                                              c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p,
@@ -402,10 +404,21 @@ class Problem:
         _check(self.lib.opt_problem_set_chunking(self.h, units_per_block), "opt_problem_set_chunking")
 
     def autotune(self):
-        """Picks the work granularity with the fastest applyJTJ + update."""
+        """Picks the work granularity (and a mesh's apply form, a grid's tile
+        width) with the fastest applyJTJ + update."""
         c, ms = c_int32(), c_float()
         _check(self.lib.opt_problem_autotune(self.h, ctypes.byref(c), ctypes.byref(ms)), "opt_problem_autotune")
         return c.value, ms.value
+
+    def config(self) -> dict:
+        """The launch configuration in use (opt_problem_get_config)."""
+        tw, ch, af = c_int32(), c_int32(), c_int32()
+        _check(self.lib.opt_problem_get_config(self.h, ctypes.byref(tw), ctypes.byref(ch), ctypes.byref(af)),
+               "opt_problem_get_config")
+        return {"tile_w": tw.value, "chunking": ch.value, "apply_form": af.value}
+
+    def set_apply_form(self, form: int):
+        _check(self.lib.opt_problem_set_apply_form(self.h, form), "opt_problem_set_apply_form")
 
     def pcg_state(self):
         import torch

@@ -272,7 +272,7 @@ GridLaunch grid_launch(const opt_problem* pb, cudaStream_t st) {
 MeshLaunch mesh_launch(const opt_problem* pb, cudaStream_t st) {
   return MeshLaunch{pb->dm, pb->d_vchunks, pb->d_echunks, pb->d_part, pb->nvchunks,
                     pb->nechunks, st, pb->kind == K_WARPG ? 2 : (pb->kind == K_EMBED ? 12 : 3),
-                    pb->kind == K_VOLUME ? 1 : 0, pb->d_tchunks, pb->ntchunks};
+                    pb->kind == K_VOLUME ? 1 : 0, pb->apply_form ? pb->d_tchunks : nullptr, pb->ntchunks};
 }
 
 opt_status upload_desc(opt_problem* pb, cudaStream_t st) {
@@ -578,6 +578,9 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   if (tw == 128) CK(grid_kernels_prepare());
   std::unique_ptr<opt_problem> pb(new opt_problem());
   pb->kind = warp ? K_WARP : K_POISSON;
+  pb->tile_w = tw;
+  pb->grid_desc = *d;
+  pb->has_grid_desc = true;
   pb->nx = nx;
   pb->nm = nm;
   pb->W = d->W;
@@ -874,46 +877,50 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
 
   // Vertex-tile tables of the tiled ARAP-mesh apply: per tile of VT vertices
   // the out-of-tile neighbours (halo), each edge's far end as an index into
-  // the tile's vertex + halo table, the shared-memory slot of every in-edge
-  // that starts in the same tile (its own out-edge slot), and for every edge
-  // that crosses into another tile an export slot, grouped by its far end
-  // (imp_row), through which the far end's vertex update receives J_e p.  A
-  // tile over the kernel's capacities leaves the problem on the general path.
-  std::vector<int> hptr, hvtx, lnbr, itslot, xpos, imp_row;
+  // the tile's vertex + halo table, the in-edges arriving from outside the
+  // tile, and the shared-memory slot of every in-edge's J_e p (the edge's own
+  // slot when it starts inside the tile).  A tile over the kernel's
+  // capacities leaves the problem on the general path (no tables).
+  std::vector<int> hptr, hvtx, lnbr, rptr, rin, itslot;
   bool tiled = !ed && !grid3 && D == 3;
   if (tiled) {
     hptr.assign((size_t)nvt + 1, 0);
+    rptr.assign((size_t)nvt + 1, 0);
     lnbr.assign((size_t)E, 0);
-    itslot.assign((size_t)E, -1);
-    xpos.assign((size_t)E, -1);
-    imp_row.assign((size_t)V + 1, 0);
+    itslot.assign((size_t)E, 0);
     std::vector<int> halo;
-    int ncross = 0;
     for (int T = 0; T < nvt && tiled; ++T) {
       const int vb = T * VT, ve = std::min(V, vb + VT);
       const int eb = orow[vb], ee = orow[ve];
-      if (ee - eb > MT_SLOTS) { tiled = false; break; }
       halo.clear();
       for (int k = eb; k < ee; ++k)
         if (e1[k] < vb || e1[k] >= ve) halo.push_back(e1[k]);
+      for (int k = irow[vb]; k < irow[ve]; ++k)
+        if (isrc[k] < vb || isrc[k] >= ve) halo.push_back(isrc[k]);
       std::sort(halo.begin(), halo.end());
       halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
       if ((int)halo.size() > MT_HALO) { tiled = false; break; }
-      for (int k = eb; k < ee; ++k)
-        lnbr[k] = (e1[k] >= vb && e1[k] < ve)
-                      ? e1[k] - vb
-                      : VT + (int)(std::lower_bound(halo.begin(), halo.end(), e1[k]) - halo.begin());
-      for (int i = vb; i < ve; ++i) {
-        imp_row[i] = ncross;
+      auto local = [&](int v) {
+        if (v >= vb && v < ve) return v - vb;
+        return VT + (int)(std::lower_bound(halo.begin(), halo.end(), v) - halo.begin());
+      };
+      for (int k = eb; k < ee; ++k) lnbr[k] = local(e1[k]);
+      const int nout = ee - eb;
+      int nrin = 0;
+      for (int i = vb; i < ve; ++i)
         for (int k = irow[i]; k < irow[(size_t)i + 1]; ++k) {
-          if (isrc[k] >= vb && isrc[k] < ve) itslot[k] = itpos[k] - eb;
-          else xpos[itpos[k]] = ncross++;
+          if (isrc[k] >= vb && isrc[k] < ve) {
+            itslot[k] = itpos[k] - eb;
+          } else {
+            itslot[k] = nout + nrin++;
+            rin.push_back((local(isrc[k]) << 16) | (i - vb));
+          }
         }
-      }
+      if (nout + nrin > MT_SLOTS) { tiled = false; break; }
       hvtx.insert(hvtx.end(), halo.begin(), halo.end());
       hptr[(size_t)T + 1] = (int)hvtx.size();
+      rptr[(size_t)T + 1] = (int)rin.size();
     }
-    imp_row[V] = ncross;
   }
 
   const int target = std::max(1, q->sms * 8);
@@ -948,9 +955,7 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   if (E > 0) CKS(upload(disrc, isrc));
   CKS(dalloc(q, &ditpos, std::max<size_t>(1, itpos.size())));
   if (E > 0) CKS(upload(ditpos, itpos));
-  int *dhptr = nullptr, *dhvtx = nullptr, *dlnbr = nullptr, *ditslot = nullptr, *dxpos = nullptr,
-      *dimp = nullptr;
-  float4* dex = nullptr;
+  int *dhptr = nullptr, *dhvtx = nullptr, *dlnbr = nullptr, *drptr = nullptr, *drin = nullptr, *ditslot = nullptr;
   if (tiled) {
     CKS(dalloc(q, &dhptr, hptr.size()));
     CKS(upload(dhptr, hptr));
@@ -958,13 +963,12 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
     if (!hvtx.empty()) CKS(upload(dhvtx, hvtx));
     CKS(dalloc(q, &dlnbr, std::max<size_t>(1, lnbr.size())));
     if (E > 0) CKS(upload(dlnbr, lnbr));
+    CKS(dalloc(q, &drptr, rptr.size()));
+    CKS(upload(drptr, rptr));
+    CKS(dalloc(q, &drin, std::max<size_t>(1, rin.size())));
+    if (!rin.empty()) CKS(upload(drin, rin));
     CKS(dalloc(q, &ditslot, std::max<size_t>(1, itslot.size())));
     if (E > 0) CKS(upload(ditslot, itslot));
-    CKS(dalloc(q, &dxpos, std::max<size_t>(1, xpos.size())));
-    if (E > 0) CKS(upload(dxpos, xpos));
-    CKS(dalloc(q, &dimp, imp_row.size()));
-    CKS(upload(dimp, imp_row));
-    CKS(dalloc(q, &dex, std::max<size_t>(1, (size_t)imp_row[V])));
   }
   for (int c = 0; c < D; ++c) {
     std::vector<float> Ui((size_t)V);
@@ -1014,8 +1018,7 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   g.x = q->x; g.U = U; g.degw = dgw; g.e0 = de0; g.e1 = de1;
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
   g.orow = dorow; g.irow = dirow; g.isrc = disrc; g.itpos = ditpos;
-  g.hptr = dhptr; g.hvtx = dhvtx; g.lnbr = dlnbr; g.itslot = ditslot; g.xpos = dxpos; g.imp_row = dimp;
-  g.ex = dex;
+  g.hptr = dhptr; g.hvtx = dhvtx; g.lnbr = dlnbr; g.rptr = drptr; g.rin = drin; g.itslot = ditslot;
   g.gw = grid3 ? grid3[0] : 0; g.gh = grid3 ? grid3[1] : 0; g.gd = grid3 ? grid3[2] : 0; g.gpad = 0;
   g.grec = grec; g.vrec = vrec;
   g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;
@@ -1306,6 +1309,7 @@ opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, flo
 // (graph) per block; 0 restores the default (balanced, 2 blocks per SM for grids, 8 for graphs).
 static opt_status rechunk(opt_problem* pb, int per) {
   CK(cudaDeviceSynchronize());
+  pb->chunking = per;
   if (pb->gexec) {
     cudaGraphExecDestroy(pb->gexec);
     pb->gexec = nullptr;
@@ -1351,26 +1355,88 @@ opt_status opt_problem_set_chunking(opt_problem* prob, int32_t units_per_block) 
   return rechunk(prob, units_per_block);
 }
 
-opt_status opt_problem_autotune(opt_problem* prob, int32_t* chosen, float* best_ms) {
-  if (!prob) return OPT_ERR_INVALID_ARG;
+// Best granularity of a problem's current layout and apply form: the
+// summed applyJTJ + vector-update time of a short PCG run.
+static opt_status tune_granularity(opt_problem* prob, int* best, float* bms) {
   // balanced splits with 1..8 blocks per SM, and fixed runs of 1 and 4 units
   const int cand[] = {-1, -2, -3, -4, -6, -8, 1, 4};
-  int best = 0;
-  float bms = 1e30f;
+  *best = 0;
+  *bms = 1e30f;
   for (int c : cand) {
     CKS(rechunk(prob, c));
     float ms[3];
     CKS(opt_profile_pcg(prob, 4, nullptr, ms));
     CKS(opt_profile_pcg(prob, 8, nullptr, ms));
     const float t = ms[1] + ms[2];
-    if (t < bms) {
-      bms = t;
-      best = c;
+    if (t < *bms) {
+      *bms = t;
+      *best = c;
     }
   }
-  CKS(rechunk(prob, best));
+  return rechunk(prob, *best);
+}
+
+opt_status opt_problem_autotune(opt_problem* prob, int32_t* chosen, float* best_ms) {
+  if (!prob) return OPT_ERR_INVALID_ARG;
+  int best = 0;
+  float bms = 1e30f;
+  if (prob->d_tchunks) {
+    // graphs with tile tables: the tiled apply against the two-pass gather
+    int b1 = 0, b0 = 0;
+    float t1 = 0.f, t0 = 0.f;
+    prob->apply_form = 1;
+    CKS(tune_granularity(prob, &b1, &t1));
+    prob->apply_form = 0;
+    CKS(tune_granularity(prob, &b0, &t0));
+    prob->apply_form = t1 <= t0 ? 1 : 0;
+    best = t1 <= t0 ? b1 : b0;
+    bms = std::min(t1, t0);
+    CKS(rechunk(prob, best));
+  } else {
+    CKS(tune_granularity(prob, &best, &bms));
+  }
+  if (is_grid(prob) && prob->has_grid_desc) {
+    // grids: the other tile width, planned afresh from the same descriptor;
+    // the faster layout is kept (the handle stays the same)
+    opt_solve_params prm;
+    opt_solve_params_default(&prm);
+    prm.tile_w = prob->tile_w == 128 ? 32 : 128;
+    opt_problem* alt = nullptr;
+    CKS(opt_problem_create_grid(&prob->grid_desc, &prm, &alt));
+    int b2 = 0;
+    float t2 = 0.f;
+    opt_status st = tune_granularity(alt, &b2, &t2);
+    if (st == OPT_OK && t2 < bms) {
+      CK(cudaDeviceSynchronize());
+      prob->swap_contents(*alt);
+      best = b2;
+      bms = t2;
+    }
+    opt_problem_destroy(alt);
+    if (st != OPT_OK) return st;
+  }
   if (chosen) *chosen = best;
   if (best_ms) *best_ms = bms;
+  return OPT_OK;
+}
+
+opt_status opt_problem_get_config(const opt_problem* prob, int32_t* tile_w, int32_t* chunking, int32_t* apply_form) {
+  if (!prob) return OPT_ERR_INVALID_ARG;
+  if (tile_w) *tile_w = is_grid(prob) ? prob->tile_w : 0;
+  if (chunking) *chunking = prob->chunking;
+  if (apply_form) *apply_form = prob->d_tchunks ? prob->apply_form : -1;
+  return OPT_OK;
+}
+
+opt_status opt_problem_set_apply_form(opt_problem* prob, int32_t form) {
+  if (!prob || form < 0 || form > 1 || (form == 1 && !prob->d_tchunks)) return OPT_ERR_INVALID_ARG;
+  CK(cudaDeviceSynchronize());
+  if (prob->gexec) {
+    cudaGraphExecDestroy(prob->gexec);
+    prob->gexec = nullptr;
+    prob->gkey.clear();
+  }
+  prob->apply_form = form;
   return OPT_OK;
 }
 

@@ -210,7 +210,10 @@ opt_status build_tables(opt_batch* b, int tpc) {
     std::vector<MeshProb> mp;
     std::vector<Chunk> vch, ech, tch;
     bool tiled = true;
-    for (size_t mi = 0; mi < g.members.size(); ++mi) tiled = tiled && b->probs[g.members[mi]]->d_tchunks;
+    for (size_t mi = 0; mi < g.members.size(); ++mi) {
+      const opt_problem* pm = b->probs[g.members[mi]];
+      tiled = tiled && pm->d_tchunks && pm->apply_form;
+    }
     for (size_t mi = 0; mi < g.members.size(); ++mi) {
       opt_problem* pb = b->probs[g.members[mi]];
       std::vector<Chunk> v(pb->nvchunks), e(pb->nechunks);

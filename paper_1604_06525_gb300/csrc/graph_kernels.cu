@@ -415,22 +415,21 @@ __global__ void __launch_bounds__(NT, MESH_PULL_MIN_BLOCKS) k_mesh_apply_pull(co
 // ---------------------------------------------------------------------------
 // One block per vertex tile of VT vertices (the tile-chunk table), one vertex
 // per thread.  The block stages the tile's vertices and its halo (the
-// out-of-tile far ends of its edges, a table built at planning) in shared
-// memory: the displacement rows of the direction p = M^-1 r + beta p_old
-// (formed here, halo included, with the same roundings everywhere) and the
-// rest position U.  With M_i = sum_m p_i,m dR/dA_m(A_i) formed once per vertex
-// (rot3 / rot3_dir), the linearized residual of an out-edge e = (i, j) is
+// out-of-tile neighbours, a table built at planning) in shared memory: the
+// displacement rows of the direction p = M^-1 r + beta p_old (formed here,
+// halo included, with the same roundings everywhere) and the rest position U.
+// With M_i = sum_m p_i,m dR/dA_m(A_i) formed once per vertex (rot3 /
+// rot3_dir), the linearized residual of an out-edge e = (i, j) is
 //   t_e = J_e p = s_w [(p_i,d - p_j,d) - M_i v],   v = U_i - U_j;
-// it adds s_w t_e to i's displacement rows, and its angle rows
+// it adds s_w t_e to i's displacement rows and its angle rows
 // -s_w (dR/dA_m v) . t_e are summed through S_i = sum_e t_e v^T, one
 // contraction per vertex (rot3_contract) instead of three derivative vectors
-// per edge.  j's displacement rows subtract s_w t_e: from a shared-memory slot
-// when j is in the tile, else through an export slot that j's vector update
-// adds (the tile-crossing edges, grouped by far end at planning).  So every
-// residual is evaluated exactly once, no atomic is used, and every row is
-// summed in a fixed order.  p.q = sum_e |J_e p|^2 + p.(fit + damping) p, the
-// same quantity as p.(J^T J + lambda D) p, summed as each vertex's own edges
-// come (its q is only complete after the imports).
+// per edge.  Each t_e goes to a shared-memory slot; in-edges that start
+// outside the tile are evaluated edge-parallel from their source's data into
+// further slots; every vertex then subtracts s_w t_e of its in-edges, read
+// from their slots (a slot table built at planning).  So each residual is
+// evaluated once inside a tile and once more per tile border it crosses, no
+// atomic is used, and every row is summed in a fixed order.
 
 // Rotation R = Rz(az) Ry(ay) Rx(ax) from the angles' cos / sin, with
 // u' = dR_:0 / day; the angle derivatives are then
@@ -517,9 +516,8 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
   const MeshProb pr = probs[ch.prob];
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
-  __shared__ float4 sp4[VT + MT_HALO];     // the tile's vertices, then its halo: s_w p_d, 0
-  __shared__ float4 su4[VT + MT_HALO];     //   and U, 0
-  __shared__ float4 st4[MT_SLOTS];         // J_e p of the tile's out-edges
+  __shared__ float spu[6][VT + MT_HALO];   // the tile's vertices, then its halo: p_d (3), U (3)
+  __shared__ float st[3][MT_SLOTS];        // J_e p of the tile's out-edges, then of the remote in-edges
   const long long pl = pr.Vp;
   const float sw = pr.s_w;
   const float beta = s->beta_f;
@@ -529,17 +527,21 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
   const int vb = ch.begin, ve = ch.end, T = vb / VT;
   const int i = vb + tid;
   const bool own = i < ve;
-  const int ebase = pr.orow[vb];
+  const int ebase = pr.orow[vb], nout = pr.orow[ve] - ebase;
+  const int ibase = pr.irow[vb];
   // A: this vertex's direction and geometry, its edge tables fetched ahead
   int o0 = 0, o1 = 0, n0 = 0, n1 = 0;
-  int ln[KB];
+  int ln[KB], sl[KB];
   float pi[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float ui[3] = {0.f, 0.f, 0.f}, cs[6] = {1.f, 0.f, 1.f, 0.f, 1.f, 0.f};
   if (own) {
     o0 = pr.orow[i]; o1 = pr.orow[i + 1];
     n0 = pr.irow[i]; n1 = pr.irow[i + 1];
 #pragma unroll
-    for (int t = 0; t < KB; ++t) ln[t] = o0 + t < o1 ? pr.lnbr[o0 + t] : 0;
+    for (int t = 0; t < KB; ++t) {
+      ln[t] = o0 + t < o1 ? pr.lnbr[o0 + t] : 0;
+      sl[t] = n0 + t < n1 ? pr.itslot[n0 + t] : 0;
+    }
     mesh_direction<6>(pr, i, pl, update, beta, pin, pi);
     if (update) {
 #pragma unroll
@@ -551,8 +553,8 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
 #pragma unroll
     for (int c = 0; c < 6; ++c) cs[c] = g.cs[c];
   }
-  sp4[tid] = make_float4(sw * pi[0], sw * pi[1], sw * pi[2], 0.f);
-  su4[tid] = make_float4(ui[0], ui[1], ui[2], 0.f);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) { spu[c][tid] = pi[c]; spu[3 + c][tid] = ui[c]; }
   {
     const int h0 = pr.hptr[T], nh = pr.hptr[T + 1] - h0;
     for (int l = tid; l < nh; l += NT) {
@@ -560,88 +562,86 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
       float pj[3];
       mesh_direction<3>(pr, j, pl, update, beta, pin, pj);
       const float4 g = __ldg(pr.grec + 3 * j);
-      sp4[VT + l] = make_float4(sw * pj[0], sw * pj[1], sw * pj[2], 0.f);
-      su4[VT + l] = make_float4(g.x, g.y, g.z, 0.f);
+      spu[0][VT + l] = pj[0]; spu[1][VT + l] = pj[1]; spu[2][VT + l] = pj[2];
+      spu[3][VT + l] = g.x; spu[4][VT + l] = g.y; spu[5][VT + l] = g.z;
     }
   }
   __syncthreads();
-  // B: own edges (displacement rows, S_i, |J_e p|^2), J_e p into its slot or export slot
+  // B: own edges (displacement rows, S_i), their J_e p into the slots
   float q[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float S[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  float jj = 0.f;
   if (own) {
-    // s_w folded into M and p: t = s_w p_i - s_w p_j - (s_w M) v
     float M[3][3];
-    rot3_dir(rot3(cs), sw * pi[3], sw * pi[4], sw * pi[5], M);
-    const float4 spi = sp4[tid];
+    rot3_dir(rot3(cs), pi[3], pi[4], pi[5], M);
     auto own_edge = [&](int k, int l) {
-      const float4 pj = sp4[l], uj = su4[l];
-      const float v[3] = {ui[0] - uj.x, ui[1] - uj.y, ui[2] - uj.z};
-      const float pd[3] = {spi.x - pj.x, spi.y - pj.y, spi.z - pj.z};
+      const float pj[3] = {spu[0][l], spu[1][l], spu[2][l]};
+      const float v[3] = {ui[0] - spu[3][l], ui[1] - spu[4][l], ui[2] - spu[5][l]};
       float t[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) t[a] = pd[a] - fmaf(M[a][0], v[0], fmaf(M[a][1], v[1], M[a][2] * v[2]));
+      edge_jp(sw, M, pi, pj, v, t);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        q[a] += t[a];
-        jj = fmaf(t[a], t[a], jj);
+        q[a] = fmaf(sw, t[a], q[a]);
 #pragma unroll
         for (int b = 0; b < 3; ++b) S[a][b] = fmaf(t[a], v[b], S[a][b]);
+        st[a][k - ebase] = t[a];
       }
-      const float4 t4 = make_float4(t[0], t[1], t[2], 0.f);
-      st4[k - ebase] = t4;
-      if (l >= VT) pr.ex[pr.xpos[k]] = t4;
     };
 #pragma unroll
     for (int t = 0; t < KB; ++t)
       if (o0 + t < o1) own_edge(o0 + t, ln[t]);
     for (int k = o0 + KB; k < o1; ++k) own_edge(k, pr.lnbr[k]);
   }
+  {
+    // in-edges arriving from outside the tile, edge-parallel, from the source's data
+    const int r0 = pr.rptr[T], nr = pr.rptr[T + 1] - r0, h0 = pr.hptr[T];
+    for (int r = tid; r < nr; r += NT) {
+      const int w = pr.rin[r0 + r];
+      const int dl = w & 0xffff;
+      const int j = pr.hvtx[h0 + (w >> 16) - VT];
+      float pj[6];
+      mesh_direction<6>(pr, j, pl, update, beta, pin, pj);
+      const GeoRec gj = load_geo(pr.grec, j);
+      float Mj[3][3], t[3];
+      rot3_dir(rot3(gj.cs), pj[3], pj[4], pj[5], Mj);
+      const float d[3] = {spu[0][dl], spu[1][dl], spu[2][dl]};
+      const float v[3] = {gj.U[0] - spu[3][dl], gj.U[1] - spu[4][dl], gj.U[2] - spu[5][dl]};
+      edge_jp(sw, Mj, pj, d, v, t);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) st[a][nout + r] = t[a];
+    }
+  }
   __syncthreads();
-  // C: angle rows, the displacement rows of the in-edges from this tile, fit,
-  // damping; p.q
+  // C: angle rows, in-edge displacement rows, fit, damping; p.q
   F2 acc = f2_zero();
   if (own) {
-    int sl[KB];
-#pragma unroll
-    for (int t = 0; t < KB; ++t) sl[t] = n0 + t < n1 ? pr.itslot[n0 + t] : -1;
     float ga[3];
     rot3_contract(rot3(cs), S, ga);
 #pragma unroll
     for (int m = 0; m < 3; ++m) q[3 + m] = -sw * ga[m];
     auto in_edge = [&](int slot) {
-      if (slot < 0) return;                  // starts in another tile: arrives through the exports
-      const float4 t = st4[slot];
-      q[0] -= t.x;
-      q[1] -= t.y;
-      q[2] -= t.z;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) q[a] = fmaf(-sw, st[a][slot], q[a]);
     };
 #pragma unroll
     for (int t = 0; t < KB; ++t)
       if (n0 + t < n1) in_edge(sl[t]);
     for (int k = n0 + KB; k < n1; ++k) in_edge(pr.itslot[k]);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) q[c] *= sw;
     if (handle_of(pr, i) >= 0) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        q[c] = fmaf(pr.w_fit, pi[c], q[c]);
-        jj = fmaf(pr.w_fit * pi[c], pi[c], jj);
-      }
+      for (int c = 0; c < 3; ++c) q[c] = fmaf(pr.w_fit, pi[c], q[c]);
     }
     if (pr.lm) {
       const float lam = s->lambda_f;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const float dl = lam * pr.dc[(c < 3 ? 0 : c - 2) * pl + i];
-        q[c] = fmaf(dl, pi[c], q[c]);
-        jj = fmaf(dl * pi[c], pi[c], jj);
-      }
+      for (int c = 0; c < 6; ++c) q[c] = fmaf(lam * pr.dc[(c < 3 ? 0 : c - 2) * pl + i], pi[c], q[c]);
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) pr.q[c * pl + i] = q[c];
-    f2_add(acc, jj);
+    for (int c = 0; c < 6; ++c) {
+      pr.q[c * pl + i] = q[c];
+      f2_add_prod(acc, pi[c], q[c]);
+    }
   }
+  (void)ibase;
   pdl_trigger();
   if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.tchunk_end - pr.tchunk_begin)) {
     double pq, unused;
@@ -656,31 +656,6 @@ __global__ void __launch_bounds__(NT, MESH_TILED_MIN_BLOCKS) k_mesh_apply_tiled(
         if (!isfinite(pq)) s->nonfinite = 1;
       }
     }
-  }
-}
-
-// The imports of a tiled problem: J_e p of the edges arriving from other
-// tiles subtracted from the displacement rows of q (after the tiled apply,
-// before anything reads q); vertices without imports are not touched.
-__global__ void __launch_bounds__(NT) k_mesh_import(const MeshProb* __restrict__ probs,
-                                                    const Chunk* __restrict__ vchunks) {
-  pdl_begin();
-  const Chunk ch = vchunks[blockIdx.x];
-  const MeshProb pr = probs[ch.prob];
-  if (pr.s->done || !pr.s->pcg_active) return;
-  const long long pl = pr.Vp;
-  for (int i = ch.begin + threadIdx.x; i < ch.end; i += NT) {
-    const int c0 = pr.imp_row[i], c1 = pr.imp_row[i + 1];
-    if (c0 == c1) continue;
-    float m[3] = {0.f, 0.f, 0.f};
-    for (int c = c0; c < c1; ++c) {
-      const float4 t = pr.ex[c];
-      m[0] += t.x;
-      m[1] += t.y;
-      m[2] += t.z;
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) pr.q[a * pl + i] = fmaf(-pr.s_w, m[a], pr.q[a * pl + i]);
   }
 }
 
@@ -875,7 +850,6 @@ void launch_mesh_apply(const MeshLaunch& L, const float* p_override, int par, in
   if (L.dim == 12) return launch_ed_apply(L, p_override, par, update);
   if (!L.grid3 && L.tchunks) {
     launch_pdl(k_mesh_apply_tiled, L.ntchunks, NT, 0, L.stream, L.probs, L.tchunks, L.part, p_override, par, update);
-    launch_pdl(k_mesh_import, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks);
     return;
   }
   launch_pdl(k_mesh_apply_v, L.nvchunks, NT, 0, L.stream, L.probs, L.vchunks, p_override, par, update);

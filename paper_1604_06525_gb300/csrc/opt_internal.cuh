@@ -45,8 +45,8 @@ constexpr int VT = 256;           // vertices per vertex tile (graph)
 // capacities of the tiled ARAP-mesh apply (one tile of VT vertices per pass):
 // out-of-tile neighbours staged with the tile, and J_e p slots (the tile's
 // out-edges plus its in-edges that start outside the tile)
-constexpr int MT_HALO = 320;
-constexpr int MT_SLOTS = 1792;
+constexpr int MT_HALO = 384;
+constexpr int MT_SLOTS = 2304;
 
 // Device-resident scalars of one problem.  Written only by the single
 // finishing block of a reduction or by the one-thread LM decision kernel.
@@ -132,11 +132,9 @@ struct MeshProb {
   const int* hptr;              // tiles + 1: the halo of tile T is hvtx[hptr[T] .. hptr[T+1])
   const int* hvtx;              // out-of-tile vertices adjacent to the tile, ascending
   const int* lnbr;              // E: each edge's far end as an index into its tile's vertex + halo table
-  const int* itslot;            // E: shared-memory slot of each in-edge's J_e p (irow order), -1 if it
-                                //    starts in another tile
-  const int* xpos;              // E: export slot of an edge whose far end lies in another tile, else -1
-  const int* imp_row;           // V + 1: the exports arriving at v are ex[imp_row[v] .. imp_row[v+1])
-  float4* ex;                   // J_e p of the tile-crossing edges (x, y, z, 0), grouped by far end
+  const int* rptr;              // tiles + 1: in-edges from outside tile T are rin[rptr[T] .. rptr[T+1])
+  const int* rin;               // (source table index << 16) | target index within the tile
+  const int* itslot;            // E: shared-memory slot of each in-edge's J_e p (irow order)
   float *d, *r, *p, *q;         // 6 planes each
   float *m, *dc;                // 4 planes: displacement, ax, ay, az
   float4* grec;                 // 3 float4 per vertex: U, cos / sin of the angles (PCGInit)

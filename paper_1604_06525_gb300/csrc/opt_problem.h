@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <utility>
 #include <vector>
 
 #include "opt_gb300.h"
@@ -60,6 +61,11 @@ struct opt_problem {
   int nvchunks = 0, nechunks = 0;
   optgb::Chunk* d_tchunks = nullptr;   // tiled ARAP-mesh apply: one chunk per vertex tile (NULL: untiled)
   int ntchunks = 0;
+  int apply_form = 1;                   // problems with tile tables: 1 tiled apply, 0 two-pass gather
+  int chunking = 0;                     // the granularity last set (0 = default)
+  int tile_w = 0;                       // grids: tile width (32 or 128)
+  bool has_grid_desc = false;           // grids: the planning input, kept for re-planning at another
+  opt_grid_desc grid_desc{};            //   tile width (its arrays are the caller's and outlive the problem)
   // host copies kept for building the materialized Jacobian
   std::vector<unsigned char> h_mask;    // grid mask (empty = none)
   std::vector<int> h_hpix;              // grid handles (pitched index) / mesh handles (vertex)
@@ -91,6 +97,30 @@ struct opt_problem {
   cudaGraphExec_t gexec = nullptr;
   std::vector<double> gkey;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // Exchanges everything two problems hold (the autotuner keeps a layout
+  // planned afresh under the caller's handle).  Member by member, so every
+  // device allocation, stream, event and graph keeps exactly one owner.
+  void swap_contents(opt_problem& o) {
+    using std::swap;
+    swap(kind, o.kind); swap(nx, o.nx); swap(nm, o.nm); swap(sms, o.sms);
+    swap(W, o.W); swap(H, o.H); swap(P, o.P); swap(V, o.V); swap(E, o.E);
+    swap(plane, o.plane); swap(ulen, o.ulen);
+    swap(hg, o.hg); swap(dg, o.dg); swap(d_chunks, o.d_chunks); swap(nchunks, o.nchunks);
+    swap(d_tiles, o.d_tiles); swap(ntiles, o.ntiles);
+    swap(hm, o.hm); swap(dm, o.dm); swap(d_vchunks, o.d_vchunks); swap(d_echunks, o.d_echunks);
+    swap(nvchunks, o.nvchunks); swap(nechunks, o.nechunks); swap(d_tchunks, o.d_tchunks);
+    swap(ntchunks, o.ntchunks); swap(apply_form, o.apply_form); swap(chunking, o.chunking);
+    swap(tile_w, o.tile_w); swap(has_grid_desc, o.has_grid_desc); swap(grid_desc, o.grid_desc);
+    swap(h_mask, o.h_mask); swap(h_hpix, o.h_hpix); swap(h_e0, o.h_e0); swap(h_e1, o.h_e1);
+    swap(d_perm, o.d_perm); swap(csr, o.csr);
+    swap(d_part, o.d_part); swap(d_s, o.d_s); swap(d_Ehist, o.d_Ehist); swap(Ehist_cap, o.Ehist_cap);
+    swap(user_x, o.user_x); swap(d_tmp, o.d_tmp); swap(d_jtf, o.d_jtf); swap(d_diag, o.d_diag);
+    swap(x, o.x); swap(pbuf, o.pbuf); swap(dvec, o.dvec); swap(rvec, o.rvec); swap(qvec, o.qvec);
+    swap(allocs, o.allocs); swap(pooled, o.pooled); swap(pcg_par, o.pcg_par);
+    swap(d_gbar, o.d_gbar); swap(coop_cap, o.coop_cap); swap(cap_stream, o.cap_stream);
+    swap(gexec, o.gexec); swap(gkey, o.gkey); swap(ev0, o.ev0); swap(ev1, o.ev1);
+  }
 
   ~opt_problem() {
     if (gexec) cudaGraphExecDestroy(gexec);

@@ -624,3 +624,48 @@ def test_plain_cg_matches_oracle(api, kind, inner):
     for a, b in zip(rep["E_history"], ref.E_history):
         assert relE(a, b) <= TOL_ENERGY
     gp.close()
+
+
+def test_autotuned_configurations_keep_results(api):
+    """The autotuner's choices -- granularity, a grid's tile width (re-planned
+    from the creation descriptor), an ARAP mesh's apply form -- give the same
+    results within 1e-6: every sum is compensated, so only the float32
+    arithmetic of each element's own rows may differ."""
+    import torch
+    w = synth.warp_problem(300, 90, 9, seed=171)
+    a = api.Problem(w)
+    ref = a.solve_gn(3, 8)
+    for tw in (32, 128):
+        b = api.Problem(w, tile_w=tw)
+        assert b.config()["tile_w"] == tw and b.config()["apply_form"] == -1
+        r = b.solve_gn(3, 8)
+        for x, y in zip(r["E_history"], ref["E_history"]):
+            assert relE(x, y) <= 1e-6
+        b.close()
+    a.autotune()
+    cfg = a.config()
+    assert cfg["tile_w"] in (32, 128) and cfg["chunking"] in (-1, -2, -3, -4, -6, -8, 1, 4)
+    a.x.copy_(torch.as_tensor(w.x0, device="cuda"))
+    r = a.solve_gn(3, 8)
+    for x, y in zip(r["E_history"], ref["E_history"]):
+        assert relE(x, y) <= 1e-6
+    a.close()
+    m = synth.mesh_problem(3, seed=172, handle_frac=0.03)
+    g = api.Problem(m)
+    assert g.config()["apply_form"] == 1
+    p = random_direction(m, 3)
+    q1, pq1 = g.apply_jtj(torch.as_tensor(p, device="cuda"), 0.2)
+    r1 = g.solve_lm(4, 10)
+    g.set_apply_form(0)
+    g.x.copy_(torch.as_tensor(m.x0, device="cuda"))
+    q0, pq0 = g.apply_jtj(torch.as_tensor(p, device="cuda"), 0.2)
+    r0 = g.solve_lm(4, 10)
+    assert rel(q1.cpu().numpy(), q0.cpu().numpy()) <= 1e-6 and relE(pq1, pq0) <= 1e-6
+    assert r1["outer_done"] == r0["outer_done"]
+    for x, y in zip(r1["E_history"], r0["E_history"]):
+        assert relE(x, y) <= 1e-6
+    g.autotune()
+    assert g.config()["apply_form"] in (0, 1)
+    with pytest.raises(api.OptError):
+        g.set_apply_form(2)
+    g.close()
