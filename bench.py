@@ -49,25 +49,23 @@ BYTES_INIT_WARP = 60       # read x 12, UrShape 8; write r 12, M^-1 8, delta 12,
 BYTES_APPLY_POISSON = 69   # read r 16, M^-1 4, p_old 16, mask 1; write p 16, q 16
 BYTES_UPDATE_POISSON = 100  # read delta 16, p 16, r 16, q 16, M^-1 4; write delta 16, r 16
 BYTES_INIT_POISSON = 69    # read X 16, T 16, mask 1; write r 16, M^-1 4, delta 16 (GN)
-# ARAP mesh, per vertex (6 unknowns, 6 directed edges per vertex on an icosphere)
-BYTES_APPLY_MESH = 268     # vertex pass: read r 24, M^-1 16, p_old 24; write p 24, q 24 (112);
-#                            edge pass: (v0, v1) 6 x 8, U 12, cos/sin 24, p 24, q read + write 48 (156)
+# ARAP mesh, per vertex (6 unknowns, 6 directed edges per vertex on an icosphere): the
+# algorithmic bytes of the method, each array touched once, records and padding the
+# kernels add not counted (a lower numerator than the bytes they move)
+BYTES_APPLY_MESH = 192     # direction: read r 24, M^-1 16, p_old 24; write p 24 (88); applyJTJ: read
+#                            angles 12, U 12, out-edge CSR 4 + 6 x 4, in-edge CSR 4 + 6 x 4; write q 24 (104)
 BYTES_UPDATE_MESH = 160    # read delta 24, p 24, r 24, q 24, M^-1 16; write delta 24, r 24
-BYTES_INIT_MESH = 356      # vertex pass: read angles 12; write JtF 24, acc 12, cos/sin 24 (72);
-#                            edge pass: (v0, v1) 48, U 12, x 24, cos/sin 24, JtF and acc read + write 72 (180);
-#                            final pass: read degree 4, acc 12, JtF 24; write M^-1 16, r 24, delta 24 (104)
-# volumetric ARAP, per voxel (the gather form: neighbour records hit cache)
-BYTES_APPLY_VOLUME = 224   # direction pass: read r 24, M^-1 16, p_old 24; write p 24, p record 32 (120);
-#                            gather pass: read own records 32 + 48; write q 24 (104)
+BYTES_INIT_MESH = 156      # read x 24, U 12, out-edge CSR 28, in-edge CSR 28; write r 24, M^-1 16, delta 24 (GN)
+# volumetric ARAP, per voxel (7-point stencil: no index lists)
+BYTES_APPLY_VOLUME = 160   # direction 88 as the mesh; applyJTJ: read angles 12, U 12; write q 24 (48);
+#                            the neighbours' p, angles and U counted once with their own voxel
 BYTES_UPDATE_VOLUME = 160  # as the mesh
-BYTES_INIT_VOLUME = 264    # vertex pass: read x 24, U 12; write records 80 (116); gather pass: read
-#                            records 80, degree 4; write r 24, M^-1 16, delta 24 (148)
+BYTES_INIT_VOLUME = 100    # read x 24, U 12; write r 24, M^-1 16, delta 24 (GN)
 # embedded deformation, per vertex (12 unknowns, 10 diagonal planes, 6 directed edges)
-BYTES_APPLY_ED = 380       # direction pass: read r 48, M^-1 40, p_old 48; write p 48, records 48 (232);
-#                            gather pass: read own records 48 + 16, matrix at x 36; write q 48 (148)
+BYTES_APPLY_ED = 384       # direction: read r 48, M^-1 40, p_old 48; write p 48 (184); applyJTJ: read
+#                            matrix at x 36, U 12, out-edge CSR 28, in-edge CSR 28; write q 48 (152)
 BYTES_UPDATE_ED = 328      # read delta 48, p 48, r 48, q 48, M^-1 40; write delta 48, r 48
-BYTES_INIT_ED = 328        # vertex pass: read x 48, U 12; write records 64 (124); gather pass: read
-#                            own records 64, degree 4; write r 48, M^-1 40, delta 48 (204)
+BYTES_INIT_ED = 252        # read x 48, U 12, out-edge CSR 28, in-edge CSR 28; write r 48, M^-1 40, delta 48 (GN)
 # float64 solver: algorithmic flops of applyJTJ per unit in the scatter form of
 # Fig. 10 / 11 (every residual's J p evaluated once; an FMA counts 2), the
 # numerators of the float64 arithmetic roofline
@@ -341,10 +339,15 @@ def run_reference(args):
 
 def kernel_roofline(gp, kernels, units, peak, iters=20):
     """Live timing of a problem's PCG kernels (CUDA events on the launching
-    stream, mean over `iters` launches) after autotuning its granularity.
+    stream, mean over `iters` launches) after autotuning its configuration.
     kernels: (name, algorithmic bytes per unit, launches per solve) for the
-    init, apply and update passes, in that order."""
+    init, apply and update passes, in that order, or a function of the
+    chosen configuration (opt_problem_get_config) returning them.  Returns
+    the per-kernel figures and the configuration."""
     gp.autotune()
+    cfg = gp.config()
+    if callable(kernels):
+        kernels = kernels(cfg)
     gp.profile_pcg(3)
     times = gp.profile_pcg(iters)
     out = {}
@@ -352,21 +355,24 @@ def kernel_roofline(gp, kernels, units, peak, iters=20):
         ach = bpu * units / (ms * 1e-3) / 1e9
         out[name] = {"ms": ms, "bytes": bpu * units, "achieved": ach, "frac": ach / peak,
                      "launches_per_solve": per_solve}
-    return out
+    return out, cfg
 
 
 def roofline_for(api, synth, torch, W, H, peak, iters=20):
     """Per-kernel roofline of the matrix-free ARAP warp at W x H."""
     prob = synth.warp_problem(W, H, max(8, int(round(64.0 * W * H / 2 ** 20))), seed=synth.BASE_SEED)
     gp = api.Problem(prob)
-    wide = W >= 128                      # 128-pixel tiles (k_warp_*_wide) from 128 pixels up
-    out = kernel_roofline(gp, (("k_warp_init_wide" if wide else "k_warp_init", BYTES_INIT_WARP, OUTER),
-                               ("k_warp_apply_wide" if wide else "k_warp_apply", BYTES_APPLY_WARP, OUTER * INNER),
-                               ("k_grid_update<3>", BYTES_UPDATE_WARP, OUTER * INNER)), W * H, peak, iters)
+
+    def names(cfg):                      # 128-pixel tiles run the k_warp_*_wide kernels
+        wide = cfg["tile_w"] == 128
+        return (("k_warp_init_wide" if wide else "k_warp_init", BYTES_INIT_WARP, OUTER),
+                ("k_warp_apply_wide" if wide else "k_warp_apply", BYTES_APPLY_WARP, OUTER * INNER),
+                ("k_grid_update<3>", BYTES_UPDATE_WARP, OUTER * INNER))
+    out, cfg = kernel_roofline(gp, names, W * H, peak, iters)
     gp.close()
     del prob
     torch.cuda.empty_cache()
-    return out, out[next(iter(out))]["ms"]
+    return out, cfg
 
 
 def roofline_beyond_l2(api, synth, torch, peak):
@@ -374,46 +380,46 @@ def roofline_beyond_l2(api, synth, torch, peak):
     applies): ARAP warp 4096^2, Poisson 4096^2 x 4 (free pixels), icosphere
     level 9 (vertices: ARAP mesh and embedded deformation), 128^3 voxels."""
     res = {}
-    warp, _ = roofline_for(api, synth, torch, 4096, 4096, peak)
-    res["warp_4096x4096"] = {"unit_of_work": "pixel", "units": 4096 * 4096, "kernels": warp}
+    warp, cfg = roofline_for(api, synth, torch, 4096, 4096, peak)
+    res["warp_4096x4096"] = {"unit_of_work": "pixel", "units": 4096 * 4096, "kernels": warp, "config": cfg}
     pp = synth.poisson_problem(4096, 4096, seed=synth.BASE_SEED)
     free = int((pp.mask == 0).sum())
     gp = api.Problem(pp)
-    res["poisson_4096x4096x4"] = {
-        "unit_of_work": "free pixel", "units": free,
-        "kernels": kernel_roofline(gp, (("k_poisson_init_wide", BYTES_INIT_POISSON, OUTER),
-                                        ("k_poisson_apply_wide", BYTES_APPLY_POISSON, OUTER * INNER),
-                                        ("k_grid_update<4>", BYTES_UPDATE_POISSON, OUTER * INNER)), free, peak)}
+    kp, cfg = kernel_roofline(gp, lambda c: (
+        ("k_poisson_init_wide" if c["tile_w"] == 128 else "k_poisson_init", BYTES_INIT_POISSON, OUTER),
+        ("k_poisson_apply_wide" if c["tile_w"] == 128 else "k_poisson_apply", BYTES_APPLY_POISSON, OUTER * INNER),
+        ("k_grid_update<4>", BYTES_UPDATE_POISSON, OUTER * INNER)), free, peak)
+    res["poisson_4096x4096x4"] = {"unit_of_work": "free pixel", "units": free, "kernels": kp, "config": cfg}
     gp.close()
     del pp
     torch.cuda.empty_cache()
     mp = synth.mesh_problem(9, seed=synth.BASE_SEED)
     gp = api.Problem(mp)
-    res["mesh_icosphere9"] = {
-        "unit_of_work": "vertex", "units": mp.V, "directed_edges": int(len(mp.v0)),
-        "kernels": kernel_roofline(gp, (("k_mesh_init_v+e+f", BYTES_INIT_MESH, 15),
-                                        ("k_mesh_apply_v+e", BYTES_APPLY_MESH, 15 * 30),
-                                        ("k_mesh_update", BYTES_UPDATE_MESH, 15 * 30)), mp.V, peak)}
+    km, cfg = kernel_roofline(gp, lambda c: (
+        ("k_mesh_init_v+pull", BYTES_INIT_MESH, 15),
+        ("k_mesh_apply_tiled" if c["apply_form"] == 1 else "k_mesh_apply_v+pull", BYTES_APPLY_MESH, 15 * 30),
+        ("k_mesh_update", BYTES_UPDATE_MESH, 15 * 30)), mp.V, peak)
+    res["mesh_icosphere9"] = {"unit_of_work": "vertex", "units": mp.V, "directed_edges": int(len(mp.v0)),
+                              "kernels": km, "config": cfg}
     gp.close()
     del mp
     torch.cuda.empty_cache()
     ep = synth.embedded_problem(9, seed=synth.BASE_SEED)
     gp = api.Problem(ep)
-    res["embedded_icosphere9"] = {
-        "unit_of_work": "vertex", "units": ep.V, "directed_edges": int(len(ep.v0)),
-        "kernels": kernel_roofline(gp, (("k_ed_init_v+pull", BYTES_INIT_ED, 15),
-                                        ("k_ed_apply_v+pull", BYTES_APPLY_ED, 15 * 30),
-                                        ("k_ed_update", BYTES_UPDATE_ED, 15 * 30)), ep.V, peak)}
+    ke, cfg = kernel_roofline(gp, (("k_ed_init_v+pull", BYTES_INIT_ED, 15),
+                                   ("k_ed_apply_v+pull", BYTES_APPLY_ED, 15 * 30),
+                                   ("k_ed_update", BYTES_UPDATE_ED, 15 * 30)), ep.V, peak)
+    res["embedded_icosphere9"] = {"unit_of_work": "vertex", "units": ep.V, "directed_edges": int(len(ep.v0)),
+                                  "kernels": ke, "config": cfg}
     gp.close()
     del ep
     torch.cuda.empty_cache()
     vp = synth.volume_problem(128, 128, 128, 2048, seed=synth.BASE_SEED)
     gp = api.Problem(vp)
-    res["volume_128x128x128"] = {
-        "unit_of_work": "voxel", "units": vp.V,
-        "kernels": kernel_roofline(gp, (("k_mesh_init_v+pull<grid>", BYTES_INIT_VOLUME, 10),
-                                        ("k_mesh_apply_v+pull<grid>", BYTES_APPLY_VOLUME, 10 * 10),
-                                        ("k_mesh_update", BYTES_UPDATE_VOLUME, 10 * 10)), vp.V, peak)}
+    kv, cfg = kernel_roofline(gp, (("k_mesh_init_v+pull<grid>", BYTES_INIT_VOLUME, 10),
+                                   ("k_mesh_apply_v+pull<grid>", BYTES_APPLY_VOLUME, 10 * 10),
+                                   ("k_mesh_update", BYTES_UPDATE_VOLUME, 10 * 10)), vp.V, peak)
+    res["volume_128x128x128"] = {"unit_of_work": "voxel", "units": vp.V, "kernels": kv, "config": cfg}
     gp.close()
     del vp
     torch.cuda.empty_cache()
@@ -658,10 +664,11 @@ def run_ours(args):
     prob = synth.warp_problem(W_BENCH, H_BENCH, HANDLES, seed=synth.BASE_SEED)
     gp = api.Problem(prob)
     if args.chunking is None:
-        chunking, _ = gp.autotune()      # work granularity (outside the timed region)
+        chunking, _ = gp.autotune()      # granularity and tile width (outside the timed region)
     else:
         chunking = args.chunking         # fixed (profiler runs: ncu's serialised timing misleads the autotuner)
         gp.set_chunking(chunking)
+    head_cfg = gp.config()
     x0 = gp.x.clone()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
@@ -769,6 +776,7 @@ def run_ours(args):
             "matrix_free_speedup": ms_jtj / ms_per_step, "E_final": rr_jtj[-1]["E_final"]}
         pp = synth.poisson_problem(W_BENCH, H_BENCH, seed=synth.BASE_SEED)
         gpp = api.Problem(pp)
+        gpp.autotune()
         xp0 = gpp.x.clone()
         rr = timed(gpp, xp0, gpp.solve_gn)
         rrm = timed(gpp, xp0, gpp.solve_gn, materialized=1)
@@ -776,7 +784,8 @@ def run_ours(args):
         msp = statistics.median(r_["ms"] for r_ in rr)
         mspm = statistics.median(r_["ms"] for r_ in rrm)
         extra["poisson_1024x1024x4_gn20x20"] = {"pcg_iters_per_s": OUTER * INNER / (msp / 1e3), "ms_per_solve": msp,
-                                               "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
+                                               "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"],
+                                               "config": gpp.config()}
         e_pois = rr[-1]["E_history"]
         extra["poisson_1024x1024x4_materialized_gn20x20"] = {
             "pcg_iters_per_s": OUTER * INNER / (mspm / 1e3), "ms_per_solve": mspm,
@@ -788,6 +797,7 @@ def run_ours(args):
         gpp.close()
         mp = synth.mesh_problem(7, seed=synth.BASE_SEED)
         gmp = api.Problem(mp)
+        gmp.autotune()
         x0m = gmp.x.clone()
         rr = []
         for _ in range(3):
@@ -795,7 +805,8 @@ def run_ours(args):
             rr.append(gmp.solve_lm(15, 30, lambda0=1e-3))
         msm = statistics.median(r_["ms"] for r_ in rr)
         extra["mesh_icosphere7_lm15x30"] = {"pcg_iters_per_s": rr[-1]["pcg_done"] / (msm / 1e3), "ms_per_solve": msm,
-                                           "accepted": rr[-1]["accepted"], "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"]}
+                                           "accepted": rr[-1]["accepted"], "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"],
+                                           "config": gmp.config()}
         rep_mesh = rr[-1]
         gmp.close()
 
@@ -924,7 +935,7 @@ def run_ours(args):
                                f"GN {OUTER} outer x {INNER} PCG, Jacobi, matrix-free, one CUDA graph per solve",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed between steps (512 MB write)", "precision": "f32 vectors, f64 dots/energies",
-                   "chunking": chunking,
+                   "chunking": chunking, "tile_w": head_cfg["tile_w"],
                    "chunking_meaning": "n > 0: n tiles per block; n < 0: balanced over -n blocks per SM",
                    "E_final": E_final, "wall_s": wall},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": roof[dom]["achieved"], "peak": peak,
