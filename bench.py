@@ -548,29 +548,37 @@ def bench_batched(api, synth, torch, flush, n=512, outer=10, inner=10):
             "max_rel_diff_E_final_default_chunking_vs_plain": rel0}
 
 
-def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, max_active=256):
+def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, max_active=256,
+                  sweep=((100.0, 150), (200.0, 300), (400.0, 600))):
     """Serving form: Poisson arrivals (mean `rate` per second), 50/50 mix of
     ARAP warps (square, side log-uniform in [64, 1024]) and icosphere mesh
     deformations (levels 4-6, 2.5k-41k vertices), each LM <= 10 outer x 10 PCG
     to relative energy change 1e-6, admission by an HBM budget of 120 GB.
-    Requests reuse a pool of 24 warp templates and 3 meshes (fresh unknowns per
-    request).  Served = continuous batching (opt_server_*), admission by the
-    budget alone and, second, with at most `max_active` requests admitted at
-    once; plain = one request at a time in arrival order (opt_solve_lm, direct
-    launches)."""
+    Requests reuse a pool of 24 warp templates and 3 meshes whose constants
+    stay on the device (fresh unknowns per request).  Both arms take the same
+    input path: every request is planned from its device-resident template.
+    Served = continuous batching (opt_server_*), admission by the budget alone
+    and, second, with at most `max_active` requests admitted at once; plain =
+    one request at a time in arrival order (opt_problem_create + opt_solve_lm
+    with direct launches).  Beside the 2,000/s stream (arrivals outpace both
+    arms: latency measures the backlog), `sweep` offers (rate, requests) below
+    capacity, where latency measures service."""
     import numpy as np
-    rng = np.random.default_rng(synth.BASE_SEED + 5)
     sides = synth.batch_sides(24, 64, 1024, seed=synth.BASE_SEED + 6)
     warps = [synth.warp_problem(int(s), int(s), synth.warp_handle_count(int(s), int(s)), seed=900 + i)
              for i, s in enumerate(sides)]
     meshes = [synth.mesh_problem(l, seed=950 + l) for l in (4, 5, 6)]
     templates = [api.make_descriptor(p, "cuda") + (p.kind,) for p in warps + meshes]
-    kinds = rng.random(n_req) < 0.5
-    pick = np.where(kinds, rng.integers(0, len(warps), n_req), len(warps) + rng.integers(0, 3, n_req))
-    arrivals = synth.arrival_times(n_req, rate, seed=synth.BASE_SEED + 7)
-    OUT, INN, TOL = 10, 10, 1e-6
+    OUT, INN, TOL = SERVE_OUT, SERVE_INN, SERVE_TOL
 
-    def served(cap):
+    def stream(n, r, seed_off):
+        rng = np.random.default_rng(synth.BASE_SEED + 5 + seed_off)
+        kinds = rng.random(n) < 0.5
+        pick = np.where(kinds, rng.integers(0, len(warps), n), len(warps) + rng.integers(0, 3, n))
+        return pick, synth.arrival_times(n, r, seed=synth.BASE_SEED + 7 + seed_off)
+
+    def served(cap, pick, arrivals):
+        n = len(pick)
         srv = api.Server(budget, outer=OUT, inner=INN, rel_tol=TOL, max_active=cap)
         # warm-up: one request of each template kind
         for t in (0, len(warps)):
@@ -581,9 +589,9 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, 
         done, lat, nxt, rounds = {}, {}, 0, 0
         pending = {}
         t0 = time.perf_counter()
-        while len(done) < n_req:
+        while len(done) < n:
             now = time.perf_counter() - t0
-            while nxt < n_req and arrivals[nxt] <= now:
+            while nxt < n and arrivals[nxt] <= now:
                 pending[srv.submit_template(templates[pick[nxt]])] = nxt
                 nxt += 1
             if pending:
@@ -598,41 +606,59 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, 
                         lat[i] = tnow - arrivals[i]
             else:
                 time.sleep(max(0.0, min(1e-3, arrivals[nxt] - now)))
-        span = max(arrivals[i] + lat[i] for i in range(n_req)) - arrivals[0]
+        span = max(arrivals[i] + lat[i] for i in range(n)) - arrivals[0]
         srv.close()
-        return done, list(lat.values()), span, rounds
+        return done, [lat[i] for i in range(n)], span, rounds
 
-    done, L, span_served, rounds = served(0)
-    done_c, LC, span_capped, rounds_c = served(max_active)
-
-    # plain: a single worker, requests in arrival order
-    plain_lat, plain_done = {}, {}
-    probs = warps + meshes
-    t0 = time.perf_counter()
-    for i in range(n_req):
-        now = time.perf_counter() - t0
-        if arrivals[i] > now:
-            time.sleep(arrivals[i] - now)
-        g = api.Problem(probs[pick[i]])
-        r = g.solve_lm(OUT, INN, rel_tol=TOL, use_graph=0)
+    def plain(pick, arrivals):
+        # a single worker, requests in arrival order, each planned from its template
+        n = len(pick)
+        g = api.Problem.from_template(templates[0])      # warm-up
+        g.solve_lm(OUT, INN, rel_tol=TOL, use_graph=0)
         g.close()
-        plain_done[i] = r
-        plain_lat[i] = time.perf_counter() - t0 - arrivals[i]
-    span_plain = max(arrivals[i] + plain_lat[i] for i in range(n_req)) - arrivals[0]
+        torch.cuda.synchronize()
+        lat, done = {}, {}
+        t0 = time.perf_counter()
+        for i in range(n):
+            now = time.perf_counter() - t0
+            if arrivals[i] > now:
+                time.sleep(arrivals[i] - now)
+            g = api.Problem.from_template(templates[pick[i]])
+            done[i] = g.solve_lm(OUT, INN, rel_tol=TOL, use_graph=0)
+            g.close()
+            lat[i] = time.perf_counter() - t0 - arrivals[i]
+        span = max(arrivals[i] + lat[i] for i in range(n)) - arrivals[0]
+        return done, [lat[i] for i in range(n)], span
 
-    def maxdiff(d):
-        return max(abs(d[i]["E_final"] - plain_done[i]["E_final"]) / max(abs(plain_done[i]["E_final"]), 1e-30)
-                   for i in range(n_req))
+    pick, arrivals = stream(n_req, rate, 0)
+    done, L, span_served, rounds = served(0, pick, arrivals)
+    done_c, LC, span_capped, rounds_c = served(max_active, pick, arrivals)
+    plain_done, PL, span_plain = plain(pick, arrivals)
+
+    def maxdiff(d, ref, n):
+        return max(abs(d[i]["E_final"] - ref[i]["E_final"]) / max(abs(ref[i]["E_final"]), 1e-30) for i in range(n))
 
     same_outer = sum(done[i]["outer_done"] == plain_done[i]["outer_done"] for i in range(n_req))
     same_outer_c = sum(done_c[i]["outer_done"] == plain_done[i]["outer_done"] for i in range(n_req))
-    PL = list(plain_lat.values())
+    # offered rates below capacity: service latency, continuous batching (capped) against plain
+    below = []
+    for k, (r_, n_) in enumerate(sweep):
+        pk, ar = stream(n_, r_, 10 + k)
+        dc, lc, sc, _ = served(max_active, pk, ar)
+        dp, lp, sp = plain(pk, ar)
+        below.append({"rate_per_s": r_, "requests": n_,
+                      "served_solves_per_s": n_ / sc, "served_p50_ms": 1e3 * pct(lc, 50),
+                      "served_p99_ms": 1e3 * pct(lc, 99),
+                      "plain_solves_per_s": n_ / sp, "plain_p50_ms": 1e3 * pct(lp, 50),
+                      "plain_p99_ms": 1e3 * pct(lp, 99),
+                      "max_rel_diff_E_final_served_vs_plain": maxdiff(dc, dp, n_)})
     for tpl in templates:
         del tpl
     torch.cuda.empty_cache()
     details = {"template": [int(t) for t in pick], "served": [done_c[i] for i in range(n_req)],
                "plain": [plain_done[i] for i in range(n_req)]}
     return details, {"requests": n_req, "rate_per_s": rate, "budget_gb": budget / 2 ** 30, "rounds": rounds,
+            "input_path": "both arms plan every request from device-resident templates",
             "served_solves_per_s": n_req / span_served, "served_p50_ms": 1e3 * pct(L, 50),
             "served_p99_ms": 1e3 * pct(L, 99),
             "capped_max_active": max_active, "capped_rounds": rounds_c,
@@ -642,9 +668,10 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, 
             "plain_p99_ms": 1e3 * pct(PL, 99),
             "speedup_solves_per_s": span_plain / span_served,
             "capped_speedup_solves_per_s": span_plain / span_capped,
-            "max_rel_diff_E_final_served_vs_plain": maxdiff(done),
-            "max_rel_diff_E_final_capped_vs_plain": maxdiff(done_c),
-            "same_outer_count": same_outer, "capped_same_outer_count": same_outer_c}
+            "max_rel_diff_E_final_served_vs_plain": maxdiff(done, plain_done, n_req),
+            "max_rel_diff_E_final_capped_vs_plain": maxdiff(done_c, plain_done, n_req),
+            "same_outer_count": same_outer, "capped_same_outer_count": same_outer_c,
+            "below_capacity": below}
 
 
 def run_ours(args):

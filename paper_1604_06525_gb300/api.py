@@ -320,6 +320,36 @@ class Problem:
             _check(create(ctypes.byref(d), None, ctypes.byref(h)), "opt_problem_create_graph")
         self.h = h
 
+    @classmethod
+    def from_template(cls, template, tile_w: int = 0):
+        """Plans a problem over a device-resident template (template =
+        make_descriptor(prob, device) + (kind,)): the constants are shared,
+        only the unknowns are fresh -- the input path of a server request."""
+        import torch
+        d0, x0, keep, kind = template
+        self = cls.__new__(cls)
+        self.lib = load_library()
+        self.kind = kind
+        self.device = x0.device
+        self.x = x0.clone()
+        self._keep = [keep]
+        d = type(d0).from_buffer_copy(d0)
+        for c in range(self.x.shape[0]):
+            d.unknowns[c] = _ptr(self.x[c])
+        h = c_void_p()
+        if kind in ("warp", "poisson"):
+            self.W, self.H = d.W, d.H
+            plan = default_params(tile_w=tile_w)
+            _check(self.lib.opt_problem_create_grid(ctypes.byref(d), ctypes.byref(plan), ctypes.byref(h)),
+                   "opt_problem_create_grid")
+        elif kind == "mesh":
+            self.V = d.V
+            _check(self.lib.opt_problem_create_graph(ctypes.byref(d), None, ctypes.byref(h)), "opt_problem_create_graph")
+        else:
+            raise ValueError(f"templates of kind {kind} are not supported")
+        self.h = h
+        return self
+
     # ------------------------------------------------------------------
     def close(self):
         if getattr(self, "h", None) and self.h.value:

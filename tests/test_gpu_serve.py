@@ -202,3 +202,20 @@ def test_serve_failed_rebuild_ends_active_requests_and_keeps_serving(api):
     with pytest.raises(api.OptError):
         srv.inject_rebuild_failure(0)
     srv.close()
+
+
+def test_problem_from_template_equals_plain_problem(api):
+    """Planning from a device-resident template (the input path both serving
+    arms take) gives the same solve as planning from host arrays."""
+    for prob in (synth.warp_problem(70, 50, 6, seed=430), synth.mesh_problem(2, seed=431, handle_frac=0.05)):
+        tpl = api.make_descriptor(prob, "cuda") + (prob.kind,)
+        a = api.Problem(prob)
+        b = api.Problem.from_template(tpl)
+        ra = a.solve_lm(OUTER, INNER, rel_tol=REL_TOL)
+        rb = b.solve_lm(OUTER, INNER, rel_tol=REL_TOL)
+        assert ra["E_history"] == rb["E_history"] and ra["outer_done"] == rb["outer_done"]
+        assert np.array_equal(a.x.cpu().numpy(), b.x.cpu().numpy())
+        # the template's own unknowns are untouched
+        assert np.array_equal(tpl[1].cpu().numpy().reshape(-1), prob.x0.reshape(-1).astype(np.float32))
+        a.close()
+        b.close()
