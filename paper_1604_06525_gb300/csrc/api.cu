@@ -690,9 +690,11 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   CKS(upload(dhtgt, hts));
   CKS(dalloc(q, &q->d_tiles, tiles.size()));
   CKS(upload(q->d_tiles, tiles));
+  q->h_tiles = tiles;
   q->ntiles = (int)tiles.size();
   CKS(dalloc(q, &q->d_chunks, chunks.size()));
   CKS(upload(q->d_chunks, chunks));
+  q->h_chunks = chunks;
   q->nchunks = (int)chunks.size();
   CKS(dalloc(q, &q->d_part, 2 * chunks.size()));
   CKS(dalloc(q, &q->dg, 1));
@@ -992,6 +994,9 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   CKS(upload(q->d_vchunks, vch));
   CKS(dalloc(q, &q->d_echunks, ech.size()));
   CKS(upload(q->d_echunks, ech));
+  q->h_vch = vch;
+  q->h_ech = ech;
+  q->h_tch = tch;
   q->nvchunks = (int)vch.size();
   q->nechunks = (int)ech.size();
   if (tiled) {
@@ -1325,6 +1330,7 @@ static opt_status rechunk(opt_problem* pb, int per) {
       CKS(dalloc(pb, &pb->d_part, 2 * chunks.size()));
     }
     CKS(upload(pb->d_chunks, chunks));
+    pb->h_chunks = chunks;
     pb->nchunks = (int)chunks.size();
     pb->hg.chunk_begin = 0;
     pb->hg.chunk_end = pb->nchunks;
@@ -1339,6 +1345,8 @@ static opt_status rechunk(opt_problem* pb, int per) {
     if (need > 2 * (size_t)std::max({pb->nvchunks, pb->nechunks, pb->ntchunks})) CKS(dalloc(pb, &pb->d_part, need));
     CKS(upload(pb->d_vchunks, vch));
     CKS(upload(pb->d_echunks, ech));
+    pb->h_vch = vch;
+    pb->h_ech = ech;
     pb->nvchunks = (int)vch.size();
     pb->nechunks = (int)ech.size();
     pb->hm.vchunk_begin = 0;

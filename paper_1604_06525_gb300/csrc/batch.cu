@@ -180,8 +180,7 @@ opt_status build_tables(opt_batch* b, int tpc) {
     std::vector<int> tiles;
     for (size_t mi = 0; mi < g.members.size(); ++mi) {
       opt_problem* pb = b->probs[g.members[mi]];
-      std::vector<int> t(pb->ntiles);
-      BCK(cudaMemcpy(t.data(), pb->d_tiles, t.size() * sizeof(int), cudaMemcpyDeviceToHost));
+      const std::vector<int>& t = pb->h_tiles;
       GridProb d = pb->hg;
       d.chunk_begin = (int)chunks.size();
       const int base = (int)tiles.size();
@@ -190,9 +189,7 @@ opt_status build_tables(opt_batch* b, int tpc) {
           chunks.push_back(Chunk{(int)mi, base + s, base + std::min(s + tpc, pb->ntiles), 0});
       } else {
         // the member's own split: identical reductions to its solo solve
-        std::vector<Chunk> own(pb->nchunks);
-        BCK(cudaMemcpy(own.data(), pb->d_chunks, own.size() * sizeof(Chunk), cudaMemcpyDeviceToHost));
-        for (Chunk c : own) chunks.push_back(Chunk{(int)mi, base + c.begin, base + c.end, 0});
+        for (Chunk c : pb->h_chunks) chunks.push_back(Chunk{(int)mi, base + c.begin, base + c.end, 0});
       }
       d.chunk_end = (int)chunks.size();
       tiles.insert(tiles.end(), t.begin(), t.end());
@@ -216,9 +213,8 @@ opt_status build_tables(opt_batch* b, int tpc) {
     }
     for (size_t mi = 0; mi < g.members.size(); ++mi) {
       opt_problem* pb = b->probs[g.members[mi]];
-      std::vector<Chunk> v(pb->nvchunks), e(pb->nechunks);
-      BCK(cudaMemcpy(v.data(), pb->d_vchunks, v.size() * sizeof(Chunk), cudaMemcpyDeviceToHost));
-      BCK(cudaMemcpy(e.data(), pb->d_echunks, e.size() * sizeof(Chunk), cudaMemcpyDeviceToHost));
+      const std::vector<Chunk>& v = pb->h_vch;
+      const std::vector<Chunk>& e = pb->h_ech;
       MeshProb d = pb->hm;
       d.vchunk_begin = (int)vch.size();
       for (Chunk c : v) { c.prob = (int)mi; vch.push_back(c); }
@@ -228,9 +224,7 @@ opt_status build_tables(opt_batch* b, int tpc) {
       d.echunk_end = (int)ech.size();
       d.tchunk_begin = (int)tch.size();
       if (tiled) {
-        std::vector<Chunk> t(pb->ntchunks);
-        BCK(cudaMemcpy(t.data(), pb->d_tchunks, t.size() * sizeof(Chunk), cudaMemcpyDeviceToHost));
-        for (Chunk c : t) { c.prob = (int)mi; tch.push_back(c); }
+        for (Chunk c : pb->h_tch) { c.prob = (int)mi; tch.push_back(c); }
       }
       d.tchunk_end = (int)tch.size();
       mp.push_back(d);

@@ -66,6 +66,9 @@ struct opt_problem {
   int tile_w = 0;                       // grids: tile width (32 or 128)
   bool has_grid_desc = false;           // grids: the planning input, kept for re-planning at another
   opt_grid_desc grid_desc{};            //   tile width (its arrays are the caller's and outlive the problem)
+  // host mirrors of the work tables (batches build their combined tables from these)
+  std::vector<int> h_tiles;
+  std::vector<optgb::Chunk> h_chunks, h_vch, h_ech, h_tch;
   // host copies kept for building the materialized Jacobian
   std::vector<unsigned char> h_mask;    // grid mask (empty = none)
   std::vector<int> h_hpix;              // grid handles (pitched index) / mesh handles (vertex)
@@ -112,6 +115,8 @@ struct opt_problem {
     swap(nvchunks, o.nvchunks); swap(nechunks, o.nechunks); swap(d_tchunks, o.d_tchunks);
     swap(ntchunks, o.ntchunks); swap(apply_form, o.apply_form); swap(chunking, o.chunking);
     swap(tile_w, o.tile_w); swap(has_grid_desc, o.has_grid_desc); swap(grid_desc, o.grid_desc);
+    swap(h_tiles, o.h_tiles); swap(h_chunks, o.h_chunks); swap(h_vch, o.h_vch); swap(h_ech, o.h_ech);
+    swap(h_tch, o.h_tch);
     swap(h_mask, o.h_mask); swap(h_hpix, o.h_hpix); swap(h_e0, o.h_e0); swap(h_e1, o.h_e1);
     swap(d_perm, o.d_perm); swap(csr, o.csr);
     swap(d_part, o.d_part); swap(d_s, o.d_s); swap(d_Ehist, o.d_Ehist); swap(Ehist_cap, o.Ehist_cap);
