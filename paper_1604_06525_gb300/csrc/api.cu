@@ -859,7 +859,7 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   }
   // out-edge rows of the sorted list, and the in-edges of every vertex
   // (sources ascending, as the sorted list visits them)
-  std::vector<int> orow((size_t)V + 1, 0), irow((size_t)V + 1, 0), isrc((size_t)E), itpos((size_t)E);
+  std::vector<int> orow((size_t)V + 1, 0), irow((size_t)V + 1, 0), isrc((size_t)E);
   for (int e = 0; e < E; ++e) {
     orow[(size_t)e0[e] + 1] += 1;
     irow[(size_t)e1[e] + 1] += 1;
@@ -870,68 +870,13 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   }
   {
     std::vector<int> fill(irow.begin(), irow.end() - 1);
-    for (int e = 0; e < E; ++e) {
-      const size_t k = (size_t)fill[e1[e]]++;
-      isrc[k] = e0[e];
-      itpos[k] = e;            // the edge's position in the sorted list
-    }
-  }
-
-  // Vertex-tile tables of the tiled ARAP-mesh apply: per tile of VT vertices
-  // the out-of-tile neighbours (halo), each edge's far end as an index into
-  // the tile's vertex + halo table, the in-edges arriving from outside the
-  // tile, and the shared-memory slot of every in-edge's J_e p (the edge's own
-  // slot when it starts inside the tile).  A tile over the kernel's
-  // capacities leaves the problem on the general path (no tables).
-  std::vector<int> hptr, hvtx, lnbr, rptr, rin, itslot;
-  bool tiled = !ed && !grid3 && D == 3;
-  if (tiled) {
-    hptr.assign((size_t)nvt + 1, 0);
-    rptr.assign((size_t)nvt + 1, 0);
-    lnbr.assign((size_t)E, 0);
-    itslot.assign((size_t)E, 0);
-    std::vector<int> halo;
-    for (int T = 0; T < nvt && tiled; ++T) {
-      const int vb = T * VT, ve = std::min(V, vb + VT);
-      const int eb = orow[vb], ee = orow[ve];
-      halo.clear();
-      for (int k = eb; k < ee; ++k)
-        if (e1[k] < vb || e1[k] >= ve) halo.push_back(e1[k]);
-      for (int k = irow[vb]; k < irow[ve]; ++k)
-        if (isrc[k] < vb || isrc[k] >= ve) halo.push_back(isrc[k]);
-      std::sort(halo.begin(), halo.end());
-      halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
-      if ((int)halo.size() > MT_HALO) { tiled = false; break; }
-      auto local = [&](int v) {
-        if (v >= vb && v < ve) return v - vb;
-        return VT + (int)(std::lower_bound(halo.begin(), halo.end(), v) - halo.begin());
-      };
-      for (int k = eb; k < ee; ++k) lnbr[k] = local(e1[k]);
-      const int nout = ee - eb;
-      int nrin = 0;
-      for (int i = vb; i < ve; ++i)
-        for (int k = irow[i]; k < irow[(size_t)i + 1]; ++k) {
-          if (isrc[k] >= vb && isrc[k] < ve) {
-            itslot[k] = itpos[k] - eb;
-          } else {
-            itslot[k] = nout + nrin++;
-            rin.push_back((local(isrc[k]) << 16) | (i - vb));
-          }
-        }
-      if (nout + nrin > MT_SLOTS) { tiled = false; break; }
-      hvtx.insert(hvtx.end(), halo.begin(), halo.end());
-      hptr[(size_t)T + 1] = (int)hvtx.size();
-      rptr[(size_t)T + 1] = (int)rin.size();
-    }
+    for (int e = 0; e < E; ++e) isrc[(size_t)fill[e1[e]]++] = e0[e];
   }
 
   const int target = std::max(1, q->sms * 8);
   std::vector<Chunk> vch = make_chunks_balanced(nvt, target, 0);
   for (Chunk& c : vch) { c.begin *= VT; c.end = std::min(V, c.end * VT); }
   std::vector<Chunk> ech = make_chunks_balanced(E, target, 0);
-  std::vector<Chunk> tch;
-  if (tiled)
-    for (int T = 0; T < nvt; ++T) tch.push_back(Chunk{0, T * VT, std::min(V, (T + 1) * VT), 0});
 
   const size_t pl = (size_t)Vp;
   float *U = nullptr, *dgw = nullptr, *m = nullptr, *dc = nullptr, *dhtgt = nullptr;
@@ -948,30 +893,13 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   float4 *grec = nullptr, *vrec = nullptr;
   CKS(dalloc(q, &grec, (size_t)NGR * V));
   CKS(dalloc(q, &vrec, (size_t)NVR * V));
-  int *dorow = nullptr, *dirow = nullptr, *disrc = nullptr, *ditpos = nullptr;
+  int *dorow = nullptr, *dirow = nullptr, *disrc = nullptr;
   CKS(dalloc(q, &dorow, orow.size()));
   CKS(upload(dorow, orow));
   CKS(dalloc(q, &dirow, irow.size()));
   CKS(upload(dirow, irow));
   CKS(dalloc(q, &disrc, std::max<size_t>(1, isrc.size())));
   if (E > 0) CKS(upload(disrc, isrc));
-  CKS(dalloc(q, &ditpos, std::max<size_t>(1, itpos.size())));
-  if (E > 0) CKS(upload(ditpos, itpos));
-  int *dhptr = nullptr, *dhvtx = nullptr, *dlnbr = nullptr, *drptr = nullptr, *drin = nullptr, *ditslot = nullptr;
-  if (tiled) {
-    CKS(dalloc(q, &dhptr, hptr.size()));
-    CKS(upload(dhptr, hptr));
-    CKS(dalloc(q, &dhvtx, std::max<size_t>(1, hvtx.size())));
-    if (!hvtx.empty()) CKS(upload(dhvtx, hvtx));
-    CKS(dalloc(q, &dlnbr, std::max<size_t>(1, lnbr.size())));
-    if (E > 0) CKS(upload(dlnbr, lnbr));
-    CKS(dalloc(q, &drptr, rptr.size()));
-    CKS(upload(drptr, rptr));
-    CKS(dalloc(q, &drin, std::max<size_t>(1, rin.size())));
-    if (!rin.empty()) CKS(upload(drin, rin));
-    CKS(dalloc(q, &ditslot, std::max<size_t>(1, itslot.size())));
-    if (E > 0) CKS(upload(ditslot, itslot));
-  }
   for (int c = 0; c < D; ++c) {
     std::vector<float> Ui((size_t)V);
     for (int k = 0; k < V; ++k) Ui[k] = Uh[c][perm[k]];
@@ -996,15 +924,10 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   CKS(upload(q->d_echunks, ech));
   q->h_vch = vch;
   q->h_ech = ech;
-  q->h_tch = tch;
+  q->tileable = !ed && !grid3 && D == 3;
   q->nvchunks = (int)vch.size();
   q->nechunks = (int)ech.size();
-  if (tiled) {
-    CKS(dalloc(q, &q->d_tchunks, tch.size()));
-    CKS(upload(q->d_tchunks, tch));
-    q->ntchunks = (int)tch.size();
-  }
-  CKS(dalloc(q, &q->d_part, 2 * std::max({vch.size(), ech.size(), tch.size()})));
+  CKS(dalloc(q, &q->d_part, 2 * std::max(vch.size(), ech.size())));
   CKS(dalloc(q, &q->dm, 1));
   for (int k = 0; k < NXg; ++k) q->user_x[k] = ux[k];
   q->h_e0 = e0;
@@ -1022,8 +945,8 @@ static opt_status create_graph_impl(const opt_graph_desc* d, int D, opt_problem*
   g.use_precond = 1; g.lm = 0;
   g.x = q->x; g.U = U; g.degw = dgw; g.e0 = de0; g.e1 = de1;
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
-  g.orow = dorow; g.irow = dirow; g.isrc = disrc; g.itpos = ditpos;
-  g.hptr = dhptr; g.hvtx = dhvtx; g.lnbr = dlnbr; g.rptr = drptr; g.rin = drin; g.itslot = ditslot;
+  g.orow = dorow; g.irow = dirow; g.isrc = disrc;
+  g.hptr = nullptr; g.hvtx = nullptr; g.lnbr = nullptr; g.rptr = nullptr; g.rin = nullptr; g.itslot = nullptr;
   g.gw = grid3 ? grid3[0] : 0; g.gh = grid3 ? grid3[1] : 0; g.gd = grid3 ? grid3[2] : 0; g.gpad = 0;
   g.grec = grec; g.vrec = vrec;
   g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;
@@ -1310,6 +1233,106 @@ opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, flo
   return status;
 }
 
+// Vertex-tile tables of the tiled ARAP-mesh apply, built on first use (the
+// autotuner, opt_problem_set_apply_form) from the sorted edge list: per tile of
+// VT vertices the out-of-tile neighbours (halo), each edge's far end as an
+// index into the tile's vertex + halo table, the in-edges arriving from
+// outside the tile, the shared-memory slot of every in-edge's J_e p (the
+// edge's own slot when it starts inside the tile), and one chunk per tile.
+// A tile over the kernel's capacities marks the problem untileable.
+static opt_status ensure_tile_tables(opt_problem* q) {
+  if (q->d_tchunks) return OPT_OK;
+  if (!q->tileable) return OPT_ERR_INVALID_ARG;
+  const int V = q->V, E = q->E, nvt = (V + VT - 1) / VT;
+  const std::vector<int>& e0 = q->h_e0;
+  const std::vector<int>& e1 = q->h_e1;
+  std::vector<int> orow((size_t)V + 1, 0), irow((size_t)V + 1, 0), isrc((size_t)E), itpos((size_t)E);
+  for (int e = 0; e < E; ++e) {
+    orow[(size_t)e0[e] + 1] += 1;
+    irow[(size_t)e1[e] + 1] += 1;
+  }
+  for (int v = 0; v < V; ++v) {
+    orow[(size_t)v + 1] += orow[v];
+    irow[(size_t)v + 1] += irow[v];
+  }
+  {
+    std::vector<int> fill(irow.begin(), irow.end() - 1);
+    for (int e = 0; e < E; ++e) {
+      const size_t k = (size_t)fill[e1[e]]++;
+      isrc[k] = e0[e];
+      itpos[k] = e;
+    }
+  }
+  std::vector<int> hptr((size_t)nvt + 1, 0), rptr((size_t)nvt + 1, 0), hvtx, rin;
+  std::vector<int> lnbr((size_t)E, 0), itslot((size_t)E, 0), halo;
+  for (int T = 0; T < nvt; ++T) {
+    const int vb = T * VT, ve = std::min(V, vb + VT);
+    const int eb = orow[vb], ee = orow[ve];
+    halo.clear();
+    for (int k = eb; k < ee; ++k)
+      if (e1[k] < vb || e1[k] >= ve) halo.push_back(e1[k]);
+    for (int k = irow[vb]; k < irow[ve]; ++k)
+      if (isrc[k] < vb || isrc[k] >= ve) halo.push_back(isrc[k]);
+    std::sort(halo.begin(), halo.end());
+    halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+    if ((int)halo.size() > MT_HALO) {
+      q->tileable = false;
+      return OPT_ERR_INVALID_ARG;
+    }
+    auto local = [&](int v) {
+      if (v >= vb && v < ve) return v - vb;
+      return VT + (int)(std::lower_bound(halo.begin(), halo.end(), v) - halo.begin());
+    };
+    for (int k = eb; k < ee; ++k) lnbr[k] = local(e1[k]);
+    const int nout = ee - eb;
+    int nrin = 0;
+    for (int i = vb; i < ve; ++i)
+      for (int k = irow[i]; k < irow[(size_t)i + 1]; ++k) {
+        if (isrc[k] >= vb && isrc[k] < ve) {
+          itslot[k] = itpos[k] - eb;
+        } else {
+          itslot[k] = nout + nrin++;
+          rin.push_back((local(isrc[k]) << 16) | (i - vb));
+        }
+      }
+    if (nout + nrin > MT_SLOTS) {
+      q->tileable = false;
+      return OPT_ERR_INVALID_ARG;
+    }
+    hvtx.insert(hvtx.end(), halo.begin(), halo.end());
+    hptr[(size_t)T + 1] = (int)hvtx.size();
+    rptr[(size_t)T + 1] = (int)rin.size();
+  }
+  std::vector<Chunk> tch;
+  for (int T = 0; T < nvt; ++T) tch.push_back(Chunk{0, T * VT, std::min(V, (T + 1) * VT), 0});
+  CK(cudaDeviceSynchronize());
+  int *dhptr = nullptr, *dhvtx = nullptr, *dlnbr = nullptr, *drptr = nullptr, *drin = nullptr, *ditslot = nullptr;
+  CKS(dalloc(q, &dhptr, hptr.size()));
+  CKS(upload(dhptr, hptr));
+  CKS(dalloc(q, &dhvtx, std::max<size_t>(1, hvtx.size())));
+  if (!hvtx.empty()) CKS(upload(dhvtx, hvtx));
+  CKS(dalloc(q, &dlnbr, std::max<size_t>(1, lnbr.size())));
+  if (E > 0) CKS(upload(dlnbr, lnbr));
+  CKS(dalloc(q, &drptr, rptr.size()));
+  CKS(upload(drptr, rptr));
+  CKS(dalloc(q, &drin, std::max<size_t>(1, rin.size())));
+  if (!rin.empty()) CKS(upload(drin, rin));
+  CKS(dalloc(q, &ditslot, std::max<size_t>(1, itslot.size())));
+  if (E > 0) CKS(upload(ditslot, itslot));
+  Chunk* dtch = nullptr;
+  CKS(dalloc(q, &dtch, tch.size()));
+  CKS(upload(dtch, tch));
+  if (tch.size() > (size_t)std::max(q->nvchunks, q->nechunks)) CKS(dalloc(q, &q->d_part, 2 * tch.size()));
+  q->d_tchunks = dtch;
+  q->ntchunks = (int)tch.size();
+  q->h_tch = tch;
+  MeshProb& g = q->hm;
+  g.hptr = dhptr; g.hvtx = dhvtx; g.lnbr = dlnbr; g.rptr = drptr; g.rin = drin; g.itslot = ditslot;
+  g.tchunk_begin = 0;
+  g.tchunk_end = q->ntchunks;
+  return upload_desc(q, nullptr);
+}
+
 // Rebuilds the problem's chunk table with `per` tiles (grid) or vertex tiles
 // (graph) per block; 0 restores the default (balanced, 2 blocks per SM for grids, 8 for graphs).
 static opt_status rechunk(opt_problem* pb, int per) {
@@ -1388,8 +1411,8 @@ opt_status opt_problem_autotune(opt_problem* prob, int32_t* chosen, float* best_
   if (!prob) return OPT_ERR_INVALID_ARG;
   int best = 0;
   float bms = 1e30f;
-  if (prob->d_tchunks) {
-    // graphs with tile tables: the tiled apply against the two-pass gather
+  if (prob->tileable && ensure_tile_tables(prob) == OPT_OK) {
+    // ARAP meshes within the tile capacities: the tiled apply against the two-pass gather
     int b1 = 0, b0 = 0;
     float t1 = 0.f, t0 = 0.f;
     prob->apply_form = 1;
@@ -1432,12 +1455,13 @@ opt_status opt_problem_get_config(const opt_problem* prob, int32_t* tile_w, int3
   if (!prob) return OPT_ERR_INVALID_ARG;
   if (tile_w) *tile_w = is_grid(prob) ? prob->tile_w : 0;
   if (chunking) *chunking = prob->chunking;
-  if (apply_form) *apply_form = prob->d_tchunks ? prob->apply_form : -1;
+  if (apply_form) *apply_form = (prob->d_tchunks || prob->tileable) ? prob->apply_form : -1;
   return OPT_OK;
 }
 
 opt_status opt_problem_set_apply_form(opt_problem* prob, int32_t form) {
-  if (!prob || form < 0 || form > 1 || (form == 1 && !prob->d_tchunks)) return OPT_ERR_INVALID_ARG;
+  if (!prob || form < 0 || form > 1) return OPT_ERR_INVALID_ARG;
+  if (form == 1) CKS(ensure_tile_tables(prob));
   CK(cudaDeviceSynchronize());
   if (prob->gexec) {
     cudaGraphExecDestroy(prob->gexec);

@@ -126,7 +126,6 @@ struct MeshProb {
   const int* orow;              // V + 1: out-edges of v are e1[orow[v] .. orow[v+1])
   const int* irow;              // V + 1: in-edges of v come from isrc[irow[v] .. irow[v+1])
   const int* isrc;              // E: sources of the in-edges, ascending per vertex
-  const int* itpos;             // E: position of each in-edge (irow order) in the sorted edge list
   // vertex-tile tables of the tiled apply (NULL: the problem exceeds the
   // capacities above and uses the general path)
   const int* hptr;              // tiles + 1: the halo of tile T is hvtx[hptr[T] .. hptr[T+1])

@@ -61,7 +61,8 @@ struct opt_problem {
   int nvchunks = 0, nechunks = 0;
   optgb::Chunk* d_tchunks = nullptr;   // tiled ARAP-mesh apply: one chunk per vertex tile (NULL: untiled)
   int ntchunks = 0;
-  int apply_form = 1;                   // problems with tile tables: 1 tiled apply, 0 two-pass gather
+  bool tileable = false;                // an ARAP mesh the tiled apply may take (tables built on first use)
+  int apply_form = 0;                   // ARAP meshes: 1 tiled apply, 0 two-pass gather (the default)
   int chunking = 0;                     // the granularity last set (0 = default)
   int tile_w = 0;                       // grids: tile width (32 or 128)
   bool has_grid_desc = false;           // grids: the planning input, kept for re-planning at another
@@ -113,7 +114,7 @@ struct opt_problem {
     swap(d_tiles, o.d_tiles); swap(ntiles, o.ntiles);
     swap(hm, o.hm); swap(dm, o.dm); swap(d_vchunks, o.d_vchunks); swap(d_echunks, o.d_echunks);
     swap(nvchunks, o.nvchunks); swap(nechunks, o.nechunks); swap(d_tchunks, o.d_tchunks);
-    swap(ntchunks, o.ntchunks); swap(apply_form, o.apply_form); swap(chunking, o.chunking);
+    swap(ntchunks, o.ntchunks); swap(tileable, o.tileable); swap(apply_form, o.apply_form); swap(chunking, o.chunking);
     swap(tile_w, o.tile_w); swap(has_grid_desc, o.has_grid_desc); swap(grid_desc, o.grid_desc);
     swap(h_tiles, o.h_tiles); swap(h_chunks, o.h_chunks); swap(h_vch, o.h_vch); swap(h_ech, o.h_ech);
     swap(h_tch, o.h_tch);

@@ -126,13 +126,15 @@ def make_mesh(level, noise, seed=31):
 
 @pytest.mark.parametrize("level,noise", MESH_CASES)
 @pytest.mark.parametrize("lam", [0.0, 0.5])
-def test_mesh_apply_jtj(api, level, noise, lam):
+@pytest.mark.parametrize("form", [0, 1])
+def test_mesh_apply_jtj(api, level, noise, lam, form):
     import torch
     prob = make_mesh(level, noise)
     e = oracle.make_energy(prob)
     x = prob.x0.reshape(-1).astype(np.float64)
     p = random_direction(prob, 7)
     gp = api.Problem(prob)
+    gp.set_apply_form(form)
     q, pq = gp.apply_jtj(torch.as_tensor(p, device="cuda"), lam)
     _, diag, _ = oracle.jtf_diag(e, x)
     qref = oracle.apply_jtj(e, x, p.astype(np.float64), lam, np.clip(diag, 1e-6, 1e32))
@@ -175,7 +177,8 @@ def test_mesh_one_way_edges_and_isolated_vertices(api, keep):
     x = prob.x0.reshape(-1).astype(np.float64)
     gp = api.Problem(prob)
     p = random_direction(prob, 4)
-    for lam in (0.0, 0.4):
+    for lam, form in ((0.0, 0), (0.4, 0), (0.0, 1), (0.4, 1)):
+        gp.set_apply_form(form)
         q, pq = gp.apply_jtj(torch.as_tensor(p, device="cuda"), lam)
         jtf, diag, E = oracle.jtf_diag(e, x)
         qref = oracle.apply_jtj(e, x, p.astype(np.float64), lam, np.clip(diag, 1e-6, 1e32))
@@ -206,6 +209,9 @@ def test_mesh_hub_vertex(api, hub_edges):
     e = oracle.make_energy(prob)
     x = prob.x0.reshape(-1).astype(np.float64)
     gp = api.Problem(prob)
+    with pytest.raises(api.OptError):
+        gp.set_apply_form(1)                       # beyond the tiled apply's capacities
+    assert gp.config()["apply_form"] == -1
     p = random_direction(prob, 6)
     jtf, diag, E = oracle.jtf_diag(e, x)
     for lam in (0.0, 0.3):
@@ -315,11 +321,13 @@ def check_lm_trajectory(rep, ref):
     assert relE(rep["lambda_final"], ref.lambda_final) <= tol, (rep["lambda_final"], ref.lambda_final, tol)
 
 
-def test_lm_mesh_small(api):
+@pytest.mark.parametrize("form", [0, 1])
+def test_lm_mesh_small(api, form):
     prob = synth.mesh_problem(3, seed=91, handle_frac=0.02)
     e = oracle.make_energy(prob)
     ref = oracle.levenberg_marquardt(e, prob.x0.reshape(-1), 6, 15)
     gp = api.Problem(prob)
+    gp.set_apply_form(form)
     rep = gp.solve_lm(6, 15, lambda0=1e-3)
     check_lm_trajectory(rep, ref)
 
@@ -652,6 +660,8 @@ def test_autotuned_configurations_keep_results(api):
     a.close()
     m = synth.mesh_problem(3, seed=172, handle_frac=0.03)
     g = api.Problem(m)
+    assert g.config()["apply_form"] == 0          # the two-pass gather by default
+    g.set_apply_form(1)                            # tiled: tables built on first use
     assert g.config()["apply_form"] == 1
     p = random_direction(m, 3)
     q1, pq1 = g.apply_jtj(torch.as_tensor(p, device="cuda"), 0.2)
