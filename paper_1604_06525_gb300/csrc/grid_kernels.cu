@@ -867,7 +867,10 @@ __device__ __forceinline__ void init_pair2(const OwnI2& o, float2 dxj, float2 dy
 }
 
 template <bool MASK>
-__global__ void __launch_bounds__(NT, 2) k_warp_init_wide(const GridProb* __restrict__ probs,
+#ifndef WARP_INIT_WIDE_MINB
+#define WARP_INIT_WIDE_MINB 2       // resident blocks per SM the wide warp PCGInit is compiled for
+#endif
+__global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(const GridProb* __restrict__ probs,
                                                           const Chunk* __restrict__ chunks,
                                                           const int* __restrict__ tiles,
                                                           double* __restrict__ part, int k_outer,
@@ -1418,10 +1421,16 @@ struct PoisWideSmem {
   float stg[NSTG_P][HH][SP];
   unsigned char mk[HH][SPB];
 };
+// PCGInit stages one raw plane fewer (X0..X3, T0..T3)
+struct PoisInitSmem {
+  float raw[NRAW_PI][HH][SP];
+  float stg[NSTG_P][HH][SP];
+  unsigned char mk[HH][SPB];
+};
 
 // weight of the staged pixel (gx, gy): 0 outside the grid, 1 fixed, 2 free
-template <bool MASK>
-__device__ __forceinline__ float4 pois_weights(const PoisWideSmem& sm, int row, int lane, const GridProb& pr,
+template <bool MASK, class S>
+__device__ __forceinline__ float4 pois_weights(const S& sm, int row, int lane, const GridProb& pr,
                                                int gx, int gy) {
   float w[4] = {0.f, 0.f, 0.f, 0.f};
   if (gy >= 0 && gy < pr.H) {
@@ -1447,8 +1456,8 @@ struct Nb5 {
 // warp's row.  O: own staged values (swizzled), lane 0 / 31 take the halo
 // columns.  Returns, per pack (A = pixels {0, 2}, B = {1, 3}) and channel,
 // S v_i - sum_j w_j v_j, and (init only) the own-residual energy sum.
-template <bool ENERGY>
-__device__ __forceinline__ void pois_stencil(const PoisWideSmem& sm, int ty, int lane, const float4 (&O)[NSTG_P],
+template <bool ENERGY, class S>
+__device__ __forceinline__ void pois_stencil(const S& sm, int ty, int lane, const float4 (&O)[NSTG_P],
                                              float2 (&outA)[4], float2 (&outB)[4], float2& SA, float2& SB,
                                              float2& eA, float2& eB) {
   const int c = 4 + 4 * lane;
@@ -1653,14 +1662,17 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __
 }
 
 template <bool MASK>
-__global__ void __launch_bounds__(NT, 2) k_poisson_init_wide(const GridProb* __restrict__ probs,
+#ifndef POIS_INIT_WIDE_MINB
+#define POIS_INIT_WIDE_MINB 2       // resident blocks per SM the wide Poisson PCGInit is compiled for
+#endif
+__global__ void __launch_bounds__(NT, POIS_INIT_WIDE_MINB) k_poisson_init_wide(const GridProb* __restrict__ probs,
                                                              const Chunk* __restrict__ chunks,
                                                              const int* __restrict__ tiles,
                                                              double* __restrict__ part, int k_outer,
                                                              float dmin, float dmax) {
   pdl_begin();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  PoisWideSmem& sm = *reinterpret_cast<PoisWideSmem*>(dyn_smem);
+  PoisInitSmem& sm = *reinterpret_cast<PoisInitSmem*>(dyn_smem);
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   Scalars* s = pr.s;
@@ -2027,9 +2039,11 @@ cudaError_t grid_kernels_prepare() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_poisson_apply_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_poisson_init_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
+      e = cudaFuncSetAttribute(k_poisson_init_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sizeof(PoisInitSmem));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_poisson_init_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
+      e = cudaFuncSetAttribute(k_poisson_init_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sizeof(PoisInitSmem));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_warp_pcg_coop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
@@ -2054,10 +2068,10 @@ void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, fl
     launch_pdl(k_warp_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
   else
     if (L.tw == W4 && L.masked)
-      launch_pdl(k_poisson_init_wide<true>, L.nchunks, NT, sizeof(PoisWideSmem), L.stream, L.probs, L.chunks, L.tiles,
+      launch_pdl(k_poisson_init_wide<true>, L.nchunks, NT, sizeof(PoisInitSmem), L.stream, L.probs, L.chunks, L.tiles,
                  L.part, k_outer, dmin, dmax);
     else if (L.tw == W4)
-      launch_pdl(k_poisson_init_wide<false>, L.nchunks, NT, sizeof(PoisWideSmem), L.stream, L.probs, L.chunks,
+      launch_pdl(k_poisson_init_wide<false>, L.nchunks, NT, sizeof(PoisInitSmem), L.stream, L.probs, L.chunks,
                  L.tiles, L.part, k_outer, dmin, dmax);
     else
       launch_pdl(k_poisson_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
