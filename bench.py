@@ -998,6 +998,9 @@ PROFILE_CASES = {
     "poisson2048": (lambda synth: synth.poisson_problem(2048, 2048, seed=synth.BASE_SEED), "Poisson 2048^2 x 4",
                     False),
     "mesh8": (lambda synth: synth.mesh_problem(8, seed=synth.BASE_SEED), "ARAP mesh, icosphere level 8", False),
+    # the mesh configuration's size with the tiled apply form pinned
+    "mesh7tiled": (lambda synth: synth.mesh_problem(7, seed=synth.BASE_SEED),
+                   "ARAP mesh, icosphere level 7, tiled apply", False, 0, 1),
     "embedded8": (lambda synth: synth.embedded_problem(8, seed=synth.BASE_SEED),
                   "embedded deformation, icosphere level 8", False),
     "volume128": (lambda synth: synth.volume_problem(128, 128, 128, 2048, seed=synth.BASE_SEED),
@@ -1060,12 +1063,15 @@ def run_profile_case(name):
         return run_profile_batch()
     builder, desc, f64 = PROFILE_CASES[name][:3]
     materialized = PROFILE_CASES[name][3] if len(PROFILE_CASES[name]) > 3 else 0
+    form = PROFILE_CASES[name][4] if len(PROFILE_CASES[name]) > 4 else None
     if f64:
         gp = api.ProblemF64(builder(synth))
         chunking = None
     else:
         gp = api.Problem(builder(synth))
         chunking, _ = gp.autotune()
+        if form is not None:
+            gp.set_apply_form(form)
     if materialized:
         x0 = gp.x.clone()
         gp.solve_gn(1, 3, materialized=materialized)          # structure built, graph captured
