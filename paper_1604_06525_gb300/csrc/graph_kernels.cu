@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__
   const long long pl = pr.Vp;
   const float alpha = s->alpha_f;
   const float* __restrict__ pn = pr.p + (long long)((par + 1) & 1) * 6 * pl;
-  F2 acc = f2_zero();
+  F2x2 acc = f2x2_zero();
   const int q0 = ch.begin / 4, q1 = (ch.end + 3) / 4;
   for (int qi = q0 + threadIdx.x; qi < q1; qi += NT) {
     const int v0 = 4 * qi;
@@ -693,16 +693,15 @@ __global__ void __launch_bounds__(NT) k_mesh_update(const MeshProb* __restrict__
       dv[c].z += alpha * pv[c].z; dv[c].w += alpha * pv[c].w;
       rv[c].x -= alpha * qv[c].x; rv[c].y -= alpha * qv[c].y;
       rv[c].z -= alpha * qv[c].z; rv[c].w -= alpha * qv[c].w;
-      f2_add_prod(acc, rv[c].x, __fmul_rn(m.x, rv[c].x));
-      f2_add_prod(acc, rv[c].y, __fmul_rn(m.y, rv[c].y));
-      f2_add_prod(acc, rv[c].z, __fmul_rn(m.z, rv[c].z));
-      f2_add_prod(acc, rv[c].w, __fmul_rn(m.w, rv[c].w));
+      const float2 r01 = make_float2(rv[c].x, rv[c].y), r23 = make_float2(rv[c].z, rv[c].w);
+      f2x2_add_prod(acc, r01, pk_mul(make_float2(m.x, m.y), r01));
+      f2x2_add_prod(acc, r23, pk_mul(make_float2(m.z, m.w), r23));
       *reinterpret_cast<float4*>(pr.d + c * pl + v0) = dv[c];
       *reinterpret_cast<float4*>(pr.r + c * pl + v0) = rv[c];
     }
   }
   pdl_trigger();
-  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
+  if (publish_partials(part, blockIdx.x, f2x2_fold(acc), f2_zero(), &s->counter, pr.vchunk_end - pr.vchunk_begin)) {
     double rz, unused;
     gather_partials(part, pr.vchunk_begin, pr.vchunk_end, &s->counter, rz, unused);
     if (threadIdx.x == 0) {

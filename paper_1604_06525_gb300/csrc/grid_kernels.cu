@@ -595,7 +595,7 @@ __device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, c
   pp.src[10] = pr.c;
   pp.src[11] = pr.c + pl;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  F2 acc = f2_zero();
+  F2x2 acc = f2x2_zero();
   // the tile index one tile ahead and the handle range of the current tile
   // are loaded an iteration early: the inline-assembly copies order all
   // memory accesses, so a late load would stall the warp at its use
@@ -737,16 +737,16 @@ __device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, c
       *reinterpret_cast<float4*>(pr.q + i) = make_float4(qx[0], qx[1], qx[2], qx[3]);
       *reinterpret_cast<float4*>(pr.q + pl + i) = make_float4(qy[0], qy[1], qy[2], qy[3]);
       *reinterpret_cast<float4*>(pr.q + 2 * pl + i) = make_float4(qt[0], qt[1], qt[2], qt[3]);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        f2_add_prod(acc, cmp(opx, k), qx[k]);
-        f2_add_prod(acc, cmp(opy, k), qy[k]);
-        f2_add_prod(acc, cmp(opt, k), qt[k]);
-      }
+      f2x2_add_prod(acc, lo2(opx), make_float2(qx[0], qx[1]));
+      f2x2_add_prod(acc, hi2(opx), make_float2(qx[2], qx[3]));
+      f2x2_add_prod(acc, lo2(opy), make_float2(qy[0], qy[1]));
+      f2x2_add_prod(acc, hi2(opy), make_float2(qy[2], qy[3]));
+      f2x2_add_prod(acc, lo2(opt), make_float2(qt[0], qt[1]));
+      f2x2_add_prod(acc, hi2(opt), make_float2(qt[2], qt[3]));
     }
   }
   cp_async_wait_all();
-  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
+  if (publish_partials(part, blockIdx.x, f2x2_fold(acc), f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double pq, unused;
     gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(cons
   const float2 w2 = make_float2(w, w);
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  F2 acc_rz = f2_zero(), acc_E = f2_zero();
+  F2x2 acc_rz = f2x2_zero(), acc_E = f2x2_zero();
   InitPlanes ip;
   ip.src[0] = pr.x; ip.src[1] = pr.x + pl; ip.src[2] = pr.x + 2 * pl; ip.src[3] = pr.c; ip.src[4] = pr.c + pl;
   int tc = tiles[ch.begin];
@@ -1008,10 +1008,16 @@ __global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(cons
         bx[k] = -gxv[k];
         by[k] = -gyv[k];
         bt[k] = -gtv[k];
-        f2_add_prod(acc_rz, bx[k], __fmul_rn(md[k], bx[k]));
-        f2_add_prod(acc_rz, by[k], __fmul_rn(md[k], by[k]));
-        f2_add_prod(acc_rz, bt[k], __fmul_rn(mt[k], bt[k]));
-        f2_add(acc_E, ev[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k += 2) {
+        const float2 md2 = make_float2(md[k], md[k + 1]), mt2 = make_float2(mt[k], mt[k + 1]);
+        const float2 bx2 = make_float2(bx[k], bx[k + 1]), by2 = make_float2(by[k], by[k + 1]);
+        const float2 bt2 = make_float2(bt[k], bt[k + 1]);
+        f2x2_add_prod(acc_rz, bx2, pk_mul(md2, bx2));
+        f2x2_add_prod(acc_rz, by2, pk_mul(md2, by2));
+        f2x2_add_prod(acc_rz, bt2, pk_mul(mt2, bt2));
+        f2x2_add(acc_E, make_float2(ev[k], ev[k + 1]));
       }
       const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
       *reinterpret_cast<float4*>(pr.r + i) = make_float4(bx[0], bx[1], bx[2], bx[3]);
@@ -1040,7 +1046,8 @@ __global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(cons
     }
   }
   cp_async_wait_all();
-  if (publish_partials(part, blockIdx.x, acc_rz, acc_E, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+  if (publish_partials(part, blockIdx.x, f2x2_fold(acc_rz), f2x2_fold(acc_E), &s->counter,
+                       pr.chunk_end - pr.chunk_begin)) {
     double rz, E;
     gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, rz, E);
     if (threadIdx.x == 0) {
@@ -1556,7 +1563,7 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __
   }
   src[4] = update ? pr.m : nullptr;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  F2 acc = f2_zero();
+  F2x2 acc = f2x2_zero();
   int tc = tiles[ch.begin];
   int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
   tile_issue<NRAW_PA, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
@@ -1637,15 +1644,13 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __
         const float2 a = mul2(lo2(fo), fma2(dA, lo2(O[k]), qA[k]));
         const float2 b = mul2(hi2(fo), fma2(dB, hi2(O[k]), qB[k]));
         *reinterpret_cast<float4*>(pr.q + k * pl + i) = swz4(cat4(a, b));
-        f2_add_prod(acc, O[k].x, a.x);
-        f2_add_prod(acc, O[k].y, a.y);
-        f2_add_prod(acc, O[k].z, b.x);
-        f2_add_prod(acc, O[k].w, b.y);
+        f2x2_add_prod(acc, lo2(O[k]), a);
+        f2x2_add_prod(acc, hi2(O[k]), b);
       }
     }
   }
   cp_async_wait_all();
-  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
+  if (publish_partials(part, blockIdx.x, f2x2_fold(acc), f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double pq, unused;
     gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, pq, unused);
     if (threadIdx.x == 0) {
@@ -1686,7 +1691,7 @@ __global__ void __launch_bounds__(NT, POIS_INIT_WIDE_MINB) k_poisson_init_wide(c
     src[4 + k] = pr.c + k * pl;
   }
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  F2 acc_rz = f2_zero(), acc_E = f2_zero();
+  F2x2 acc_rz = f2x2_zero(), acc_E = f2x2_zero();
   int tc = tiles[ch.begin];
   int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
   tile_issue<NRAW_PI, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
@@ -1754,20 +1759,17 @@ __global__ void __launch_bounds__(NT, POIS_INIT_WIDE_MINB) k_poisson_init_wide(c
         *reinterpret_cast<float4*>(pr.r + k * pl + i) = b;
         *reinterpret_cast<float4*>(pr.d + k * pl + i) = zero;
         if (pr.jtf_out) *reinterpret_cast<float4*>(pr.jtf_out + k * pl + i) = g;
-        f2_add_prod(acc_rz, b.x, __fmul_rn(mv.x, b.x));
-        f2_add_prod(acc_rz, b.y, __fmul_rn(mv.y, b.y));
-        f2_add_prod(acc_rz, b.z, __fmul_rn(mv.z, b.z));
-        f2_add_prod(acc_rz, b.w, __fmul_rn(mv.w, b.w));
+        f2x2_add_prod(acc_rz, lo2(b), pk_mul(lo2(mv), lo2(b)));
+        f2x2_add_prod(acc_rz, hi2(b), pk_mul(hi2(mv), hi2(b)));
       }
       const float2 ea = mul2(lo2(fo), eA), eb = mul2(hi2(fo), eB);
-      f2_add(acc_E, ea.x);
-      f2_add(acc_E, ea.y);
-      f2_add(acc_E, eb.x);
-      f2_add(acc_E, eb.y);
+      f2x2_add(acc_E, ea);
+      f2x2_add(acc_E, eb);
     }
   }
   cp_async_wait_all();
-  if (publish_partials(part, blockIdx.x, acc_rz, acc_E, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+  if (publish_partials(part, blockIdx.x, f2x2_fold(acc_rz), f2x2_fold(acc_E), &s->counter,
+                       pr.chunk_end - pr.chunk_begin)) {
     double rz, E;
     gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, rz, E);
     if (threadIdx.x == 0) {
@@ -1882,7 +1884,7 @@ __device__ __forceinline__ void update_body(const Chunk& ch, const GridProb& pr,
   const float4* __restrict__ m4 = reinterpret_cast<const float4*>(pr.m);
   float4* __restrict__ d4 = reinterpret_cast<float4*>(pr.d);
   float4* __restrict__ r4 = reinterpret_cast<float4*>(pr.r);
-  F2 acc = f2_zero();
+  F2x2 acc = f2x2_zero();
   const int qrow = pr.tw / 4;        // float4 quads per tile row
   const int QPT = qrow * TH;         // float4 quads per tile
   const int nq = (ch.end - ch.begin) * QPT;
@@ -1914,15 +1916,13 @@ __device__ __forceinline__ void update_body(const Chunk& ch, const GridProb& pr,
       dv[c].z = __fmaf_rn(alpha, pv[c].z, dv[c].z); dv[c].w = __fmaf_rn(alpha, pv[c].w, dv[c].w);
       rv[c].x = __fmaf_rn(-alpha, qv[c].x, rv[c].x); rv[c].y = __fmaf_rn(-alpha, qv[c].y, rv[c].y);
       rv[c].z = __fmaf_rn(-alpha, qv[c].z, rv[c].z); rv[c].w = __fmaf_rn(-alpha, qv[c].w, rv[c].w);
-      f2_add_prod(acc, rv[c].x, __fmul_rn(m.x, rv[c].x));
-      f2_add_prod(acc, rv[c].y, __fmul_rn(m.y, rv[c].y));
-      f2_add_prod(acc, rv[c].z, __fmul_rn(m.z, rv[c].z));
-      f2_add_prod(acc, rv[c].w, __fmul_rn(m.w, rv[c].w));
+      f2x2_add_prod(acc, lo2(rv[c]), pk_mul(lo2(m), lo2(rv[c])));
+      f2x2_add_prod(acc, hi2(rv[c]), pk_mul(hi2(m), hi2(rv[c])));
       d4[c * pl4 + j] = dv[c];
       r4[c * pl4 + j] = rv[c];
     }
   }
-  if (publish_partials(part, blockIdx.x, acc, f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
+  if (publish_partials(part, blockIdx.x, f2x2_fold(acc), f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double rz, unused;
     gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, rz, unused);
     if (threadIdx.x == 0) {

@@ -299,6 +299,46 @@ __device__ __forceinline__ void f2_add_f2(F2& a, F2 b) {
 
 __device__ __forceinline__ double f2_to_double(F2 a) { return (double)a.hi + (double)a.lo; }
 
+// Two compensated pairs side by side (lanes x and y), advanced by the packed
+// float32 pair instructions of this architecture: one instruction serves both
+// lanes, and each lane runs exactly the scalar F2 arithmetic above.
+struct F2x2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 pk_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pk_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pk_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ F2x2 f2x2_zero() {
+  return F2x2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+}
+__device__ __forceinline__ void f2x2_add(F2x2& a, float2 x) {
+  const float2 s = pk_add(a.hi, x);
+  const float2 z = pk_sub(s, a.hi);
+  const float2 e = pk_add(pk_sub(a.hi, pk_sub(s, z)), pk_sub(x, z));
+  a.hi = s;
+  a.lo = pk_add(a.lo, e);
+}
+__device__ __forceinline__ void f2x2_add_prod(F2x2& a, float2 x, float2 y) {
+  const float2 p = pk_mul(x, y);
+  const float2 e = pk_fma(x, y, make_float2(-p.x, -p.y));
+  f2x2_add(a, p);
+  a.lo = pk_add(a.lo, e);
+}
+// the two lanes combined into one pair
+__device__ __forceinline__ F2 f2x2_fold(const F2x2& a) {
+  F2 r{a.hi.x, a.lo.x};
+  f2_add_f2(r, F2{a.hi.y, a.lo.y});
+  return r;
+}
+
 // Sum of a pair over the warp (fixed shuffle order); valid in lane 0.
 __device__ __forceinline__ F2 warp_sum_f2(F2 v) {
 #pragma unroll
