@@ -679,3 +679,34 @@ def test_autotuned_configurations_keep_results(api):
     with pytest.raises(api.OptError):
         g.set_apply_form(2)
     g.close()
+
+
+@pytest.mark.parametrize("case", ["warp128", "warp32", "poisson", "mesh_gather", "mesh_tiled", "volume", "embedded"])
+def test_dot_products_carry_float64_accuracy(api, case):
+    """p.q from the applyJTJ pass (the scalar behind alpha) equals the float64
+    dot product of the float32 vectors p and q the pass returns, to 1e-9
+    relative: the compensated (Dot2) accumulation loses essentially nothing,
+    where a float32 sum over ~1e6 terms would be off by ~1e-6."""
+    import torch
+    if case.startswith("warp"):
+        prob = perturbed(synth.warp_problem(520, 300, 40, seed=181), 0.3, 2)
+        gp = api.Problem(prob, tile_w=128 if case == "warp128" else 32)
+    elif case == "poisson":
+        prob = synth.poisson_problem(600, 400, seed=182)
+        gp = api.Problem(prob)
+    elif case == "volume":
+        prob = synth.volume_problem(40, 30, 20, 50, seed=184)
+        gp = api.Problem(prob)
+    elif case == "embedded":
+        prob = synth.embedded_problem(5, seed=185, x0_noise=0.05)
+        gp = api.Problem(prob)
+    else:
+        prob = make_mesh(5, 0.1, seed=183)
+        gp = api.Problem(prob)
+        gp.set_apply_form(1 if case == "mesh_tiled" else 0)
+    p = random_direction(prob, 11)
+    for lam in (0.0, 0.25):
+        q, pq = gp.apply_jtj(torch.as_tensor(p, device="cuda"), lam)
+        exact = float(np.dot(p.astype(np.float64), q.cpu().numpy().reshape(-1).astype(np.float64)))
+        assert relE(pq, exact) <= 1e-9, (case, lam, pq, exact)
+    gp.close()
