@@ -45,12 +45,12 @@ MUTATIONS = [
     (E, "                vals.append(-sw * v[c])", "                vals.append(sw * v[c])"),
     (E, "Rv = np.einsum('rce,ce->re', Rm[:, :, a], v)", "Rv = np.einsum('rce,re->ce', Rm[:, :, a], v)"),
     # PCG / GN / LM (Sec. 4)
-    (S, "        beta = rho_new / rho", "        beta = rho / rho_new"),
-    (S, "        z = Minv * r", "        z = r"),
-    (S, "        x = x + d", "        x = x - d"),
+    (S, "        beta = float(rd(rho_new / rho))", "        beta = float(rd(rho / rho_new))"),
+    (S, "        z = rd(Minv * r)", "        z = rd(r)"),
+    (S, "        x = rd(x + d)", "        x = rd(x - d)"),
     (S, "lam = lam * max(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3)",
         "lam = lam * min(1.0 / 3.0, 1.0 - (2.0 * rho - 1.0) ** 3)"),
-    (S, "        r = r - alpha * q", "        r = r - alpha * p"),
+    (S, "        r = rd(r - alpha * q)", "        r = rd(r - alpha * p)"),
     (S, "pred = E - float(Fl @ Fl)", "pred = E + float(Fl @ Fl)"),
     (S, "        q = q + lam * Dc * p", "        q = q + lam * p"),
 ]
