@@ -658,10 +658,12 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   CKS(dalloc(q, &q->x, nx * pl));
   CKS(dalloc(q, &dc, nm * pl));
   // one slab for every plane the PCG launches touch, in the order r, M^-1,
-  // p (two), q, delta, cos / sin, constants, mask (planes are multiples of
-  // 32 floats, so every plane stays 128-byte aligned)
+  // p (two), q, delta, cos / sin, constants, mask, degree bytes (planes are
+  // multiples of 32 floats, so every plane stays 128-byte aligned)
   const bool has_csn = warp && tw == 128;
-  const size_t nslab = (size_t)(nx + nm + 2 * nx + nx + nx + (has_csn ? 2 : 0) + nc) * pl + (d->mask ? pl / 4 : 0);
+  const bool has_sdeg = !warp && tw == 128;
+  const size_t nslab = (size_t)(nx + nm + 2 * nx + nx + nx + (has_csn ? 2 : 0) + nc) * pl + (d->mask ? pl / 4 : 0) +
+                       (has_sdeg ? pl / 4 : 0);
   float* slab = nullptr;
   CKS(dalloc(q, &slab, nslab));
   float* cur = slab;
@@ -674,11 +676,30 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   float* csn = has_csn ? take(2 * pl) : nullptr;
   c = take(nc * pl);
   if (d->mask) dmask = reinterpret_cast<uint8_t*>(take(pl / 4));
+  uint8_t* dsdeg = has_sdeg ? reinterpret_cast<uint8_t*>(take(pl / 4)) : nullptr;
   if (has_csn) {
     CKS(dalloc(q, &q->d_gbar, 1));
     q->coop_cap = grid_coop_capacity(d->mask != nullptr);
   }
   if (d->mask) CK(cudaMemcpy2D(dmask, P, d->mask, W, W, H, cudaMemcpyDeviceToDevice));
+  if (has_sdeg) {
+    launch_pois_sdeg(W, H, P, dmask, dsdeg, nullptr);
+    CK(cudaGetLastError());
+  }
+  // Poisson, 128-pixel tiles with fixed pixels: the quads holding a free
+  // pixel (one word per row and tile column, bit l for the quad at
+  // 128 tx + 4 l); the vector update skips the others
+  unsigned int* dlive = nullptr;
+  if (has_sdeg && !mask.empty()) {
+    std::vector<unsigned int> lv((size_t)H * ntx, 0u);
+    for (int y = 0; y < H; ++y) {
+      const uint8_t* mr = mask.data() + (size_t)y * W;
+      for (int x = 0; x < W; ++x)
+        if (mr[x] == 0) lv[(size_t)y * ntx + x / 128] |= 1u << ((x % 128) / 4);
+    }
+    CKS(dalloc(q, &dlive, lv.size()));
+    CKS(upload(dlive, lv));
+  }
   for (int k = 0; k < nc; ++k)
     CK(cudaMemcpy2D(c + k * pl, (size_t)P * 4, d->consts[k], (size_t)W * 4, (size_t)W * 4, H,
                     cudaMemcpyDeviceToDevice));
@@ -717,7 +738,8 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   g.s_f = std::sqrt(g.w_fit);
   g.use_precond = 1;
   g.lm = 0;
-  g.x = q->x; g.c = c; g.mask = dmask;
+  g.x = q->x; g.c = c; g.mask = dmask; g.sdeg = dsdeg;
+  g.live = dlive;
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
   g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;
   g.jtf_out = nullptr; g.diag_out = nullptr;

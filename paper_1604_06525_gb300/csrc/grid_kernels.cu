@@ -62,9 +62,9 @@ __global__ void __launch_bounds__(NT) k_warp_init(const GridProb* __restrict__ p
                                                   const int* __restrict__ tiles,
                                                   double* __restrict__ part, int k_outer,
                                                   float dmin, float dmax) {
-  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   Scalars* s = pr.s;
   if (s->done) return;
   __shared__ WarpStage st;
@@ -270,9 +270,9 @@ __global__ void __launch_bounds__(NT, 3) k_warp_apply(const GridProb* __restrict
                                                       double* __restrict__ part,
                                                       const float* __restrict__ p_in_override,
                                                       int par, int update) {
-  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
   __shared__ WarpApplyStage st;
@@ -425,13 +425,15 @@ struct WidePlanes {
 // aligned quad holding column -1 (x0-4 .. x0-1, staged at 0..3) or column
 // 128 (x0+128 .. x0+131, staged at 132..135); x0 is a multiple of 128, so
 // both quads lie inside the pitched row when valid.  Rows / columns outside
-// the grid are zero-filled.  src[k] == nullptr skips plane k.  The mask bytes
-// of the own / halo rows land at mk[row][16 + k], those of the halo columns
+// the grid are zero-filled.  src[k] == nullptr skips plane k.  The bytes of
+// the byte plane (mask or degree plane; skipped unless MASK) of the own /
+// halo rows land at mk[row][16 + k], those of the halo columns
 // as the aligned 4-byte words around them (column -1 at mk[row][15], column
 // 128 at mk[row][144]).
 template <int NR, bool MASK>
 __device__ __forceinline__ void tile_issue(float (*raw)[HH][SP], unsigned char (*mk)[SPB],
-                                           const float* const* src, const GridProb& pr, int x0, int y0, int tid) {
+                                           const float* const* src, const uint8_t* __restrict__ bytes,
+                                           const GridProb& pr, int x0, int y0, int tid) {
   const int lane = tid & 31, ty = tid >> 5;
   const int gx = x0 + 4 * lane;
   {
@@ -441,7 +443,7 @@ __device__ __forceinline__ void tile_issue(float (*raw)[HH][SP], unsigned char (
 #pragma unroll
     for (int k = 0; k < NR; ++k)
       if (src[k]) cp_async16(&raw[k][ty + 1][4 + 4 * lane], src[k] + i, ok);
-    if (MASK) cp_async4(&mk[ty + 1][16 + 4 * lane], pr.mask + i, ok);
+    if (MASK) cp_async4(&mk[ty + 1][16 + 4 * lane], bytes + i, ok);
   }
   if (tid < 64) {
     const int row = tid < 32 ? 0 : HH - 1;
@@ -451,7 +453,7 @@ __device__ __forceinline__ void tile_issue(float (*raw)[HH][SP], unsigned char (
 #pragma unroll
     for (int k = 0; k < NR; ++k)
       if (src[k]) cp_async16(&raw[k][row][4 + 4 * lane], src[k] + i, ok);
-    if (MASK) cp_async4(&mk[row][16 + 4 * lane], pr.mask + i, ok);
+    if (MASK) cp_async4(&mk[row][16 + 4 * lane], bytes + i, ok);
   } else if (tid < 64 + 2 * TH) {
     const int h = tid - 64;
     const int row = 1 + (h % TH), side = h / TH;
@@ -462,7 +464,7 @@ __device__ __forceinline__ void tile_issue(float (*raw)[HH][SP], unsigned char (
 #pragma unroll
     for (int k = 0; k < NR; ++k)
       if (src[k]) cp_async16(&raw[k][row][col], src[k] + i, ok);
-    if (MASK) cp_async4(&mk[row][side ? 16 + W4 : 12], pr.mask + i, ok);
+    if (MASK) cp_async4(&mk[row][side ? 16 + W4 : 12], bytes + i, ok);
   }
   cp_async_commit();
 }
@@ -475,7 +477,7 @@ __device__ __forceinline__ unsigned char halo_mask(const unsigned char (*mk)[SPB
 template <bool MASK>
 __device__ __forceinline__ void wide_issue(WideSmem& sm, const WidePlanes& pp, const GridProb& pr, int x0, int y0,
                                            int tid) {
-  tile_issue<NRAW, MASK>(sm.raw, sm.mk, pp.src, pr, x0, y0, tid);
+  tile_issue<NRAW, MASK>(sm.raw, sm.mk, pp.src, pr.mask, pr, x0, y0, tid);
 }
 
 // Packed float32 pairs (one instruction for two lanes of a float2).  All are
@@ -769,11 +771,11 @@ __global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __res
                                                            double* __restrict__ part,
                                                            const float* __restrict__ p_in_override,
                                                            int par, int update) {
-  pdl_begin();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   WideSmem& sm = *reinterpret_cast<WideSmem*>(dyn_smem);
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   apply_wide_body<MASK>(sm, ch, pr, tiles, part, p_in_override, par, update);
 }
 
@@ -805,7 +807,7 @@ struct InitPlanes {
 template <bool MASK>
 __device__ __forceinline__ void init_issue(InitSmem& sm, const InitPlanes& pp, const GridProb& pr, int x0, int y0,
                                            int tid) {
-  tile_issue<NRAW_I, MASK>(sm.raw, sm.mk, pp.src, pr, x0, y0, tid);
+  tile_issue<NRAW_I, MASK>(sm.raw, sm.mk, pp.src, pr.mask, pr, x0, y0, tid);
 }
 
 // Phase 2 for one staged quad: cos / sin of theta, copied values, validity,
@@ -875,11 +877,11 @@ __global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(cons
                                                           const int* __restrict__ tiles,
                                                           double* __restrict__ part, int k_outer,
                                                           float dmin, float dmax) {
-  pdl_begin();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   InitSmem& sm = *reinterpret_cast<InitSmem*>(dyn_smem);
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   Scalars* s = pr.s;
   if (s->done) return;
   const int pl = (int)pr.plane;
@@ -1067,9 +1069,9 @@ __global__ void __launch_bounds__(NT) k_warp_energy(const GridProb* __restrict__
                                                     const int* __restrict__ tiles,
                                                     double* __restrict__ part, int mode,
                                                     int hist_idx) {
-  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   Scalars* s = pr.s;
   if (mode == 1 && s->done) return;
   __shared__ WarpStage st;
@@ -1189,9 +1191,9 @@ __global__ void __launch_bounds__(NT) k_poisson_init(const GridProb* __restrict_
                                                      const int* __restrict__ tiles,
                                                      double* __restrict__ part, int k_outer,
                                                      float dmin, float dmax) {
-  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   Scalars* s = pr.s;
   if (s->done) return;
   __shared__ PoissonStage st;
@@ -1332,9 +1334,9 @@ __global__ void __launch_bounds__(NT, 3) k_poisson_apply(const GridProb* __restr
                                                          double* __restrict__ part,
                                                          const float* __restrict__ p_in_override,
                                                          int par, int update) {
-  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
   __shared__ PoisApplyStage st;
@@ -1410,246 +1412,242 @@ __global__ void __launch_bounds__(NT, 3) k_poisson_apply(const GridProb* __restr
 }
 
 // ---------------------------------------------------------------------------
-// Wide-tile Poisson kernels (tw = 128), staged like the wide warp apply.
+// Wide-tile Poisson kernels (tw = 128).
 // Per channel the J^T J row of a free pixel i is q_i = sum_j w_j (p_i - p_j)
 // with w_j = 2 for a free neighbour (own + incoming residual), 1 for a fixed
 // one (own residual only; p_j = 0 there) and 0 outside the grid, i.e.
 // q_i = S_i p_i - sum_j w_j p_j with S_i = sum_j w_j = diag(J^T J)_i.  With
 // Y = X - T every residual is r_(i,j) = Y_i - Y_j, so PCGInit is the same
 // stencil on Y: J^T F_i = S_i Y_i - sum_j w_j Y_j, E += sum_(j in grid)
-// (Y_i - Y_j)^2 over free i.  The staged weight plane holds w (0 / 1 / 2).
+// (Y_i - Y_j)^2 over free i.  Quads are held swizzled (pixels 0 2 1 3) so
+// that the float2 packs {0, 2} and {1, 3} have their left / right
+// neighbours in one register pair.
 // ---------------------------------------------------------------------------
 constexpr int NRAW_PA = 9;       // r0..r3, M^-1, p_old0..p_old3
 constexpr int NRAW_PI = 8;       // X0..X3, T0..T3
-constexpr int NSTG_P = 5;        // 4 channels + weight, quads stored as pixels 0 2 1 3
 
+// Both wide Poisson kernels keep two tiles in shared memory: while a block
+// computes tile t from its raw planes, the copies of tile t + 1 land in the
+// other slot (two blocks per SM).  Nothing is staged in between: every thread
+// forms the direction (apply) or Y = X - T (PCGInit) of its own quad and of
+// the quads above and below it straight from the raw planes, and takes the
+// left / right neighbours by warp shuffles (lanes 0 / 31 from the halo
+// columns).  Instead of the mask they read the degree plane (one byte per
+// pixel, see k_pois_sdeg): S_i + 1 on a free pixel i, S_i = diag(J^T J)_i,
+// and 0 on fixed pixels and the row padding.
+constexpr int PST = 2;
 struct PoisWideSmem {
-  float raw[NRAW_PA][HH][SP];
-  float stg[NSTG_P][HH][SP];
-  unsigned char mk[HH][SPB];
+  float raw[PST][NRAW_PA][HH][SP];
+  unsigned char mk[PST][HH][SPB];
 };
-// PCGInit stages one raw plane fewer (X0..X3, T0..T3)
 struct PoisInitSmem {
-  float raw[NRAW_PI][HH][SP];
-  float stg[NSTG_P][HH][SP];
-  unsigned char mk[HH][SPB];
+  float raw[PST][NRAW_PI][HH][SP];
+  unsigned char mk[PST][HH][SPB];
 };
 
-// weight of the staged pixel (gx, gy): 0 outside the grid, 1 fixed, 2 free
-template <bool MASK, class S>
-__device__ __forceinline__ float4 pois_weights(const S& sm, int row, int lane, const GridProb& pr,
-                                               int gx, int gy) {
-  float w[4] = {0.f, 0.f, 0.f, 0.f};
-  if (gy >= 0 && gy < pr.H) {
-    const unsigned int m4 = MASK ? *reinterpret_cast<const unsigned int*>(&sm.mk[row][16 + 4 * lane]) : 0u;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (gx + k < pr.W) w[k] = (!MASK || ((m4 >> (8 * k)) & 0xffu) == 0u) ? 2.f : 1.f;
-  }
-  return make_float4(w[0], w[1], w[2], w[3]);
+// the four degree bytes of the staged quad (row, lane)
+__device__ __forceinline__ unsigned int pois_deg4(const unsigned char (*mk)[SPB], int row, int lane) {
+  return *reinterpret_cast<const unsigned int*>(&mk[row][16 + 4 * lane]);
 }
-
+// degree byte of a halo column (side 0: column -1, side 1: column 128)
+__device__ __forceinline__ unsigned int pois_deg_halo(const unsigned char (*mk)[SPB], int row, int side) {
+  return halo_mask(mk, row, side);
+}
+// neighbour weight from its degree byte and whether it lies in the grid: 2
+// free, 1 fixed, 0 outside
+__device__ __forceinline__ float pois_w(unsigned int deg, bool inb) {
+  return inb ? (deg != 0u ? 2.f : 1.f) : 0.f;
+}
+// weights of the staged quad (row, lane) at (gx, gy), plain order
+__device__ __forceinline__ float4 pois_weights(const unsigned char (*mk)[SPB], int row, int lane, const GridProb& pr,
+                                               int gx, int gy) {
+  const unsigned int d4 = pois_deg4(mk, row, lane);
+  const bool iny = gy >= 0 && gy < pr.H;
+  return make_float4(pois_w(d4 & 0xffu, iny && gx < pr.W), pois_w((d4 >> 8) & 0xffu, iny && gx + 1 < pr.W),
+                     pois_w((d4 >> 16) & 0xffu, iny && gx + 2 < pr.W), pois_w(d4 >> 24, iny && gx + 3 < pr.W));
+}
 __device__ __forceinline__ float4 free01(const float4& w) {
   return make_float4(w.x > 1.5f ? 1.f : 0.f, w.y > 1.5f ? 1.f : 0.f, w.z > 1.5f ? 1.f : 0.f, w.w > 1.5f ? 1.f : 0.f);
 }
+// own free flags (1 / 0) and S of the staged quad from its degree bytes, plain order
+__device__ __forceinline__ void pois_own(unsigned int d4, float4& fo, float4& S) {
+  const float b0 = (float)(d4 & 0xffu), b1 = (float)((d4 >> 8) & 0xffu);
+  const float b2 = (float)((d4 >> 16) & 0xffu), b3 = (float)(d4 >> 24);
+  fo = make_float4(b0 > 0.f ? 1.f : 0.f, b1 > 0.f ? 1.f : 0.f, b2 > 0.f ? 1.f : 0.f, b3 > 0.f ? 1.f : 0.f);
+  S = make_float4(fmaxf(b0 - 1.f, 0.f), fmaxf(b1 - 1.f, 0.f), fmaxf(b2 - 1.f, 0.f), fmaxf(b3 - 1.f, 0.f));
+}
+__device__ __forceinline__ float4 keep_if(unsigned int d4, const float4& v) {
+  return make_float4((d4 & 0xffu) ? v.x : 0.f, (d4 & 0xff00u) ? v.y : 0.f, (d4 & 0xff0000u) ? v.z : 0.f,
+                     (d4 & 0xff000000u) ? v.w : 0.f);
+}
 
-// Weighted neighbour sums of one float2 pack for the 4 channels:
-// out_c = S p_c - sum_j w_j p_(j,c), with (w_j, p_j) of the 4 neighbours.
-struct Nb5 {
-  float2 v[NSTG_P];
-};
+// Direction of the PCG step on the staged quad (row, c) of one channel, plain
+// order: p = M^-1 r + beta p_old with the fused vector update, else the given
+// p (raw planes: r0..r3, M^-1, p0..p3).
+template <bool UPD>
+__device__ __forceinline__ float4 pois_dir4(const float (*raw)[HH][SP], int k, int row, int c, const float4& m,
+                                            bool use_beta, float2 beta2) {
+  if (!UPD) return lds4(&raw[5 + k][row][c]);
+  float4 v = mul4p(m, lds4(&raw[k][row][c]));
+  if (use_beta) v = fma4p(beta2, lds4(&raw[5 + k][row][c]), v);
+  return v;
+}
+template <bool UPD>
+__device__ __forceinline__ float pois_dir1(const float (*raw)[HH][SP], int k, int row, int col, bool use_beta,
+                                           float beta) {
+  if (!UPD) return raw[5 + k][row][col];
+  float v = raw[4][row][col] * raw[k][row][col];
+  if (use_beta) v = fmaf(beta, raw[5 + k][row][col], v);
+  return v;
+}
 
-// Phase 3 of the wide Poisson kernels: the stencil on the own quad of the
-// warp's row.  O: own staged values (swizzled), lane 0 / 31 take the halo
-// columns.  Returns, per pack (A = pixels {0, 2}, B = {1, 3}) and channel,
-// S v_i - sum_j w_j v_j, and (init only) the own-residual energy sum.
-template <bool ENERGY, class S>
-__device__ __forceinline__ void pois_stencil(const S& sm, int ty, int lane, const float4 (&O)[NSTG_P],
-                                             float2 (&outA)[4], float2 (&outB)[4], float2& SA, float2& SB,
-                                             float2& eA, float2& eB) {
+// Directions of one staged quad, swizzled (pixels 0 2 1 3).  With the fused
+// update they are zero off the free pixels by construction (r and p_old vanish
+// there: PCGInit writes r = 0 on every pixel that is not free, the vector
+// update keeps it, and the planes start zeroed); a given p (the J^T J p hook)
+// is zeroed there from the degree bytes.
+template <bool UPD>
+__device__ __forceinline__ void pois_dir_quad(const float (*raw)[HH][SP], const unsigned char (*mk)[SPB], int row,
+                                              int lane, bool use_beta, float2 beta2, float4 (&out)[4]) {
   const int c = 4 + 4 * lane;
-  float L[NSTG_P], R[NSTG_P];
+  const float4 m = UPD ? lds4(&raw[4][row][c]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const unsigned int d4 = UPD ? 0u : pois_deg4(mk, row, lane);
 #pragma unroll
-  for (int k = 0; k < NSTG_P; ++k) {
-    L[k] = __shfl_up_sync(0xffffffffu, O[k].w, 1);
-    R[k] = __shfl_down_sync(0xffffffffu, O[k].x, 1);
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NSTG_P; ++k) L[k] = sm.stg[k][ty + 1][3];
-  }
-  if (lane == 31) {
-#pragma unroll
-    for (int k = 0; k < NSTG_P; ++k) R[k] = sm.stg[k][ty + 1][4 + W4];
-  }
-  float4 U[NSTG_P], D[NSTG_P];
-#pragma unroll
-  for (int k = 0; k < NSTG_P; ++k) {
-    U[k] = lds4(&sm.stg[k][ty][c]);
-    D[k] = lds4(&sm.stg[k][ty + 2][c]);
-  }
-  // neighbour packs: A left {-1, 1}, right {1, 3}; B left {0, 2}, right {2, 4}
-  Nb5 aL, aR, bL, bR, aU, aD, bU, bD;
-#pragma unroll
-  for (int k = 0; k < NSTG_P; ++k) {
-    aL.v[k] = make_float2(L[k], O[k].z);
-    aR.v[k] = hi2(O[k]);
-    bL.v[k] = lo2(O[k]);
-    bR.v[k] = make_float2(O[k].y, R[k]);
-    aU.v[k] = lo2(U[k]);
-    aD.v[k] = lo2(D[k]);
-    bU.v[k] = hi2(U[k]);
-    bD.v[k] = hi2(D[k]);
-  }
-  SA = add2(add2(aL.v[4], aR.v[4]), add2(aU.v[4], aD.v[4]));
-  SB = add2(add2(bL.v[4], bR.v[4]), add2(bU.v[4], bD.v[4]));
-#pragma unroll
-  for (int ch = 0; ch < 4; ++ch) {
-    const float2 nA = fma2(aL.v[4], aL.v[ch], fma2(aR.v[4], aR.v[ch], fma2(aU.v[4], aU.v[ch], mul2(aD.v[4], aD.v[ch]))));
-    const float2 nB = fma2(bL.v[4], bL.v[ch], fma2(bR.v[4], bR.v[ch], fma2(bU.v[4], bU.v[ch], mul2(bD.v[4], bD.v[ch]))));
-    outA[ch] = sub2(mul2(SA, lo2(O[ch])), nA);
-    outB[ch] = sub2(mul2(SB, hi2(O[ch])), nB);
-  }
-  if (ENERGY) {
-    // own residuals towards every in-grid neighbour (weight > 0)
-    eA = make_float2(0.f, 0.f);
-    eB = make_float2(0.f, 0.f);
-    const Nb5* na[4] = {&aL, &aR, &aU, &aD};
-    const Nb5* nb[4] = {&bL, &bR, &bU, &bD};
-#pragma unroll
-    for (int d = 0; d < 4; ++d) {
-      const float2 ma = make_float2(na[d]->v[4].x > 0.5f ? 1.f : 0.f, na[d]->v[4].y > 0.5f ? 1.f : 0.f);
-      const float2 mb = make_float2(nb[d]->v[4].x > 0.5f ? 1.f : 0.f, nb[d]->v[4].y > 0.5f ? 1.f : 0.f);
-      float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int ch = 0; ch < 4; ++ch) {
-        const float2 da = sub2(lo2(O[ch]), na[d]->v[ch]);
-        const float2 db = sub2(hi2(O[ch]), nb[d]->v[ch]);
-        sa = fma2(da, da, sa);
-        sb = fma2(db, db, sb);
-      }
-      eA = fma2(ma, sa, eA);
-      eB = fma2(mb, sb, eB);
-    }
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = pois_dir4<UPD>(raw, k, row, c, m, use_beta, beta2);
+    out[k] = swz4(UPD ? v : keep_if(d4, v));
   }
 }
 
-template <bool MASK>
+// applyJTJ stencil: with the directions zero off the free pixels, every
+// neighbour term w_j p_j is 2 p_j, so per pack and channel
+// S p_i - 2 (p_L + (p_R + (p_U + p_D))) (the same roundings as the weighted
+// sum: scaling by 2 is exact).  O / U / D swizzled, L / R as in the init.
+__device__ __forceinline__ void pois_core_apply(const float4 (&O)[4], const float4 (&U)[4], const float4 (&D)[4],
+                                                const float (&L)[4], const float (&R)[4], float2 SA, float2 SB,
+                                                float2 (&outA)[4], float2 (&outB)[4]) {
+  const float2 two = make_float2(2.f, 2.f);
+#pragma unroll
+  for (int ch = 0; ch < 4; ++ch) {
+    const float2 nA = add2(make_float2(L[ch], O[ch].z), add2(hi2(O[ch]), add2(lo2(U[ch]), lo2(D[ch]))));
+    const float2 nB = add2(lo2(O[ch]), add2(make_float2(O[ch].y, R[ch]), add2(hi2(U[ch]), hi2(D[ch]))));
+    outA[ch] = sub2(mul2(SA, lo2(O[ch])), mul2(two, nA));
+    outB[ch] = sub2(mul2(SB, hi2(O[ch])), mul2(two, nB));
+  }
+}
+
+// left / right neighbours of the own quad by shuffles (O swizzled: .w is
+// pixel 3, .x pixel 0); lanes 0 / 31 leave theirs for the halo columns
+template <int N>
+__device__ __forceinline__ void pois_side_nbrs(const float4 (&O)[N], float (&L)[N], float (&R)[N]) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    L[k] = __shfl_up_sync(0xffffffffu, O[k].w, 1);
+    R[k] = __shfl_down_sync(0xffffffffu, O[k].x, 1);
+  }
+}
+
+// Issues the copies of one Poisson tile: the raw planes and the degree bytes.
+template <int NR>
+__device__ __forceinline__ void pois_issue(float (*raw)[HH][SP], unsigned char (*mk)[SPB], const float* const* src,
+                                           const GridProb& pr, int tc, int tid) {
+  tile_issue<NR, true>(raw, mk, src, pr.sdeg, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+}
+
+// applyJTJ on the thread's own quad of a staged Poisson tile (slot raw / mk;
+// i: the quad's pixel index): the direction p = M^-1 r + beta p_old (fused
+// update) or the given p on the own quad and its neighbours, q = (J^T J +
+// lambda D) p on the free pixels, p and q stored, p.q accumulated.
+template <bool UPD>
+__device__ __forceinline__ void pois_apply_quad(const float (*raw)[HH][SP], const unsigned char (*mk)[SPB],
+                                                const GridProb& pr, int ty, int lane, long long i,
+                                                bool use_beta, float beta, float2 beta2, float lam,
+                                                float* __restrict__ pout, int pl, F2x2& acc) {
+  float4 O[4], U[4], D[4];
+  float L[4], R[4];
+  pois_dir_quad<UPD>(raw, mk, ty + 1, lane, use_beta, beta2, O);
+  pois_side_nbrs(O, L, R);
+  if (lane == 0) {
+    const bool fr = UPD || pois_deg_halo(mk, ty + 1, 0) != 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) L[k] = fr ? pois_dir1<UPD>(raw, k, ty + 1, 3, use_beta, beta) : 0.f;
+  }
+  if (lane == 31) {
+    const bool fr = UPD || pois_deg_halo(mk, ty + 1, 1) != 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) R[k] = fr ? pois_dir1<UPD>(raw, k, ty + 1, 4 + W4, use_beta, beta) : 0.f;
+  }
+  pois_dir_quad<UPD>(raw, mk, ty, lane, use_beta, beta2, U);
+  pois_dir_quad<UPD>(raw, mk, ty + 2, lane, use_beta, beta2, D);
+  float4 fo, S;
+  pois_own(pois_deg4(mk, ty + 1, lane), fo, S);
+  fo = swz4(fo);
+  S = swz4(S);
+  if (UPD) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) *reinterpret_cast<float4*>(pout + k * pl + i) = swz4(O[k]);
+  }
+  float2 qA[4], qB[4];
+  pois_core_apply(O, U, D, L, R, lo2(S), hi2(S), qA, qB);
+  float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (pr.lm) dd = swz4(ld4(pr.dc + i));
+  const float2 lam2 = make_float2(lam, lam);
+  const float2 dA = mul2(lam2, lo2(dd)), dB = mul2(lam2, hi2(dd));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 a = mul2(lo2(fo), fma2(dA, lo2(O[k]), qA[k]));
+    const float2 b2 = mul2(hi2(fo), fma2(dB, hi2(O[k]), qB[k]));
+    *reinterpret_cast<float4*>(pr.q + k * pl + i) = swz4(cat4(a, b2));
+    f2x2_add_prod(acc, lo2(O[k]), a);
+    f2x2_add_prod(acc, hi2(O[k]), b2);
+  }
+}
+
+template <bool UPD>
 __global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __restrict__ probs,
                                                               const Chunk* __restrict__ chunks,
                                                               const int* __restrict__ tiles,
                                                               double* __restrict__ part,
                                                               const float* __restrict__ p_in_override,
-                                                              int par, int update) {
-  pdl_begin();
+                                                              int par) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   PoisWideSmem& sm = *reinterpret_cast<PoisWideSmem*>(dyn_smem);
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
   const int pl = (int)pr.plane;
   const float beta = s->beta_f;
   const float2 beta2 = make_float2(beta, beta);
-  const int use_beta = beta != 0.0f;
+  const bool use_beta = beta != 0.0f;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const float* __restrict__ pin = p_in_override ? p_in_override : pr.p + (long long)(par & 1) * 4 * pl;
   float* __restrict__ pout = pr.p + (long long)((par + 1) & 1) * 4 * pl;
   const float* src[NRAW_PA];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    src[k] = update ? pr.r + k * pl : nullptr;
-    src[5 + k] = (!update || use_beta) ? pin + k * pl : nullptr;
+    src[k] = UPD ? pr.r + k * pl : nullptr;
+    src[5 + k] = (!UPD || use_beta) ? pin + k * pl : nullptr;
   }
-  src[4] = update ? pr.m : nullptr;
+  src[4] = UPD ? pr.m : nullptr;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   F2x2 acc = f2x2_zero();
-  int tc = tiles[ch.begin];
+  pois_issue<NRAW_PA>(sm.raw[0], sm.mk[0], src, pr, tiles[ch.begin], tid);
   int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
-  tile_issue<NRAW_PA, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
-  // phase 2 of one staged quad: p = (M^-1 r + beta p_old) on free pixels, 0
-  // elsewhere; weights
-  auto stage = [&](int row, int gx, int gy) {
-    const int c = 4 + 4 * lane;
-    const float4 w = pois_weights<MASK>(sm, row, lane, pr, gx, gy);
-    const float4 f = free01(w);
-    const float4 m = update ? lds4(&sm.raw[4][row][c]) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      float4 v;
-      if (update) {
-        v = mul4p(m, lds4(&sm.raw[k][row][c]));
-        if (use_beta) v = fma4p(beta2, lds4(&sm.raw[5 + k][row][c]), v);
-      } else {
-        v = lds4(&sm.raw[5 + k][row][c]);
-      }
-      sts4(&sm.stg[k][row][c], swz4(mul4p(f, v)));
-    }
-    sts4(&sm.stg[4][row][c], swz4(w));
-  };
-  for (int t = ch.begin; t < ch.end; ++t) {
-    const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
-    const int gx = x0 + 4 * lane, gy = y0 + ty;
+  for (int t = ch.begin, b = 0; t < ch.end; ++t, b ^= 1) {
+    const int tc = tiles[t];
+    const int gx = tile_x0(tc, W4) + 4 * lane, gy = tile_y0(tc) + ty;
     cp_async_wait_all();
-    __syncthreads();
-    stage(ty + 1, gx, gy);
-    if (tid < 64) {
-      const int row = tid < 32 ? 0 : HH - 1;
-      stage(row, gx, y0 - 1 + row);
-    } else if (tid < 64 + 2 * TH) {
-      const int h = tid - 64;
-      const int row = 1 + (h % TH), side = h / TH;
-      const int col = side ? 4 + W4 : 3;
-      const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
-      const bool inb = hy < pr.H && hx >= 0 && hx < pr.W;
-      const bool fr = inb && (!MASK || halo_mask(sm.mk, row, side) == 0);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        float v;
-        if (update) {
-          v = sm.raw[4][row][col] * sm.raw[k][row][col];
-          if (use_beta) v = fmaf(beta, sm.raw[5 + k][row][col], v);
-        } else {
-          v = sm.raw[5 + k][row][col];
-        }
-        sm.stg[k][row][col] = fr ? v : 0.f;
-      }
-      sm.stg[4][row][col] = inb ? (fr ? 2.f : 1.f) : 0.f;
-    }
-    __syncthreads();
+    __syncthreads();    // tile t landed; every thread is done with the other slot (tile t - 1)
     if (t + 1 < ch.end) {
-      tc = tn;
-      tile_issue<NRAW_PA, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+      pois_issue<NRAW_PA>(sm.raw[b ^ 1], sm.mk[b ^ 1], src, pr, tn, tid);
       if (t + 2 < ch.end) tn = tiles[t + 2];
     }
-    if (gy < pr.H) {
-      const long long i = (long long)gy * pr.P + gx;
-      const int c = 4 + 4 * lane;
-      float4 O[NSTG_P];
-#pragma unroll
-      for (int k = 0; k < NSTG_P; ++k) O[k] = lds4(&sm.stg[k][ty + 1][c]);
-      if (update) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) *reinterpret_cast<float4*>(pout + k * pl + i) = swz4(O[k]);
-      }
-      float2 qA[4], qB[4], SA, SB, eA, eB;
-      pois_stencil<false>(sm, ty, lane, O, qA, qB, SA, SB, eA, eB);
-      const float4 fo = free01(O[4]);                 // own pixels free (staged order)
-      float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (pr.lm) dd = swz4(ld4(pr.dc + i));
-      const float2 lam2 = make_float2(lam, lam);
-      const float2 dA = mul2(lam2, lo2(dd)), dB = mul2(lam2, hi2(dd));
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float2 a = mul2(lo2(fo), fma2(dA, lo2(O[k]), qA[k]));
-        const float2 b = mul2(hi2(fo), fma2(dB, hi2(O[k]), qB[k]));
-        *reinterpret_cast<float4*>(pr.q + k * pl + i) = swz4(cat4(a, b));
-        f2x2_add_prod(acc, lo2(O[k]), a);
-        f2x2_add_prod(acc, hi2(O[k]), b);
-      }
-    }
+    if (gy < pr.H)
+      pois_apply_quad<UPD>(sm.raw[b], sm.mk[b], pr, ty, lane, (long long)gy * pr.P + gx, use_beta, beta, beta2, lam,
+                           pout, pl, acc);
   }
-  cp_async_wait_all();
   if (publish_partials(part, blockIdx.x, f2x2_fold(acc), f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double pq, unused;
     gather_partials(part, pr.chunk_begin, pr.chunk_end, &s->counter, pq, unused);
@@ -1666,20 +1664,103 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __
   }
 }
 
-template <bool MASK>
-#ifndef POIS_INIT_WIDE_MINB
-#define POIS_INIT_WIDE_MINB 2       // resident blocks per SM the wide Poisson PCGInit is compiled for
-#endif
-__global__ void __launch_bounds__(NT, POIS_INIT_WIDE_MINB) k_poisson_init_wide(const GridProb* __restrict__ probs,
+// PCGInit on the thread's own quad of a staged Poisson tile (slot raw / mk):
+// J^T F, diag(J^T J), M^-1 and the LM diagonal of the free pixels, r = -J^T F
+// and delta = 0 stored, r.z and the energy of the own residuals accumulated.
+__device__ __forceinline__ void pois_init_quad(const float (*raw)[HH][SP], const unsigned char (*mk)[SPB],
+                                               const GridProb& pr, int ty, int lane, int x0, int gx, int gy,
+                                               float lam, float dmin, float dmax, int pl,
+                                               F2x2& acc_rz, F2x2& acc_E) {
+  const int c = 4 + 4 * lane;
+  // neighbour weights (swizzled packs: A = pixels {0, 2}, B = {1, 3})
+  const float4 wO = swz4(pois_weights(mk, ty + 1, lane, pr, gx, gy));
+  const float4 wU = swz4(pois_weights(mk, ty, lane, pr, gx, gy - 1));
+  const float4 wD = swz4(pois_weights(mk, ty + 2, lane, pr, gx, gy + 1));
+  float wL = __shfl_up_sync(0xffffffffu, wO.w, 1), wR = __shfl_down_sync(0xffffffffu, wO.x, 1);
+  if (lane == 0) wL = pois_w(pois_deg_halo(mk, ty + 1, 0), x0 > 0);
+  if (lane == 31) wR = pois_w(pois_deg_halo(mk, ty + 1, 1), x0 + W4 < pr.W);
+  const float2 waL = make_float2(wL, wO.z), waR = hi2(wO), wbL = lo2(wO), wbR = make_float2(wO.y, wR);
+  const float2 waU = lo2(wU), waD = lo2(wD), wbU = hi2(wU), wbD = hi2(wD);
+  const float2 SA = add2(add2(waL, waR), add2(waU, waD));
+  const float2 SB = add2(add2(wbL, wbR), add2(wbU, wbD));
+  const long long i = (long long)gy * pr.P + gx;
+  // own pixels free (staged order): free pixels have a non-zero degree byte
+  const unsigned int d4 = pois_deg4(mk, ty + 1, lane);
+  const float4 fo = swz4(make_float4((d4 & 0xffu) ? 1.f : 0.f, (d4 & 0xff00u) ? 1.f : 0.f,
+                                     (d4 & 0xff0000u) ? 1.f : 0.f, (d4 & 0xff000000u) ? 1.f : 0.f));
+  // diagonal S on free pixels (0 elsewhere), M^-1, LM damping diagonal
+  const float4 dg = swz4(cat4(mul2(lo2(fo), SA), mul2(hi2(fo), SB)));   // plain order
+  float4 mv, dcv;
+  mv.x = minv_entry(dg.x, lam, dmin, dmax, pr.use_precond, &dcv.x);
+  mv.y = minv_entry(dg.y, lam, dmin, dmax, pr.use_precond, &dcv.y);
+  mv.z = minv_entry(dg.z, lam, dmin, dmax, pr.use_precond, &dcv.z);
+  mv.w = minv_entry(dg.w, lam, dmin, dmax, pr.use_precond, &dcv.w);
+  *reinterpret_cast<float4*>(pr.m + i) = mv;
+  if (pr.lm) *reinterpret_cast<float4*>(pr.dc + i) = dcv;
+  if (pr.diag_out) *reinterpret_cast<float4*>(pr.diag_out + i) = dg;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  // per direction (L, R, U, D) and pack: sum over the channels of the own
+  // residuals squared (in-grid neighbours only, applied after the loop)
+  float2 sa[4], sb[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) sa[d] = sb[d] = make_float2(0.f, 0.f);
+  // one channel at a time: J^T F_i = S_i Y_i - sum_j w_j Y_j, with Y = X - T
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 xo = lds4(&raw[k][ty + 1][c]), go = lds4(&raw[4 + k][ty + 1][c]);
+    const float4 O = swz4(cat4(sub2(lo2(xo), lo2(go)), sub2(hi2(xo), hi2(go))));
+    const float4 xu = lds4(&raw[k][ty][c]), gu = lds4(&raw[4 + k][ty][c]);
+    const float4 U = swz4(cat4(sub2(lo2(xu), lo2(gu)), sub2(hi2(xu), hi2(gu))));
+    const float4 xd = lds4(&raw[k][ty + 2][c]), gd = lds4(&raw[4 + k][ty + 2][c]);
+    const float4 D = swz4(cat4(sub2(lo2(xd), lo2(gd)), sub2(hi2(xd), hi2(gd))));
+    float L = __shfl_up_sync(0xffffffffu, O.w, 1), R = __shfl_down_sync(0xffffffffu, O.x, 1);
+    if (lane == 0) L = raw[k][ty + 1][3] - raw[4 + k][ty + 1][3];
+    if (lane == 31) R = raw[k][ty + 1][4 + W4] - raw[4 + k][ty + 1][4 + W4];
+    const float2 aL = make_float2(L, O.z), aR = hi2(O), bL = lo2(O), bR = make_float2(O.y, R);
+    const float2 aU = lo2(U), aD = lo2(D), bU = hi2(U), bD = hi2(D);
+    const float2 nA = fma2(waL, aL, fma2(waR, aR, fma2(waU, aU, mul2(waD, aD))));
+    const float2 nB = fma2(wbL, bL, fma2(wbR, bR, fma2(wbU, bU, mul2(wbD, bD))));
+    const float2 gA = sub2(mul2(SA, lo2(O)), nA), gB = sub2(mul2(SB, hi2(O)), nB);
+    const float4 g = swz4(cat4(mul2(lo2(fo), gA), mul2(hi2(fo), gB)));   // J^T F, plain order
+    const float4 bb = make_float4(-g.x, -g.y, -g.z, -g.w);
+    *reinterpret_cast<float4*>(pr.r + k * pl + i) = bb;
+    *reinterpret_cast<float4*>(pr.d + k * pl + i) = zero;
+    if (pr.jtf_out) *reinterpret_cast<float4*>(pr.jtf_out + k * pl + i) = g;
+    f2x2_add_prod(acc_rz, lo2(bb), pk_mul(lo2(mv), lo2(bb)));
+    f2x2_add_prod(acc_rz, hi2(bb), pk_mul(hi2(mv), hi2(bb)));
+    const float2 na[4] = {aL, aR, aU, aD}, nb[4] = {bL, bR, bU, bD};
+#pragma unroll
+    for (int d = 0; d < 4; ++d) {
+      const float2 da = sub2(lo2(O), na[d]), db = sub2(hi2(O), nb[d]);
+      sa[d] = fma2(da, da, sa[d]);
+      sb[d] = fma2(db, db, sb[d]);
+    }
+  }
+  // own residuals towards every in-grid neighbour (weight > 0)
+  const float2 wa[4] = {waL, waR, waU, waD}, wb[4] = {wbL, wbR, wbU, wbD};
+  float2 eA = make_float2(0.f, 0.f), eB = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const float2 ma = make_float2(wa[d].x > 0.5f ? 1.f : 0.f, wa[d].y > 0.5f ? 1.f : 0.f);
+    const float2 mb = make_float2(wb[d].x > 0.5f ? 1.f : 0.f, wb[d].y > 0.5f ? 1.f : 0.f);
+    eA = fma2(ma, sa[d], eA);
+    eB = fma2(mb, sb[d], eB);
+  }
+  const float2 ea = mul2(lo2(fo), eA), eb = mul2(hi2(fo), eB);
+  f2x2_add(acc_E, ea);
+  f2x2_add(acc_E, eb);
+}
+
+__global__ void __launch_bounds__(NT, 2) k_poisson_init_wide(const GridProb* __restrict__ probs,
                                                              const Chunk* __restrict__ chunks,
                                                              const int* __restrict__ tiles,
                                                              double* __restrict__ part, int k_outer,
                                                              float dmin, float dmax) {
-  pdl_begin();
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   PoisInitSmem& sm = *reinterpret_cast<PoisInitSmem*>(dyn_smem);
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   Scalars* s = pr.s;
   if (s->done) return;
   const int pl = (int)pr.plane;
@@ -1692,82 +1773,20 @@ __global__ void __launch_bounds__(NT, POIS_INIT_WIDE_MINB) k_poisson_init_wide(c
   }
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   F2x2 acc_rz = f2x2_zero(), acc_E = f2x2_zero();
-  int tc = tiles[ch.begin];
+  pois_issue<NRAW_PI>(sm.raw[0], sm.mk[0], src, pr, tiles[ch.begin], tid);
   int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
-  tile_issue<NRAW_PI, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
-  // phase 2: Y = X - T (staged order) and weights
-  auto stage = [&](int row, int gx, int gy) {
-    const int c = 4 + 4 * lane;
-    const float4 w = pois_weights<MASK>(sm, row, lane, pr, gx, gy);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float4 x = lds4(&sm.raw[k][row][c]), g = lds4(&sm.raw[4 + k][row][c]);
-      sts4(&sm.stg[k][row][c], swz4(cat4(sub2(lo2(x), lo2(g)), sub2(hi2(x), hi2(g)))));
-    }
-    sts4(&sm.stg[4][row][c], swz4(w));
-  };
-  for (int t = ch.begin; t < ch.end; ++t) {
+  for (int t = ch.begin, b = 0; t < ch.end; ++t, b ^= 1) {
+    const int tc = tiles[t];
     const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
     const int gx = x0 + 4 * lane, gy = y0 + ty;
     cp_async_wait_all();
-    __syncthreads();
-    stage(ty + 1, gx, gy);
-    if (tid < 64) {
-      const int row = tid < 32 ? 0 : HH - 1;
-      stage(row, gx, y0 - 1 + row);
-    } else if (tid < 64 + 2 * TH) {
-      const int h = tid - 64;
-      const int row = 1 + (h % TH), side = h / TH;
-      const int col = side ? 4 + W4 : 3;
-      const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
-      const bool inb = hy < pr.H && hx >= 0 && hx < pr.W;
-      const bool fr = inb && (!MASK || halo_mask(sm.mk, row, side) == 0);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) sm.stg[k][row][col] = sm.raw[k][row][col] - sm.raw[4 + k][row][col];
-      sm.stg[4][row][col] = inb ? (fr ? 2.f : 1.f) : 0.f;
-    }
-    __syncthreads();
+    __syncthreads();    // tile t landed; every thread is done with the other slot (tile t - 1)
     if (t + 1 < ch.end) {
-      tc = tn;
-      tile_issue<NRAW_PI, MASK>(sm.raw, sm.mk, src, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+      pois_issue<NRAW_PI>(sm.raw[b ^ 1], sm.mk[b ^ 1], src, pr, tn, tid);
       if (t + 2 < ch.end) tn = tiles[t + 2];
     }
-    if (gy < pr.H) {
-      const long long i = (long long)gy * pr.P + gx;
-      const int c = 4 + 4 * lane;
-      float4 O[NSTG_P];
-#pragma unroll
-      for (int k = 0; k < NSTG_P; ++k) O[k] = lds4(&sm.stg[k][ty + 1][c]);
-      float2 gA[4], gB[4], SA, SB, eA, eB;
-      pois_stencil<true>(sm, ty, lane, O, gA, gB, SA, SB, eA, eB);
-      const float4 fo = free01(O[4]);
-      // diagonal S on free pixels (0 elsewhere), M^-1, LM damping diagonal
-      const float4 dg = swz4(cat4(mul2(lo2(fo), SA), mul2(hi2(fo), SB)));   // plain order
-      float4 mv, dcv;
-      mv.x = minv_entry(dg.x, lam, dmin, dmax, pr.use_precond, &dcv.x);
-      mv.y = minv_entry(dg.y, lam, dmin, dmax, pr.use_precond, &dcv.y);
-      mv.z = minv_entry(dg.z, lam, dmin, dmax, pr.use_precond, &dcv.z);
-      mv.w = minv_entry(dg.w, lam, dmin, dmax, pr.use_precond, &dcv.w);
-      *reinterpret_cast<float4*>(pr.m + i) = mv;
-      if (pr.lm) *reinterpret_cast<float4*>(pr.dc + i) = dcv;
-      if (pr.diag_out) *reinterpret_cast<float4*>(pr.diag_out + i) = dg;
-      const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float4 g = swz4(cat4(mul2(lo2(fo), gA[k]), mul2(hi2(fo), gB[k])));   // J^T F, plain order
-        const float4 b = make_float4(-g.x, -g.y, -g.z, -g.w);
-        *reinterpret_cast<float4*>(pr.r + k * pl + i) = b;
-        *reinterpret_cast<float4*>(pr.d + k * pl + i) = zero;
-        if (pr.jtf_out) *reinterpret_cast<float4*>(pr.jtf_out + k * pl + i) = g;
-        f2x2_add_prod(acc_rz, lo2(b), pk_mul(lo2(mv), lo2(b)));
-        f2x2_add_prod(acc_rz, hi2(b), pk_mul(hi2(mv), hi2(b)));
-      }
-      const float2 ea = mul2(lo2(fo), eA), eb = mul2(hi2(fo), eB);
-      f2x2_add(acc_E, ea);
-      f2x2_add(acc_E, eb);
-    }
+    if (gy < pr.H) pois_init_quad(sm.raw[b], sm.mk[b], pr, ty, lane, x0, gx, gy, lam, dmin, dmax, pl, acc_rz, acc_E);
   }
-  cp_async_wait_all();
   if (publish_partials(part, blockIdx.x, f2x2_fold(acc_rz), f2x2_fold(acc_E), &s->counter,
                        pr.chunk_end - pr.chunk_begin)) {
     double rz, E;
@@ -1783,14 +1802,37 @@ __global__ void __launch_bounds__(NT, POIS_INIT_WIDE_MINB) k_poisson_init_wide(c
   }
 }
 
+// Degree plane of a wide Poisson problem: S_i + 1 on a free pixel i, where
+// S_i = diag(J^T J)_i sums 2 per free and 1 per fixed in-grid neighbour
+// (Fig. 27: each free pixel owns one residual per in-grid neighbour, a free
+// neighbour adds its own residual towards i); 0 on fixed pixels and on the
+// row padding.
+__global__ void k_pois_sdeg(int W, int H, int P, const uint8_t* __restrict__ mask, uint8_t* __restrict__ out) {
+  const long long n = (long long)P * H;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(i / P), x = (int)(i % P);
+    unsigned int v = 0;
+    if (x < W && (!mask || mask[i] == 0)) {
+      unsigned int S = 0;
+      const int nx[4] = {x - 1, x + 1, x, x}, ny[4] = {y, y, y - 1, y + 1};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (nx[k] >= 0 && nx[k] < W && ny[k] >= 0 && ny[k] < H)
+          S += (!mask || mask[(long long)ny[k] * P + nx[k]] == 0) ? 2u : 1u;
+      v = S + 1;
+    }
+    out[i] = (uint8_t)v;
+  }
+}
+
 __global__ void __launch_bounds__(NT) k_poisson_energy(const GridProb* __restrict__ probs,
                                                        const Chunk* __restrict__ chunks,
                                                        const int* __restrict__ tiles,
                                                        double* __restrict__ part, int mode,
                                                        int hist_idx) {
-  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   Scalars* s = pr.s;
   if (mode == 1 && s->done) return;
   __shared__ PoissonStage st;
@@ -1896,6 +1938,9 @@ __device__ __forceinline__ void update_body(const Chunk& ch, const GridProb& pr,
     const int w = k % QPT;
     const int y = tile_y0(tc) + w / qrow;
     if (y >= pr.H) continue;
+    // Poisson, 128-pixel tiles: a quad without a free pixel keeps zero
+    // delta, r, p and q, so it is skipped
+    if (NX == 4 && pr.live && !((__ldg(pr.live + (long long)y * pr.ntx + (tc & 0xffff)) >> (w % qrow)) & 1u)) continue;
     const long long j = (long long)y * P4 + tile_x0(tc, pr.tw) / 4 + w % qrow;
     float4 pv[NX], qv[NX], dv[NX], rv[NX], mv[NM];
 #pragma unroll
@@ -1942,9 +1987,9 @@ __global__ void __launch_bounds__(NT) k_grid_update(const GridProb* __restrict__
                                                     const Chunk* __restrict__ chunks,
                                                     const int* __restrict__ tiles,
                                                     double* __restrict__ part, int par) {
-  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   update_body<NX>(ch, pr, tiles, part, par);
 }
 
@@ -1976,9 +2021,9 @@ template <int NX>
 __global__ void __launch_bounds__(NT) k_grid_step(const GridProb* __restrict__ probs,
                                                   const Chunk* __restrict__ chunks,
                                                   const int* __restrict__ tiles, int cond) {
-  pdl_begin();
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  pdl_begin();
   if (cond && !pr.s->accept) return;
   if (!cond && pr.s->done) return;
   const long long pl = pr.plane;
@@ -2039,10 +2084,7 @@ cudaError_t grid_kernels_prepare() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_poisson_apply_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_poisson_init_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sizeof(PoisInitSmem));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_poisson_init_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_poisson_init_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sizeof(PoisInitSmem));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_warp_pcg_coop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -2067,12 +2109,9 @@ void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, fl
   else if (kind == K_WARP)
     launch_pdl(k_warp_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
   else
-    if (L.tw == W4 && L.masked)
-      launch_pdl(k_poisson_init_wide<true>, L.nchunks, NT, sizeof(PoisInitSmem), L.stream, L.probs, L.chunks, L.tiles,
+    if (L.tw == W4)
+      launch_pdl(k_poisson_init_wide, L.nchunks, NT, sizeof(PoisInitSmem), L.stream, L.probs, L.chunks, L.tiles,
                  L.part, k_outer, dmin, dmax);
-    else if (L.tw == W4)
-      launch_pdl(k_poisson_init_wide<false>, L.nchunks, NT, sizeof(PoisInitSmem), L.stream, L.probs, L.chunks,
-                 L.tiles, L.part, k_outer, dmin, dmax);
     else
       launch_pdl(k_poisson_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
 }
@@ -2087,12 +2126,12 @@ void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, i
   else if (kind == K_WARP)
     launch_pdl(k_warp_apply, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, p_override, par, update);
   else
-    if (L.tw == W4 && L.masked)
+    if (L.tw == W4 && update)
       launch_pdl(k_poisson_apply_wide<true>, L.nchunks, NT, sizeof(PoisWideSmem), L.stream, L.probs, L.chunks,
-                 L.tiles, L.part, p_override, par, update);
+                 L.tiles, L.part, p_override, par);
     else if (L.tw == W4)
       launch_pdl(k_poisson_apply_wide<false>, L.nchunks, NT, sizeof(PoisWideSmem), L.stream, L.probs, L.chunks,
-                 L.tiles, L.part, p_override, par, update);
+                 L.tiles, L.part, p_override, par);
     else
       launch_pdl(k_poisson_apply, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, p_override, par,
                  update);
@@ -2110,6 +2149,12 @@ void launch_grid_energy(int kind, const GridLaunch& L, int mode, int hist_idx) {
     launch_pdl(k_warp_energy, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, mode, hist_idx);
   else
     launch_pdl(k_poisson_energy, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, mode, hist_idx);
+}
+
+void launch_pois_sdeg(int W, int H, int P, const uint8_t* mask, uint8_t* out, cudaStream_t st) {
+  const long long n = (long long)P * H;
+  const int blocks = (int)std::min<long long>((n + NT - 1) / NT, 152LL * 16);
+  k_pois_sdeg<<<blocks, NT, 0, st>>>(W, H, P, mask, out);
 }
 
 void launch_grid_step(int kind, const GridLaunch& L, int cond) {

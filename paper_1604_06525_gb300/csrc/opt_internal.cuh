@@ -96,6 +96,11 @@ struct GridProb {
   float* x;                     // unknown planes (working copy)
   const float* c;               // constant planes (UrShape or guidance)
   const uint8_t* mask;          // pitched mask, NULL = none
+  const uint8_t* sdeg;          // Poisson, tw = 128: degree plane (S_i + 1 on free pixels, 0 elsewhere)
+  // Poisson, tw = 128, masked: quads holding a free pixel, one 32-bit word per
+  // (row, tile column), bit l for the quad at x = 128 tx + 4 l (NULL: all);
+  // the vector update skips the others
+  const unsigned int* live;
   float *d, *r, *p, *q;         // PCG vectors
   float *m, *dc;                // M^-1 and LM diagonal (distinct-diagonal planes)
   float* csn;                   // warp, tw = 128: cos / sin of theta (2 planes, written by PCGInit)
@@ -152,9 +157,11 @@ struct MeshProb {
 // ---------------------------------------------------------------------------
 // Every solver kernel is launched with programmatic stream serialization
 // (launch_pdl), so the launch of the next kernel of the chain overlaps the end
-// of this one.  Each kernel begins with pdl_begin(): it waits, before it reads
-// or writes anything, until the kernel before it has completed and its writes
-// are visible.  By default a kernel's dependents launch as its blocks exit;
+// of this one.  Each kernel calls pdl_begin() before it reads or writes
+// anything a solver kernel writes: it waits until the kernel before it has
+// completed and its writes are visible.  The grid kernels read their work
+// chunk and problem descriptor (written only by the host, before the launch)
+// ahead of it, overlapping those loads with the previous kernel's tail.  By default a kernel's dependents launch as its blocks exit;
 // the graph kernels release them earlier with pdl_trigger() once the block's
 // main pass is over (measured: 5% faster for the mesh, slower for the grid
 // kernels, whose blocks would crowd onto the SMs that free up first).

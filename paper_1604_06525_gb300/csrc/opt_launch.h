@@ -55,6 +55,9 @@ void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, i
 void launch_grid_update(int kind, const GridLaunch& L, int par);
 void launch_grid_energy(int kind, const GridLaunch& L, int mode, int hist_idx);
 void launch_grid_step(int kind, const GridLaunch& L, int cond);
+// Poisson, tile width 128: the degree plane the wide kernels read (S_i + 1 on
+// free pixels, 0 elsewhere; pitched like the mask, P x H bytes)
+void launch_pois_sdeg(int W, int H, int P, const uint8_t* mask, uint8_t* out, cudaStream_t st);
 // Persistent PCG loop (wide warp tiles only): the largest chunk count whose
 // blocks are all resident at once (0 if unknown), and the cooperative launch
 // of n_inner PCG iterations (applyJTJ + update) starting at parity par0.

@@ -291,6 +291,37 @@ def test_gn_poisson_small(api):
     np.testing.assert_array_equal(gp.x.cpu().numpy()[:, fixed], prob.x0[:, fixed])
 
 
+@pytest.mark.parametrize("layout", ["rectangle", "scattered"])
+@pytest.mark.parametrize("lm", [False, True])
+def test_wide_poisson_solves_skip_quads_without_free_pixels(api, layout, lm):
+    """128-pixel Poisson tiles read and write only quads that hold a free
+    pixel (PCGInit: quads within one pixel of one).  A free rectangle whose
+    edges cut through tiles and a scattered free set (70 % of the pixels
+    fixed at random, so most quads are partly free) solve like the oracle and
+    like 32-pixel tiles, which skip nothing, and fixed pixels never move."""
+    W, H = 300, 41
+    prob = synth.poisson_problem(W, H, seed=191)
+    if layout == "scattered":
+        prob.mask = (np.random.default_rng(192).random((H, W)) < 0.7).astype(np.uint8)
+    e = oracle.make_energy(prob)
+    outer, inner = (4, 15) if lm else (3, 20)
+    x0 = prob.x0.reshape(-1)
+    ref = oracle.levenberg_marquardt(e, x0, outer, inner) if lm else oracle.gauss_newton(e, x0, outer, inner)
+    a = api.Problem(prob, tile_w=128)
+    b = api.Problem(prob, tile_w=32)
+    solve = (lambda g: g.solve_lm(outer, inner)) if lm else (lambda g: g.solve_gn(outer, inner))
+    ra, rb = solve(a), solve(b)
+    assert len(ra["E_history"]) == len(ref.E_history)
+    for x, y, z in zip(ra["E_history"], rb["E_history"], ref.E_history):
+        assert relE(x, z) <= TOL_ENERGY
+        assert relE(x, y) <= 1e-5
+    fixed = prob.mask != 0
+    np.testing.assert_array_equal(a.x.cpu().numpy()[:, fixed], prob.x0[:, fixed])
+    assert rel(a.x.cpu().numpy(), b.x.cpu().numpy()) <= 1e-4
+    a.close()
+    b.close()
+
+
 def test_gn_graph_replay_equals_direct_launches(api):
     prob = synth.warp_problem(50, 40, 6, seed=81)
     a = api.Problem(prob)
