@@ -577,6 +577,16 @@ opt_status opt_measure_fp64_fma_rate(void* stream, double* gflops);
  * NULL pointer. */
 opt_status opt_selftest_grid_barrier(int32_t extra, int32_t rounds, int32_t* timed_out);
 
+/* Self-test of the bounded wait behind the tensor-copy (TMA) staging of the
+ * wide grid kernels: each thread of 2 blocks waits on a shared-memory
+ * mbarrier phase, as the kernels wait for a tile.  complete = 1: one thread
+ * arrives first, the phase completes, *timed_out = 0.  complete = 0: nothing
+ * arrives; every wait gives up after 50 ms (the solver kernels allow 1 s, then
+ * flag the problem and the solve returns OPT_ERR_TIMEOUT), the launch ends
+ * and *timed_out = 1, leaving the context usable.  Synchronous.
+ * OPT_ERR_INVALID_ARG for complete outside {0, 1} or a NULL pointer. */
+opt_status opt_selftest_staging_wait(int32_t complete, int32_t* timed_out);
+
 /* Human-readable name of a status code; never NULL. */
 const char* opt_status_str(opt_status s);
 

@@ -119,6 +119,7 @@ _SIGNATURES = [
                                              c_int32, c_float, c_float, c_void_p, c_void_p, c_void_p,
                                              c_void_p]),
     ("opt_selftest_grid_barrier", c_int32, [c_int32, c_int32, POINTER(c_int32)]),
+    ("opt_selftest_staging_wait", c_int32, [c_int32, POINTER(c_int32)]),
     ("opt_problem_create_grid_f64", c_int32, [POINTER(GridDescF64), POINTER(SolveParams), POINTER(c_void_p)]),
     ("opt_problem_create_graph_f64", c_int32, [POINTER(GraphDescF64), POINTER(SolveParams), POINTER(c_void_p)]),
     ("opt_problem_destroy_f64", c_int32, [c_void_p]),

@@ -9,6 +9,8 @@
 // copy of x out.  Every decision (PCG breakdown, LM accept / reject, LM
 // convergence) is taken on the device and read by later kernels, so the
 // sequence never needs the host and is captured once as a CUDA graph.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -460,7 +462,68 @@ opt_status run_solve(opt_problem* pb, const opt_solve_params* prm_in, opt_report
     CK(cudaMemcpy(&gb, pb->d_gbar, sizeof(gb), cudaMemcpyDeviceToHost));
     if (gb.timeout) return OPT_ERR_TIMEOUT;
   }
+  if (s.timeout) return OPT_ERR_TIMEOUT;
+  if (s.misaligned) return OPT_ERR_CUDA;
   if (s.nonfinite) return OPT_ERR_NUMERIC;
+  return OPT_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver, through the runtime's entry-point
+// query (no link-time dependency on the driver library)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor maps of a grid with 128-pixel tiles (GridProb::tmap): [0] the nfp
+// float planes of the slab, [1] the nx unknown planes, [2] the byte plane
+// (if any).  Boxes: WIDE_BOX_W x HH x 1 floats, WIDE_BYTE_BOX_W x HH bytes;
+// out-of-range elements are zero-filled.  All bases are device allocations
+// (256-byte aligned) and every stride (P * 4, plane * 4, P) is a multiple of
+// 16 bytes because P is a multiple of 128.
+static opt_status make_grid_tmaps(opt_problem* q, const float* slab, int nfp, const uint8_t* bytes) {
+  // L2 fill granularity of the copies (measured at 4096^2: 256-byte fills
+  // suit the warp, whose neighbouring tiles reuse them, 64-byte fills the
+  // Poisson kernels, 2-4 % apart)
+  const CUtensorMapL2promotion l2 =
+      q->kind == K_WARP ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_L2_64B;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cuda_fail(cudaErrorNotSupported, "cuTensorMapEncodeTiled");
+  CUtensorMap maps[3];
+  std::memset(maps, 0, sizeof(maps));
+  const cuuint64_t P = (cuuint64_t)q->P, H = (cuuint64_t)q->H, pl = (cuuint64_t)q->plane;
+  const cuuint32_t es[3] = {1, 1, 1};
+  const cuuint32_t box3[3] = {(cuuint32_t)WIDE_BOX_W, (cuuint32_t)HH, 1};
+  const cuuint64_t str3[2] = {P * 4, pl * 4};
+  auto f32 = [&](CUtensorMap* m, const float* base, int planes) {
+    const cuuint64_t dims[3] = {P, H, (cuuint64_t)planes};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, str3, box3, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, l2,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  };
+  if (f32(&maps[0], slab, nfp) != CUDA_SUCCESS || f32(&maps[1], q->x, q->nx) != CUDA_SUCCESS)
+    return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
+  if (bytes) {
+    const cuuint64_t dims[2] = {P, H}, str[1] = {P};
+    const cuuint32_t box[2] = {(cuuint32_t)WIDE_BYTE_BOX_W, (cuuint32_t)HH};
+    if (enc(&maps[2], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(bytes), dims, str, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, l2,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cuda_fail(cudaErrorInvalidValue, "cuTensorMapEncodeTiled");
+  }
+  static_assert(sizeof(CUtensorMap) == 128, "tensor maps are 128 bytes");
+  unsigned long long* dmap = nullptr;
+  CKS(dalloc(q, &dmap, 3 * sizeof(CUtensorMap) / sizeof(unsigned long long)));
+  CK(cudaMemcpy(dmap, maps, sizeof(maps), cudaMemcpyHostToDevice));
+  q->hg.tmap = dmap;
   return OPT_OK;
 }
 
@@ -532,6 +595,21 @@ opt_status opt_selftest_grid_barrier(int32_t extra, int32_t rounds, int32_t* tim
   cudaFree(gb);
   if (e != cudaSuccess) return cuda_fail(e, "opt_selftest_grid_barrier");
   *timed_out = h.timeout ? 1 : 0;
+  return OPT_OK;
+}
+
+opt_status opt_selftest_staging_wait(int32_t complete, int32_t* timed_out) {
+  if (!timed_out || complete < 0 || complete > 1) return OPT_ERR_INVALID_ARG;
+  int* d = nullptr;
+  CK(cudaMalloc(&d, sizeof(int)));
+  int h = 0;
+  cudaError_t e = cudaMemset(d, 0, sizeof(int));
+  if (e == cudaSuccess) e = launch_staging_selftest(complete, 50000000ull, d, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "opt_selftest_staging_wait");
+  *timed_out = h ? 1 : 0;
   return OPT_OK;
 }
 
@@ -740,6 +818,13 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   g.lm = 0;
   g.x = q->x; g.c = c; g.mask = dmask; g.sdeg = dsdeg;
   g.live = dlive;
+  // 128-pixel tiles: tensor maps of the staged planes, and where each plane
+  // group lies in the slab
+  g.tmap = nullptr;
+  const auto zof = [&](const float* ptr) { return ptr ? (int)((ptr - slab) / (ptrdiff_t)pl) : -1; };
+  g.zpack = zof(q->rvec) | zof(m) << 6 | zof(q->pbuf) << 12 | (csn ? zof(csn) : 0) << 18 | zof(c) << 24;
+  if (tw == 128) CKS(make_grid_tmaps(q, slab, (int)(nx + nm + 2 * nx + nx + nx + (has_csn ? 2 : 0) + nc),
+                                     warp ? dmask : dsdeg));
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
   g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;
   g.jtf_out = nullptr; g.diag_out = nullptr;
@@ -1122,6 +1207,8 @@ opt_status opt_pcg_init(opt_problem* prob, double lambda, double* energy) {
   Scalars s;
   CK(cudaMemcpy(&s, prob->d_s, sizeof(Scalars), cudaMemcpyDeviceToHost));
   if (energy) *energy = s.E;
+  if (s.timeout) return OPT_ERR_TIMEOUT;
+  if (s.misaligned) return OPT_ERR_CUDA;
   return s.nonfinite ? OPT_ERR_NUMERIC : OPT_OK;
 }
 
@@ -1505,6 +1592,8 @@ opt_status opt_eval_energy(opt_problem* prob, double* energy) {
   Scalars s;
   CK(cudaMemcpy(&s, prob->d_s, sizeof(Scalars), cudaMemcpyDeviceToHost));
   if (energy) *energy = s.E;
+  if (s.timeout) return OPT_ERR_TIMEOUT;
+  if (s.misaligned) return OPT_ERR_CUDA;
   return s.nonfinite ? OPT_ERR_NUMERIC : OPT_OK;
 }
 

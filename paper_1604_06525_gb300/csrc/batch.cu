@@ -403,10 +403,12 @@ opt_status batch_solve(opt_batch* b, const opt_solve_params* prm_in, opt_report*
   std::vector<double> hv((size_t)n * hlen);
   BCK(cudaMemcpy(sv.data(), b->d_sout, n * sizeof(Scalars), cudaMemcpyDeviceToHost));
   BCK(cudaMemcpy(hv.data(), b->d_hout, hv.size() * sizeof(double), cudaMemcpyDeviceToHost));
-  bool nonfinite = false;
+  bool nonfinite = false, timeout = false, misaligned = false;
   for (int i = 0; i < n; ++i) {
     const Scalars& t = sv[i];
     nonfinite |= t.nonfinite != 0;
+    timeout |= t.timeout != 0;
+    misaligned |= t.misaligned != 0;
     if (!reports) continue;
     opt_report& r = reports[i];
     const int od = lm ? t.outer_done : p.outer;
@@ -420,6 +422,8 @@ opt_status batch_solve(opt_batch* b, const opt_solve_params* prm_in, opt_report*
     if (r.E_history) std::memcpy(r.E_history, &hv[(size_t)i * hlen], sizeof(double) * (od + 1));
     r.ms = ms;
   }
+  if (timeout) return OPT_ERR_TIMEOUT;
+  if (misaligned) return OPT_ERR_CUDA;
   return nonfinite ? OPT_ERR_NUMERIC : OPT_OK;
 }
 

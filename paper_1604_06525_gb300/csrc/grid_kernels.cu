@@ -388,13 +388,31 @@ __global__ void __launch_bounds__(NT, 3) k_warp_apply(const GridProb* __restrict
 constexpr int W4 = 128;          // wide tile width
 constexpr int SP = W4 + 8;       // staged row pitch (floats): columns -1..128 live at 3..132
 constexpr int SPB = W4 + 32;     // mask row pitch (bytes): columns 0..127 live at 16..143
+static_assert(SP == WIDE_BOX_W && SPB == WIDE_BYTE_BOX_W, "staged boxes and tensor-map boxes must agree");
 constexpr int NRAW = 12;         // r0 r1 r2 m0 m1 p0 p1 p2 cos sin ux uy
 constexpr int NSTG = 8;          // px py pt cos sin ux uy valid, each quad stored as pixels 0 2 1 3
 
+// One staged plane: the halo-extended tile (rows y0 - 1 .. y0 + 8, columns
+// x0 - 4 .. x0 + 131 at v[row][0 .. 135]), padded to a multiple of 128 bytes
+// so that every plane of a staging area starts where a tensor copy may write.
+struct __align__(128) PlaneT {
+  float v[HH][SP];
+  float pad[16];
+};
+static_assert(sizeof(PlaneT) % 128 == 0, "plane slots must keep 128-byte alignment");
+// The staged byte plane (mask or degree bytes): columns x0 - 16 .. x0 + 143
+// at v[row][0 .. 159].
+struct __align__(128) BytesT {
+  unsigned char v[HH][SPB];
+  unsigned char pad[64];
+};
+static_assert(sizeof(BytesT) % 128 == 0, "byte slots must keep 128-byte alignment");
+
 struct WideSmem {
-  float raw[NRAW][HH][SP];
+  PlaneT raw[NRAW];
   float stg[NSTG][HH][SP];       // halo columns -1 / 128 live at 3 / 132, in plain order
-  unsigned char mk[HH][SPB];
+  BytesT mk;
+  unsigned long long bar;        // tensor-copy completion of the raw planes
 };
 
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
@@ -415,11 +433,124 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool val
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// ---------------------------------------------------------------------------
+// Tensor copies (TMA) of the staged tiles.  One thread issues one copy per
+// plane (box: 136 columns x 10 rows x 1 plane from (x0 - 4, y0 - 1); the byte
+// plane: 160 x 10 from (x0 - 16, y0 - 1): both x offsets are multiples of 16
+// bytes); the copy engine zero-fills rows and columns outside the tensor, as
+// the cp.async path does.  Completion is counted in bytes on an mbarrier in
+// shared memory.  Every thread waits for the phase itself, bounded by 1 s of
+// %globaltimer: a wait that runs out reports failure (the kernel then sets
+// Scalars::timeout and returns; the host reports OPT_ERR_TIMEOUT).
+// ---------------------------------------------------------------------------
+constexpr unsigned kPlaneBox = HH * SP * 4;     // bytes one plane copy writes
+constexpr unsigned kByteBox = HH * SPB;         // bytes one byte-plane copy writes
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// Waits for the completion of the phase with the given parity; false once
+// limit_ns (1 s) has passed without it.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          unsigned long long limit_ns = kBarrierLimitNs) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_test(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_plane(PlaneT* dst, const unsigned long long* map, int x, int y, int z,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_bytes(BytesT* dst, const unsigned long long* map, int x, int y,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];\n" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// tensor copies write only to 128-byte aligned staging areas (checked once
+// per launch; an unaligned area is staged by cp.async instead)
+__device__ __forceinline__ bool smem_aligned128(const void* p) { return (smem_u32(p) & 127u) == 0u; }
+// slab plane index of a plane group (0 r, 1 M^-1, 2 p of parity 0, 3 cos /
+// sin, 4 constants)
+__device__ __forceinline__ int zslab(const GridProb& pr, int g) { return (pr.zpack >> (6 * g)) & 63; }
+// whether a launch stages by tensor copies: the problem has tensor maps and
+// the staging area is aligned
+__device__ __forceinline__ bool wide_tma(const GridProb& pr, const void* smem) {
+  return pr.tmap != nullptr && smem_aligned128(smem);
+}
+// Kernels that stage only by tensor copies check this first; on failure
+// (no tensor maps, or an unaligned staging area, which the 128-byte aligned
+// dynamic shared memory rules out) they flag the problem and do nothing.
+__device__ __forceinline__ bool tma_ready(const GridProb& pr, const void* smem) {
+  if (wide_tma(pr, smem)) return true;
+  if (threadIdx.x == 0) atomicExch(&pr.s->misaligned, 1u);
+  return false;
+}
+// tensor map m of a problem (0 slab, 1 unknowns, 2 byte plane)
+__device__ __forceinline__ const unsigned long long* tmap_of(const GridProb& pr, int m) { return pr.tmap + 16 * m; }
+
+// Issues the tensor copies of one tile (one thread): raw[k] from the plane
+// that plane(k, z, m) names (plane z of map m; z < 0: not copied), the byte
+// plane into mk if `bytes`.  Every thread has finished reading the slot
+// before the call (a block barrier lies between); the proxy fence orders
+// those reads before the copy engine's writes.
+template <int NR, class F>
+__device__ __forceinline__ void tile_tma(PlaneT* raw, BytesT* mk, F plane, bool bytes, const GridProb& pr, int x0,
+                                         int y0, unsigned long long* bar) {
+  unsigned total = bytes ? kByteBox : 0u;
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    int z, m;
+    plane(k, z, m);
+    if (z >= 0) total += kPlaneBox;
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  mbar_expect(bar, total);
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    int z, m;
+    plane(k, z, m);
+    if (z >= 0) tma_plane(&raw[k], tmap_of(pr, m), x0 - 4, y0 - 1, z, bar);
+  }
+  if (bytes) tma_bytes(mk, tmap_of(pr, 2), x0 - 16, y0 - 1, bar);
+}
+
+// Timeout of a staging wait: flags the problem and returns once the copies
+// still in flight into the slot have landed (or another second has passed).
+__device__ __forceinline__ void staging_timeout(Scalars* s, unsigned long long* bar, unsigned parity) {
+  if (threadIdx.x == 0) {
+    atomicExch(&s->timeout, 1u);
+    mbar_wait(bar, parity);
+  }
+}
+
 struct WidePlanes {
   const float* src[NRAW];        // plane base pointers (nullptr: not needed this launch)
 };
 
-// Issues the copies of one 128 x 8 tile with its halo into raw[NR][HH][SP]
+// Issues the copies of one 128 x 8 tile with its halo into raw[0..NR-1]
 // (column x0 + k at 4 + k): quads of the own rows by every thread, of the two
 // halo rows by threads 0..63, and the halo columns by threads 64..79 as the
 // aligned quad holding column -1 (x0-4 .. x0-1, staged at 0..3) or column
@@ -431,7 +562,7 @@ struct WidePlanes {
 // as the aligned 4-byte words around them (column -1 at mk[row][15], column
 // 128 at mk[row][144]).
 template <int NR, bool MASK>
-__device__ __forceinline__ void tile_issue(float (*raw)[HH][SP], unsigned char (*mk)[SPB],
+__device__ __forceinline__ void tile_issue(PlaneT* raw, unsigned char (*mk)[SPB],
                                            const float* const* src, const uint8_t* __restrict__ bytes,
                                            const GridProb& pr, int x0, int y0, int tid) {
   const int lane = tid & 31, ty = tid >> 5;
@@ -442,7 +573,7 @@ __device__ __forceinline__ void tile_issue(float (*raw)[HH][SP], unsigned char (
     const long long i = ok ? (long long)gy * pr.P + gx : 0;
 #pragma unroll
     for (int k = 0; k < NR; ++k)
-      if (src[k]) cp_async16(&raw[k][ty + 1][4 + 4 * lane], src[k] + i, ok);
+      if (src[k]) cp_async16(&raw[k].v[ty + 1][4 + 4 * lane], src[k] + i, ok);
     if (MASK) cp_async4(&mk[ty + 1][16 + 4 * lane], bytes + i, ok);
   }
   if (tid < 64) {
@@ -452,7 +583,7 @@ __device__ __forceinline__ void tile_issue(float (*raw)[HH][SP], unsigned char (
     const long long i = ok ? (long long)gy * pr.P + gx : 0;
 #pragma unroll
     for (int k = 0; k < NR; ++k)
-      if (src[k]) cp_async16(&raw[k][row][4 + 4 * lane], src[k] + i, ok);
+      if (src[k]) cp_async16(&raw[k].v[row][4 + 4 * lane], src[k] + i, ok);
     if (MASK) cp_async4(&mk[row][16 + 4 * lane], bytes + i, ok);
   } else if (tid < 64 + 2 * TH) {
     const int h = tid - 64;
@@ -463,7 +594,7 @@ __device__ __forceinline__ void tile_issue(float (*raw)[HH][SP], unsigned char (
     const int col = side ? 4 + W4 : 0;
 #pragma unroll
     for (int k = 0; k < NR; ++k)
-      if (src[k]) cp_async16(&raw[k][row][col], src[k] + i, ok);
+      if (src[k]) cp_async16(&raw[k].v[row][col], src[k] + i, ok);
     if (MASK) cp_async4(&mk[row][side ? 16 + W4 : 12], bytes + i, ok);
   }
   cp_async_commit();
@@ -477,7 +608,7 @@ __device__ __forceinline__ unsigned char halo_mask(const unsigned char (*mk)[SPB
 template <bool MASK>
 __device__ __forceinline__ void wide_issue(WideSmem& sm, const WidePlanes& pp, const GridProb& pr, int x0, int y0,
                                            int tid) {
-  tile_issue<NRAW, MASK>(sm.raw, sm.mk, pp.src, pr.mask, pr, x0, y0, tid);
+  tile_issue<NRAW, MASK>(sm.raw, sm.mk.v, pp.src, pr.mask, pr, x0, y0, tid);
 }
 
 // Packed float32 pairs (one instruction for two lanes of a float2).  All are
@@ -514,7 +645,7 @@ template <bool MASK>
 __device__ __forceinline__ void wide_stage_quad(WideSmem& sm, int row, int lane, const GridProb& pr, int gx, int gy,
                                                 int update, int use_beta, float2 beta2) {
   const int c = 4 + 4 * lane;
-  auto R = [&](int k) { return lds4(&sm.raw[k][row][c]); };
+  auto R = [&](int k) { return lds4(&sm.raw[k].v[row][c]); };
   float4 a, b, t;
   if (update) {
     const float4 m0 = R(3), m1 = R(4);
@@ -536,7 +667,7 @@ __device__ __forceinline__ void wide_stage_quad(WideSmem& sm, int row, int lane,
   for (int k = 0; k < 4; ++k) sts4(&sm.stg[3 + k][row][c], swz4(R(8 + k)));
   float vk[4] = {0.f, 0.f, 0.f, 0.f};
   if (gy >= 0 && gy < pr.H) {
-    const unsigned int m4 = MASK ? *reinterpret_cast<const unsigned int*>(&sm.mk[row][16 + 4 * lane]) : 0u;
+    const unsigned int m4 = MASK ? *reinterpret_cast<const unsigned int*>(&sm.mk.v[row][16 + 4 * lane]) : 0u;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       vk[k] = (gx + k < pr.W && (!MASK || ((m4 >> (8 * k)) & 0xffu) == 0u)) ? 1.f : 0.f;
@@ -568,10 +699,14 @@ __device__ __forceinline__ void pair2(const Own2& o, float2 pxj, float2 pyj, flo
 
 // One applyJTJ pass of the block's chunk (shared by the per-step kernel and
 // the persistent PCG kernel).
-template <bool MASK>
+// The raw planes of the PCG path arrive by tensor copies (sm.bar, whose next
+// phase has parity `phase`; the caller initialised it), a caller's p by
+// cp.async.
+template <bool MASK, bool TMA>
 __device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, const GridProb& pr,
                                                 const int* __restrict__ tiles, double* __restrict__ part,
-                                                const float* __restrict__ p_in_override, int par, int update) {
+                                                const float* __restrict__ p_in_override, int par, int update,
+                                                unsigned& phase) {
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
   const int pl = (int)pr.plane;
@@ -601,16 +736,42 @@ __device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, c
   // the tile index one tile ahead and the handle range of the current tile
   // are loaded an iteration early: the inline-assembly copies order all
   // memory accesses, so a late load would stall the warp at its use
+  constexpr bool tma = TMA;   // the caller checked wide_tma()
+  // raw planes r0 r1 r2 m0 m1 p0 p1 p2 cos sin ux uy, all in the slab
+  auto plane = [&](int k, int& z, int& m) {
+    m = 0;
+    z = k < 3 ? zslab(pr, 0) + k
+              : k < 5 ? zslab(pr, 1) + k - 3
+                      : k < 8 ? (use_beta ? zslab(pr, 2) + (par & 1) * 3 + k - 5 : -1)
+                              : k < 10 ? zslab(pr, 3) + k - 8 : zslab(pr, 4) + k - 10;
+  };
+  auto issue = [&](int tcx) {
+    if (tma) {
+      if (tid == 0) tile_tma<NRAW>(sm.raw, &sm.mk, plane, MASK, pr, tile_x0(tcx, W4), tile_y0(tcx), &sm.bar);
+    } else {
+      wide_issue<MASK>(sm, pp, pr, tile_x0(tcx, W4), tile_y0(tcx), tid);
+    }
+  };
   int tc = tiles[ch.begin];
   int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
   int hb0 = pr.hbeg[tile_id(pr, tc)], hb1 = pr.hbeg[tile_id(pr, tc) + 1];
-  wide_issue<MASK>(sm, pp, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+  issue(tc);
   for (int t = ch.begin; t < ch.end; ++t) {
     const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
     const int gx = x0 + 4 * lane, gy = y0 + ty;
     const int hcur0 = hb0, hcur1 = hb1;
-    cp_async_wait_all();
-    __syncthreads();
+    const unsigned pb = phase;
+    bool ok = true;
+    if (tma) {
+      ok = mbar_wait(&sm.bar, pb);
+      phase ^= 1u;
+    } else {
+      cp_async_wait_all();
+    }
+    if (__syncthreads_or(!ok)) {
+      staging_timeout(s, &sm.bar, pb);
+      return;
+    }
     // phase 2: staged direction, geometry and validity
     wide_stage_quad<MASK>(sm, ty + 1, lane, pr, gx, gy, update, use_beta, beta2);
     if (tid < 64) {
@@ -622,29 +783,29 @@ __device__ __forceinline__ void apply_wide_body(WideSmem& sm, const Chunk& ch, c
       const int col = side ? 4 + W4 : 3;
       float a, b, c;
       if (update) {
-        a = __fmul_rn(sm.raw[3][row][col], sm.raw[0][row][col]);
-        b = __fmul_rn(sm.raw[3][row][col], sm.raw[1][row][col]);
-        c = __fmul_rn(sm.raw[4][row][col], sm.raw[2][row][col]);
+        a = __fmul_rn(sm.raw[3].v[row][col], sm.raw[0].v[row][col]);
+        b = __fmul_rn(sm.raw[3].v[row][col], sm.raw[1].v[row][col]);
+        c = __fmul_rn(sm.raw[4].v[row][col], sm.raw[2].v[row][col]);
         if (use_beta) {
-          a = __fmaf_rn(beta, sm.raw[5][row][col], a);
-          b = __fmaf_rn(beta, sm.raw[6][row][col], b);
-          c = __fmaf_rn(beta, sm.raw[7][row][col], c);
+          a = __fmaf_rn(beta, sm.raw[5].v[row][col], a);
+          b = __fmaf_rn(beta, sm.raw[6].v[row][col], b);
+          c = __fmaf_rn(beta, sm.raw[7].v[row][col], c);
         }
       } else {
-        a = sm.raw[5][row][col]; b = sm.raw[6][row][col]; c = sm.raw[7][row][col];
+        a = sm.raw[5].v[row][col]; b = sm.raw[6].v[row][col]; c = sm.raw[7].v[row][col];
       }
       sm.stg[0][row][col] = a; sm.stg[1][row][col] = b; sm.stg[2][row][col] = c;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) sm.stg[3 + k][row][col] = sm.raw[8 + k][row][col];
+      for (int k = 0; k < 4; ++k) sm.stg[3 + k][row][col] = sm.raw[8 + k].v[row][col];
       const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
       const bool ok = hy < pr.H && hx >= 0 && hx < pr.W;
-      sm.stg[7][row][col] = (ok && (!MASK || halo_mask(sm.mk, row, side) == 0)) ? 1.f : 0.f;
+      sm.stg[7][row][col] = (ok && (!MASK || halo_mask(sm.mk.v, row, side) == 0)) ? 1.f : 0.f;
     }
     __syncthreads();
     // the raw buffer is free: start the next tile's copies
     if (t + 1 < ch.end) {
       tc = tn;
-      wide_issue<MASK>(sm, pp, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+      issue(tc);
       const int tidn = tile_id(pr, tc);
       hb0 = pr.hbeg[tidn];
       hb1 = pr.hbeg[tidn + 1];
@@ -771,18 +932,25 @@ __global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __res
                                                            double* __restrict__ part,
                                                            const float* __restrict__ p_in_override,
                                                            int par, int update) {
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
   WideSmem& sm = *reinterpret_cast<WideSmem*>(dyn_smem);
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   pdl_begin();
-  apply_wide_body<MASK>(sm, ch, pr, tiles, part, p_in_override, par, update);
+  if (threadIdx.x == 0) mbar_init(&sm.bar);
+  __syncthreads();
+  unsigned phase = 0;
+  // the PCG path stages by tensor copies, a caller's p (the J^T J p hook) by cp.async
+  if (update && !p_in_override && wide_tma(pr, &sm))
+    apply_wide_body<MASK, true>(sm, ch, pr, tiles, part, p_in_override, par, update, phase);
+  else
+    apply_wide_body<MASK, false>(sm, ch, pr, tiles, part, p_in_override, par, update, phase);
 }
 
-// Wide-tile warp PCGInit (tw = 128), staged with asynchronous copies like the
-// wide apply: raw planes (dx, dy, theta, UrShape) of the halo-extended tile are
-// copied global -> shared, phase 2 evaluates cos / sin of theta once per staged
-// pixel, then the next tile's copies overlap phase 3.  Per valid neighbour
+// Wide-tile warp PCGInit (tw = 128), staged like the wide apply: tensor
+// copies bring the raw planes (dx, dy, theta, UrShape) of the halo-extended
+// tile into shared memory, phase 2 evaluates cos / sin of theta once per
+// staged pixel, then the next tile's copies overlap phase 3.  Per valid neighbour
 // pair (i, j), with a = d_i - d_j, v = U_i - U_j, e_k = v - R(theta_k) v and
 // G_i = -R'(theta_i) v:
 //   own residual       r_(i,j) =  s_w (a + e_i)
@@ -795,41 +963,32 @@ constexpr int NRAW_I = 5;        // dx dy theta ux uy
 constexpr int NSTG_I = 7;        // dx dy cos sin ux uy valid, quads stored as pixels 0 2 1 3
 
 struct InitSmem {
-  float raw[NRAW_I][HH][SP];
+  PlaneT raw[NRAW_I];
   float stg[NSTG_I][HH][SP];     // halo columns -1 / 128 live at 3 / 132, in plain order
-  unsigned char mk[HH][SPB];
+  BytesT mk;
+  unsigned long long bar;        // tensor-copy completion of the raw planes
 };
-
-struct InitPlanes {
-  const float* src[NRAW_I];      // dx, dy, theta, UrShape x, y
-};
-
-template <bool MASK>
-__device__ __forceinline__ void init_issue(InitSmem& sm, const InitPlanes& pp, const GridProb& pr, int x0, int y0,
-                                           int tid) {
-  tile_issue<NRAW_I, MASK>(sm.raw, sm.mk, pp.src, pr.mask, pr, x0, y0, tid);
-}
 
 // Phase 2 for one staged quad: cos / sin of theta, copied values, validity,
 // in the staged order 0 2 1 3.
 template <bool MASK>
 __device__ __forceinline__ void init_stage_quad(InitSmem& sm, int row, int lane, const GridProb& pr, int gx, int gy) {
   const int c = 4 + 4 * lane;
-  const float4 th = lds4(&sm.raw[2][row][c]);
+  const float4 th = lds4(&sm.raw[2].v[row][c]);
   float4 cs, sn;
   sincosf(th.x, &sn.x, &cs.x);
   sincosf(th.y, &sn.y, &cs.y);
   sincosf(th.z, &sn.z, &cs.z);
   sincosf(th.w, &sn.w, &cs.w);
-  sts4(&sm.stg[0][row][c], swz4(lds4(&sm.raw[0][row][c])));
-  sts4(&sm.stg[1][row][c], swz4(lds4(&sm.raw[1][row][c])));
+  sts4(&sm.stg[0][row][c], swz4(lds4(&sm.raw[0].v[row][c])));
+  sts4(&sm.stg[1][row][c], swz4(lds4(&sm.raw[1].v[row][c])));
   sts4(&sm.stg[2][row][c], swz4(cs));
   sts4(&sm.stg[3][row][c], swz4(sn));
-  sts4(&sm.stg[4][row][c], swz4(lds4(&sm.raw[3][row][c])));
-  sts4(&sm.stg[5][row][c], swz4(lds4(&sm.raw[4][row][c])));
+  sts4(&sm.stg[4][row][c], swz4(lds4(&sm.raw[3].v[row][c])));
+  sts4(&sm.stg[5][row][c], swz4(lds4(&sm.raw[4].v[row][c])));
   float vk[4] = {0.f, 0.f, 0.f, 0.f};
   if (gy >= 0 && gy < pr.H) {
-    const unsigned int m4 = MASK ? *reinterpret_cast<const unsigned int*>(&sm.mk[row][16 + 4 * lane]) : 0u;
+    const unsigned int m4 = MASK ? *reinterpret_cast<const unsigned int*>(&sm.mk.v[row][16 + 4 * lane]) : 0u;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       vk[k] = (gx + k < pr.W && (!MASK || ((m4 >> (8 * k)) & 0xffu) == 0u)) ? 1.f : 0.f;
@@ -869,19 +1028,8 @@ __device__ __forceinline__ void init_pair2(const OwnI2& o, float2 dxj, float2 dy
 }
 
 template <bool MASK>
-#ifndef WARP_INIT_WIDE_MINB
-#define WARP_INIT_WIDE_MINB 2       // resident blocks per SM the wide warp PCGInit is compiled for
-#endif
-__global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(const GridProb* __restrict__ probs,
-                                                          const Chunk* __restrict__ chunks,
-                                                          const int* __restrict__ tiles,
-                                                          double* __restrict__ part, int k_outer,
-                                                          float dmin, float dmax) {
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
-  InitSmem& sm = *reinterpret_cast<InitSmem*>(dyn_smem);
-  const Chunk ch = chunks[blockIdx.x];
-  const GridProb pr = probs[ch.prob];
-  pdl_begin();
+__device__ __forceinline__ void k_warp_init_wide_body(InitSmem& sm, const Chunk& ch, const GridProb& pr,
+    const int* __restrict__ tiles, double* __restrict__ part, int k_outer, float dmin, float dmax) {
   Scalars* s = pr.s;
   if (s->done) return;
   const int pl = (int)pr.plane;
@@ -890,18 +1038,33 @@ __global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(cons
   const float lam = pr.lm ? s->lambda_f : 0.0f;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   F2x2 acc_rz = f2x2_zero(), acc_E = f2x2_zero();
-  InitPlanes ip;
-  ip.src[0] = pr.x; ip.src[1] = pr.x + pl; ip.src[2] = pr.x + 2 * pl; ip.src[3] = pr.c; ip.src[4] = pr.c + pl;
+  // raw planes by tensor copies: dx, dy, theta from the unknowns, UrShape
+  // from the slab
+  auto plane = [&](int k, int& z, int& m) {
+    m = k < 3 ? 1 : 0;
+    z = k < 3 ? k : zslab(pr, 4) + k - 3;
+  };
+  if (tid == 0) mbar_init(&sm.bar);
+  __syncthreads();
+  auto issue = [&](int tcx) {
+    if (tid == 0) tile_tma<NRAW_I>(sm.raw, &sm.mk, plane, MASK, pr, tile_x0(tcx, W4), tile_y0(tcx), &sm.bar);
+  };
+  unsigned phase = 0;
   int tc = tiles[ch.begin];
   int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
   int hb0 = pr.hbeg[tile_id(pr, tc)], hb1 = pr.hbeg[tile_id(pr, tc) + 1];
-  init_issue<MASK>(sm, ip, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+  issue(tc);
   for (int t = ch.begin; t < ch.end; ++t) {
     const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
     const int gx = x0 + 4 * lane, gy = y0 + ty;
     const int hcur0 = hb0, hcur1 = hb1;
-    cp_async_wait_all();
-    __syncthreads();
+    const unsigned pb = phase;
+    const bool ok = mbar_wait(&sm.bar, pb);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      staging_timeout(s, &sm.bar, pb);
+      return;
+    }
     init_stage_quad<MASK>(sm, ty + 1, lane, pr, gx, gy);
     if (tid < 64) {
       const int row = tid < 32 ? 0 : HH - 1;
@@ -911,21 +1074,21 @@ __global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(cons
       const int row = 1 + (h % TH), side = h / TH;
       const int col = side ? 4 + W4 : 3;
       float sn, cs;
-      sincosf(sm.raw[2][row][col], &sn, &cs);
-      sm.stg[0][row][col] = sm.raw[0][row][col];
-      sm.stg[1][row][col] = sm.raw[1][row][col];
+      sincosf(sm.raw[2].v[row][col], &sn, &cs);
+      sm.stg[0][row][col] = sm.raw[0].v[row][col];
+      sm.stg[1][row][col] = sm.raw[1].v[row][col];
       sm.stg[2][row][col] = cs;
       sm.stg[3][row][col] = sn;
-      sm.stg[4][row][col] = sm.raw[3][row][col];
-      sm.stg[5][row][col] = sm.raw[4][row][col];
+      sm.stg[4][row][col] = sm.raw[3].v[row][col];
+      sm.stg[5][row][col] = sm.raw[4].v[row][col];
       const int hy = y0 + row - 1, hx = side ? x0 + W4 : x0 - 1;
       const bool ok = hy < pr.H && hx >= 0 && hx < pr.W;
-      sm.stg[6][row][col] = (ok && (!MASK || halo_mask(sm.mk, row, side) == 0)) ? 1.f : 0.f;
+      sm.stg[6][row][col] = (ok && (!MASK || halo_mask(sm.mk.v, row, side) == 0)) ? 1.f : 0.f;
     }
     __syncthreads();
     if (t + 1 < ch.end) {
       tc = tn;
-      init_issue<MASK>(sm, ip, pr, tile_x0(tc, W4), tile_y0(tc), tid);
+      issue(tc);
       const int tidn = tile_id(pr, tc);
       hb0 = pr.hbeg[tidn];
       hb1 = pr.hbeg[tidn + 1];
@@ -1047,7 +1210,6 @@ __global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(cons
       }
     }
   }
-  cp_async_wait_all();
   if (publish_partials(part, blockIdx.x, f2x2_fold(acc_rz), f2x2_fold(acc_E), &s->counter,
                        pr.chunk_end - pr.chunk_begin)) {
     double rz, E;
@@ -1061,6 +1223,21 @@ __global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(cons
       if (!isfinite(rz) || !isfinite(E)) s->nonfinite = 1;
     }
   }
+}
+
+#ifndef WARP_INIT_WIDE_MINB
+#define WARP_INIT_WIDE_MINB 2       // resident blocks per SM the wide warp PCGInit is compiled for
+#endif
+template <bool MASK>
+__global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(const GridProb* __restrict__ probs,
+    const Chunk* __restrict__ chunks, const int* __restrict__ tiles, double* __restrict__ part, int k_outer,
+    float dmin, float dmax) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  InitSmem& sm = *reinterpret_cast<InitSmem*>(dyn_smem);
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  pdl_begin();
+  if (tma_ready(pr, &sm)) k_warp_init_wide_body<MASK>(sm, ch, pr, tiles, part, k_outer, dmin, dmax);
 }
 
 // E(x) (mode 0) or E(x + delta) and |F(x) + J(x) delta|^2 (mode 1).
@@ -1436,13 +1613,18 @@ constexpr int NRAW_PI = 8;       // X0..X3, T0..T3
 // pixel, see k_pois_sdeg): S_i + 1 on a free pixel i, S_i = diag(J^T J)_i,
 // and 0 on fixed pixels and the row padding.
 constexpr int PST = 2;
+template <int NR>
+struct PoisSlot {
+  PlaneT raw[NR];
+  BytesT mk;
+};
 struct PoisWideSmem {
-  float raw[PST][NRAW_PA][HH][SP];
-  unsigned char mk[PST][HH][SPB];
+  PoisSlot<NRAW_PA> slot[PST];
+  unsigned long long bar[PST];    // tensor-copy completion of each slot
 };
 struct PoisInitSmem {
-  float raw[PST][NRAW_PI][HH][SP];
-  unsigned char mk[PST][HH][SPB];
+  PoisSlot<NRAW_PI> slot[PST];
+  unsigned long long bar[PST];
 };
 
 // the four degree bytes of the staged quad (row, lane)
@@ -1485,19 +1667,19 @@ __device__ __forceinline__ float4 keep_if(unsigned int d4, const float4& v) {
 // order: p = M^-1 r + beta p_old with the fused vector update, else the given
 // p (raw planes: r0..r3, M^-1, p0..p3).
 template <bool UPD>
-__device__ __forceinline__ float4 pois_dir4(const float (*raw)[HH][SP], int k, int row, int c, const float4& m,
+__device__ __forceinline__ float4 pois_dir4(const PlaneT* raw, int k, int row, int c, const float4& m,
                                             bool use_beta, float2 beta2) {
-  if (!UPD) return lds4(&raw[5 + k][row][c]);
-  float4 v = mul4p(m, lds4(&raw[k][row][c]));
-  if (use_beta) v = fma4p(beta2, lds4(&raw[5 + k][row][c]), v);
+  if (!UPD) return lds4(&raw[5 + k].v[row][c]);
+  float4 v = mul4p(m, lds4(&raw[k].v[row][c]));
+  if (use_beta) v = fma4p(beta2, lds4(&raw[5 + k].v[row][c]), v);
   return v;
 }
 template <bool UPD>
-__device__ __forceinline__ float pois_dir1(const float (*raw)[HH][SP], int k, int row, int col, bool use_beta,
+__device__ __forceinline__ float pois_dir1(const PlaneT* raw, int k, int row, int col, bool use_beta,
                                            float beta) {
-  if (!UPD) return raw[5 + k][row][col];
-  float v = raw[4][row][col] * raw[k][row][col];
-  if (use_beta) v = fmaf(beta, raw[5 + k][row][col], v);
+  if (!UPD) return raw[5 + k].v[row][col];
+  float v = raw[4].v[row][col] * raw[k].v[row][col];
+  if (use_beta) v = fmaf(beta, raw[5 + k].v[row][col], v);
   return v;
 }
 
@@ -1507,10 +1689,10 @@ __device__ __forceinline__ float pois_dir1(const float (*raw)[HH][SP], int k, in
 // update keeps it, and the planes start zeroed); a given p (the J^T J p hook)
 // is zeroed there from the degree bytes.
 template <bool UPD>
-__device__ __forceinline__ void pois_dir_quad(const float (*raw)[HH][SP], const unsigned char (*mk)[SPB], int row,
+__device__ __forceinline__ void pois_dir_quad(const PlaneT* raw, const unsigned char (*mk)[SPB], int row,
                                               int lane, bool use_beta, float2 beta2, float4 (&out)[4]) {
   const int c = 4 + 4 * lane;
-  const float4 m = UPD ? lds4(&raw[4][row][c]) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 m = UPD ? lds4(&raw[4].v[row][c]) : make_float4(0.f, 0.f, 0.f, 0.f);
   const unsigned int d4 = UPD ? 0u : pois_deg4(mk, row, lane);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -1549,7 +1731,7 @@ __device__ __forceinline__ void pois_side_nbrs(const float4 (&O)[N], float (&L)[
 
 // Issues the copies of one Poisson tile: the raw planes and the degree bytes.
 template <int NR>
-__device__ __forceinline__ void pois_issue(float (*raw)[HH][SP], unsigned char (*mk)[SPB], const float* const* src,
+__device__ __forceinline__ void pois_issue(PlaneT* raw, unsigned char (*mk)[SPB], const float* const* src,
                                            const GridProb& pr, int tc, int tid) {
   tile_issue<NR, true>(raw, mk, src, pr.sdeg, pr, tile_x0(tc, W4), tile_y0(tc), tid);
 }
@@ -1559,7 +1741,7 @@ __device__ __forceinline__ void pois_issue(float (*raw)[HH][SP], unsigned char (
 // update) or the given p on the own quad and its neighbours, q = (J^T J +
 // lambda D) p on the free pixels, p and q stored, p.q accumulated.
 template <bool UPD>
-__device__ __forceinline__ void pois_apply_quad(const float (*raw)[HH][SP], const unsigned char (*mk)[SPB],
+__device__ __forceinline__ void pois_apply_quad(const PlaneT* raw, const unsigned char (*mk)[SPB],
                                                 const GridProb& pr, int ty, int lane, long long i,
                                                 bool use_beta, float beta, float2 beta2, float lam,
                                                 float* __restrict__ pout, int pl, F2x2& acc) {
@@ -1604,17 +1786,8 @@ __device__ __forceinline__ void pois_apply_quad(const float (*raw)[HH][SP], cons
 }
 
 template <bool UPD>
-__global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __restrict__ probs,
-                                                              const Chunk* __restrict__ chunks,
-                                                              const int* __restrict__ tiles,
-                                                              double* __restrict__ part,
-                                                              const float* __restrict__ p_in_override,
-                                                              int par) {
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
-  PoisWideSmem& sm = *reinterpret_cast<PoisWideSmem*>(dyn_smem);
-  const Chunk ch = chunks[blockIdx.x];
-  const GridProb pr = probs[ch.prob];
-  pdl_begin();
+__device__ __forceinline__ void k_poisson_apply_wide_body(PoisWideSmem& sm, const Chunk& ch, const GridProb& pr,
+    const int* __restrict__ tiles, double* __restrict__ part, const float* __restrict__ p_in_override, int par) {
   Scalars* s = pr.s;
   if (s->done || !s->pcg_active) return;
   const int pl = (int)pr.plane;
@@ -1633,20 +1806,54 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __
   src[4] = UPD ? pr.m : nullptr;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   F2x2 acc = f2x2_zero();
-  pois_issue<NRAW_PA>(sm.raw[0], sm.mk[0], src, pr, tiles[ch.begin], tid);
+  // tiles arrive by tensor copies (one thread issues them) on the PCG path
+  // (the kernel checked tma_ready), by cp.async (every thread) for a caller's p
+  constexpr bool tma = UPD;
+  // raw planes r0..r3, M^-1, p_old0..p_old3, all in the slab
+  auto plane = [&](int k, int& z, int& m) {
+    m = 0;
+    z = k < 4 ? zslab(pr, 0) + k : k == 4 ? zslab(pr, 1) : (use_beta ? zslab(pr, 2) + (par & 1) * 4 + k - 5 : -1);
+  };
+  if (tma && tid == 0) {
+    mbar_init(&sm.bar[0]);
+    mbar_init(&sm.bar[1]);
+  }
+  __syncthreads();
+  auto issue = [&](int slot, int tc) {
+    if (tma) {
+      if (tid == 0)
+        tile_tma<NRAW_PA>(sm.slot[slot].raw, &sm.slot[slot].mk, plane, true, pr, tile_x0(tc, W4), tile_y0(tc),
+                          &sm.bar[slot]);
+    } else {
+      pois_issue<NRAW_PA>(sm.slot[slot].raw, sm.slot[slot].mk.v, src, pr, tc, tid);
+    }
+  };
+  unsigned ph = 0;     // bit b: parity of slot b's next phase
+  issue(0, tiles[ch.begin]);
   int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
   for (int t = ch.begin, b = 0; t < ch.end; ++t, b ^= 1) {
     const int tc = tiles[t];
     const int gx = tile_x0(tc, W4) + 4 * lane, gy = tile_y0(tc) + ty;
-    cp_async_wait_all();
-    __syncthreads();    // tile t landed; every thread is done with the other slot (tile t - 1)
+    const unsigned pb = (ph >> b) & 1u;
+    bool ok = true;
+    if (tma) {
+      ok = mbar_wait(&sm.bar[b], pb);
+      ph ^= 1u << b;
+    } else {
+      cp_async_wait_all();
+    }
+    // tile t landed; every thread is done with the other slot (tile t - 1)
+    if (__syncthreads_or(!ok)) {
+      staging_timeout(s, &sm.bar[b], pb);
+      return;
+    }
     if (t + 1 < ch.end) {
-      pois_issue<NRAW_PA>(sm.raw[b ^ 1], sm.mk[b ^ 1], src, pr, tn, tid);
+      issue(b ^ 1, tn);
       if (t + 2 < ch.end) tn = tiles[t + 2];
     }
     if (gy < pr.H)
-      pois_apply_quad<UPD>(sm.raw[b], sm.mk[b], pr, ty, lane, (long long)gy * pr.P + gx, use_beta, beta, beta2, lam,
-                           pout, pl, acc);
+      pois_apply_quad<UPD>(sm.slot[b].raw, sm.slot[b].mk.v, pr, ty, lane, (long long)gy * pr.P + gx, use_beta, beta,
+                           beta2, lam, pout, pl, acc);
   }
   if (publish_partials(part, blockIdx.x, f2x2_fold(acc), f2_zero(), &s->counter, pr.chunk_end - pr.chunk_begin)) {
     double pq, unused;
@@ -1664,10 +1871,24 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __
   }
 }
 
+template <bool UPD>
+__global__ void __launch_bounds__(NT, 2) k_poisson_apply_wide(const GridProb* __restrict__ probs,
+    const Chunk* __restrict__ chunks, const int* __restrict__ tiles, double* __restrict__ part,
+    const float* __restrict__ p_in_override, int par) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  PoisWideSmem& sm = *reinterpret_cast<PoisWideSmem*>(dyn_smem);
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  pdl_begin();
+  // the fused update (the PCG path) stages by tensor copies, a caller's p
+  // (the J^T J p hook, UPD = false) by cp.async
+  if (!UPD || tma_ready(pr, &sm)) k_poisson_apply_wide_body<UPD>(sm, ch, pr, tiles, part, p_in_override, par);
+}
+
 // PCGInit on the thread's own quad of a staged Poisson tile (slot raw / mk):
 // J^T F, diag(J^T J), M^-1 and the LM diagonal of the free pixels, r = -J^T F
 // and delta = 0 stored, r.z and the energy of the own residuals accumulated.
-__device__ __forceinline__ void pois_init_quad(const float (*raw)[HH][SP], const unsigned char (*mk)[SPB],
+__device__ __forceinline__ void pois_init_quad(const PlaneT* raw, const unsigned char (*mk)[SPB],
                                                const GridProb& pr, int ty, int lane, int x0, int gx, int gy,
                                                float lam, float dmin, float dmax, int pl,
                                                F2x2& acc_rz, F2x2& acc_E) {
@@ -1707,15 +1928,15 @@ __device__ __forceinline__ void pois_init_quad(const float (*raw)[HH][SP], const
   // one channel at a time: J^T F_i = S_i Y_i - sum_j w_j Y_j, with Y = X - T
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float4 xo = lds4(&raw[k][ty + 1][c]), go = lds4(&raw[4 + k][ty + 1][c]);
+    const float4 xo = lds4(&raw[k].v[ty + 1][c]), go = lds4(&raw[4 + k].v[ty + 1][c]);
     const float4 O = swz4(cat4(sub2(lo2(xo), lo2(go)), sub2(hi2(xo), hi2(go))));
-    const float4 xu = lds4(&raw[k][ty][c]), gu = lds4(&raw[4 + k][ty][c]);
+    const float4 xu = lds4(&raw[k].v[ty][c]), gu = lds4(&raw[4 + k].v[ty][c]);
     const float4 U = swz4(cat4(sub2(lo2(xu), lo2(gu)), sub2(hi2(xu), hi2(gu))));
-    const float4 xd = lds4(&raw[k][ty + 2][c]), gd = lds4(&raw[4 + k][ty + 2][c]);
+    const float4 xd = lds4(&raw[k].v[ty + 2][c]), gd = lds4(&raw[4 + k].v[ty + 2][c]);
     const float4 D = swz4(cat4(sub2(lo2(xd), lo2(gd)), sub2(hi2(xd), hi2(gd))));
     float L = __shfl_up_sync(0xffffffffu, O.w, 1), R = __shfl_down_sync(0xffffffffu, O.x, 1);
-    if (lane == 0) L = raw[k][ty + 1][3] - raw[4 + k][ty + 1][3];
-    if (lane == 31) R = raw[k][ty + 1][4 + W4] - raw[4 + k][ty + 1][4 + W4];
+    if (lane == 0) L = raw[k].v[ty + 1][3] - raw[4 + k].v[ty + 1][3];
+    if (lane == 31) R = raw[k].v[ty + 1][4 + W4] - raw[4 + k].v[ty + 1][4 + W4];
     const float2 aL = make_float2(L, O.z), aR = hi2(O), bL = lo2(O), bR = make_float2(O.y, R);
     const float2 aU = lo2(U), aD = lo2(D), bU = hi2(U), bD = hi2(D);
     const float2 nA = fma2(waL, aL, fma2(waR, aR, fma2(waU, aU, mul2(waD, aD))));
@@ -1751,41 +1972,51 @@ __device__ __forceinline__ void pois_init_quad(const float (*raw)[HH][SP], const
   f2x2_add(acc_E, eb);
 }
 
-__global__ void __launch_bounds__(NT, 2) k_poisson_init_wide(const GridProb* __restrict__ probs,
-                                                             const Chunk* __restrict__ chunks,
-                                                             const int* __restrict__ tiles,
-                                                             double* __restrict__ part, int k_outer,
-                                                             float dmin, float dmax) {
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
-  PoisInitSmem& sm = *reinterpret_cast<PoisInitSmem*>(dyn_smem);
-  const Chunk ch = chunks[blockIdx.x];
-  const GridProb pr = probs[ch.prob];
-  pdl_begin();
+__device__ __forceinline__ void k_poisson_init_wide_body(PoisInitSmem& sm, const Chunk& ch, const GridProb& pr,
+    const int* __restrict__ tiles, double* __restrict__ part, int k_outer, float dmin, float dmax) {
   Scalars* s = pr.s;
   if (s->done) return;
   const int pl = (int)pr.plane;
   const float lam = pr.lm ? s->lambda_f : 0.0f;
-  const float* src[NRAW_PI];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    src[k] = pr.x + k * pl;
-    src[4 + k] = pr.c + k * pl;
-  }
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   F2x2 acc_rz = f2x2_zero(), acc_E = f2x2_zero();
-  pois_issue<NRAW_PI>(sm.raw[0], sm.mk[0], src, pr, tiles[ch.begin], tid);
+  // raw planes by tensor copies (the kernel checked tma_ready): X0..X3 (the
+  // unknowns), T0..T3 (guidance, in the slab)
+  auto plane = [&](int k, int& z, int& m) {
+    m = k < 4 ? 1 : 0;
+    z = k < 4 ? k : zslab(pr, 4) + k - 4;
+  };
+  if (tid == 0) {
+    mbar_init(&sm.bar[0]);
+    mbar_init(&sm.bar[1]);
+  }
+  __syncthreads();
+  auto issue = [&](int slot, int tc) {
+    if (tid == 0)
+      tile_tma<NRAW_PI>(sm.slot[slot].raw, &sm.slot[slot].mk, plane, true, pr, tile_x0(tc, W4), tile_y0(tc),
+                        &sm.bar[slot]);
+  };
+  unsigned ph = 0;     // bit b: parity of slot b's next phase
+  issue(0, tiles[ch.begin]);
   int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
   for (int t = ch.begin, b = 0; t < ch.end; ++t, b ^= 1) {
     const int tc = tiles[t];
     const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
     const int gx = x0 + 4 * lane, gy = y0 + ty;
-    cp_async_wait_all();
-    __syncthreads();    // tile t landed; every thread is done with the other slot (tile t - 1)
+    const unsigned pb = (ph >> b) & 1u;
+    const bool ok = mbar_wait(&sm.bar[b], pb);
+    ph ^= 1u << b;
+    // tile t landed; every thread is done with the other slot (tile t - 1)
+    if (__syncthreads_or(!ok)) {
+      staging_timeout(s, &sm.bar[b], pb);
+      return;
+    }
     if (t + 1 < ch.end) {
-      pois_issue<NRAW_PI>(sm.raw[b ^ 1], sm.mk[b ^ 1], src, pr, tn, tid);
+      issue(b ^ 1, tn);
       if (t + 2 < ch.end) tn = tiles[t + 2];
     }
-    if (gy < pr.H) pois_init_quad(sm.raw[b], sm.mk[b], pr, ty, lane, x0, gx, gy, lam, dmin, dmax, pl, acc_rz, acc_E);
+    if (gy < pr.H)
+      pois_init_quad(sm.slot[b].raw, sm.slot[b].mk.v, pr, ty, lane, x0, gx, gy, lam, dmin, dmax, pl, acc_rz, acc_E);
   }
   if (publish_partials(part, blockIdx.x, f2x2_fold(acc_rz), f2x2_fold(acc_E), &s->counter,
                        pr.chunk_end - pr.chunk_begin)) {
@@ -1800,6 +2031,17 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_init_wide(const GridProb* __r
       if (!isfinite(rz) || !isfinite(E)) s->nonfinite = 1;
     }
   }
+}
+
+__global__ void __launch_bounds__(NT, 2) k_poisson_init_wide(const GridProb* __restrict__ probs,
+    const Chunk* __restrict__ chunks, const int* __restrict__ tiles, double* __restrict__ part, int k_outer,
+    float dmin, float dmax) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  PoisInitSmem& sm = *reinterpret_cast<PoisInitSmem*>(dyn_smem);
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  pdl_begin();
+  if (tma_ready(pr, &sm)) k_poisson_init_wide_body(sm, ch, pr, tiles, part, k_outer, dmin, dmax);
 }
 
 // Degree plane of a wide Poisson problem: S_i + 1 on a free pixel i, where
@@ -2005,12 +2247,19 @@ __global__ void __launch_bounds__(NT, 2) k_warp_pcg_coop(const GridProb* __restr
                                                          const int* __restrict__ tiles,
                                                          double* __restrict__ part, GridBarrier* gb,
                                                          int par0, int n_inner) {
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
   WideSmem& sm = *reinterpret_cast<WideSmem*>(dyn_smem);
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
+  if (threadIdx.x == 0) mbar_init(&sm.bar);
+  __syncthreads();
+  unsigned phase = 0;
+  const bool tma = wide_tma(pr, &sm);
   for (int it = 0; it < n_inner; ++it) {
-    apply_wide_body<MASK>(sm, ch, pr, tiles, part, nullptr, par0 + it, 1);
+    if (tma)
+      apply_wide_body<MASK, true>(sm, ch, pr, tiles, part, nullptr, par0 + it, 1, phase);
+    else
+      apply_wide_body<MASK, false>(sm, ch, pr, tiles, part, nullptr, par0 + it, 1, phase);
     if (!grid_sync(gb, gridDim.x)) return;
     update_body<3>(ch, pr, tiles, part, par0 + it);
     if (it + 1 < n_inner && !grid_sync(gb, gridDim.x)) return;
@@ -2199,6 +2448,24 @@ __global__ void k_barrier_selftest(GridBarrier* gb, unsigned int expected, int r
                                    unsigned long long limit_ns) {
   for (int r = 0; r < rounds; ++r)
     if (!grid_sync(gb, expected, limit_ns)) return;
+}
+
+// Self-test of the bounded staging wait: complete = 1 arrives on the
+// mbarrier (no bytes expected), so the phase completes; complete = 0 leaves
+// it pending, so every thread's wait runs out after limit_ns.  *out = 1 if
+// any wait ran out.
+__global__ void k_staging_selftest(int complete, unsigned long long limit_ns, int* out) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
+  if (complete && threadIdx.x == 0) mbar_expect(&bar, 0u);
+  const bool ok = mbar_wait(&bar, 0u, limit_ns);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) *out = 1;
+}
+
+cudaError_t launch_staging_selftest(int complete, unsigned long long limit_ns, int* out, cudaStream_t st) {
+  k_staging_selftest<<<2, NT, 0, st>>>(complete, limit_ns, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_barrier_selftest(GridBarrier* gb, int nblocks, unsigned int expected, int rounds,

@@ -41,6 +41,10 @@ constexpr int TH = 8;             // grid tile height (pixels)
 constexpr int NT = 256;           // threads per block (grid and graph kernels)
 constexpr int HW = TW + 2;        // staged halo width
 constexpr int HH = TH + 2;        // staged halo height
+// 128-pixel tiles: the staged box of a float plane (columns x0 - 4 .. x0 + 131)
+// and of the byte plane (columns x0 - 16 .. x0 + 143), HH rows each
+constexpr int WIDE_BOX_W = 136;
+constexpr int WIDE_BYTE_BOX_W = 160;
 constexpr int VT = 256;           // vertices per vertex tile (graph)
 // capacities of the tiled ARAP-mesh apply (one tile of VT vertices per pass):
 // out-of-tile neighbours staged with the tile, and J_e p slots (the tile's
@@ -73,7 +77,9 @@ struct __align__(16) Scalars {
   int converged;
   int nonfinite;      // a non-finite scalar was produced
   unsigned int counter;   // last-block counter
-  unsigned int pad1[3];
+  unsigned int timeout;   // a bounded wait for a tensor copy ran out (the solve reports OPT_ERR_TIMEOUT)
+  unsigned int misaligned;  // a staging area could not take tensor copies (the solve reports OPT_ERR_CUDA)
+  unsigned int pad1;
   double alpha_d;     // float64 solver: alpha = rz / pq
   double beta_d;      // float64 solver: beta  = rz' / rz
 };
@@ -101,6 +107,14 @@ struct GridProb {
   // (row, tile column), bit l for the quad at x = 128 tx + 4 l (NULL: all);
   // the vector update skips the others
   const unsigned int* live;
+  // tw = 128: tensor maps (CUtensorMap, 128 bytes each) of the planes the wide
+  // kernels stage: [0] the float slab (3-D: P x H x planes), [1] the unknowns
+  // (3-D: P x H x nx), [2] the byte plane (2-D: mask, or the Poisson degree
+  // plane; absent for an unmasked warp); NULL: staged with cp.async
+  const unsigned long long* tmap;
+  // slab plane index (6 bits each) of r, M^-1, p (parity 0), cos / sin and
+  // the constants: zpack = z_r | z_m << 6 | z_p << 12 | z_csn << 18 | z_c << 24
+  int zpack;
   float *d, *r, *p, *q;         // PCG vectors
   float *m, *dc;                // M^-1 and LM diagonal (distinct-diagonal planes)
   float* csn;                   // warp, tw = 128: cos / sin of theta (2 planes, written by PCGInit)

@@ -63,6 +63,8 @@ void launch_pois_sdeg(int W, int H, int P, const uint8_t* mask, uint8_t* out, cu
 // of n_inner PCG iterations (applyJTJ + update) starting at parity par0.
 int grid_coop_capacity(int masked);
 cudaError_t launch_grid_pcg_coop(const GridLaunch& L, GridBarrier* gb, int par0, int n_inner);
+// bounded staging-wait self-test (complete = 0: the wait runs out)
+cudaError_t launch_staging_selftest(int complete, unsigned long long limit_ns, int* out, cudaStream_t st);
 cudaError_t launch_barrier_selftest(GridBarrier* gb, int nblocks, unsigned int expected, int rounds,
                                     unsigned long long limit_ns, cudaStream_t st);
 

@@ -260,7 +260,7 @@ opt_status opt_server_step(opt_server* s, int32_t* n_active, int32_t* n_queued) 
       const Scalars& t = s->sbuf[i];
       r->hist.push_back(t.E);
       const bool capped = t.outer_done >= s->prm.outer;
-      if (!t.done && !capped && !t.nonfinite) {
+      if (!t.done && !capped && !t.nonfinite && !t.timeout && !t.misaligned) {
         keep.push_back(r);
         continue;
       }
@@ -277,7 +277,7 @@ opt_status opt_server_step(opt_server* s, int32_t* n_active, int32_t* n_queued) 
       opt_status ws = write_back(r->pb, s->st);
       cudaStreamSynchronize(s->st);
       std::lock_guard<std::mutex> lk(s->mu);
-      finish(s, r, t.nonfinite ? OPT_ERR_NUMERIC : ws);
+      finish(s, r, t.timeout ? OPT_ERR_TIMEOUT : t.misaligned ? OPT_ERR_CUDA : (t.nonfinite ? OPT_ERR_NUMERIC : ws));
       s->dirty = true;
     }
     s->active.swap(keep);

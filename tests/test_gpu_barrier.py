@@ -1,6 +1,6 @@
-"""The grid-wide barrier of the persistent PCG loop never waits without
-bound: a barrier that cannot complete gives up, reports a timeout and leaves
-the context usable."""
+"""The grid-wide barrier of the persistent PCG loop and the mbarrier wait of
+the tensor-copy staging never wait without bound: a wait that cannot complete
+gives up, reports a timeout and leaves the context usable."""
 import ctypes
 import time
 
@@ -45,3 +45,22 @@ def test_barrier_wait_is_bounded_and_context_survives(api):
     g = api.Problem(prob)
     r = g.solve_gn(2, 6, persistent=1)
     assert r["status"] == "OPT_OK"
+
+
+def test_staging_wait_is_bounded_and_context_survives(api):
+    lib = api.load_library()
+    t = ctypes.c_int32(-1)
+    assert lib.opt_selftest_staging_wait(1, ctypes.byref(t)) == 0
+    assert t.value == 0
+    t0 = time.perf_counter()
+    assert lib.opt_selftest_staging_wait(0, ctypes.byref(t)) == 0
+    assert t.value == 1
+    assert time.perf_counter() - t0 < 10.0
+    assert lib.opt_selftest_staging_wait(2, ctypes.byref(t)) == 1
+    assert lib.opt_selftest_staging_wait(1, None) == 1
+    # the context still runs a solve staged by tensor copies (128-pixel tiles)
+    prob = synth.poisson_problem(300, 40, seed=172)
+    g = api.Problem(prob, tile_w=128)
+    rep = g.solve_gn(2, 5)
+    assert rep["E_history"][-1] < rep["E_history"][0]
+    g.close()
