@@ -1052,7 +1052,7 @@ def run_profile_batch():
     return 0
 
 
-def run_profile_case(name):
+def run_profile_case(name, chunking_pin=None):
     """One autotuned problem, its PCGInit once and three PCG iterations (the
     launches an ncu capture selects from); prints the per-kernel times."""
     import torch
@@ -1069,7 +1069,13 @@ def run_profile_case(name):
         chunking = None
     else:
         gp = api.Problem(builder(synth))
-        chunking, _ = gp.autotune()
+        if chunking_pin is not None:
+            # pinned granularity, planned tile width: under ncu's serialised
+            # replay the autotuner's own timings would mislead it
+            gp.set_chunking(chunking_pin)
+            chunking = chunking_pin
+        else:
+            chunking, _ = gp.autotune()
         if form is not None:
             gp.set_apply_form(form)
     if materialized:
@@ -1111,7 +1117,7 @@ def main():
                     help="run one small profiling workload (for ncu captures) instead of the benchmark")
     args = ap.parse_args()
     if args.profile:
-        return run_profile_case(args.profile)
+        return run_profile_case(args.profile, args.chunking)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
