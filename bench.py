@@ -45,6 +45,11 @@ W_BENCH, H_BENCH, HANDLES, OUTER, INNER = 1024, 1024, 64, 20, 20
 BYTES_APPLY_WARP = 72      # read r 12, M^-1 8, p_old 12, cos/sin 8, UrShape 8; write p 12, q 12
 BYTES_UPDATE_WARP = 80     # read delta 12, p 12, r 12, q 12, M^-1 8; write delta 12, r 12
 BYTES_INIT_WARP = 60       # read x 12, UrShape 8; write r 12, M^-1 8, delta 12, cos/sin 8 (GN)
+# single-reduction PCG iteration (pcg_form = 1), one launch per PCG iteration
+BYTES_FUSED_WARP = 120     # read z 12, w 12, p_old 12, cos/sin 8, UrShape 8, M^-1 8, delta 12;
+#                            write z 12, w 12, p 12, delta 12
+BYTES_FIN_WARP = 36        # the last iteration's step: read delta 12, p 12; write delta 12
+PCG_FORM = 1               # the headline's PCG iteration: 1 single-reduction, 0 two-pass
 # Poisson, per free pixel (4 channels, one M^-1 plane)
 BYTES_APPLY_POISSON = 69   # read r 16, M^-1 4, p_old 16, mask 1; write p 16, q 16
 BYTES_UPDATE_POISSON = 100  # read delta 16, p 16, r 16, q 16, M^-1 4; write delta 16, r 16
@@ -359,7 +364,9 @@ def kernel_roofline(gp, kernels, units, peak, iters=20):
 
 
 def roofline_for(api, synth, torch, W, H, peak, iters=20):
-    """Per-kernel roofline of the matrix-free ARAP warp at W x H."""
+    """Per-kernel roofline of the matrix-free ARAP warp at W x H: the PCG
+    iteration the headline runs (single-reduction on 128-pixel tiles) and
+    the two-pass form's kernels beside it."""
     prob = synth.warp_problem(W, H, max(8, int(round(64.0 * W * H / 2 ** 20))), seed=synth.BASE_SEED)
     gp = api.Problem(prob)
 
@@ -368,7 +375,19 @@ def roofline_for(api, synth, torch, W, H, peak, iters=20):
         return (("k_warp_init_wide" if wide else "k_warp_init", BYTES_INIT_WARP, OUTER),
                 ("k_warp_apply_wide" if wide else "k_warp_apply", BYTES_APPLY_WARP, OUTER * INNER),
                 ("k_grid_update<3>", BYTES_UPDATE_WARP, OUTER * INNER))
-    out, cfg = kernel_roofline(gp, names, W * H, peak, iters)
+    two_pass, cfg = kernel_roofline(gp, names, W * H, peak, iters)
+    out = two_pass
+    if PCG_FORM == 1 and cfg["tile_w"] == 128:
+        gp.profile_pcg_fused(4)
+        times = gp.profile_pcg_fused(iters)
+        out = {}
+        for (name, bpu, per_solve), ms in zip((("k_warp_init_wide", BYTES_INIT_WARP, OUTER),
+                                               ("k_warp_fused_wide", BYTES_FUSED_WARP, OUTER * INNER),
+                                               ("k_warp_fused_fin", BYTES_FIN_WARP, OUTER)), times):
+            ach = bpu * W * H / (ms * 1e-3) / 1e9
+            out[name] = {"ms": ms, "bytes": bpu * W * H, "achieved": ach, "frac": ach / peak,
+                         "launches_per_solve": per_solve}
+        cfg = dict(cfg, pcg_form=1, two_pass_kernels=two_pass)
     gp.close()
     del prob
     torch.cuda.empty_cache()
@@ -702,7 +721,7 @@ def run_ours(args):
     def one_step():
         flush.zero_()
         gp.x.copy_(x0)
-        return gp.solve_gn(OUTER, INNER)
+        return gp.solve_gn(OUTER, INNER, pcg_form=PCG_FORM)
 
     for _ in range(max(3, args.warmup)):
         one_step()
@@ -735,7 +754,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         gp.x.copy_(host_in, non_blocking=True)
-        r = gp.solve_gn(OUTER, INNER)
+        r = gp.solve_gn(OUTER, INNER, pcg_form=PCG_FORM)
         host_out.copy_(gp.x, non_blocking=True)
         torch.cuda.synchronize()
         if i >= args.warmup:
@@ -744,7 +763,7 @@ def run_ours(args):
     nbytes = host_in.numel() * 4
 
     # roofline of the dominant kernel, timed live at the bench size and beyond L2
-    roof, _ = roofline_for(api, synth, torch, W_BENCH, H_BENCH, peak)
+    roof, roof_cfg = roofline_for(api, synth, torch, W_BENCH, H_BENCH, peak)
     dom = max(roof, key=lambda k: roof[k]["ms"] * roof[k]["launches_per_solve"])   # largest share of a solve
     roof_big, extra = {}, {}
     checks, cpu_base, cpu_all = {}, None, None
@@ -790,6 +809,12 @@ def run_ours(args):
                 out.append(fn(OUTER, INNER, **kw))
             return out[1:]
 
+        # the two-pass PCG iteration on the headline workload
+        rr_tp = timed(gp, x0, gp.solve_gn, n=5, pcg_form=0)
+        ms_tp = statistics.median(r_["ms"] for r_ in rr_tp)
+        extra["warp_1024x1024_two_pass_gn20x20"] = {
+            "pcg_iters_per_s": OUTER * INNER / (ms_tp / 1e3), "ms_per_solve": ms_tp,
+            "E_final": rr_tp[-1]["E_final"], "E_final_rel_diff_vs_headline": rel_err(rr_tp[-1]["E_final"], E_final)}
         rr_mat = timed(gp, x0, gp.solve_gn, materialized=1)
         ms_mat = statistics.median(r_["ms"] for r_ in rr_mat)
         extra["warp_1024x1024_materialized_gn20x20"] = {
@@ -953,7 +978,8 @@ def run_ours(args):
                              f"sum of per-member CPU seconds",
                    "gpu_batched_solves_per_s": extra["batched_512_warps_gn10x10"]["batched_solves_per_s"]}
 
-    launches_per_step = 2 + OUTER * (2 + 2 * INNER)
+    fused = PCG_FORM == 1 and head_cfg["tile_w"] == 128
+    launches_per_step = 2 + OUTER * ((3 + INNER) if fused else (2 + 2 * INNER))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -963,13 +989,16 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "flushed between steps (512 MB write)", "precision": "f32 vectors, f64 dots/energies",
                    "chunking": chunking, "tile_w": head_cfg["tile_w"],
+                   "pcg_form": ("single-reduction: one launch per PCG iteration (p.q, q.z, q.M^-1 q, r.z in "
+                                "one reduction)" if fused else "two-pass: applyJTJ + vector update"),
                    "chunking_meaning": "n > 0: n tiles per block; n < 0: balanced over -n blocks per SM",
                    "E_final": E_final, "wall_s": wall},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": roof[dom]["achieved"], "peak": peak,
                      "unit": "GB/s", "frac": roof[dom]["frac"],
                      "traffic": ncu_traffic(dom, "warp1024"),
                      "algorithmic_bytes_per_launch": roof[dom]["bytes"], "ms_per_launch": roof[dom]["ms"],
-                     "peak_source": f"{peak_src} hbm_gbs", "kernels": roof},
+                     "peak_source": f"{peak_src} hbm_gbs", "kernels": roof,
+                     "two_pass_kernels": roof_cfg.get("two_pass_kernels")},
         "roofline_beyond_l2": {"bound": "hbm", "peak": peak, "unit": "GB/s", "peak_source": f"{peak_src} hbm_gbs",
                                "workloads": roof_big},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},

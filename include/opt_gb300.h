@@ -191,6 +191,18 @@ typedef struct {
                                  programmatic dependent launch).  Same arithmetic either way.  A
                                  barrier wait is bounded (1 s): OPT_ERR_TIMEOUT. */
     void* stream;             /* cudaStream_t; NULL = legacy default stream */
+    int32_t pcg_form;         /* 0 (default) = the two-pass Jacobi-PCG iteration of Sec. 4.1
+                                 (applyJTJ with p.q, then the vector update with r.z: two
+                                 grid-wide reductions, two launches per iteration).
+                                 1 = single-reduction iteration, taken by matrix-free solves of
+                                 OPT_ARAP_WARP_2D grids planned with 128-pixel tiles (other
+                                 problems run form 0): one launch per iteration computes p.q,
+                                 q.z and q.M^-1 q, from which alpha and the next r.z follow
+                                 (r.z' = r.z - 2 alpha q.z + alpha^2 q.M^-1 q), and carries
+                                 z = M^-1 r and w = M^-1 q instead of r and q.  The same
+                                 iterates in exact arithmetic; in float32 they differ from form 0
+                                 by rounding.  Batches and the server run form 0.  Other values:
+                                 OPT_ERR_INVALID_ARG. */
 } opt_solve_params;
 
 /* Result of a solve.  E_history, when not NULL, is a host array of at least
@@ -309,6 +321,17 @@ opt_status opt_eval_energy(opt_problem* prob, double* energy);
  * direction update), ms[2] = vector update.  ms: host, 3 floats.  Leaves the
  * PCG state as opt_pcg_init + opt_pcg_step would (lambda = 0). */
 opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, float* ms);
+
+/* Measurement hook of the single-reduction PCG iteration (pcg_form = 1 of
+ * opt_solve_params; the Jacobi-PCG of Sec. 4.1 with one reduction per
+ * iteration): PCGInit, n_iters (>= 2) single-reduction iterations and the
+ * final step, each launch bracketed by CUDA events on `stream`; writes ms[0]
+ * = PCGInit, ms[1] = mean of iterations 1 .. n_iters - 1 (iteration 0 reads
+ * r and M^-1 instead of z and w), ms[2] = the final step (host, 3 floats).
+ * OPT_ERR_INVALID_ARG unless the problem is an OPT_ARAP_WARP_2D grid planned
+ * with 128-pixel tiles, or n_iters < 2.  Leaves delta = the PCG step after
+ * n_iters iterations (lambda = 0). */
+opt_status opt_profile_pcg_fused(opt_problem* prob, int32_t n_iters, void* stream, float* ms);
 
 /* Work granularity of the problem's kernels.  units_per_block > 0: that many
  * consecutive tiles (grid) or 256-vertex tiles and units_per_block * 256 edges

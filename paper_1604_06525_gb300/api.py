@@ -69,7 +69,8 @@ class SolveParams(ctypes.Structure):
                 ("lambda_min", c_double), ("lambda_max", c_double), ("diag_min", c_double),
                 ("diag_max", c_double), ("eta", c_double), ("rel_tol", c_double),
                 ("use_precond", c_int32), ("materialized", c_int32), ("use_graph", c_int32),
-                ("tile_w", c_int32), ("persistent", c_int32), ("stream", c_void_p)]
+                ("tile_w", c_int32), ("persistent", c_int32), ("stream", c_void_p),
+                ("pcg_form", c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -96,6 +97,7 @@ _SIGNATURES = [
     ("opt_eval_jtf", c_int32, [c_void_p, c_void_p, c_void_p, POINTER(c_double)]),
     ("opt_eval_energy", c_int32, [c_void_p, POINTER(c_double)]),
     ("opt_profile_pcg", c_int32, [c_void_p, c_int32, c_void_p, POINTER(c_float)]),
+    ("opt_profile_pcg_fused", c_int32, [c_void_p, c_int32, c_void_p, POINTER(c_float)]),
     ("opt_problem_set_chunking", c_int32, [c_void_p, c_int32]),
     ("opt_problem_autotune", c_int32, [c_void_p, POINTER(c_int32), POINTER(c_float)]),
     ("opt_problem_info", c_int32, [c_void_p, POINTER(c_int64), POINTER(c_int32), POINTER(c_int64)]),
@@ -429,6 +431,15 @@ class Problem:
         ms = (c_float * 3)()
         st = torch.cuda.current_stream(self.device).cuda_stream
         _check(self.lib.opt_profile_pcg(self.h, n_iters, st, ms), "opt_profile_pcg")
+        return ms[0], ms[1], ms[2]
+
+    def profile_pcg_fused(self, n_iters: int) -> tuple:
+        """Mean device ms of (PCGInit, one single-reduction PCG iteration,
+        the final step) for a wide-tile warp."""
+        import torch
+        ms = (c_float * 3)()
+        st = torch.cuda.current_stream(self.device).cuda_stream
+        _check(self.lib.opt_profile_pcg_fused(self.h, n_iters, st, ms), "opt_profile_pcg_fused")
         return ms[0], ms[1], ms[2]
 
     def set_chunking(self, units_per_block: int):

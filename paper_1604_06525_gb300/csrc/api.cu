@@ -340,16 +340,26 @@ bool use_persistent(const opt_problem* pb, const opt_solve_params& p) {
   return p.persistent && !p.materialized && p.inner > 0 && pb->d_gbar && pb->nchunks <= pb->coop_cap;
 }
 
+// The single-reduction PCG iteration runs where asked for on wide-tile warps
+// (planned with z / w buffers), matrix-free; elsewhere the two-pass form.
+bool use_fused(const opt_problem* pb, const opt_solve_params& p) {
+  return p.pcg_form == 1 && !p.materialized && pb->kind == K_WARP && pb->hg.zb != nullptr;
+}
+
 opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cudaStream_t st) {
   const float dmin = (float)p.diag_min, dmax = (float)p.diag_max;
   CKS(copy_planes_in(pb, pb->x, pb->user_x, pb->nx, st));
   k_reset<<<1, 32, 0, st>>>(pb->d_s, 1, lm ? p.lambda0 : 0.0);
-  const bool coop = use_persistent(pb, p);
+  const bool fused = use_fused(pb, p) && p.inner > 0;
+  const bool coop = !fused && use_persistent(pb, p);
   if (coop) CK(cudaMemsetAsync(pb->d_gbar, 0, sizeof(GridBarrier), st));
   for (int k = 0; k < p.outer; ++k) {
     st_init(pb, st, k, dmin, dmax);
     if (p.materialized) csr_evalj(pb, st, p.materialized);
-    if (coop) {
+    if (fused) {
+      for (int i = 0; i < p.inner; ++i) launch_grid_fused(grid_launch(pb, st), i);
+      launch_grid_fused_fin(grid_launch(pb, st), p.inner);
+    } else if (coop) {
       // the barrier's counter restarts at 0 (a timed-out launch may leave it
       // mid-count); its timeout flag accumulates over the solve
       CK(cudaMemsetAsync(&pb->d_gbar->count, 0, sizeof(unsigned int), st));
@@ -377,7 +387,8 @@ opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cu
 
 std::vector<double> graph_key(const opt_solve_params& p, bool lm, cudaStream_t) {
   return {double(p.outer), double(p.inner), double(lm), double(p.use_precond), p.lambda0, p.lambda_min,
-          p.lambda_max, p.diag_min, p.diag_max, p.eta, p.rel_tol, double(p.materialized), double(p.persistent)};
+          p.lambda_max, p.diag_min, p.diag_max, p.eta, p.rel_tol, double(p.materialized), double(p.persistent),
+          double(p.pcg_form)};
 }
 
 opt_status ensure_ehist(opt_problem* pb, int n) {
@@ -401,6 +412,7 @@ opt_status run_solve(opt_problem* pb, const opt_solve_params* prm_in, opt_report
   else opt_solve_params_default(&p);
   CKS(check_params(p, lm));
   if (p.materialized < 0 || p.materialized > 2) return OPT_ERR_INVALID_ARG;
+  if (p.pcg_form < 0 || p.pcg_form > 1) return OPT_ERR_INVALID_ARG;
   if (p.materialized && (pb->kind == K_WARPG || pb->kind == K_EMBED)) return OPT_ERR_INVALID_ARG;   // no CSR form
   if (p.materialized) CKS(csr_build(pb, p.materialized));
   cudaStream_t st = (cudaStream_t)p.stream;
@@ -740,8 +752,10 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   // multiples of 32 floats, so every plane stays 128-byte aligned)
   const bool has_csn = warp && tw == 128;
   const bool has_sdeg = !warp && tw == 128;
-  const size_t nslab = (size_t)(nx + nm + 2 * nx + nx + nx + (has_csn ? 2 : 0) + nc) * pl + (d->mask ? pl / 4 : 0) +
-                       (has_sdeg ? pl / 4 : 0);
+  // wide warps: the single-reduction PCG's double-buffered z and w planes
+  const int nzw = has_csn ? 4 * nx : 0;
+  const int nfp = nx + nm + 2 * nx + nx + nx + (has_csn ? 2 : 0) + nc + nzw;
+  const size_t nslab = (size_t)nfp * pl + (d->mask ? pl / 4 : 0) + (has_sdeg ? pl / 4 : 0);
   float* slab = nullptr;
   CKS(dalloc(q, &slab, nslab));
   float* cur = slab;
@@ -753,6 +767,8 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   q->dvec = take(nx * pl);
   float* csn = has_csn ? take(2 * pl) : nullptr;
   c = take(nc * pl);
+  float* zb = nzw ? take(2 * nx * pl) : nullptr;
+  float* wb = nzw ? take(2 * nx * pl) : nullptr;
   if (d->mask) dmask = reinterpret_cast<uint8_t*>(take(pl / 4));
   uint8_t* dsdeg = has_sdeg ? reinterpret_cast<uint8_t*>(take(pl / 4)) : nullptr;
   if (has_csn) {
@@ -795,7 +811,7 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   CKS(upload(q->d_chunks, chunks));
   q->h_chunks = chunks;
   q->nchunks = (int)chunks.size();
-  CKS(dalloc(q, &q->d_part, 2 * chunks.size()));
+  CKS(dalloc(q, &q->d_part, 4 * chunks.size()));   // up to three partials per chunk
   CKS(dalloc(q, &q->dg, 1));
   for (int k = 0; k < nx; ++k) q->user_x[k] = d->unknowns[k];
   q->h_mask = mask;
@@ -823,8 +839,10 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   g.tmap = nullptr;
   const auto zof = [&](const float* ptr) { return ptr ? (int)((ptr - slab) / (ptrdiff_t)pl) : -1; };
   g.zpack = zof(q->rvec) | zof(m) << 6 | zof(q->pbuf) << 12 | (csn ? zof(csn) : 0) << 18 | zof(c) << 24;
-  if (tw == 128) CKS(make_grid_tmaps(q, slab, (int)(nx + nm + 2 * nx + nx + nx + (has_csn ? 2 : 0) + nc),
-                                     warp ? dmask : dsdeg));
+  g.zb = zb;
+  g.wb = wb;
+  g.zpack2 = zb ? (zof(zb) | zof(wb) << 6) : 0;
+  if (tw == 128) CKS(make_grid_tmaps(q, slab, nfp, warp ? dmask : dsdeg));
   g.d = q->dvec; g.r = q->rvec; g.p = q->pbuf; g.q = q->qvec; g.m = m; g.dc = dc;
   g.hbeg = dhbeg; g.hpix = dhpix; g.htgt = dhtgt;
   g.jtf_out = nullptr; g.diag_out = nullptr;
@@ -1342,6 +1360,57 @@ opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, flo
   return status;
 }
 
+opt_status opt_profile_pcg_fused(opt_problem* prob, int32_t n_iters, void* stream, float* ms) {
+  if (!prob || n_iters < 2 || !ms) return OPT_ERR_INVALID_ARG;
+  if (prob->kind != K_WARP || !prob->hg.zb) return OPT_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CKS(hook_prepare(prob, 0.0, false));
+  const int nev = 2 * (n_iters + 2);
+  std::vector<cudaEvent_t> ev(nev, nullptr);
+  opt_status status = OPT_OK;
+  for (int i = 0; i < nev && status == OPT_OK; ++i)
+    if (cudaEventCreate(&ev[i]) != cudaSuccess) status = OPT_ERR_CUDA;
+  if (status == OPT_OK) {
+    copy_planes_in(prob, prob->x, prob->user_x, prob->nx, st);
+    k_reset<<<1, 32, 0, st>>>(prob->d_s, 1, 0.0);
+    cudaEventRecord(ev[0], st);
+    st_init(prob, st, -1, 1e-6f, 1e32f);
+    cudaEventRecord(ev[1], st);
+    for (int i = 0; i < n_iters; ++i) {
+      cudaEventRecord(ev[2 + 2 * i], st);
+      launch_grid_fused(grid_launch(prob, st), i);
+      cudaEventRecord(ev[3 + 2 * i], st);
+    }
+    cudaEventRecord(ev[2 + 2 * n_iters], st);
+    launch_grid_fused_fin(grid_launch(prob, st), n_iters);
+    cudaEventRecord(ev[3 + 2 * n_iters], st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) status = cuda_fail(e, "opt_profile_pcg_fused");
+  }
+  if (status == OPT_OK) {
+    float t = 0.f, a = 0.f, f = 0.f;
+    cudaEventElapsedTime(&t, ev[0], ev[1]);
+    for (int i = 1; i < n_iters; ++i) {
+      float x = 0.f;
+      cudaEventElapsedTime(&x, ev[2 + 2 * i], ev[3 + 2 * i]);
+      a += x;
+    }
+    cudaEventElapsedTime(&f, ev[2 + 2 * n_iters], ev[3 + 2 * n_iters]);
+    ms[0] = t;
+    ms[1] = a / (n_iters - 1);
+    ms[2] = f;
+    prob->pcg_par = n_iters;
+    Scalars sc;
+    if (cudaMemcpy(&sc, prob->d_s, sizeof(Scalars), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      if (sc.timeout) status = OPT_ERR_TIMEOUT;
+      else if (sc.misaligned) status = OPT_ERR_CUDA;
+    }
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  return status;
+}
+
 // Vertex-tile tables of the tiled ARAP-mesh apply, built on first use (the
 // autotuner, opt_problem_set_apply_form) from the sorted edge list: per tile of
 // VT vertices the out-of-tile neighbours (halo), each edge's far end as an
@@ -1459,7 +1528,7 @@ static opt_status rechunk(opt_problem* pb, int per) {
                                         : make_chunks_balanced(pb->ntiles, target, 0);
     if ((int)chunks.size() > pb->nchunks) {
       CKS(dalloc(pb, &pb->d_chunks, chunks.size()));
-      CKS(dalloc(pb, &pb->d_part, 2 * chunks.size()));
+      CKS(dalloc(pb, &pb->d_part, 4 * chunks.size()));
     }
     CKS(upload(pb->d_chunks, chunks));
     pb->h_chunks = chunks;

@@ -947,6 +947,428 @@ __global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __res
     apply_wide_body<MASK, false>(sm, ch, pr, tiles, part, p_in_override, par, update, phase);
 }
 
+// ---------------------------------------------------------------------------
+// Single-reduction PCG iteration of the wide warp (tw = 128): one launch per
+// PCG iteration instead of applyJTJ + vector update.  The Jacobi-PCG of
+// Sec. 4.1 needs two grid-wide reductions per iteration (p.q for alpha, then
+// r.z for beta), so its update and the next direction normally sit in two
+// launches.  Here the kernel of iteration i forms, in one reduction, p.q,
+// q.z, q.M^-1 q and r.z (r = z / M^-1, the residual the stored z stands
+// for, in iteration 0 as well).  Its last block sets
+//   alpha_i = rz_i / pq_i,
+//   rz_{i+1} = (r_i - alpha_i q_i) . M^-1 (r_i - alpha_i q_i)
+//            = rz_i - 2 alpha_i (q_i . z_i) + alpha_i^2 (q_i . M^-1 q_i),
+//   beta_{i+1} = rz_{i+1} / rz_i
+// (the recurrence of single-synchronisation CG variants such as Chronopoulos
+// & Gear's; the same Krylov iterates as the two-pass form in exact
+// arithmetic).  The recurrence only sets beta: alpha always divides the r.z
+// measured on the stored vectors, so that once the residual reaches the
+// float32 rounding floor (where the recurrence is dominated by rounding) the
+// steps stay at rounding size.  The vector update of iteration i - 1 moves
+// into the kernel of iteration i, which forms on its tile and halo
+//   z_i = z_{i-1} - alpha_{i-1} w_{i-1}       (w = M^-1 q, so z = M^-1 r)
+//   p_i = z_i + beta_i p_{i-1}
+// and on its own pixels delta += alpha_{i-1} p_{i-1}, q_i = (J^T J + lambda D)
+// p_i, w_i = M^-1 q_i.  r and q themselves are never stored.  z, w and p are
+// double-buffered (halo reads of the previous iterate while other blocks
+// write the next).  Iteration 0 starts from r_0 and M^-1 (z_0 = M^-1 r_0, p_0
+// = z_0); the last iteration's update is applied by k_warp_fused_fin.
+// Per pixel: read z, w, p (halos), cos / sin, UrShape, M^-1, delta; write z,
+// w, p, delta: 120 B against 152 B for the two-pass form.
+// Breakdown (p.q <= 0 or r.z = 0, or a recurrence r.z <= 0) stops the loop
+// as in the two-pass form; a step whose alpha is known is still applied.
+// ---------------------------------------------------------------------------
+constexpr int NRAW_F = 13;       // z0 z1 z2 w0 w1 w2 p0 p1 p2 cos sin ux uy (iteration 0: r0 r1 r2 m0 m1 at 0..4)
+constexpr int NSTG_F = 7;        // px py pt cos sin ux uy, each quad stored as pixels 0 2 1 3
+
+struct FusedSmem {
+  PlaneT raw[NRAW_F];
+  float stg[NSTG_F][HH][SP];     // halo columns -1 / 128 live at 3 / 132, in plain order
+  BytesT mk[2];                  // masked problems: byte plane of the current / next tile
+  unsigned long long bar;
+};
+
+__device__ __forceinline__ float4 fma4s(float a, const float4& x, const float4& y) {
+  return make_float4(__fmaf_rn(a, x.x, y.x), __fmaf_rn(a, x.y, y.y), __fmaf_rn(a, x.z, y.z), __fmaf_rn(a, x.w, y.w));
+}
+__device__ __forceinline__ float4 mul4s(const float4& a, const float4& b) {
+  return make_float4(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y), __fmul_rn(a.z, b.z), __fmul_rn(a.w, b.w));
+}
+__device__ __forceinline__ float2 valid2(bool a, bool b) { return make_float2(a ? 1.f : 0.f, b ? 1.f : 0.f); }
+
+// Pending-only pass: the loop stopped after an iteration whose step is known
+// (alpha != 0): delta += alpha p over the block's pixels, and the last block
+// clears alpha.
+__device__ __forceinline__ void fused_pending(const Chunk& ch, const GridProb& pr, const int* __restrict__ tiles,
+                                              double* __restrict__ part, const float* __restrict__ pin,
+                                              float alpha) {
+  Scalars* s = pr.s;
+  const long long pl = pr.plane;
+  constexpr int QPT = (W4 / 4) * TH;
+  const int nq = (ch.end - ch.begin) * QPT;
+  for (int k = threadIdx.x; k < nq; k += NT) {
+    const int tc = tiles[ch.begin + k / QPT];
+    const int w = k % QPT;
+    const int y = tile_y0(tc) + w / (W4 / 4);
+    if (y >= pr.H) continue;
+    const long long i = (long long)y * pr.P + tile_x0(tc, W4) + 4 * (w % (W4 / 4));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float4* d = reinterpret_cast<float4*>(pr.d + c * pl + i);
+      *d = fma4s(alpha, __ldcg(reinterpret_cast<const float4*>(pin + c * pl + i)), *d);
+    }
+  }
+  const F2 none[4] = {f2_zero(), f2_zero(), f2_zero(), f2_zero()};
+  if (publish_partials4(part, blockIdx.x, none, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+    double unused[4];
+    gather_partials4(part, pr.chunk_begin, pr.chunk_end, &s->counter, unused);
+    if (threadIdx.x == 0) s->alpha_f = 0.f;
+  }
+}
+
+// One single-reduction PCG iteration `it` of the block's chunk (staged by
+// tensor copies, like the wide apply).
+template <bool MASK>
+__device__ __forceinline__ void fused_wide_body(FusedSmem& sm, const Chunk& ch, const GridProb& pr,
+                                                const int* __restrict__ tiles, double* __restrict__ part, int it) {
+  Scalars* s = pr.s;
+  if (s->done) return;
+  const int first = it == 0;
+  const float alpha = first ? 0.f : s->alpha_f;
+  const long long pl = pr.plane;
+  const float* __restrict__ pin = pr.p + (long long)(it & 1) * 3 * pl;
+  if (!s->pcg_active) {
+    if (alpha != 0.f) fused_pending(ch, pr, tiles, part, pin, alpha);
+    return;
+  }
+  const float beta = first ? 0.f : s->beta_f;
+  const int use_beta = beta != 0.0f;
+  const float wfit = pr.w_fit;
+  const float2 w2 = make_float2(pr.w_reg, pr.w_reg);
+  const float lam = pr.lm ? s->lambda_f : 0.0f;
+  float* __restrict__ pout = pr.p + (long long)((it + 1) & 1) * 3 * pl;
+  float* __restrict__ zout = pr.zb + (long long)((it + 1) & 1) * 3 * pl;
+  float* __restrict__ wout = pr.wb + (long long)((it + 1) & 1) * 3 * pl;
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  F2x2 acc_pq = f2x2_zero(), acc_qz = f2x2_zero(), acc_qw = f2x2_zero(), acc_zr = f2x2_zero();
+  const int zz = pr.zpack2 & 63, zw = (pr.zpack2 >> 6) & 63, par3 = (it & 1) * 3;
+  // raw planes, all in the slab (tensor map 0)
+  auto plane = [&](int k, int& z, int& m) {
+    m = 0;
+    if (k >= 9) {
+      z = k < 11 ? zslab(pr, 3) + k - 9 : zslab(pr, 4) + k - 11;
+    } else if (first) {
+      z = k < 3 ? zslab(pr, 0) + k : k < 5 ? zslab(pr, 1) + k - 3 : -1;
+    } else {
+      z = k < 3 ? zz + par3 + k : k < 6 ? zw + par3 + k - 3 : zslab(pr, 2) + par3 + k - 6;
+    }
+  };
+  auto issue = [&](int tcx, int slot) {
+    if (tid == 0) tile_tma<NRAW_F>(sm.raw, &sm.mk[slot], plane, MASK, pr, tile_x0(tcx, W4), tile_y0(tcx), &sm.bar);
+  };
+  // direction and z of one quad of staged row `row` (column c); ownrow:
+  // also the z / delta stores of the thread's own pixels
+  // delta of the thread's own pixels, loaded before the staging wait
+  float4 dl[3];
+  auto stage = [&](int row, int gy, bool own, long long i) {
+    const int c = 4 + 4 * lane;
+    auto R = [&](int k) { return lds4(&sm.raw[k].v[row][c]); };
+    float4 zx, zy, zt;
+    if (first) {
+      const float4 m0 = R(3), m1 = R(4);
+      zx = mul4s(m0, R(0)); zy = mul4s(m0, R(1)); zt = mul4s(m1, R(2));
+    } else {
+      zx = fma4s(-alpha, R(3), R(0)); zy = fma4s(-alpha, R(4), R(1)); zt = fma4s(-alpha, R(5), R(2));
+    }
+    float4 px = zx, py = zy, pt = zt;
+    if (use_beta) {
+      px = fma4s(beta, R(6), zx); py = fma4s(beta, R(7), zy); pt = fma4s(beta, R(8), zt);
+    }
+    sts4(&sm.stg[0][row][c], swz4(px));
+    sts4(&sm.stg[1][row][c], swz4(py));
+    sts4(&sm.stg[2][row][c], swz4(pt));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) sts4(&sm.stg[3 + k][row][c], swz4(R(9 + k)));
+    if (own && gy < pr.H) {
+      *reinterpret_cast<float4*>(zout + i) = zx;
+      *reinterpret_cast<float4*>(zout + pl + i) = zy;
+      *reinterpret_cast<float4*>(zout + 2 * pl + i) = zt;
+      if (!first) {
+        *reinterpret_cast<float4*>(pr.d + i) = fma4s(alpha, R(6), dl[0]);
+        *reinterpret_cast<float4*>(pr.d + pl + i) = fma4s(alpha, R(7), dl[1]);
+        *reinterpret_cast<float4*>(pr.d + 2 * pl + i) = fma4s(alpha, R(8), dl[2]);
+      }
+    }
+  };
+  int tc = tiles[ch.begin];
+  int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
+  int hb0 = pr.hbeg[tile_id(pr, tc)], hb1 = pr.hbeg[tile_id(pr, tc) + 1];
+  unsigned phase = 0;
+  int slot = 0;
+  issue(tc, 0);
+  for (int t = ch.begin; t < ch.end; ++t) {
+    const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
+    const int gx = x0 + 4 * lane, gy = y0 + ty;
+    const long long i = (long long)gy * pr.P + gx;
+    const int hcur0 = hb0, hcur1 = hb1;
+    if (!first && gy < pr.H) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dl[k] = *reinterpret_cast<const float4*>(pr.d + k * pl + i);
+    }
+    const unsigned pb = phase;
+    const bool ok = mbar_wait(&sm.bar, pb);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      staging_timeout(s, &sm.bar, pb);
+      return;
+    }
+    const unsigned char (*mk)[SPB] = sm.mk[slot].v;
+    // phase 2: z and the direction on the tile and its halo
+    stage(ty + 1, gy, true, i);
+    if (tid < 64) {
+      const int row = tid < 32 ? 0 : HH - 1;
+      stage(row, y0 - 1 + row, false, 0);
+    } else if (tid < 64 + 2 * TH) {
+      const int h = tid - 64;
+      const int row = 1 + (h % TH), side = h / TH;
+      const int col = side ? 4 + W4 : 3;
+      auto R = [&](int k) { return sm.raw[k].v[row][col]; };
+      float zx, zy, zt;
+      if (first) {
+        zx = __fmul_rn(R(3), R(0)); zy = __fmul_rn(R(3), R(1)); zt = __fmul_rn(R(4), R(2));
+      } else {
+        zx = __fmaf_rn(-alpha, R(3), R(0)); zy = __fmaf_rn(-alpha, R(4), R(1)); zt = __fmaf_rn(-alpha, R(5), R(2));
+      }
+      if (use_beta) {
+        zx = __fmaf_rn(beta, R(6), zx); zy = __fmaf_rn(beta, R(7), zy); zt = __fmaf_rn(beta, R(8), zt);
+      }
+      sm.stg[0][row][col] = zx; sm.stg[1][row][col] = zy; sm.stg[2][row][col] = zt;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sm.stg[3 + k][row][col] = R(9 + k);
+    }
+    __syncthreads();
+    // the raw buffer is free: start the next tile's copies
+    if (t + 1 < ch.end) {
+      tc = tn;
+      issue(tc, slot ^ 1);
+      const int tidn = tile_id(pr, tc);
+      hb0 = pr.hbeg[tidn];
+      hb1 = pr.hbeg[tidn + 1];
+      if (t + 2 < ch.end) tn = tiles[t + 2];
+    }
+    if (gy < pr.H) {                          // warp-uniform: one warp per row
+      const int c = 4 + 4 * lane;
+      float4 O[NSTG_F];
+#pragma unroll
+      for (int k = 0; k < NSTG_F; ++k) O[k] = lds4(&sm.stg[k][ty + 1][c]);
+      *reinterpret_cast<float4*>(pout + i) = swz4(O[0]);
+      *reinterpret_cast<float4*>(pout + pl + i) = swz4(O[1]);
+      *reinterpret_cast<float4*>(pout + 2 * pl + i) = swz4(O[2]);
+      // validity of the own pixels and of their neighbours (1 / 0): inside
+      // the grid and, with a mask, not excluded; staged order 0 2 1 3
+      float2 vA, vB, lA, rA, rB, up2A, up2B, dn2A, dn2B;
+      {
+        const bool upok = gy > 0, dnok = gy + 1 < pr.H;
+        if (!MASK) {
+          vA = valid2(gx < pr.W, gx + 2 < pr.W);
+          vB = valid2(gx + 1 < pr.W, gx + 3 < pr.W);
+          lA = valid2(gx > 0, true);
+          rA = vB;
+          rB = valid2(gx + 2 < pr.W, gx + 4 < pr.W);
+          up2A = up2B = valid2(upok, upok);
+          dn2A = dn2B = valid2(dnok, dnok);
+        } else {
+          // byte of column x0 + k at mk[row][16 + k]; halo columns at 15 / 144
+          auto fr = [&](int row, int k) {
+            return gx + k >= 0 && gx + k < pr.W && mk[row][16 + 4 * lane + k] == 0;
+          };
+          const int ro = ty + 1;
+          vA = valid2(fr(ro, 0), fr(ro, 2));
+          vB = valid2(fr(ro, 1), fr(ro, 3));
+          lA = valid2(gx > 0 && mk[ro][15 + 4 * lane] == 0, fr(ro, 1));
+          rA = vB;
+          rB = valid2(fr(ro, 2), gx + 4 < pr.W && mk[ro][20 + 4 * lane] == 0);
+          up2A = valid2(upok && fr(ro - 1, 0), upok && fr(ro - 1, 2));
+          up2B = valid2(upok && fr(ro - 1, 1), upok && fr(ro - 1, 3));
+          dn2A = valid2(dnok && fr(ro + 1, 0), dnok && fr(ro + 1, 2));
+          dn2B = valid2(dnok && fr(ro + 1, 1), dnok && fr(ro + 1, 3));
+        }
+      }
+      float2 axA = make_float2(0.f, 0.f), ayA = axA, atA = axA, axB = axA, ayB = axA, atB = axA;
+      const Own2 oa = {lo2(O[0]), lo2(O[1]), lo2(O[2]), lo2(O[3]), lo2(O[4]), lo2(O[5]), lo2(O[6])};
+      const Own2 ob = {hi2(O[0]), hi2(O[1]), hi2(O[2]), hi2(O[3]), hi2(O[4]), hi2(O[5]), hi2(O[6])};
+      {
+        float L[NSTG_F], R[NSTG_F];
+#pragma unroll
+        for (int k = 0; k < NSTG_F; ++k) {
+          L[k] = __shfl_up_sync(0xffffffffu, O[k].w, 1);
+          R[k] = __shfl_down_sync(0xffffffffu, O[k].x, 1);
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < NSTG_F; ++k) L[k] = sm.stg[k][ty + 1][3];
+        }
+        if (lane == 31) {
+#pragma unroll
+          for (int k = 0; k < NSTG_F; ++k) R[k] = sm.stg[k][ty + 1][4 + W4];
+        }
+        pair2(oa, make_float2(L[0], O[0].z), make_float2(L[1], O[1].z), make_float2(L[2], O[2].z),
+              make_float2(L[3], O[3].z), make_float2(L[4], O[4].z), make_float2(L[5], O[5].z),
+              make_float2(L[6], O[6].z), lA, axA, ayA, atA);
+        pair2(oa, ob.px, ob.py, ob.pt, ob.c, ob.s, ob.ux, ob.uy, rA, axA, ayA, atA);
+        pair2(ob, oa.px, oa.py, oa.pt, oa.c, oa.s, oa.ux, oa.uy, vA, axB, ayB, atB);
+        pair2(ob, make_float2(O[0].y, R[0]), make_float2(O[1].y, R[1]), make_float2(O[2].y, R[2]),
+              make_float2(O[3].y, R[3]), make_float2(O[4].y, R[4]), make_float2(O[5].y, R[5]),
+              make_float2(O[6].y, R[6]), rB, axB, ayB, atB);
+      }
+#pragma unroll 1
+      for (int dr = 0; dr < 2; ++dr) {        // rows above and below
+        float4 U[NSTG_F];
+        const int row = dr ? ty + 2 : ty;
+#pragma unroll
+        for (int k = 0; k < NSTG_F; ++k) U[k] = lds4(&sm.stg[k][row][c]);
+        const float2 mA = dr ? dn2A : up2A, mB = dr ? dn2B : up2B;
+        pair2(oa, lo2(U[0]), lo2(U[1]), lo2(U[2]), lo2(U[3]), lo2(U[4]), lo2(U[5]), lo2(U[6]), mA, axA, ayA, atA);
+        pair2(ob, hi2(U[0]), hi2(U[1]), hi2(U[2]), hi2(U[3]), hi2(U[4]), hi2(U[5]), hi2(U[6]), mB, axB, ayB, atB);
+      }
+      const float2 wa = mul2(w2, vA), wb = mul2(w2, vB);
+      axA = mul2(wa, axA); ayA = mul2(wa, ayA); atA = mul2(wa, atA);
+      axB = mul2(wb, axB); ayB = mul2(wb, ayB); atB = mul2(wb, atB);
+      float qx[4] = {axA.x, axB.x, axA.y, axB.y};
+      float qy[4] = {ayA.x, ayB.x, ayA.y, ayB.y};
+      float qt[4] = {atA.x, atB.x, atA.y, atB.y};
+      const float vf[4] = {vA.x, vB.x, vA.y, vB.y};
+      const float4 opx = swz4(O[0]), opy = swz4(O[1]), opt = swz4(O[2]);
+      for (int h = hcur0; h < hcur1; ++h) {
+        const long long k = pr.hpix[h] - i;
+        if (k >= 0 && k < 4) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            if (kk == k && vf[kk] != 0.f) {
+              qx[kk] = __fmaf_rn(wfit, cmp(opx, kk), qx[kk]);
+              qy[kk] = __fmaf_rn(wfit, cmp(opy, kk), qy[kk]);
+            }
+        }
+      }
+      if (pr.lm) {
+        const float4 dd = ld4(pr.dc + i), dt = ld4(pr.dc + pl + i);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (vf[k] == 0.f) continue;
+          qx[k] = __fmaf_rn(__fmul_rn(lam, cmp(dd, k)), cmp(opx, k), qx[k]);
+          qy[k] = __fmaf_rn(__fmul_rn(lam, cmp(dd, k)), cmp(opy, k), qy[k]);
+          qt[k] = __fmaf_rn(__fmul_rn(lam, cmp(dt, k)), cmp(opt, k), qt[k]);
+        }
+      }
+      // w = M^-1 q and the three inner products; z of the own pixels comes
+      // back from the stores of phase 2 (this thread's own writes)
+      const float4 m0 = ld4(pr.m + i), m1 = ld4(pr.m + pl + i);
+      const float4 qxv = make_float4(qx[0], qx[1], qx[2], qx[3]);
+      const float4 qyv = make_float4(qy[0], qy[1], qy[2], qy[3]);
+      const float4 qtv = make_float4(qt[0], qt[1], qt[2], qt[3]);
+      const float4 wx = mul4s(m0, qxv), wy = mul4s(m0, qyv), wt = mul4s(m1, qtv);
+      *reinterpret_cast<float4*>(wout + i) = wx;
+      *reinterpret_cast<float4*>(wout + pl + i) = wy;
+      *reinterpret_cast<float4*>(wout + 2 * pl + i) = wt;
+      const float4 zxv = *reinterpret_cast<const float4*>(zout + i);
+      const float4 zyv = *reinterpret_cast<const float4*>(zout + pl + i);
+      const float4 ztv = *reinterpret_cast<const float4*>(zout + 2 * pl + i);
+      f2x2_add_prod(acc_pq, lo2(opx), lo2(qxv)); f2x2_add_prod(acc_pq, hi2(opx), hi2(qxv));
+      f2x2_add_prod(acc_pq, lo2(opy), lo2(qyv)); f2x2_add_prod(acc_pq, hi2(opy), hi2(qyv));
+      f2x2_add_prod(acc_pq, lo2(opt), lo2(qtv)); f2x2_add_prod(acc_pq, hi2(opt), hi2(qtv));
+      f2x2_add_prod(acc_qw, lo2(wx), lo2(qxv)); f2x2_add_prod(acc_qw, hi2(wx), hi2(qxv));
+      f2x2_add_prod(acc_qw, lo2(wy), lo2(qyv)); f2x2_add_prod(acc_qw, hi2(wy), hi2(qyv));
+      f2x2_add_prod(acc_qw, lo2(wt), lo2(qtv)); f2x2_add_prod(acc_qw, hi2(wt), hi2(qtv));
+      f2x2_add_prod(acc_qz, lo2(zxv), lo2(qxv)); f2x2_add_prod(acc_qz, hi2(zxv), hi2(qxv));
+      f2x2_add_prod(acc_qz, lo2(zyv), lo2(qyv)); f2x2_add_prod(acc_qz, hi2(zyv), hi2(qyv));
+      f2x2_add_prod(acc_qz, lo2(ztv), lo2(qtv)); f2x2_add_prod(acc_qz, hi2(ztv), hi2(qtv));
+      // r.z of the own pixels, with r = z / M^-1
+      const float4 d0 = make_float4(__frcp_rn(m0.x), __frcp_rn(m0.y), __frcp_rn(m0.z), __frcp_rn(m0.w));
+      const float4 d1 = make_float4(__frcp_rn(m1.x), __frcp_rn(m1.y), __frcp_rn(m1.z), __frcp_rn(m1.w));
+      const float4 rx = mul4s(d0, zxv), ry = mul4s(d0, zyv), rt = mul4s(d1, ztv);
+      f2x2_add_prod(acc_zr, lo2(zxv), lo2(rx)); f2x2_add_prod(acc_zr, hi2(zxv), hi2(rx));
+      f2x2_add_prod(acc_zr, lo2(zyv), lo2(ry)); f2x2_add_prod(acc_zr, hi2(zyv), hi2(ry));
+      f2x2_add_prod(acc_zr, lo2(ztv), lo2(rt)); f2x2_add_prod(acc_zr, hi2(ztv), hi2(rt));
+    }
+    slot ^= 1;
+  }
+  const F2 sums[4] = {f2x2_fold(acc_pq), f2x2_fold(acc_qz), f2x2_fold(acc_qw), f2x2_fold(acc_zr)};
+  if (publish_partials4(part, blockIdx.x, sums, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+    double v[4];
+    gather_partials4(part, pr.chunk_begin, pr.chunk_end, &s->counter, v);
+    if (threadIdx.x == 0) {
+      // v = p.q, q.z, q.M^-1 q and r.z of this iteration's vectors
+      const double pq = v[0], qz = v[1], qw = v[2], rz = v[3];
+      s->pq = pq;
+      if (pq > 0.0 && isfinite(pq) && rz > 0.0 && isfinite(rz)) {
+        // alpha from the r.z of the stored z (as the two-pass form takes it);
+        // the recurrence only carries r.z one iteration ahead, to set beta
+        const float af = (float)(rz / pq);
+        const double a = (double)af;
+        const double rz_next = fma(a * a, qw, fma(-2.0 * a, qz, rz));
+        s->alpha_f = af;
+        s->rz = rz;
+        s->pcg_iters += 1;
+        if (rz_next > 0.0 && isfinite(rz_next)) {
+          s->beta_f = (float)(rz_next / rz);
+        } else {
+          s->pcg_active = 0;        // the step alpha p is still applied
+          if (!isfinite(rz_next)) s->nonfinite = 1;
+        }
+      } else {
+        s->alpha_f = 0.f;
+        s->pcg_active = 0;
+        if (!isfinite(pq) || !isfinite(rz)) s->nonfinite = 1;
+      }
+    }
+  }
+}
+
+template <bool MASK>
+__global__ void __launch_bounds__(NT, 2) k_warp_fused_wide(const GridProb* __restrict__ probs,
+                                                           const Chunk* __restrict__ chunks,
+                                                           const int* __restrict__ tiles,
+                                                           double* __restrict__ part, int it) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  FusedSmem& sm = *reinterpret_cast<FusedSmem*>(dyn_smem);
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  pdl_begin();
+  if (threadIdx.x == 0) mbar_init(&sm.bar);
+  __syncthreads();
+  if (tma_ready(pr, &sm)) fused_wide_body<MASK>(sm, ch, pr, tiles, part, it);
+}
+
+// After the last single-reduction iteration: delta += alpha p for the step
+// whose alpha is known (p of parity `par`), unless the loop has none pending.
+__global__ void __launch_bounds__(NT) k_warp_fused_fin(const GridProb* __restrict__ probs,
+                                                       const Chunk* __restrict__ chunks,
+                                                       const int* __restrict__ tiles, int par) {
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  pdl_begin();
+  const Scalars* s = pr.s;
+  if (s->done) return;
+  const float alpha = s->alpha_f;
+  if (alpha == 0.f) return;
+  const long long pl = pr.plane;
+  const float* __restrict__ pin = pr.p + (long long)(par & 1) * 3 * pl;
+  constexpr int QPT = (W4 / 4) * TH;
+  const int nq = (ch.end - ch.begin) * QPT;
+  for (int k = threadIdx.x; k < nq; k += NT) {
+    const int tc = tiles[ch.begin + k / QPT];
+    const int w = k % QPT;
+    const int y = tile_y0(tc) + w / (W4 / 4);
+    if (y >= pr.H) continue;
+    const long long i = (long long)y * pr.P + tile_x0(tc, W4) + 4 * (w % (W4 / 4));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float4* d = reinterpret_cast<float4*>(pr.d + c * pl + i);
+      *d = fma4s(alpha, __ldcg(reinterpret_cast<const float4*>(pin + c * pl + i)), *d);
+    }
+  }
+}
+
 // Wide-tile warp PCGInit (tw = 128), staged like the wide apply: tensor
 // copies bring the raw planes (dx, dy, theta, UrShape) of the halo-extended
 // tile into shared memory, phase 2 evaluates cos / sin of theta once per
@@ -1219,6 +1641,7 @@ __device__ __forceinline__ void k_warp_init_wide_body(InitSmem& sm, const Chunk&
       s->E = E;
       if (pr.Ehist && k_outer >= 0) pr.Ehist[k_outer] = E;
       s->beta_f = 0.f;
+      s->alpha_f = 0.f;         // no step pending (single-reduction PCG)
       s->pcg_active = (rz != 0.0) && isfinite(rz);
       if (!isfinite(rz) || !isfinite(E)) s->nonfinite = 1;
     }
@@ -2335,6 +2758,15 @@ cudaError_t grid_kernels_prepare() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_poisson_init_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sizeof(PoisInitSmem));
+    const int fbytes = (int)sizeof(FusedSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_fused_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fbytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_fused_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fbytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_fused_wide<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_fused_wide<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_warp_pcg_coop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
@@ -2391,6 +2823,19 @@ void launch_grid_update(int kind, const GridLaunch& L, int par) {
     launch_pdl(k_grid_update<3>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, par);
   else
     launch_pdl(k_grid_update<4>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, par);
+}
+
+void launch_grid_fused(const GridLaunch& L, int it) {
+  if (L.masked)
+    launch_pdl(k_warp_fused_wide<true>, L.nchunks, NT, sizeof(FusedSmem), L.stream, L.probs, L.chunks, L.tiles,
+               L.part, it);
+  else
+    launch_pdl(k_warp_fused_wide<false>, L.nchunks, NT, sizeof(FusedSmem), L.stream, L.probs, L.chunks, L.tiles,
+               L.part, it);
+}
+
+void launch_grid_fused_fin(const GridLaunch& L, int par) {
+  launch_pdl(k_warp_fused_fin, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, par);
 }
 
 void launch_grid_energy(int kind, const GridLaunch& L, int mode, int hist_idx) {

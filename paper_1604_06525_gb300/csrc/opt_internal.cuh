@@ -115,6 +115,12 @@ struct GridProb {
   // slab plane index (6 bits each) of r, M^-1, p (parity 0), cos / sin and
   // the constants: zpack = z_r | z_m << 6 | z_p << 12 | z_csn << 18 | z_c << 24
   int zpack;
+  // warp, tw = 128: the single-reduction PCG iteration's double-buffered
+  // z = M^-1 r and w = M^-1 q (3 planes per buffer, buffer 1 at + 3 planes;
+  // NULL where the problem has none) and their slab plane indices
+  // (zpack2 = z_z | z_w << 6)
+  float *zb, *wb;
+  int zpack2;
   float *d, *r, *p, *q;         // PCG vectors
   float *m, *dc;                // M^-1 and LM diagonal (distinct-diagonal planes)
   float* csn;                   // warp, tw = 128: cos / sin of theta (2 planes, written by PCGInit)
@@ -422,6 +428,65 @@ __device__ __forceinline__ void gather_partials(const double* part, int cb, int 
   }
   block_sum2(a, b);
   if (threadIdx.x == 0) *counter = 0u;
+}
+
+// Four partial sums per chunk (the single-reduction PCG iteration): as
+// publish_partials / gather_partials, with slots part[4 * chunk + 0..3] (the
+// grid problems' partial buffers hold four doubles per chunk).
+__device__ __forceinline__ bool publish_partials4(double* part, int chunk, const F2 (&f)[4],
+                                                  unsigned int* counter, unsigned int nchunks) {
+  __shared__ double s4[4][NT / 32];
+  __shared__ int s_last;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const F2 v = warp_sum_f2(f[k]);
+    if (l == 0) s4[k][w] = f2_to_double(v);
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double a = 0.0;
+#pragma unroll
+    for (int j = 0; j < NT / 32; ++j) a += s4[threadIdx.x][j];
+    __stcg(&part[4 * chunk + threadIdx.x], a);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    s_last = (prev == nchunks - 1);
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+// In the last block: the four sums over chunks [cb, ce) in chunk order
+// (thread-strided, then a fixed tree); valid in thread 0; resets the counter.
+__device__ __forceinline__ void gather_partials4(const double* part, int cb, int ce, unsigned int* counter,
+                                                 double (&out)[4]) {
+  __shared__ double g4[4][NT / 32];
+  __threadfence();
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 2
+  for (int c = cb + (int)threadIdx.x; c < ce; c += NT) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] += __ldcg(&part[4 * c + k]);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    a[k] = warp_sum(a[k]);
+    if (l == 0) g4[k][w] = a[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      out[k] = 0.0;
+      for (int j = 0; j < NT / 32; ++j) out[k] += g4[k][j];
+    }
+    *counter = 0u;
+  }
 }
 
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }

@@ -1,0 +1,183 @@
+"""The single-reduction PCG iteration (opt_solve_params.pcg_form = 1) of the
+wide-tile ARAP warp against the FP64 oracle's textbook Jacobi-PCG (Saad,
+Alg. 9.1; the paper's PCG of Sec. 4.1) and GN / LM (Sec. 4).
+
+The form computes the same Krylov iterates as the two-pass PCG in exact
+arithmetic, so the oracle is the same: the step delta after k iterations
+(read back as x - x0 after one GN outer iteration of k PCG iterations, since
+GN sets x = x0 + delta) within 1e-4 norm-wise, as the two-pass iterates are
+held in test_gpu_parity.py, and energies within the stated 1e-4 with the
+same outer-iteration count.  Grids are at least 128 pixels wide (the form
+runs on 128-pixel tiles), with ragged widths and heights, masks, handles.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_06525_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_ENERGY = 1e-4
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_1604_06525_gb300 import build, api as api_mod
+    build.build()
+    api_mod.load_library()
+    return api_mod
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).reshape(-1)
+    b = np.asarray(b, np.float64).reshape(-1)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def relE(a, b):
+    return abs(a - b) / max(abs(b), 1e-30)
+
+
+def warp(W, H, mask_frac, seed, perturb=0.5, n_handles=None):
+    mask = synth.random_mask(W, H, mask_frac, seed + 1) if mask_frac else None
+    prob = synth.warp_problem(W, H, n_handles or max(1, (W * H) // 200), seed=seed, mask=mask)
+    if perturb:
+        rng = np.random.default_rng(seed + 2)
+        prob.x0 = (prob.x0 + rng.uniform(-perturb, perturb, size=prob.x0.shape)).astype(np.float32)
+    return prob
+
+
+CASES = [(128, 8, 0.0), (256, 24, 0.0), (300, 21, 0.0), (301, 17, 0.2), (520, 9, 0.0), (200, 37, 0.3)]
+
+
+@pytest.mark.parametrize("W,H,mf", CASES)
+def test_fused_iterates_match_oracle(api, W, H, mf):
+    """delta after k = 1, 3, 6 single-reduction iterations equals the
+    oracle's textbook PCG step from the same start."""
+    import torch
+    prob = warp(W, H, mf, seed=W + H)
+    e = oracle.make_energy(prob)
+    x0 = prob.x0.reshape(-1).astype(np.float64)
+    J = e.jacobian(x0)
+    b = -(J.T @ e.residuals(x0))
+    diag = np.asarray(J.multiply(J).sum(0)).ravel()
+    Minv = oracle.solver.jacobi_minv(diag)
+    gp = api.Problem(prob)
+    assert gp.config()["tile_w"] == 128
+    for k in (1, 3, 6):
+        gp.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
+        rep = gp.solve_gn(1, k, pcg_form=1)
+        d_ref, n_done, _ = oracle.jacobi_pcg(lambda v: J.T @ (J @ v), b, Minv, k)
+        assert rep["pcg_done"] == n_done == k
+        d = gp.x.cpu().numpy().reshape(-1).astype(np.float64) - prob.x0.reshape(-1)
+        assert rel(d, d_ref) <= 1e-4, (k, rel(d, d_ref))
+
+
+@pytest.mark.parametrize("W,H,mf", [(320, 64, 0.0), (300, 41, 0.2)])
+def test_fused_gn_matches_oracle_and_two_pass(api, W, H, mf):
+    """GN 4 x 10 from the unperturbed start: every outer energy within 1e-4
+    of the oracle, the same PCG count, and within rounding of the two-pass
+    form."""
+    import torch
+    prob = warp(W, H, mf, seed=141, perturb=0.0, n_handles=12)
+    e = oracle.make_energy(prob)
+    ref = oracle.gauss_newton(e, prob.x0.reshape(-1), 4, 10)
+    gp = api.Problem(prob)
+    rep1 = gp.solve_gn(4, 10, pcg_form=1)
+    x1 = gp.x.cpu().numpy()
+    gp.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
+    rep0 = gp.solve_gn(4, 10, pcg_form=0)
+    assert rep1["outer_done"] == rep0["outer_done"] == 4
+    assert rep1["pcg_done"] == ref.pcg_done
+    for k, (a, b) in enumerate(zip(rep1["E_history"], ref.E_history)):
+        assert relE(a, b) <= TOL_ENERGY, (k, a, b)
+    for a, b in zip(rep1["E_history"], rep0["E_history"]):
+        assert relE(a, b) <= 1e-5
+    assert relE(e.energy(x1.reshape(-1)), ref.E_history[-1]) <= TOL_ENERGY
+
+
+def test_fused_lm_matches_oracle(api):
+    """LM (damping in the product and in the preconditioner): the same
+    accept / reject sequence and outer count as the oracle, energies within
+    1e-4."""
+    prob = warp(260, 40, 0.1, seed=77, perturb=0.3)
+    e = oracle.make_energy(prob)
+    ref = oracle.levenberg_marquardt(e, prob.x0.reshape(-1), 6, 15)
+    gp = api.Problem(prob)
+    rep = gp.solve_lm(6, 15, pcg_form=1)
+    assert rep["outer_done"] == ref.outer_done
+    assert rep["accepted"] == sum(ref.accepted)
+    for k, (a, b) in enumerate(zip(rep["E_history"], ref.E_history)):
+        assert relE(a, b) <= TOL_ENERGY, (k, a, b)
+
+
+def test_fused_isolated_pixels_stop_after_exact_step(api):
+    """Every free pixel isolated (no free neighbour): J^T J is diagonal, the
+    Jacobi preconditioner inverts it and the first PCG step is exact.  The
+    recurrence r.z then drops to rounding level (or below zero, which stops
+    the loop with the known step still applied); the remaining iterations
+    must leave delta at the exact step."""
+    import torch
+    W, H = 160, 9
+    mask = np.ones((H, W), np.uint8)
+    mask[::2, ::2] = 0
+    prob = synth.warp_problem(W, H, 20, seed=5, mask=mask)
+    rng = np.random.default_rng(8)
+    prob.x0 = (prob.x0 + rng.uniform(-0.5, 0.5, size=prob.x0.shape)).astype(np.float32)
+    e = oracle.make_energy(prob)
+    x0 = prob.x0.reshape(-1).astype(np.float64)
+    J = e.jacobian(x0)
+    b = -(J.T @ e.residuals(x0))
+    diag = np.asarray(J.multiply(J).sum(0)).ravel()
+    d_exact = np.where(diag > 0, b / np.where(diag > 0, diag, 1.0), 0.0)
+    gp = api.Problem(prob)
+    for inner in (1, 2, 5):
+        gp.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
+        rep = gp.solve_gn(1, inner, pcg_form=1)
+        assert rep["status"] == "OPT_OK"
+        d = gp.x.cpu().numpy().reshape(-1).astype(np.float64) - x0
+        assert rel(d, d_exact) <= 1e-5, (inner, rel(d, d_exact))
+
+
+def test_fused_full_size_configuration(api):
+    """ARAP warp 1024 x 1024, 64 handles, GN 20 x 20 (the grid-at-scale
+    configuration) at the autotuned launch configuration: the first two outer
+    iterations' energies against the oracle, the whole solve's energies
+    within rounding of the two-pass form."""
+    import torch
+    prob = synth.warp_problem(1024, 1024, 64, seed=synth.BASE_SEED)
+    e = oracle.make_energy(prob)
+    ref = oracle.gauss_newton(e, prob.x0.reshape(-1), 2, 20)
+    gp = api.Problem(prob)
+    gp.autotune()
+    gp.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
+    rep = gp.solve_gn(2, 20, pcg_form=1)
+    for a, b in zip(rep["E_history"], ref.E_history):
+        assert relE(a, b) <= TOL_ENERGY
+    gp.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
+    r1 = gp.solve_gn(20, 20, pcg_form=1)
+    gp.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
+    r0 = gp.solve_gn(20, 20, pcg_form=0)
+    assert r1["pcg_done"] == r0["pcg_done"] == 400
+    for a, b in zip(r1["E_history"], r0["E_history"]):
+        assert relE(a, b) <= 1e-5
+
+
+def test_fused_form_on_other_problems_runs_two_pass(api):
+    """pcg_form = 1 on problems the form does not cover (32-pixel tiles,
+    Poisson) runs the two-pass iteration: bit-identical results."""
+    import torch
+    for prob in (warp(100, 30, 0.0, seed=3), synth.poisson_problem(260, 40, seed=4)):
+        gp = api.Problem(prob)
+        r0 = gp.solve_gn(2, 5, pcg_form=0)
+        gp.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
+        r1 = gp.solve_gn(2, 5, pcg_form=1)
+        assert r0["E_history"] == r1["E_history"]
+    gp = api.Problem(warp(256, 8, 0.0, seed=9))
+    with pytest.raises(Exception):
+        gp.solve_gn(1, 1, pcg_form=2)
