@@ -517,30 +517,30 @@ def bench_batched(api, synth, torch, flush, n=512, outer=10, inner=10):
             m.x.copy_(x)
 
     batch = api.Batch(members)
-    chosen, _ = batch.autotune(inner=4)
+    chosen, _ = batch.autotune(inner=4, pcg_form=PCG_FORM)
     reset()
-    batch.solve_gn(outer, inner)           # capture + warm
+    batch.solve_gn(outer, inner, pcg_form=PCG_FORM)           # capture + warm
     bt = []
     for _ in range(3):
         reset()
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        reps_b, ms_b = batch.solve_gn(outer, inner)
+        reps_b, ms_b = batch.solve_gn(outer, inner, pcg_form=PCG_FORM)
         bt.append((time.perf_counter() - t0, ms_b))
     wall_b = statistics.median(t for t, _ in bt)
     dev_b = statistics.median(m for _, m in bt)
     # plain: one problem at a time (graphs captured in a warm-up pass)
     reset()
     for m in members:
-        m.solve_gn(outer, inner)
+        m.solve_gn(outer, inner, pcg_form=PCG_FORM)
     reset()
     flush.zero_()
     torch.cuda.synchronize()
     lat, dev_p, reps_p = [], 0.0, []
     t0 = time.perf_counter()
     for m in members:
-        r = m.solve_gn(outer, inner)
+        r = m.solve_gn(outer, inner, pcg_form=PCG_FORM)
         reps_p.append(r)
         dev_p += r["ms"]
         lat.append(time.perf_counter() - t0)
@@ -549,7 +549,7 @@ def bench_batched(api, synth, torch, flush, n=512, outer=10, inner=10):
     # at the members' own chunking the batch is bit-identical to the plain solves
     batch.set_chunking(0)
     reset()
-    reps_0, _ = batch.solve_gn(outer, inner)
+    reps_0, _ = batch.solve_gn(outer, inner, pcg_form=PCG_FORM)
     rel0 = max(abs(a["E_final"] - b["E_final"]) / max(abs(b["E_final"]), 1e-30) for a, b in zip(reps_0, reps_p))
     batch.close()
     for m in members:
@@ -979,7 +979,9 @@ def run_ours(args):
                    "gpu_batched_solves_per_s": extra["batched_512_warps_gn10x10"]["batched_solves_per_s"]}
 
     fused = PCG_FORM == 1 and head_cfg["tile_w"] == 128
-    launches_per_step = 2 + OUTER * ((3 + INNER) if fused else (2 + 2 * INNER))
+    # per outer iteration: PCGInit, the PCG launches, and the outer update (the
+    # single-reduction form applies its last step and x += delta in one pass)
+    launches_per_step = 2 + OUTER * ((2 + INNER) if fused else (2 + 2 * INNER))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -201,7 +201,8 @@ typedef struct {
                                  (r.z' = r.z - 2 alpha q.z + alpha^2 q.M^-1 q), and carries
                                  z = M^-1 r and w = M^-1 q instead of r and q.  The same
                                  iterates in exact arithmetic; in float32 they differ from form 0
-                                 by rounding.  Batches and the server run form 0.  Other values:
+                                 by rounding.  Batches (and the server) apply it to their members
+                                 of that kind, the others run form 0.  Other values:
                                  OPT_ERR_INVALID_ARG. */
 } opt_solve_params;
 

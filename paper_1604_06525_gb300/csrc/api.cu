@@ -358,7 +358,8 @@ opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cu
     if (p.materialized) csr_evalj(pb, st, p.materialized);
     if (fused) {
       for (int i = 0; i < p.inner; ++i) launch_grid_fused(grid_launch(pb, st), i);
-      launch_grid_fused_fin(grid_launch(pb, st), p.inner);
+      // Gauss-Newton: the last step and x += delta in one pass
+      launch_grid_fused_fin(grid_launch(pb, st), p.inner, lm ? 0 : 1);
     } else if (coop) {
       // the barrier's counter restarts at 0 (a timed-out launch may leave it
       // mid-count); its timeout flag accumulates over the solve
@@ -372,7 +373,7 @@ opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cu
       }
     }
     if (!lm) {
-      st_step(pb, st, 0);
+      if (!fused) st_step(pb, st, 0);
     } else {
       st_energy(pb, st, 1, -2);
       k_lm_decide<<<1, 32, 0, st>>>(pb->d_s, 1, p.eta, p.lambda_min, p.lambda_max, p.rel_tol);
@@ -1382,7 +1383,7 @@ opt_status opt_profile_pcg_fused(opt_problem* prob, int32_t n_iters, void* strea
       cudaEventRecord(ev[3 + 2 * i], st);
     }
     cudaEventRecord(ev[2 + 2 * n_iters], st);
-    launch_grid_fused_fin(grid_launch(prob, st), n_iters);
+    launch_grid_fused_fin(grid_launch(prob, st), n_iters, 0);
     cudaEventRecord(ev[3 + 2 * n_iters], st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) status = cuda_fail(e, "opt_profile_pcg_fused");

@@ -199,7 +199,7 @@ opt_status build_tables(opt_batch* b, int tpc) {
     if ((s = bupload(b->table_allocs, &g.d_probs, gp)) != OPT_OK) return s;
     if ((s = bupload(b->table_allocs, &g.d_chunks, chunks)) != OPT_OK) return s;
     if ((s = bupload(b->table_allocs, &g.d_tiles, tiles)) != OPT_OK) return s;
-    if ((s = balloc(b->table_allocs, &g.d_part, 2 * chunks.size())) != OPT_OK) return s;
+    if ((s = balloc(b->table_allocs, &g.d_part, 4 * chunks.size())) != OPT_OK) return s;   // up to 4 partials
     g.nchunks = (int)chunks.size();
   }
   for (MeshGroup& g : b->graphs) {
@@ -316,17 +316,25 @@ void enqueue_batch(opt_batch* b, const opt_solve_params& p, bool lm, cudaStream_
   const int n = (int)b->probs.size();
   enqueue_copies(b, b->d_copy_in, st);
   k_reset_tab<<<(n + 127) / 128, 128, 0, st>>>(b->d_stab, n, lm ? p.lambda0 : 0.0);
+  // wide-tile warp groups take the single-reduction PCG iteration when asked
+  // for (as a solo solve of each member would), the others the two-pass one
+  auto fused = [&](const GridGroup& g) { return p.pcg_form == 1 && p.inner > 0 && g.kind == K_WARP && g.tw == 128; };
   for (int k = 0; k < outer; ++k) {
     for (GridGroup& g : b->grids) launch_grid_init(g.kind, gl(g, st), k, dmin, dmax);
     for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_init(ml(g, st), k, dmin, dmax);
     for (int i = 0; i < p.inner; ++i) {
-      for (GridGroup& g : b->grids) launch_grid_apply(g.kind, gl(g, st), nullptr, i, 1);
+      for (GridGroup& g : b->grids) {
+        if (fused(g)) launch_grid_fused(gl(g, st), i);
+        else launch_grid_apply(g.kind, gl(g, st), nullptr, i, 1);
+      }
       for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_apply(ml(g, st), nullptr, i, 1);
-      for (GridGroup& g : b->grids) launch_grid_update(g.kind, gl(g, st), i);
+      for (GridGroup& g : b->grids) if (!fused(g)) launch_grid_update(g.kind, gl(g, st), i);
       for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_update(ml(g, st), i);
     }
+    // the single-reduction groups' last step (with x += delta under GN)
+    for (GridGroup& g : b->grids) if (fused(g)) launch_grid_fused_fin(gl(g, st), p.inner, lm ? 0 : 1);
     if (!lm) {
-      for (GridGroup& g : b->grids) launch_grid_step(g.kind, gl(g, st), 0);
+      for (GridGroup& g : b->grids) if (!fused(g)) launch_grid_step(g.kind, gl(g, st), 0);
       for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_step(ml(g, st), 0);
     } else {
       for (GridGroup& g : b->grids) launch_grid_energy(g.kind, gl(g, st), 1, -2);
@@ -347,7 +355,7 @@ opt_status batch_solve(opt_batch* b, const opt_solve_params* prm_in, opt_report*
   opt_solve_params p;
   if (prm_in) p = *prm_in;
   else opt_solve_params_default(&p);
-  if (p.outer < 1 || p.inner < 0 || p.materialized) return OPT_ERR_INVALID_ARG;
+  if (p.outer < 1 || p.inner < 0 || p.materialized || p.pcg_form < 0 || p.pcg_form > 1) return OPT_ERR_INVALID_ARG;
   if (lm && (!(p.lambda0 >= 0.0) || !(p.lambda_min <= p.lambda_max) || !(p.diag_min <= p.diag_max)))
     return OPT_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)p.stream;
@@ -362,7 +370,7 @@ opt_status batch_solve(opt_batch* b, const opt_solve_params* prm_in, opt_report*
   }
   const std::vector<double> key = {double(p.outer), double(p.inner), double(lm), double(p.use_precond), p.lambda0,
                                    p.lambda_min, p.lambda_max, p.diag_min, p.diag_max, p.eta, p.rel_tol,
-                                   double(write_back)};
+                                   double(write_back), double(p.pcg_form)};
   if (p.use_graph) {
     if (!b->gexec || key != b->gkey) {
       if (b->gexec) {

@@ -972,7 +972,8 @@ __global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __res
 // p_i, w_i = M^-1 q_i.  r and q themselves are never stored.  z, w and p are
 // double-buffered (halo reads of the previous iterate while other blocks
 // write the next).  Iteration 0 starts from r_0 and M^-1 (z_0 = M^-1 r_0, p_0
-// = z_0); the last iteration's update is applied by k_warp_fused_fin.
+// = z_0); the last iteration's update is applied by k_warp_fused_fin (for
+// Gauss-Newton together with the outer update x += delta).
 // Per pixel: read z, w, p (halos), cos / sin, UrShape, M^-1, delta; write z,
 // w, p, delta: 120 B against 152 B for the two-pass form.
 // Breakdown (p.q <= 0 or r.z = 0, or a recurrence r.z <= 0) stops the loop
@@ -988,13 +989,24 @@ struct FusedSmem {
   unsigned long long bar;
 };
 
+// a x + y and a * b per lane, as packed float32 pairs (correctly rounded per
+// lane: the same bits as scalar fmaf / fmul)
 __device__ __forceinline__ float4 fma4s(float a, const float4& x, const float4& y) {
-  return make_float4(__fmaf_rn(a, x.x, y.x), __fmaf_rn(a, x.y, y.y), __fmaf_rn(a, x.z, y.z), __fmaf_rn(a, x.w, y.w));
+  return fma4p(make_float2(a, a), x, y);
 }
-__device__ __forceinline__ float4 mul4s(const float4& a, const float4& b) {
-  return make_float4(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y), __fmul_rn(a.z, b.z), __fmul_rn(a.w, b.w));
-}
+__device__ __forceinline__ float4 mul4s(const float4& a, const float4& b) { return mul4p(a, b); }
 __device__ __forceinline__ float2 valid2(bool a, bool b) { return make_float2(a ? 1.f : 0.f, b ? 1.f : 0.f); }
+// approximate reciprocal (the PTX rcp.approx instruction: one special-function
+// op, a few ulp): r = z / M^-1 only feeds the r.z that alpha divides, which is
+// rounded to float32 anyway
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float4 rcp4(const float4& v) {
+  return make_float4(rcp_approx(v.x), rcp_approx(v.y), rcp_approx(v.z), rcp_approx(v.w));
+}
 
 // Pending-only pass: the loop stopped after an iteration whose step is known
 // (alpha != 0): delta += alpha p over the block's pixels, and the last block
@@ -1283,8 +1295,7 @@ __device__ __forceinline__ void fused_wide_body(FusedSmem& sm, const Chunk& ch, 
       f2x2_add_prod(acc_qz, lo2(zyv), lo2(qyv)); f2x2_add_prod(acc_qz, hi2(zyv), hi2(qyv));
       f2x2_add_prod(acc_qz, lo2(ztv), lo2(qtv)); f2x2_add_prod(acc_qz, hi2(ztv), hi2(qtv));
       // r.z of the own pixels, with r = z / M^-1
-      const float4 d0 = make_float4(__frcp_rn(m0.x), __frcp_rn(m0.y), __frcp_rn(m0.z), __frcp_rn(m0.w));
-      const float4 d1 = make_float4(__frcp_rn(m1.x), __frcp_rn(m1.y), __frcp_rn(m1.z), __frcp_rn(m1.w));
+      const float4 d0 = rcp4(m0), d1 = rcp4(m1);
       const float4 rx = mul4s(d0, zxv), ry = mul4s(d0, zyv), rt = mul4s(d1, ztv);
       f2x2_add_prod(acc_zr, lo2(zxv), lo2(rx)); f2x2_add_prod(acc_zr, hi2(zxv), hi2(rx));
       f2x2_add_prod(acc_zr, lo2(zyv), lo2(ry)); f2x2_add_prod(acc_zr, hi2(zyv), hi2(ry));
@@ -1341,16 +1352,19 @@ __global__ void __launch_bounds__(NT, 2) k_warp_fused_wide(const GridProb* __res
 
 // After the last single-reduction iteration: delta += alpha p for the step
 // whose alpha is known (p of parity `par`), unless the loop has none pending.
+// step = 1 (Gauss-Newton): the outer update x += delta follows in the same
+// pass (the same roundings as the update, then k_grid_step), and delta is
+// not stored.
 __global__ void __launch_bounds__(NT) k_warp_fused_fin(const GridProb* __restrict__ probs,
                                                        const Chunk* __restrict__ chunks,
-                                                       const int* __restrict__ tiles, int par) {
+                                                       const int* __restrict__ tiles, int par, int step) {
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   pdl_begin();
   const Scalars* s = pr.s;
   if (s->done) return;
   const float alpha = s->alpha_f;
-  if (alpha == 0.f) return;
+  if (alpha == 0.f && !step) return;
   const long long pl = pr.plane;
   const float* __restrict__ pin = pr.p + (long long)(par & 1) * 3 * pl;
   constexpr int QPT = (W4 / 4) * TH;
@@ -1364,7 +1378,15 @@ __global__ void __launch_bounds__(NT) k_warp_fused_fin(const GridProb* __restric
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       float4* d = reinterpret_cast<float4*>(pr.d + c * pl + i);
-      *d = fma4s(alpha, __ldcg(reinterpret_cast<const float4*>(pin + c * pl + i)), *d);
+      float4 dv = *d;
+      if (alpha != 0.f) dv = fma4s(alpha, __ldcg(reinterpret_cast<const float4*>(pin + c * pl + i)), dv);
+      if (step) {
+        float4* x = reinterpret_cast<float4*>(pr.x + c * pl + i);
+        const float4 xv = *x;
+        *x = make_float4(xv.x + dv.x, xv.y + dv.y, xv.z + dv.z, xv.w + dv.w);
+      } else {
+        *d = dv;
+      }
     }
   }
 }
@@ -2834,8 +2856,8 @@ void launch_grid_fused(const GridLaunch& L, int it) {
                L.part, it);
 }
 
-void launch_grid_fused_fin(const GridLaunch& L, int par) {
-  launch_pdl(k_warp_fused_fin, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, par);
+void launch_grid_fused_fin(const GridLaunch& L, int par, int step) {
+  launch_pdl(k_warp_fused_fin, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, par, step);
 }
 
 void launch_grid_energy(int kind, const GridLaunch& L, int mode, int hist_idx) {

@@ -56,9 +56,10 @@ void launch_grid_update(int kind, const GridLaunch& L, int par);
 void launch_grid_energy(int kind, const GridLaunch& L, int mode, int hist_idx);
 // Single-reduction PCG (wide warp tiles; problems planned with z / w
 // buffers): iteration `it` (0 starts from r_0, M^-1), and the pending step of
-// the last iteration (p of parity par = the iteration count)
+// the last iteration (p of parity par = the iteration count); step = 1 also
+// applies the Gauss-Newton update x += delta
 void launch_grid_fused(const GridLaunch& L, int it);
-void launch_grid_fused_fin(const GridLaunch& L, int par);
+void launch_grid_fused_fin(const GridLaunch& L, int par, int step);
 void launch_grid_step(int kind, const GridLaunch& L, int cond);
 // Poisson, tile width 128: the degree plane the wide kernels read (S_i + 1 on
 // free pixels, 0 elsewhere; pitched like the mask, P x H bytes)

@@ -58,7 +58,8 @@ size_t estimate_grid(const opt_grid_desc& d, int tile_w) {
   const bool warp = d.kind == OPT_ARAP_WARP_2D;
   const size_t tw = tile_w ? tile_w : (d.W >= 128 ? 128 : 32);
   const size_t pl = ((size_t)d.W + tw - 1) / tw * tw * (size_t)d.H;
-  const size_t planes = warp ? (tw == 128 ? 26 : 24) : 30;
+  // wide warps also hold the single-reduction PCG's z and w buffers (12 planes)
+  const size_t planes = warp ? (tw == 128 ? 38 : 24) : 30;
   const size_t tiles = ((size_t)d.W + tw - 1) / tw * ((size_t)(d.H + 7) / 8);
   return planes * pl * 4 + (d.mask ? pl : 0) + tiles * 64 + (size_t)d.n_handles * 16 + (1 << 16);
 }
@@ -153,7 +154,8 @@ opt_status opt_server_create(size_t hbm_budget_bytes, const opt_solve_params* pa
   std::unique_ptr<opt_server> s(new opt_server());
   if (params) s->prm = *params;
   else opt_solve_params_default(&s->prm);
-  if (s->prm.outer < 1 || s->prm.inner < 0 || s->prm.materialized) return OPT_ERR_INVALID_ARG;
+  if (s->prm.outer < 1 || s->prm.inner < 0 || s->prm.materialized || s->prm.pcg_form < 0 || s->prm.pcg_form > 1)
+    return OPT_ERR_INVALID_ARG;
   s->budget = hbm_budget_bytes;
   if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
     (void)cudaGetLastError();

@@ -181,3 +181,39 @@ def test_fused_form_on_other_problems_runs_two_pass(api):
     gp = api.Problem(warp(256, 8, 0.0, seed=9))
     with pytest.raises(Exception):
         gp.solve_gn(1, 1, pcg_form=2)
+
+
+@pytest.mark.parametrize("method", ["gn", "lm"])
+def test_fused_batch_matches_solo_and_oracle(api, method):
+    """A batch with pcg_form = 1: its wide-tile warps (masked and not) take
+    the single-reduction iteration, its narrow warps and Poisson members the
+    two-pass one; every member equals its solo solve with the same parameter
+    bit for bit (the batch keeps each member's chunks), and the wide warps
+    match the oracle within 1e-4."""
+    probs = [warp(260, 20, 0.0, seed=301, perturb=0.0, n_handles=6),
+             warp(300, 16, 0.1, seed=302, perturb=0.0, n_handles=6),
+             warp(129, 40, 0.0, seed=303, perturb=0.0, n_handles=4),
+             warp(60, 33, 0.0, seed=304, perturb=0.0, n_handles=4),
+             synth.poisson_problem(300, 24, seed=305)]
+    outer, inner = (3, 8) if method == "gn" else (4, 8)
+    solo = []
+    for p in probs:
+        g = api.Problem(p)
+        solo.append(getattr(g, f"solve_{method}")(outer, inner, pcg_form=1))
+        g.close()
+    members = [api.Problem(p) for p in probs]
+    batch = api.Batch(members)
+    reps, _ = getattr(batch, f"solve_{method}")(outer, inner, pcg_form=1)
+    for r, s in zip(reps, solo):
+        assert r["outer_done"] == s["outer_done"] and r["accepted"] == s["accepted"]
+        assert r["E_history"] == s["E_history"]
+    for i in (0, 1, 2):
+        e = oracle.make_energy(probs[i])
+        x0 = probs[i].x0.reshape(-1)
+        ref = (oracle.gauss_newton(e, x0, outer, inner) if method == "gn"
+               else oracle.levenberg_marquardt(e, x0, outer, inner))
+        for a, b in zip(reps[i]["E_history"], ref.E_history):
+            assert relE(a, b) <= TOL_ENERGY
+    batch.close()
+    for m in members:
+        m.close()
