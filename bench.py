@@ -598,7 +598,7 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, 
 
     def served(cap, pick, arrivals):
         n = len(pick)
-        srv = api.Server(budget, outer=OUT, inner=INN, rel_tol=TOL, max_active=cap)
+        srv = api.Server(budget, outer=OUT, inner=INN, rel_tol=TOL, max_active=cap, pcg_form=PCG_FORM)
         # warm-up: one request of each template kind
         for t in (0, len(warps)):
             tk = srv.submit_template(templates[t])
@@ -633,7 +633,7 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, 
         # a single worker, requests in arrival order, each planned from its template
         n = len(pick)
         g = api.Problem.from_template(templates[0])      # warm-up
-        g.solve_lm(OUT, INN, rel_tol=TOL, use_graph=0)
+        g.solve_lm(OUT, INN, rel_tol=TOL, use_graph=0, pcg_form=PCG_FORM)
         g.close()
         torch.cuda.synchronize()
         lat, done = {}, {}
@@ -643,7 +643,7 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, 
             if arrivals[i] > now:
                 time.sleep(arrivals[i] - now)
             g = api.Problem.from_template(templates[pick[i]])
-            done[i] = g.solve_lm(OUT, INN, rel_tol=TOL, use_graph=0)
+            done[i] = g.solve_lm(OUT, INN, rel_tol=TOL, use_graph=0, pcg_form=PCG_FORM)
             g.close()
             lat[i] = time.perf_counter() - t0 - arrivals[i]
         span = max(arrivals[i] + lat[i] for i in range(n)) - arrivals[0]

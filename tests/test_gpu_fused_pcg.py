@@ -217,3 +217,65 @@ def test_fused_batch_matches_solo_and_oracle(api, method):
     batch.close()
     for m in members:
         m.close()
+
+
+def test_fused_lm_relative_tolerance_stops_like_oracle(api):
+    """LM with rel_tol: the loop stops at the oracle's outer iteration, the
+    later launches of the solve graph (single-reduction iterations and last
+    step included) leave the converged state alone."""
+    prob = warp(256, 30, 0.0, seed=91, perturb=0.2)
+    e = oracle.make_energy(prob)
+    prm = oracle.solver.LMParams(rel_tol=1e-2)
+    ref = oracle.levenberg_marquardt(e, prob.x0.reshape(-1), 12, 10, prm)
+    gp = api.Problem(prob)
+    rep = gp.solve_lm(12, 10, rel_tol=1e-2, pcg_form=1)
+    assert rep["outer_done"] == ref.outer_done < 12
+    assert rep["converged"] == 1
+    assert rep["accepted"] == sum(ref.accepted)
+    for a, b in zip(rep["E_history"], ref.E_history):
+        assert relE(a, b) <= TOL_ENERGY
+    x = gp.x.cpu().numpy().reshape(-1)
+    assert relE(e.energy(x), ref.E_history[-1]) <= TOL_ENERGY
+
+
+def test_fused_server_requests_equal_solo(api):
+    """The server with pcg_form = 1: wide warps (single-reduction), a narrow
+    warp and a mesh (two-pass), some joining while others run; every result
+    equals its solo LM solve with the same parameters."""
+    probs = [warp(200, 24, 0.0, seed=501, perturb=0.0, n_handles=5),
+             warp(300, 17, 0.1, seed=502, perturb=0.0, n_handles=5),
+             warp(64, 40, 0.0, seed=503, perturb=0.0, n_handles=3),
+             warp(140, 60, 0.0, seed=504, perturb=0.0, n_handles=6),
+             synth.mesh_problem(1, seed=505, handle_frac=0.1)]
+    refs = []
+    for p in probs:
+        g = api.Problem(p)
+        r = g.solve_lm(8, 10, rel_tol=1e-6, pcg_form=1)
+        refs.append((r, g.x.cpu().numpy().copy()))
+        g.close()
+    srv = api.Server(4 << 30, outer=8, inner=10, rel_tol=1e-6, pcg_form=1)
+    tickets = [srv.submit(p) for p in probs[:3]]
+    srv.step()
+    tickets += [srv.submit(p) for p in probs[3:]]
+    done = {}
+    for _ in range(200):
+        srv.step()
+        for t in tickets:
+            if t not in done:
+                r = srv.poll(t)
+                if r is not None:
+                    done[t] = r
+        if len(done) == len(tickets):
+            break
+    assert len(done) == len(tickets)
+    for p, t, (ref, xref) in zip(probs, tickets, refs):
+        rep, x = done[t]
+        assert rep["status"] == "OPT_OK"
+        assert rep["outer_done"] == ref["outer_done"] and rep["accepted"] == ref["accepted"]
+        tol = 1e-5 if p.kind == "mesh" else 1e-6
+        for a, b in zip(rep["E_history"][:-1], ref["E_history"][:-1]):
+            assert relE(a, b) <= tol
+        assert relE(rep["E_final"], ref["E_final"]) <= 1e-5
+        d = np.linalg.norm(x.cpu().numpy().reshape(-1) - xref.reshape(-1)) / max(np.linalg.norm(xref), 1e-30)
+        assert d <= (1e-4 if p.kind == "mesh" else 1e-6)
+    srv.close()
