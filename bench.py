@@ -44,7 +44,9 @@ W_BENCH, H_BENCH, HANDLES, OUTER, INNER = 1024, 1024, 64, 20, 20
 # algorithmic bytes per pixel (float32 planes, each touched once per launch)
 BYTES_APPLY_WARP = 72      # read r 12, M^-1 8, p_old 12, cos/sin 8, UrShape 8; write p 12, q 12
 BYTES_UPDATE_WARP = 80     # read delta 12, p 12, r 12, q 12, M^-1 8; write delta 12, r 12
-BYTES_INIT_WARP = 60       # read x 12, UrShape 8; write r 12, M^-1 8, delta 12, cos/sin 8 (GN)
+BYTES_INIT_WARP = 56       # as a solve runs it from the second outer iteration on (cos / sin of theta written by
+#                            the previous outer update): read dx, dy 8, cos/sin 8, UrShape 8; write r 12, M^-1 8,
+#                            delta 12 (GN)
 # single-reduction PCG iteration (pcg_form = 1), one launch per PCG iteration
 BYTES_FUSED_WARP = 120     # read z 12, w 12, p_old 12, cos/sin 8, UrShape 8, M^-1 8, delta 12;
 #                            write z 12, w 12, p 12, delta 12
@@ -1026,6 +1028,9 @@ PROFILE_CASES = {
     # name: (builder, description, float64 solver); small enough for ncu --set
     # full (a few GB on the device at most) and larger than L2
     "warp2048": (lambda synth: synth.warp_problem(2048, 2048, 256, seed=synth.BASE_SEED), "ARAP warp 2048^2", False),
+    # the single-reduction PCG iteration (pcg_form = 1): PCGInit, four iterations, the last step
+    "warp2048_fused": (lambda synth: synth.warp_problem(2048, 2048, 256, seed=synth.BASE_SEED),
+                       "ARAP warp 2048^2, single-reduction PCG iteration", False, 0, None, True),
     "poisson2048": (lambda synth: synth.poisson_problem(2048, 2048, seed=synth.BASE_SEED), "Poisson 2048^2 x 4",
                     False),
     "mesh8": (lambda synth: synth.mesh_problem(8, seed=synth.BASE_SEED), "ARAP mesh, icosphere level 8", False),
@@ -1095,6 +1100,7 @@ def run_profile_case(name, chunking_pin=None):
     builder, desc, f64 = PROFILE_CASES[name][:3]
     materialized = PROFILE_CASES[name][3] if len(PROFILE_CASES[name]) > 3 else 0
     form = PROFILE_CASES[name][4] if len(PROFILE_CASES[name]) > 4 else None
+    fused = PROFILE_CASES[name][5] if len(PROFILE_CASES[name]) > 5 else False
     if f64:
         gp = api.ProblemF64(builder(synth))
         chunking = None
@@ -1118,12 +1124,15 @@ def run_profile_case(name, chunking_pin=None):
     if materialized:
         rep = gp.solve_gn(1, 3, materialized=materialized)
         ms = rep["ms"]
+    elif fused:
+        ms = gp.profile_pcg_fused(4)
     else:
         ms = gp.profile_pcg(3)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     print(json.dumps({"profile_case": name, "workload": desc, "chunking": chunking,
-                      "ms_solve" if materialized else "ms_init_apply_update": ms}), flush=True)
+                      ("ms_solve" if materialized else "ms_init_iteration_last_step" if fused
+                       else "ms_init_apply_update"): ms}), flush=True)
     gp.close()
     return 0
 

@@ -299,8 +299,12 @@ void set_flags(opt_problem* pb, int lm, int use_precond, double* ehist) {
 }
 
 // --- stage launchers (dispatch on the domain) ------------------------------
-void st_init(opt_problem* pb, cudaStream_t st, int k, float dmin, float dmax) {
-  if (is_grid(pb)) launch_grid_init(pb->kind, grid_launch(pb, st), k, dmin, dmax);
+bool wide_warp(const opt_problem* pb) { return pb->kind == K_WARP && pb->hg.csn != nullptr; }
+
+// csn_in: a wide warp's PCGInit reads cos / sin of theta written by the
+// previous outer update (or launch_grid_csn)
+void st_init(opt_problem* pb, cudaStream_t st, int k, float dmin, float dmax, int csn_in = 0) {
+  if (is_grid(pb)) launch_grid_init(pb->kind, grid_launch(pb, st), k, dmin, dmax, csn_in);
   else launch_mesh_init(mesh_launch(pb, st), k, dmin, dmax);
 }
 void st_apply(opt_problem* pb, cudaStream_t st, const float* pov, int par, int update) {
@@ -315,8 +319,9 @@ void st_energy(opt_problem* pb, cudaStream_t st, int mode, int hist_idx) {
   if (is_grid(pb)) launch_grid_energy(pb->kind, grid_launch(pb, st), mode, hist_idx);
   else launch_mesh_energy(mesh_launch(pb, st), mode, hist_idx);
 }
-void st_step(opt_problem* pb, cudaStream_t st, int cond) {
-  if (is_grid(pb)) launch_grid_step(pb->kind, grid_launch(pb, st), cond);
+// csn_out: a wide warp's update also writes cos / sin of the new theta
+void st_step(opt_problem* pb, cudaStream_t st, int cond, int csn_out = 0) {
+  if (is_grid(pb)) launch_grid_step(pb->kind, grid_launch(pb, st), cond, csn_out);
   else launch_mesh_step(mesh_launch(pb, st), cond);
 }
 
@@ -354,12 +359,15 @@ opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cu
   const bool coop = !fused && use_persistent(pb, p);
   if (coop) CK(cudaMemsetAsync(pb->d_gbar, 0, sizeof(GridBarrier), st));
   for (int k = 0; k < p.outer; ++k) {
-    st_init(pb, st, k, dmin, dmax);
+    // from the second outer iteration on, cos / sin of theta come from the
+    // previous outer update (wide warps)
+    const int csn_next = k + 1 < p.outer;
+    st_init(pb, st, k, dmin, dmax, k > 0);
     if (p.materialized) csr_evalj(pb, st, p.materialized);
     if (fused) {
       for (int i = 0; i < p.inner; ++i) launch_grid_fused(grid_launch(pb, st), i);
       // Gauss-Newton: the last step and x += delta in one pass
-      launch_grid_fused_fin(grid_launch(pb, st), p.inner, lm ? 0 : 1);
+      launch_grid_fused_fin(grid_launch(pb, st), p.inner, lm ? 0 : 1, lm ? 0 : csn_next);
     } else if (coop) {
       // the barrier's counter restarts at 0 (a timed-out launch may leave it
       // mid-count); its timeout flag accumulates over the solve
@@ -373,11 +381,11 @@ opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cu
       }
     }
     if (!lm) {
-      if (!fused) st_step(pb, st, 0);
+      if (!fused) st_step(pb, st, 0, csn_next);
     } else {
       st_energy(pb, st, 1, -2);
       k_lm_decide<<<1, 32, 0, st>>>(pb->d_s, 1, p.eta, p.lambda_min, p.lambda_max, p.rel_tol);
-      st_step(pb, st, 1);
+      st_step(pb, st, 1, csn_next);
     }
   }
   st_energy(pb, st, 0, lm ? -1 : p.outer);
@@ -1327,8 +1335,12 @@ opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, flo
   if (status == OPT_OK) {
     copy_planes_in(prob, prob->x, prob->user_x, prob->nx, st);
     k_reset<<<1, 32, 0, st>>>(prob->d_s, 1, 0.0);
+    // wide warps: PCGInit as a solve runs it from the second outer iteration
+    // on, reading cos / sin of theta written ahead of it (not timed)
+    const int csn = wide_warp(prob);
+    if (csn) launch_grid_csn(grid_launch(prob, st));
     cudaEventRecord(ev[0], st);
-    st_init(prob, st, -1, 1e-6f, 1e32f);
+    st_init(prob, st, -1, 1e-6f, 1e32f, csn);
     cudaEventRecord(ev[1], st);
     for (int i = 0; i < n_iters; ++i) {
       cudaEventRecord(ev[2 + 4 * i], st);
@@ -1374,8 +1386,9 @@ opt_status opt_profile_pcg_fused(opt_problem* prob, int32_t n_iters, void* strea
   if (status == OPT_OK) {
     copy_planes_in(prob, prob->x, prob->user_x, prob->nx, st);
     k_reset<<<1, 32, 0, st>>>(prob->d_s, 1, 0.0);
+    launch_grid_csn(grid_launch(prob, st));
     cudaEventRecord(ev[0], st);
-    st_init(prob, st, -1, 1e-6f, 1e32f);
+    st_init(prob, st, -1, 1e-6f, 1e32f, 1);
     cudaEventRecord(ev[1], st);
     for (int i = 0; i < n_iters; ++i) {
       cudaEventRecord(ev[2 + 2 * i], st);
@@ -1383,7 +1396,7 @@ opt_status opt_profile_pcg_fused(opt_problem* prob, int32_t n_iters, void* strea
       cudaEventRecord(ev[3 + 2 * i], st);
     }
     cudaEventRecord(ev[2 + 2 * n_iters], st);
-    launch_grid_fused_fin(grid_launch(prob, st), n_iters, 0);
+    launch_grid_fused_fin(grid_launch(prob, st), n_iters, 0, 0);
     cudaEventRecord(ev[3 + 2 * n_iters], st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) status = cuda_fail(e, "opt_profile_pcg_fused");

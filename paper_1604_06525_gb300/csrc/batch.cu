@@ -320,7 +320,10 @@ void enqueue_batch(opt_batch* b, const opt_solve_params& p, bool lm, cudaStream_
   // for (as a solo solve of each member would), the others the two-pass one
   auto fused = [&](const GridGroup& g) { return p.pcg_form == 1 && p.inner > 0 && g.kind == K_WARP && g.tw == 128; };
   for (int k = 0; k < outer; ++k) {
-    for (GridGroup& g : b->grids) launch_grid_init(g.kind, gl(g, st), k, dmin, dmax);
+    // from the second outer iteration on, the wide warps' cos / sin of theta
+    // come from the previous outer update
+    const int csn_next = k + 1 < outer;
+    for (GridGroup& g : b->grids) launch_grid_init(g.kind, gl(g, st), k, dmin, dmax, k > 0);
     for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_init(ml(g, st), k, dmin, dmax);
     for (int i = 0; i < p.inner; ++i) {
       for (GridGroup& g : b->grids) {
@@ -332,15 +335,16 @@ void enqueue_batch(opt_batch* b, const opt_solve_params& p, bool lm, cudaStream_
       for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_update(ml(g, st), i);
     }
     // the single-reduction groups' last step (with x += delta under GN)
-    for (GridGroup& g : b->grids) if (fused(g)) launch_grid_fused_fin(gl(g, st), p.inner, lm ? 0 : 1);
+    for (GridGroup& g : b->grids)
+      if (fused(g)) launch_grid_fused_fin(gl(g, st), p.inner, lm ? 0 : 1, lm ? 0 : csn_next);
     if (!lm) {
-      for (GridGroup& g : b->grids) if (!fused(g)) launch_grid_step(g.kind, gl(g, st), 0);
+      for (GridGroup& g : b->grids) if (!fused(g)) launch_grid_step(g.kind, gl(g, st), 0, csn_next);
       for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_step(ml(g, st), 0);
     } else {
       for (GridGroup& g : b->grids) launch_grid_energy(g.kind, gl(g, st), 1, -2);
       for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_energy(ml(g, st), 1, -2);
       k_lm_decide_tab<<<(n + 127) / 128, 128, 0, st>>>(b->d_stab, n, p.eta, p.lambda_min, p.lambda_max, p.rel_tol);
-      for (GridGroup& g : b->grids) launch_grid_step(g.kind, gl(g, st), 1);
+      for (GridGroup& g : b->grids) launch_grid_step(g.kind, gl(g, st), 1, csn_next);
       for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_step(ml(g, st), 1);
     }
   }
@@ -574,7 +578,7 @@ opt_status batch_prepare_round(opt_batch* b, const opt_solve_params& p) {
 void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_t st) {
   const float dmin = (float)p.diag_min, dmax = (float)p.diag_max;
   const int n = (int)b->probs.size();
-  for (GridGroup& g : b->grids) launch_grid_init(g.kind, gl(g, st), -2, dmin, dmax);
+  for (GridGroup& g : b->grids) launch_grid_init(g.kind, gl(g, st), -2, dmin, dmax, 0);
   for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_init(ml(g, st), -2, dmin, dmax);
   for (int i = 0; i < p.inner; ++i) {
     for (GridGroup& g : b->grids) launch_grid_apply(g.kind, gl(g, st), nullptr, i, 1);
@@ -585,7 +589,7 @@ void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_
   for (GridGroup& g : b->grids) launch_grid_energy(g.kind, gl(g, st), 1, -2);
   for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_energy(ml(g, st), 1, -2);
   k_lm_decide_tab<<<(n + 127) / 128, 128, 0, st>>>(b->d_stab, n, p.eta, p.lambda_min, p.lambda_max, p.rel_tol);
-  for (GridGroup& g : b->grids) launch_grid_step(g.kind, gl(g, st), 1);
+  for (GridGroup& g : b->grids) launch_grid_step(g.kind, gl(g, st), 1, 0);
   for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_step(ml(g, st), 1);
   k_gather_results<<<n, 128, 0, st>>>(b->d_stab, b->d_htab, n, 0, b->d_sout, b->d_hout);
 }

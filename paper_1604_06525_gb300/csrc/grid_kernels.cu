@@ -947,6 +947,18 @@ __global__ void __launch_bounds__(NT, 2) k_warp_apply_wide(const GridProb* __res
     apply_wide_body<MASK, false>(sm, ch, pr, tiles, part, p_in_override, par, update, phase);
 }
 
+// cos / sin of the new theta quad into the cos / sin planes (wide warps: the
+// next PCGInit reads them instead of evaluating them on its tile and halo)
+__device__ __forceinline__ void store_csn(const GridProb& pr, long long i, const float4& th) {
+  float4 cs, sn;
+  sincosf(th.x, &sn.x, &cs.x);
+  sincosf(th.y, &sn.y, &cs.y);
+  sincosf(th.z, &sn.z, &cs.z);
+  sincosf(th.w, &sn.w, &cs.w);
+  *reinterpret_cast<float4*>(pr.csn + i) = cs;
+  *reinterpret_cast<float4*>(pr.csn + pr.plane + i) = sn;
+}
+
 // ---------------------------------------------------------------------------
 // Single-reduction PCG iteration of the wide warp (tw = 128): one launch per
 // PCG iteration instead of applyJTJ + vector update.  The Jacobi-PCG of
@@ -1354,10 +1366,11 @@ __global__ void __launch_bounds__(NT, 2) k_warp_fused_wide(const GridProb* __res
 // whose alpha is known (p of parity `par`), unless the loop has none pending.
 // step = 1 (Gauss-Newton): the outer update x += delta follows in the same
 // pass (the same roundings as the update, then k_grid_step), and delta is
-// not stored.
+// not stored; csn_out: also cos / sin of the new theta.
 __global__ void __launch_bounds__(NT) k_warp_fused_fin(const GridProb* __restrict__ probs,
                                                        const Chunk* __restrict__ chunks,
-                                                       const int* __restrict__ tiles, int par, int step) {
+                                                       const int* __restrict__ tiles, int par, int step,
+                                                       int csn_out) {
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   pdl_begin();
@@ -1382,8 +1395,10 @@ __global__ void __launch_bounds__(NT) k_warp_fused_fin(const GridProb* __restric
       if (alpha != 0.f) dv = fma4s(alpha, __ldcg(reinterpret_cast<const float4*>(pin + c * pl + i)), dv);
       if (step) {
         float4* x = reinterpret_cast<float4*>(pr.x + c * pl + i);
-        const float4 xv = *x;
-        *x = make_float4(xv.x + dv.x, xv.y + dv.y, xv.z + dv.z, xv.w + dv.w);
+        float4 xv = *x;
+        xv = make_float4(xv.x + dv.x, xv.y + dv.y, xv.z + dv.z, xv.w + dv.w);
+        *x = xv;
+        if (c == 2 && csn_out) store_csn(pr, i, xv);
       } else {
         *d = dv;
       }
@@ -1403,7 +1418,7 @@ __global__ void __launch_bounds__(NT) k_warp_fused_fin(const GridProb* __restric
 //   diag (d rows)   += 2 w,                   diag (theta row)  += w |G_i|^2
 //   E               += w |a + e_i|^2   (own residuals only)
 // Writes r = b = -J^T F, M^-1, delta = 0, the LM diagonal, cos / sin of theta.
-constexpr int NRAW_I = 5;        // dx dy theta ux uy
+constexpr int NRAW_I = 6;        // dx dy theta ux uy (-), or with cos / sin read: dx dy cos ux uy sin
 constexpr int NSTG_I = 7;        // dx dy cos sin ux uy valid, quads stored as pixels 0 2 1 3
 
 struct InitSmem {
@@ -1413,17 +1428,23 @@ struct InitSmem {
   unsigned long long bar;        // tensor-copy completion of the raw planes
 };
 
-// Phase 2 for one staged quad: cos / sin of theta, copied values, validity,
-// in the staged order 0 2 1 3.
-template <bool MASK>
+// Phase 2 for one staged quad: cos / sin of theta (evaluated, or with CSN
+// copied from the planes the previous outer update wrote), copied values,
+// validity, in the staged order 0 2 1 3.
+template <bool MASK, bool CSN>
 __device__ __forceinline__ void init_stage_quad(InitSmem& sm, int row, int lane, const GridProb& pr, int gx, int gy) {
   const int c = 4 + 4 * lane;
-  const float4 th = lds4(&sm.raw[2].v[row][c]);
   float4 cs, sn;
-  sincosf(th.x, &sn.x, &cs.x);
-  sincosf(th.y, &sn.y, &cs.y);
-  sincosf(th.z, &sn.z, &cs.z);
-  sincosf(th.w, &sn.w, &cs.w);
+  if (CSN) {
+    cs = lds4(&sm.raw[2].v[row][c]);
+    sn = lds4(&sm.raw[5].v[row][c]);
+  } else {
+    const float4 th = lds4(&sm.raw[2].v[row][c]);
+    sincosf(th.x, &sn.x, &cs.x);
+    sincosf(th.y, &sn.y, &cs.y);
+    sincosf(th.z, &sn.z, &cs.z);
+    sincosf(th.w, &sn.w, &cs.w);
+  }
   sts4(&sm.stg[0][row][c], swz4(lds4(&sm.raw[0].v[row][c])));
   sts4(&sm.stg[1][row][c], swz4(lds4(&sm.raw[1].v[row][c])));
   sts4(&sm.stg[2][row][c], swz4(cs));
@@ -1471,7 +1492,7 @@ __device__ __forceinline__ void init_pair2(const OwnI2& o, float2 dxj, float2 dy
   A.np = add2(A.np, mj);
 }
 
-template <bool MASK>
+template <bool MASK, bool CSN>
 __device__ __forceinline__ void k_warp_init_wide_body(InitSmem& sm, const Chunk& ch, const GridProb& pr,
     const int* __restrict__ tiles, double* __restrict__ part, int k_outer, float dmin, float dmax) {
   Scalars* s = pr.s;
@@ -1483,10 +1504,10 @@ __device__ __forceinline__ void k_warp_init_wide_body(InitSmem& sm, const Chunk&
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   F2x2 acc_rz = f2x2_zero(), acc_E = f2x2_zero();
   // raw planes by tensor copies: dx, dy, theta from the unknowns, UrShape
-  // from the slab
+  // from the slab; with CSN cos / sin (slab) in place of theta
   auto plane = [&](int k, int& z, int& m) {
-    m = k < 3 ? 1 : 0;
-    z = k < 3 ? k : zslab(pr, 4) + k - 3;
+    m = (k < 2 || (k == 2 && !CSN)) ? 1 : 0;
+    z = k < 2 ? k : k == 2 ? (CSN ? zslab(pr, 3) : 2) : k < 5 ? zslab(pr, 4) + k - 3 : (CSN ? zslab(pr, 3) + 1 : -1);
   };
   if (tid == 0) mbar_init(&sm.bar);
   __syncthreads();
@@ -1509,16 +1530,21 @@ __device__ __forceinline__ void k_warp_init_wide_body(InitSmem& sm, const Chunk&
       staging_timeout(s, &sm.bar, pb);
       return;
     }
-    init_stage_quad<MASK>(sm, ty + 1, lane, pr, gx, gy);
+    init_stage_quad<MASK, CSN>(sm, ty + 1, lane, pr, gx, gy);
     if (tid < 64) {
       const int row = tid < 32 ? 0 : HH - 1;
-      init_stage_quad<MASK>(sm, row, lane, pr, gx, y0 - 1 + row);
+      init_stage_quad<MASK, CSN>(sm, row, lane, pr, gx, y0 - 1 + row);
     } else if (tid < 64 + 2 * TH) {
       const int h = tid - 64;
       const int row = 1 + (h % TH), side = h / TH;
       const int col = side ? 4 + W4 : 3;
       float sn, cs;
-      sincosf(sm.raw[2].v[row][col], &sn, &cs);
+      if (CSN) {
+        cs = sm.raw[2].v[row][col];
+        sn = sm.raw[5].v[row][col];
+      } else {
+        sincosf(sm.raw[2].v[row][col], &sn, &cs);
+      }
       sm.stg[0][row][col] = sm.raw[0].v[row][col];
       sm.stg[1][row][col] = sm.raw[1].v[row][col];
       sm.stg[2][row][col] = cs;
@@ -1637,8 +1663,10 @@ __device__ __forceinline__ void k_warp_init_wide_body(InitSmem& sm, const Chunk&
       *reinterpret_cast<float4*>(pr.d + i) = z;
       *reinterpret_cast<float4*>(pr.d + pl + i) = z;
       *reinterpret_cast<float4*>(pr.d + 2 * pl + i) = z;
-      *reinterpret_cast<float4*>(pr.csn + i) = swz4(O[2]);
-      *reinterpret_cast<float4*>(pr.csn + pl + i) = swz4(O[3]);
+      if (!CSN) {
+        *reinterpret_cast<float4*>(pr.csn + i) = swz4(O[2]);
+        *reinterpret_cast<float4*>(pr.csn + pl + i) = swz4(O[3]);
+      }
       if (pr.lm) {
         *reinterpret_cast<float4*>(pr.dc + i) = make_float4(cd[0], cd[1], cd[2], cd[3]);
         *reinterpret_cast<float4*>(pr.dc + pl + i) = make_float4(ct[0], ct[1], ct[2], ct[3]);
@@ -1673,7 +1701,10 @@ __device__ __forceinline__ void k_warp_init_wide_body(InitSmem& sm, const Chunk&
 #ifndef WARP_INIT_WIDE_MINB
 #define WARP_INIT_WIDE_MINB 2       // resident blocks per SM the wide warp PCGInit is compiled for
 #endif
-template <bool MASK>
+// CSN: cos / sin of theta are read from the planes the previous outer
+// update wrote (k_grid_step / k_warp_fused_fin with csn_out) instead of being
+// evaluated on the tile and its halo; the same bits either way.
+template <bool MASK, bool CSN>
 __global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(const GridProb* __restrict__ probs,
     const Chunk* __restrict__ chunks, const int* __restrict__ tiles, double* __restrict__ part, int k_outer,
     float dmin, float dmax) {
@@ -1682,7 +1713,7 @@ __global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(cons
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   pdl_begin();
-  if (tma_ready(pr, &sm)) k_warp_init_wide_body<MASK>(sm, ch, pr, tiles, part, k_outer, dmin, dmax);
+  if (tma_ready(pr, &sm)) k_warp_init_wide_body<MASK, CSN>(sm, ch, pr, tiles, part, k_outer, dmin, dmax);
 }
 
 // E(x) (mode 0) or E(x + delta) and |F(x) + J(x) delta|^2 (mode 1).
@@ -2711,10 +2742,12 @@ __global__ void __launch_bounds__(NT, 2) k_warp_pcg_coop(const GridProb* __restr
   }
 }
 
+// x += delta over the owned pixels (cond: 0 always, 1 only if s->accept);
+// csn_out (wide warps): also cos / sin of the new theta.
 template <int NX>
 __global__ void __launch_bounds__(NT) k_grid_step(const GridProb* __restrict__ probs,
                                                   const Chunk* __restrict__ chunks,
-                                                  const int* __restrict__ tiles, int cond) {
+                                                  const int* __restrict__ tiles, int cond, int csn_out) {
   const Chunk ch = chunks[blockIdx.x];
   const GridProb pr = probs[ch.prob];
   pdl_begin();
@@ -2723,6 +2756,7 @@ __global__ void __launch_bounds__(NT) k_grid_step(const GridProb* __restrict__ p
   const long long pl = pr.plane;
   float* __restrict__ x = pr.x;
   const float* __restrict__ d = pr.d;
+  const bool csn = NX == 3 && csn_out && pr.csn;
   // float4 quads of the chunk's tiles; the pitched padding columns hold zeros
   // in both planes, so only rows past H are skipped
   const int qrow = pr.tw / 4, qpt = qrow * TH;
@@ -2740,9 +2774,31 @@ __global__ void __launch_bounds__(NT) k_grid_step(const GridProb* __restrict__ p
       dv[c] = __ldg(reinterpret_cast<const float4*>(d + c * pl + i));
     }
 #pragma unroll
-    for (int c = 0; c < NX; ++c)
-      *reinterpret_cast<float4*>(x + c * pl + i) =
-          make_float4(xv[c].x + dv[c].x, xv[c].y + dv[c].y, xv[c].z + dv[c].z, xv[c].w + dv[c].w);
+    for (int c = 0; c < NX; ++c) {
+      xv[c] = make_float4(xv[c].x + dv[c].x, xv[c].y + dv[c].y, xv[c].z + dv[c].z, xv[c].w + dv[c].w);
+      *reinterpret_cast<float4*>(x + c * pl + i) = xv[c];
+    }
+    if (csn) store_csn(pr, i, xv[2]);
+  }
+}
+
+// cos / sin of theta at the current unknowns (wide warps; before a PCGInit
+// that reads them when no outer update wrote them)
+__global__ void __launch_bounds__(NT) k_warp_csn(const GridProb* __restrict__ probs, const Chunk* __restrict__ chunks,
+                                                 const int* __restrict__ tiles) {
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  pdl_begin();
+  if (!pr.csn) return;
+  const int qrow = W4 / 4, qpt = qrow * TH;
+  const int nq = (ch.end - ch.begin) * qpt;
+  for (int u = threadIdx.x; u < nq; u += NT) {
+    const int tc = tiles[ch.begin + u / qpt];
+    const int q = u % qpt;
+    const int gy = tile_y0(tc) + q / qrow;
+    if (gy >= pr.H) continue;
+    const long long i = (long long)gy * pr.P + tile_x0(tc, W4) + 4 * (q % qrow);
+    store_csn(pr, i, *reinterpret_cast<const float4*>(pr.x + 2 * pr.plane + i));
   }
 }
 
@@ -2765,13 +2821,21 @@ cudaError_t grid_kernels_prepare() {
       e = cudaFuncSetAttribute(k_warp_apply_wide<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     const int ibytes = (int)sizeof(InitSmem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_warp_init_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ibytes);
+      e = cudaFuncSetAttribute(k_warp_init_wide<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ibytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_warp_init_wide<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ibytes);
+      e = cudaFuncSetAttribute(k_warp_init_wide<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, ibytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_warp_init_wide<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      e = cudaFuncSetAttribute(k_warp_init_wide<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ibytes);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_warp_init_wide<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      e = cudaFuncSetAttribute(k_warp_init_wide<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ibytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_init_wide<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_init_wide<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_init_wide<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_warp_init_wide<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     const int pbytes = (int)sizeof(PoisWideSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_poisson_apply_wide<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, pbytes);
@@ -2802,21 +2866,19 @@ cudaError_t grid_kernels_prepare() {
   return status;
 }
 
-void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, float dmax) {
-  if (kind == K_WARP && L.tw == 128 && L.masked)
-    launch_pdl(k_warp_init_wide<true>, L.nchunks, NT, sizeof(InitSmem), L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer,
-                                                                        dmin, dmax);
-  else if (kind == K_WARP && L.tw == 128)
-    launch_pdl(k_warp_init_wide<false>, L.nchunks, NT, sizeof(InitSmem), L.stream, L.probs, L.chunks, L.tiles, L.part,
-                                                                         k_outer, dmin, dmax);
-  else if (kind == K_WARP)
+void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, float dmax, int csn_in) {
+  if (kind == K_WARP && L.tw == 128) {
+    auto k = L.masked ? (csn_in ? k_warp_init_wide<true, true> : k_warp_init_wide<true, false>)
+                      : (csn_in ? k_warp_init_wide<false, true> : k_warp_init_wide<false, false>);
+    launch_pdl(k, L.nchunks, NT, sizeof(InitSmem), L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
+  } else if (kind == K_WARP) {
     launch_pdl(k_warp_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
-  else
-    if (L.tw == W4)
-      launch_pdl(k_poisson_init_wide, L.nchunks, NT, sizeof(PoisInitSmem), L.stream, L.probs, L.chunks, L.tiles,
-                 L.part, k_outer, dmin, dmax);
-    else
-      launch_pdl(k_poisson_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
+  } else if (L.tw == W4) {
+    launch_pdl(k_poisson_init_wide, L.nchunks, NT, sizeof(PoisInitSmem), L.stream, L.probs, L.chunks, L.tiles,
+               L.part, k_outer, dmin, dmax);
+  } else {
+    launch_pdl(k_poisson_init, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, k_outer, dmin, dmax);
+  }
 }
 
 void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, int par, int update) {
@@ -2856,8 +2918,12 @@ void launch_grid_fused(const GridLaunch& L, int it) {
                L.part, it);
 }
 
-void launch_grid_fused_fin(const GridLaunch& L, int par, int step) {
-  launch_pdl(k_warp_fused_fin, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, par, step);
+void launch_grid_fused_fin(const GridLaunch& L, int par, int step, int csn_out) {
+  launch_pdl(k_warp_fused_fin, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, par, step, csn_out);
+}
+
+void launch_grid_csn(const GridLaunch& L) {
+  launch_pdl(k_warp_csn, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles);
 }
 
 void launch_grid_energy(int kind, const GridLaunch& L, int mode, int hist_idx) {
@@ -2873,11 +2939,11 @@ void launch_pois_sdeg(int W, int H, int P, const uint8_t* mask, uint8_t* out, cu
   k_pois_sdeg<<<blocks, NT, 0, st>>>(W, H, P, mask, out);
 }
 
-void launch_grid_step(int kind, const GridLaunch& L, int cond) {
+void launch_grid_step(int kind, const GridLaunch& L, int cond, int csn_out) {
   if (kind == K_WARP)
-    launch_pdl(k_grid_step<3>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, cond);
+    launch_pdl(k_grid_step<3>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, cond, csn_out);
   else
-    launch_pdl(k_grid_step<4>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, cond);
+    launch_pdl(k_grid_step<4>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, cond, 0);
 }
 
 int grid_coop_capacity(int masked) {

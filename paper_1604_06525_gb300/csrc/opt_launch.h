@@ -50,17 +50,21 @@ inline void launch_pdl(void (*k)(KArgs...), unsigned grid, unsigned block, size_
 
 // grid_kernels.cu
 cudaError_t grid_kernels_prepare();   // one-time kernel attributes (call outside capture)
-void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, float dmax);
+// csn_in (wide warps): PCGInit reads cos / sin of theta from the planes an
+// outer update (csn_out) or launch_grid_csn wrote instead of evaluating them
+void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, float dmax, int csn_in);
 void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, int par, int update);
 void launch_grid_update(int kind, const GridLaunch& L, int par);
 void launch_grid_energy(int kind, const GridLaunch& L, int mode, int hist_idx);
 // Single-reduction PCG (wide warp tiles; problems planned with z / w
 // buffers): iteration `it` (0 starts from r_0, M^-1), and the pending step of
 // the last iteration (p of parity par = the iteration count); step = 1 also
-// applies the Gauss-Newton update x += delta
+// applies the Gauss-Newton update x += delta (csn_out: and cos / sin of theta)
 void launch_grid_fused(const GridLaunch& L, int it);
-void launch_grid_fused_fin(const GridLaunch& L, int par, int step);
-void launch_grid_step(int kind, const GridLaunch& L, int cond);
+void launch_grid_fused_fin(const GridLaunch& L, int par, int step, int csn_out);
+void launch_grid_step(int kind, const GridLaunch& L, int cond, int csn_out);
+// cos / sin of theta at the current unknowns into the cos / sin planes (wide warps)
+void launch_grid_csn(const GridLaunch& L);
 // Poisson, tile width 128: the degree plane the wide kernels read (S_i + 1 on
 // free pixels, 0 elsewhere; pitched like the mask, P x H bytes)
 void launch_pois_sdeg(int W, int H, int P, const uint8_t* mask, uint8_t* out, cudaStream_t st);

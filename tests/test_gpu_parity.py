@@ -741,3 +741,27 @@ def test_dot_products_carry_float64_accuracy(api, case):
         exact = float(np.dot(p.astype(np.float64), q.cpu().numpy().reshape(-1).astype(np.float64)))
         assert relE(pq, exact) <= 1e-9, (case, lam, pq, exact)
     gp.close()
+
+
+@pytest.mark.parametrize("method,mf,form", [("gn", 0.0, 0), ("gn", 0.2, 1), ("lm", 0.0, 1), ("lm", 0.2, 0)])
+def test_wide_warp_init_reads_cos_sin_of_previous_update(api, method, mf, form):
+    """From the second outer iteration on, the wide warp's PCGInit takes cos /
+    sin of theta from the planes the previous outer update wrote instead of
+    evaluating them: E(x_k) it reports must equal the energy evaluated
+    independently (opt_eval_energy, its own cos / sin) at the same x_k, to
+    the rounding of two differently ordered float32 residual evaluations
+    (both sums compensated; about 1e-9 here, where cos / sin of the previous
+    iterate would be off by the step's rotation, 1e-3 and more)."""
+    import torch
+    prob = make_grid("warp", 260, 24, mf, seed=171)
+    gp = api.Problem(prob)
+    x0 = torch.as_tensor(prob.x0, device="cuda")
+    solve = getattr(gp, f"solve_{method}")
+    rep = solve(3, 6, pcg_form=form)
+    for k in (1, 2):
+        gp.x.copy_(x0)
+        rk = solve(k, 6, pcg_form=form)
+        assert rk["E_history"][:k] == rep["E_history"][:k]
+        Ek = gp.energy()
+        assert relE(rep["E_history"][k], Ek) <= 1e-8, (k, rep["E_history"][k], Ek)
+        assert relE(rk["E_history"][k], Ek) <= 1e-8
