@@ -547,7 +547,9 @@ __device__ __forceinline__ float minv_entry(float dg, float lam, float dmin, flo
   if (dc_out) *dc_out = dc;
   if (!use_precond) return 1.0f;
   const float m = dg + lam * dc;
-  return m != 0.0f ? 1.0f / m : 1.0f;
+  // the correctly rounded reciprocal: the same value as 1.0f / m, without the
+  // general division's numerator handling
+  return m != 0.0f ? __frcp_rn(m) : 1.0f;
 }
 
 // ---------------------------------------------------------------------------
