@@ -56,6 +56,9 @@ PCG_FORM = 1               # the headline's PCG iteration: 1 single-reduction, 0
 BYTES_APPLY_POISSON = 69   # read r 16, M^-1 4, p_old 16, mask 1; write p 16, q 16
 BYTES_UPDATE_POISSON = 100  # read delta 16, p 16, r 16, q 16, M^-1 4; write delta 16, r 16
 BYTES_INIT_POISSON = 69    # read X 16, T 16, mask 1; write r 16, M^-1 4, delta 16 (GN)
+BYTES_FUSED_POISSON = 133  # single-reduction iteration: read z, w, p_old 48, degree 1, M^-1 4, delta 16;
+#                            write z, w, p, delta 64
+BYTES_FIN_POISSON = 48     # the last iteration's step: read delta 16, p 16; write delta 16
 # ARAP mesh, per vertex (6 unknowns, 6 directed edges per vertex on an icosphere): the
 # algorithmic bytes of the method, each array touched once, records and padding the
 # kernels add not counted (a lower numerator than the bytes they move)
@@ -411,6 +414,18 @@ def roofline_beyond_l2(api, synth, torch, peak):
         ("k_poisson_init_wide" if c["tile_w"] == 128 else "k_poisson_init", BYTES_INIT_POISSON, OUTER),
         ("k_poisson_apply_wide" if c["tile_w"] == 128 else "k_poisson_apply", BYTES_APPLY_POISSON, OUTER * INNER),
         ("k_grid_update<4>", BYTES_UPDATE_POISSON, OUTER * INNER)), free, peak)
+    if PCG_FORM == 1 and cfg["tile_w"] == 128:
+        gp.profile_pcg_fused(4)
+        times = gp.profile_pcg_fused(20)
+        two_pass = kp
+        kp = {}
+        for (name, bpu, per_solve), ms in zip((("k_poisson_init_wide", BYTES_INIT_POISSON, OUTER),
+                                               ("k_poisson_fused_wide", BYTES_FUSED_POISSON, OUTER * INNER),
+                                               ("k_grid_fused_fin<4>", BYTES_FIN_POISSON, OUTER)), times):
+            ach = bpu * free / (ms * 1e-3) / 1e9
+            kp[name] = {"ms": ms, "bytes": bpu * free, "achieved": ach, "frac": ach / peak,
+                        "launches_per_solve": per_solve}
+        cfg = dict(cfg, pcg_form=1, two_pass_kernels=two_pass)
     res["poisson_4096x4096x4"] = {"unit_of_work": "free pixel", "units": free, "kernels": kp, "config": cfg}
     gp.close()
     del pp
@@ -836,14 +851,18 @@ def run_ours(args):
         gpp = api.Problem(pp)
         gpp.autotune()
         xp0 = gpp.x.clone()
-        rr = timed(gpp, xp0, gpp.solve_gn)
+        rr = timed(gpp, xp0, gpp.solve_gn, pcg_form=PCG_FORM)
+        rr_ptp = timed(gpp, xp0, gpp.solve_gn, pcg_form=0)
         rrm = timed(gpp, xp0, gpp.solve_gn, materialized=1)
         rra = timed(gpp, xp0, gpp.solve_gn, materialized=2)
         msp = statistics.median(r_["ms"] for r_ in rr)
         mspm = statistics.median(r_["ms"] for r_ in rrm)
+        ms_ptp = statistics.median(r_["ms"] for r_ in rr_ptp)
         extra["poisson_1024x1024x4_gn20x20"] = {"pcg_iters_per_s": OUTER * INNER / (msp / 1e3), "ms_per_solve": msp,
                                                "E0": rr[-1]["E0"], "E_final": rr[-1]["E_final"],
-                                               "config": gpp.config()}
+                                               "config": dict(gpp.config(), pcg_form=PCG_FORM),
+                                               "two_pass_ms_per_solve": ms_ptp,
+                                               "two_pass_E_final": rr_ptp[-1]["E_final"]}
         e_pois = rr[-1]["E_history"]
         extra["poisson_1024x1024x4_materialized_gn20x20"] = {
             "pcg_iters_per_s": OUTER * INNER / (mspm / 1e3), "ms_per_solve": mspm,

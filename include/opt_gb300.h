@@ -195,14 +195,15 @@ typedef struct {
                                  (applyJTJ with p.q, then the vector update with r.z: two
                                  grid-wide reductions, two launches per iteration).
                                  1 = single-reduction iteration, taken by matrix-free solves of
-                                 OPT_ARAP_WARP_2D grids planned with 128-pixel tiles (other
-                                 problems run form 0): one launch per iteration computes p.q,
-                                 q.z and q.M^-1 q, from which alpha and the next r.z follow
-                                 (r.z' = r.z - 2 alpha q.z + alpha^2 q.M^-1 q), and carries
-                                 z = M^-1 r and w = M^-1 q instead of r and q.  The same
-                                 iterates in exact arithmetic; in float32 they differ from form 0
-                                 by rounding.  Batches (and the server) apply it to their members
-                                 of that kind, the others run form 0.  Other values:
+                                 OPT_ARAP_WARP_2D and OPT_POISSON_2D grids planned with 128-pixel
+                                 tiles (other problems run form 0): it carries z = M^-1 r and
+                                 w = M^-1 q instead of r and q, and one launch per iteration
+                                 reduces p.q, q.z, q.M^-1 q and r.z together: alpha = r.z / p.q
+                                 as in form 0, and the next r.z, which sets beta, by
+                                 r.z' = r.z - 2 alpha q.z + alpha^2 q.M^-1 q.  The same iterates
+                                 in exact arithmetic; in float32 they differ from form 0 by
+                                 rounding.  Batches (and the server) apply it to their members of
+                                 those kinds, the others run form 0.  Other values:
                                  OPT_ERR_INVALID_ARG. */
 } opt_solve_params;
 
@@ -329,8 +330,8 @@ opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, flo
  * final step, each launch bracketed by CUDA events on `stream`; writes ms[0]
  * = PCGInit, ms[1] = mean of iterations 1 .. n_iters - 1 (iteration 0 reads
  * r and M^-1 instead of z and w), ms[2] = the final step (host, 3 floats).
- * OPT_ERR_INVALID_ARG unless the problem is an OPT_ARAP_WARP_2D grid planned
- * with 128-pixel tiles, or n_iters < 2.  Leaves delta = the PCG step after
+ * OPT_ERR_INVALID_ARG unless the problem is an OPT_ARAP_WARP_2D or
+ * OPT_POISSON_2D grid planned with 128-pixel tiles, or n_iters < 2.  Leaves delta = the PCG step after
  * n_iters iterations (lambda = 0). */
 opt_status opt_profile_pcg_fused(opt_problem* prob, int32_t n_iters, void* stream, float* ms);
 

@@ -345,10 +345,12 @@ bool use_persistent(const opt_problem* pb, const opt_solve_params& p) {
   return p.persistent && !p.materialized && p.inner > 0 && pb->d_gbar && pb->nchunks <= pb->coop_cap;
 }
 
-// The single-reduction PCG iteration runs where asked for on wide-tile warps
-// (planned with z / w buffers), matrix-free; elsewhere the two-pass form.
+// The single-reduction PCG iteration runs where asked for on warps and
+// Poisson problems planned with 128-pixel tiles (they have z / w buffers),
+// matrix-free; elsewhere the two-pass form.
 bool use_fused(const opt_problem* pb, const opt_solve_params& p) {
-  return p.pcg_form == 1 && !p.materialized && pb->kind == K_WARP && pb->hg.zb != nullptr;
+  return p.pcg_form == 1 && !p.materialized && (pb->kind == K_WARP || pb->kind == K_POISSON) &&
+         pb->hg.zb != nullptr;
 }
 
 opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cudaStream_t st) {
@@ -365,9 +367,9 @@ opt_status enqueue_solve(opt_problem* pb, const opt_solve_params& p, bool lm, cu
     st_init(pb, st, k, dmin, dmax, k > 0);
     if (p.materialized) csr_evalj(pb, st, p.materialized);
     if (fused) {
-      for (int i = 0; i < p.inner; ++i) launch_grid_fused(grid_launch(pb, st), i);
+      for (int i = 0; i < p.inner; ++i) launch_grid_fused(pb->kind, grid_launch(pb, st), i);
       // Gauss-Newton: the last step and x += delta in one pass
-      launch_grid_fused_fin(grid_launch(pb, st), p.inner, lm ? 0 : 1, lm ? 0 : csn_next);
+      launch_grid_fused_fin(pb->kind, grid_launch(pb, st), p.inner, lm ? 0 : 1, lm ? 0 : csn_next);
     } else if (coop) {
       // the barrier's counter restarts at 0 (a timed-out launch may leave it
       // mid-count); its timeout flag accumulates over the solve
@@ -761,8 +763,8 @@ opt_status opt_problem_create_grid(const opt_grid_desc* d, const opt_solve_param
   // multiples of 32 floats, so every plane stays 128-byte aligned)
   const bool has_csn = warp && tw == 128;
   const bool has_sdeg = !warp && tw == 128;
-  // wide warps: the single-reduction PCG's double-buffered z and w planes
-  const int nzw = has_csn ? 4 * nx : 0;
+  // 128-pixel tiles: the single-reduction PCG's double-buffered z and w planes
+  const int nzw = tw == 128 ? 4 * nx : 0;
   const int nfp = nx + nm + 2 * nx + nx + nx + (has_csn ? 2 : 0) + nc + nzw;
   const size_t nslab = (size_t)nfp * pl + (d->mask ? pl / 4 : 0) + (has_sdeg ? pl / 4 : 0);
   float* slab = nullptr;
@@ -1375,7 +1377,7 @@ opt_status opt_profile_pcg(opt_problem* prob, int32_t n_iters, void* stream, flo
 
 opt_status opt_profile_pcg_fused(opt_problem* prob, int32_t n_iters, void* stream, float* ms) {
   if (!prob || n_iters < 2 || !ms) return OPT_ERR_INVALID_ARG;
-  if (prob->kind != K_WARP || !prob->hg.zb) return OPT_ERR_INVALID_ARG;
+  if ((prob->kind != K_WARP && prob->kind != K_POISSON) || !prob->hg.zb) return OPT_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   CKS(hook_prepare(prob, 0.0, false));
   const int nev = 2 * (n_iters + 2);
@@ -1386,17 +1388,18 @@ opt_status opt_profile_pcg_fused(opt_problem* prob, int32_t n_iters, void* strea
   if (status == OPT_OK) {
     copy_planes_in(prob, prob->x, prob->user_x, prob->nx, st);
     k_reset<<<1, 32, 0, st>>>(prob->d_s, 1, 0.0);
-    launch_grid_csn(grid_launch(prob, st));
+    const int csn = wide_warp(prob);
+    if (csn) launch_grid_csn(grid_launch(prob, st));
     cudaEventRecord(ev[0], st);
-    st_init(prob, st, -1, 1e-6f, 1e32f, 1);
+    st_init(prob, st, -1, 1e-6f, 1e32f, csn);
     cudaEventRecord(ev[1], st);
     for (int i = 0; i < n_iters; ++i) {
       cudaEventRecord(ev[2 + 2 * i], st);
-      launch_grid_fused(grid_launch(prob, st), i);
+      launch_grid_fused(prob->kind, grid_launch(prob, st), i);
       cudaEventRecord(ev[3 + 2 * i], st);
     }
     cudaEventRecord(ev[2 + 2 * n_iters], st);
-    launch_grid_fused_fin(grid_launch(prob, st), n_iters, 0, 0);
+    launch_grid_fused_fin(prob->kind, grid_launch(prob, st), n_iters, 0, 0);
     cudaEventRecord(ev[3 + 2 * n_iters], st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) status = cuda_fail(e, "opt_profile_pcg_fused");

@@ -318,7 +318,9 @@ void enqueue_batch(opt_batch* b, const opt_solve_params& p, bool lm, cudaStream_
   k_reset_tab<<<(n + 127) / 128, 128, 0, st>>>(b->d_stab, n, lm ? p.lambda0 : 0.0);
   // wide-tile warp groups take the single-reduction PCG iteration when asked
   // for (as a solo solve of each member would), the others the two-pass one
-  auto fused = [&](const GridGroup& g) { return p.pcg_form == 1 && p.inner > 0 && g.kind == K_WARP && g.tw == 128; };
+  auto fused = [&](const GridGroup& g) {
+    return p.pcg_form == 1 && p.inner > 0 && (g.kind == K_WARP || g.kind == K_POISSON) && g.tw == 128;
+  };
   for (int k = 0; k < outer; ++k) {
     // from the second outer iteration on, the wide warps' cos / sin of theta
     // come from the previous outer update
@@ -327,7 +329,7 @@ void enqueue_batch(opt_batch* b, const opt_solve_params& p, bool lm, cudaStream_
     for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_init(ml(g, st), k, dmin, dmax);
     for (int i = 0; i < p.inner; ++i) {
       for (GridGroup& g : b->grids) {
-        if (fused(g)) launch_grid_fused(gl(g, st), i);
+        if (fused(g)) launch_grid_fused(g.kind, gl(g, st), i);
         else launch_grid_apply(g.kind, gl(g, st), nullptr, i, 1);
       }
       for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_apply(ml(g, st), nullptr, i, 1);
@@ -336,7 +338,7 @@ void enqueue_batch(opt_batch* b, const opt_solve_params& p, bool lm, cudaStream_
     }
     // the single-reduction groups' last step (with x += delta under GN)
     for (GridGroup& g : b->grids)
-      if (fused(g)) launch_grid_fused_fin(gl(g, st), p.inner, lm ? 0 : 1, lm ? 0 : csn_next);
+      if (fused(g)) launch_grid_fused_fin(g.kind, gl(g, st), p.inner, lm ? 0 : 1, lm ? 0 : csn_next);
     if (!lm) {
       for (GridGroup& g : b->grids) if (!fused(g)) launch_grid_step(g.kind, gl(g, st), 0, csn_next);
       for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_step(ml(g, st), 0);

@@ -984,7 +984,7 @@ __device__ __forceinline__ void store_csn(const GridProb& pr, long long i, const
 // p_i, w_i = M^-1 q_i.  r and q themselves are never stored.  z, w and p are
 // double-buffered (halo reads of the previous iterate while other blocks
 // write the next).  Iteration 0 starts from r_0 and M^-1 (z_0 = M^-1 r_0, p_0
-// = z_0); the last iteration's update is applied by k_warp_fused_fin (for
+// = z_0); the last iteration's update is applied by k_grid_fused_fin (for
 // Gauss-Newton together with the outer update x += delta).
 // Per pixel: read z, w, p (halos), cos / sin, UrShape, M^-1, delta; write z,
 // w, p, delta: 120 B against 152 B for the two-pass form.
@@ -1023,6 +1023,7 @@ __device__ __forceinline__ float4 rcp4(const float4& v) {
 // Pending-only pass: the loop stopped after an iteration whose step is known
 // (alpha != 0): delta += alpha p over the block's pixels, and the last block
 // clears alpha.
+template <int NX>
 __device__ __forceinline__ void fused_pending(const Chunk& ch, const GridProb& pr, const int* __restrict__ tiles,
                                               double* __restrict__ part, const float* __restrict__ pin,
                                               float alpha) {
@@ -1037,7 +1038,7 @@ __device__ __forceinline__ void fused_pending(const Chunk& ch, const GridProb& p
     if (y >= pr.H) continue;
     const long long i = (long long)y * pr.P + tile_x0(tc, W4) + 4 * (w % (W4 / 4));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < NX; ++c) {
       float4* d = reinterpret_cast<float4*>(pr.d + c * pl + i);
       *d = fma4s(alpha, __ldcg(reinterpret_cast<const float4*>(pin + c * pl + i)), *d);
     }
@@ -1047,6 +1048,43 @@ __device__ __forceinline__ void fused_pending(const Chunk& ch, const GridProb& p
     double unused[4];
     gather_partials4(part, pr.chunk_begin, pr.chunk_end, &s->counter, unused);
     if (threadIdx.x == 0) s->alpha_f = 0.f;
+  }
+}
+
+// End of a single-reduction iteration: the block's four compensated sums
+// (p.q, q.z, q.M^-1 q, r.z) published; the last block of the problem sets
+// alpha, the next r.z and beta (or ends the loop on a breakdown).
+__device__ __forceinline__ void fused_finish(const GridProb& pr, double* __restrict__ part, const F2x2& acc_pq,
+                                             const F2x2& acc_qz, const F2x2& acc_qw, const F2x2& acc_zr) {
+  Scalars* s = pr.s;
+  const F2 sums[4] = {f2x2_fold(acc_pq), f2x2_fold(acc_qz), f2x2_fold(acc_qw), f2x2_fold(acc_zr)};
+  if (publish_partials4(part, blockIdx.x, sums, &s->counter, pr.chunk_end - pr.chunk_begin)) {
+    double v[4];
+    gather_partials4(part, pr.chunk_begin, pr.chunk_end, &s->counter, v);
+    if (threadIdx.x == 0) {
+      const double pq = v[0], qz = v[1], qw = v[2], rz = v[3];
+      s->pq = pq;
+      if (pq > 0.0 && isfinite(pq) && rz > 0.0 && isfinite(rz)) {
+        // alpha from the r.z of the stored z (as the two-pass form takes it);
+        // the recurrence only carries r.z one iteration ahead, to set beta
+        const float af = (float)(rz / pq);
+        const double a = (double)af;
+        const double rz_next = fma(a * a, qw, fma(-2.0 * a, qz, rz));
+        s->alpha_f = af;
+        s->rz = rz;
+        s->pcg_iters += 1;
+        if (rz_next > 0.0 && isfinite(rz_next)) {
+          s->beta_f = (float)(rz_next / rz);
+        } else {
+          s->pcg_active = 0;        // the step alpha p is still applied
+          if (!isfinite(rz_next)) s->nonfinite = 1;
+        }
+      } else {
+        s->alpha_f = 0.f;
+        s->pcg_active = 0;
+        if (!isfinite(pq) || !isfinite(rz)) s->nonfinite = 1;
+      }
+    }
   }
 }
 
@@ -1062,7 +1100,7 @@ __device__ __forceinline__ void fused_wide_body(FusedSmem& sm, const Chunk& ch, 
   const long long pl = pr.plane;
   const float* __restrict__ pin = pr.p + (long long)(it & 1) * 3 * pl;
   if (!s->pcg_active) {
-    if (alpha != 0.f) fused_pending(ch, pr, tiles, part, pin, alpha);
+    if (alpha != 0.f) fused_pending<3>(ch, pr, tiles, part, pin, alpha);
     return;
   }
   const float beta = first ? 0.f : s->beta_f;
@@ -1315,36 +1353,7 @@ __device__ __forceinline__ void fused_wide_body(FusedSmem& sm, const Chunk& ch, 
     }
     slot ^= 1;
   }
-  const F2 sums[4] = {f2x2_fold(acc_pq), f2x2_fold(acc_qz), f2x2_fold(acc_qw), f2x2_fold(acc_zr)};
-  if (publish_partials4(part, blockIdx.x, sums, &s->counter, pr.chunk_end - pr.chunk_begin)) {
-    double v[4];
-    gather_partials4(part, pr.chunk_begin, pr.chunk_end, &s->counter, v);
-    if (threadIdx.x == 0) {
-      // v = p.q, q.z, q.M^-1 q and r.z of this iteration's vectors
-      const double pq = v[0], qz = v[1], qw = v[2], rz = v[3];
-      s->pq = pq;
-      if (pq > 0.0 && isfinite(pq) && rz > 0.0 && isfinite(rz)) {
-        // alpha from the r.z of the stored z (as the two-pass form takes it);
-        // the recurrence only carries r.z one iteration ahead, to set beta
-        const float af = (float)(rz / pq);
-        const double a = (double)af;
-        const double rz_next = fma(a * a, qw, fma(-2.0 * a, qz, rz));
-        s->alpha_f = af;
-        s->rz = rz;
-        s->pcg_iters += 1;
-        if (rz_next > 0.0 && isfinite(rz_next)) {
-          s->beta_f = (float)(rz_next / rz);
-        } else {
-          s->pcg_active = 0;        // the step alpha p is still applied
-          if (!isfinite(rz_next)) s->nonfinite = 1;
-        }
-      } else {
-        s->alpha_f = 0.f;
-        s->pcg_active = 0;
-        if (!isfinite(pq) || !isfinite(rz)) s->nonfinite = 1;
-      }
-    }
-  }
+  fused_finish(pr, part, acc_pq, acc_qz, acc_qw, acc_zr);
 }
 
 template <bool MASK>
@@ -1367,7 +1376,8 @@ __global__ void __launch_bounds__(NT, 2) k_warp_fused_wide(const GridProb* __res
 // step = 1 (Gauss-Newton): the outer update x += delta follows in the same
 // pass (the same roundings as the update, then k_grid_step), and delta is
 // not stored; csn_out: also cos / sin of the new theta.
-__global__ void __launch_bounds__(NT) k_warp_fused_fin(const GridProb* __restrict__ probs,
+template <int NX>
+__global__ void __launch_bounds__(NT) k_grid_fused_fin(const GridProb* __restrict__ probs,
                                                        const Chunk* __restrict__ chunks,
                                                        const int* __restrict__ tiles, int par, int step,
                                                        int csn_out) {
@@ -1379,7 +1389,7 @@ __global__ void __launch_bounds__(NT) k_warp_fused_fin(const GridProb* __restric
   const float alpha = s->alpha_f;
   if (alpha == 0.f && !step) return;
   const long long pl = pr.plane;
-  const float* __restrict__ pin = pr.p + (long long)(par & 1) * 3 * pl;
+  const float* __restrict__ pin = pr.p + (long long)(par & 1) * NX * pl;
   constexpr int QPT = (W4 / 4) * TH;
   const int nq = (ch.end - ch.begin) * QPT;
   for (int k = threadIdx.x; k < nq; k += NT) {
@@ -1389,7 +1399,7 @@ __global__ void __launch_bounds__(NT) k_warp_fused_fin(const GridProb* __restric
     if (y >= pr.H) continue;
     const long long i = (long long)y * pr.P + tile_x0(tc, W4) + 4 * (w % (W4 / 4));
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < NX; ++c) {
       float4* d = reinterpret_cast<float4*>(pr.d + c * pl + i);
       float4 dv = *d;
       if (alpha != 0.f) dv = fma4s(alpha, __ldcg(reinterpret_cast<const float4*>(pin + c * pl + i)), dv);
@@ -1398,7 +1408,7 @@ __global__ void __launch_bounds__(NT) k_warp_fused_fin(const GridProb* __restric
         float4 xv = *x;
         xv = make_float4(xv.x + dv.x, xv.y + dv.y, xv.z + dv.z, xv.w + dv.w);
         *x = xv;
-        if (c == 2 && csn_out) store_csn(pr, i, xv);
+        if (NX == 3 && c == 2 && csn_out) store_csn(pr, i, xv);
       } else {
         *d = dv;
       }
@@ -1702,7 +1712,7 @@ __device__ __forceinline__ void k_warp_init_wide_body(InitSmem& sm, const Chunk&
 #define WARP_INIT_WIDE_MINB 2       // resident blocks per SM the wide warp PCGInit is compiled for
 #endif
 // CSN: cos / sin of theta are read from the planes the previous outer
-// update wrote (k_grid_step / k_warp_fused_fin with csn_out) instead of being
+// update wrote (k_grid_step / k_grid_fused_fin with csn_out) instead of being
 // evaluated on the tile and its halo; the same bits either way.
 template <bool MASK, bool CSN>
 __global__ void __launch_bounds__(NT, WARP_INIT_WIDE_MINB) k_warp_init_wide(const GridProb* __restrict__ probs,
@@ -2503,6 +2513,7 @@ __device__ __forceinline__ void k_poisson_init_wide_body(PoisInitSmem& sm, const
       s->E = E;
       if (pr.Ehist && k_outer >= 0) pr.Ehist[k_outer] = E;
       s->beta_f = 0.f;
+      s->alpha_f = 0.f;         // no step pending (single-reduction PCG)
       s->pcg_active = (rz != 0.0) && isfinite(rz);
       if (!isfinite(rz) || !isfinite(E)) s->nonfinite = 1;
     }
@@ -2518,6 +2529,198 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_init_wide(const GridProb* __r
   const GridProb pr = probs[ch.prob];
   pdl_begin();
   if (tma_ready(pr, &sm)) k_poisson_init_wide_body(sm, ch, pr, tiles, part, k_outer, dmin, dmax);
+}
+
+// ---------------------------------------------------------------------------
+// Single-reduction PCG iteration of wide Poisson tiles (tw = 128): the
+// iteration of k_warp_fused_wide for the four channels of Fig. 27.  z = M^-1 r,
+// w = M^-1 q and p are double-buffered; one M^-1 plane serves the four
+// channels.  Staged like the warp kernel: tensor copies bring z, w, p_old of
+// the tile and its halo into one slot (iteration 0: r and M^-1), phase 2
+// forms z = z - alpha w and p = z + beta p_old on every staged quad into a
+// staging area (and z, delta += alpha p_old on the own pixels), the next
+// tile's copies overlap phase 3, the stencil of k_poisson_apply_wide (the
+// directions vanish off the free pixels: q = S p - 2 (p_L + p_R + p_U + p_D)
+// per channel, LM damping on the free pixels), w = M^-1 q and the four
+// compensated dot products.  Per pixel of an active tile: read z, w, p_old
+// 48, degree byte 1, M^-1 4, delta 16; write z, w, p, delta 64 = 133 B
+// (two-pass: 69 + 100 B).
+// ---------------------------------------------------------------------------
+constexpr int NRAW_PF = 12;      // z0..z3 w0..w3 p0..p3 (iteration 0: r0..r3 at 0..3, M^-1 at 4)
+constexpr int NSTG_PF = 4;       // p0..p3, each quad stored as pixels 0 2 1 3
+
+struct PoisFusedSmem {
+  PlaneT raw[NRAW_PF];
+  float stg[NSTG_PF][HH][SP];    // halo columns -1 / 128 live at 3 / 132, in plain order
+  BytesT mk[2];                  // degree bytes of the current / next tile
+  unsigned long long bar;
+};
+
+__device__ __forceinline__ void pois_fused_body(PoisFusedSmem& sm, const Chunk& ch, const GridProb& pr,
+                                                const int* __restrict__ tiles, double* __restrict__ part, int it) {
+  Scalars* s = pr.s;
+  if (s->done) return;
+  const int first = it == 0;
+  const float alpha = first ? 0.f : s->alpha_f;
+  const long long pl = pr.plane;
+  const float* __restrict__ pin = pr.p + (long long)(it & 1) * 4 * pl;
+  if (!s->pcg_active) {
+    if (alpha != 0.f) fused_pending<4>(ch, pr, tiles, part, pin, alpha);
+    return;
+  }
+  const float beta = first ? 0.f : s->beta_f;
+  const int use_beta = beta != 0.0f;
+  const float lam = pr.lm ? s->lambda_f : 0.0f;
+  float* __restrict__ pout = pr.p + (long long)((it + 1) & 1) * 4 * pl;
+  float* __restrict__ zout = pr.zb + (long long)((it + 1) & 1) * 4 * pl;
+  float* __restrict__ wout = pr.wb + (long long)((it + 1) & 1) * 4 * pl;
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  F2x2 acc_pq = f2x2_zero(), acc_qz = f2x2_zero(), acc_qw = f2x2_zero(), acc_zr = f2x2_zero();
+  const int zz = pr.zpack2 & 63, zw = (pr.zpack2 >> 6) & 63, par4 = (it & 1) * 4;
+  // raw planes, all in the slab (tensor map 0); the degree bytes by map 2
+  auto plane = [&](int k, int& z, int& m) {
+    m = 0;
+    if (first)
+      z = k < 4 ? zslab(pr, 0) + k : k == 4 ? zslab(pr, 1) : -1;
+    else
+      z = k < 4 ? zz + par4 + k : k < 8 ? zw + par4 + k - 4 : zslab(pr, 2) + par4 + k - 8;
+  };
+  auto issue = [&](int tcx, int slot) {
+    if (tid == 0) tile_tma<NRAW_PF>(sm.raw, &sm.mk[slot], plane, true, pr, tile_x0(tcx, W4), tile_y0(tcx), &sm.bar);
+  };
+  float4 dl[4];       // delta of the own pixels, loaded before the staging wait
+  auto stage = [&](int row, bool own, long long i) {
+    const int c = 4 + 4 * lane;
+    auto R = [&](int k) { return lds4(&sm.raw[k].v[row][c]); };
+    const float4 m = first ? R(4) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float4 z = first ? mul4s(m, R(k)) : fma4s(-alpha, R(4 + k), R(k));
+      const float4 p = use_beta ? fma4s(beta, R(8 + k), z) : z;
+      sts4(&sm.stg[k][row][c], swz4(p));
+      if (own) {
+        *reinterpret_cast<float4*>(zout + k * pl + i) = z;
+        if (!first) *reinterpret_cast<float4*>(pr.d + k * pl + i) = fma4s(alpha, R(8 + k), dl[k]);
+      }
+    }
+  };
+  int tc = tiles[ch.begin];
+  int tn = ch.begin + 1 < ch.end ? tiles[ch.begin + 1] : 0;
+  unsigned phase = 0;
+  int slot = 0;
+  issue(tc, 0);
+  for (int t = ch.begin; t < ch.end; ++t) {
+    const int x0 = tile_x0(tc, W4), y0 = tile_y0(tc);
+    const int gx = x0 + 4 * lane, gy = y0 + ty;
+    const long long i = (long long)gy * pr.P + gx;
+    if (!first && gy < pr.H) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) dl[k] = *reinterpret_cast<const float4*>(pr.d + k * pl + i);
+    }
+    const unsigned pb = phase;
+    const bool ok = mbar_wait(&sm.bar, pb);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      staging_timeout(s, &sm.bar, pb);
+      return;
+    }
+    const unsigned char (*mk)[SPB] = sm.mk[slot].v;
+    // phase 2: z and the direction on the tile and its halo
+    stage(ty + 1, gy < pr.H, i);
+    if (tid < 64) {
+      stage(tid < 32 ? 0 : HH - 1, false, 0);
+    } else if (tid < 64 + 2 * TH) {
+      const int h = tid - 64;
+      const int row = 1 + (h % TH), side = h / TH;
+      const int col = side ? 4 + W4 : 3;
+      auto R = [&](int k) { return sm.raw[k].v[row][col]; };
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float z = first ? __fmul_rn(R(4), R(k)) : __fmaf_rn(-alpha, R(4 + k), R(k));
+        if (use_beta) z = __fmaf_rn(beta, R(8 + k), z);
+        sm.stg[k][row][col] = z;
+      }
+    }
+    __syncthreads();
+    // the raw buffer is free: start the next tile's copies
+    if (t + 1 < ch.end) {
+      tc = tn;
+      issue(tc, slot ^ 1);
+      if (t + 2 < ch.end) tn = tiles[t + 2];
+    }
+    if (gy < pr.H) {                          // warp-uniform: one warp per row
+      const int c = 4 + 4 * lane;
+      float4 O[4], U[4], D[4];
+      float L[4], R[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        O[k] = lds4(&sm.stg[k][ty + 1][c]);
+        *reinterpret_cast<float4*>(pout + k * pl + i) = swz4(O[k]);
+      }
+      pois_side_nbrs(O, L, R);
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) L[k] = sm.stg[k][ty + 1][3];
+      }
+      if (lane == 31) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) R[k] = sm.stg[k][ty + 1][4 + W4];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        U[k] = lds4(&sm.stg[k][ty][c]);
+        D[k] = lds4(&sm.stg[k][ty + 2][c]);
+      }
+      float4 fo, S;
+      pois_own(pois_deg4(mk, ty + 1, lane), fo, S);
+      fo = swz4(fo);
+      S = swz4(S);
+      float2 qA[4], qB[4];
+      pois_core_apply(O, U, D, L, R, lo2(S), hi2(S), qA, qB);
+      float4 dd = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (pr.lm) dd = swz4(ld4(pr.dc + i));
+      const float2 lam2 = make_float2(lam, lam);
+      const float2 dA = mul2(lam2, lo2(dd)), dB = mul2(lam2, hi2(dd));
+      // w = M^-1 q and the four inner products (swizzled packs: A = pixels
+      // {0, 2}, B = {1, 3}); z of the own pixels comes back from the stores
+      // of phase 2 (this thread's own writes)
+      const float4 ms = swz4(ld4(pr.m + i));
+      const float4 rc = rcp4(ms);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 a = mul2(lo2(fo), fma2(dA, lo2(O[k]), qA[k]));
+        const float2 b2 = mul2(hi2(fo), fma2(dB, hi2(O[k]), qB[k]));
+        const float2 wa = mul2(lo2(ms), a), wb = mul2(hi2(ms), b2);
+        *reinterpret_cast<float4*>(wout + k * pl + i) = swz4(cat4(wa, wb));
+        const float4 zs = swz4(*reinterpret_cast<const float4*>(zout + k * pl + i));
+        const float2 ra = mul2(lo2(rc), lo2(zs)), rb = mul2(hi2(rc), hi2(zs));
+        f2x2_add_prod(acc_pq, lo2(O[k]), a);
+        f2x2_add_prod(acc_pq, hi2(O[k]), b2);
+        f2x2_add_prod(acc_qw, wa, a);
+        f2x2_add_prod(acc_qw, wb, b2);
+        f2x2_add_prod(acc_qz, lo2(zs), a);
+        f2x2_add_prod(acc_qz, hi2(zs), b2);
+        f2x2_add_prod(acc_zr, lo2(zs), ra);
+        f2x2_add_prod(acc_zr, hi2(zs), rb);
+      }
+    }
+    slot ^= 1;
+  }
+  fused_finish(pr, part, acc_pq, acc_qz, acc_qw, acc_zr);
+}
+
+__global__ void __launch_bounds__(NT, 2) k_poisson_fused_wide(const GridProb* __restrict__ probs,
+                                                              const Chunk* __restrict__ chunks,
+                                                              const int* __restrict__ tiles,
+                                                              double* __restrict__ part, int it) {
+  extern __shared__ __align__(128) unsigned char dyn_smem[];
+  PoisFusedSmem& sm = *reinterpret_cast<PoisFusedSmem*>(dyn_smem);
+  const Chunk ch = chunks[blockIdx.x];
+  const GridProb pr = probs[ch.prob];
+  pdl_begin();
+  if (threadIdx.x == 0) mbar_init(&sm.bar);
+  __syncthreads();
+  if (tma_ready(pr, &sm)) pois_fused_body(sm, ch, pr, tiles, part, it);
 }
 
 // Degree plane of a wide Poisson problem: S_i + 1 on a free pixel i, where
@@ -2854,6 +3057,9 @@ cudaError_t grid_kernels_prepare() {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_warp_fused_wide<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_poisson_fused_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sizeof(PoisFusedSmem));
+    if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_warp_pcg_coop<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_warp_pcg_coop<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -2909,8 +3115,11 @@ void launch_grid_update(int kind, const GridLaunch& L, int par) {
     launch_pdl(k_grid_update<4>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, L.part, par);
 }
 
-void launch_grid_fused(const GridLaunch& L, int it) {
-  if (L.masked)
+void launch_grid_fused(int kind, const GridLaunch& L, int it) {
+  if (kind == K_POISSON)
+    launch_pdl(k_poisson_fused_wide, L.nchunks, NT, sizeof(PoisFusedSmem), L.stream, L.probs, L.chunks, L.tiles,
+               L.part, it);
+  else if (L.masked)
     launch_pdl(k_warp_fused_wide<true>, L.nchunks, NT, sizeof(FusedSmem), L.stream, L.probs, L.chunks, L.tiles,
                L.part, it);
   else
@@ -2918,8 +3127,11 @@ void launch_grid_fused(const GridLaunch& L, int it) {
                L.part, it);
 }
 
-void launch_grid_fused_fin(const GridLaunch& L, int par, int step, int csn_out) {
-  launch_pdl(k_warp_fused_fin, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, par, step, csn_out);
+void launch_grid_fused_fin(int kind, const GridLaunch& L, int par, int step, int csn_out) {
+  if (kind == K_POISSON)
+    launch_pdl(k_grid_fused_fin<4>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, par, step, 0);
+  else
+    launch_pdl(k_grid_fused_fin<3>, L.nchunks, NT, 0, L.stream, L.probs, L.chunks, L.tiles, par, step, csn_out);
 }
 
 void launch_grid_csn(const GridLaunch& L) {

@@ -56,12 +56,13 @@ void launch_grid_init(int kind, const GridLaunch& L, int k_outer, float dmin, fl
 void launch_grid_apply(int kind, const GridLaunch& L, const float* p_override, int par, int update);
 void launch_grid_update(int kind, const GridLaunch& L, int par);
 void launch_grid_energy(int kind, const GridLaunch& L, int mode, int hist_idx);
-// Single-reduction PCG (wide warp tiles; problems planned with z / w
-// buffers): iteration `it` (0 starts from r_0, M^-1), and the pending step of
-// the last iteration (p of parity par = the iteration count); step = 1 also
-// applies the Gauss-Newton update x += delta (csn_out: and cos / sin of theta)
-void launch_grid_fused(const GridLaunch& L, int it);
-void launch_grid_fused_fin(const GridLaunch& L, int par, int step, int csn_out);
+// Single-reduction PCG (warp or Poisson on 128-pixel tiles; problems planned
+// with z / w buffers): iteration `it` (0 starts from r_0, M^-1), and the
+// pending step of the last iteration (p of parity par = the iteration count);
+// step = 1 also applies the Gauss-Newton update x += delta (csn_out, warp:
+// and cos / sin of theta)
+void launch_grid_fused(int kind, const GridLaunch& L, int it);
+void launch_grid_fused_fin(int kind, const GridLaunch& L, int par, int step, int csn_out);
 void launch_grid_step(int kind, const GridLaunch& L, int cond, int csn_out);
 // cos / sin of theta at the current unknowns into the cos / sin planes (wide warps)
 void launch_grid_csn(const GridLaunch& L);

@@ -58,8 +58,9 @@ size_t estimate_grid(const opt_grid_desc& d, int tile_w) {
   const bool warp = d.kind == OPT_ARAP_WARP_2D;
   const size_t tw = tile_w ? tile_w : (d.W >= 128 ? 128 : 32);
   const size_t pl = ((size_t)d.W + tw - 1) / tw * tw * (size_t)d.H;
-  // wide warps also hold the single-reduction PCG's z and w buffers (12 planes)
-  const size_t planes = warp ? (tw == 128 ? 38 : 24) : 30;
+  // 128-pixel tiles also hold the single-reduction PCG's z and w buffers
+  // (12 planes for a warp, 16 for Poisson)
+  const size_t planes = warp ? (tw == 128 ? 38 : 24) : (tw == 128 ? 46 : 30);
   const size_t tiles = ((size_t)d.W + tw - 1) / tw * ((size_t)(d.H + 7) / 8);
   return planes * pl * 4 + (d.mask ? pl : 0) + tiles * 64 + (size_t)d.n_handles * 16 + (1 << 16);
 }

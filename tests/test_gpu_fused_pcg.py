@@ -169,10 +169,10 @@ def test_fused_full_size_configuration(api):
 
 
 def test_fused_form_on_other_problems_runs_two_pass(api):
-    """pcg_form = 1 on problems the form does not cover (32-pixel tiles,
-    Poisson) runs the two-pass iteration: bit-identical results."""
+    """pcg_form = 1 on problems the form does not cover (32-pixel tiles) runs
+    the two-pass iteration: bit-identical results."""
     import torch
-    for prob in (warp(100, 30, 0.0, seed=3), synth.poisson_problem(260, 40, seed=4)):
+    for prob in (warp(100, 30, 0.0, seed=3), synth.poisson_problem(100, 40, seed=4)):
         gp = api.Problem(prob)
         r0 = gp.solve_gn(2, 5, pcg_form=0)
         gp.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
@@ -279,3 +279,62 @@ def test_fused_server_requests_equal_solo(api):
         d = np.linalg.norm(x.cpu().numpy().reshape(-1) - xref.reshape(-1)) / max(np.linalg.norm(xref), 1e-30)
         assert d <= (1e-4 if p.kind == "mesh" else 1e-6)
     srv.close()
+
+
+POISSON_CASES = [(256, 24), (300, 41), (520, 9), (129, 33)]
+
+
+@pytest.mark.parametrize("W,H", POISSON_CASES)
+def test_fused_poisson_iterates_match_oracle(api, W, H):
+    """Poisson editing on 128-pixel tiles: delta after k = 1, 3, 6
+    single-reduction iterations equals the oracle's textbook PCG step; fixed
+    pixels never move."""
+    import torch
+    prob = synth.poisson_problem(W, H, seed=W + 2 * H)
+    rng = np.random.default_rng(W)
+    free = prob.mask == 0
+    prob.x0[:, free] += rng.uniform(-0.2, 0.2, size=(4, int(free.sum()))).astype(np.float32)
+    e = oracle.make_energy(prob)
+    x0 = prob.x0.reshape(-1).astype(np.float64)
+    J = e.jacobian(x0)
+    b = -(J.T @ e.residuals(x0))
+    diag = np.asarray(J.multiply(J).sum(0)).ravel()
+    Minv = oracle.solver.jacobi_minv(diag)
+    gp = api.Problem(prob)
+    assert gp.config()["tile_w"] == 128
+    for k in (1, 3, 6):
+        gp.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
+        rep = gp.solve_gn(1, k, pcg_form=1)
+        d_ref, n_done, _ = oracle.jacobi_pcg(lambda v: J.T @ (J @ v), b, Minv, k)
+        assert rep["pcg_done"] == n_done == k
+        x = gp.x.cpu().numpy()
+        d = x.reshape(-1).astype(np.float64) - x0
+        assert rel(d, d_ref) <= 1e-4, (k, rel(d, d_ref))
+        np.testing.assert_array_equal(x[:, ~free], prob.x0[:, ~free])
+
+
+@pytest.mark.parametrize("method", ["gn", "lm"])
+def test_fused_poisson_solve_matches_oracle_and_two_pass(api, method):
+    """Poisson 300 x 41 x 4 through GN 4 x 20 / LM 5 x 15 with the
+    single-reduction iteration: energies within 1e-4 of the oracle (same
+    outer count and accepted steps under LM) and within rounding of the
+    two-pass form."""
+    import torch
+    prob = synth.poisson_problem(300, 41, seed=77)
+    e = oracle.make_energy(prob)
+    outer, inner = (4, 20) if method == "gn" else (5, 15)
+    x0 = prob.x0.reshape(-1)
+    ref = oracle.gauss_newton(e, x0, outer, inner) if method == "gn" else \
+        oracle.levenberg_marquardt(e, x0, outer, inner)
+    gp = api.Problem(prob)
+    solve = getattr(gp, f"solve_{method}")
+    r1 = solve(outer, inner, pcg_form=1)
+    gp.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
+    r0 = solve(outer, inner, pcg_form=0)
+    assert r1["outer_done"] == r0["outer_done"] == (outer if method == "gn" else ref.outer_done)
+    if method == "lm":
+        assert r1["accepted"] == sum(ref.accepted)
+    for k, (a, b) in enumerate(zip(r1["E_history"], ref.E_history)):
+        assert relE(a, b) <= TOL_ENERGY, (k, a, b)
+    for a, b in zip(r1["E_history"], r0["E_history"]):
+        assert relE(a, b) <= 1e-5
