@@ -1056,6 +1056,8 @@ PROFILE_CASES = {
                        "ARAP warp 2048^2, single-reduction PCG iteration", False, 0, None, True),
     "poisson2048": (lambda synth: synth.poisson_problem(2048, 2048, seed=synth.BASE_SEED), "Poisson 2048^2 x 4",
                     False),
+    "poisson2048_fused": (lambda synth: synth.poisson_problem(2048, 2048, seed=synth.BASE_SEED),
+                          "Poisson 2048^2 x 4, single-reduction PCG iteration", False, 0, None, True),
     "mesh8": (lambda synth: synth.mesh_problem(8, seed=synth.BASE_SEED), "ARAP mesh, icosphere level 8", False),
     # the mesh configuration's size with the tiled apply form pinned
     "mesh7tiled": (lambda synth: synth.mesh_problem(7, seed=synth.BASE_SEED),
