@@ -338,3 +338,19 @@ def test_fused_poisson_solve_matches_oracle_and_two_pass(api, method):
         assert relE(a, b) <= TOL_ENERGY, (k, a, b)
     for a, b in zip(r1["E_history"], r0["E_history"]):
         assert relE(a, b) <= 1e-5
+
+
+@pytest.mark.parametrize("kind", ["warp", "poisson"])
+def test_fused_plain_cg_matches_oracle(api, kind):
+    """Without the preconditioner (M^-1 = 1, so z = r and w = q) the
+    single-reduction iteration is plain CG: GN energies within 1e-4 of the
+    oracle's GN with unpreconditioned CG."""
+    prob = warp(300, 24, 0.0, seed=61, perturb=0.0, n_handles=8) if kind == "warp" else \
+        synth.poisson_problem(260, 30, seed=62)
+    e = oracle.make_energy(prob)
+    ref = oracle.gauss_newton(e, prob.x0.reshape(-1), 3, 15, use_precond=False)
+    gp = api.Problem(prob)
+    rep = gp.solve_gn(3, 15, use_precond=0, pcg_form=1)
+    assert rep["pcg_done"] == ref.pcg_done
+    for k, (a, b) in enumerate(zip(rep["E_history"], ref.E_history)):
+        assert relE(a, b) <= TOL_ENERGY, (k, a, b)
