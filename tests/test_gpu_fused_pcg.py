@@ -340,17 +340,26 @@ def test_fused_poisson_solve_matches_oracle_and_two_pass(api, method):
         assert relE(a, b) <= 1e-5
 
 
-@pytest.mark.parametrize("kind", ["warp", "poisson"])
-def test_fused_plain_cg_matches_oracle(api, kind):
+@pytest.mark.parametrize("kind,inner", [("warp", 3), ("poisson", 10)])
+def test_fused_plain_cg_matches_oracle(api, kind, inner):
     """Without the preconditioner (M^-1 = 1, so z = r and w = q) the
     single-reduction iteration is plain CG: GN energies within 1e-4 of the
-    oracle's GN with unpreconditioned CG."""
+    oracle's GN with unpreconditioned CG and within rounding of the two-pass
+    form.  The warp is held over 3 CG iterations, as in test_gpu_parity.py:
+    its fit rows weigh 100 against stencil rows of 4 .. 8, and unpreconditioned
+    CG in float32 amplifies rounding about 100-fold per iteration (both forms
+    alike: 3 % apart from the float64 oracle after one GN step of 15)."""
+    import torch
     prob = warp(300, 24, 0.0, seed=61, perturb=0.0, n_handles=8) if kind == "warp" else \
         synth.poisson_problem(260, 30, seed=62)
     e = oracle.make_energy(prob)
-    ref = oracle.gauss_newton(e, prob.x0.reshape(-1), 3, 15, use_precond=False)
+    ref = oracle.gauss_newton(e, prob.x0.reshape(-1), 2, inner, use_precond=False)
     gp = api.Problem(prob)
-    rep = gp.solve_gn(3, 15, use_precond=0, pcg_form=1)
+    rep = gp.solve_gn(2, inner, use_precond=0, pcg_form=1)
+    gp.x.copy_(torch.as_tensor(prob.x0, device="cuda"))
+    rep0 = gp.solve_gn(2, inner, use_precond=0, pcg_form=0)
     assert rep["pcg_done"] == ref.pcg_done
     for k, (a, b) in enumerate(zip(rep["E_history"], ref.E_history)):
         assert relE(a, b) <= TOL_ENERGY, (k, a, b)
+    for a, b in zip(rep["E_history"], rep0["E_history"]):
+        assert relE(a, b) <= 1e-5
