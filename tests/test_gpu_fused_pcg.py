@@ -363,3 +363,4 @@ def test_fused_plain_cg_matches_oracle(api, kind, inner):
         assert relE(a, b) <= TOL_ENERGY, (k, a, b)
     for a, b in zip(rep["E_history"], rep0["E_history"]):
         assert relE(a, b) <= 1e-5
+
