@@ -580,14 +580,23 @@ opt_status batch_prepare_round(opt_batch* b, const opt_solve_params& p) {
 void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_t st) {
   const float dmin = (float)p.diag_min, dmax = (float)p.diag_max;
   const int n = (int)b->probs.size();
+  // 128-pixel-tile warp and Poisson groups on the single-reduction iteration
+  // when asked for, as in enqueue_batch
+  auto fused = [&](const GridGroup& g) {
+    return p.pcg_form == 1 && p.inner > 0 && (g.kind == K_WARP || g.kind == K_POISSON) && g.tw == 128;
+  };
   for (GridGroup& g : b->grids) launch_grid_init(g.kind, gl(g, st), -2, dmin, dmax, 0);
   for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_init(ml(g, st), -2, dmin, dmax);
   for (int i = 0; i < p.inner; ++i) {
-    for (GridGroup& g : b->grids) launch_grid_apply(g.kind, gl(g, st), nullptr, i, 1);
+    for (GridGroup& g : b->grids) {
+      if (fused(g)) launch_grid_fused(g.kind, gl(g, st), i);
+      else launch_grid_apply(g.kind, gl(g, st), nullptr, i, 1);
+    }
     for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_apply(ml(g, st), nullptr, i, 1);
-    for (GridGroup& g : b->grids) launch_grid_update(g.kind, gl(g, st), i);
+    for (GridGroup& g : b->grids) if (!fused(g)) launch_grid_update(g.kind, gl(g, st), i);
     for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_update(ml(g, st), i);
   }
+  for (GridGroup& g : b->grids) if (fused(g)) launch_grid_fused_fin(g.kind, gl(g, st), p.inner, 0, 0);
   for (GridGroup& g : b->grids) launch_grid_energy(g.kind, gl(g, st), 1, -2);
   for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_energy(ml(g, st), 1, -2);
   k_lm_decide_tab<<<(n + 127) / 128, 128, 0, st>>>(b->d_stab, n, p.eta, p.lambda_min, p.lambda_max, p.rel_tol);
