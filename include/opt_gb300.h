@@ -445,7 +445,8 @@ opt_status opt_server_destroy(opt_server* server);
 opt_status opt_server_submit_grid(opt_server* server, const opt_grid_desc* desc, uint64_t* ticket);
 opt_status opt_server_submit_graph(opt_server* server, const opt_graph_desc* desc, uint64_t* ticket);
 
-/* Admits, runs one LM outer iteration of every admitted request, retires the
+/* Admits, runs one LM outer iteration of every admitted request (or more
+ * when no request is waiting, see opt_server_set_max_rounds), retires the
  * finished ones (synchronises the server's stream).  n_active / n_queued
  * (host, may be NULL) receive the counts after the step.  If rebuilding the
  * batch after an admission or a retirement fails (e.g. OPT_ERR_OOM), or the
@@ -467,6 +468,16 @@ opt_status opt_server_inject_rebuild_failure(opt_server* server, opt_status stat
  * Takes effect at the next opt_server_step.  OPT_ERR_INVALID_ARG on a NULL
  * server or a negative cap. */
 opt_status opt_server_set_max_active(opt_server* server, int32_t max_active);
+
+/* LM outer iterations per opt_server_step when no request is waiting after
+ * admission: as many as the admitted request closest to its iteration cap
+ * has left, at most max_rounds (1 .. 64; 1, the default, is one per step).
+ * With max_rounds > 1 a lightly loaded server synchronises once per step
+ * instead of once per outer iteration; a request that converges earlier idles
+ * through the rest of the step, and requests arriving meanwhile wait for the
+ * next step.  Results are the same either way.  Takes effect at the next
+ * step.  OPT_ERR_INVALID_ARG on a NULL server or a value outside 1 .. 64. */
+opt_status opt_server_set_max_rounds(opt_server* server, int32_t max_rounds);
 
 /* OPT_OK and the report (E_history, if not NULL, receives outer_done + 1
  * values) once the request finished; the ticket is then forgotten.

@@ -114,6 +114,7 @@ _SIGNATURES = [
     ("opt_server_step", c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
     ("opt_server_poll", c_int32, [c_void_p, ctypes.c_uint64, POINTER(Report)]),
     ("opt_server_set_max_active", c_int32, [c_void_p, c_int32]),
+    ("opt_server_set_max_rounds", c_int32, [c_void_p, c_int32]),
     ("opt_problem_get_config", c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]),
     ("opt_problem_set_apply_form", c_int32, [c_void_p, c_int32]),
     ("opt_server_inject_rebuild_failure", c_int32, [c_void_p, c_int32]),
@@ -681,10 +682,12 @@ class Server:
     takes a synth problem instance, uploads its arrays and queues it; step()
     admits under the HBM budget and advances every admitted request by one LM
     outer iteration; poll() returns the report once the request finished.
-    max_active > 0 caps the requests admitted at once (opt_server_set_max_active)."""
+    max_active > 0 caps the requests admitted at once (opt_server_set_max_active);
+    max_rounds > 1 lets a step run several outer iterations when nothing waits
+    (opt_server_set_max_rounds)."""
 
     def __init__(self, hbm_budget_bytes: int, outer: int = 10, inner: int = 10, rel_tol: float = 1e-6,
-                 device: str = "cuda", max_active: int = 0, **kw):
+                 device: str = "cuda", max_active: int = 0, max_rounds: int = 1, **kw):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -698,9 +701,14 @@ class Server:
         self.inflight = {}
         if max_active:
             self.set_max_active(max_active)
+        if max_rounds != 1:
+            self.set_max_rounds(max_rounds)
 
     def set_max_active(self, max_active: int):
         _check(self.lib.opt_server_set_max_active(self.h, max_active), "opt_server_set_max_active")
+
+    def set_max_rounds(self, max_rounds: int):
+        _check(self.lib.opt_server_set_max_rounds(self.h, max_rounds), "opt_server_set_max_rounds")
 
     def inject_rebuild_failure(self, status: int):
         """Test hook: the next batch rebuild fails with `status` (host only)."""

@@ -76,6 +76,14 @@ __global__ void k_lm_decide_tab(Scalars* const* __restrict__ tab, int n, double 
   if (i < n) lm_decide(tab[i], eta, lmin, lmax, rel_tol);
 }
 
+// Each member's round record (server rounds).
+__global__ void k_record_round(Scalars* const* __restrict__ tab, int n, RoundRec* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Scalars* t = tab[i];
+  out[i] = RoundRec{t->E, t->E_trial, t->accept, t->outer_done};
+}
+
 // Copies every member's scalars and energy history into contiguous buffers.
 __global__ void k_gather_results(Scalars* const* __restrict__ tab, double* const* __restrict__ hist, int n,
                                  int hlen, Scalars* __restrict__ s_out, double* __restrict__ h_out) {
@@ -144,6 +152,8 @@ struct opt_batch {
   Scalars* d_sout = nullptr;
   double* d_hout = nullptr;
   int hcap = 0;
+  RoundRec* d_rounds = nullptr;     // server rounds: records, round-major
+  int rounds_cap = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<double> gkey;
@@ -577,7 +587,14 @@ opt_status batch_prepare_round(opt_batch* b, const opt_solve_params& p) {
   return refresh_descriptors(b, 1, p.use_precond, 1);
 }
 
-void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_t st) {
+opt_status batch_reserve_rounds(opt_batch* b, int rounds) {
+  if (rounds <= b->rounds_cap) return OPT_OK;
+  opt_status s = balloc(b->allocs, &b->d_rounds, (size_t)rounds * b->probs.size());
+  if (s == OPT_OK) b->rounds_cap = rounds;
+  return s;
+}
+
+void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_t st, int round) {
   const float dmin = (float)p.diag_min, dmax = (float)p.diag_max;
   const int n = (int)b->probs.size();
   // 128-pixel-tile warp and Poisson groups on the single-reduction iteration
@@ -602,11 +619,16 @@ void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_
   k_lm_decide_tab<<<(n + 127) / 128, 128, 0, st>>>(b->d_stab, n, p.eta, p.lambda_min, p.lambda_max, p.rel_tol);
   for (GridGroup& g : b->grids) launch_grid_step(g.kind, gl(g, st), 1, 0);
   for (const MeshGroup& g : b->graphs) if (!g.members.empty()) launch_mesh_step(ml(g, st), 1);
+  if (round < b->rounds_cap)
+    k_record_round<<<(n + 127) / 128, 128, 0, st>>>(b->d_stab, n, b->d_rounds + (size_t)round * n);
   k_gather_results<<<n, 128, 0, st>>>(b->d_stab, b->d_htab, n, 0, b->d_sout, b->d_hout);
 }
 
-opt_status batch_read_scalars(opt_batch* b, Scalars* host_out, cudaStream_t st) {
-  BCK(cudaMemcpyAsync(host_out, b->d_sout, b->probs.size() * sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+opt_status batch_read_scalars(opt_batch* b, Scalars* host_out, RoundRec* rounds_out, int rounds, cudaStream_t st) {
+  const size_t n = b->probs.size();
+  BCK(cudaMemcpyAsync(host_out, b->d_sout, n * sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+  if (rounds_out && rounds > 0 && rounds <= b->rounds_cap)
+    BCK(cudaMemcpyAsync(rounds_out, b->d_rounds, (size_t)rounds * n * sizeof(RoundRec), cudaMemcpyDeviceToHost, st));
   BCK(cudaStreamSynchronize(st));
   return OPT_OK;
 }

@@ -146,9 +146,22 @@ namespace optgb {
 // api.cu: records a failed CUDA call for opt_last_error (OOM or CUDA status)
 opt_status cuda_fail(cudaError_t e, const char* what);
 // batch.cu (serving engine interface)
+// What a server round leaves of each member after its LM decision: the
+// energy at the start of the round, the trial energy, the decision and the
+// outer iterations done.
+struct RoundRec {
+  double E, E_trial;
+  int accept, outer_done;
+};
 opt_status batch_prepare_round(opt_batch* b, const opt_solve_params& p);
-void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_t st);
-opt_status batch_read_scalars(opt_batch* b, Scalars* host_out, cudaStream_t st);
+// Room for `rounds` rounds of records (one RoundRec per member and round).
+opt_status batch_reserve_rounds(opt_batch* b, int rounds);
+// One LM outer iteration of every member; the records of round `round` (of
+// the reserved ones) are written at its end.
+void batch_enqueue_lm_round(opt_batch* b, const opt_solve_params& p, cudaStream_t st, int round);
+// Copies the members' scalars and the records of the first `rounds` rounds
+// (round-major) to the host; synchronises the stream.
+opt_status batch_read_scalars(opt_batch* b, Scalars* host_out, RoundRec* rounds_out, int rounds, cudaStream_t st);
 // api.cu: caller planes (dense rows for grids, caller vertex order for
 // graphs) <-> internal planes
 opt_status copy_planes_in(const opt_problem* pb, float* internal, float* const* user, int n, cudaStream_t st);

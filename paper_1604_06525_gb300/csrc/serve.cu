@@ -44,6 +44,7 @@ struct ServeReq {
   size_t est_bytes = 0;
   opt_problem* pb = nullptr;
   std::vector<double> hist;
+  int outer_seen = 0;   // LM outer iterations done at the last step
   opt_report rep{};
   opt_status status = OPT_OK;
   int state = 0;   // 0 queued, 1 active, 2 finished
@@ -52,6 +53,8 @@ struct ServeReq {
 __global__ void k_serve_reset(Scalars* s, double lambda0) { scalars_reset(s, lambda0); }
 
 size_t round32(size_t v) { return (v + 31) / 32 * 32; }
+
+constexpr int kServeMaxRounds = 64;   // cap of opt_server_set_max_rounds
 
 // Device bytes a planned problem allocates (planes, tables, reduction slots).
 size_t estimate_grid(const opt_grid_desc& d, int tile_w) {
@@ -76,10 +79,12 @@ size_t estimate_graph(const opt_graph_desc& d) {
 struct opt_server {
   size_t budget = 0, used = 0;
   int max_active = 0;                // 0: admission by the budget alone
+  int max_rounds = 1;                // LM outer iterations per step when no request waits
   opt_solve_params prm{};
   cudaStream_t st = nullptr;
   std::mutex mu;
   std::deque<ServeReq*> queue;
+  std::vector<RoundRec> rbuf;        // round records of the last step
   std::vector<ServeReq*> active;
   std::unordered_map<uint64_t, std::unique_ptr<ServeReq>> reqs;
   uint64_t next_ticket = 1;
@@ -251,23 +256,50 @@ opt_status opt_server_step(opt_server* s, int32_t* n_active, int32_t* n_queued) 
       if (st != OPT_OK) return counts(fail_active(s, st));
       s->dirty = false;
     }
-    batch_enqueue_lm_round(s->batch, s->prm, s->st);
+    // One round when requests are waiting (they are admitted at the next
+    // step); otherwise as many rounds as the admitted request closest to its
+    // iteration cap has left (at most max_rounds), so that a lightly loaded
+    // server does not synchronise after every outer iteration.  A member that
+    // converges earlier idles through the remaining rounds (its kernels skip
+    // finished problems).
+    int rounds = 1, cap = 1;
+    bool waiting;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      waiting = !s->queue.empty();
+      cap = s->max_rounds;
+    }
+    if (!waiting && cap > 1) {
+      int left = cap;
+      for (const ServeReq* r : s->active) left = std::min(left, s->prm.outer - r->outer_seen);
+      rounds = std::max(1, left);
+    }
+    if (batch_reserve_rounds(s->batch, rounds) != OPT_OK) rounds = 1;
+    for (int k = 0; k < rounds; ++k) batch_enqueue_lm_round(s->batch, s->prm, s->st, k);
     if (cudaGetLastError() != cudaSuccess) return counts(fail_active(s, OPT_ERR_CUDA));
-    s->sbuf.resize(s->active.size());
-    opt_status st = batch_read_scalars(s->batch, s->sbuf.data(), s->st);
+    const size_t n = s->active.size();
+    s->sbuf.resize(n);
+    s->rbuf.resize((size_t)rounds * n);
+    opt_status st = batch_read_scalars(s->batch, s->sbuf.data(), s->rbuf.data(), rounds, s->st);
     if (st != OPT_OK) return counts(fail_active(s, st));
-    // 3. retire converged / capped members
+    // 3. the energies of the rounds each member ran; retire converged / capped members
     std::vector<ServeReq*> keep;
-    for (size_t i = 0; i < s->active.size(); ++i) {
+    for (size_t i = 0; i < n; ++i) {
       ServeReq* r = s->active[i];
       const Scalars& t = s->sbuf[i];
-      r->hist.push_back(t.E);
+      const int live = std::min(rounds, std::max(0, t.outer_done - r->outer_seen));
+      for (int k = 0; k < live; ++k) r->hist.push_back(s->rbuf[(size_t)k * n + i].E);
+      r->outer_seen = t.outer_done;
       const bool capped = t.outer_done >= s->prm.outer;
       if (!t.done && !capped && !t.nonfinite && !t.timeout && !t.misaligned) {
         keep.push_back(r);
         continue;
       }
-      const double Ef = t.accept ? t.E_trial : t.E;
+      // the final energy: after the member's last decision
+      const RoundRec last = live > 0 ? s->rbuf[(size_t)(live - 1) * n + i]
+                                     : RoundRec{t.E, t.E_trial, t.accept, t.outer_done};
+      if (live == 0) r->hist.push_back(t.E);
+      const double Ef = last.accept ? last.E_trial : last.E;
       r->hist.push_back(Ef);
       r->rep.outer_done = t.outer_done;
       r->rep.pcg_done = t.pcg_iters;
@@ -292,6 +324,13 @@ opt_status opt_server_inject_rebuild_failure(opt_server* s, opt_status status) {
   if (!s || status == OPT_OK) return OPT_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
   s->inject = status;
+  return OPT_OK;
+}
+
+opt_status opt_server_set_max_rounds(opt_server* s, int32_t max_rounds) {
+  if (!s || max_rounds < 1 || max_rounds > kServeMaxRounds) return OPT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->max_rounds = max_rounds;
   return OPT_OK;
 }
 

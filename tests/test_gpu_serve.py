@@ -56,10 +56,14 @@ def check_same(prob, rep, x, ref, xref):
     assert d <= (1e-4 if prob.kind == "mesh" else 1e-6)
 
 
-def test_serve_alone_equals_mix(api):
+@pytest.mark.parametrize("max_rounds", [1, 16])
+def test_serve_alone_equals_mix(api, max_rounds):
+    """Requests joining while others run equal their solo solves, with one
+    LM outer iteration per step and with up to 16 per step when nothing
+    waits (the energy history then comes from the per-round records)."""
     probs = requests()
     refs = [solo(api, p) for p in probs]
-    srv = api.Server(4 << 30, outer=OUTER, inner=INNER, rel_tol=REL_TOL)
+    srv = api.Server(4 << 30, outer=OUTER, inner=INNER, rel_tol=REL_TOL, max_rounds=max_rounds)
     tickets = [srv.submit(p) for p in probs[:5]]
     srv.step()
     srv.step()
@@ -145,6 +149,10 @@ def test_serve_max_active_caps_admission_in_arrival_order(api):
     with pytest.raises(api.OptError) as ei:
         srv.set_max_active(-1)
     assert ei.value.status == 1
+    for bad in (0, 65):
+        with pytest.raises(api.OptError) as ei:
+            srv.set_max_rounds(bad)
+        assert ei.value.status == 1
     srv.close()
 
 
