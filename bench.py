@@ -52,6 +52,7 @@ BYTES_FUSED_WARP = 120     # read z 12, w 12, p_old 12, cos/sin 8, UrShape 8, M^
 #                            write z 12, w 12, p 12, delta 12
 BYTES_FIN_WARP = 36        # the last iteration's step: read delta 12, p 12; write delta 12
 PCG_FORM = 1               # the headline's PCG iteration: 1 single-reduction, 0 two-pass
+SERVE_MAX_ROUNDS = 16      # served arm: LM outer iterations per server step when no request waits
 # Poisson, per free pixel (4 channels, one M^-1 plane)
 BYTES_APPLY_POISSON = 69   # read r 16, M^-1 4, p_old 16, mask 1; write p 16, q 16
 BYTES_UPDATE_POISSON = 100  # read delta 16, p 16, r 16, q 16, M^-1 4; write delta 16, r 16
@@ -619,7 +620,8 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, 
 
     def served(cap, pick, arrivals):
         n = len(pick)
-        srv = api.Server(budget, outer=OUT, inner=INN, rel_tol=TOL, max_active=cap, pcg_form=PCG_FORM)
+        srv = api.Server(budget, outer=OUT, inner=INN, rel_tol=TOL, max_active=cap, pcg_form=PCG_FORM,
+                         max_rounds=SERVE_MAX_ROUNDS)
         # warm-up: one request of each template kind
         for t in (0, len(warps)):
             tk = srv.submit_template(templates[t])
@@ -698,6 +700,7 @@ def bench_serving(api, synth, torch, n_req=2000, rate=2000.0, budget=120 << 30, 
     details = {"template": [int(t) for t in pick], "served": [done_c[i] for i in range(n_req)],
                "plain": [plain_done[i] for i in range(n_req)]}
     return details, {"requests": n_req, "rate_per_s": rate, "budget_gb": budget / 2 ** 30, "rounds": rounds,
+            "served_max_rounds_per_step": SERVE_MAX_ROUNDS,
             "input_path": "both arms plan every request from device-resident templates",
             "served_solves_per_s": n_req / span_served, "served_p50_ms": 1e3 * pct(L, 50),
             "served_p99_ms": 1e3 * pct(L, 99),
