@@ -124,7 +124,12 @@ __global__ void __launch_bounds__(NT) k_ed_init_v(const MeshProb* __restrict__ p
 
 // Gather pass: J^T F, diag(J^T J), the energy of the vertex's own rows
 // (out-edges, constraints, fit), then b = -J^T F, M^-1, r = b, delta = 0.
-__global__ void __launch_bounds__(NT) k_ed_init_pull(const MeshProb* __restrict__ probs,
+// resident blocks per SM the gather PCGInit is compiled for (64 registers, a
+// few spills that stay in L1; measured against 2 and 3 at level 9: 362 / 393 -> 355 us)
+#ifndef ED_INIT_MIN_BLOCKS
+#define ED_INIT_MIN_BLOCKS 4
+#endif
+__global__ void __launch_bounds__(NT, ED_INIT_MIN_BLOCKS) k_ed_init_pull(const MeshProb* __restrict__ probs,
                                                      const Chunk* __restrict__ chunks,
                                                      double* __restrict__ part, int k_outer, float dmin,
                                                      float dmax) {

@@ -125,8 +125,13 @@ __global__ void __launch_bounds__(NT) k_mesh_init_v(const MeshProb* __restrict__
 // their angle rows, incoming edge residuals), diag(J^T J) (displacement:
 // planned w_reg * degree + w_fit; angles: sum |g_m|^2 over the out-edges),
 // the energy of the own residuals, then b = -J^T F, M^-1, r = b, delta = 0.
+// resident blocks per SM the gather PCGInit is compiled for (85 registers;
+// measured against 2 and 4: level-9 PCGInit 330 -> 316 us, level 7 39.8 -> 36.1 us)
+#ifndef MESH_INIT_MIN_BLOCKS
+#define MESH_INIT_MIN_BLOCKS 3
+#endif
 template <bool G3>
-__global__ void __launch_bounds__(NT) k_mesh_init_pull(const MeshProb* __restrict__ probs,
+__global__ void __launch_bounds__(NT, MESH_INIT_MIN_BLOCKS) k_mesh_init_pull(const MeshProb* __restrict__ probs,
                                                        const Chunk* __restrict__ chunks,
                                                        double* __restrict__ part, int k_outer, float dmin,
                                                        float dmax) {
