@@ -1,19 +1,29 @@
 // Matrix-free grid kernels (Sec. 4.1 "Stencil-based Array Access").
 //
-// One block per chunk of 32x8 tiles.  Each tile is staged with a one-pixel
-// halo in shared memory (the 5-point stencil of Fig. 24 / Fig. 27), then one
-// thread computes the output rows of one pixel in gather form: the residuals
-// centred at the pixel ("own") and the residuals of the four neighbours that
-// reach it ("incoming") -- the set the paper's stencil JTJ generator finds by
-// shifting the residual template (Sec. 5.3.1, Fig. 10).
+// One block per chunk of tiles (32 x 8 pixels, or 128 x 8 for grids at least
+// 128 pixels wide).  Each tile is staged with a one-pixel halo in shared
+// memory (the 5-point stencil of Fig. 24 / Fig. 27), then one thread computes
+// the output rows of its pixels in gather form: the residuals centred at the
+// pixel ("own") and the residuals of the four neighbours that reach it
+// ("incoming") -- the set the paper's stencil JTJ generator finds by shifting
+// the residual template (Sec. 5.3.1, Fig. 10).
 //
-//   k_grid_init   PCGInit: F, b = -J^T F, diag(J^T J), M^-1, r = b, p = z = M^-1 r,
-//                 delta = 0, float64 r.z and E                     (Sec. 4.2 evalJTF)
-//   k_grid_apply  PCGStep1: p = z + beta p (from r, M^-1, p_old, halo included),
-//                 q = (J^T J + lambda D) p, float64 p.q -> alpha   (Sec. 4.2 applyJTJ)
-//   k_grid_update PCGStep2: delta += alpha p, r -= alpha q, z = M^-1 r, float64 r.z -> beta
-//   k_grid_energy E(x) (evalF) or, for LM, E(x + delta) and |F(x) + J(x) delta|^2
-//   k_grid_step   x += delta (GN always, LM when the step was accepted)
+//   PCGInit (Sec. 4.2 evalJTF): F, b = -J^T F, diag(J^T J), M^-1, r = b,
+//     delta = 0, float64 r.z and E        k_warp_init(_wide), k_poisson_init(_wide)
+//   Two-pass PCG iteration (Sec. 4.1, 4.2):
+//     applyJTJ with the direction p = z + beta p_old (halo included),
+//     q = (J^T J + lambda D) p, float64 p.q -> alpha
+//                                          k_warp_apply(_wide), k_poisson_apply(_wide)
+//     vector update delta += alpha p, r -= alpha q, z = M^-1 r, float64 r.z -> beta
+//                                          k_grid_update
+//   Single-reduction PCG iteration (128-pixel tiles): the update of the
+//     previous iteration, the direction, applyJTJ and p.q, q.z, q.M^-1 q, r.z
+//     in one launch                        k_warp_fused_wide, k_poisson_fused_wide,
+//                                          k_grid_fused_fin (the last step)
+//   Energies: E(x) (evalF) or, for LM, E(x + delta) and |F(x) + J(x) delta|^2
+//                                          k_warp_energy, k_poisson_energy
+//   Outer update: x += delta (GN always, LM when the step was accepted)
+//                                          k_grid_step
 //
 // ARAP warp algebra (unknown displacement d = O - U, v = U_k - U_{k+d}):
 //   r_{k,d}  = s_w [(d_k - d_{k+d}) + (v - R(t_k) v)]                  (= Fig. 24)
