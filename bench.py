@@ -57,8 +57,8 @@ SERVE_MAX_ROUNDS = 16      # served arm: LM outer iterations per server step whe
 BYTES_APPLY_POISSON = 69   # read r 16, M^-1 4, p_old 16, mask 1; write p 16, q 16
 BYTES_UPDATE_POISSON = 100  # read delta 16, p 16, r 16, q 16, M^-1 4; write delta 16, r 16
 BYTES_INIT_POISSON = 69    # read X 16, T 16, mask 1; write r 16, M^-1 4, delta 16 (GN)
-BYTES_FUSED_POISSON = 133  # single-reduction iteration: read z, w, p_old 48, degree 1, M^-1 4, delta 16;
-#                            write z, w, p, delta 64
+BYTES_FUSED_POISSON = 129  # single-reduction iteration (GN): read z, w, p_old 48, degree 1, delta 16 (M^-1 follows
+#                            from the degree byte); write z, w, p, delta 64
 BYTES_FIN_POISSON = 48     # the last iteration's step: read delta 16, p 16; write delta 16
 # ARAP mesh, per vertex (6 unknowns, 6 directed edges per vertex on an icosphere): the
 # algorithmic bytes of the method, each array touched once, records and padding the

@@ -344,13 +344,15 @@ opt_status opt_profile_pcg_fused(opt_problem* prob, int32_t n_iters, void* strea
  * Drops the cached solve graph.  Synchronises the device. */
 opt_status opt_problem_set_chunking(opt_problem* prob, int32_t units_per_block);
 
-/* Autotuner: times applyJTJ + vector update (opt_profile_pcg) for each
+/* Autotuner: times one PCG iteration -- the single-reduction iteration
+ * (opt_profile_pcg_fused) on warp and Poisson layouts with 128-pixel tiles,
+ * applyJTJ + vector update (opt_profile_pcg) elsewhere -- for each
  * candidate granularity {-1, -2, -3, -4, -6, -8, 1, 4} (see
  * opt_problem_set_chunking) and, beside it, each apply form of an ARAP mesh
  * with tile tables and each tile width (32, 128) of a grid (see
  * opt_problem_get_config); keeps the fastest combination and returns its
  * granularity in *chosen and its per-iteration time in *best_ms (host, either
- * may be NULL).  Leaves the PCG state as opt_profile_pcg does.  A grid whose
+ * may be NULL).  Leaves the PCG state of its last timed run.  A grid whose
  * other tile width wins is re-planned in place: autotune a problem before
  * building a batch over it, not while a batch holds it. */
 opt_status opt_problem_autotune(opt_problem* prob, int32_t* chosen, float* best_ms);

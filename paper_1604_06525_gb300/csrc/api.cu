@@ -1581,19 +1581,27 @@ opt_status opt_problem_set_chunking(opt_problem* prob, int32_t units_per_block) 
   return rechunk(prob, units_per_block);
 }
 
-// Best granularity of a problem's current layout and apply form: the
-// summed applyJTJ + vector-update time of a short PCG run.
+// Best granularity of a problem's current layout and apply form: the time of
+// one PCG iteration in a short run -- the single-reduction iteration where
+// the layout has it (warp and Poisson on 128-pixel tiles), else applyJTJ +
+// vector update.
 static opt_status tune_granularity(opt_problem* prob, int* best, float* bms) {
   // balanced splits with 1..8 blocks per SM, and fixed runs of 1 and 4 units
   const int cand[] = {-1, -2, -3, -4, -6, -8, 1, 4};
+  const bool fused = is_grid(prob) && (prob->kind == K_WARP || prob->kind == K_POISSON) && prob->hg.zb;
   *best = 0;
   *bms = 1e30f;
   for (int c : cand) {
     CKS(rechunk(prob, c));
     float ms[3];
-    CKS(opt_profile_pcg(prob, 4, nullptr, ms));
-    CKS(opt_profile_pcg(prob, 8, nullptr, ms));
-    const float t = ms[1] + ms[2];
+    if (fused) {
+      CKS(opt_profile_pcg_fused(prob, 4, nullptr, ms));
+      CKS(opt_profile_pcg_fused(prob, 8, nullptr, ms));
+    } else {
+      CKS(opt_profile_pcg(prob, 4, nullptr, ms));
+      CKS(opt_profile_pcg(prob, 8, nullptr, ms));
+    }
+    const float t = fused ? ms[1] : ms[1] + ms[2];
     if (t < *bms) {
       *bms = t;
       *best = c;

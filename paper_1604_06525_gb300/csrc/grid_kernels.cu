@@ -2552,9 +2552,10 @@ __global__ void __launch_bounds__(NT, 2) k_poisson_init_wide(const GridProb* __r
 // tile's copies overlap phase 3, the stencil of k_poisson_apply_wide (the
 // directions vanish off the free pixels: q = S p - 2 (p_L + p_R + p_U + p_D)
 // per channel, LM damping on the free pixels), w = M^-1 q and the four
-// compensated dot products.  Per pixel of an active tile: read z, w, p_old
-// 48, degree byte 1, M^-1 4, delta 16; write z, w, p, delta 64 = 133 B
-// (two-pass: 69 + 100 B).
+// compensated dot products (M^-1 of the own pixels from the degree bytes
+// under Gauss-Newton).  Per pixel of an active tile: read z, w, p_old 48,
+// degree byte 1, M^-1 4 (LM), delta 16; write z, w, p, delta 64 = 133 B (GN:
+// 129 B; two-pass: 69 + 100 B).
 // ---------------------------------------------------------------------------
 constexpr int NRAW_PF = 12;      // z0..z3 w0..w3 p0..p3 (iteration 0: r0..r3 at 0..3, M^-1 at 4)
 constexpr int NSTG_PF = 4;       // p0..p3, each quad stored as pixels 0 2 1 3
@@ -2693,9 +2694,20 @@ __device__ __forceinline__ void pois_fused_body(PoisFusedSmem& sm, const Chunk& 
       const float2 dA = mul2(lam2, lo2(dd)), dB = mul2(lam2, hi2(dd));
       // w = M^-1 q and the four inner products (swizzled packs: A = pixels
       // {0, 2}, B = {1, 3}); z of the own pixels comes back from the stores
-      // of phase 2 (this thread's own writes)
-      const float4 ms = swz4(ld4(pr.m + i));
-      const float4 rc = rcp4(ms);
+      // of phase 2 (this thread's own writes).  Under Gauss-Newton M^-1 and
+      // the diagonal (r = diag z) follow from the degree bytes: diag = S, M^-1
+      // = 1 / S, the values PCGInit wrote (1 where S = 0 or without the
+      // preconditioner); under LM the damping enters, so M^-1 is read.
+      float4 ms, rc;
+      if (!pr.lm) {
+        auto inv = [&](float v) { return pr.use_precond && v > 0.f ? __frcp_rn(v) : 1.f; };
+        auto dg = [&](float v) { return pr.use_precond && v > 0.f ? v : 1.f; };
+        ms = make_float4(inv(S.x), inv(S.y), inv(S.z), inv(S.w));
+        rc = make_float4(dg(S.x), dg(S.y), dg(S.z), dg(S.w));
+      } else {
+        ms = swz4(ld4(pr.m + i));
+        rc = rcp4(ms);
+      }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const float2 a = mul2(lo2(fo), fma2(dA, lo2(O[k]), qA[k]));
