@@ -168,6 +168,42 @@ def test_fused_full_size_configuration(api):
         assert relE(a, b) <= 1e-5
 
 
+@pytest.mark.parametrize("kind,W,H", [("warp", 32767, 1), ("warp", 32767, 2), ("warp", 128, 1), ("warp", 133, 3),
+                                      ("poisson", 4099, 2), ("poisson", 300, 3)])
+def test_fused_extreme_extents(api, kind, W, H):
+    """Grids of one row of 128-pixel tiles, below one tile's height (down to
+    a single pixel row), up to the widest extent the planner accepts: GN
+    2 x 5 with the single-reduction iteration, energies against the oracle
+    and the same PCG iteration count."""
+    prob = synth.warp_problem(W, H, 20, seed=5) if kind == "warp" else synth.poisson_problem(W, H, seed=4)
+    e = oracle.make_energy(prob)
+    ref = oracle.gauss_newton(e, prob.x0.reshape(-1).astype(np.float64), 2, 5)
+    gp = api.Problem(prob)
+    assert gp.config()["tile_w"] == 128
+    rep = gp.solve_gn(2, 5, pcg_form=1)
+    assert rep["status"] == "OPT_OK" and rep["pcg_done"] == ref.pcg_done
+    for k, (a, b) in enumerate(zip(rep["E_history"], ref.E_history)):
+        assert relE(a, b) <= TOL_ENERGY, (k, a, b)
+    gp.close()
+
+
+def test_fused_all_pixels_excluded_or_fixed(api):
+    """Every warp pixel masked or every Poisson pixel fixed, on 128-pixel
+    tiles: r = 0, the first iteration breaks down (p.q = 0) with no step,
+    E = 0 and nothing moves."""
+    w = synth.warp_problem(130, 8, 0, seed=5, mask=np.ones((8, 130), np.uint8))
+    p = synth.poisson_problem(140, 10, seed=4)
+    p.mask = np.ones((10, 140), np.uint8)
+    for prob in (w, p):
+        gp = api.Problem(prob)
+        assert gp.config()["tile_w"] == 128
+        rep = gp.solve_gn(2, 5, pcg_form=1)
+        assert rep["status"] == "OPT_OK"
+        assert rep["E_history"] == [0.0, 0.0, 0.0] and rep["pcg_done"] == 0
+        np.testing.assert_array_equal(gp.x.cpu().numpy(), prob.x0)
+        gp.close()
+
+
 def test_fused_form_on_other_problems_runs_two_pass(api):
     """pcg_form = 1 on problems the form does not cover (32-pixel tiles) runs
     the two-pass iteration: bit-identical results."""
